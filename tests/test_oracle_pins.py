@@ -1,0 +1,353 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against mathematics the paper states or relies on:
+closed-form nodes and weights, Gauss exactness, the node-distance bounds of
+Lemma 2.3, the change of basis P = T M of Sec. 3, the discrete orthogonality of
+Sec. 4, exact error-free transformations, and an independent multiprecision
+library where one is available.  A dropped term, a wrong sign or index, or a
+transposed operand in any oracle function fails at least one of them.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+rng = np.random.default_rng(12345)
+
+
+# --------------------------------------------------------------------------
+# double-double arithmetic
+# --------------------------------------------------------------------------
+def test_two_prod_two_sum_exact(orc):
+    for _ in range(200):
+        a, b = rng.standard_normal(2) * 10.0 ** rng.integers(-20, 20, 2)
+        hi, lo = orc.two_prod(a, b)
+        assert Fraction(hi) + Fraction(lo) == Fraction(a) * Fraction(b)
+        hi, lo = orc.two_sum(a, b)
+        assert Fraction(hi) + Fraction(lo) == Fraction(a) + Fraction(b)
+
+
+def test_dd_div_sqrt(orc):
+    for _ in range(100):
+        a = (float(rng.standard_normal()), float(rng.standard_normal()) * 1e-17)
+        b = (float(rng.uniform(0.5, 3.0)), float(rng.standard_normal()) * 1e-17)
+        q = orc.dd_div(a, b)
+        A = Fraction(a[0]) + Fraction(a[1])
+        B = Fraction(b[0]) + Fraction(b[1])
+        Q = Fraction(q[0]) + Fraction(q[1])
+        assert abs(float((Q - A / B) / (A / B))) < 1e-30
+        s = orc.dd_sqrt((abs(a[0]), 0.0))
+        S = Fraction(s[0]) + Fraction(s[1])
+        assert abs(float((S * S - Fraction(abs(a[0]))) / Fraction(abs(a[0])))) < 1e-30
+
+
+def test_sincos_dd(orc):
+    # sin^2 + cos^2 = 1 to dd accuracy, and agreement with a multiprecision library
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for _ in range(50):
+        t = float(rng.uniform(0.0, math.pi))
+        (sh, sl), (ch, cl) = orc.sincos_dd(t, 0.0)
+        S = Fraction(sh) + Fraction(sl)
+        C = Fraction(ch) + Fraction(cl)
+        assert abs(float(S * S + C * C - 1)) < 1e-30
+        assert abs(float(mp.mpf(sh) + mp.mpf(sl) - mp.sin(mp.mpf(t)))) < 1e-30
+        assert abs(float(mp.mpf(ch) + mp.mpf(cl) - mp.cos(mp.mpf(t)))) < 1e-30
+
+
+# --------------------------------------------------------------------------
+# polynomials
+# --------------------------------------------------------------------------
+def test_legendre_endpoints(orc):
+    for n in [0, 1, 2, 7, 64, 1000, 4097]:
+        assert orc.legendre_p(n, [1.0])[0] == pytest.approx(1.0, abs=1e-14)
+        assert orc.legendre_p(n, [-1.0])[0] == pytest.approx((-1.0) ** n, abs=1e-14)
+
+
+def test_legendre_closed_forms(orc):
+    x = rng.uniform(-1, 1, 64)
+    closed = {
+        0: np.ones_like(x),
+        1: x,
+        2: (3 * x**2 - 1) / 2,
+        3: (5 * x**3 - 3 * x) / 2,
+        4: (35 * x**4 - 30 * x**2 + 3) / 8,
+        5: (63 * x**5 - 70 * x**3 + 15 * x) / 8,
+    }
+    for n, ref in closed.items():
+        np.testing.assert_allclose(orc.legendre_p(n, x), ref, rtol=0, atol=2e-15)
+
+
+def test_legendre_vs_mpmath(orc):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    x = rng.uniform(-1, 1, 8)
+    for n in [50, 777, 3000]:
+        got = orc.legendre_p(n, x)
+        ref = np.array([float(mp.legendre(n, mp.mpf(v))) for v in x])
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-15)
+
+
+def test_chebyshev_is_cos(orc):
+    t = rng.uniform(0, math.pi, 64)
+    for n in [0, 1, 2, 5, 33]:
+        np.testing.assert_allclose(orc.chebyshev_t(n, np.cos(t)), np.cos(n * t), atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# nodes and weights
+# --------------------------------------------------------------------------
+CLOSED_NODES = {
+    1: ([0.0], [2.0]),
+    2: ([1 / math.sqrt(3), -1 / math.sqrt(3)], [1.0, 1.0]),
+    3: ([math.sqrt(3 / 5), 0.0, -math.sqrt(3 / 5)], [5 / 9, 8 / 9, 5 / 9]),
+    4: (
+        [math.sqrt(3 / 7 + 2 / 7 * math.sqrt(6 / 5)), math.sqrt(3 / 7 - 2 / 7 * math.sqrt(6 / 5)),
+         -math.sqrt(3 / 7 - 2 / 7 * math.sqrt(6 / 5)), -math.sqrt(3 / 7 + 2 / 7 * math.sqrt(6 / 5))],
+        [(18 - math.sqrt(30)) / 36, (18 + math.sqrt(30)) / 36,
+         (18 + math.sqrt(30)) / 36, (18 - math.sqrt(30)) / 36],
+    ),
+    5: (
+        [math.sqrt(5 + 2 * math.sqrt(10 / 7)) / 3, math.sqrt(5 - 2 * math.sqrt(10 / 7)) / 3, 0.0,
+         -math.sqrt(5 - 2 * math.sqrt(10 / 7)) / 3, -math.sqrt(5 + 2 * math.sqrt(10 / 7)) / 3],
+        [(322 - 13 * math.sqrt(70)) / 900, (322 + 13 * math.sqrt(70)) / 900, 128 / 225,
+         (322 + 13 * math.sqrt(70)) / 900, (322 - 13 * math.sqrt(70)) / 900],
+    ),
+}
+
+
+@pytest.mark.parametrize("N", sorted(CLOSED_NODES))
+def test_legpts_closed_forms(orc, N):
+    nd = orc.legpts(N)
+    x_ref, w_ref = CLOSED_NODES[N]
+    np.testing.assert_allclose(nd.x, x_ref, atol=1e-15)
+    np.testing.assert_allclose(nd.w, w_ref, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [37, 100])
+def test_legpts_vs_scipy(orc, N):
+    sp = pytest.importorskip("scipy.special")
+    xs, ws = sp.roots_legendre(N)
+    nd = orc.legpts(N)
+    np.testing.assert_allclose(nd.x, xs[::-1], atol=4e-16)
+    # scipy's weights carry about 1e-12 relative error (its nodes are better)
+    np.testing.assert_allclose(nd.w, ws[::-1], rtol=1e-11)
+
+
+@pytest.mark.parametrize("degree", [2, 4, 6])
+def test_legpts_vs_mpmath_gauss_legendre(orc, degree):
+    """mpmath's own Gauss-Legendre rule (3 * 2^(degree-1) points, 40 digits)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    rule = mp.calculus.quadrature.GaussLegendre(mp.mp).calc_nodes(degree, mp.mp.prec)
+    rule = sorted(rule, key=lambda t: -t[0])
+    N = len(rule)
+    nd = orc.legpts(N)
+    for k, (xr, wr) in enumerate(rule):
+        x = mp.mpf(nd["x_hi"][k]) + mp.mpf(nd["x_lo"][k])
+        w = mp.mpf(nd["w_hi"][k]) + mp.mpf(nd["w_lo"][k])
+        assert abs(x - xr) < mp.mpf("1e-26"), (N, k)
+        assert abs(w - wr) < mp.mpf("1e-26") * wr, (N, k)
+
+
+@pytest.mark.parametrize("N", [6, 64, 255, 1024])
+def test_gauss_exactness(orc, N):
+    nd = orc.legpts(N)
+    assert abs(nd.w.sum() - 2.0) < 1e-14
+    np.testing.assert_allclose(nd.x, -nd.x[::-1], atol=1e-16)
+    np.testing.assert_allclose(nd.w, nd.w[::-1], rtol=1e-14)
+    for j in sorted({0, 1, 2, 3, N - 1, N, 2 * N - 2, 2 * N - 1}):
+        got = float(np.dot(nd.w, orc.legendre_p(j, nd.x)))
+        assert got == pytest.approx(2.0 if j == 0 else 0.0, abs=5e-15), (N, j)
+    # degree 2N is no longer integrated exactly: the weights are not a trivially
+    # "right" answer for every degree
+    got = float(np.dot(nd.w, orc.legendre_p(2 * N, nd.x)))
+    assert abs(got) > 1e-6
+
+
+@pytest.mark.parametrize("N", [8, 33, 1000, 4096])
+def test_lemma_2_3_bounds(orc, N):
+    """Lemma 2.3: 0 < theta^leg_k - theta^cheb*_k <= 1/(3pi(2N+1)) for k < N/2 and
+    |theta^leg_k - theta^cheb1_k| <= (3pi^2+2)/(6pi(2N+1)) <= 0.83845/N."""
+    nd = orc.legpts(N)
+    k = np.arange(N)
+    th_star = (k + 0.75) * np.pi / (N + 0.5)
+    d_star = nd.theta - th_star
+    half = N // 2
+    assert np.all(d_star[:half] > 0)
+    assert np.all(np.abs(d_star) <= 1 / (3 * np.pi * (2 * N + 1)) * (1 + 1e-12))
+    bound1 = (3 * np.pi**2 + 2) / (6 * np.pi * (2 * N + 1))
+    assert np.all(np.abs(nd["dtheta"]) <= bound1 * (1 + 1e-12))
+    assert bound1 <= 0.83845 / N
+    # dtheta is theta - (k+1/2)pi/N
+    np.testing.assert_allclose(nd["dtheta"], nd.theta - (k + 0.5) * np.pi / N, atol=1e-15)
+
+
+def test_lemma_2_3_tight(orc):
+    """Fig. 2 reports the bounds of Lemma 2.3 as tight."""
+    N = 4096
+    nd = orc.legpts(N)
+    k = np.arange(N)
+    r1 = np.max(np.abs(nd["dtheta"])) / ((3 * np.pi**2 + 2) / (6 * np.pi * (2 * N + 1)))
+    rs = np.max(np.abs(nd.theta - (k + 0.75) * np.pi / (N + 0.5))) * 3 * np.pi * (2 * N + 1)
+    assert 0.98 < r1 <= 1.0
+    assert 0.85 < rs <= 1.0
+
+
+def test_legpts_sampled_large(orc):
+    """Sampled nodes at N = 2^20 obey Lemma 2.3 and are roots of P_N."""
+    N = 2**20
+    ks = np.array([0, 1, 2, 17, 4097, N // 2 - 1, N // 2, N - 1], dtype=np.int64)
+    nd = orc.legpts(N, ks)
+    assert np.all(np.abs(nd["dtheta"]) * N <= 0.83845)
+    # symmetry: theta_{N-1-k} = pi - theta_k
+    a = orc.legpts(N, np.array([3], dtype=np.int64))
+    b = orc.legpts(N, np.array([N - 4], dtype=np.int64))
+    assert abs((a.theta[0] + b.theta[0]) - math.pi) < 1e-15
+    assert abs(a.w[0] - b.w[0]) < 1e-15 * a.w[0]
+
+
+# --------------------------------------------------------------------------
+# DLT / IDLT / NDCT definitions
+# --------------------------------------------------------------------------
+def test_dlt_unit_vectors(orc):
+    N = 64
+    nd = orc.legpts(N)
+    for n in [0, 1, 5, N - 1]:
+        e = np.zeros(N)
+        e[n] = 1.0
+        np.testing.assert_allclose(orc.dlt_rows(e, nd), orc.legendre_p(n, nd.x), atol=2e-15)
+    np.testing.assert_allclose(orc.dlt_rows(np.eye(N)[0], nd), np.ones(N), atol=0)
+
+
+def test_dlt_closed_form_n3(orc):
+    nd = orc.legpts(3)
+    c = rng.standard_normal(3)
+    x = np.array(CLOSED_NODES[3][0])
+    ref = c[0] + c[1] * x + c[2] * (3 * x**2 - 1) / 2
+    np.testing.assert_allclose(orc.dlt_rows(c, nd), ref, atol=1e-15)
+
+
+def test_dlt_linear(orc):
+    N = 100
+    nd = orc.legpts(N)
+    a, b = rng.standard_normal(N), rng.standard_normal(N)
+    np.testing.assert_allclose(orc.dlt_rows(2 * a - 3 * b, nd),
+                               2 * orc.dlt_rows(a, nd) - 3 * orc.dlt_rows(b, nd), atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 256, 1024])
+def test_idlt_inverts_dlt(orc, N):
+    nd = orc.legpts(N)
+    c = rng.standard_normal(N)
+    f = orc.dlt_rows(c, nd)
+    np.testing.assert_allclose(orc.idlt(f, nd), c, atol=2e-14)
+
+
+def test_idlt_simple_functions(orc):
+    N = 50
+    nd = orc.legpts(N)
+    e0 = np.zeros(N)
+    e0[0] = 1
+    e1 = np.zeros(N)
+    e1[1] = 1
+    np.testing.assert_allclose(orc.idlt(np.ones(N), nd), e0, atol=1e-15)
+    np.testing.assert_allclose(orc.idlt(nd.x, nd), e1, atol=1e-15)
+
+
+def test_discrete_orthogonality(orc):
+    """Sec. 4: P^T D_w P = D_s^{-1}, s_n = n + 1/2."""
+    N = 40
+    nd = orc.legpts(N)
+    for j in [0, 3, N - 1]:
+        e = np.zeros(N)
+        e[j] = 1
+        col = orc.dlt_t(nd.w * orc.dlt_rows(e, nd), nd)
+        ref = np.zeros(N)
+        ref[j] = 1 / (j + 0.5)
+        np.testing.assert_allclose(col, ref, atol=1e-15)
+
+
+def test_ndct_unit_vectors(orc):
+    N = 128
+    nd = orc.legpts(N)
+    for n in [0, 1, 2, 77, N - 1]:
+        e = np.zeros(N)
+        e[n] = 1
+        np.testing.assert_allclose(orc.ndct_rows(e, nd), np.cos(n * nd.theta), atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Legendre -> Chebyshev matrix M (Sec. 3)
+# --------------------------------------------------------------------------
+def test_m_small_entries(orc):
+    M = orc.leg2cheb_matrix(6)
+    # P_2 = 1/4 T_0 + 3/4 T_2, P_3 = 3/8 T_1 + 5/8 T_3, P_1 = T_1, P_0 = T_0
+    np.testing.assert_allclose(M[:, 0], [1, 0, 0, 0, 0, 0], atol=1e-16)
+    np.testing.assert_allclose(M[:, 1], [0, 1, 0, 0, 0, 0], atol=1e-16)
+    np.testing.assert_allclose(M[:, 2], [0.25, 0, 0.75, 0, 0, 0], atol=1e-16)
+    np.testing.assert_allclose(M[:, 3], [0, 0.375, 0, 0.625, 0, 0], atol=1e-16)
+    assert np.all(np.tril(M, -1) == 0)
+
+
+def test_m_is_change_of_basis(orc):
+    """P_n(x) = sum_k M_{kn} T_k(x) with T_k(x) = cos(k arccos x)."""
+    N = 300
+    M = orc.leg2cheb_matrix(N)
+    x = rng.uniform(-1, 1, 20)
+    T = np.cos(np.outer(np.arccos(x), np.arange(N)))
+    for n in [0, 1, 2, 9, 150, N - 1]:
+        np.testing.assert_allclose(T @ M[:, n], orc.legendre_p(n, x), atol=1e-13)
+
+
+def test_leg2cheb_matches_matrix_and_transpose(orc):
+    N = 200
+    M = orc.leg2cheb_matrix(N)
+    c, y = rng.standard_normal(N), rng.standard_normal(N)
+    np.testing.assert_allclose(orc.leg2cheb(c), M @ c, atol=1e-13)
+    np.testing.assert_allclose(orc.leg2cheb_t(y), M.T @ y, atol=1e-13)
+
+
+def test_eq14_change_of_basis_on_nodes(orc):
+    """Eq. 14: sum_n c_n P_n(x_k) = sum_n chat_n T_n(x_k), chat = M c."""
+    N = 512
+    nd = orc.legpts(N)
+    c = rng.standard_normal(N)
+    np.testing.assert_allclose(orc.ndct_rows(orc.leg2cheb(c), nd), orc.dlt_rows(c, nd), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# transposes (adjoint identity)
+# --------------------------------------------------------------------------
+def test_adjoints(orc):
+    N = 96
+    nd = orc.legpts(N)
+    y, z = rng.standard_normal(N), rng.standard_normal(N)
+    assert np.dot(orc.leg2cheb(y), z) == pytest.approx(np.dot(y, orc.leg2cheb_t(z)), abs=1e-12)
+    assert np.dot(orc.ndct_rows(y, nd), z) == pytest.approx(np.dot(y, orc.ndct_t(z, nd)), abs=1e-12)
+    assert np.dot(orc.dlt_rows(y, nd), z) == pytest.approx(np.dot(y, orc.dlt_t(z, nd)), abs=1e-12)
+    # IDLT = D_s P^T D_w
+    s = np.arange(N) + 0.5
+    np.testing.assert_allclose(orc.idlt(z, nd), s * orc.dlt_t(nd.w * z, nd), atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Table 1 (the paper's printed numbers)
+# --------------------------------------------------------------------------
+def test_table1_values():
+    """The printed values of Table 1 equal 0.83845^L/L! and ((6pi)^L L!)^-1 to the
+    two digits shown, and the (3pi^2+2)/(12pi) constant of Lemma 2.3 rounds to
+    0.83845."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_taylor_bounds.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 18
+    for L, a, b in rows:
+        L = int(L)
+        va = 0.83845**L / math.factorial(L)
+        vb = 1.0 / ((6 * math.pi) ** L * math.factorial(L))
+        for printed, val in ((float(a), va), (float(b), vb)):
+            ulp = 10.0 ** (math.floor(math.log10(printed)) - 1)
+            assert abs(val - printed) <= 1.01 * ulp, (L, printed, val)
+    assert round((3 * math.pi**2 + 2) / (12 * math.pi), 5) == 0.83845
