@@ -1,0 +1,134 @@
+/*
+ * gbdlt: fast discrete Legendre transform on one GPU (GB300, sm_103a).
+ *
+ * The method is Hale & Townsend, "A fast FFT-based discrete Legendre
+ * transform": the DLT of Eq. (1) is computed as a Legendre -> Chebyshev
+ * coefficient conversion (Sec. 3; asymptotic expansion of P_n(cos theta) summed
+ * by DCT/DST over theta-bands, three-term recurrence where the expansion is not
+ * accurate) followed by the non-uniform DCT of Sec. 2 (Taylor series in
+ * delta-theta_k = theta^leg_k - theta^cheb1_k, each term one DCT or DST, Eq. 13).
+ * The IDLT of Eq. (2) is the transposed chain of Sec. 4,
+ * c = D_s M^T T_N^T(x^leg) D_w f with s_n = n + 1/2.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: GBDLT_OK (0) or a negative code.
+ *   - Pointers to vector data are DEVICE pointers unless a name says "host".
+ *     Data vectors are contiguous, [batch][N] row-major, element type given by
+ *     the plan precision: double for GBDLT_FP64, float for GBDLT_FP32.  Node
+ *     and weight arrays are always double.  Device data pointers must be
+ *     aligned to their element size (8 bytes for double, 4 for float).
+ *   - Inputs and outputs must not overlap unless a function says otherwise.
+ *   - batch == 0 is a no-op that returns GBDLT_OK without reading the data
+ *     pointers (they may be NULL); batch < 0 or a NULL data pointer with
+ *     batch > 0 returns GBDLT_ERR_INVALID_ARG.
+ *   - All work is enqueued on the plan's CUDA stream and is asynchronous; the
+ *     caller owns every input/output buffer, the plan owns its node cache,
+ *     tables and workspace.  gbdlt_plan_sync() waits for the stream and reports
+ *     device-side failures (for instance a node iteration that did not settle).
+ *   - N is the transform length: a power of two with 1 <= N <= 2^24.  Any
+ *     other N makes gbdlt_plan_create return GBDLT_ERR_UNSUPPORTED_N.
+ *   - A plan is not thread-safe: calls on one plan must be serialised.
+ */
+#ifndef GBDLT_H
+#define GBDLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbdlt_plan_s* gbdlt_plan;
+
+/* Arithmetic form.  GBDLT_FP64: every transform step in double.  GBDLT_FP32:
+ * DCT/DST transforms, asymptotic and Taylor combines in float (nodes, weights,
+ * delta-theta and the recurrence region stay in double); float data in/out. */
+enum { GBDLT_FP64 = 0, GBDLT_FP32 = 1 };
+
+enum {
+  GBDLT_OK = 0,
+  GBDLT_ERR_INVALID_ARG = -1,    /* null pointer, batch < 0, bad precision, ... */
+  GBDLT_ERR_UNSUPPORTED_N = -2,  /* N not a power of two or out of range      */
+  GBDLT_ERR_CUDA = -3,           /* a CUDA runtime call failed                */
+  GBDLT_ERR_OOM = -4,            /* device allocation failed                  */
+  GBDLT_ERR_NOT_CONVERGED = -5,  /* a node Newton iteration did not settle    */
+  GBDLT_ERR_UNIMPLEMENTED = -6
+};
+
+/* Parameters the plan derives from (N, precision, eps) by the error bounds of
+ * the paper (Table 1 / Corollary 2.4 for L) and of the asymptotic expansion of
+ * P_n(cos theta) (band cuts), choosing the cheapest feasible band layout. */
+#define GBDLT_MAX_BANDS 32
+typedef struct {
+  int64_t N;
+  int prec;
+  double eps;          /* target max|error| / ||c||_1                          */
+  int L;               /* Taylor terms (l = 0..L-1), Corollary 2.4             */
+  int M;               /* terms of the asymptotic expansion of P_n(cos theta)  */
+  int K;               /* number of theta-bands using the expansion            */
+  int64_t band_ns[GBDLT_MAX_BANDS]; /* column cut: band b uses n >= band_ns[b]  */
+  int64_t band_ka[GBDLT_MAX_BANDS]; /* rows [ka, kb) and [N-kb, N-ka)          */
+  int64_t band_kb[GBDLT_MAX_BANDS];
+  int64_t rec_steps;   /* recurrence (row, n) pairs, both halves              */
+  int seg_len;         /* recurrence segment length                           */
+  double flops_dlt;    /* modelled arithmetic per DLT (flop)                  */
+  double bytes_dlt;    /* algorithmic HBM bytes per DLT: read c, dtheta; write f */
+  double bytes_idlt;   /* same for the IDLT (adds the weights)                */
+  size_t workspace_bytes; /* device workspace the plan allocates              */
+} gbdlt_params;
+
+/* Host-only parameter derivation: no GPU, no allocation.  eps <= 0 selects the
+ * default (1e-14 for GBDLT_FP64, 2e-6 for GBDLT_FP32).  Returns
+ * GBDLT_ERR_UNSUPPORTED_N or GBDLT_ERR_INVALID_ARG on bad input. */
+int gbdlt_plan_params(int64_t N, int prec, double eps, gbdlt_params* out);
+
+/* Create a plan on the current CUDA device.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Computes the Legendre nodes and weights
+ * (gbdlt_legpts), the per-N tables and allocates the workspace.  On error *out
+ * is set to NULL and nothing is leaked. */
+int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_plan* out);
+int gbdlt_plan_destroy(gbdlt_plan plan);
+/* Change the stream later calls enqueue on. */
+int gbdlt_plan_set_stream(gbdlt_plan plan, void* cuda_stream);
+/* Wait for the plan's stream; returns GBDLT_ERR_NOT_CONVERGED if a node
+ * iteration failed since the last sync, GBDLT_ERR_CUDA on a CUDA error. */
+int gbdlt_plan_sync(gbdlt_plan plan);
+int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out);
+
+/* Legendre nodes and weights (Eq. 1 and Eq. 2; Sec. 2.1-2.2): recomputes the
+ * plan's node cache on the GPU and copies any requested array out.  Ordering:
+ * theta ascending, x = cos(theta) descending (1 > x_0 > ... > x_{N-1} > -1).
+ * Outputs (device, N doubles each, any may be NULL): x, theta, w (Gauss-Legendre
+ * weights), dtheta = theta_k - (k+1/2)pi/N (offset from the Chebyshev points of
+ * the first kind, Eq. 5). */
+int gbdlt_legpts(gbdlt_plan plan, double* x, double* theta, double* w, double* dtheta);
+
+/* Legendre -> Chebyshev coefficients (Sec. 3): chat = M c. */
+int gbdlt_leg2cheb(gbdlt_plan plan, const void* c, void* chat, int64_t batch);
+/* Transpose: out = M^T y (Sec. 4, item 3). */
+int gbdlt_leg2cheb_t(gbdlt_plan plan, const void* y, void* out, int64_t batch);
+/* Chebyshev expansion evaluated at the Legendre nodes, Eq. (3) (the NDCT of
+ * Sec. 2): f_k = sum_n chat_n T_n(x^leg_k). */
+int gbdlt_chebeval(gbdlt_plan plan, const void* chat, void* f, int64_t batch);
+/* Transpose (Sec. 4, item 2): out_n = sum_k g_k T_n(x^leg_k). */
+int gbdlt_chebeval_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
+/* DLT, Eq. (1): f_k = sum_n c_n P_n(x^leg_k). */
+int gbdlt_dlt(gbdlt_plan plan, const void* c, void* f, int64_t batch);
+/* Transposed DLT (Sec. 4): out_n = sum_k g_k P_n(x^leg_k). */
+int gbdlt_dlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
+/* IDLT, Eq. (2): c_n = (n + 1/2) sum_k w_k f_k P_n(x^leg_k). */
+int gbdlt_idlt(gbdlt_plan plan, const void* f, void* c, int64_t batch);
+/* Transposed IDLT: out = D_w P_N(x^leg) D_s g, i.e. out_k = w_k sum_n (n+1/2) g_n P_n(x_k). */
+int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
+
+/* Human-readable name of a status code (static string). */
+const char* gbdlt_status_string(int status);
+/* Number of kernels this library has launched since it was loaded (all plans,
+ * all threads). */
+uint64_t gbdlt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBDLT_H */

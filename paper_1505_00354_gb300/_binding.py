@@ -1,0 +1,272 @@
+"""ctypes binding of the gbdlt C ABI (include/gbdlt.h).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+library ``_lib/libgbdlt.so``.  There is no CPU fallback; if the library is
+missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+FP64 = 0
+FP32 = 1
+MAX_BANDS = 32
+
+STATUS = {
+    0: "ok",
+    -1: "invalid argument",
+    -2: "unsupported N",
+    -3: "CUDA error",
+    -4: "device allocation failed",
+    -5: "node iteration did not converge",
+    -6: "unimplemented",
+}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgbdlt.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class GbdltError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"gbdlt {where}: {STATUS.get(status, 'unknown')} ({status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64),
+        ("prec", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("L", ctypes.c_int),
+        ("M", ctypes.c_int),
+        ("K", ctypes.c_int),
+        ("band_ns", ctypes.c_int64 * MAX_BANDS),
+        ("band_ka", ctypes.c_int64 * MAX_BANDS),
+        ("band_kb", ctypes.c_int64 * MAX_BANDS),
+        ("rec_steps", ctypes.c_int64),
+        ("seg_len", ctypes.c_int),
+        ("flops_dlt", ctypes.c_double),
+        ("bytes_dlt", ctypes.c_double),
+        ("bytes_idlt", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+    def to_dict(self) -> dict:
+        K = self.K
+        return {
+            "N": self.N, "prec": self.prec, "eps": self.eps, "L": self.L, "M": self.M, "K": K,
+            "bands": [(self.band_ns[i], self.band_ka[i], self.band_kb[i]) for i in range(K)],
+            "rec_steps": self.rec_steps, "seg_len": self.seg_len, "flops_dlt": self.flops_dlt,
+            "bytes_dlt": self.bytes_dlt, "bytes_idlt": self.bytes_idlt,
+            "workspace_bytes": self.workspace_bytes,
+        }
+
+
+ENTRY_POINTS = (
+    "gbdlt_plan_params", "gbdlt_plan_create", "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
+    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_leg2cheb",
+    "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
+    "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_status_string", "gbdlt_launch_count",
+)
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"gbdlt CUDA library not found at {LIB_PATH}; build it with "
+                "`python -m paper_1505_00354_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.gbdlt_plan_params.argtypes = [i64, i32, dbl, ctypes.POINTER(Params)]
+        L.gbdlt_plan_create.argtypes = [i64, i32, dbl, vp, ctypes.POINTER(vp)]
+        L.gbdlt_plan_destroy.argtypes = [vp]
+        L.gbdlt_plan_set_stream.argtypes = [vp, vp]
+        L.gbdlt_plan_sync.argtypes = [vp]
+        L.gbdlt_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.gbdlt_legpts.argtypes = [vp, vp, vp, vp, vp]
+        for name in ("gbdlt_leg2cheb", "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t",
+                     "gbdlt_dlt", "gbdlt_dlt_t", "gbdlt_idlt", "gbdlt_idlt_t"):
+            getattr(L, name).argtypes = [vp, vp, vp, i64]
+        L.gbdlt_status_string.argtypes = [i32]
+        L.gbdlt_status_string.restype = ctypes.c_char_p
+        L.gbdlt_launch_count.restype = ctypes.c_uint64
+        for name in ENTRY_POINTS:
+            if name not in ("gbdlt_status_string", "gbdlt_launch_count"):
+                getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise GbdltError(status, where)
+
+
+def plan_params(N: int, prec: int = FP64, eps: float = 0.0) -> dict:
+    """Parameters the library derives for (N, prec, eps); host only, no GPU."""
+    p = Params()
+    _check(lib().gbdlt_plan_params(N, prec, eps, ctypes.byref(p)), "plan_params")
+    return p.to_dict()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().gbdlt_launch_count())
+
+
+def _dtype(prec: int):
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+class Plan:
+    """A transform plan for one length N and precision on the current CUDA device.
+
+    Methods mirror the C ABI: leg2cheb, leg2cheb_t, chebeval, chebeval_t, dlt,
+    dlt_t, idlt, idlt_t take a CUDA tensor of shape [..., N] (float64 for FP64
+    plans, float32 for FP32 plans) and return a new tensor (or write ``out``).
+    """
+
+    def __init__(self, N: int, prec: int = FP64, eps: float = 0.0, stream=None, device=None):
+        self._h = None
+        self.N = int(N)
+        self.prec = prec
+        self.dtype = _dtype(prec)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream() if stream is None else stream
+            self.stream = s
+            h = ctypes.c_void_p()
+            _check(lib().gbdlt_plan_create(self.N, prec, eps, ctypes.c_void_p(s.cuda_stream),
+                                           ctypes.byref(h)), "plan_create")
+        self._h = h
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.gbdlt_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self) -> dict:
+        p = Params()
+        _check(lib().gbdlt_plan_get_params(self._h, ctypes.byref(p)), "plan_get_params")
+        return p.to_dict()
+
+    def sync(self):
+        _check(lib().gbdlt_plan_sync(self._h), "plan_sync")
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(lib().gbdlt_plan_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), "set_stream")
+
+    def legpts(self):
+        """Recompute the nodes on the GPU; returns (x, theta, w, dtheta) float64 tensors."""
+        outs = [torch.empty(self.N, dtype=torch.float64, device=self.device) for _ in range(4)]
+        _check(lib().gbdlt_legpts(self._h, *[ctypes.c_void_p(t.data_ptr()) for t in outs]), "legpts")
+        return tuple(outs)
+
+    def _run(self, name: str, x: torch.Tensor, out: torch.Tensor | None):
+        if not x.is_cuda or x.dtype != self.dtype or x.shape[-1] != self.N:
+            raise ValueError(f"{name}: expected a CUDA {self.dtype} tensor [..., {self.N}], got "
+                             f"{x.dtype} {tuple(x.shape)} on {x.device}")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise ValueError(f"{name}: out must be a contiguous tensor like the input")
+        batch = x.numel() // self.N if self.N else 0
+        _check(getattr(lib(), "gbdlt_" + name)(self._h, ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), batch), name)
+        return out
+
+    def leg2cheb(self, c, out=None):
+        return self._run("leg2cheb", c, out)
+
+    def leg2cheb_t(self, y, out=None):
+        return self._run("leg2cheb_t", y, out)
+
+    def chebeval(self, chat, out=None):
+        return self._run("chebeval", chat, out)
+
+    def chebeval_t(self, g, out=None):
+        return self._run("chebeval_t", g, out)
+
+    def dlt(self, c, out=None):
+        return self._run("dlt", c, out)
+
+    def dlt_t(self, g, out=None):
+        return self._run("dlt_t", g, out)
+
+    def idlt(self, f, out=None):
+        return self._run("idlt", f, out)
+
+    def idlt_t(self, g, out=None):
+        return self._run("idlt_t", g, out)
+
+
+# --------------------------------------------------------------------------
+# convenience functions with a plan cache keyed by (N, prec, device, stream)
+# --------------------------------------------------------------------------
+_plans: dict = {}
+
+
+def get_plan(N: int, prec: int, device=None) -> Plan:
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    stream = torch.cuda.current_stream(dev)
+    key = (int(N), prec, dev, stream.cuda_stream)
+    p = _plans.get(key)
+    if p is None:
+        p = Plan(N, prec, stream=stream, device=dev)
+        _plans[key] = p
+    return p
+
+
+def _prec_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return FP64
+    if t.dtype == torch.float32:
+        return FP32
+    raise ValueError(f"unsupported dtype {t.dtype}")
+
+
+def _op(name):
+    def f(x: torch.Tensor, out=None):
+        p = get_plan(x.shape[-1], _prec_of(x), x.device)
+        return getattr(p, name)(x, out)
+    f.__name__ = name
+    f.__doc__ = f"{name} of a CUDA tensor [..., N] through a cached plan."
+    return f
+
+
+leg2cheb = _op("leg2cheb")
+leg2cheb_t = _op("leg2cheb_t")
+chebeval = _op("chebeval")
+chebeval_t = _op("chebeval_t")
+dlt = _op("dlt")
+dlt_t = _op("dlt_t")
+idlt = _op("idlt")
+idlt_t = _op("idlt_t")
+
+
+def legpts(N: int, device=None):
+    """(x, theta, w, dtheta) of the N-point Gauss-Legendre rule, computed on the GPU."""
+    return get_plan(N, FP64, device).legpts()

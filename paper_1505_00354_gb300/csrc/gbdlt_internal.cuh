@@ -1,0 +1,248 @@
+// Internal declarations of the gbdlt CUDA library: plan layout, device
+// arithmetic helpers and kernel launchers.  Every launcher enqueues on the
+// plan's stream and bumps the library's launch counter.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "gbdlt.h"
+
+namespace gbdlt {
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 / double2)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> {
+  using type = double2;
+};
+template <>
+struct Cx<float> {
+  using type = float2;
+};
+template <typename T>
+using C2 = typename Cx<T>::type;
+
+template <typename T>
+__host__ __device__ __forceinline__ C2<T> mk(T a, T b) {
+  C2<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) {
+  return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) {
+  return mk<T>(a.x - b.x, a.y - b.y);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cconj(C2<T> a) {
+  return mk<T>(a.x, -a.y);
+}
+// multiply by +i (DIR > 0) or -i (DIR < 0)
+template <typename T, int DIR>
+__device__ __forceinline__ C2<T> cmul_i(C2<T> a) {
+  return DIR > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> to_c(double2 a) {
+  return mk<T>((T)a.x, (T)a.y);
+}
+
+// ---------------------------------------------------------------------------
+// double-double helpers for the node kernel (error-free transformations with
+// explicitly rounded operations so the compiler cannot contract them)
+// ---------------------------------------------------------------------------
+struct ddv {
+  double hi, lo;
+};
+__device__ __forceinline__ ddv dd_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ddv dd_quick(double a, double b) {
+  double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ ddv dd_add(ddv a, ddv b) {
+  ddv s = dd_two_sum(a.hi, b.hi);
+  ddv t = dd_two_sum(a.lo, b.lo);
+  s.lo = __dadd_rn(s.lo, t.hi);
+  s = dd_quick(s.hi, s.lo);
+  s.lo = __dadd_rn(s.lo, t.lo);
+  return dd_quick(s.hi, s.lo);
+}
+__device__ __forceinline__ ddv dd_mul(ddv a, ddv b) {
+  double p = __dmul_rn(a.hi, b.hi);
+  double e = __fma_rn(a.hi, b.hi, -p);
+  e = __fma_rn(a.hi, b.lo, e);
+  e = __fma_rn(a.lo, b.hi, e);
+  return dd_quick(p, e);
+}
+__device__ __forceinline__ ddv dd_mul_d(ddv a, double b) {
+  double p = __dmul_rn(a.hi, b);
+  double e = __fma_rn(a.hi, b, -p);
+  e = __fma_rn(a.lo, b, e);
+  return dd_quick(p, e);
+}
+// a / b for doubles, correct to dd precision
+__device__ __forceinline__ ddv dd_div_dd(double a, double b) {
+  double q = __ddiv_rn(a, b);
+  double r = __fma_rn(-q, b, a);
+  return dd_quick(q, __ddiv_rn(r, b));
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct Band {
+  int64_t ns;  // columns n >= ns use the asymptotic expansion
+  int64_t ka;  // rows [ka, kb) and [N-kb, N-ka)
+  int64_t kb;
+};
+
+// Two-level twiddle table for e^{2 pi i e / B}, 0 <= e < B:
+// value = hi[e >> 12] * lo[e & 4095].
+struct Twiddle2 {
+  double2* lo = nullptr;  // 4096 entries
+  double2* hi = nullptr;  // max(1, B / 4096) entries
+  int64_t B = 0;
+};
+
+struct Params {
+  int64_t N = 0;
+  int prec = GBDLT_FP64;
+  double eps = 0;
+  int L = 1;
+  int M = 0;
+  int K = 0;
+  std::vector<Band> bands;
+  int seg = 512;
+  int64_t rec_steps = 0;
+  double flops_dlt = 0, bytes_dlt = 0, bytes_idlt = 0;
+};
+
+// Fills Params from (N, prec, eps): Taylor terms, asymptotic terms and bands.
+int derive_params(int64_t N, int prec, double eps, Params* p);
+// Host table of C_n = sqrt(4/pi) Gamma(n+1)/Gamma(n+3/2), n = 0..N (double-double recurrence).
+std::vector<double> cn_table(int64_t N);
+
+struct RecLayout {
+  int64_t H = 0;              // half rows (N / 2)
+  int S = 512;                // segment length
+  int64_t nseg_total = 0;     // sum over half rows of nseg(k)
+  int64_t n_long = 0;         // rows [0, n_long) have nseg > 64
+  int64_t nblocks = 0;        // row blocks of 256 half rows
+  int64_t ncta = 0;           // (row block, segment) pairs
+  int64_t tbuf_total = 0;     // transposed partial buffer length
+  // device arrays
+  int32_t* cut = nullptr;     // [H] recurrence cut per half row
+  int64_t* poff = nullptr;    // [H] offset of row k's segments
+  int32_t* cta_rb = nullptr;  // [ncta]
+  int32_t* cta_j = nullptr;   // [ncta]
+  int64_t* toff = nullptr;    // [nblocks] offset of row block partials (length nseg_max*S)
+  int32_t* bcutmax = nullptr; // [nblocks] nseg_max(rb) * S (partial array length)
+  double2* state = nullptr;   // [nseg_total] (P, D) at segment starts
+  double2* part = nullptr;    // [nseg_total] forward partial sums (E, O)
+  double* tbuf = nullptr;     // [tbuf_total] transposed partial sums
+};
+
+struct Plan {
+  Params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // nodes (double)
+  double* theta = nullptr;
+  double* x = nullptr;
+  double* w = nullptr;
+  double* tN = nullptr;  // N * dtheta_k
+  // tables
+  double* Cn = nullptr;     // [N+1]
+  double* ra = nullptr;     // (2n+1)/(n+1)
+  double* rb = nullptr;     // n/(n+1)
+  double2* tw4096 = nullptr;
+  Twiddle2 twN, tw4N;
+  int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
+  RecLayout rec;
+  // workspace (element type = plan precision)
+  void* bufA = nullptr;
+  void* bufB = nullptr;
+  int64_t nfft_max = 0;  // vectors per FFT buffer
+  void* v = nullptr;     // [N]
+  void* chat = nullptr;  // [N]
+  void* z = nullptr;     // [N]
+  void* tmp = nullptr;   // [N]
+  void* tmp2 = nullptr;  // [N]
+  int* status = nullptr; // device status word
+  void* arena = nullptr; // single device allocation holding everything above
+  size_t ws_bytes = 0;
+  double CN = 0;         // C_N for the node kernel
+};
+
+// ---------------------------------------------------------------------------
+// launch bookkeeping
+// ---------------------------------------------------------------------------
+void count_launch(int n = 1);
+int check_launch();  // GBDLT_OK or GBDLT_ERR_CUDA after a launch
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// tables.cu
+int launch_twiddle_init(Plan& P);
+// legpts.cu
+int launch_legpts(Plan& P, double CN);
+int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N
+// fft.cu: in-place batched FFT of length N, sign DIR (+1: e^{+2 pi i nk/N}).
+// Input in `a`; result in `a` when N <= 4096, else in `b` (returned pointer).
+template <typename T>
+void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir);
+// rec.cu
+int launch_rec_state_init(Plan& P);
+template <typename T>
+int launch_rec_forward(Plan& P, const T* c, T* vrec);
+template <typename T>
+int launch_rec_transpose(Plan& P, const T* z, T* out);
+// stages.cu (prologues / epilogues)
+template <typename T>
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U);
+template <typename T>
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v);
+template <typename T>
+int launch_a4_pro(Plan& P, const T* v, C2<T>* U);
+template <typename T>
+int launch_a4_epi(Plan& P, const C2<T>* F, T* chat);
+template <typename T>
+int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d);
+template <typename T>
+int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair);
+template <typename T>
+int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair);
+template <typename T>
+int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair);
+template <typename T>
+int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair);
+template <typename T>
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U);
+template <typename T>
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s);
+template <typename T>
+int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out);
+template <typename T>
+int launch_scale(Plan& P, const T* in, T* out, int which);
+
+}  // namespace gbdlt

@@ -1,0 +1,205 @@
+// Gauss-Legendre nodes and weights on the GPU (Sec. 2.1-2.2).
+//
+// One thread per node k < ceil(N/2) (theta < pi/2); the other half follows from
+// the symmetry theta_{N-1-k} = pi - theta_k, w_{N-1-k} = w_k.  Newton's method
+// runs in delta = theta - theta*_k, started at the cheb* point
+// theta*_k = (k+3/4)pi/(N+1/2) of Sec. 2.2, which Lemma 2.3 places within
+// 1/(3 pi (2N+1)) of the root.  Working in delta keeps the phase of P_N exact:
+// (N+1/2) theta*_k - pi/4 = (k+1/2) pi, so cos/sin of the phase are those of the
+// small angle eps = (N+1/2) delta, with no large-argument reduction.
+//
+// P_N(cos theta) and dP_N/dtheta are evaluated by one of three methods:
+//  * N <= 64: the three-term recurrence in difference form,
+//      D_{n+1} = [(2n+1)(x-1) P_n + n D_n]/(n+1),  P_{n+1} = P_n + D_{n+1},
+//    with x - 1 = -2 sin^2(theta/2) (no cancellation near x = 1);
+//  * N sin(theta) >= 25: the large-degree asymptotic expansion whose leading
+//    term is quoted in Sec. 2.2 (Stieltjes), carried to the order where the
+//    next term is below 1e-18 of the leading amplitude:
+//      P_N(cos t) = C_N sum_m h_{m,N} cos((N+m+1/2)t - (m+1/2)pi/2) / (2 sin t)^{m+1/2},
+//      C_N = sqrt(4/pi) Gamma(N+1)/Gamma(N+3/2),
+//      h_{0,N} = 1, h_{m+1,N} = h_{m,N} (m+1/2)^2 / ((m+1)(N+m+3/2));
+//  * otherwise (the few nodes near theta = 0): the terminating hypergeometric
+//    series P_N(cos t) = sum_j (-N)_j (N+1)_j / (j!)^2 s^j, s = sin^2(t/2),
+//    summed in double-double (its terms reach ~1e10 before they cancel).
+// Weight: w_k = 2 / (dP_N/dtheta)^2 at the root (Gauss-Legendre weight written
+// in theta).  Outputs per node: theta_k, x_k = cos theta_k, w_k and
+// t_k = N * (theta_k - (k+1/2)pi/N), the scaled offset from the cheb1 grid used
+// by the Taylor series of Sec. 2.1 (computed from the exact difference
+// theta*_k - theta^cheb1_k = pi (N-2k-1) / (4N(N+1/2)) plus delta, so it keeps
+// full relative accuracy).
+#include "gbdlt_internal.cuh"
+
+namespace gbdlt {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238;
+
+struct PD {
+  double p, dp;
+};
+
+__device__ PD eval_rec(int64_t N, double s, double c, double sh) {
+  // s = sin(theta), c = cos(theta), sh = sin(theta/2)
+  double xm1 = -2.0 * sh * sh;
+  double P = 1.0, D = 1.0;
+  for (int64_t n = 0; n < N; ++n) {
+    double Dn = ((double)(2 * n + 1) * xm1 * P + (double)n * D) / (double)(n + 1);
+    P += Dn;
+    D = Dn;
+  }
+  // P_{N-1} - x P_N = -(x-1) P_N - D_N
+  PD r;
+  r.p = P;
+  r.dp = (double)N * (xm1 * P + D) / s;
+  return r;
+}
+
+__device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, double CN) {
+  const double eps = ((double)N + 0.5) * d;
+  const double e2 = eps * eps;
+  // sin/cos of |eps| <= 0.06 by Taylor polynomials (error < 1e-19)
+  double se = eps * (1.0 + e2 * (-1.0 / 6 + e2 * (1.0 / 120 + e2 * (-1.0 / 5040 + e2 * (1.0 / 362880)))));
+  double ce = 1.0 + e2 * (-0.5 + e2 * (1.0 / 24 + e2 * (-1.0 / 720 + e2 * (1.0 / 40320))));
+  const double sg = (k & 1) ? -1.0 : 1.0;
+  double cr = -sg * se, ci = sg * ce;  // e^{i phi_0}, phi_0 = (k+1/2)pi + eps
+  const double rr = s, ri = -c;        // e^{i(theta - pi/2)}
+  const double g = 0.5 / s;
+  const double cot = c / s;
+  const double sg0 = sqrt(g);
+  double gm = sg0;  // g^{m+1/2}
+  double h = 1.0;
+  double P = 0.0, dP = 0.0;
+  for (int m = 0; m < 40; ++m) {
+    double term = h * gm;
+    P += term * cr;
+    dP += term * (-((double)N + m + 0.5) * ci - (m + 0.5) * cot * cr);
+    h *= (m + 0.5) * (m + 0.5) / ((m + 1.0) * ((double)N + m + 1.5));
+    gm *= g;
+    double ncr = cr * rr - ci * ri;
+    ci = cr * ri + ci * rr;
+    cr = ncr;
+    if (h * gm < 1e-18 * sg0) break;
+  }
+  PD r;
+  r.p = CN * P;
+  r.dp = CN * dP;
+  return r;
+}
+
+__device__ PD eval_series(int64_t N, double s, double c, double sh, double ch) {
+  const double sq = sh * sh;  // s = sin^2(theta/2)
+  ddv t = {1.0, 0.0};
+  ddv sp = {1.0, 0.0};
+  ddv sj = {0.0, 0.0};
+  const double Nd = (double)N;
+  for (int j = 0; j < 400 && j < N; ++j) {
+    double num = -(Nd - j) * (Nd + j + 1.0);  // exact in double for N <= 2^26
+    double den = (double)(j + 1) * (double)(j + 1);
+    ddv ratio = dd_div_dd(num, den);
+    t = dd_mul_d(dd_mul(t, ratio), sq);
+    sp = dd_add(sp, t);
+    sj = dd_add(sj, dd_mul_d(t, (double)(j + 1)));
+    if (j > 4 && fabs(t.hi) < 1e-34) break;
+  }
+  PD r;
+  r.p = sp.hi + sp.lo;
+  r.dp = (ch / sh) * (sj.hi + sj.lo);  // dP/dtheta = cot(theta/2) sum_j j t_j
+  return r;
+}
+
+__global__ void k_legpts(int64_t N, double CN, double* __restrict__ theta, double* __restrict__ x,
+                         double* __restrict__ w, double* __restrict__ tN, int* __restrict__ status) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t half = (N + 1) / 2;
+  if (k >= half) return;
+  const double Nh = (double)N + 0.5;
+  const double th0 = ((double)k + 0.75) * kPi / Nh;
+  double s0, c0;
+  sincos(th0, &s0, &c0);
+  int mode;
+  if (N <= 64)
+    mode = 0;
+  else if ((double)N * s0 >= 25.0)
+    mode = 1;
+  else
+    mode = 2;
+  double d = 0.0;
+  bool ok = false;
+  PD r;
+  double s = s0, c = c0, sh = 0, ch = 0;
+  for (int it = 0; it < 2 * 12 + 1; ++it) {
+    // sin/cos of theta = th0 + d by the angle-addition formula; |d| <= 1/(3 pi (2N+1))
+    // (Lemma 2.3), so the Taylor polynomials below are exact to < 1e-20
+    const double d2 = d * d;
+    const double sd =
+        d * (1.0 - d2 / 6.0 * (1.0 - d2 / 20.0 * (1.0 - d2 / 42.0 * (1.0 - d2 / 72.0))));
+    const double cd =
+        1.0 - d2 / 2.0 * (1.0 - d2 / 12.0 * (1.0 - d2 / 30.0 * (1.0 - d2 / 56.0 * (1.0 - d2 / 90.0))));
+    s = s0 * cd + c0 * sd;
+    c = c0 * cd - s0 * sd;
+    if (mode != 1) {
+      double th = th0 + d;
+      sincos(0.5 * th, &sh, &ch);
+    }
+    if (mode == 0)
+      r = eval_rec(N, s, c, sh);
+    else if (mode == 1)
+      r = eval_asy(N, k, d, s, c, CN);
+    else
+      r = eval_series(N, s, c, sh, ch);
+    if (ok) break;  // this evaluation was at the converged point
+    double step = r.p / r.dp;
+    d -= step;
+    if (!(fabs(d) < 1.0)) break;  // diverged (NaN or runaway)
+    if (fabs(step) <= 1e-11 / (double)N) ok = true;
+  }
+  if (!ok) atomicOr(status, 1);
+  const double th = th0 + d;
+  const double wk = 2.0 / (r.dp * r.dp);
+  double xk;
+  if (th < 1.0) {
+    double shh = sin(0.5 * th);
+    xk = 1.0 - 2.0 * shh * shh;
+  } else {
+    xk = c;
+  }
+  const double tk = kPi * (double)(N - 2 * k - 1) / (4.0 * Nh) + (double)N * d;
+  theta[k] = th;
+  x[k] = xk;
+  w[k] = wk;
+  tN[k] = tk;
+  const int64_t km = N - 1 - k;
+  if (km != k) {
+    theta[km] = kPi - th;
+    x[km] = -xk;
+    w[km] = wk;
+    tN[km] = -tk;
+  }
+}
+
+__global__ void k_dtheta(const double* __restrict__ tN, double* __restrict__ out, int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) out[k] = tN[k] / (double)N;  // exact: N is a power of two
+}
+
+}  // namespace
+
+int launch_dtheta(Plan& P, double* out) {
+  const int64_t N = P.p.N;
+  k_dtheta<<<(unsigned)((N + 255) / 256), 256, 0, P.stream>>>(P.tN, out, N);
+  count_launch();
+  return check_launch();
+}
+
+int launch_legpts(Plan& P, double CN) {
+  const int64_t N = P.p.N;
+  const int64_t half = (N + 1) / 2;
+  const int threads = 128;
+  const int64_t blocks = (half + threads - 1) / threads;
+  k_legpts<<<(unsigned)blocks, threads, 0, P.stream>>>(N, CN, P.theta, P.x, P.w, P.tN, P.status);
+  count_launch();
+  return check_launch();
+}
+
+}  // namespace gbdlt

@@ -1,0 +1,766 @@
+// Plan creation, parameter derivation and the C-ABI entry points.
+//
+// Parameters (Sec. 2.2 Corollary 2.4 / Table 1; Sec. 3 "parameters determined
+// by analysis for any working tolerance"):
+//  * L (Taylor terms): the smallest L with 0.83845^L / L! <= eps/2.
+//  * Asymptotic expansion of P_n(cos theta) with M terms and error bound
+//    |R_M| <= 2 C_n h_{M,n} / (2 sin theta)^{M+1/2}: row theta_k may use it for
+//    columns n >= n_cut(k) where the bound is <= eps/20.  Rows are grouped into
+//    bands sharing one column cut; rows whose cut would exceed N use the
+//    recurrence for every column.  M and the band cuts (from a geometric grid
+//    of candidate cuts, ratio 2^(1/4)) minimise a cost model: each band costs M
+//    FFTs of length N, each recurrence step a fixed cost per half row.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "gbdlt_internal.cuh"
+
+namespace gbdlt {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GBDLT_OK : GBDLT_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// host double-double (for the C_n table)
+// ---------------------------------------------------------------------------
+namespace {
+struct hdd {
+  double hi, lo;
+};
+hdd h_quick(double a, double b) {
+  double s = a + b;
+  return {s, b - (s - a)};
+}
+hdd h_two_prod(double a, double b) {
+  double p = a * b;
+  return {p, std::fma(a, b, -p)};
+}
+hdd h_mul_d(hdd a, double b) {
+  hdd p = h_two_prod(a.hi, b);
+  p.lo = std::fma(a.lo, b, p.lo);
+  return h_quick(p.hi, p.lo);
+}
+hdd h_div_d(hdd a, double b) {
+  double q1 = a.hi / b;
+  hdd p = h_two_prod(q1, b);
+  double r = ((a.hi - p.hi) - p.lo) + a.lo;
+  double q2 = r / b;
+  return h_quick(q1, q2);
+}
+}  // namespace
+
+std::vector<double> cn_table(int64_t N) {
+  // C_0 = 4/pi; C_{n+1} = C_n (n+1)/(n+3/2)
+  std::vector<double> C((size_t)N + 1);
+  hdd c = {1.2732395447351628, -7.871470670072994e-17};  // 4/pi to double-double
+  for (int64_t n = 0; n <= N; ++n) {
+    C[(size_t)n] = c.hi + c.lo;
+    c = h_div_d(h_mul_d(c, (double)(n + 1)), (double)n + 1.5);
+  }
+  return C;
+}
+
+// ---------------------------------------------------------------------------
+// parameter derivation
+// ---------------------------------------------------------------------------
+static double log_gM(int M, double n) {
+  // log(2 C_n h_{M,n})
+  double lc = 0.5 * std::log(4.0 / M_PI) + std::lgamma(n + 1.0) - std::lgamma(n + 1.5);
+  double lh = 0.0;
+  for (int j = 1; j <= M; ++j) lh += 2.0 * std::log(j - 0.5) - std::log((double)j) - std::log(n + j + 0.5);
+  return std::log(2.0) + lc + lh;
+}
+
+struct DPResult {
+  double cost = 0;
+  std::vector<Band> bands;
+};
+
+static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, double c_rec) {
+  const int64_t H = N / 2;
+  DPResult best_res;
+  // candidate cuts, descending
+  std::vector<int64_t> cands;
+  int lg = 0;
+  while ((1ll << lg) < N) ++lg;
+  for (int i = 4 * lg; i >= 4; --i) {
+    int64_t v = (int64_t)std::llround(std::pow(2.0, i / 4.0));
+    v = std::min<int64_t>(v, N);
+    if (v >= 2 && (cands.empty() || cands.back() != v)) cands.push_back(v);
+  }
+  const int nc = (int)cands.size();
+  // first half row whose n_cut <= cand
+  std::vector<int64_t> Kc(nc);
+  for (int i = 0; i < nc; ++i) {
+    double lgm = log_gM(M, (double)cands[i]);
+    double lsmin = (lgm - std::log(eps_asy)) / (M + 0.5) - std::log(2.0);
+    double smin = std::exp(lsmin);
+    int64_t k;
+    if (smin >= 1.0) {
+      k = H;
+    } else {
+      double kk = (double)N * std::asin(smin) / M_PI - 0.5;
+      k = (int64_t)std::ceil(kk);
+      if (k < 0) k = 0;
+      // guard against rounding of asin: move to the first row that satisfies the bound
+      while (k < H && std::sin((k + 0.5) * M_PI / N) < smin) ++k;
+      while (k > 0 && std::sin((k - 0.5) * M_PI / N) >= smin) --k;
+      if (k > H) k = H;
+    }
+    Kc[i] = k;
+  }
+  const double tcost = (double)M * c_fft;
+  std::vector<double> best(nc, 0.0);
+  std::vector<int> choice(nc, -1);
+  for (int i = nc - 1; i >= 0; --i) {
+    const int64_t ka = Kc[i];
+    if (ka >= H) {
+      best[i] = 0.0;
+      choice[i] = -2;  // empty
+      continue;
+    }
+    double opt = tcost + (double)cands[i] * c_rec * (double)(H - ka);
+    int ch = -1;
+    for (int j = i + 1; j < nc; ++j) {
+      const int64_t kb = Kc[j];
+      if (kb <= ka) continue;
+      double c2 = tcost + (double)cands[i] * c_rec * (double)(kb - ka) + best[j];
+      if (c2 < opt) {
+        opt = c2;
+        ch = j;
+      }
+    }
+    best[i] = opt;
+    choice[i] = ch;
+  }
+  double top = (double)N * c_rec * (double)H;
+  int topi = -1;
+  for (int i = 0; i < nc; ++i) {
+    if (choice[i] == -2) continue;
+    double c0 = (double)N * c_rec * (double)Kc[i] + best[i];
+    if (c0 < top) {
+      top = c0;
+      topi = i;
+    }
+  }
+  best_res.cost = top;
+  int i = topi;
+  while (i >= 0) {
+    const int j = choice[i];
+    const int64_t ka = Kc[i];
+    const int64_t kb = j >= 0 ? Kc[j] : H;
+    if (kb > ka) best_res.bands.push_back(Band{cands[i], ka, kb});
+    i = j;
+  }
+  return best_res;
+}
+
+int derive_params(int64_t N, int prec, double eps, Params* p) {
+  if (N < 1 || N > (1ll << 24) || (N & (N - 1))) return GBDLT_ERR_UNSUPPORTED_N;
+  if (prec != GBDLT_FP64 && prec != GBDLT_FP32) return GBDLT_ERR_INVALID_ARG;
+  if (eps <= 0.0) eps = prec == GBDLT_FP64 ? 1e-14 : 2e-6;
+  if (!(eps < 1.0) || !std::isfinite(eps)) return GBDLT_ERR_INVALID_ARG;
+  Params q;
+  q.N = N;
+  q.prec = prec;
+  q.eps = eps;
+  // Corollary 2.4 with theta* = theta^cheb1: |f - f_L| <= 0.83845^L / L! ||c||_1
+  int L = 1;
+  double b = 0.83845;
+  while (b > 0.5 * eps && L < 24) {
+    ++L;
+    b *= 0.83845 / L;
+  }
+  q.L = L;
+  q.seg = 512;
+  q.M = 0;
+  q.K = 0;
+  int lg = 0;
+  while ((1ll << lg) < N) ++lg;
+  if (N >= 4) {
+    const double eps_asy = eps / 20.0;
+    const double fft_ops = (4.25 * lg + 30.0) * (double)N;
+    double c_fft, c_rec;
+    int Mmax;
+    if (prec == GBDLT_FP64) {
+      c_fft = fft_ops;
+      c_rec = 5.5;
+      Mmax = 24;
+    } else {
+      // FP32 transforms are bound by memory traffic (~48 bytes per point per
+      // FFT of the pipeline, ~5 FP32 ops per byte of HBM); the recurrence is FP64
+      // (58 FP32 ops per FP64 op on this part)
+      c_fft = std::max(fft_ops, 240.0 * (double)N);
+      c_rec = 5.5 * 58.0;
+      Mmax = 16;
+    }
+    double best = (double)N * c_rec * (double)(N / 2);  // all recurrence
+    for (int M = 2; M <= Mmax; ++M) {
+      DPResult r = plan_bands(N, M, eps_asy, c_fft, c_rec);
+      if ((int)r.bands.size() > GBDLT_MAX_BANDS) continue;
+      if (r.cost < best) {
+        best = r.cost;
+        q.M = M;
+        q.bands = r.bands;
+      }
+    }
+    q.K = (int)q.bands.size();
+    if (q.K == 0) q.M = 0;
+  }
+  // recurrence work
+  const int64_t H = N / 2;
+  int64_t half_steps = 0;
+  {
+    int64_t k0 = q.K > 0 ? q.bands[0].ka : H;
+    half_steps += k0 * N;
+    for (const Band& bd : q.bands) half_steps += (bd.kb - bd.ka) * bd.ns;
+  }
+  q.rec_steps = 2 * half_steps;
+  const int npair = (q.L - 1 + 1) / 2;
+  const double fft_flops = 5.0 * (double)N * (double)std::max(lg, 1);
+  q.flops_dlt = (double)(q.K * q.M + 1 + npair) * fft_flops + 7.0 * (double)half_steps;
+  const double dsz = prec == GBDLT_FP64 ? 8.0 : 4.0;
+  q.bytes_dlt = (2.0 * dsz + 8.0) * (double)N;
+  q.bytes_idlt = (2.0 * dsz + 16.0) * (double)N;
+  *p = q;
+  return GBDLT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tables on the device
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_twiddle(double2* out, int64_t count, int64_t B, int64_t mult) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t e = (i * mult) % B;
+  double s, c;
+  sincospi(2.0 * (double)e / (double)B, &s, &c);
+  out[i] = make_double2(c, s);
+}
+void twiddle_fill(Plan& P, double2* out, int64_t count, int64_t B, int64_t mult) {
+  k_twiddle<<<(unsigned)((count + 255) / 256), 256, 0, P.stream>>>(out, count, B, mult);
+  count_launch();
+}
+}  // namespace
+
+int launch_twiddle_init(Plan& P) {
+  twiddle_fill(P, P.tw4096, 4096, 4096, 1);
+  twiddle_fill(P, P.twN.lo, 4096, P.twN.B, 1);
+  twiddle_fill(P, P.twN.hi, std::max<int64_t>(1, P.twN.B / 4096), P.twN.B, 4096);
+  twiddle_fill(P, P.tw4N.lo, 4096, P.tw4N.B, 1);
+  twiddle_fill(P, P.tw4N.hi, std::max<int64_t>(1, P.tw4N.B / 4096), P.tw4N.B, 4096);
+  return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// plan lifecycle
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Arena {
+  size_t off = 0;
+  template <typename U>
+  size_t take(int64_t count) {
+    size_t o = off;
+    off += ((size_t)std::max<int64_t>(count, 1) * sizeof(U) + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+void free_plan(Plan* P) {
+  if (!P) return;
+  if (P->arena) cudaFree(P->arena);
+  delete P;
+}
+
+}  // namespace
+
+static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, Plan** out) {
+  Params prm;
+  int st = derive_params(N, prec, eps, &prm);
+  if (st != GBDLT_OK) return st;
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) return GBDLT_ERR_OOM;
+  P->p = prm;
+  P->stream = stream;
+  cudaGetDevice(&P->device);
+  const size_t ts = prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
+  const size_t cs = 2 * ts;
+  const int64_t H = N / 2;
+  // recurrence layout (host)
+  RecLayout& R = P->rec;
+  R.H = H;
+  R.S = prm.seg;
+  std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1));
+  std::vector<int64_t> poff((size_t)std::max<int64_t>(H, 1));
+  std::vector<int32_t> cta_rb, cta_j, maxcut;
+  std::vector<int64_t> toff;
+  if (H > 0) {
+    for (int64_t k = 0; k < H; ++k) cut[(size_t)k] = (int32_t)N;
+    for (const Band& b : prm.bands)
+      for (int64_t k = b.ka; k < b.kb; ++k) cut[(size_t)k] = (int32_t)b.ns;
+    int64_t o = 0;
+    R.n_long = 0;
+    for (int64_t k = 0; k < H; ++k) {
+      poff[(size_t)k] = o;
+      int64_t ns = (cut[(size_t)k] + R.S - 1) / R.S;
+      o += ns;
+      if (ns > 64) R.n_long = k + 1;
+    }
+    R.nseg_total = o;
+    R.nblocks = (H + 255) / 256;
+    int64_t to = 0;
+    for (int64_t rb = 0; rb < R.nblocks; ++rb) {
+      int32_t mc = cut[(size_t)(rb * 256)];
+      int64_t nsm = (mc + R.S - 1) / R.S;
+      maxcut.push_back(mc);
+      toff.push_back(to);
+      to += nsm * R.S;
+      for (int64_t j = 0; j < nsm; ++j) {
+        cta_rb.push_back((int32_t)rb);
+        cta_j.push_back((int32_t)j);
+      }
+    }
+    R.tbuf_total = to;
+    R.ncta = (int64_t)cta_rb.size();
+  }
+  const int npair = (prm.L + 1) / 2;
+  P->nfft_max = std::max<int64_t>({(int64_t)prm.K * prm.M, (int64_t)npair, 1});
+  // arena layout
+  Arena A;
+  size_t o_theta = A.take<double>(N), o_x = A.take<double>(N), o_w = A.take<double>(N),
+         o_t = A.take<double>(N);
+  size_t o_cn = A.take<double>(N + 1), o_ra = A.take<double>(N + 1024), o_rb = A.take<double>(N + 1024);
+  size_t o_tw = A.take<double2>(4096);
+  P->twN.B = N;
+  P->tw4N.B = 4 * N;
+  size_t o_twNlo = A.take<double2>(4096), o_twNhi = A.take<double2>(std::max<int64_t>(1, N / 4096));
+  size_t o_tw4lo = A.take<double2>(4096), o_tw4hi = A.take<double2>(std::max<int64_t>(1, 4 * N / 4096));
+  size_t o_cut = A.take<int32_t>(H), o_poff = A.take<int64_t>(H), o_crb = A.take<int32_t>(R.ncta),
+         o_cj = A.take<int32_t>(R.ncta), o_toff = A.take<int64_t>(R.nblocks),
+         o_mc = A.take<int32_t>(R.nblocks), o_state = A.take<double2>(R.nseg_total),
+         o_part = A.take<double2>(R.nseg_total), o_tbuf = A.take<double>(R.tbuf_total);
+  size_t o_bufA = A.off;
+  A.off += ((size_t)P->nfft_max * (size_t)N * cs + 255) & ~(size_t)255;
+  size_t o_bufB = A.off;
+  A.off += ((size_t)P->nfft_max * (size_t)N * cs + 255) & ~(size_t)255;
+  size_t o_v = A.off;
+  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
+  size_t o_chat = A.off;
+  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
+  size_t o_z = A.off;
+  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
+  size_t o_tmp = A.off;
+  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
+  size_t o_tmp2 = A.off;
+  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
+  size_t o_status = A.take<int>(1);
+  P->ws_bytes = A.off;
+  if (cudaMalloc(&P->arena, A.off) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(P);
+    return GBDLT_ERR_OOM;
+  }
+  char* base = (char*)P->arena;
+  P->theta = (double*)(base + o_theta);
+  P->x = (double*)(base + o_x);
+  P->w = (double*)(base + o_w);
+  P->tN = (double*)(base + o_t);
+  P->Cn = (double*)(base + o_cn);
+  P->ra = (double*)(base + o_ra);
+  P->rb = (double*)(base + o_rb);
+  P->tw4096 = (double2*)(base + o_tw);
+  P->twN.lo = (double2*)(base + o_twNlo);
+  P->twN.hi = (double2*)(base + o_twNhi);
+  P->tw4N.lo = (double2*)(base + o_tw4lo);
+  P->tw4N.hi = (double2*)(base + o_tw4hi);
+  R.cut = (int32_t*)(base + o_cut);
+  R.poff = (int64_t*)(base + o_poff);
+  R.cta_rb = (int32_t*)(base + o_crb);
+  R.cta_j = (int32_t*)(base + o_cj);
+  R.toff = (int64_t*)(base + o_toff);
+  R.bcutmax = (int32_t*)(base + o_mc);
+  R.state = (double2*)(base + o_state);
+  R.part = (double2*)(base + o_part);
+  R.tbuf = (double*)(base + o_tbuf);
+  P->bufA = base + o_bufA;
+  P->bufB = base + o_bufB;
+  P->v = base + o_v;
+  P->chat = base + o_chat;
+  P->z = base + o_z;
+  P->tmp = base + o_tmp;
+  P->tmp2 = base + o_tmp2;
+  P->status = (int*)(base + o_status);
+
+  bool ok = true;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+  };
+  {
+    std::vector<double> C = cn_table(N);
+    up(P->Cn, C.data(), sizeof(double) * C.size());
+    P->CN = C[(size_t)N];
+    std::vector<double> ra((size_t)N + 1024), rb((size_t)N + 1024);
+    for (int64_t n = 0; n < N + 1024; ++n) {
+      ra[(size_t)n] = (double)(2 * n + 1) / (double)(n + 1);
+      rb[(size_t)n] = (double)n / (double)(n + 1);
+    }
+    up(P->ra, ra.data(), sizeof(double) * ra.size());
+    up(P->rb, rb.data(), sizeof(double) * rb.size());
+  }
+  if (H > 0) {
+    up(R.cut, cut.data(), sizeof(int32_t) * (size_t)H);
+    up(R.poff, poff.data(), sizeof(int64_t) * (size_t)H);
+    up(R.cta_rb, cta_rb.data(), sizeof(int32_t) * cta_rb.size());
+    up(R.cta_j, cta_j.data(), sizeof(int32_t) * cta_j.size());
+    up(R.toff, toff.data(), sizeof(int64_t) * toff.size());
+    up(R.bcutmax, maxcut.data(), sizeof(int32_t) * maxcut.size());
+  }
+  if (cudaMemsetAsync(P->status, 0, sizeof(int), P->stream) != cudaSuccess) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    free_plan(P);
+    return GBDLT_ERR_CUDA;
+  }
+  st = launch_twiddle_init(*P);
+  if (st == GBDLT_OK) st = launch_rec_state_init(*P);
+  if (st == GBDLT_OK) st = launch_legpts(*P, P->CN);
+  if (st == GBDLT_OK && cudaStreamSynchronize(P->stream) != cudaSuccess) st = GBDLT_ERR_CUDA;
+  if (st == GBDLT_OK) {
+    int hs = 0;
+    if (cudaMemcpy(&hs, P->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = GBDLT_ERR_CUDA;
+    else if (hs & 1)
+      st = GBDLT_ERR_NOT_CONVERGED;
+  }
+  if (st != GBDLT_OK) {
+    cudaGetLastError();
+    free_plan(P);
+    return st;
+  }
+  *out = P;
+  return GBDLT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// transform chains
+// ---------------------------------------------------------------------------
+namespace {
+
+// the FFT buffer that does not hold `p`
+inline void* other(Plan& P, const void* p) { return p == P.bufA ? P.bufB : P.bufA; }
+
+// chat = M c (Sec. 3); also leaves v (values on the cheb1 grid) in P.v
+template <typename T>
+int run_leg2cheb(Plan& P, const T* c, T* chat) {
+  const int64_t KM = (int64_t)P.p.K * P.p.M;
+  T* vrec = (T*)P.tmp;
+  T* v = (T*)P.v;
+  int st = launch_rec_forward<T>(P, c, vrec);
+  if (st) return st;
+  const C2<T>* Y = nullptr;
+  if (KM > 0) {
+    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA);
+    if (st) return st;
+    Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, KM, +1);
+  }
+  st = launch_l2c_epi<T>(P, Y, vrec, v);
+  if (st) return st;
+  st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA);
+  if (st) return st;
+  const C2<T>* F = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, 1, -1);
+  return launch_a4_epi<T>(P, F, chat);
+}
+
+// Taylor NDCT (Sec. 2): f = [v] + sum_{l} ...; inc0 = 1 includes l = 0 (standalone chebeval)
+template <typename T>
+int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0) {
+  const int npair = inc0 ? (P.p.L + 1) / 2 : P.p.L / 2;
+  if (npair == 0) {
+    if (!inc0) return cudaMemcpyAsync(f, v, sizeof(T) * P.p.N, cudaMemcpyDeviceToDevice, P.stream) ==
+                              cudaSuccess
+                          ? GBDLT_OK
+                          : GBDLT_ERR_CUDA;
+  }
+  int st = launch_tay_pro<T>(P, chat, (C2<T>*)P.bufA, inc0, npair);
+  if (st) return st;
+  const C2<T>* Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, npair, +1);
+  return launch_tay_epi<T>(P, Y, v, f, inc0, npair);
+}
+
+// transposed chain: out = [D_s] P^T [D_w] g (idlt when weighted), Sec. 4
+template <typename T>
+int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s) {
+  const int64_t KM = (int64_t)P.p.K * P.p.M;
+  const int npair = P.p.L / 2;  // l = 1..L-1
+  T* z = (T*)P.z;
+  T* rect = (T*)P.tmp;
+  int st;
+  const C2<T>* Y = nullptr;  // A4^T FFT output
+  if (npair > 0) {
+    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, 0, npair);
+    if (st) return st;
+    const void* F = launch_fft<T>(P, P.bufA, P.bufB, npair, -1);
+    void* q = other(P, F);
+    st = launch_tayt_epi<T>(P, (const C2<T>*)F, (C2<T>*)q, nullptr, 0, npair);
+    if (st) return st;
+    Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), 1, +1);
+  }
+  void* U = Y ? other(P, Y) : P.bufA;
+  st = launch_l2ct_pro<T>(P, Y, g, use_w, z, (C2<T>*)U);
+  if (st) return st;
+  st = launch_rec_transpose<T>(P, z, rect);
+  if (st) return st;
+  const C2<T>* F2 = nullptr;
+  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), KM, -1);
+  return launch_l2ct_epi<T>(P, F2, rect, out, scale_s);
+}
+
+// out = M^T y: z = A4^T y, then P_cheb^T z
+template <typename T>
+int run_leg2cheb_t(Plan& P, const T* y, T* out) {
+  const int64_t KM = (int64_t)P.p.K * P.p.M;
+  T* z = (T*)P.z;
+  T* rect = (T*)P.tmp;
+  int st = launch_fcs_pro<T>(P, y, (C2<T>*)P.bufA, 1);
+  if (st) return st;
+  const void* Y = launch_fft<T>(P, P.bufA, P.bufB, 1, +1);
+  void* U = other(P, Y);
+  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U);
+  if (st) return st;
+  st = launch_rec_transpose<T>(P, z, rect);
+  if (st) return st;
+  const C2<T>* F2 = nullptr;
+  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), KM, -1);
+  return launch_l2ct_epi<T>(P, F2, rect, out, 0);
+}
+
+template <typename T>
+int run_chebeval_t(Plan& P, const T* g, T* out) {
+  const int npair = (P.p.L + 1) / 2;  // l = 0..L-1
+  int st = launch_tayt_pro<T>(P, g, 0, (C2<T>*)P.bufA, 1, npair);
+  if (st) return st;
+  const void* F = launch_fft<T>(P, P.bufA, P.bufB, npair, -1);
+  return launch_tayt_epi<T>(P, (const C2<T>*)F, nullptr, out, 1, npair);
+}
+
+enum Op { OP_L2C, OP_L2C_T, OP_CHEB, OP_CHEB_T, OP_DLT, OP_DLT_T, OP_IDLT, OP_IDLT_T };
+
+template <typename T>
+int run_one(Plan& P, int op, const T* in, T* out) {
+  const int64_t N = P.p.N;
+  if (N == 1) {
+    // every operator is the identity at N = 1 (P_0 = T_0 = 1, w_0 = 2, s_0 = 1/2)
+    return cudaMemcpyAsync(out, in, sizeof(T), cudaMemcpyDeviceToDevice, P.stream) == cudaSuccess
+               ? GBDLT_OK
+               : GBDLT_ERR_CUDA;
+  }
+  switch (op) {
+    case OP_L2C:
+      return run_leg2cheb<T>(P, in, out);
+    case OP_L2C_T:
+      return run_leg2cheb_t<T>(P, in, out);
+    case OP_CHEB:
+      return run_taylor<T>(P, in, nullptr, out, 1);
+    case OP_CHEB_T:
+      return run_chebeval_t<T>(P, in, out);
+    case OP_DLT: {
+      int st = run_leg2cheb<T>(P, in, (T*)P.chat);
+      if (st) return st;
+      return run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0);
+    }
+    case OP_DLT_T:
+      return run_transposed<T>(P, in, out, 0, 0);
+    case OP_IDLT:
+      return run_transposed<T>(P, in, out, 1, 1);
+    case OP_IDLT_T: {
+      // out = D_w P D_s g
+      T* sg = (T*)P.tmp2;
+      int st = launch_scale<T>(P, in, sg, 1);
+      if (st) return st;
+      st = run_leg2cheb<T>(P, sg, (T*)P.chat);
+      if (st) return st;
+      st = run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0);
+      if (st) return st;
+      return launch_scale<T>(P, out, out, 2);
+    }
+  }
+  return GBDLT_ERR_INVALID_ARG;
+}
+
+int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch) {
+  if (!plan || batch < 0) return GBDLT_ERR_INVALID_ARG;
+  if (batch == 0) return GBDLT_OK;  // nothing to do; the pointers are not read
+  if (!in || !out) return GBDLT_ERR_INVALID_ARG;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const int64_t N = P.p.N;
+  const size_t es = P.p.prec == GBDLT_FP64 ? 8 : 4;
+  if (((uintptr_t)in % es) || ((uintptr_t)out % es)) return GBDLT_ERR_INVALID_ARG;
+  const char* a = (const char*)in;
+  const char* ae = a + (size_t)batch * N * es;
+  const char* b = (const char*)out;
+  const char* be = b + (size_t)batch * N * es;
+  if (batch > 0 && a < be && b < ae) return GBDLT_ERR_INVALID_ARG;  // overlap
+  for (int64_t i = 0; i < batch; ++i) {
+    int st;
+    if (P.p.prec == GBDLT_FP64)
+      st = run_one<double>(P, op, (const double*)in + i * N, (double*)out + i * N);
+    else
+      st = run_one<float>(P, op, (const float*)in + i * N, (float*)out + i * N);
+    if (st) return st;
+  }
+  return check_launch();
+}
+
+}  // namespace
+
+}  // namespace gbdlt
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace gbdlt;
+
+struct gbdlt_plan_s {};  // opaque tag; the pointer is a gbdlt::Plan
+
+extern "C" {
+
+static void fill_public(const Params& q, size_t ws, gbdlt_params* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->N = q.N;
+  out->prec = q.prec;
+  out->eps = q.eps;
+  out->L = q.L;
+  out->M = q.M;
+  out->K = q.K;
+  for (int s = 0; s < q.K && s < GBDLT_MAX_BANDS; ++s) {
+    out->band_ns[s] = q.bands[s].ns;
+    out->band_ka[s] = q.bands[s].ka;
+    out->band_kb[s] = q.bands[s].kb;
+  }
+  out->rec_steps = q.rec_steps;
+  out->seg_len = q.seg;
+  out->flops_dlt = q.flops_dlt;
+  out->bytes_dlt = q.bytes_dlt;
+  out->bytes_idlt = q.bytes_idlt;
+  out->workspace_bytes = ws;
+}
+
+int gbdlt_plan_params(int64_t N, int prec, double eps, gbdlt_params* out) {
+  if (!out) return GBDLT_ERR_INVALID_ARG;
+  Params q;
+  int st = derive_params(N, prec, eps, &q);
+  if (st) return st;
+  fill_public(q, 0, out);
+  return GBDLT_OK;
+}
+
+int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_plan* out) {
+  if (!out) return GBDLT_ERR_INVALID_ARG;
+  *out = nullptr;
+  Plan* P = nullptr;
+  int st = plan_create_impl(N, prec, eps, (cudaStream_t)cuda_stream, &P);
+  if (st) return st;
+  *out = reinterpret_cast<gbdlt_plan>(P);
+  return GBDLT_OK;
+}
+
+int gbdlt_plan_destroy(gbdlt_plan plan) {
+  if (!plan) return GBDLT_ERR_INVALID_ARG;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  cudaStreamSynchronize(P->stream);
+  if (P->arena) cudaFree(P->arena);
+  delete P;
+  return GBDLT_OK;
+}
+
+int gbdlt_plan_set_stream(gbdlt_plan plan, void* cuda_stream) {
+  if (!plan) return GBDLT_ERR_INVALID_ARG;
+  reinterpret_cast<Plan*>(plan)->stream = (cudaStream_t)cuda_stream;
+  return GBDLT_OK;
+}
+
+int gbdlt_plan_sync(gbdlt_plan plan) {
+  if (!plan) return GBDLT_ERR_INVALID_ARG;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return GBDLT_ERR_CUDA;
+  int hs = 0;
+  if (cudaMemcpy(&hs, P->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBDLT_ERR_CUDA;
+  if (hs) {
+    cudaMemset(P->status, 0, sizeof(int));
+    if (hs & 1) return GBDLT_ERR_NOT_CONVERGED;
+  }
+  return check_launch();
+}
+
+int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out) {
+  if (!plan || !out) return GBDLT_ERR_INVALID_ARG;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  fill_public(P->p, P->ws_bytes, out);
+  return GBDLT_OK;
+}
+
+int gbdlt_legpts(gbdlt_plan plan, double* x, double* theta, double* w, double* dtheta) {
+  if (!plan) return GBDLT_ERR_INVALID_ARG;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  int st = launch_legpts(P, P.CN);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * (size_t)P.p.N;
+  if (x && cudaMemcpyAsync(x, P.x, bytes, cudaMemcpyDeviceToDevice, P.stream) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  if (theta && cudaMemcpyAsync(theta, P.theta, bytes, cudaMemcpyDeviceToDevice, P.stream) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  if (w && cudaMemcpyAsync(w, P.w, bytes, cudaMemcpyDeviceToDevice, P.stream) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  if (dtheta) {
+    st = launch_dtheta(P, dtheta);
+    if (st) return st;
+  }
+  return GBDLT_OK;
+}
+
+int gbdlt_leg2cheb(gbdlt_plan p, const void* c, void* chat, int64_t batch) {
+  return run_op(p, OP_L2C, c, chat, batch);
+}
+int gbdlt_leg2cheb_t(gbdlt_plan p, const void* y, void* out, int64_t batch) {
+  return run_op(p, OP_L2C_T, y, out, batch);
+}
+int gbdlt_chebeval(gbdlt_plan p, const void* chat, void* f, int64_t batch) {
+  return run_op(p, OP_CHEB, chat, f, batch);
+}
+int gbdlt_chebeval_t(gbdlt_plan p, const void* g, void* out, int64_t batch) {
+  return run_op(p, OP_CHEB_T, g, out, batch);
+}
+int gbdlt_dlt(gbdlt_plan p, const void* c, void* f, int64_t batch) { return run_op(p, OP_DLT, c, f, batch); }
+int gbdlt_dlt_t(gbdlt_plan p, const void* g, void* out, int64_t batch) {
+  return run_op(p, OP_DLT_T, g, out, batch);
+}
+int gbdlt_idlt(gbdlt_plan p, const void* f, void* c, int64_t batch) { return run_op(p, OP_IDLT, f, c, batch); }
+int gbdlt_idlt_t(gbdlt_plan p, const void* g, void* out, int64_t batch) {
+  return run_op(p, OP_IDLT_T, g, out, batch);
+}
+
+const char* gbdlt_status_string(int s) {
+  switch (s) {
+    case GBDLT_OK: return "ok";
+    case GBDLT_ERR_INVALID_ARG: return "invalid argument";
+    case GBDLT_ERR_UNSUPPORTED_N: return "unsupported N (power of two, 1..2^24)";
+    case GBDLT_ERR_CUDA: return "CUDA error";
+    case GBDLT_ERR_OOM: return "device allocation failed";
+    case GBDLT_ERR_NOT_CONVERGED: return "node iteration did not converge";
+    case GBDLT_ERR_UNIMPLEMENTED: return "unimplemented";
+  }
+  return "unknown status";
+}
+
+uint64_t gbdlt_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

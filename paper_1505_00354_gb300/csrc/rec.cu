@@ -1,0 +1,332 @@
+// Recurrence region of leg2cheb and of its transpose (Sec. 3; the direct
+// three-term recurrence of Sec. 2.4 / Sec. 4.1 applied where the asymptotic
+// expansion of P_n(cos theta) is not accurate).
+//
+// Rows are the cheb1 points theta_k = (k+1/2)pi/N.  Row k uses the recurrence for
+// columns n < cut(k) (cut = N for the rows nearest theta = 0, pi; the band's
+// column cut otherwise).  Rows k and N-1-k share one recurrence because
+// P_n(-x) = (-1)^n P_n(x): with E = sum over even n and O over odd n of c_n P_n(x_k),
+//   v_k = E + O,  v_{N-1-k} = E - O.
+// The recurrence runs in difference form with x - 1 = -2 sin^2(theta/2) computed
+// directly (no cancellation near x = 1, where the plain form loses ~n^2 u):
+//   D_{n+1} = [(2n+1)(x-1) P_n + n D_n] / (n+1),   P_{n+1} = P_n + D_{n+1},
+//   (P_0, D_0) = (1, 1).
+// Each half row's column range is cut into segments of S = 512 columns; the
+// state (P, D) at every segment start depends only on N, so the plan computes it
+// once (two basis solutions per segment, then a scan per row) and the transforms
+// run every segment independently.  All recurrence arithmetic is FP64.
+#include "gbdlt_internal.cuh"
+
+namespace gbdlt {
+
+namespace {
+
+constexpr int RT = 256;  // threads per CTA = half rows per row block
+
+struct RecArgs {
+  int64_t N, H;
+  int S;
+  int64_t nblocks;
+  const int32_t* cut;
+  const int64_t* poff;
+  const double2* state;
+  const int32_t* cta_rb;
+  const int32_t* cta_j;
+  const int64_t* toff;
+  const int32_t* maxcut;
+  const double* ra;
+  const double* rb;
+};
+
+RecArgs rec_args(const Plan& P) {
+  RecArgs a;
+  a.N = P.p.N;
+  a.H = P.rec.H;
+  a.S = P.rec.S;
+  a.nblocks = P.rec.nblocks;
+  a.cut = P.rec.cut;
+  a.poff = P.rec.poff;
+  a.state = P.rec.state;
+  a.cta_rb = P.rec.cta_rb;
+  a.cta_j = P.rec.cta_j;
+  a.toff = P.rec.toff;
+  a.maxcut = P.rec.bcutmax;
+  a.ra = P.ra;
+  a.rb = P.rb;
+  return a;
+}
+
+__device__ __forceinline__ double xm1_of(int64_t k, int64_t N) {
+  const double s = sinpi((double)(2 * k + 1) / (double)(4 * N));
+  return -2.0 * s * s;
+}
+
+__device__ __forceinline__ int nseg_of(const RecArgs& R, int64_t k) {
+  return (R.cut[k] + R.S - 1) / R.S;
+}
+
+// transfer matrix of one full segment: images of the basis states (1,0), (0,1)
+__global__ void k_rec_basis(RecArgs R, double2* __restrict__ Tbuf) {
+  const int64_t rbk = R.cta_rb[blockIdx.x];
+  const int j = R.cta_j[blockIdx.x];
+  const int64_t k = rbk * RT + threadIdx.x;
+  if (k >= R.H) return;
+  if (j >= nseg_of(R, k) - 1) return;
+  const double xm1 = xm1_of(k, R.N);
+  double P1 = 1.0, D1 = 0.0, P2 = 0.0, D2 = 1.0;
+  const int64_t n0 = (int64_t)j * R.S;
+  for (int64_t n = n0; n < n0 + R.S; ++n) {
+    const double t = R.ra[n] * xm1;
+    const double b = R.rb[n];
+    D1 = fma(t, P1, b * D1);
+    P1 += D1;
+    D2 = fma(t, P2, b * D2);
+    P2 += D2;
+  }
+  const int64_t o = 2 * (R.poff[k] + j);
+  Tbuf[o] = make_double2(P1, D1);
+  Tbuf[o + 1] = make_double2(P2, D2);
+}
+
+__global__ void k_rec_scan(RecArgs R, const double2* __restrict__ Tbuf, double2* __restrict__ state) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= R.H) return;
+  const int ns = nseg_of(R, k);
+  if (ns == 0) return;
+  const int64_t o = R.poff[k];
+  double P = 1.0, D = 1.0;
+  state[o] = make_double2(P, D);
+  for (int j = 0; j + 1 < ns; ++j) {
+    const double2 a = Tbuf[2 * (o + j)], b = Tbuf[2 * (o + j) + 1];
+    const double nP = a.x * P + b.x * D;
+    const double nD = a.y * P + b.y * D;
+    P = nP;
+    D = nD;
+    state[o + j + 1] = make_double2(P, D);
+  }
+}
+
+// forward: per (half row, segment) the partial sums E (even n) and O (odd n)
+template <typename T>
+__global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__ c,
+                                                double2* __restrict__ part) {
+  const int64_t rbk = R.cta_rb[blockIdx.x];
+  const int j = R.cta_j[blockIdx.x];
+  const int64_t k = rbk * RT + threadIdx.x;
+  if (k >= R.H) return;
+  const int cut = R.cut[k];
+  if (j >= (cut + R.S - 1) / R.S) return;
+  const int64_t o = R.poff[k] + j;
+  const double2 st = R.state[o];
+  double P = st.x, D = st.y;
+  const double xm1 = xm1_of(k, R.N);
+  const int64_t n0 = (int64_t)j * R.S;
+  const int64_t n1 = min(n0 + R.S, (int64_t)cut);
+  double E = 0.0, O = 0.0;
+  int64_t n = n0;
+  for (; n + 1 < n1; n += 2) {
+    E = fma((double)c[n], P, E);
+    double t = R.ra[n] * xm1;
+    D = fma(t, P, R.rb[n] * D);
+    P += D;
+    O = fma((double)c[n + 1], P, O);
+    t = R.ra[n + 1] * xm1;
+    D = fma(t, P, R.rb[n + 1] * D);
+    P += D;
+  }
+  if (n < n1) E = fma((double)c[n], P, E);
+  part[o] = make_double2(E, O);
+}
+
+// sum of a half row's segment partials; warp per row for rows [r0, r1) when
+// warp_mode, thread per row otherwise
+template <typename T>
+__global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T* __restrict__ vrec,
+                                 int64_t r0, int64_t r1, int warp_mode) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double E = 0.0, O = 0.0;
+  int64_t k;
+  if (warp_mode) {
+    k = r0 + gt / 32;
+    const int lane = threadIdx.x & 31;
+    if (k >= r1) return;  // whole warp leaves together
+    const int ns = nseg_of(R, k);
+    const int64_t o = R.poff[k];
+    for (int j = lane; j < ns; j += 32) {
+      const double2 p = part[o + j];
+      E += p.x;
+      O += p.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      E += __shfl_down_sync(0xffffffffu, E, off);
+      O += __shfl_down_sync(0xffffffffu, O, off);
+    }
+    if (lane != 0) return;
+  } else {
+    k = r0 + gt;
+    if (k >= r1) return;
+    const int ns = nseg_of(R, k);
+    const int64_t o = R.poff[k];
+    for (int j = 0; j < ns; ++j) {
+      const double2 p = part[o + j];
+      E += p.x;
+      O += p.y;
+    }
+  }
+  vrec[k] = (T)(E + O);
+  vrec[R.N - 1 - k] = (T)(E - O);
+}
+
+// transposed: out_n = sum_k z_k P_n(x_k) over rows with n < cut(k).  A CTA takes
+// 256 half rows x one segment; every 32 columns each lane writes its 32 products
+// into a per-warp tile, the tile is summed by columns (shared-memory transpose),
+// and the 8 warp sums are added into the row block's partial array.
+constexpr int TP = 33;  // tile pitch (doubles)
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z,
+                                              double* __restrict__ tbuf) {
+  extern __shared__ double sm[];
+  double* tile = sm;                  // [8][32][TP]
+  double* wsum = sm + 8 * 32 * TP;    // [8][32]
+  const int64_t rbk = R.cta_rb[blockIdx.x];
+  const int j = R.cta_j[blockIdx.x];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = rbk * RT + threadIdx.x;
+  bool active = k < R.H;
+  int cut = 0;
+  double zp = 0.0, zm = 0.0, P = 0.0, D = 0.0, xm1 = 0.0;
+  if (active) {
+    cut = R.cut[k];
+    active = j < (cut + R.S - 1) / R.S;
+  }
+  if (active) {
+    const double a = (double)z[k], b = (double)z[R.N - 1 - k];
+    zp = a + b;
+    zm = a - b;
+    const double2 st = R.state[R.poff[k] + j];
+    P = st.x;
+    D = st.y;
+    xm1 = xm1_of(k, R.N);
+  } else {
+    cut = 0;
+  }
+  const int64_t n0s = (int64_t)j * R.S;
+  const int64_t seg_end = min(n0s + R.S, (int64_t)R.maxcut[rbk]);
+  double* mytile = tile + (w * 32 + lane) * TP;
+  for (int64_t n0 = n0s; n0 < seg_end; n0 += 32) {
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const int64_t n = n0 + i;
+      double val = 0.0;
+      if (n < cut) {
+        val = ((n & 1) ? zm : zp) * P;
+        const double t = R.ra[n] * xm1;
+        D = fma(t, P, R.rb[n] * D);
+        P += D;
+      }
+      mytile[i] = val;
+    }
+    __syncwarp();
+    double colsum = 0.0;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) colsum += tile[(w * 32 + r) * TP + lane];
+    wsum[w * 32 + lane] = colsum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += wsum[q * 32 + threadIdx.x];
+      const int64_t n = n0 + threadIdx.x;
+      if (n < seg_end) tbuf[R.toff[rbk] + n] = s;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_rec_t_reduce(RecArgs R, const double* __restrict__ tbuf, T* __restrict__ out) {
+  __shared__ double red[8][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (n < R.N) {
+    for (int64_t rb = w; rb < R.nblocks && (int64_t)R.maxcut[rb] > n; rb += 8) s += tbuf[R.toff[rb] + n];
+  }
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && n < R.N) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    out[n] = (T)t;
+  }
+}
+
+}  // namespace
+
+int launch_rec_state_init(Plan& P) {
+  RecLayout& L = P.rec;
+  if (L.H == 0 || L.nseg_total == 0) return GBDLT_OK;
+  double2* Tbuf = nullptr;
+  if (cudaMalloc(&Tbuf, sizeof(double2) * 2 * (size_t)L.nseg_total) != cudaSuccess) {
+    cudaGetLastError();
+    return GBDLT_ERR_OOM;
+  }
+  RecArgs R = rec_args(P);
+  k_rec_basis<<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, Tbuf);
+  count_launch();
+  k_rec_scan<<<(unsigned)((L.H + 127) / 128), 128, 0, P.stream>>>(R, Tbuf, L.state);
+  count_launch();
+  int st = check_launch();
+  cudaStreamSynchronize(P.stream);
+  cudaFree(Tbuf);
+  return st;
+}
+
+template <typename T>
+int launch_rec_forward(Plan& P, const T* c, T* vrec) {
+  RecLayout& L = P.rec;
+  RecArgs R = rec_args(P);
+  if (L.H == 0) return GBDLT_OK;
+  k_rec_fwd<T><<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, c, L.part);
+  count_launch();
+  if (L.n_long > 0) {
+    const int64_t threads = L.n_long * 32;
+    k_rec_fwd_reduce<T><<<(unsigned)((threads + 255) / 256), 256, 0, P.stream>>>(R, L.part, vrec, 0,
+                                                                                 L.n_long, 1);
+    count_launch();
+  }
+  if (L.H > L.n_long) {
+    const int64_t rows = L.H - L.n_long;
+    k_rec_fwd_reduce<T><<<(unsigned)((rows + 255) / 256), 256, 0, P.stream>>>(R, L.part, vrec,
+                                                                              L.n_long, L.H, 0);
+    count_launch();
+  }
+  return check_launch();
+}
+
+template <typename T>
+int launch_rec_transpose(Plan& P, const T* z, T* out) {
+  RecLayout& L = P.rec;
+  RecArgs R = rec_args(P);
+  if (L.H == 0) return GBDLT_OK;
+  const size_t smem = sizeof(double) * (8 * 32 * TP + 8 * 32);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_rec_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_rec_t<T><<<(unsigned)L.ncta, RT, smem, P.stream>>>(R, z, L.tbuf);
+  count_launch();
+  k_rec_t_reduce<T><<<(unsigned)((P.p.N + 31) / 32), 256, 0, P.stream>>>(R, L.tbuf, out);
+  count_launch();
+  return check_launch();
+}
+
+template int launch_rec_forward<double>(Plan&, const double*, double*);
+template int launch_rec_forward<float>(Plan&, const float*, float*);
+template int launch_rec_transpose<double>(Plan&, const double*, double*);
+template int launch_rec_transpose<float>(Plan&, const float*, float*);
+
+}  // namespace gbdlt

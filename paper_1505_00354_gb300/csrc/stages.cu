@@ -1,0 +1,519 @@
+// Pre- and post-processing kernels around the FFT engine.
+//
+// Grid: theta_k = (k+1/2) pi / N, the Chebyshev points of the first kind (Eq. 5).
+// Every DCT/DST the method needs (Eq. 13 and its transpose, Sec. 4 item 2) is
+// one complex FFT of length N through one of three reductions:
+//
+//  FCS  (forward, one real input a):  Z_k = sum_n a_n e^{i n theta_k}.
+//       u_n = a_n e^{i pi n/(2N)},  y = FFT+(u),  Z_{2m} = y_m,
+//       Z_{2m+1} = conj(y_{N-1-m}).  Re Z is the DCT-III of Sec. 2.3, Im Z the DST-III.
+//  F2   (forward pair, X of a and Y of b):  U_n = e^{i pi n/(2N)} [(a_n + b_n) - i(a_{N-n} - b_{N-n})],
+//       U_0 = 2 a_0, y = FFT+(U);  X_a(2m) = Re y_m / 2, X_a(2m+1) = Re y_{N-1-m} / 2,
+//       Y_b(k) = (-1)^k Im y_{m'} / 2 at the same index (a_N = b_N = 0).
+//  T2   (transposed pair, DCT-II of a and DST-II of b):  with h_k = (-1)^k b_k,
+//       v_{k'} = a_{2k'} + i h_{2k'},  v_{N-1-k'} = a_{2k'+1} + i h_{2k'+1},  F = FFT-(v);
+//       U_n = Re[e^{-i pi n/(2N)} (F_n + conj F_{N-n})/2],
+//       V_n = Re[e^{-i pi (N-n)/(2N)} (F_{N-n} - conj F_n)/(2i)]  (V_0 = 0).
+//
+// Stage kernels (one launch each; thread per output element):
+//  l2c_pro / l2c_epi   asymptotic part of leg2cheb (Sec. 3, expansion of
+//                      P_n(cos theta)): per band s and term m the FCS of
+//                      a^{(m)}_n = C_n h_{m,n} c_n [n >= ns], combined as
+//                      v_k += sum_m Re[e^{i(m+1/2)(theta_k - pi/2)} Z^{(s,m)}_k] / (2 sin theta_k)^{m+1/2}
+//  a4_pro / a4_epi     values on the cheb1 grid -> Chebyshev coefficients:
+//                      chat_j = (2/N) sum_k v_k cos(j theta_k), halved at j = 0
+//  tay_pro / tay_epi   Taylor NDCT, Eq. (13): f_k = [v_k] + sum_l Re[(i t_k)^l/l! Z_l(k)],
+//                      Z_l = FCS((n/N)^l chat), t_k = N dtheta_k; terms paired (F2)
+//  tayt_pro / tayt_epi transposed Taylor sum (Sec. 4 item 2), pairs through T2
+//  l2ct_pro / l2ct_epi transposed asymptotic part (Sec. 4 item 3)
+#include "gbdlt_internal.cuh"
+
+namespace gbdlt {
+
+namespace {
+
+struct BandArgs {
+  int K;
+  int64_t ns[GBDLT_MAX_BANDS];
+  int64_t ka[GBDLT_MAX_BANDS];
+  int64_t kb[GBDLT_MAX_BANDS];
+};
+
+BandArgs band_args(const Plan& P) {
+  BandArgs b{};
+  b.K = P.p.K;
+  for (int s = 0; s < P.p.K; ++s) {
+    b.ns[s] = P.p.bands[s].ns;
+    b.ka[s] = P.p.bands[s].ka;
+    b.kb[s] = P.p.bands[s].kb;
+  }
+  return b;
+}
+
+struct TwArgs {
+  const double2* hi;
+  const double2* lo;
+};
+
+// e^{2 pi i e / B} from the two-level table, multiplied in precision T
+template <typename T>
+__device__ __forceinline__ C2<T> twid(TwArgs t, int64_t e) {
+  double2 h = t.hi[e >> 12];
+  double2 l = t.lo[e & 4095];
+  return cmul<T>(to_c<T>(h), to_c<T>(l));
+}
+
+__device__ __forceinline__ void sincospi_t(double a, double* s, double* c) { sincospi(a, s, c); }
+__device__ __forceinline__ void sincospi_t(float a, float* s, float* c) { sincospif(a, s, c); }
+
+__device__ __forceinline__ int band_of(const BandArgs& B, int64_t k, int64_t N) {
+  int64_t kk = k < N - 1 - k ? k : N - 1 - k;
+  for (int s = 0; s < B.K; ++s)
+    if (kk >= B.ka[s] && kk < B.kb[s]) return s;
+  return -1;
+}
+
+// signed Taylor coefficient of the cos part ((-1)^{l/2}, l even) and of the sin
+// part ((-1)^{(l+1)/2}, l odd), Eq. (6)
+__device__ __forceinline__ int sgn_even(int l) { return ((l >> 1) & 1) ? -1 : 1; }
+__device__ __forceinline__ int sgn_odd(int l) { return (((l + 1) >> 1) & 1) ? -1 : 1; }
+
+// ---------------------------------------------------------------- leg2cheb
+template <typename T>
+__global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, int64_t N, int M,
+                          BandArgs B, const double* __restrict__ Cn, TwArgs tw4N) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const T cn = (T)Cn[n] * c[n];
+  const C2<T> e = twid<T>(tw4N, n);
+  const T nn = (T)n;
+  T h = (T)1;
+  for (int m = 0; m < M; ++m) {
+    const T a = cn * h;
+    const C2<T> val = mk<T>(a * e.x, a * e.y);
+    const C2<T> zero = mk<T>((T)0, (T)0);
+    for (int s = 0; s < B.K; ++s) U[(int64_t)(s * M + m) * N + n] = (n >= B.ns[s]) ? val : zero;
+    const T mh = (T)m + (T)0.5;
+    h = h * (mh * mh) / (((T)m + (T)1) * (nn + (T)m + (T)1.5));
+  }
+}
+
+template <typename T>
+__global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const T* __restrict__ vrec, T* __restrict__ v,
+                          int64_t N, int M, BandArgs B) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  T acc = vrec[k];
+  const int s = band_of(B, k, N);
+  if (s >= 0) {
+    T st, ct, sa, ca;
+    sincospi_t((T)(2 * k + 1) / (T)(2 * N), &st, &ct);            // theta_k
+    sincospi_t((T)(2 * k + 1 - N) / (T)(4 * N), &sa, &ca);        // theta_k/2 - pi/4
+    const T g = (T)0.5 / st;
+    const T sq = sqrt(g);
+    C2<T> al = mk<T>(ca * sq, sa * sq);
+    const C2<T> rho = mk<T>(st * g, -ct * g);
+    const bool odd = k & 1;
+    const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
+    const C2<T>* y = Y + (int64_t)s * M * N + idx;
+    for (int m = 0; m < M; ++m) {
+      C2<T> z = y[(int64_t)m * N];
+      if (odd) z.y = -z.y;
+      acc += al.x * z.x - al.y * z.y;
+      al = cmul<T>(al, rho);
+    }
+  }
+  v[k] = acc;
+}
+
+// ---------------------------------------------------------------- A4: values -> coefficients
+template <typename T>
+__global__ void k_a4_pro(const T* __restrict__ v, C2<T>* __restrict__ U, int64_t N) {
+  const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= N / 2) return;
+  U[kp] = mk<T>(v[2 * kp], (T)0);
+  U[N - 1 - kp] = mk<T>(v[2 * kp + 1], (T)0);
+}
+
+template <typename T>
+__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, TwArgs tw4N) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const C2<T> Fn = F[n];
+  const C2<T> Fm = F[(N - n) & (N - 1)];
+  const C2<T> Vh = mk<T>((Fn.x + Fm.x) * (T)0.5, (Fn.y - Fm.y) * (T)0.5);
+  const C2<T> e = twid<T>(tw4N, n);  // conj(e) = e^{-i pi n/(2N)}
+  const T U = e.x * Vh.x + e.y * Vh.y;
+  chat[n] = (n == 0 ? (T)1 / (T)N : (T)2 / (T)N) * U;
+}
+
+// ---------------------------------------------------------------- FCS helpers
+template <typename T>
+__global__ void k_fcs_pro(const T* __restrict__ a, C2<T>* __restrict__ U, int64_t N, int scale_d,
+                          TwArgs tw4N) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  T an = a[n];
+  if (scale_d) an *= (n == 0 ? (T)1 : (T)2) / (T)N;
+  const C2<T> e = twid<T>(tw4N, n);
+  U[n] = mk<T>(an * e.x, an * e.y);
+}
+
+template <typename T>
+__global__ void k_fcs_re_epi(const C2<T>* __restrict__ Y, T* __restrict__ out, int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t idx = (k & 1) ? N - 1 - (k >> 1) : (k >> 1);
+  out[k] = Y[idx].x;
+}
+
+// ---------------------------------------------------------------- Taylor (forward)
+// pair p: X part l_a = 2p + (inc0 ? 0 : 2), Y part l_b = 2p + 1; a term is used
+// only when its l <= L-1.
+template <typename T>
+__global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int64_t N, int L,
+                          int inc0, int npair, TwArgs tw4N) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const T r = (T)n / (T)N;
+  const T rN = (T)(N - n) / (T)N;
+  const T cn = chat[n];
+  const T cm = n > 0 ? chat[N - n] : (T)0;
+  const C2<T> e = twid<T>(tw4N, n);
+  // r^l and rN^l for the current pair, advanced by r^2 per pair
+  const T r2 = r * r, rN2 = rN * rN;
+  T pa = inc0 ? (T)1 : r2, paN = inc0 ? (T)1 : rN2;  // r^{l_a}
+  T pb = r, pbN = rN;                               // r^{l_b}
+  for (int p = 0; p < npair; ++p) {
+    const int la = 2 * p + (inc0 ? 0 : 2);
+    const int lb = 2 * p + 1;
+    const T ua = la <= L - 1 ? (T)1 : (T)0;
+    const T ub = lb <= L - 1 ? (T)1 : (T)0;
+    C2<T> val;
+    if (n == 0) {
+      val = mk<T>((T)2 * ua * pa * cn, (T)0);  // 0^0 = 1 for l_a = 0
+    } else {
+      const T a = ua * pa * cn, b = ub * pb * cn;
+      const T aN = ua * paN * cm, bN = ub * pbN * cm;
+      const T re = a + b, im = -(aN - bN);
+      val = mk<T>(re * e.x - im * e.y, re * e.y + im * e.x);
+    }
+    U[(int64_t)p * N + n] = val;
+    pa *= r2;
+    paN *= rN2;
+    pb *= r2;
+    pbN *= rN2;
+  }
+}
+
+template <typename T>
+__global__ void k_tay_epi(const C2<T>* __restrict__ Y, const T* __restrict__ v, T* __restrict__ f,
+                          const double* __restrict__ tN, int64_t N, int L, int inc0, int npair) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const T t = (T)tN[k];
+  const bool odd = k & 1;
+  const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
+  const T sk = odd ? (T)-1 : (T)1;
+  T acc = inc0 ? (T)0 : v[k];
+  // q_l = t^l / l!
+  T q[2 * 16 + 3];
+  q[0] = (T)1;
+  for (int l = 1; l < L; ++l) q[l] = q[l - 1] * t / (T)l;
+  for (int p = 0; p < npair; ++p) {
+    const int la = 2 * p + (inc0 ? 0 : 2);
+    const int lb = 2 * p + 1;
+    const C2<T> y = Y[(int64_t)p * N + idx];
+    if (la <= L - 1) acc += (T)sgn_even(la) * q[la] * (T)0.5 * y.x;
+    if (lb <= L - 1) acc += (T)sgn_odd(lb) * q[lb] * (T)0.5 * sk * y.y;
+  }
+  f[k] = acc;
+}
+
+// ---------------------------------------------------------------- Taylor (transposed)
+template <typename T>
+__global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__ wscale,
+                           const double* __restrict__ tN, C2<T>* __restrict__ U, int64_t N, int L,
+                           int inc0, int npair) {
+  const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= N / 2) return;
+  const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
+  T g0 = fin[k0], g1 = fin[k1];
+  if (wscale) {
+    g0 *= (T)wscale[k0];
+    g1 *= (T)wscale[k1];
+  }
+  const T t0 = (T)tN[k0], t1 = (T)tN[k1];
+  const T t02 = t0 * t0, t12 = t1 * t1;
+  T pa0 = inc0 ? (T)1 : t02, pa1 = inc0 ? (T)1 : t12;
+  T pb0 = t0, pb1 = t1;
+  for (int p = 0; p < npair; ++p) {
+    const int la = 2 * p + (inc0 ? 0 : 2);
+    const int lb = 2 * p + 1;
+    const T ua = la <= L - 1 ? (T)1 : (T)0;
+    const T ub = lb <= L - 1 ? (T)1 : (T)0;
+    // h_k = (-1)^k b_k: k0 even, k1 odd
+    U[(int64_t)p * N + kp] = mk<T>(ua * pa0 * g0, ub * pb0 * g0);
+    U[(int64_t)p * N + N - 1 - kp] = mk<T>(ua * pa1 * g1, -ub * pb1 * g1);
+    pa0 *= t02;
+    pa1 *= t12;
+    pb0 *= t02;
+    pb1 *= t12;
+  }
+}
+
+// mode 0: write the FCS input of A4^T, Q_n = d_n u'_n e^{i pi n/(2N)};
+// mode 1: write u_n to uout.
+template <typename T>
+__global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T* __restrict__ uout,
+                           int64_t N, int L, int inc0, int npair, int mode, TwArgs tw4N) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const T r = (T)n / (T)N;
+  const C2<T> e = twid<T>(tw4N, n);
+  const int64_t nm = (N - n) & (N - 1);
+  T q[2 * 16 + 3];
+  q[0] = (T)1;
+  for (int l = 1; l < L; ++l) q[l] = q[l - 1] * r / (T)l;
+  T acc = (T)0;
+  for (int p = 0; p < npair; ++p) {
+    const int la = 2 * p + (inc0 ? 0 : 2);
+    const int lb = 2 * p + 1;
+    const C2<T> Fn = F[(int64_t)p * N + n];
+    const C2<T> Fm = F[(int64_t)p * N + nm];
+    if (la <= L - 1) {
+      // U_n = Re[conj(e) (Fn + conj Fm)/2]
+      const T vx = (Fn.x + Fm.x) * (T)0.5, vy = (Fn.y - Fm.y) * (T)0.5;
+      acc += (T)sgn_even(la) * q[la] * (e.x * vx + e.y * vy);
+    }
+    if (lb <= L - 1 && n > 0) {
+      // V_n = Re[(-i e) (Fm - conj Fn)/(2i)] = Re[-e (Fm - conj Fn)]/2
+      const T wx = Fm.x - Fn.x, wy = Fm.y + Fn.y;
+      acc += (T)sgn_odd(lb) * q[lb] * (T)(-0.5) * (e.x * wx - e.y * wy);
+    }
+  }
+  if (mode == 0) {
+    const T d = (n == 0 ? (T)1 : (T)2) / (T)N;
+    const T a = d * acc;
+    Q[n] = mk<T>(a * e.x, a * e.y);
+  } else {
+    uout[n] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- leg2cheb (transposed)
+// Per row: z_k = [g_k] + Re Z_k (A4^T output, when Y != null); then for its band
+// s and each m the T2 input beta = z_k alpha_{m,k} (alpha as in the forward
+// combine) is written for (s, m) and zeros for every other band.
+template <typename T>
+__device__ __forceinline__ T row_z(const C2<T>* Y, const T* g, const double* wscale, int64_t k,
+                                   int64_t N) {
+  T z = (T)0;
+  if (g) {
+    z = g[k];
+    if (wscale) z *= (T)wscale[k];
+  }
+  if (Y) {
+    const int64_t idx = (k & 1) ? N - 1 - (k >> 1) : (k >> 1);
+    z += Y[idx].x;
+  }
+  return z;
+}
+
+template <typename T>
+__device__ __forceinline__ void alpha_init(int64_t k, int64_t N, C2<T>* al, C2<T>* rho) {
+  T st, ct, sa, ca;
+  sincospi_t((T)(2 * k + 1) / (T)(2 * N), &st, &ct);
+  sincospi_t((T)(2 * k + 1 - N) / (T)(4 * N), &sa, &ca);
+  const T g = (T)0.5 / st;
+  const T sq = sqrt(g);
+  *al = mk<T>(ca * sq, sa * sq);
+  *rho = mk<T>(st * g, -ct * g);
+}
+
+template <typename T>
+__global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
+                           const double* __restrict__ wscale, T* __restrict__ zout,
+                           C2<T>* __restrict__ U, int64_t N, int M, BandArgs B) {
+  const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= N / 2) return;
+  const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
+  const T z0 = row_z<T>(Y, g, wscale, k0, N);
+  const T z1 = row_z<T>(Y, g, wscale, k1, N);
+  zout[k0] = z0;
+  zout[k1] = z1;
+  const int s0 = band_of(B, k0, N), s1 = band_of(B, k1, N);
+  C2<T> al0 = mk<T>(0, 0), rho0 = mk<T>(0, 0), al1 = mk<T>(0, 0), rho1 = mk<T>(0, 0);
+  if (s0 >= 0) alpha_init<T>(k0, N, &al0, &rho0);
+  if (s1 >= 0) alpha_init<T>(k1, N, &al1, &rho1);
+  for (int m = 0; m < M; ++m) {
+    // beta = z alpha; a = Re beta, h = (-1)^k Im beta
+    const C2<T> v0 = mk<T>(z0 * al0.x, z0 * al0.y);
+    const C2<T> v1 = mk<T>(z1 * al1.x, -z1 * al1.y);
+    for (int s = 0; s < B.K; ++s) {
+      C2<T>* u = U + (int64_t)(s * M + m) * N;
+      u[kp] = (s == s0) ? v0 : mk<T>(0, 0);
+      u[N - 1 - kp] = (s == s1) ? v1 : mk<T>(0, 0);
+    }
+    if (s0 >= 0) al0 = cmul<T>(al0, rho0);
+    if (s1 >= 0) al1 = cmul<T>(al1, rho1);
+  }
+}
+
+template <typename T>
+__global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ rect, T* __restrict__ out,
+                           int64_t N, int M, BandArgs B, const double* __restrict__ Cn, int scale_s,
+                           TwArgs tw4N) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  T acc = rect[n];
+  if (B.K > 0 && M > 0) {
+    const C2<T> e = twid<T>(tw4N, n);
+    const int64_t nm = (N - n) & (N - 1);
+    const T cn = (T)Cn[n];
+    const T nn = (T)n;
+    T h = (T)1;
+    for (int m = 0; m < M; ++m) {
+      T sum = (T)0;
+      for (int s = 0; s < B.K; ++s) {
+        if (n < B.ns[s]) continue;
+        const C2<T>* f = F + (int64_t)(s * M + m) * N;
+        const C2<T> Fn = f[n], Fm = f[nm];
+        const T U = e.x * (Fn.x + Fm.x) + e.y * (Fn.y - Fm.y);  // 2 * DCT-II part
+        T V = (T)0;
+        if (n > 0) V = -(e.x * (Fm.x - Fn.x) - e.y * (Fm.y + Fn.y));  // 2 * DST-II part
+        sum += (U - V);
+      }
+      acc += (T)0.5 * cn * h * sum;
+      const T mh = (T)m + (T)0.5;
+      h = h * (mh * mh) / (((T)m + (T)1) * (nn + (T)m + (T)1.5));
+    }
+  }
+  out[n] = scale_s ? ((T)n + (T)0.5) * acc : acc;
+}
+
+// which: 0 copy, 1 multiply by (n + 1/2), 2 multiply by w_k, 3 dtheta = tN / N (double out)
+template <typename T>
+__global__ void k_scale(const T* __restrict__ in, T* __restrict__ out, const double* __restrict__ w,
+                        int64_t N, int which) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  T v = in[n];
+  if (which == 1) v *= ((T)n + (T)0.5);
+  if (which == 2) v *= (T)w[n];
+  out[n] = v;
+}
+
+constexpr int TPB = 256;
+inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+}  // namespace
+
+template <typename T>
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U) {
+  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  k_l2c_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn, tw);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v) {
+  k_l2c_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P));
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_a4_pro(Plan& P, const T* v, C2<T>* U) {
+  k_a4_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(v, U, P.p.N);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_a4_epi(Plan& P, const C2<T>* F, T* chat) {
+  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  k_a4_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, chat, P.p.N, tw);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d) {
+  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  k_fcs_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, tw);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out) {
+  k_fcs_re_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, out, P.p.N);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair) {
+  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  k_tay_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(chat, U, P.p.N, P.p.L, inc0, npair, tw);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair) {
+  k_tay_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, v, f, P.tN, P.p.N, P.p.L, inc0, npair);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair) {
+  const double* w = use_w ? P.w : nullptr;
+  k_tayt_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(f, w, P.tN, U, P.p.N, P.p.L, inc0, npair);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair) {
+  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const int mode = Q ? 0 : 1;
+  k_tayt_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, mode, tw);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U) {
+  const double* w = use_w ? P.w : nullptr;
+  k_l2ct_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P));
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s) {
+  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  k_l2ct_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
+                                                     scale_s, tw);
+  count_launch();
+  return check_launch();
+}
+template <typename T>
+int launch_scale(Plan& P, const T* in, T* out, int which) {
+  k_scale<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(in, out, P.w, P.p.N, which);
+  count_launch();
+  return check_launch();
+}
+
+#define INST(T)                                                                              \
+  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*);                                   \
+  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const T*, T*);                         \
+  template int launch_a4_pro<T>(Plan&, const T*, C2<T>*);                                    \
+  template int launch_a4_epi<T>(Plan&, const C2<T>*, T*);                                    \
+  template int launch_fcs_pro<T>(Plan&, const T*, C2<T>*, int);                              \
+  template int launch_fcs_re_epi<T>(Plan&, const C2<T>*, T*);                                \
+  template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, int, int);                         \
+  template int launch_tay_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int);                   \
+  template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, int, int);                   \
+  template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int);                \
+  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*);           \
+  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const T*, T*, int);                   \
+  template int launch_scale<T>(Plan&, const T*, T*, int);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace gbdlt

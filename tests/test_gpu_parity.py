@@ -1,0 +1,288 @@
+"""GPU parity: every entry point of the C ABI against the CPU oracle.
+
+Inputs come from the seeded generators in paper_1505_00354_gb300.inputs (the
+distributions of the paper's experiments).  Error measures:
+  * DLT / NDCT / leg2cheb: max_k |f_gpu - f_oracle| / ||c||_1  (Corollary 2.2's
+    normalisation); bar 1e-12 for the FP64 form, 5e-6 for the FP32 form.
+  * IDLT: max_n |c_gpu - c_oracle| / ((n+1/2) ||w f||_1), the same bound carried
+    through the transposed chain; same bars.
+  * nodes: |x_gpu - x|, |w_gpu - w|/w, N |dtheta_gpu - dtheta| (t_k scale).
+Full vectors at N <= 4096 (one to several FFT tiles plus the recurrence region);
+sampled rows (oracle computes each row on its own) at N = 2^13 .. 2^22.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 5e-6
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_00354_gb300 import build
+    build.build()
+    import paper_1505_00354_gb300 as g
+    return g
+
+
+@functools.lru_cache(maxsize=None)
+def onodes(N, rows=None):
+    import oracle
+    return oracle.legpts(N, None if rows is None else np.array(rows, dtype=np.int64))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+SMALL = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+
+
+# --------------------------------------------------------------------------
+# nodes and weights
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", SMALL)
+def test_legpts_full(gb, N):
+    x, th, w, dth = [host(t) for t in gb.Plan(N).legpts()]
+    nd = onodes(N)
+    ex = np.max(np.abs(x - nd.x))
+    ew = np.max(np.abs(w - nd.w) / nd.w)
+    et = np.max(np.abs(dth - nd["dtheta"])) * N
+    eth = np.max(np.abs(th - nd.theta))
+    print(f"N={N} x {ex:.2e} w {ew:.2e} t {et:.2e} theta {eth:.2e}")
+    assert ex <= 4e-16
+    assert ew <= 1e-14
+    assert et <= 2e-14
+    assert eth <= 1e-15
+    # ordering: theta ascending, x descending
+    assert np.all(np.diff(th) > 0) and np.all(np.diff(x) < 0)
+
+
+@pytest.mark.parametrize("N", [2**13, 2**16, 2**20, 2**22])
+def test_legpts_sampled(gb, N):
+    import paper_1505_00354_gb300.inputs as inp
+    rows = inp.sample_rows(N, 96, seed=1000 + int(math.log2(N)), include_ends=24)
+    x, th, w, dth = [host(t) for t in gb.Plan(N).legpts()]
+    nd = onodes(N, tuple(rows.tolist()))
+    ex = np.max(np.abs(x[rows] - nd.x))
+    ew = np.max(np.abs(w[rows] - nd.w) / nd.w)
+    et = np.max(np.abs(dth[rows] - nd["dtheta"])) * N
+    print(f"N={N} x {ex:.2e} w {ew:.2e} t {et:.2e}")
+    assert ex <= 4e-16
+    assert ew <= 1e-14
+    assert et <= 2e-14
+
+
+# --------------------------------------------------------------------------
+# transforms, full vectors
+# --------------------------------------------------------------------------
+def _c(N, seed, decay=0.0):
+    import paper_1505_00354_gb300.inputs as inp
+    return inp.coeffs(N, seed, decay)
+
+
+@pytest.mark.parametrize("N", SMALL)
+def test_leg2cheb_full(gb, N):
+    import oracle
+    c = _c(N, 1)
+    got = host(gb.Plan(N).leg2cheb(dev(c)))
+    err = np.max(np.abs(got - oracle.leg2cheb(c))) / np.abs(c).sum()
+    print(f"N={N} leg2cheb err/||c||1 = {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("N", SMALL)
+def test_chebeval_full(gb, N):
+    import oracle
+    c = _c(N, 2)
+    got = host(gb.Plan(N).chebeval(dev(c)))
+    ref = oracle.ndct_rows(c, onodes(N))
+    err = np.max(np.abs(got - ref)) / np.abs(c).sum()
+    print(f"N={N} chebeval err/||c||1 = {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("decay", [0.0, 1.0])
+@pytest.mark.parametrize("N", SMALL)
+def test_dlt_full(gb, N, decay):
+    import oracle
+    c = _c(N, 3, decay)
+    got = host(gb.Plan(N).dlt(dev(c)))
+    ref = oracle.dlt_rows(c, onodes(N))
+    err = np.max(np.abs(got - ref)) / np.abs(c).sum()
+    print(f"N={N} decay={decay} dlt err/||c||1 = {err:.2e}")
+    assert err <= TOL64
+
+
+def _idlt_err(got, ref, w, f):
+    N = f.size
+    scale = (np.arange(N) + 0.5) * np.abs(w * f).sum()
+    return np.max(np.abs(got - ref) / scale)
+
+
+@pytest.mark.parametrize("N", SMALL)
+def test_idlt_full(gb, N):
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    f = inp.values(N, 4)
+    nd = onodes(N)
+    got = host(gb.Plan(N).idlt(dev(f)))
+    ref = oracle.idlt(f, nd)
+    err = _idlt_err(got, ref, nd.w, f)
+    print(f"N={N} idlt err = {err:.2e} (abs {np.max(np.abs(got - ref)):.2e})")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("N", [16, 256, 1024, 4096])
+def test_idlt_dlt_roundtrip(gb, N):
+    c = _c(N, 5)
+    p = gb.Plan(N)
+    back = host(p.idlt(p.dlt(dev(c))))
+    err = np.max(np.abs(back - c)) / np.abs(c).sum()
+    print(f"N={N} idlt(dlt(c)) - c: {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("N", [2, 8, 64, 512, 4096])
+def test_transposes_full(gb, N):
+    import oracle
+    nd = onodes(N)
+    g = _c(N, 6)
+    p = gb.Plan(N)
+    s = np.abs(g).sum()
+    e1 = np.max(np.abs(host(p.dlt_t(dev(g))) - oracle.dlt_t(g, nd))) / s
+    e2 = np.max(np.abs(host(p.chebeval_t(dev(g))) - oracle.ndct_t(g, nd))) / s
+    e3 = np.max(np.abs(host(p.leg2cheb_t(dev(g))) - oracle.leg2cheb_t(g))) / s
+    # idlt_t = D_w P D_s g
+    ref4 = nd.w * oracle.dlt_rows((np.arange(N) + 0.5) * g, nd)
+    e4 = np.max(np.abs(host(p.idlt_t(dev(g))) - ref4)) / np.abs((np.arange(N) + 0.5) * g).sum()
+    print(f"N={N} dlt_t {e1:.2e} chebeval_t {e2:.2e} leg2cheb_t {e3:.2e} idlt_t {e4:.2e}")
+    for e in (e1, e2, e3, e4):
+        assert e <= TOL64
+
+
+# --------------------------------------------------------------------------
+# large N: sampled rows / residuals
+# --------------------------------------------------------------------------
+LARGE = [(2**13, 512), (2**16, 1024), (2**20, 384), (2**22, 96)]
+
+
+@pytest.mark.parametrize("decay", [0.0, 1.0])
+@pytest.mark.parametrize("N,nrows", LARGE)
+def test_dlt_sampled(gb, N, nrows, decay):
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    p2 = int(math.log2(N))
+    c = inp.coeffs(N, (10 if decay else 20) + p2, decay)
+    rows = inp.sample_rows(N, nrows, seed=1000 + p2)
+    got = host(gb.Plan(N).dlt(dev(c)))
+    ref = oracle.dlt_rows(c, onodes(N, tuple(rows.tolist())))
+    err = np.max(np.abs(got[rows] - ref)) / np.abs(c).sum()
+    print(f"N={N} decay={decay} rows={rows.size} dlt err/||c||1 = {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("N,nrows", LARGE)
+def test_idlt_forward_residual(gb, N, nrows):
+    """IDLT above the full-oracle range: the exact inverse satisfies
+    sum_n c_n P_n(x_k) = f_k, checked at sampled rows (residual / ||c||_1)."""
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    p2 = int(math.log2(N))
+    f = inp.values(N, 30 + p2)
+    rows = inp.sample_rows(N, nrows, seed=2000 + p2)
+    c = host(gb.Plan(N).idlt(dev(f)))
+    resid = oracle.dlt_rows(c, onodes(N, tuple(rows.tolist()))) - f[rows]
+    err = np.max(np.abs(resid)) / np.abs(c).sum()
+    print(f"N={N} idlt forward residual / ||c||1 = {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("N", [2**13, 2**16, 2**20])
+def test_adjoint_identities(gb, N):
+    """<A y, z> = <y, A^T z> for every operator pair, at sizes beyond the oracle."""
+    import paper_1505_00354_gb300.inputs as inp
+    p = gb.Plan(N)
+    y, z = dev(inp.coeffs(N, 7)), dev(inp.coeffs(N, 8))
+    for fwd, tr in ((p.dlt, p.dlt_t), (p.chebeval, p.chebeval_t), (p.leg2cheb, p.leg2cheb_t),
+                    (p.idlt, p.idlt_t)):
+        a = float(torch.dot(fwd(y), z))
+        b = float(torch.dot(y, tr(z)))
+        scale = float(torch.linalg.vector_norm(y, 1) * torch.linalg.vector_norm(z, 1))
+        assert abs(a - b) <= 1e-13 * scale, (fwd.__name__, a, b)
+
+
+# --------------------------------------------------------------------------
+# FP32 form
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [64, 1024, 4096])
+def test_fp32_form_full(gb, N):
+    import oracle
+    c = _c(N, 9, 1.0)
+    p = gb.Plan(N, gb.FP32)
+    got = host(p.dlt(dev(c, torch.float32)))
+    c32 = c.astype(np.float32).astype(np.float64)
+    nd = onodes(N)
+    err = np.max(np.abs(got - oracle.dlt_rows(c32, nd))) / np.abs(c32).sum()
+    f = _c(N, 10)
+    f32 = f.astype(np.float32).astype(np.float64)
+    gi = host(p.idlt(dev(f, torch.float32)))
+    ei = _idlt_err(gi, oracle.idlt(f32, nd), nd.w, f32)
+    print(f"N={N} fp32 dlt {err:.2e} idlt {ei:.2e}")
+    assert err <= TOL32 and ei <= TOL32
+
+
+@pytest.mark.parametrize("N,nrows", [(2**16, 256), (2**20, 128), (2**22, 48)])
+def test_fp32_form_sampled(gb, N, nrows):
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    p2 = int(math.log2(N))
+    c = inp.coeffs(N, 40 + p2, 1.0).astype(np.float32).astype(np.float64)
+    rows = inp.sample_rows(N, nrows, seed=3000 + p2)
+    got = host(gb.Plan(N, gb.FP32).dlt(dev(c, torch.float32)))
+    ref = oracle.dlt_rows(c, onodes(N, tuple(rows.tolist())))
+    err = np.max(np.abs(got[rows] - ref)) / np.abs(c).sum()
+    print(f"N={N} fp32 dlt err/||c||1 = {err:.2e}")
+    assert err <= TOL32
+
+
+# --------------------------------------------------------------------------
+# batching, argument checks
+# --------------------------------------------------------------------------
+def test_batch_matches_single(gb):
+    N = 1024
+    p = gb.Plan(N)
+    C = dev(np.stack([_c(N, 100 + i) for i in range(3)]))
+    Fb = p.dlt(C)
+    for i in range(3):
+        assert torch.equal(Fb[i], p.dlt(C[i].clone()))
+    empty = torch.empty(0, N, dtype=torch.float64, device="cuda")
+    assert p.dlt(empty).shape == (0, N)
+
+
+def test_argument_errors(gb):
+    import ctypes
+    L = gb.lib()
+    h = ctypes.c_void_p()
+    for bad in (0, 3, 1000, 2**25):
+        assert L.gbdlt_plan_create(bad, 0, 0.0, None, ctypes.byref(h)) == -2
+    assert L.gbdlt_plan_create(64, 7, 0.0, None, ctypes.byref(h)) == -1
+    p = gb.Plan(64)
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    assert L.gbdlt_dlt(p.handle, None, ctypes.c_void_p(x.data_ptr()), 1) == -1
+    assert L.gbdlt_dlt(p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 1) == -1
+    assert L.gbdlt_dlt(p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), -1) == -1
+    assert L.gbdlt_plan_sync(p.handle) == 0

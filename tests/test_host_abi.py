@@ -1,0 +1,119 @@
+"""CPU-only checks of the C ABI library: it loads, exports every symbol the
+header declares, and its host-side parameter derivation follows the paper's
+bounds (Corollary 2.4 / Table 1 for L).  No compute call touches a GPU."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gb():
+    from paper_1505_00354_gb300 import build
+    build.build()
+    import paper_1505_00354_gb300 as g
+    return g
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gbdlt.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|uint64_t)\s+(gbdlt_\w+)\s*\(", src, re.M)))
+
+
+def test_exports_every_header_symbol(gb):
+    names = header_functions()
+    assert len(names) >= 17
+    lib = gb.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(gb._binding.ENTRY_POINTS)
+
+
+def test_status_strings(gb):
+    lib = gb.lib()
+    for code in range(-6, 1):
+        s = lib.gbdlt_status_string(code)
+        assert s and s != b"unknown status"
+    assert lib.gbdlt_status_string(-99) == b"unknown status"
+
+
+def test_launch_count_is_host_only(gb):
+    assert gb.launch_count() >= 0
+
+
+def test_bad_arguments(gb):
+    lib = gb.lib()
+    p = gb._binding.Params()
+    for bad in (0, 3, 6, 1000, 2**25):
+        assert lib.gbdlt_plan_params(bad, 0, 0.0, ctypes.byref(p)) == -2
+    assert lib.gbdlt_plan_params(64, 2, 0.0, ctypes.byref(p)) == -1
+    assert lib.gbdlt_plan_params(64, 0, 2.0, ctypes.byref(p)) == -1
+    assert lib.gbdlt_plan_params(64, 0, 0.0, None) == -1
+    assert lib.gbdlt_plan_destroy(None) == -1
+    assert lib.gbdlt_plan_sync(None) == -1
+    assert lib.gbdlt_dlt(None, None, None, 1) == -1
+
+
+def _taylor_L(eps):
+    # Corollary 2.4 (theta* = theta^cheb1): smallest L with 0.83845^L / L! <= eps/2
+    L = 1
+    while 0.83845**L / math.factorial(L) > eps / 2:
+        L += 1
+    return L
+
+
+@pytest.mark.parametrize("eps,L_expected", [(1e-14, 16), (2e-6, 9), (4e-16, 17), (1e-7, 10)])
+def test_taylor_terms_follow_table1(gb, eps, L_expected):
+    """The Taylor term count is the smallest L whose Table 1 entry is below eps/2;
+    Table 1 (Sec. 2.2) prints 1.4e-16 at L = 17 (double precision) and 4.7e-8
+    at L = 10."""
+    assert _taylor_L(eps) == L_expected
+    assert gb.plan_params(1024, 0, eps)["L"] == L_expected
+
+
+@pytest.mark.parametrize("N", [4, 64, 1024, 2**16, 2**20, 2**22])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_band_layout_is_consistent(gb, N, prec):
+    p = gb.plan_params(N, prec)
+    bands = p["bands"]
+    assert p["K"] == len(bands) <= 32
+    H = N // 2
+    prev_kb = None
+    prev_ns = N + 1
+    for ns, ka, kb in bands:
+        assert 0 <= ka < kb <= H
+        assert 2 <= ns <= N
+        assert ns < prev_ns  # cuts shrink toward the middle rows
+        if prev_kb is not None:
+            assert ka == prev_kb  # contiguous
+        prev_kb, prev_ns = kb, ns
+    if bands:
+        assert bands[-1][2] == H
+        assert 1 <= p["M"] <= 24
+    # recurrence work matches the layout
+    k0 = bands[0][1] if bands else H
+    steps = k0 * N + sum((kb - ka) * ns for ns, ka, kb in bands)
+    assert p["rec_steps"] == 2 * steps
+    # algorithmic bytes: c, dtheta in; f out (+ w for the IDLT)
+    ds = 8 if prec == 0 else 4
+    assert p["bytes_dlt"] == (2 * ds + 8) * N
+    assert p["bytes_idlt"] == (2 * ds + 16) * N
+
+
+def test_bands_respect_asymptotic_bound(gb):
+    """Every band row satisfies the expansion's error bound at the band's cut:
+    2 C_n h_{M,n} / (2 sin theta)^{M+1/2} <= eps/20 with n = ns at the band's
+    first (worst) row."""
+    for N in (1024, 2**16, 2**20):
+        p = gb.plan_params(N, 0)
+        M, eps = p["M"], p["eps"]
+        for ns, ka, kb in p["bands"]:
+            s = math.sin((ka + 0.5) * math.pi / N)
+            lc = 0.5 * math.log(4 / math.pi) + math.lgamma(ns + 1) - math.lgamma(ns + 1.5)
+            lh = sum(2 * math.log(j - 0.5) - math.log(j) - math.log(ns + j + 0.5) for j in range(1, M + 1))
+            bound = 2 * math.exp(lc + lh) / (2 * s) ** (M + 0.5)
+            assert bound <= eps / 20 * (1 + 1e-9), (N, ns, ka, bound)
