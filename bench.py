@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark: DLT + IDLT transforms/s at N = 2^20 on GB300 (one JSON line).
+
+A step is one pass of the whole hot path over one input vector: the
+Gauss-Legendre nodes/weights (legpts), the DLT of c (Eq. 1) and the IDLT of the
+result (Eq. 2).  Two transforms per step.  Inputs are seeded synthetic
+coefficient vectors c_n ~ N(0,1) (the paper's experiments use normally
+distributed coefficients; no dataset is involved).
+
+GPU arm (default): W warm-up steps, then K timed steps; each step is bracketed by
+CUDA events on the plan's stream and preceded (outside the events) by a 256 MiB
+write that flushes the 129 MB L2.  The per-kernel timing behind the roofline
+object is taken in the same timed steps.  Also reported: the FP32 form on the
+same workload, the error of both forms against the oracle on sampled rows, an
+end-to-end number through the public API with host buffers, and the oracle timed
+on the host cores on a bounded sample (cpu_baseline).
+
+Reference arm (--impl reference): there is no reference implementation to run;
+the baseline is the CPU oracle itself (double-double direct sums), timed on a
+bounded sample of the same workload per step and extrapolated to the full
+transform.
+
+Multi-GPU: the path does not shard; N > 1 runs independent replicas (one per
+rank) and reports the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DLT+IDLT N=2^20 transforms/s, FP64 vs FP32 form, % HBM roofline, max err"
+N_DEFAULT = 1 << 20
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 / FP32 pipe peaks derived from the unit counts (152 SMs; 2 FP64 FMA and
+# 128 FP32 FMA per SM per clock; 2070 MHz maximum SM clock).  A probe on this
+# pool's GB300 measured 1.197 FP64 and 69.9 FP32 TFLOP/s at 1987 MHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+# DRAM traffic per launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) and the hash of the kernel sources it was taken with;
+# a traffic figure is reported only while the sources are unchanged.
+TRAFFIC = {
+    # profiles/k_fft_cols_fp64_N2p20.md: one launch of 36 vectors of 2^20 complex
+    # doubles moved 604.1 MB + 548.4 MB against 1208 MB algorithmic
+    "fft_cols": {"dram_per_algorithmic_byte": (604.142336 + 548.403968) / 1207.959552,
+                 "src": "b6cda88a97851d8c"},
+}
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1505_00354_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbdlt", choices=["gbdlt", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the sampled-row error check")
+    ap.add_argument("--quick", action="store_true", help="small sample sizes (for profiling runs)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (replicas)
+# --------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def peaks():
+    try:
+        d = json.load(open(MEASURED_PEAKS))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+    import paper_1505_00354_gb300 as g
+    from paper_1505_00354_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    N = args.n
+    stream = torch.cuda.current_stream()
+    c_np = inputs.coeffs(N, 20 + int(math.log2(N)) + 1000 * rank)
+    c = torch.tensor(c_np, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def make(prec):
+        t0 = time.perf_counter()
+        p = g.Plan(N, prec, stream=stream)
+        torch.cuda.synchronize()
+        return p, time.perf_counter() - t0
+
+    def timed_loop(plan, x, K, W, profile):
+        lib = g.lib()
+        f = torch.empty_like(x)
+        cb = torch.empty_like(x)
+
+        def step():
+            st = lib.gbdlt_legpts(plan.handle, None, None, None, None)
+            if st:
+                raise g.GbdltError(st, "legpts")
+            plan.dlt(x, out=f)
+            plan.idlt(f, out=cb)
+
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        if profile:
+            plan.profile(2)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier(world)
+        torch.cuda.synchronize()
+        n0 = g.launch_count()
+        for i in range(K):
+            flush.fill_(float(i))
+            if profile:
+                plan.profile(1)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = g.launch_count() - n0
+        if profile:
+            plan.profile(0)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, launches, f, cb
+
+    # ---------------- FP64 form (headline)
+    plan64, cold64 = make(g.FP64)
+    clk = ClockSampler(getattr(torch.cuda.get_device_properties(local), "uuid", None))
+    clk.uuid = str(clk.uuid) if clk.uuid is not None else None
+    clk.start()
+    ms64, launches, f64, cb64 = timed_loop(plan64, c, args.steps, args.warmup, True)
+    clocks = clk.stop()
+    prof = plan64.profile_report()
+    t_step = sum(ms64) / len(ms64)
+    t_max = max_over_ranks(world, sum(ms64))
+    value = 2.0 * args.steps * world / (t_max / 1e3)
+
+    # ---------------- FP32 form
+    plan32, cold32 = make(g.FP32)
+    c32 = c.float()
+    ms32, _, f32, cb32 = timed_loop(plan32, c32, args.steps, args.warmup, False)
+    t32 = sum(ms32) / len(ms32)
+
+    # ---------------- end to end through the public API with host buffers
+    c_host = torch.tensor(c_np, dtype=torch.float64).pin_memory()
+    f_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    cb_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    xd = torch.empty(N, dtype=torch.float64, device="cuda")
+    fd = torch.empty_like(xd)
+    cbd = torch.empty_like(xd)
+
+    def e2e_step():
+        xd.copy_(c_host, non_blocking=True)
+        g.lib().gbdlt_legpts(plan64.handle, None, None, None, None)
+        plan64.dlt(xd, out=fd)
+        plan64.idlt(fd, out=cbd)
+        f_host.copy_(fd, non_blocking=True)
+        cb_host.copy_(cbd, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        ee.append((a, b))
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in ee))
+    e2e_value = 2.0 * args.steps * world / (t_e2e / 1e3)
+
+    out = None
+    if rank == 0:
+        hbm, hbm_src = peaks()
+        params = plan64.params()
+        # dominant kernel of the FP64 step by device time
+        dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+        name, d = dom
+        per_launch_ms = d["ms"] / d["launches"]
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        tr = TRAFFIC.get(name)
+        traffic = None
+        if tr and tr.get("src") == src_hash():
+            # the capture's DRAM/algorithmic ratio applied to this kernel's
+            # average algorithmic bytes per launch in the timed region
+            traffic = round(tr["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"], 1)
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "kernel": name, "launches_per_step": d["launches"] / args.steps,
+                    "ms_per_launch": round(per_launch_ms, 4),
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz"}
+        total_prof = sum(v["ms"] for v in prof.values())
+        breakdown = {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
+                         "share": round(v["ms"] / total_prof, 4),
+                         "launches_per_step": v["launches"] / args.steps,
+                         "tflops": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
+                         "gbs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+        step_bytes = params["bytes_dlt"] + params["bytes_idlt"]
+        hbm_frac = step_bytes / (t_step / 1e3) / 1e9 / hbm
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "transforms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded c_n ~ N(0,1), numpy PCG64)",
+            "config": {"workload": f"FP64 legpts + DLT + IDLT of one vector, N=2^{int(math.log2(N))}",
+                       "N": N, "batch": 1, "transforms_per_step": 2,
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "plan": {"L": params["L"], "M": params["M"], "K": params["K"],
+                                "bands": params["bands"], "rec_steps": params["rec_steps"]}},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": round(e2e_value, 3), "unit": "transforms/s", "h2d_bytes_per_step": 8 * N,
+                    "d2h_bytes_per_step": 16 * N, "ms_per_step": round(t_e2e / args.steps / world, 4)},
+            "roofline": roofline,
+            "hbm_algorithmic": {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (t_step / 1e3) / 1e9, 2),
+                                "peak_gbs": hbm, "peak_source": hbm_src, "frac": round(hbm_frac, 6)},
+            "fp32_form": {"value": round(2.0 * world / (t32 / 1e3), 3), "unit": "transforms/s",
+                          "ms_per_step": round(t32, 4), "speedup_vs_fp64": round(t_step / t32, 3),
+                          "dtype": "f32 transforms, f64 nodes and recurrence"},
+            "cold_plan_ms": {"fp64": round(cold64 * 1e3, 2), "fp32": round(cold32 * 1e3, 2)},
+            "breakdown": breakdown,
+        }
+        if not args.no_check:
+            out["max_err"] = error_check(N, c_np, f64, cb64, f32, cb32, quick=args.quick)
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(N, c_np, target_s=5.0 if args.quick else 15.0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def error_check(N, c, f64, cb64, f32, cb32, quick=False):
+    """max |error| / ||c||_1 of both forms at sampled rows against the oracle,
+    and the IDLT(DLT(c)) round trip."""
+    import oracle
+    from paper_1505_00354_gb300 import inputs
+    rows = inputs.sample_rows(N, 16 if quick else 48, seed=1000 + int(math.log2(N)), include_ends=4)
+    nd = oracle.legpts(N, rows)
+    ref = oracle.dlt_rows(c, nd)
+    c1 = np.abs(c).sum()
+    c32 = c.astype(np.float32).astype(np.float64)
+    ref32 = oracle.dlt_rows(c32, nd)
+    return {
+        "dlt_fp64": float(np.max(np.abs(f64.cpu().numpy()[rows] - ref)) / c1),
+        "dlt_fp32": float(np.max(np.abs(f32.double().cpu().numpy()[rows] - ref32)) / np.abs(c32).sum()),
+        "roundtrip_fp64": float(np.max(np.abs(cb64.cpu().numpy() - c)) / c1),
+        "roundtrip_fp32": float(np.max(np.abs(cb32.double().cpu().numpy() - c)) / c1),
+        "rows": int(rows.size), "norm": "max|err| / ||c||_1",
+    }
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample(N, c, rows):
+    """The oracle's work for the listed rows of one DLT + IDLT: the nodes
+    (Newton on the recurrence), the DLT row sums and the rows' IDLT
+    contributions; returns seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    nd = oracle.legpts(N, rows)
+    f = oracle.dlt_rows(c, nd)
+    oracle.idlt_rows(f, nd, N)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(N, c, target_s=15.0):
+    import oracle
+    from paper_1505_00354_gb300 import inputs
+    cores = oracle.num_threads()
+    probe = inputs.sample_rows(N, cores, seed=7, include_ends=0)
+    t = oracle_sample(N, c, probe)
+    nrows = int(min(N, max(cores, cores * round(target_s / max(t, 1e-3)))))
+    rows = inputs.sample_rows(N, nrows, seed=8, include_ends=0)
+    t = oracle_sample(N, c, rows)
+    t_full = t * N / rows.size
+    return {"value": round(2.0 / t_full, 8), "unit": "transforms/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows.size} of {N} rows of one DLT+IDLT (double-double nodes, row sums, row "
+                      f"contributions to the IDLT) in {t:.1f} s, extrapolated x{N / rows.size:.0f}"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1505_00354_gb300 import inputs
+    N = args.n
+    c = inputs.coeffs(N, 20 + int(math.log2(N)))
+    cores = oracle.num_threads()
+    nrows = max(cores, 2 * cores)
+    ts = []
+    for i in range(args.warmup + args.steps):
+        rows = inputs.sample_rows(N, nrows, seed=100 + i, include_ends=0)
+        t = oracle_sample(N, c, rows)
+        if i >= args.warmup:
+            ts.append(t * N / rows.size)
+    t_full = sum(ts) / len(ts)
+    value = 2.0 / t_full
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "transforms/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "dd (f64 pairs)",
+            "data": "synthetic (seeded c_n ~ N(0,1), numpy PCG64)",
+            "config": {"workload": f"CPU oracle legpts + DLT + IDLT of one vector, N=2^{int(math.log2(N))}",
+                       "N": N, "transforms_per_step": 2},
+            "cpu_baseline": {"value": round(value, 8), "unit": "transforms/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{nrows} of {N} rows per step, extrapolated x{N / nrows:.0f}"},
+            "e2e": {"value": round(value, 8), "unit": "transforms/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_gpu(args, world, rank, local)
+    if out is not None and rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

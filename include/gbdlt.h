@@ -122,6 +122,19 @@ int gbdlt_idlt(gbdlt_plan plan, const void* f, void* c, int64_t batch);
 /* Transposed IDLT: out = D_w P_N(x^leg) D_s g, i.e. out_k = w_k sum_n (n+1/2) g_n P_n(x_k). */
 int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
 
+/* Per-kernel device timing on the plan's stream, for profiling (off by
+ * default).  mode 1: turn on and start timing from this point (work enqueued
+ * earlier is not attributed); call again before each region to re-anchor.
+ * mode 0: turn off.  mode 2: clear the accumulated totals.  While on, the
+ * library records one CUDA event after every kernel it launches. */
+int gbdlt_plan_profile(gbdlt_plan plan, int mode);
+/* Report of the accumulated timing: one line per kernel,
+ * "name launches total_ms flops bytes", where flops and bytes are the
+ * algorithmic counts of those launches.  Waits for the recorded events.
+ * Writes at most len-1 characters and a NUL into buf (buf may be NULL when
+ * len == 0); returns the length of the full report, or a negative status. */
+int64_t gbdlt_plan_profile_read(gbdlt_plan plan, char* buf, int64_t len);
+
 /* Human-readable name of a status code (static string). */
 const char* gbdlt_status_string(int status);
 /* Number of kernels this library has launched since it was loaded (all plans,

@@ -63,6 +63,7 @@ def _load():
         lib.orc_dlt_rows.argtypes = [i64, _D, i64, _D, _D, _D]
         lib.orc_dlt_t.argtypes = [i64, _D, _D, _D, _D]
         lib.orc_idlt.argtypes = [i64, _D, _D, _D, _D, _D, _D]
+        lib.orc_idlt_rows.argtypes = [i64, _D, i64, _D, _D, _D, _D, _D]
         lib.orc_ndct_rows.argtypes = [i64, _D, i64, _D, _D, _D]
         lib.orc_ndct_t.argtypes = [i64, _D, _D, _D, _D]
         lib.orc_leg2cheb.argtypes = [i64, _D, _D]
@@ -191,6 +192,17 @@ def idlt(f, nodes: Nodes | None = None) -> np.ndarray:
     out = np.empty(N)
     _load().orc_idlt(N, _dp(f), _dp(_f64(nodes["x_hi"])), _dp(_f64(nodes["x_lo"])),
                      _dp(_f64(nodes["w_hi"])), _dp(_f64(nodes["w_lo"])), _dp(out))
+    return out
+
+
+def idlt_rows(f_rows, nodes: Nodes, N: int) -> np.ndarray:
+    """Contribution of the rows held in ``nodes`` to Eq. 2 (length-N vector);
+    summed over all rows it is the IDLT."""
+    f_rows = _f64(f_rows)
+    out = np.empty(N)
+    _load().orc_idlt_rows(N, _dp(f_rows), f_rows.size, _dp(_f64(nodes["x_hi"])),
+                          _dp(_f64(nodes["x_lo"])), _dp(_f64(nodes["w_hi"])),
+                          _dp(_f64(nodes["w_lo"])), _dp(out))
     return out
 
 

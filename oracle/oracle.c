@@ -402,6 +402,47 @@ void orc_dlt_t(int64_t N, const double* g, const double* x_hi, const double* x_l
   dlt_t_impl(N, g, x_hi, x_lo, NULL, NULL, 0, out);
 }
 
+/* Contribution of a subset of rows to Eq. 2: out_n = (n+1/2) sum_{i<nk} w_i f_i
+ * P_n(x_i) for the listed nodes (x_i, w_i in dd).  Summing it over a partition
+ * of all N rows gives the IDLT; used to time the oracle on a sample of rows. */
+void orc_idlt_rows(int64_t N, const double* f, int64_t nk, const double* x_hi,
+                   const double* x_lo, const double* w_hi, const double* w_lo, double* out) {
+  int nthr = 1;
+#ifdef _OPENMP
+  nthr = omp_get_max_threads();
+#endif
+  dd* acc = (dd*)calloc((size_t)nthr * (size_t)N, sizeof(dd));
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    dd* my = acc + (size_t)tid * (size_t)N;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nk; ++i) {
+      dd x = dd_make(x_hi[i], x_lo[i]);
+      dd gk = dd_mul(dd_from(f[i]), dd_make(w_hi[i], w_lo[i]));
+      dd pm1 = dd_from(0.0), p = dd_from(1.0);
+      for (int64_t m = 0; m < N; ++m) {
+        my[m] = dd_add(my[m], dd_mul(p, gk));
+        dd a = dd_mul_d(dd_mul(x, p), (double)(2 * m + 1));
+        dd b = dd_mul_d(pm1, (double)m);
+        dd next = dd_div_d(dd_sub(a, b), (double)(m + 1));
+        pm1 = p;
+        p = next;
+      }
+    }
+  }
+  for (int64_t m = 0; m < N; ++m) {
+    dd s = dd_from(0.0);
+    for (int t = 0; t < nthr; ++t) s = dd_add(s, acc[(size_t)t * (size_t)N + m]);
+    s = dd_mul_d(s, (double)m + 0.5);
+    out[m] = s.hi + s.lo;
+  }
+  free(acc);
+}
+
 /* Eq. 2: c_n = (n+1/2) sum_k w_k f_k P_n(x_k). */
 void orc_idlt(int64_t N, const double* f, const double* x_hi, const double* x_lo,
               const double* w_hi, const double* w_lo, double* c) {

@@ -72,7 +72,8 @@ ENTRY_POINTS = (
     "gbdlt_plan_params", "gbdlt_plan_create", "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
     "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
-    "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_status_string", "gbdlt_launch_count",
+    "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
+    "gbdlt_status_string", "gbdlt_launch_count",
 )
 
 
@@ -98,12 +99,15 @@ def lib():
         for name in ("gbdlt_leg2cheb", "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t",
                      "gbdlt_dlt", "gbdlt_dlt_t", "gbdlt_idlt", "gbdlt_idlt_t"):
             getattr(L, name).argtypes = [vp, vp, vp, i64]
+        L.gbdlt_plan_profile.argtypes = [vp, i32]
+        L.gbdlt_plan_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.gbdlt_status_string.argtypes = [i32]
         L.gbdlt_status_string.restype = ctypes.c_char_p
         L.gbdlt_launch_count.restype = ctypes.c_uint64
         for name in ENTRY_POINTS:
             if name not in ("gbdlt_status_string", "gbdlt_launch_count"):
                 getattr(L, name).restype = i32
+        L.gbdlt_plan_profile_read.restype = i64
         _lib = L
         return L
 
@@ -177,6 +181,23 @@ class Plan:
     def set_stream(self, stream):
         self.stream = stream
         _check(lib().gbdlt_plan_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), "set_stream")
+
+    def profile(self, mode: int = 1):
+        """1: start/re-anchor per-kernel timing, 0: stop, 2: clear totals."""
+        _check(lib().gbdlt_plan_profile(self._h, mode), "plan_profile")
+
+    def profile_report(self) -> dict:
+        """{kernel: {launches, ms, flops, bytes}} accumulated while profiling was on."""
+        n = lib().gbdlt_plan_profile_read(self._h, None, 0)
+        if n < 0:
+            raise GbdltError(int(n), "plan_profile_read")
+        buf = ctypes.create_string_buffer(int(n) + 1)
+        lib().gbdlt_plan_profile_read(self._h, buf, n + 1)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms, fl, by = line.split()
+            out[name] = {"launches": int(cnt), "ms": float(ms), "flops": float(fl), "bytes": float(by)}
+        return out
 
     def legpts(self):
         """Recompute the nodes on the GPU; returns (x, theta, w, dtheta) float64 tensors."""

@@ -222,7 +222,9 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
     int64_t grid = (nvec + lines - 1) / lines;
     size_t sm = (size_t)lines * L * sizeof(CT);
     k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, nvec, P.tw4096);
-    count_launch();
+    int lg = 0;
+    while ((1 << lg) < L) ++lg;
+    launched(P, "fft_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
     return a;
   }
   int p = 0;
@@ -234,11 +236,11 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   dim3 g1(L2 / C, (unsigned)nvec);
   k_fft_cols<T, DIR><<<g1, FFT_THREADS, (size_t)C * (L1 + 1) * sizeof(CT), P.stream>>>(
       (CT*)a, N, L1, L2, C, P.tw4096, P.twN.hi, P.twN.lo);
-  count_launch();
+  launched(P, "fft_cols", (5.0 * (p / 2) + 6.0) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
   dim3 g2(L1 / C2n, (unsigned)nvec);
   k_fft_rows<T, DIR><<<g2, FFT_THREADS, (size_t)C2n * (L2 + 1) * sizeof(CT), P.stream>>>(
       (const CT*)a, (CT*)b, N, L1, L2, C2n, P.tw4096);
-  count_launch();
+  launched(P, "fft_rows", 5.0 * (p - p / 2) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
   return b;
 }
 

@@ -191,6 +191,7 @@ struct Plan {
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel
+  struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
 };
 
 // ---------------------------------------------------------------------------
@@ -198,6 +199,9 @@ struct Plan {
 // ---------------------------------------------------------------------------
 void count_launch(int n = 1);
 int check_launch();  // GBDLT_OK or GBDLT_ERR_CUDA after a launch
+// Counts one launch and, when the plan's profiler is on, records an event after
+// it tagged with the kernel name and its algorithmic flops and bytes.
+void launched(Plan& P, const char* name, double flops, double bytes);
 
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)

@@ -188,7 +188,7 @@ __global__ void k_dtheta(const double* __restrict__ tN, double* __restrict__ out
 int launch_dtheta(Plan& P, double* out) {
   const int64_t N = P.p.N;
   k_dtheta<<<(unsigned)((N + 255) / 256), 256, 0, P.stream>>>(P.tN, out, N);
-  count_launch();
+  launched(P, "dtheta", (double)N, 16.0 * N);
   return check_launch();
 }
 
@@ -198,7 +198,7 @@ int launch_legpts(Plan& P, double CN) {
   const int threads = 128;
   const int64_t blocks = (half + threads - 1) / threads;
   k_legpts<<<(unsigned)blocks, threads, 0, P.stream>>>(N, CN, P.theta, P.x, P.w, P.tN, P.status);
-  count_launch();
+  launched(P, "legpts", 0.0, 32.0 * N);
   return check_launch();
 }
 

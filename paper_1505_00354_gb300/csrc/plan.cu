@@ -13,8 +13,11 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
 
 #include "gbdlt_internal.cuh"
 
@@ -25,6 +28,54 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 int check_launch() {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GBDLT_OK : GBDLT_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel profiler: one event after every launch; the interval between two
+// consecutive events is the device time of the kernel launched between them
+// (kernels on one stream run back to back)
+// ---------------------------------------------------------------------------
+struct ProfMark {
+  const char* name;
+  double flops, bytes;
+};
+struct ProfAcc {
+  int64_t count = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+struct Profiler {
+  bool on = false;
+  bool anchored = false;
+  std::vector<cudaEvent_t> ev;  // ev[0] anchor; ev[i+1] recorded after marks[i]
+  std::vector<ProfMark> marks;
+  std::map<std::string, ProfAcc> acc;
+};
+
+static void prof_flush(Plan& P) {
+  Profiler& R = *P.prof;
+  const size_t n = R.marks.size();
+  if (n == 0) return;
+  cudaEventSynchronize(R.ev[n]);
+  for (size_t i = 0; i < n; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, R.ev[i], R.ev[i + 1]);
+    ProfAcc& a = R.acc[R.marks[i].name];
+    a.count += 1;
+    a.ms += ms;
+    a.flops += R.marks[i].flops;
+    a.bytes += R.marks[i].bytes;
+  }
+  std::swap(R.ev[0], R.ev[n]);
+  R.marks.clear();
+}
+
+void launched(Plan& P, const char* name, double flops, double bytes) {
+  count_launch();
+  if (!P.prof || !P.prof->on || !P.prof->anchored) return;
+  Profiler& R = *P.prof;
+  if (R.marks.size() + 1 >= R.ev.size()) prof_flush(P);
+  cudaEventRecord(R.ev[R.marks.size() + 1], P.stream);
+  R.marks.push_back(ProfMark{name, flops, bytes});
 }
 
 // ---------------------------------------------------------------------------
@@ -278,6 +329,10 @@ struct Arena {
 void free_plan(Plan* P) {
   if (!P) return;
   if (P->arena) cudaFree(P->arena);
+  if (P->prof) {
+    for (cudaEvent_t e : P->prof->ev) cudaEventDestroy(e);
+    delete P->prof;
+  }
   delete P;
 }
 
@@ -677,9 +732,54 @@ int gbdlt_plan_destroy(gbdlt_plan plan) {
   if (!plan) return GBDLT_ERR_INVALID_ARG;
   Plan* P = reinterpret_cast<Plan*>(plan);
   cudaStreamSynchronize(P->stream);
-  if (P->arena) cudaFree(P->arena);
-  delete P;
+  free_plan(P);
   return GBDLT_OK;
+}
+
+int gbdlt_plan_profile(gbdlt_plan plan, int mode) {
+  if (!plan || mode < 0 || mode > 2) return GBDLT_ERR_INVALID_ARG;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (!P.prof) {
+    P.prof = new (std::nothrow) Profiler();
+    if (!P.prof) return GBDLT_ERR_OOM;
+    P.prof->ev.resize(1024);
+    for (cudaEvent_t& e : P.prof->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return GBDLT_ERR_CUDA;
+  }
+  Profiler& R = *P.prof;
+  prof_flush(P);
+  if (mode == 2) {
+    R.acc.clear();
+    return GBDLT_OK;
+  }
+  R.on = mode == 1;
+  R.anchored = false;
+  if (R.on) {
+    if (cudaEventRecord(R.ev[0], P.stream) != cudaSuccess) return GBDLT_ERR_CUDA;
+    R.anchored = true;
+  }
+  return GBDLT_OK;
+}
+
+int64_t gbdlt_plan_profile_read(gbdlt_plan plan, char* buf, int64_t len) {
+  if (!plan || len < 0 || (len > 0 && !buf)) return GBDLT_ERR_INVALID_ARG;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  std::string s;
+  if (P.prof) {
+    prof_flush(P);
+    char line[256];
+    for (const auto& kv : P.prof->acc) {
+      std::snprintf(line, sizeof(line), "%s %lld %.6f %.6e %.6e\n", kv.first.c_str(),
+                    (long long)kv.second.count, kv.second.ms, kv.second.flops, kv.second.bytes);
+      s += line;
+    }
+  }
+  if (len > 0) {
+    const size_t n = std::min<size_t>(s.size(), (size_t)len - 1);
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return (int64_t)s.size();
 }
 
 int gbdlt_plan_set_stream(gbdlt_plan plan, void* cuda_stream) {

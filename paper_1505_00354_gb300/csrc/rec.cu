@@ -290,18 +290,20 @@ int launch_rec_forward(Plan& P, const T* c, T* vrec) {
   RecArgs R = rec_args(P);
   if (L.H == 0) return GBDLT_OK;
   k_rec_fwd<T><<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, c, L.part);
-  count_launch();
+  launched(P, "rec_fwd", 7.0 * (double)(P.p.rec_steps / 2),
+           (double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total);
   if (L.n_long > 0) {
     const int64_t threads = L.n_long * 32;
     k_rec_fwd_reduce<T><<<(unsigned)((threads + 255) / 256), 256, 0, P.stream>>>(R, L.part, vrec, 0,
                                                                                  L.n_long, 1);
-    count_launch();
+    launched(P, "rec_fwd_reduce", 0.0, 0.0);
   }
   if (L.H > L.n_long) {
     const int64_t rows = L.H - L.n_long;
     k_rec_fwd_reduce<T><<<(unsigned)((rows + 255) / 256), 256, 0, P.stream>>>(R, L.part, vrec,
                                                                               L.n_long, L.H, 0);
-    count_launch();
+    launched(P, "rec_fwd_reduce", 2.0 * (double)L.nseg_total,
+             16.0 * (double)L.nseg_total + (double)sizeof(T) * P.p.N);
   }
   return check_launch();
 }
@@ -318,9 +320,10 @@ int launch_rec_transpose(Plan& P, const T* z, T* out) {
     attr_set = true;
   }
   k_rec_t<T><<<(unsigned)L.ncta, RT, smem, P.stream>>>(R, z, L.tbuf);
-  count_launch();
+  launched(P, "rec_t", 7.0 * (double)(P.p.rec_steps / 2),
+           (double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total);
   k_rec_t_reduce<T><<<(unsigned)((P.p.N + 31) / 32), 256, 0, P.stream>>>(R, L.tbuf, out);
-  count_launch();
+  launched(P, "rec_t_reduce", (double)L.tbuf_total, 8.0 * (double)L.tbuf_total + (double)sizeof(T) * P.p.N);
   return check_launch();
 }
 

@@ -413,59 +413,104 @@ template <typename T>
 int launch_l2c_pro(Plan& P, const T* c, C2<T>* U) {
   TwArgs tw{P.tw4N.hi, P.tw4N.lo};
   k_l2c_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn, tw);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "l2c_pro", 10.0 * P.p.M * N, ts * N + 8.0 * N + KM * N * cs);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v) {
   k_l2c_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P));
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "l2c_epi", 10.0 * P.p.M * N, P.p.M * N * cs + 2.0 * ts * N);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_a4_pro(Plan& P, const T* v, C2<T>* U) {
   k_a4_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(v, U, P.p.N);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "a4_pro", 0.0, ts * N + N * cs);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_a4_epi(Plan& P, const C2<T>* F, T* chat) {
   TwArgs tw{P.tw4N.hi, P.tw4N.lo};
   k_a4_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, chat, P.p.N, tw);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "a4_epi", 12.0 * N, 2.0 * N * cs + ts * N);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d) {
   TwArgs tw{P.tw4N.hi, P.tw4N.lo};
   k_fcs_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, tw);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "fcs_pro", 8.0 * N, ts * N + N * cs);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out) {
   k_fcs_re_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, out, P.p.N);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "fcs_re_epi", 0.0, N * cs + ts * N);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair) {
   TwArgs tw{P.tw4N.hi, P.tw4N.lo};
   k_tay_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(chat, U, P.p.N, P.p.L, inc0, npair, tw);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "tay_pro", 16.0 * npair * N, 2.0 * ts * N + npair * N * cs);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair) {
   k_tay_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, v, f, P.tN, P.p.N, P.p.L, inc0, npair);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "tay_epi", (2.0 * P.p.L + 6.0 * npair) * N, npair * N * cs + 2.0 * ts * N + 8.0 * N);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair) {
   const double* w = use_w ? P.w : nullptr;
   k_tayt_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(f, w, P.tN, U, P.p.N, P.p.L, inc0, npair);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "tayt_pro", 8.0 * npair * N, ts * N + 16.0 * N + npair * N * cs);
+  }
   return check_launch();
 }
 template <typename T>
@@ -473,14 +518,24 @@ int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int n
   TwArgs tw{P.tw4N.hi, P.tw4N.lo};
   const int mode = Q ? 0 : 1;
   k_tayt_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, mode, tw);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "tayt_epi", (2.0 * P.p.L + 16.0 * npair) * N, 2.0 * npair * N * cs + N * cs);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U) {
   const double* w = use_w ? P.w : nullptr;
   k_l2ct_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P));
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "l2ct_pro", 10.0 * P.p.M * N, N * cs + 2.0 * ts * N + 8.0 * N + KM * N * cs);
+  }
   return check_launch();
 }
 template <typename T>
@@ -488,13 +543,23 @@ int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s)
   TwArgs tw{P.tw4N.hi, P.tw4N.lo};
   k_l2ct_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
                                                      scale_s, tw);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "l2ct_epi", 14.0 * KM * N, 2.0 * KM * N * cs + 2.0 * ts * N);
+  }
   return check_launch();
 }
 template <typename T>
 int launch_scale(Plan& P, const T* in, T* out, int which) {
   k_scale<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(in, out, P.w, P.p.N, which);
-  count_launch();
+  {
+    const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
+    const double KM = (double)P.p.K * P.p.M;
+    (void)KM;
+    launched(P, "scale", N, 2.0 * ts * N + 8.0 * N);
+  }
   return check_launch();
 }
 

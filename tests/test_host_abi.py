@@ -21,7 +21,7 @@ def gb():
 
 def header_functions():
     src = open(os.path.join(ROOT, "include", "gbdlt.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*|uint64_t)\s+(gbdlt_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*|uint64_t)\s+(gbdlt_\w+)\s*\(", src, re.M)))
 
 
 def test_exports_every_header_symbol(gb):

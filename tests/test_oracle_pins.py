@@ -245,6 +245,19 @@ def test_idlt_inverts_dlt(orc, N):
     np.testing.assert_allclose(orc.idlt(f, nd), c, atol=2e-14)
 
 
+def test_idlt_rows_partition(orc):
+    """The row contributions of a partition of the nodes add up to the IDLT."""
+    N = 96
+    nd = orc.legpts(N)
+    f = rng.standard_normal(N)
+    parts = [np.arange(0, 30), np.arange(30, 31), np.arange(31, N)]
+    tot = np.zeros(N)
+    for r in parts:
+        sub = {k: nd[k][r] for k in ("x_hi", "x_lo", "w_hi", "w_lo")}
+        tot += orc.idlt_rows(f[r], sub, N)
+    np.testing.assert_allclose(tot, orc.idlt(f, nd), atol=1e-14)
+
+
 def test_idlt_simple_functions(orc):
     N = 50
     nd = orc.legpts(N)
