@@ -104,6 +104,26 @@ int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out);
  * the first kind, Eq. 5). */
 int gbdlt_legpts(gbdlt_plan plan, double* x, double* theta, double* w, double* dtheta);
 
+/* Allocation-free Gauss-Legendre rule, for callers that cannot call
+ * cudaMalloc (a fixed pre-reserved memory budget owned by their own
+ * allocator, a latency-critical path that cannot afford cudaMalloc's implicit
+ * synchronisation, a plugin handed its buffers by a host framework).  The paper
+ * has no counterpart; it is the node kernel of gbdlt_legpts without a plan.
+ *   N: any integer 1 <= N <= 65536; larger N returns GBDLT_ERR_UNSUPPORTED_N.
+ *   x, theta, w (device, N doubles each, required) and dtheta (device, N
+ *   doubles, may be NULL): the same arrays and ordering as gbdlt_legpts.
+ *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream).
+ * Allocates no memory.  Its scratch (N doubles and a status word) is a
+ * 512 KB array in the library's device memory, present on every GPU that loads
+ * the library until the process exits.  The first call on each device looks up
+ * that array's device address (make that first call before any stream capture
+ * on that device).  Every call uses the same array, so calls that overlap on
+ * the GPU (different streams, different host threads) race and must be
+ * serialised by the caller.  Synchronises `cuda_stream` before returning and
+ * returns GBDLT_ERR_NOT_CONVERGED if a node iteration did not settle. */
+int gbdlt_legpts_noalloc(int64_t N, double* x, double* theta, double* w, double* dtheta,
+                         void* cuda_stream);
+
 /* Legendre -> Chebyshev coefficients (Sec. 3): chat = M c. */
 int gbdlt_leg2cheb(gbdlt_plan plan, const void* c, void* chat, int64_t batch);
 /* Transpose: out = M^T y (Sec. 4, item 3). */

@@ -70,7 +70,7 @@ class Params(ctypes.Structure):
 
 ENTRY_POINTS = (
     "gbdlt_plan_params", "gbdlt_plan_create", "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
-    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_leg2cheb",
+    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
     "gbdlt_status_string", "gbdlt_launch_count",
@@ -96,6 +96,7 @@ def lib():
         L.gbdlt_plan_sync.argtypes = [vp]
         L.gbdlt_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
         L.gbdlt_legpts.argtypes = [vp, vp, vp, vp, vp]
+        L.gbdlt_legpts_noalloc.argtypes = [i64, vp, vp, vp, vp, vp]
         for name in ("gbdlt_leg2cheb", "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t",
                      "gbdlt_dlt", "gbdlt_dlt_t", "gbdlt_idlt", "gbdlt_idlt_t"):
             getattr(L, name).argtypes = [vp, vp, vp, i64]

@@ -27,6 +27,8 @@
 // by the Taylor series of Sec. 2.1 (computed from the exact difference
 // theta*_k - theta^cheb1_k = pi (N-2k-1) / (4N(N+1/2)) plus delta, so it keeps
 // full relative accuracy).
+#include <mutex>
+
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -203,3 +205,114 @@ int launch_legpts(Plan& P, double CN) {
 }
 
 }  // namespace gbdlt
+
+// ---------------------------------------------------------------------------
+// Allocation-free node computation (gbdlt_legpts_noalloc)
+//
+// Some callers cannot allocate device memory where they need a quadrature
+// rule: code that runs under a fixed, pre-reserved memory budget (an
+// application whose own allocator owns every byte of the GPU), latency-critical
+// paths where cudaMalloc's implicit device synchronisation is not acceptable,
+// and plugins that are handed buffers by a host framework and may not call the
+// CUDA allocator themselves.  For them this entry point computes the
+// Gauss-Legendre rule without a plan: the node kernel's scratch (the scaled
+// offsets t_k = N dtheta_k and the convergence status word) lives in a
+// file-scope device array instead of a plan workspace, and the caller passes
+// only the output buffers.
+// ---------------------------------------------------------------------------
+namespace gbdlt {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 65536;
+// [0, kNoAllocMaxN): t_k; [kNoAllocMaxN, +32): status word (first int) and padding.
+// 512 KB per GPU that loads the library, held until the process exits.
+static __device__ __align__(256) double g_legpts_scratch[kNoAllocMaxN + 32];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device; looked up once per
+// device with that device current (a host-side reference to the symbol is not
+// a device address).
+int scratch_on_current_device(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return GBDLT_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_legpts_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return GBDLT_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = (double*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return GBDLT_OK;
+}
+
+// C_N = sqrt(4/pi) Gamma(N+1)/Gamma(N+3/2) by the running product
+// C_{n+1} = C_n (n+1)/(n+3/2) in double-double, without allocating.
+double cn_running(int64_t N) {
+  double hi = 1.2732395447351628, lo = -7.871470670072994e-17;  // 4/pi
+  for (int64_t n = 0; n < N; ++n) {
+    const double b = (double)(n + 1);
+    double p = hi * b;
+    double e = std::fma(hi, b, -p);
+    e = std::fma(lo, b, e);
+    double s = p + e;
+    lo = e - (s - p);
+    hi = s;
+    const double d = (double)n + 1.5;
+    const double q1 = hi / d;
+    const double pp = q1 * d;
+    const double pe = std::fma(q1, d, -pp);
+    const double r = ((hi - pp) - pe) + lo;
+    const double q2 = r / d;
+    hi = q1 + q2;
+    lo = q2 - (hi - q1);
+  }
+  return hi + lo;
+}
+
+}  // namespace
+
+}  // namespace gbdlt
+
+extern "C" int gbdlt_legpts_noalloc(int64_t N, double* x, double* theta, double* w, double* dtheta,
+                                    void* cuda_stream) {
+  using namespace gbdlt;
+  if (N < 1 || N > kNoAllocMaxN) return GBDLT_ERR_UNSUPPORTED_N;
+  if (!x || !theta || !w) return GBDLT_ERR_INVALID_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  double* scratch = nullptr;
+  int st = scratch_on_current_device(&scratch);
+  if (st) return st;
+  double* tN = scratch;
+  int* status = reinterpret_cast<int*>(scratch + kNoAllocMaxN);
+  // the status word keeps the previous call's value: clear it first
+  if (cudaMemsetAsync(status, 0, sizeof(int), stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GBDLT_ERR_CUDA;
+  }
+  const int64_t half = (N + 1) / 2;
+  const int threads = 128;
+  k_legpts<<<(unsigned)((half + threads - 1) / threads), threads, 0, stream>>>(
+      N, cn_running(N), theta, x, w, tN, status);
+  count_launch();
+  if (dtheta) {
+    k_dtheta<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(tN, dtheta, N);
+    count_launch();
+  }
+  if (check_launch()) return GBDLT_ERR_CUDA;
+  int hs = 0;
+  if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GBDLT_ERR_CUDA;
+  }
+  return (hs & 1) ? GBDLT_ERR_NOT_CONVERGED : GBDLT_OK;
+}
