@@ -26,18 +26,18 @@ namespace gbdlt {
 constexpr int FFT_TILE = 4096;
 constexpr int FFT_THREADS = 256;
 
-__device__ __forceinline__ double2 tw_lookup(const double2* __restrict__ hi,
-                                             const double2* __restrict__ lo, int64_t e) {
-  double2 h = hi[e >> 12];
-  double2 l = lo[e & 4095];
-  return make_double2(h.x * l.x - h.y * l.y, h.x * l.y + h.y * l.x);
+// e^{2 pi i e / N} from the two-level table, multiplied in the precision T
+template <typename T>
+__device__ __forceinline__ C2<T> tw_lookup(const C2<T>* __restrict__ hi, const C2<T>* __restrict__ lo,
+                                           int64_t e) {
+  return cmul<T>(hi[e >> 12], lo[e & 4095]);
 }
 
 // In-place Stockham FFT of `lines` vectors of length L stored at
 // sm[line * pitch + i].  All threads of the CTA must call it.
 template <typename T, int DIR>
 __device__ void fft_tile(C2<T>* sm, int L, int lines, int pitch,
-                         const double2* __restrict__ tw4096) {
+                         const C2<T>* __restrict__ tw4096) {
   using CT = C2<T>;
   const int tid = threadIdx.x;
   int logL = 31 - __clz(L);
@@ -65,8 +65,8 @@ __device__ void fft_tile(C2<T>* sm, int L, int lines, int pitch,
             int step = (FFT_TILE / 4) / Ns;  // 4096 / (Ns * 4)
 #pragma unroll
             for (int r = 1; r < 4; ++r) {
-              double2 w = tw4096[r * k * step];
-              CT wt = mk<T>((T)w.x, (T)(DIR > 0 ? w.y : -w.y));
+              const CT w = tw4096[r * k * step];
+              const CT wt = mk<T>(w.x, DIR > 0 ? w.y : -w.y);
               v[q][r] = cmul<T>(v[q][r], wt);
             }
           }
@@ -108,8 +108,8 @@ __device__ void fft_tile(C2<T>* sm, int L, int lines, int pitch,
           v[q][0] = base[j];
           v[q][1] = base[j + Lh];
           if (Ns > 1) {
-            double2 w = tw4096[k * ((FFT_TILE / 2) / Ns)];
-            CT wt = mk<T>((T)w.x, (T)(DIR > 0 ? w.y : -w.y));
+            const CT w = tw4096[k * ((FFT_TILE / 2) / Ns)];
+            const CT wt = mk<T>(w.x, DIR > 0 ? w.y : -w.y);
             v[q][1] = cmul<T>(v[q][1], wt);
           }
           dst[q] = line * pitch + (j - k) * 2 + k;
@@ -134,7 +134,7 @@ __device__ void fft_tile(C2<T>* sm, int L, int lines, int pitch,
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
-    k_fft_single(C2<T>* __restrict__ data, int L, int64_t nvec, const double2* __restrict__ tw4096) {
+    k_fft_single(C2<T>* __restrict__ data, int L, int64_t nvec, const C2<T>* __restrict__ tw4096) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int lines_max = FFT_TILE / L;
@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int L2, int C,
-               const double2* __restrict__ tw4096, const double2* __restrict__ thi,
-               const double2* __restrict__ tlo) {
+               const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
+               const C2<T>* __restrict__ tlo) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int c0 = blockIdx.x * C;
@@ -171,8 +171,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
     int64_t e = (int64_t)(c0 + c) * k1;
     C2<T> val = sm[c * pitch + k1];
     if (e != 0) {
-      double2 w = tw_lookup(thi, tlo, e);
-      C2<T> wt = mk<T>((T)w.x, (T)(DIR > 0 ? w.y : -w.y));
+      const C2<T> w = tw_lookup<T>(thi, tlo, e);
+      const C2<T> wt = mk<T>(w.x, DIR > 0 ? w.y : -w.y);
       val = cmul<T>(val, wt);
     }
     g[(int64_t)k1 * L2 + c0 + c] = val;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
-               int C2n, const double2* __restrict__ tw4096) {
+               int C2n, const C2<T>* __restrict__ tw4096) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int r0 = blockIdx.x * C2n;
@@ -207,6 +207,7 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   using CT = C2<T>;
   const int64_t N = P.p.N;
   if (nvec <= 0 || N <= 1) return a;
+  const TwT<T> tw = tw_tables(P, T());
   // largest tile: C lines of L1+1 (pitch) with C * L1 = 4096 and L1 >= 64
   const size_t smax = (size_t)(FFT_TILE + 64) * sizeof(CT);
   static bool attrs = false;  // one flag per (T, DIR) instantiation
@@ -221,7 +222,7 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
     int lines = FFT_TILE / L;
     int64_t grid = (nvec + lines - 1) / lines;
     size_t sm = (size_t)lines * L * sizeof(CT);
-    k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, nvec, P.tw4096);
+    k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, nvec, tw.t4096);
     int lg = 0;
     while ((1 << lg) < L) ++lg;
     launched(P, "fft_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
@@ -235,11 +236,11 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   int C2n = FFT_TILE / L2;
   dim3 g1(L2 / C, (unsigned)nvec);
   k_fft_cols<T, DIR><<<g1, FFT_THREADS, (size_t)C * (L1 + 1) * sizeof(CT), P.stream>>>(
-      (CT*)a, N, L1, L2, C, P.tw4096, P.twN.hi, P.twN.lo);
+      (CT*)a, N, L1, L2, C, tw.t4096, tw.nhi, tw.nlo);
   launched(P, "fft_cols", (5.0 * (p / 2) + 6.0) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
   dim3 g2(L1 / C2n, (unsigned)nvec);
   k_fft_rows<T, DIR><<<g2, FFT_THREADS, (size_t)C2n * (L2 + 1) * sizeof(CT), P.stream>>>(
-      (const CT*)a, (CT*)b, N, L1, L2, C2n, P.tw4096);
+      (const CT*)a, (CT*)b, N, L1, L2, C2n, tw.t4096);
   launched(P, "fft_rows", 5.0 * (p - p / 2) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
   return b;
 }

@@ -174,8 +174,13 @@ struct Plan {
   double* Cn = nullptr;     // [N+1]
   double* ra = nullptr;     // (2n+1)/(n+1)
   double* rb = nullptr;     // n/(n+1)
+  float2* ra_ff = nullptr;  // the same as float-float (hi, lo), for the FP32 form
+  float2* rb_ff = nullptr;
   double2* tw4096 = nullptr;
   Twiddle2 twN, tw4N;
+  // the same tables rounded to float, used by the FP32 form (no FP64 work there)
+  float2* tw4096f = nullptr;
+  float2 *twNf_lo = nullptr, *twNf_hi = nullptr, *tw4Nf_lo = nullptr, *tw4Nf_hi = nullptr;
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
   RecLayout rec;
   // workspace (element type = plan precision)
@@ -193,6 +198,22 @@ struct Plan {
   double CN = 0;         // C_N for the node kernel
   struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
 };
+
+// twiddle tables in the precision T of a transform
+template <typename T>
+struct TwT {
+  const C2<T>* t4096;  // e^{2 pi i j / 4096}
+  const C2<T>* nlo;    // e^{2 pi i e / N}, two-level
+  const C2<T>* nhi;
+  const C2<T>* flo;    // e^{2 pi i e / (4N)}, two-level
+  const C2<T>* fhi;
+};
+inline TwT<double> tw_tables(const Plan& P, double) {
+  return {P.tw4096, P.twN.lo, P.twN.hi, P.tw4N.lo, P.tw4N.hi};
+}
+inline TwT<float> tw_tables(const Plan& P, float) {
+  return {P.tw4096f, P.twNf_lo, P.twNf_hi, P.tw4Nf_lo, P.tw4Nf_hi};
+}
 
 // ---------------------------------------------------------------------------
 // launch bookkeeping

@@ -2,9 +2,10 @@
 //
 // One thread per node k < ceil(N/2) (theta < pi/2); the other half follows from
 // the symmetry theta_{N-1-k} = pi - theta_k, w_{N-1-k} = w_k.  Newton's method
-// runs in delta = theta - theta*_k, started at the cheb* point
+// runs in delta = theta - theta*_k around the cheb* point
 // theta*_k = (k+3/4)pi/(N+1/2) of Sec. 2.2, which Lemma 2.3 places within
-// 1/(3 pi (2N+1)) of the root.  Working in delta keeps the phase of P_N exact:
+// 1/(3 pi (2N+1)) of the root (interior nodes start from the first-order
+// correction of that point, see k_legpts).  Working in delta keeps the phase of P_N exact:
 // (N+1/2) theta*_k - pi/4 = (k+1/2) pi, so cos/sin of the phase are those of the
 // small angle eps = (N+1/2) delta, with no large-argument reduction.
 //
@@ -126,7 +127,10 @@ __global__ void k_legpts(int64_t N, double CN, double* __restrict__ theta, doubl
     mode = 1;
   else
     mode = 2;
-  double d = 0.0;
+  // interior nodes start from the zero of the first two terms of the expansion:
+  // cos(phi_0) + h_1 cos(phi_1) / (2 sin theta) = 0 gives, to first order,
+  // (N+1/2) delta = cot(theta) / (8 (N+3/2)), i.e. about 1000 times closer than theta*
+  double d = mode == 1 ? (c0 / s0) / (8.0 * Nh * ((double)N + 1.5)) : 0.0;
   bool ok = false;
   PD r;
   double s = s0, c = c0, sh = 0, ch = 0;

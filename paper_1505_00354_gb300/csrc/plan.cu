@@ -300,6 +300,14 @@ void twiddle_fill(Plan& P, double2* out, int64_t count, int64_t B, int64_t mult)
   k_twiddle<<<(unsigned)((count + 255) / 256), 256, 0, P.stream>>>(out, count, B, mult);
   count_launch();
 }
+__global__ void k_to_float2(const double2* in, float2* out, int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+void to_float(Plan& P, const double2* in, float2* out, int64_t count) {
+  k_to_float2<<<(unsigned)((count + 255) / 256), 256, 0, P.stream>>>(in, out, count);
+  count_launch();
+}
 }  // namespace
 
 int launch_twiddle_init(Plan& P) {
@@ -308,6 +316,11 @@ int launch_twiddle_init(Plan& P) {
   twiddle_fill(P, P.twN.hi, std::max<int64_t>(1, P.twN.B / 4096), P.twN.B, 4096);
   twiddle_fill(P, P.tw4N.lo, 4096, P.tw4N.B, 1);
   twiddle_fill(P, P.tw4N.hi, std::max<int64_t>(1, P.tw4N.B / 4096), P.tw4N.B, 4096);
+  to_float(P, P.tw4096, P.tw4096f, 4096);
+  to_float(P, P.twN.lo, P.twNf_lo, 4096);
+  to_float(P, P.twN.hi, P.twNf_hi, std::max<int64_t>(1, P.twN.B / 4096));
+  to_float(P, P.tw4N.lo, P.tw4Nf_lo, 4096);
+  to_float(P, P.tw4N.hi, P.tw4Nf_hi, std::max<int64_t>(1, P.tw4N.B / 4096));
   return check_launch();
 }
 
@@ -394,11 +407,15 @@ static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream
   size_t o_theta = A.take<double>(N), o_x = A.take<double>(N), o_w = A.take<double>(N),
          o_t = A.take<double>(N);
   size_t o_cn = A.take<double>(N + 1), o_ra = A.take<double>(N + 1024), o_rb = A.take<double>(N + 1024);
+  size_t o_raff = A.take<float2>(N + 1024), o_rbff = A.take<float2>(N + 1024);
   size_t o_tw = A.take<double2>(4096);
   P->twN.B = N;
   P->tw4N.B = 4 * N;
   size_t o_twNlo = A.take<double2>(4096), o_twNhi = A.take<double2>(std::max<int64_t>(1, N / 4096));
   size_t o_tw4lo = A.take<double2>(4096), o_tw4hi = A.take<double2>(std::max<int64_t>(1, 4 * N / 4096));
+  size_t o_twf = A.take<float2>(4096), o_twNflo = A.take<float2>(4096),
+         o_twNfhi = A.take<float2>(std::max<int64_t>(1, N / 4096)), o_tw4flo = A.take<float2>(4096),
+         o_tw4fhi = A.take<float2>(std::max<int64_t>(1, 4 * N / 4096));
   size_t o_cut = A.take<int32_t>(H), o_poff = A.take<int64_t>(H), o_crb = A.take<int32_t>(R.ncta),
          o_cj = A.take<int32_t>(R.ncta), o_toff = A.take<int64_t>(R.nblocks),
          o_mc = A.take<int32_t>(R.nblocks), o_state = A.take<double2>(R.nseg_total),
@@ -432,11 +449,18 @@ static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream
   P->Cn = (double*)(base + o_cn);
   P->ra = (double*)(base + o_ra);
   P->rb = (double*)(base + o_rb);
+  P->ra_ff = (float2*)(base + o_raff);
+  P->rb_ff = (float2*)(base + o_rbff);
   P->tw4096 = (double2*)(base + o_tw);
   P->twN.lo = (double2*)(base + o_twNlo);
   P->twN.hi = (double2*)(base + o_twNhi);
   P->tw4N.lo = (double2*)(base + o_tw4lo);
   P->tw4N.hi = (double2*)(base + o_tw4hi);
+  P->tw4096f = (float2*)(base + o_twf);
+  P->twNf_lo = (float2*)(base + o_twNflo);
+  P->twNf_hi = (float2*)(base + o_twNfhi);
+  P->tw4Nf_lo = (float2*)(base + o_tw4flo);
+  P->tw4Nf_hi = (float2*)(base + o_tw4fhi);
   R.cut = (int32_t*)(base + o_cut);
   R.poff = (int64_t*)(base + o_poff);
   R.cta_rb = (int32_t*)(base + o_crb);
@@ -470,6 +494,14 @@ static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream
     }
     up(P->ra, ra.data(), sizeof(double) * ra.size());
     up(P->rb, rb.data(), sizeof(double) * rb.size());
+    std::vector<float2> raf(ra.size()), rbf(rb.size());
+    for (size_t i = 0; i < ra.size(); ++i) {
+      const float ah = (float)ra[i], bh = (float)rb[i];
+      raf[i] = make_float2(ah, (float)(ra[i] - (double)ah));
+      rbf[i] = make_float2(bh, (float)(rb[i] - (double)bh));
+    }
+    up(P->ra_ff, raf.data(), sizeof(float2) * raf.size());
+    up(P->rb_ff, rbf.data(), sizeof(float2) * rbf.size());
   }
   if (H > 0) {
     up(R.cut, cut.data(), sizeof(int32_t) * (size_t)H);

@@ -50,17 +50,22 @@ BandArgs band_args(const Plan& P) {
   return b;
 }
 
+template <typename T>
 struct TwArgs {
-  const double2* hi;
-  const double2* lo;
+  const C2<T>* hi;
+  const C2<T>* lo;
 };
 
 // e^{2 pi i e / B} from the two-level table, multiplied in precision T
 template <typename T>
-__device__ __forceinline__ C2<T> twid(TwArgs t, int64_t e) {
-  double2 h = t.hi[e >> 12];
-  double2 l = t.lo[e & 4095];
-  return cmul<T>(to_c<T>(h), to_c<T>(l));
+__device__ __forceinline__ C2<T> twid(TwArgs<T> t, int64_t e) {
+  return cmul<T>(t.hi[e >> 12], t.lo[e & 4095]);
+}
+
+template <typename T>
+TwArgs<T> tw4n_args(const Plan& P) {
+  const TwT<T> t = tw_tables(P, T());
+  return TwArgs<T>{t.fhi, t.flo};
 }
 
 __device__ __forceinline__ void sincospi_t(double a, double* s, double* c) { sincospi(a, s, c); }
@@ -81,7 +86,7 @@ __device__ __forceinline__ int sgn_odd(int l) { return (((l + 1) >> 1) & 1) ? -1
 // ---------------------------------------------------------------- leg2cheb
 template <typename T>
 __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, int64_t N, int M,
-                          BandArgs B, const double* __restrict__ Cn, TwArgs tw4N) {
+                          BandArgs B, const double* __restrict__ Cn, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const T cn = (T)Cn[n] * c[n];
@@ -136,7 +141,7 @@ __global__ void k_a4_pro(const T* __restrict__ v, C2<T>* __restrict__ U, int64_t
 }
 
 template <typename T>
-__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, TwArgs tw4N) {
+__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const C2<T> Fn = F[n];
@@ -150,7 +155,7 @@ __global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int6
 // ---------------------------------------------------------------- FCS helpers
 template <typename T>
 __global__ void k_fcs_pro(const T* __restrict__ a, C2<T>* __restrict__ U, int64_t N, int scale_d,
-                          TwArgs tw4N) {
+                          TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   T an = a[n];
@@ -172,7 +177,7 @@ __global__ void k_fcs_re_epi(const C2<T>* __restrict__ Y, T* __restrict__ out, i
 // only when its l <= L-1.
 template <typename T>
 __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int64_t N, int L,
-                          int inc0, int npair, TwArgs tw4N) {
+                          int inc0, int npair, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const T r = (T)n / (T)N;
@@ -266,7 +271,7 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
 // mode 1: write u_n to uout.
 template <typename T>
 __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T* __restrict__ uout,
-                           int64_t N, int L, int inc0, int npair, int mode, TwArgs tw4N) {
+                           int64_t N, int L, int inc0, int npair, int mode, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const T r = (T)n / (T)N;
@@ -363,7 +368,7 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
 template <typename T>
 __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ rect, T* __restrict__ out,
                            int64_t N, int M, BandArgs B, const double* __restrict__ Cn, int scale_s,
-                           TwArgs tw4N) {
+                           TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   T acc = rect[n];
@@ -411,7 +416,7 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
 template <typename T>
 int launch_l2c_pro(Plan& P, const T* c, C2<T>* U) {
-  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const TwArgs<T> tw = tw4n_args<T>(P);
   k_l2c_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
@@ -445,7 +450,7 @@ int launch_a4_pro(Plan& P, const T* v, C2<T>* U) {
 }
 template <typename T>
 int launch_a4_epi(Plan& P, const C2<T>* F, T* chat) {
-  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const TwArgs<T> tw = tw4n_args<T>(P);
   k_a4_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, chat, P.p.N, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
@@ -457,7 +462,7 @@ int launch_a4_epi(Plan& P, const C2<T>* F, T* chat) {
 }
 template <typename T>
 int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d) {
-  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const TwArgs<T> tw = tw4n_args<T>(P);
   k_fcs_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
@@ -480,7 +485,7 @@ int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out) {
 }
 template <typename T>
 int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair) {
-  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const TwArgs<T> tw = tw4n_args<T>(P);
   k_tay_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(chat, U, P.p.N, P.p.L, inc0, npair, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
@@ -515,7 +520,7 @@ int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npai
 }
 template <typename T>
 int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair) {
-  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const TwArgs<T> tw = tw4n_args<T>(P);
   const int mode = Q ? 0 : 1;
   k_tayt_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, mode, tw);
   {
@@ -540,7 +545,7 @@ int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>*
 }
 template <typename T>
 int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s) {
-  TwArgs tw{P.tw4N.hi, P.tw4N.lo};
+  const TwArgs<T> tw = tw4n_args<T>(P);
   k_l2ct_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
                                                      scale_s, tw);
   {
