@@ -246,6 +246,60 @@ def run_gpu(args, world, rank, local):
     t32 = sum(ms32) / len(ms32)
     prof32 = plan32.profile_report()
 
+    # ---------------- uneven batch (4096 transforms, N log-uniform in [16, 8192], 50/50)
+    def time_batch(prec):
+        rng = np.random.default_rng(40)
+        Ns = (2 ** np.round(rng.uniform(4, 13, 4096))).astype(np.int64)
+        dirs = rng.integers(0, 2, 4096).astype(np.int32)
+        x = np.concatenate([inputs.coeffs(int(n), 4000000 + i, 1.0) for i, n in enumerate(Ns)])
+        t0 = time.perf_counter()
+        bt = g.Batch(Ns, dirs, prec)
+        t_create = time.perf_counter() - t0
+        xd = torch.tensor(x, dtype=torch.float64 if prec == g.FP64 else torch.float32, device="cuda")
+        yd = torch.empty_like(xd)
+        for _ in range(args.warmup):
+            bt.run(xd, yd)
+        torch.cuda.synchronize()
+        ev = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.run(xd, yd)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        inf = bt.info()
+        bt.close()
+        return {"value": round(4096 / (ms / 1e3), 1), "unit": "transforms/s", "ms_per_batch": round(ms, 4),
+                "transforms": 4096, "elements": int(Ns.sum()), "groups": inf["groups"],
+                "graph_kernels": inf["graph_kernels"], "create_s": round(t_create, 3)}
+
+    batch64 = time_batch(g.FP64)
+    batch32 = time_batch(g.FP32)
+
+    # ---------------- differentiation: loss ||DLT(c) - y||^2, batch 256 x N = 4096
+    from paper_1505_00354_gb300 import autograd as gag
+    cb = torch.tensor(np.stack([inputs.coeffs(4096, 5200 + i, 1.0) for i in range(256)]), device="cuda")
+    yb = gag.dlt(cb).detach() + 1e-3
+    cvar = cb.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        cvar.grad = None
+        ((gag.dlt(cvar) - yb) ** 2).sum().backward()
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        fwd_bwd()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_ag = a.elapsed_time(b) / args.steps
+
     # ---------------- end to end through the public API with host buffers
     c_host = torch.tensor(c_np, dtype=torch.float64).pin_memory()
     f_host = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -329,6 +383,11 @@ def run_gpu(args, world, rank, local):
                           "breakdown": {k: round(v["ms"] / args.steps, 4)
                                         for k, v in sorted(prof32.items(), key=lambda kv: -kv[1]["ms"])}},
             "cold_plan_ms": {"fp64": round(cold64 * 1e3, 2), "fp32": round(cold32 * 1e3, 2)},
+            "batch_uneven": {"workload": "4096 transforms, N = 2^round(U(4,13)), DLT/IDLT 50/50, one graph replay",
+                             "fp64": batch64, "fp32": batch32},
+            "autograd": {"workload": "loss ||DLT(c) - y||^2, batch 256 x N=4096 FP64, forward + backward",
+                         "ms_per_step": round(ms_ag, 4),
+                         "transforms_per_s": round(2 * 256 / (ms_ag / 1e3), 1)},
             "breakdown": breakdown,
         }
         if not args.no_check:

@@ -142,6 +142,28 @@ int gbdlt_idlt(gbdlt_plan plan, const void* f, void* c, int64_t batch);
 /* Transposed IDLT: out = D_w P_N(x^leg) D_s g, i.e. out_k = w_k sum_n (n+1/2) g_n P_n(x_k). */
 int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
 
+/* Uneven batches (no counterpart in the paper, which transforms one vector at
+ * a time): B transforms of lengths Ns_host[i] (powers of two, 1..2^24) and
+ * directions dirs_host[i] (0 = DLT, 1 = IDLT), all of one precision, executed
+ * together.  Inputs and outputs are concatenated in the given order: transform
+ * i occupies elements [sum_{j<i} Ns[j], sum_{j<=i} Ns[j]) of `in` and `out`
+ * (device, element type of `prec`).  Creation groups the transforms by
+ * (N, direction), makes one plan per distinct N sized for its largest group,
+ * allocates grouped staging buffers and captures every group's batched chain
+ * into one CUDA graph (1 <= B <= 65535).  An execution makes the work wait for
+ * `cuda_stream`, gathers `in` into the staging buffers, replays the graph,
+ * scatters the results into `out` and makes `cuda_stream` wait for them; it
+ * allocates nothing.  Executions of one batch object must not overlap. */
+typedef struct gbdlt_batch_s* gbdlt_batch;
+int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
+                       double eps, gbdlt_batch* out);
+int gbdlt_batch_exec(gbdlt_batch batch, const void* in, void* out, void* cuda_stream);
+/* total elements of the concatenated layout, number of (N, direction) groups,
+ * kernel nodes in the captured graph (any pointer may be NULL) */
+int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int64_t* groups,
+                     int64_t* graph_kernels);
+int gbdlt_batch_destroy(gbdlt_batch batch);
+
 /* Per-kernel device timing on the plan's stream, for profiling (off by
  * default).  mode 1: turn on and start timing from this point (work enqueued
  * earlier is not attributed); call again before each region to re-anchor.

@@ -73,6 +73,7 @@ ENTRY_POINTS = (
     "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
+    "gbdlt_batch_create", "gbdlt_batch_exec", "gbdlt_batch_info", "gbdlt_batch_destroy",
     "gbdlt_status_string", "gbdlt_launch_count",
 )
 
@@ -100,6 +101,11 @@ def lib():
         for name in ("gbdlt_leg2cheb", "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t",
                      "gbdlt_dlt", "gbdlt_dlt_t", "gbdlt_idlt", "gbdlt_idlt_t"):
             getattr(L, name).argtypes = [vp, vp, vp, i64]
+        L.gbdlt_batch_create.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                         i64, i32, dbl, ctypes.POINTER(vp)]
+        L.gbdlt_batch_exec.argtypes = [vp, vp, vp, vp]
+        L.gbdlt_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.gbdlt_batch_destroy.argtypes = [vp]
         L.gbdlt_plan_profile.argtypes = [vp, i32]
         L.gbdlt_plan_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.gbdlt_status_string.argtypes = [i32]
@@ -243,6 +249,53 @@ class Plan:
 
     def idlt_t(self, g, out=None):
         return self._run("idlt_t", g, out)
+
+
+class Batch:
+    """Uneven batch of DLTs (dir 0) and IDLTs (dir 1) of power-of-two lengths,
+    executed as one CUDA-graph replay (gbdlt_batch_*).  ``run(x)`` takes and
+    returns the concatenation of the B vectors in the given order."""
+
+    def __init__(self, Ns, dirs, prec: int = FP64, eps: float = 0.0):
+        import numpy as np
+        Ns = np.ascontiguousarray(Ns, dtype=np.int64)
+        dirs = np.ascontiguousarray(dirs, dtype=np.int32)
+        if Ns.shape != dirs.shape:
+            raise ValueError("Ns and dirs must have the same length")
+        self._h = None
+        self.Ns, self.dirs, self.prec, self.dtype = Ns, dirs, prec, _dtype(prec)
+        self.offsets = np.concatenate([[0], np.cumsum(Ns)])
+        h = ctypes.c_void_p()
+        _check(lib().gbdlt_batch_create(Ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        Ns.size, prec, eps, ctypes.byref(h)), "batch_create")
+        self._h = h
+
+    def info(self) -> dict:
+        t, g, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().gbdlt_batch_info(self._h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(k)), "batch_info")
+        return {"total_elements": t.value, "groups": g.value, "graph_kernels": k.value}
+
+    def run(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        n = int(self.offsets[-1])
+        if not x.is_cuda or x.dtype != self.dtype or x.numel() != n:
+            raise ValueError(f"batch: expected a CUDA {self.dtype} tensor of {n} elements")
+        x = x.contiguous()
+        out = torch.empty_like(x) if out is None else out
+        _check(lib().gbdlt_batch_exec(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "batch_exec")
+        return out
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.gbdlt_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------------------

@@ -186,7 +186,8 @@ struct Plan {
   // workspace (element type = plan precision)
   void* bufA = nullptr;
   void* bufB = nullptr;
-  int64_t nfft_max = 0;  // vectors per FFT buffer
+  int64_t nfft_max = 0;  // FFT vectors per transform (per batch item)
+  int64_t bcap = 1;      // batch items one pass over the workspace holds
   void* v = nullptr;     // [N]
   void* chat = nullptr;  // [N]
   void* z = nullptr;     // [N]
@@ -215,6 +216,13 @@ inline TwT<float> tw_tables(const Plan& P, float) {
   return {P.tw4096f, P.twNf_lo, P.twNf_hi, P.tw4Nf_lo, P.tw4Nf_hi};
 }
 
+// plan lifecycle and the operator dispatch shared by the C ABI and the batch
+// executor; max_batch > 0 limits the batch items one workspace pass holds
+int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64_t max_batch, Plan** out);
+void free_plan(Plan* P);
+enum Op { OP_L2C, OP_L2C_T, OP_CHEB, OP_CHEB_T, OP_DLT, OP_DLT_T, OP_IDLT, OP_IDLT_T };
+int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch);
+
 // ---------------------------------------------------------------------------
 // launch bookkeeping
 // ---------------------------------------------------------------------------
@@ -239,35 +247,35 @@ void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir);
 // rec.cu
 int launch_rec_state_init(Plan& P);
 template <typename T>
-int launch_rec_forward(Plan& P, const T* c, T* vrec);
+int launch_rec_forward(Plan& P, const T* c, T* vrec, int64_t nb);
 template <typename T>
-int launch_rec_transpose(Plan& P, const T* z, T* out);
+int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb);
 // stages.cu (prologues / epilogues)
 template <typename T>
-int launch_l2c_pro(Plan& P, const T* c, C2<T>* U);
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb);
 template <typename T>
-int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v);
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v, int64_t nb);
 template <typename T>
-int launch_a4_pro(Plan& P, const T* v, C2<T>* U);
+int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb);
 template <typename T>
-int launch_a4_epi(Plan& P, const C2<T>* F, T* chat);
+int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb);
 template <typename T>
-int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d);
+int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d, int64_t nb);
 template <typename T>
-int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair);
+int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair);
+int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair);
+int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair);
+int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U);
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, int64_t nb);
 template <typename T>
-int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s);
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s, int64_t nb);
 template <typename T>
-int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out);
+int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb);
 template <typename T>
-int launch_scale(Plan& P, const T* in, T* out, int which);
+int launch_scale(Plan& P, const T* in, T* out, int which, int64_t nb);
 
 }  // namespace gbdlt

@@ -339,6 +339,8 @@ struct Arena {
   }
 };
 
+}  // namespace
+
 void free_plan(Plan* P) {
   if (!P) return;
   if (P->arena) cudaFree(P->arena);
@@ -349,9 +351,8 @@ void free_plan(Plan* P) {
   delete P;
 }
 
-}  // namespace
 
-static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, Plan** out) {
+int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64_t max_batch, Plan** out) {
   Params prm;
   int st = derive_params(N, prec, eps, &prm);
   if (st != GBDLT_OK) return st;
@@ -402,6 +403,14 @@ static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream
   }
   const int npair = (prm.L + 1) / 2;
   P->nfft_max = std::max<int64_t>({(int64_t)prm.K * prm.M, (int64_t)npair, 1});
+  {
+    // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
+    const double per_item = 2.0 * P->nfft_max * N * cs + 5.0 * N * ts + 16.0 * R.nseg_total +
+                            8.0 * R.tbuf_total;
+    P->bcap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(512.0 * (1 << 20) / per_item)));
+    if (max_batch > 0) P->bcap = std::min<int64_t>(P->bcap, max_batch);
+  }
+  const int64_t BC = P->bcap;
   // arena layout
   Arena A;
   size_t o_theta = A.take<double>(N), o_x = A.take<double>(N), o_w = A.take<double>(N),
@@ -419,21 +428,19 @@ static int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream
   size_t o_cut = A.take<int32_t>(H), o_poff = A.take<int64_t>(H), o_crb = A.take<int32_t>(R.ncta),
          o_cj = A.take<int32_t>(R.ncta), o_toff = A.take<int64_t>(R.nblocks),
          o_mc = A.take<int32_t>(R.nblocks), o_state = A.take<double2>(R.nseg_total),
-         o_part = A.take<double2>(R.nseg_total), o_tbuf = A.take<double>(R.tbuf_total);
-  size_t o_bufA = A.off;
-  A.off += ((size_t)P->nfft_max * (size_t)N * cs + 255) & ~(size_t)255;
-  size_t o_bufB = A.off;
-  A.off += ((size_t)P->nfft_max * (size_t)N * cs + 255) & ~(size_t)255;
-  size_t o_v = A.off;
-  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
-  size_t o_chat = A.off;
-  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
-  size_t o_z = A.off;
-  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
-  size_t o_tmp = A.off;
-  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
-  size_t o_tmp2 = A.off;
-  A.off += ((size_t)N * ts + 255) & ~(size_t)255;
+         o_part = A.take<double2>(BC * R.nseg_total), o_tbuf = A.take<double>(BC * R.tbuf_total);
+  auto bytes_block = [&](size_t b) {
+    size_t o = A.off;
+    A.off += (b + 255) & ~(size_t)255;
+    return o;
+  };
+  size_t o_bufA = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
+  size_t o_bufB = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
+  size_t o_v = bytes_block((size_t)BC * N * ts);
+  size_t o_chat = bytes_block((size_t)BC * N * ts);
+  size_t o_z = bytes_block((size_t)BC * N * ts);
+  size_t o_tmp = bytes_block((size_t)BC * N * ts);
+  size_t o_tmp2 = bytes_block((size_t)BC * N * ts);
   size_t o_status = A.take<int>(1);
   P->ws_bytes = A.off;
   if (cudaMalloc(&P->arena, A.off) != cudaSuccess) {
@@ -547,45 +554,45 @@ inline void* other(Plan& P, const void* p) { return p == P.bufA ? P.bufB : P.buf
 
 // chat = M c (Sec. 3); also leaves v (values on the cheb1 grid) in P.v
 template <typename T>
-int run_leg2cheb(Plan& P, const T* c, T* chat) {
+int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   T* vrec = (T*)P.tmp;
   T* v = (T*)P.v;
-  int st = launch_rec_forward<T>(P, c, vrec);
+  int st = launch_rec_forward<T>(P, c, vrec, nb);
   if (st) return st;
   const C2<T>* Y = nullptr;
   if (KM > 0) {
-    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA);
+    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, nb);
     if (st) return st;
-    Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, KM, +1);
+    Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * KM, +1);
   }
-  st = launch_l2c_epi<T>(P, Y, vrec, v);
+  st = launch_l2c_epi<T>(P, Y, vrec, v, nb);
   if (st) return st;
-  st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA);
+  st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA, nb);
   if (st) return st;
-  const C2<T>* F = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, 1, -1);
-  return launch_a4_epi<T>(P, F, chat);
+  const C2<T>* F = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb, -1);
+  return launch_a4_epi<T>(P, F, chat, nb);
 }
 
 // Taylor NDCT (Sec. 2): f = [v] + sum_{l} ...; inc0 = 1 includes l = 0 (standalone chebeval)
 template <typename T>
-int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0) {
+int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb) {
   const int npair = inc0 ? (P.p.L + 1) / 2 : P.p.L / 2;
   if (npair == 0) {
-    if (!inc0) return cudaMemcpyAsync(f, v, sizeof(T) * P.p.N, cudaMemcpyDeviceToDevice, P.stream) ==
-                              cudaSuccess
+    if (!inc0) return cudaMemcpyAsync(f, v, sizeof(T) * P.p.N * nb, cudaMemcpyDeviceToDevice,
+                                      P.stream) == cudaSuccess
                           ? GBDLT_OK
                           : GBDLT_ERR_CUDA;
   }
-  int st = launch_tay_pro<T>(P, chat, (C2<T>*)P.bufA, inc0, npair);
+  int st = launch_tay_pro<T>(P, chat, (C2<T>*)P.bufA, inc0, npair, nb);
   if (st) return st;
-  const C2<T>* Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, npair, +1);
-  return launch_tay_epi<T>(P, Y, v, f, inc0, npair);
+  const C2<T>* Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * npair, +1);
+  return launch_tay_epi<T>(P, Y, v, f, inc0, npair, nb);
 }
 
 // transposed chain: out = [D_s] P^T [D_w] g (idlt when weighted), Sec. 4
 template <typename T>
-int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s) {
+int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   const int npair = P.p.L / 2;  // l = 1..L-1
   T* z = (T*)P.z;
@@ -593,95 +600,96 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s) {
   int st;
   const C2<T>* Y = nullptr;  // A4^T FFT output
   if (npair > 0) {
-    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, 0, npair);
+    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, 0, npair, nb);
     if (st) return st;
-    const void* F = launch_fft<T>(P, P.bufA, P.bufB, npair, -1);
+    const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * npair, -1);
     void* q = other(P, F);
-    st = launch_tayt_epi<T>(P, (const C2<T>*)F, (C2<T>*)q, nullptr, 0, npair);
+    st = launch_tayt_epi<T>(P, (const C2<T>*)F, (C2<T>*)q, nullptr, 0, npair, nb);
     if (st) return st;
-    Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), 1, +1);
+    Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), nb, +1);
   }
   void* U = Y ? other(P, Y) : P.bufA;
-  st = launch_l2ct_pro<T>(P, Y, g, use_w, z, (C2<T>*)U);
+  st = launch_l2ct_pro<T>(P, Y, g, use_w, z, (C2<T>*)U, nb);
   if (st) return st;
-  st = launch_rec_transpose<T>(P, z, rect);
+  st = launch_rec_transpose<T>(P, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
-  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), KM, -1);
-  return launch_l2ct_epi<T>(P, F2, rect, out, scale_s);
+  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), nb * KM, -1);
+  return launch_l2ct_epi<T>(P, F2, rect, out, scale_s, nb);
 }
 
 // out = M^T y: z = A4^T y, then P_cheb^T z
 template <typename T>
-int run_leg2cheb_t(Plan& P, const T* y, T* out) {
+int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   T* z = (T*)P.z;
   T* rect = (T*)P.tmp;
-  int st = launch_fcs_pro<T>(P, y, (C2<T>*)P.bufA, 1);
+  int st = launch_fcs_pro<T>(P, y, (C2<T>*)P.bufA, 1, nb);
   if (st) return st;
-  const void* Y = launch_fft<T>(P, P.bufA, P.bufB, 1, +1);
+  const void* Y = launch_fft<T>(P, P.bufA, P.bufB, nb, +1);
   void* U = other(P, Y);
-  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U);
+  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, nb);
   if (st) return st;
-  st = launch_rec_transpose<T>(P, z, rect);
+  st = launch_rec_transpose<T>(P, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
-  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), KM, -1);
-  return launch_l2ct_epi<T>(P, F2, rect, out, 0);
+  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), nb * KM, -1);
+  return launch_l2ct_epi<T>(P, F2, rect, out, 0, nb);
 }
 
 template <typename T>
-int run_chebeval_t(Plan& P, const T* g, T* out) {
+int run_chebeval_t(Plan& P, const T* g, T* out, int64_t nb) {
   const int npair = (P.p.L + 1) / 2;  // l = 0..L-1
-  int st = launch_tayt_pro<T>(P, g, 0, (C2<T>*)P.bufA, 1, npair);
+  int st = launch_tayt_pro<T>(P, g, 0, (C2<T>*)P.bufA, 1, npair, nb);
   if (st) return st;
-  const void* F = launch_fft<T>(P, P.bufA, P.bufB, npair, -1);
-  return launch_tayt_epi<T>(P, (const C2<T>*)F, nullptr, out, 1, npair);
+  const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * npair, -1);
+  return launch_tayt_epi<T>(P, (const C2<T>*)F, nullptr, out, 1, npair, nb);
 }
 
-enum Op { OP_L2C, OP_L2C_T, OP_CHEB, OP_CHEB_T, OP_DLT, OP_DLT_T, OP_IDLT, OP_IDLT_T };
 
 template <typename T>
-int run_one(Plan& P, int op, const T* in, T* out) {
+int run_one(Plan& P, int op, const T* in, T* out, int64_t nb) {
   const int64_t N = P.p.N;
   if (N == 1) {
     // every operator is the identity at N = 1 (P_0 = T_0 = 1, w_0 = 2, s_0 = 1/2)
-    return cudaMemcpyAsync(out, in, sizeof(T), cudaMemcpyDeviceToDevice, P.stream) == cudaSuccess
+    return cudaMemcpyAsync(out, in, sizeof(T) * nb, cudaMemcpyDeviceToDevice, P.stream) == cudaSuccess
                ? GBDLT_OK
                : GBDLT_ERR_CUDA;
   }
   switch (op) {
     case OP_L2C:
-      return run_leg2cheb<T>(P, in, out);
+      return run_leg2cheb<T>(P, in, out, nb);
     case OP_L2C_T:
-      return run_leg2cheb_t<T>(P, in, out);
+      return run_leg2cheb_t<T>(P, in, out, nb);
     case OP_CHEB:
-      return run_taylor<T>(P, in, nullptr, out, 1);
+      return run_taylor<T>(P, in, nullptr, out, 1, nb);
     case OP_CHEB_T:
-      return run_chebeval_t<T>(P, in, out);
+      return run_chebeval_t<T>(P, in, out, nb);
     case OP_DLT: {
-      int st = run_leg2cheb<T>(P, in, (T*)P.chat);
+      int st = run_leg2cheb<T>(P, in, (T*)P.chat, nb);
       if (st) return st;
-      return run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0);
+      return run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0, nb);
     }
     case OP_DLT_T:
-      return run_transposed<T>(P, in, out, 0, 0);
+      return run_transposed<T>(P, in, out, 0, 0, nb);
     case OP_IDLT:
-      return run_transposed<T>(P, in, out, 1, 1);
+      return run_transposed<T>(P, in, out, 1, 1, nb);
     case OP_IDLT_T: {
       // out = D_w P D_s g
       T* sg = (T*)P.tmp2;
-      int st = launch_scale<T>(P, in, sg, 1);
+      int st = launch_scale<T>(P, in, sg, 1, nb);
       if (st) return st;
-      st = run_leg2cheb<T>(P, sg, (T*)P.chat);
+      st = run_leg2cheb<T>(P, sg, (T*)P.chat, nb);
       if (st) return st;
-      st = run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0);
+      st = run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0, nb);
       if (st) return st;
-      return launch_scale<T>(P, out, out, 2);
+      return launch_scale<T>(P, out, out, 2, nb);
     }
   }
   return GBDLT_ERR_INVALID_ARG;
 }
+
+}  // namespace
 
 int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch) {
   if (!plan || batch < 0) return GBDLT_ERR_INVALID_ARG;
@@ -696,18 +704,18 @@ int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch) {
   const char* b = (const char*)out;
   const char* be = b + (size_t)batch * N * es;
   if (batch > 0 && a < be && b < ae) return GBDLT_ERR_INVALID_ARG;  // overlap
-  for (int64_t i = 0; i < batch; ++i) {
+  for (int64_t i = 0; i < batch; i += P.bcap) {
+    const int64_t nb = std::min<int64_t>(P.bcap, batch - i);
     int st;
     if (P.p.prec == GBDLT_FP64)
-      st = run_one<double>(P, op, (const double*)in + i * N, (double*)out + i * N);
+      st = run_one<double>(P, op, (const double*)in + i * N, (double*)out + i * N, nb);
     else
-      st = run_one<float>(P, op, (const float*)in + i * N, (float*)out + i * N);
+      st = run_one<float>(P, op, (const float*)in + i * N, (float*)out + i * N, nb);
     if (st) return st;
   }
   return check_launch();
 }
 
-}  // namespace
 
 }  // namespace gbdlt
 
@@ -754,7 +762,7 @@ int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_
   if (!out) return GBDLT_ERR_INVALID_ARG;
   *out = nullptr;
   Plan* P = nullptr;
-  int st = plan_create_impl(N, prec, eps, (cudaStream_t)cuda_stream, &P);
+  int st = plan_create_impl(N, prec, eps, (cudaStream_t)cuda_stream, 0, &P);
   if (st) return st;
   *out = reinterpret_cast<gbdlt_plan>(P);
   return GBDLT_OK;

@@ -29,6 +29,8 @@ struct RecArgs {
   int64_t N, H;
   int S;
   int64_t nblocks;
+  int64_t nseg_total;  // batch stride of the segment partials
+  int64_t tbuf_total;  // batch stride of the transposed partials
   const int32_t* cut;
   const int64_t* poff;
   const double2* state;
@@ -87,6 +89,8 @@ RecArgs rec_args(const Plan& P) {
   a.H = P.rec.H;
   a.S = P.rec.S;
   a.nblocks = P.rec.nblocks;
+  a.nseg_total = P.rec.nseg_total;
+  a.tbuf_total = P.rec.tbuf_total;
   a.cut = P.rec.cut;
   a.poff = P.rec.poff;
   a.state = P.rec.state;
@@ -155,6 +159,8 @@ __global__ void k_rec_scan(RecArgs R, const double2* __restrict__ Tbuf, double2*
 template <typename T>
 __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__ c,
                                                 double2* __restrict__ part) {
+  c += (int64_t)blockIdx.y * R.N;
+  part += (int64_t)blockIdx.y * R.nseg_total;
   const int64_t rbk = R.cta_rb[blockIdx.x];
   const int j = R.cta_j[blockIdx.x];
   const int64_t k = rbk * RT + threadIdx.x;
@@ -187,6 +193,8 @@ __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__
 // products c_n P_n accumulated in Kahan-compensated float
 __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __restrict__ c,
                                                    double2* __restrict__ part) {
+  c += (int64_t)blockIdx.y * R.N;
+  part += (int64_t)blockIdx.y * R.nseg_total;
   const int64_t rbk = R.cta_rb[blockIdx.x];
   const int j = R.cta_j[blockIdx.x];
   const int64_t k = rbk * RT + threadIdx.x;
@@ -218,6 +226,8 @@ __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __res
 template <typename T>
 __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T* __restrict__ vrec,
                                  int64_t r0, int64_t r1, int warp_mode) {
+  part += (int64_t)blockIdx.y * R.nseg_total;
+  vrec += (int64_t)blockIdx.y * R.N;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double E = 0.0, O = 0.0;
   int64_t k;
@@ -261,6 +271,8 @@ constexpr int TP = 33;  // tile pitch (doubles)
 template <typename T>
 __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z,
                                               double* __restrict__ tbuf) {
+  z += (int64_t)blockIdx.y * R.N;
+  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
   extern __shared__ double sm[];
   double* tile = sm;                  // [8][32][TP]
   double* wsum = sm + 8 * 32 * TP;    // [8][32]
@@ -323,6 +335,8 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
 // warp sums in float, row-block partials stored in double
 __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restrict__ z,
                                                  double* __restrict__ tbuf) {
+  z += (int64_t)blockIdx.y * R.N;
+  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
   extern __shared__ float smf[];
   float* tile = smf;                 // [8][32][TP]
   float* wsum = smf + 8 * 32 * TP;   // [8][32]
@@ -384,6 +398,8 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
 template <typename T>
 __global__ void k_rec_t_reduce(RecArgs R, const double* __restrict__ tbuf, T* __restrict__ out) {
   __shared__ double red[8][32];
+  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
+  out += (int64_t)blockIdx.y * R.N;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n = (int64_t)blockIdx.x * 32 + lane;
   double s = 0.0;
@@ -422,35 +438,35 @@ int launch_rec_state_init(Plan& P) {
 }
 
 template <typename T>
-int launch_rec_forward(Plan& P, const T* c, T* vrec) {
+int launch_rec_forward(Plan& P, const T* c, T* vrec, int64_t nb) {
   RecLayout& L = P.rec;
   RecArgs R = rec_args(P);
   if (L.H == 0) return GBDLT_OK;
   if constexpr (sizeof(T) == 4) {
-    k_rec_fwd_ff<<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, (const float*)c, L.part);
+    k_rec_fwd_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, (const float*)c, L.part);
   } else {
-    k_rec_fwd<T><<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, c, L.part);
+    k_rec_fwd<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, c, L.part);
   }
-  launched(P, "rec_fwd", 7.0 * (double)(P.p.rec_steps / 2),
-           (double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total);
+  launched(P, "rec_fwd", (double)nb * 7.0 * (double)(P.p.rec_steps / 2),
+           (double)nb * ((double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total));
   if (L.n_long > 0) {
     const int64_t threads = L.n_long * 32;
-    k_rec_fwd_reduce<T><<<(unsigned)((threads + 255) / 256), 256, 0, P.stream>>>(R, L.part, vrec, 0,
-                                                                                 L.n_long, 1);
+    k_rec_fwd_reduce<T><<<dim3((unsigned)((threads + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
+        R, L.part, vrec, 0, L.n_long, 1);
     launched(P, "rec_fwd_reduce", 0.0, 0.0);
   }
   if (L.H > L.n_long) {
     const int64_t rows = L.H - L.n_long;
-    k_rec_fwd_reduce<T><<<(unsigned)((rows + 255) / 256), 256, 0, P.stream>>>(R, L.part, vrec,
-                                                                              L.n_long, L.H, 0);
-    launched(P, "rec_fwd_reduce", 2.0 * (double)L.nseg_total,
-             16.0 * (double)L.nseg_total + (double)sizeof(T) * P.p.N);
+    k_rec_fwd_reduce<T><<<dim3((unsigned)((rows + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
+        R, L.part, vrec, L.n_long, L.H, 0);
+    launched(P, "rec_fwd_reduce", (double)nb * 2.0 * (double)L.nseg_total,
+             (double)nb * (16.0 * (double)L.nseg_total + (double)sizeof(T) * P.p.N));
   }
   return check_launch();
 }
 
 template <typename T>
-int launch_rec_transpose(Plan& P, const T* z, T* out) {
+int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb) {
   RecLayout& L = P.rec;
   RecArgs R = rec_args(P);
   if (L.H == 0) return GBDLT_OK;
@@ -461,24 +477,25 @@ int launch_rec_transpose(Plan& P, const T* z, T* out) {
       cudaFuncSetAttribute(k_rec_t_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr_set = true;
     }
-    k_rec_t_ff<<<(unsigned)L.ncta, RT, smem, P.stream>>>(R, (const float*)z, L.tbuf);
+    k_rec_t_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, (const float*)z, L.tbuf);
   } else {
     if (!attr_set) {
       cudaFuncSetAttribute(k_rec_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr_set = true;
     }
-    k_rec_t<T><<<(unsigned)L.ncta, RT, smem, P.stream>>>(R, z, L.tbuf);
+    k_rec_t<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, z, L.tbuf);
   }
-  launched(P, "rec_t", 7.0 * (double)(P.p.rec_steps / 2),
-           (double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total);
-  k_rec_t_reduce<T><<<(unsigned)((P.p.N + 31) / 32), 256, 0, P.stream>>>(R, L.tbuf, out);
-  launched(P, "rec_t_reduce", (double)L.tbuf_total, 8.0 * (double)L.tbuf_total + (double)sizeof(T) * P.p.N);
+  launched(P, "rec_t", (double)nb * 7.0 * (double)(P.p.rec_steps / 2),
+           (double)nb * ((double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total));
+  k_rec_t_reduce<T><<<dim3((unsigned)((P.p.N + 31) / 32), (unsigned)nb), 256, 0, P.stream>>>(R, L.tbuf, out);
+  launched(P, "rec_t_reduce", (double)nb * (double)L.tbuf_total,
+           (double)nb * (8.0 * (double)L.tbuf_total + (double)sizeof(T) * P.p.N));
   return check_launch();
 }
 
-template int launch_rec_forward<double>(Plan&, const double*, double*);
-template int launch_rec_forward<float>(Plan&, const float*, float*);
-template int launch_rec_transpose<double>(Plan&, const double*, double*);
-template int launch_rec_transpose<float>(Plan&, const float*, float*);
+template int launch_rec_forward<double>(Plan&, const double*, double*, int64_t);
+template int launch_rec_forward<float>(Plan&, const float*, float*, int64_t);
+template int launch_rec_transpose<double>(Plan&, const double*, double*, int64_t);
+template int launch_rec_transpose<float>(Plan&, const float*, float*, int64_t);
 
 }  // namespace gbdlt

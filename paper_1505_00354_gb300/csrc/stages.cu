@@ -89,6 +89,9 @@ __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, int64_
                           BandArgs B, const double* __restrict__ Cn, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  const int64_t bt = blockIdx.y;
+  c += bt * N;
+  U += bt * (int64_t)B.K * M * N;
   const T cn = (T)Cn[n] * c[n];
   const C2<T> e = twid<T>(tw4N, n);
   const T nn = (T)n;
@@ -108,6 +111,10 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const T* __restrict__ vre
                           int64_t N, int M, BandArgs B) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
+  const int64_t bt = blockIdx.y;
+  vrec += bt * N;
+  v += bt * N;
+  if (Y) Y += bt * (int64_t)B.K * M * N;
   T acc = vrec[k];
   const int s = band_of(B, k, N);
   if (s >= 0) {
@@ -136,6 +143,8 @@ template <typename T>
 __global__ void k_a4_pro(const T* __restrict__ v, C2<T>* __restrict__ U, int64_t N) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
+  v += (int64_t)blockIdx.y * N;
+  U += (int64_t)blockIdx.y * N;
   U[kp] = mk<T>(v[2 * kp], (T)0);
   U[N - 1 - kp] = mk<T>(v[2 * kp + 1], (T)0);
 }
@@ -144,6 +153,8 @@ template <typename T>
 __global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  F += (int64_t)blockIdx.y * N;
+  chat += (int64_t)blockIdx.y * N;
   const C2<T> Fn = F[n];
   const C2<T> Fm = F[(N - n) & (N - 1)];
   const C2<T> Vh = mk<T>((Fn.x + Fm.x) * (T)0.5, (Fn.y - Fm.y) * (T)0.5);
@@ -158,6 +169,8 @@ __global__ void k_fcs_pro(const T* __restrict__ a, C2<T>* __restrict__ U, int64_
                           TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  a += (int64_t)blockIdx.y * N;
+  U += (int64_t)blockIdx.y * N;
   T an = a[n];
   if (scale_d) an *= (n == 0 ? (T)1 : (T)2) / (T)N;
   const C2<T> e = twid<T>(tw4N, n);
@@ -168,6 +181,8 @@ template <typename T>
 __global__ void k_fcs_re_epi(const C2<T>* __restrict__ Y, T* __restrict__ out, int64_t N) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
+  Y += (int64_t)blockIdx.y * N;
+  out += (int64_t)blockIdx.y * N;
   const int64_t idx = (k & 1) ? N - 1 - (k >> 1) : (k >> 1);
   out[k] = Y[idx].x;
 }
@@ -180,6 +195,8 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int
                           int inc0, int npair, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  chat += (int64_t)blockIdx.y * N;
+  U += (int64_t)blockIdx.y * npair * N;
   const T r = (T)n / (T)N;
   const T rN = (T)(N - n) / (T)N;
   const T cn = chat[n];
@@ -216,6 +233,10 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const T* __restrict__ v, 
                           const double* __restrict__ tN, int64_t N, int L, int inc0, int npair) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
+  const int64_t bt = blockIdx.y;
+  Y += bt * npair * N;
+  f += bt * N;
+  if (v) v += bt * N;
   const T t = (T)tN[k];
   const bool odd = k & 1;
   const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
@@ -242,6 +263,8 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
                            int inc0, int npair) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
+  fin += (int64_t)blockIdx.y * N;
+  U += (int64_t)blockIdx.y * npair * N;
   const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
   T g0 = fin[k0], g1 = fin[k1];
   if (wscale) {
@@ -274,6 +297,10 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
                            int64_t N, int L, int inc0, int npair, int mode, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  const int64_t bt = blockIdx.y;
+  F += bt * npair * N;
+  if (Q) Q += bt * N;
+  if (uout) uout += bt * N;
   const T r = (T)n / (T)N;
   const C2<T> e = twid<T>(tw4N, n);
   const int64_t nm = (N - n) & (N - 1);
@@ -342,6 +369,11 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
                            C2<T>* __restrict__ U, int64_t N, int M, BandArgs B) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
+  const int64_t bt = blockIdx.y;
+  if (Y) Y += bt * N;
+  if (g) g += bt * N;
+  zout += bt * N;
+  U += bt * (int64_t)B.K * M * N;
   const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
   const T z0 = row_z<T>(Y, g, wscale, k0, N);
   const T z1 = row_z<T>(Y, g, wscale, k1, N);
@@ -371,6 +403,10 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ re
                            TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  const int64_t bt = blockIdx.y;
+  rect += bt * N;
+  out += bt * N;
+  if (F) F += bt * (int64_t)B.K * M * N;
   T acc = rect[n];
   if (B.K > 0 && M > 0) {
     const C2<T> e = twid<T>(tw4N, n);
@@ -403,6 +439,8 @@ __global__ void k_scale(const T* __restrict__ in, T* __restrict__ out, const dou
                         int64_t N, int which) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  in += (int64_t)blockIdx.y * N;
+  out += (int64_t)blockIdx.y * N;
   T v = in[n];
   if (which == 1) v *= ((T)n + (T)0.5);
   if (which == 2) v *= (T)w[n];
@@ -415,173 +453,173 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 }  // namespace
 
 template <typename T>
-int launch_l2c_pro(Plan& P, const T* c, C2<T>* U) {
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2c_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn, tw);
+  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "l2c_pro", 10.0 * P.p.M * N, ts * N + 8.0 * N + KM * N * cs);
+    launched(P, "l2c_pro", (double)nb * (10.0 * P.p.M * N), (double)nb * (ts * N + 8.0 * N + KM * N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v) {
-  k_l2c_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P));
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v, int64_t nb) {
+  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "l2c_epi", 10.0 * P.p.M * N, P.p.M * N * cs + 2.0 * ts * N);
+    launched(P, "l2c_epi", (double)nb * (10.0 * P.p.M * N), (double)nb * (P.p.M * N * cs + 2.0 * ts * N));
   }
   return check_launch();
 }
 template <typename T>
-int launch_a4_pro(Plan& P, const T* v, C2<T>* U) {
-  k_a4_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(v, U, P.p.N);
+int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb) {
+  k_a4_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(v, U, P.p.N);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "a4_pro", 0.0, ts * N + N * cs);
+    launched(P, "a4_pro", (double)nb * (0.0), (double)nb * (ts * N + N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_a4_epi(Plan& P, const C2<T>* F, T* chat) {
+int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_a4_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, chat, P.p.N, tw);
+  k_a4_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, chat, P.p.N, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "a4_epi", 12.0 * N, 2.0 * N * cs + ts * N);
+    launched(P, "a4_epi", (double)nb * (12.0 * N), (double)nb * (2.0 * N * cs + ts * N));
   }
   return check_launch();
 }
 template <typename T>
-int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d) {
+int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_fcs_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, tw);
+  k_fcs_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "fcs_pro", 8.0 * N, ts * N + N * cs);
+    launched(P, "fcs_pro", (double)nb * (8.0 * N), (double)nb * (ts * N + N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out) {
-  k_fcs_re_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, out, P.p.N);
+int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb) {
+  k_fcs_re_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, out, P.p.N);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "fcs_re_epi", 0.0, N * cs + ts * N);
+    launched(P, "fcs_re_epi", (double)nb * (0.0), (double)nb * (N * cs + ts * N));
   }
   return check_launch();
 }
 template <typename T>
-int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair) {
+int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_tay_pro<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(chat, U, P.p.N, P.p.L, inc0, npair, tw);
+  k_tay_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(chat, U, P.p.N, P.p.L, inc0, npair, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "tay_pro", 16.0 * npair * N, 2.0 * ts * N + npair * N * cs);
+    launched(P, "tay_pro", (double)nb * (16.0 * npair * N), (double)nb * (2.0 * ts * N + npair * N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair) {
-  k_tay_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(Y, v, f, P.tN, P.p.N, P.p.L, inc0, npair);
+int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair, int64_t nb) {
+  k_tay_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, v, f, P.tN, P.p.N, P.p.L, inc0, npair);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "tay_epi", (2.0 * P.p.L + 6.0 * npair) * N, npair * N * cs + 2.0 * ts * N + 8.0 * N);
+    launched(P, "tay_epi", (double)nb * ((2.0 * P.p.L + 6.0 * npair) * N), (double)nb * (npair * N * cs + 2.0 * ts * N + 8.0 * N));
   }
   return check_launch();
 }
 template <typename T>
-int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair) {
+int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair, int64_t nb) {
   const double* w = use_w ? P.w : nullptr;
-  k_tayt_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(f, w, P.tN, U, P.p.N, P.p.L, inc0, npair);
+  k_tayt_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(f, w, P.tN, U, P.p.N, P.p.L, inc0, npair);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "tayt_pro", 8.0 * npair * N, ts * N + 16.0 * N + npair * N * cs);
+    launched(P, "tayt_pro", (double)nb * (8.0 * npair * N), (double)nb * (ts * N + 16.0 * N + npair * N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair) {
+int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
   const int mode = Q ? 0 : 1;
-  k_tayt_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, mode, tw);
+  k_tayt_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, mode, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "tayt_epi", (2.0 * P.p.L + 16.0 * npair) * N, 2.0 * npair * N * cs + N * cs);
+    launched(P, "tayt_epi", (double)nb * ((2.0 * P.p.L + 16.0 * npair) * N), (double)nb * (2.0 * npair * N * cs + N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U) {
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, int64_t nb) {
   const double* w = use_w ? P.w : nullptr;
-  k_l2ct_pro<T><<<nblk(P.p.N / 2), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P));
+  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "l2ct_pro", 10.0 * P.p.M * N, N * cs + 2.0 * ts * N + 8.0 * N + KM * N * cs);
+    launched(P, "l2ct_pro", (double)nb * (10.0 * P.p.M * N), (double)nb * (N * cs + 2.0 * ts * N + 8.0 * N + KM * N * cs));
   }
   return check_launch();
 }
 template <typename T>
-int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s) {
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2ct_epi<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
+  k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
                                                      scale_s, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "l2ct_epi", 14.0 * KM * N, 2.0 * KM * N * cs + 2.0 * ts * N);
+    launched(P, "l2ct_epi", (double)nb * (14.0 * KM * N), (double)nb * (2.0 * KM * N * cs + 2.0 * ts * N));
   }
   return check_launch();
 }
 template <typename T>
-int launch_scale(Plan& P, const T* in, T* out, int which) {
-  k_scale<T><<<nblk(P.p.N), TPB, 0, P.stream>>>(in, out, P.w, P.p.N, which);
+int launch_scale(Plan& P, const T* in, T* out, int which, int64_t nb) {
+  k_scale<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(in, out, P.w, P.p.N, which);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "scale", N, 2.0 * ts * N + 8.0 * N);
+    launched(P, "scale", (double)nb * (N), (double)nb * (2.0 * ts * N + 8.0 * N));
   }
   return check_launch();
 }
 
 #define INST(T)                                                                              \
-  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*);                                   \
-  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const T*, T*);                         \
-  template int launch_a4_pro<T>(Plan&, const T*, C2<T>*);                                    \
-  template int launch_a4_epi<T>(Plan&, const C2<T>*, T*);                                    \
-  template int launch_fcs_pro<T>(Plan&, const T*, C2<T>*, int);                              \
-  template int launch_fcs_re_epi<T>(Plan&, const C2<T>*, T*);                                \
-  template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, int, int);                         \
-  template int launch_tay_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int);                   \
-  template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, int, int);                   \
-  template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int);                \
-  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*);           \
-  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const T*, T*, int);                   \
-  template int launch_scale<T>(Plan&, const T*, T*, int);
+  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*, int64_t);                                   \
+  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const T*, T*, int64_t);                         \
+  template int launch_a4_pro<T>(Plan&, const T*, C2<T>*, int64_t);                                    \
+  template int launch_a4_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                    \
+  template int launch_fcs_pro<T>(Plan&, const T*, C2<T>*, int, int64_t);                              \
+  template int launch_fcs_re_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                \
+  template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, int, int, int64_t);                         \
+  template int launch_tay_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int, int64_t);                   \
+  template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, int, int, int64_t);                   \
+  template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int, int64_t);                \
+  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, int64_t);           \
+  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int64_t);                   \
+  template int launch_scale<T>(Plan&, const T*, T*, int, int64_t);
 INST(double)
 INST(float)
 #undef INST

@@ -1,0 +1,102 @@
+"""Batched transforms: same-N batches through one plan, and uneven batches
+(many lengths, both directions) through gbdlt_batch_* (one CUDA-graph replay).
+
+Uneven workload: 4096 transforms, N_i = 2^round(U(4, 13)) (log-uniform lengths
+16 .. 8192 rounded to the power of two the fast path needs), directions 50/50,
+c ~ N(0,1) (n+1)^-1 (seed 40).  Every transform is compared with the same
+transform through a single-vector call, and a seeded sample with the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_00354_gb300 import build
+    build.build()
+    import paper_1505_00354_gb300 as g
+    return g
+
+
+def uneven_workload(B=4096, seed=40):
+    from paper_1505_00354_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    Ns = (2 ** np.round(rng.uniform(4, 13, B))).astype(np.int64)
+    dirs = rng.integers(0, 2, B).astype(np.int32)
+    x = np.concatenate([inputs.coeffs(int(N), seed * 100000 + i, 1.0) for i, N in enumerate(Ns)])
+    return Ns, dirs, x
+
+
+@pytest.mark.parametrize("N", [16, 256, 4096, 8192])
+def test_same_n_batch_bitwise(gb, N):
+    from paper_1505_00354_gb300 import inputs
+    p = gb.Plan(N)
+    C = torch.tensor(np.stack([inputs.coeffs(N, 900 + i, 1.0) for i in range(33)]), device="cuda")
+    for op in ("dlt", "idlt", "dlt_t", "leg2cheb", "chebeval_t"):
+        full = getattr(p, op)(C)
+        for i in (0, 7, 32):
+            assert torch.equal(full[i], getattr(p, op)(C[i].clone())), (op, i)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uneven_batch(gb, prec):
+    import oracle
+    Ns, dirs, x = uneven_workload()
+    dt = torch.float64 if prec == 0 else torch.float32
+    b = gb.Batch(Ns, dirs, prec)
+    info = b.info()
+    assert info["groups"] == len(set(zip(Ns.tolist(), dirs.tolist())))
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    y = b.run(xd)
+    y2 = b.run(xd)
+    assert torch.equal(y, y2)  # replays are deterministic
+    off = b.offsets
+    # every transform against the single-vector call
+    for N in sorted(set(Ns.tolist())):
+        p = gb.get_plan(int(N), prec)
+        for d in (0, 1):
+            idx = np.nonzero((Ns == N) & (dirs == d))[0]
+            if idx.size == 0:
+                continue
+            X = torch.stack([xd[off[i]:off[i + 1]] for i in idx])
+            Y = p.dlt(X) if d == 0 else p.idlt(X)
+            got = torch.stack([y[off[i]:off[i + 1]] for i in idx])
+            assert torch.equal(got, Y), (N, d)
+    # a seeded sample against the oracle
+    rng = np.random.default_rng(41)
+    worst = 0.0
+    for i in rng.choice(len(Ns), 24, replace=False):
+        N = int(Ns[i])
+        xi = xd[off[i]:off[i + 1]].double().cpu().numpy()
+        yi = y[off[i]:off[i + 1]].double().cpu().numpy()
+        nd = oracle.legpts(N)
+        if dirs[i] == 0:
+            err = np.max(np.abs(yi - oracle.dlt_rows(xi, nd))) / np.abs(xi).sum()
+        else:
+            ref = oracle.idlt(xi, nd)
+            err = np.max(np.abs(yi - ref) / ((np.arange(N) + 0.5) * np.abs(nd.w * xi).sum()))
+        worst = max(worst, err)
+    print(f"prec={prec} uneven batch: {info}, worst sampled error {worst:.2e}")
+    assert worst <= (1e-12 if prec == 0 else 5e-6)
+
+
+def test_batch_errors(gb):
+    import ctypes
+    L = gb.lib()
+    h = ctypes.c_void_p()
+    Ns = (ctypes.c_int64 * 2)(16, 24)
+    dirs = (ctypes.c_int32 * 2)(0, 1)
+    assert L.gbdlt_batch_create(Ns, dirs, 2, 0, 0.0, ctypes.byref(h)) == -2
+    Ns = (ctypes.c_int64 * 2)(16, 32)
+    bad = (ctypes.c_int32 * 2)(0, 2)
+    assert L.gbdlt_batch_create(Ns, bad, 2, 0, 0.0, ctypes.byref(h)) == -1
+    assert L.gbdlt_batch_create(Ns, dirs, 0, 0, 0.0, ctypes.byref(h)) == -1
+    assert L.gbdlt_batch_exec(None, None, None, None) == -1
