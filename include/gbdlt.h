@@ -42,8 +42,10 @@ extern "C" {
 typedef struct gbdlt_plan_s* gbdlt_plan;
 
 /* Arithmetic form.  GBDLT_FP64: every transform step in double.  GBDLT_FP32:
- * DCT/DST transforms, asymptotic and Taylor combines in float (nodes, weights,
- * delta-theta and the recurrence region stay in double); float data in/out. */
+ * DCT/DST transforms, asymptotic and Taylor combines in float; the recurrence
+ * region in float-float (compensated float, ~2^-44 per operation) with
+ * compensated sums; nodes, weights and delta-theta are computed in double.
+ * Float data in/out. */
 enum { GBDLT_FP64 = 0, GBDLT_FP32 = 1 };
 
 enum {

@@ -42,6 +42,13 @@ struct PD {
   double p, dp;
 };
 
+// h_{m,N} of the expansion for m < kMaxTerms; the same for every node of a plan,
+// so the host computes them once per launch
+constexpr int kMaxTerms = 40;
+struct HTab {
+  double h[kMaxTerms];
+};
+
 __device__ PD eval_rec(int64_t N, double s, double c, double sh) {
   // s = sin(theta), c = cos(theta), sh = sin(theta/2)
   double xm1 = -2.0 * sh * sh;
@@ -58,7 +65,7 @@ __device__ PD eval_rec(int64_t N, double s, double c, double sh) {
   return r;
 }
 
-__device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, double CN) {
+__device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, double CN, const HTab& H) {
   const double eps = ((double)N + 0.5) * d;
   const double e2 = eps * eps;
   // sin/cos of |eps| <= 0.06 by Taylor polynomials (error < 1e-19)
@@ -71,18 +78,16 @@ __device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, doubl
   const double cot = c / s;
   const double sg0 = sqrt(g);
   double gm = sg0;  // g^{m+1/2}
-  double h = 1.0;
   double P = 0.0, dP = 0.0;
-  for (int m = 0; m < 40; ++m) {
-    double term = h * gm;
+  for (int m = 0; m < kMaxTerms - 1; ++m) {
+    const double term = H.h[m] * gm;
     P += term * cr;
     dP += term * (-((double)N + m + 0.5) * ci - (m + 0.5) * cot * cr);
-    h *= (m + 0.5) * (m + 0.5) / ((m + 1.0) * ((double)N + m + 1.5));
     gm *= g;
-    double ncr = cr * rr - ci * ri;
+    const double ncr = cr * rr - ci * ri;
     ci = cr * ri + ci * rr;
     cr = ncr;
-    if (h * gm < 1e-18 * sg0) break;
+    if (H.h[m + 1] * gm < 1e-18 * sg0) break;
   }
   PD r;
   r.p = CN * P;
@@ -111,7 +116,7 @@ __device__ PD eval_series(int64_t N, double s, double c, double sh, double ch) {
   return r;
 }
 
-__global__ void k_legpts(int64_t N, double CN, double* __restrict__ theta, double* __restrict__ x,
+__global__ void k_legpts(int64_t N, double CN, HTab H, double* __restrict__ theta, double* __restrict__ x,
                          double* __restrict__ w, double* __restrict__ tN, int* __restrict__ status) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t half = (N + 1) / 2;
@@ -133,8 +138,8 @@ __global__ void k_legpts(int64_t N, double CN, double* __restrict__ theta, doubl
   double d = mode == 1 ? (c0 / s0) / (8.0 * Nh * ((double)N + 1.5)) : 0.0;
   bool ok = false;
   PD r;
-  double s = s0, c = c0, sh = 0, ch = 0;
-  for (int it = 0; it < 2 * 12 + 1; ++it) {
+  double s = s0, c = c0, sh = 0, ch = 0, dp_final = 0.0;
+  for (int it = 0; it < 24; ++it) {
     // sin/cos of theta = th0 + d by the angle-addition formula; |d| <= 1/(3 pi (2N+1))
     // (Lemma 2.3), so the Taylor polynomials below are exact to < 1e-20
     const double d2 = d * d;
@@ -151,25 +156,29 @@ __global__ void k_legpts(int64_t N, double CN, double* __restrict__ theta, doubl
     if (mode == 0)
       r = eval_rec(N, s, c, sh);
     else if (mode == 1)
-      r = eval_asy(N, k, d, s, c, CN);
+      r = eval_asy(N, k, d, s, c, CN, H);
     else
       r = eval_series(N, s, c, sh, ch);
-    if (ok) break;  // this evaluation was at the converged point
-    double step = r.p / r.dp;
+    const double step = r.p / r.dp;
     d -= step;
     if (!(fabs(d) < 1.0)) break;  // diverged (NaN or runaway)
-    if (fabs(step) <= 1e-11 / (double)N) ok = true;
+    if (fabs(step) <= 1e-11 / (double)N) {
+      // dP/dtheta at the updated point by one Taylor step, with the second
+      // derivative from Legendre's equation in theta:
+      //   P'' = -cot(theta) P' - N(N+1) P   (step^2 N^3 is below 1e-20 here)
+      dp_final = r.dp + step * ((c / s) * r.dp + (double)N * ((double)N + 1.0) * r.p);
+      // cos/sin at the updated point (theta decreased by step)
+      const double cn = c + s * step;
+      s = s - c * step;
+      c = cn;
+      ok = true;
+      break;
+    }
   }
   if (!ok) atomicOr(status, 1);
   const double th = th0 + d;
-  const double wk = 2.0 / (r.dp * r.dp);
-  double xk;
-  if (th < 1.0) {
-    double shh = sin(0.5 * th);
-    xk = 1.0 - 2.0 * shh * shh;
-  } else {
-    xk = c;
-  }
+  const double wk = 2.0 / (dp_final * dp_final);
+  const double xk = c;
   const double tk = kPi * (double)(N - 2 * k - 1) / (4.0 * Nh) + (double)N * d;
   theta[k] = th;
   x[k] = xk;
@@ -189,6 +198,15 @@ __global__ void k_dtheta(const double* __restrict__ tN, double* __restrict__ out
   if (k < N) out[k] = tN[k] / (double)N;  // exact: N is a power of two
 }
 
+// h_{0,N} = 1, h_{m+1,N} = h_{m,N} (m+1/2)^2 / ((m+1)(N+m+3/2))
+HTab htab(int64_t N) {
+  HTab H;
+  H.h[0] = 1.0;
+  for (int m = 0; m + 1 < kMaxTerms; ++m)
+    H.h[m + 1] = H.h[m] * (m + 0.5) * (m + 0.5) / ((m + 1.0) * ((double)N + m + 1.5));
+  return H;
+}
+
 }  // namespace
 
 int launch_dtheta(Plan& P, double* out) {
@@ -203,7 +221,7 @@ int launch_legpts(Plan& P, double CN) {
   const int64_t half = (N + 1) / 2;
   const int threads = 128;
   const int64_t blocks = (half + threads - 1) / threads;
-  k_legpts<<<(unsigned)blocks, threads, 0, P.stream>>>(N, CN, P.theta, P.x, P.w, P.tN, P.status);
+  k_legpts<<<(unsigned)blocks, threads, 0, P.stream>>>(N, CN, htab(N), P.theta, P.x, P.w, P.tN, P.status);
   launched(P, "legpts", 0.0, 32.0 * N);
   return check_launch();
 }
@@ -305,7 +323,7 @@ extern "C" int gbdlt_legpts_noalloc(int64_t N, double* x, double* theta, double*
   const int64_t half = (N + 1) / 2;
   const int threads = 128;
   k_legpts<<<(unsigned)((half + threads - 1) / threads), threads, 0, stream>>>(
-      N, cn_running(N), theta, x, w, tN, status);
+      N, cn_running(N), htab(N), theta, x, w, tN, status);
   count_launch();
   if (dtheta) {
     k_dtheta<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(tN, dtheta, N);

@@ -237,19 +237,18 @@ int derive_params(int64_t N, int prec, double eps, Params* p) {
   while ((1ll << lg) < N) ++lg;
   if (N >= 4) {
     const double eps_asy = eps / 20.0;
-    const double fft_ops = (4.25 * lg + 30.0) * (double)N;
+    // costs in picoseconds of GB300 time, fitted to the measured kernels at
+    // N = 2^20: one FFT vector of the pipeline (forward and transposed chain)
+    // per point, and one recurrence step of a half row (both directions averaged)
     double c_fft, c_rec;
     int Mmax;
     if (prec == GBDLT_FP64) {
-      c_fft = fft_ops;
-      c_rec = 5.5;
+      c_fft = (5.7 * lg + 21.0) * (double)N;  // ~85 FP64 instructions per point at 2^20
+      c_rec = 10.5;                           // ~6.6 FP64 instructions per step
       Mmax = 24;
     } else {
-      // FP32 transforms are bound by memory traffic (~48 bytes per point per
-      // FFT of the pipeline, ~5 FP32 ops per byte of HBM); the recurrence is FP64
-      // (58 FP32 ops per FP64 op on this part)
-      c_fft = std::max(fft_ops, 240.0 * (double)N);
-      c_rec = 5.5 * 58.0;
+      c_fft = (0.6 * lg + 2.3) * (double)N;   // memory and shared-memory bound FP32 passes
+      c_rec = 4.9;                            // float-float recurrence
       Mmax = 16;
     }
     double best = (double)N * c_rec * (double)(N / 2);  // all recurrence

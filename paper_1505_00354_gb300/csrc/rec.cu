@@ -14,7 +14,11 @@
 // Each half row's column range is cut into segments of S = 512 columns; the
 // state (P, D) at every segment start depends only on N, so the plan computes it
 // once (two basis solutions per segment, then a scan per row) and the transforms
-// run every segment independently.  The FP64 form runs the recurrence in FP64;
+// run every segment independently.  The FP64 kernels carry G_n = D_n / (x - 1)
+// instead of D_n, which takes one FP64 instruction less per step (FP64 issue is
+// what bounds them on GB300) with the same roundings:
+//   G_{n+1} = (2n+1)/(n+1) P_n + n/(n+1) G_n,   P_{n+1} = P_n + (x-1) G_{n+1}
+// (one multiply and two fused multiply-adds).  The FP64 form runs the recurrence in FP64;
 // the FP32 form runs it in float-float (compensated FP32, ~2^-44 per operation)
 // on the FP32 pipe, which is 58 times faster than the FP64 pipe on GB300.
 #include "gbdlt_internal.cuh"
@@ -169,21 +173,19 @@ __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__
   if (j >= (cut + R.S - 1) / R.S) return;
   const int64_t o = R.poff[k] + j;
   const double2 st = R.state[o];
-  double P = st.x, D = st.y;
   const double xm1 = xm1_of(k, R.N);
+  double P = st.x, G = st.y / xm1;
   const int64_t n0 = (int64_t)j * R.S;
   const int64_t n1 = min(n0 + R.S, (int64_t)cut);
   double E = 0.0, O = 0.0;
   int64_t n = n0;
   for (; n + 1 < n1; n += 2) {
     E = fma((double)c[n], P, E);
-    double t = R.ra[n] * xm1;
-    D = fma(t, P, R.rb[n] * D);
-    P += D;
+    G = fma(R.ra[n], P, R.rb[n] * G);
+    P = fma(xm1, G, P);
     O = fma((double)c[n + 1], P, O);
-    t = R.ra[n + 1] * xm1;
-    D = fma(t, P, R.rb[n + 1] * D);
-    P += D;
+    G = fma(R.ra[n + 1], P, R.rb[n + 1] * G);
+    P = fma(xm1, G, P);
   }
   if (n < n1) E = fma((double)c[n], P, E);
   part[o] = make_double2(E, O);
@@ -263,10 +265,17 @@ __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T*
 }
 
 // transposed: out_n = sum_k z_k P_n(x_k) over rows with n < cut(k).  A CTA takes
-// 256 half rows x one segment; every 32 columns each lane writes its 32 products
-// into a per-warp tile, the tile is summed by columns (shared-memory transpose),
-// and the 8 warp sums are added into the row block's partial array.
-constexpr int TP = 33;  // tile pitch (doubles)
+// 256 half rows x one segment of S = 512 columns.  Every 32 columns each lane
+// writes its 32 values P_n(x_k) (0 past its cut) into its warp's tile; then lane
+// i forms the dot product of tile column i with the warp's 32 row weights (a
+// shared-memory transpose; the weight product rides in the fused multiply-add
+// of the sum) into the warp's partial for that column.  Only warp-level
+// synchronisation is needed until the end of the segment, where the 8 warp
+// partials of each column are added into the row block's partial array.  Row
+// weights: z_k + z_{N-1-k} for even n, z_k - z_{N-1-k} for odd n, by
+// P_n(-x) = (-1)^n P_n(x); segments start at multiples of 32, so the parity of
+// lane i's column is that of i.
+constexpr int TP = 33;  // tile pitch
 
 template <typename T>
 __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z,
@@ -275,14 +284,15 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
   tbuf += (int64_t)blockIdx.y * R.tbuf_total;
   extern __shared__ double sm[];
   double* tile = sm;                  // [8][32][TP]
-  double* wsum = sm + 8 * 32 * TP;    // [8][32]
+  double* wsum = sm + 8 * 32 * TP;    // [8][S] per-warp column partials
+  double2* zt = reinterpret_cast<double2*>(wsum + 8 * R.S);  // [8][32] (z+, z-)
   const int64_t rbk = R.cta_rb[blockIdx.x];
   const int j = R.cta_j[blockIdx.x];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = rbk * RT + threadIdx.x;
   bool active = k < R.H;
   int cut = 0;
-  double zp = 0.0, zm = 0.0, P = 0.0, D = 0.0, xm1 = 0.0;
+  double zp = 0.0, zm = 0.0, P = 0.0, G = 0.0, xm1 = 0.0;
   if (active) {
     cut = R.cut[k];
     active = j < (cut + R.S - 1) / R.S;
@@ -292,42 +302,43 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
     zp = a + b;
     zm = a - b;
     const double2 st = R.state[R.poff[k] + j];
-    P = st.x;
-    D = st.y;
     xm1 = xm1_of(k, R.N);
+    P = st.x;
+    G = st.y / xm1;
   } else {
     cut = 0;
   }
+  zt[threadIdx.x] = make_double2(zp, zm);
   const int64_t n0s = (int64_t)j * R.S;
   const int64_t seg_end = min(n0s + R.S, (int64_t)R.maxcut[rbk]);
   double* mytile = tile + (w * 32 + lane) * TP;
+  double* mysum = wsum + w * R.S;
+  const double* zw = reinterpret_cast<const double*>(zt + w * 32) + (lane & 1);
   for (int64_t n0 = n0s; n0 < seg_end; n0 += 32) {
 #pragma unroll 4
     for (int i = 0; i < 32; ++i) {
       const int64_t n = n0 + i;
       double val = 0.0;
       if (n < cut) {
-        val = ((n & 1) ? zm : zp) * P;
-        const double t = R.ra[n] * xm1;
-        D = fma(t, P, R.rb[n] * D);
-        P += D;
+        val = P;
+        G = fma(R.ra[n], P, R.rb[n] * G);
+        P = fma(xm1, G, P);
       }
       mytile[i] = val;
     }
     __syncwarp();
     double colsum = 0.0;
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) colsum += tile[(w * 32 + r) * TP + lane];
-    wsum[w * 32 + lane] = colsum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double s = 0.0;
+    for (int r = 0; r < 32; ++r) colsum = fma(zw[2 * r], tile[(w * 32 + r) * TP + lane], colsum);
+    mysum[(n0 - n0s) + lane] = colsum;
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < seg_end - n0s; c += RT) {
+    double s = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += wsum[q * 32 + threadIdx.x];
-      const int64_t n = n0 + threadIdx.x;
-      if (n < seg_end) tbuf[R.toff[rbk] + n] = s;
-    }
-    __syncthreads();
+    for (int q = 0; q < 8; ++q) s += wsum[q * R.S + c];
+    tbuf[R.toff[rbk] + n0s + c] = s;
   }
 }
 
@@ -339,7 +350,7 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
   tbuf += (int64_t)blockIdx.y * R.tbuf_total;
   extern __shared__ float smf[];
   float* tile = smf;                 // [8][32][TP]
-  float* wsum = smf + 8 * 32 * TP;   // [8][32]
+  float* wsum = smf + 8 * 32 * TP;   // [8][S]
   const int64_t rbk = R.cta_rb[blockIdx.x];
   const int j = R.cta_j[blockIdx.x];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -366,6 +377,7 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
   const int64_t n0s = (int64_t)j * R.S;
   const int64_t seg_end = min(n0s + R.S, (int64_t)R.maxcut[rbk]);
   float* mytile = tile + (w * 32 + lane) * TP;
+  float* mysum = wsum + w * R.S;
   for (int64_t n0 = n0s; n0 < seg_end; n0 += 32) {
 #pragma unroll 4
     for (int i = 0; i < 32; ++i) {
@@ -382,16 +394,15 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
     float colsum = 0.f;
 #pragma unroll 8
     for (int r = 0; r < 32; ++r) colsum += tile[(w * 32 + r) * TP + lane];
-    wsum[w * 32 + lane] = colsum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double s = 0.0;
+    mysum[(n0 - n0s) + lane] = colsum;
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < seg_end - n0s; c += RT) {
+    double s = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += (double)wsum[q * 32 + threadIdx.x];
-      const int64_t n = n0 + threadIdx.x;
-      if (n < seg_end) tbuf[R.toff[rbk] + n] = s;
-    }
-    __syncthreads();
+    for (int q = 0; q < 8; ++q) s += (double)wsum[q * R.S + c];
+    tbuf[R.toff[rbk] + n0s + c] = s;
   }
 }
 
@@ -470,7 +481,7 @@ int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb) {
   RecLayout& L = P.rec;
   RecArgs R = rec_args(P);
   if (L.H == 0) return GBDLT_OK;
-  const size_t smem = sizeof(T) * (8 * 32 * TP + 8 * 32);
+  const size_t smem = sizeof(T) * (8 * 32 * TP + 8 * (size_t)L.S) + (sizeof(T) == 8 ? 16 * RT : 0);
   static bool attr_set = false;
   if constexpr (sizeof(T) == 4) {
     if (!attr_set) {
