@@ -54,19 +54,22 @@ HBM_FALLBACK_GBS = 6800.0
 # dram__bytes_write.sum) and the hash of the kernel sources it was taken with;
 # a traffic figure is reported only while the sources are unchanged.
 TRAFFIC = {
-    # profiles/k_fft_cols_fp64_N2p20.md: one launch of 36 vectors of 2^20 complex
-    # doubles moved 604.1 MB + 548.4 MB against 1208 MB algorithmic
-    "fft_cols": {"dram_per_algorithmic_byte": (604.142336 + 548.403968) / 1207.959552,
-                 "src": "b6cda88a97851d8c"},
+    # profiles/k_fft_fp64_N2p20.md: one launch of 48 vectors of 2^20 complex
+    # doubles (the leg2cheb band FFTs) moved these DRAM bytes against
+    # 2 x 48 x 2^20 x 16 B = 1610.6 MB algorithmic; valid while the sources
+    # the kernel is built from hash to "src"
+    "fft_cols": {"dram_per_algorithmic_byte": (805.594624 + 750.065920) / 1610.612736,
+                 "files": ("fft.cu", "gbdlt_internal.cuh"), "src": "5a0de5543c39cdfc"},
+    "fft_rows": {"dram_per_algorithmic_byte": (805.710336 + 758.273792) / 1610.612736,
+                 "files": ("fft.cu", "gbdlt_internal.cuh"), "src": "5a0de5543c39cdfc"},
 }
 
 
-def src_hash() -> str:
+def src_hash(files) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1505_00354_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, name), "rb").read())
+    for name in files:
+        h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -342,7 +345,7 @@ def run_gpu(args, world, rank, local):
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
         tr = TRAFFIC.get(name)
         traffic = None
-        if tr and tr.get("src") == src_hash():
+        if tr and tr.get("src") == src_hash(tr["files"]):
             # the capture's DRAM/algorithmic ratio applied to this kernel's
             # average algorithmic bytes per launch in the timed region
             traffic = round(tr["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"], 1)
