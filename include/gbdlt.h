@@ -51,12 +51,22 @@ enum { GBDLT_FP64 = 0, GBDLT_FP32 = 1 };
 enum {
   GBDLT_OK = 0,
   GBDLT_ERR_INVALID_ARG = -1,    /* null pointer, batch < 0, bad precision, ... */
-  GBDLT_ERR_UNSUPPORTED_N = -2,  /* N not a power of two or out of range      */
+  GBDLT_ERR_UNSUPPORTED_N = -2,  /* N out of range for the method asked for    */
   GBDLT_ERR_CUDA = -3,           /* a CUDA runtime call failed                */
   GBDLT_ERR_OOM = -4,            /* device allocation failed                  */
   GBDLT_ERR_NOT_CONVERGED = -5,  /* a node Newton iteration did not settle    */
   GBDLT_ERR_UNIMPLEMENTED = -6
 };
+
+/* How a plan computes gbdlt_dlt, gbdlt_idlt and their transposes.
+ * GBDLT_METHOD_FAST: the FFT-based chain of Sec. 2-4 (N a power of two).
+ * GBDLT_METHOD_DIRECT: the O(N^2) sums of Eq. (1) and (2) evaluated by the
+ *   three-term recurrence at the Legendre nodes (any N <= 65536); the direct
+ *   approach the paper compares against, and faster on GB300 for small N.
+ * GBDLT_METHOD_AUTO: DIRECT when N is not a power of two or N <= 256, FAST
+ *   otherwise.  leg2cheb and chebeval always run the FFT-based chain and need
+ *   N to be a power of two. */
+enum { GBDLT_METHOD_AUTO = 0, GBDLT_METHOD_FAST = 1, GBDLT_METHOD_DIRECT = 2 };
 
 /* Parameters the plan derives from (N, precision, eps) by the error bounds of
  * the paper (Table 1 / Corollary 2.4 for L) and of the asymptotic expansion of
@@ -78,18 +88,26 @@ typedef struct {
   double bytes_dlt;    /* algorithmic HBM bytes per DLT: read c, dtheta; write f */
   double bytes_idlt;   /* same for the IDLT (adds the weights)                */
   size_t workspace_bytes; /* device workspace the plan allocates              */
+  int method;          /* GBDLT_METHOD_FAST or GBDLT_METHOD_DIRECT (resolved)  */
+  int64_t direct_steps; /* half-row recurrence steps of one direct transform   */
 } gbdlt_params;
 
 /* Host-only parameter derivation: no GPU, no allocation.  eps <= 0 selects the
  * default (1e-14 for GBDLT_FP64, 2e-6 for GBDLT_FP32).  Returns
  * GBDLT_ERR_UNSUPPORTED_N or GBDLT_ERR_INVALID_ARG on bad input. */
 int gbdlt_plan_params(int64_t N, int prec, double eps, gbdlt_params* out);
+/* The same for a given method (GBDLT_METHOD_*); GBDLT_ERR_UNSUPPORTED_N if N
+ * does not suit it (FAST: not a power of two; DIRECT: N > 65536). */
+int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out);
 
 /* Create a plan on the current CUDA device.  `cuda_stream` is a cudaStream_t
  * (NULL = legacy default stream).  Computes the Legendre nodes and weights
  * (gbdlt_legpts), the per-N tables and allocates the workspace.  On error *out
  * is set to NULL and nothing is leaked. */
 int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_plan* out);
+/* gbdlt_plan_create with the method given (GBDLT_METHOD_AUTO is what
+ * gbdlt_plan_create uses). */
+int gbdlt_plan_create_ex(int64_t N, int prec, double eps, int method, void* cuda_stream, gbdlt_plan* out);
 int gbdlt_plan_destroy(gbdlt_plan plan);
 /* Change the stream later calls enqueue on. */
 int gbdlt_plan_set_stream(gbdlt_plan plan, void* cuda_stream);
@@ -145,21 +163,36 @@ int gbdlt_idlt(gbdlt_plan plan, const void* f, void* c, int64_t batch);
 int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
 
 /* Uneven batches (no counterpart in the paper, which transforms one vector at
- * a time): B transforms of lengths Ns_host[i] (powers of two, 1..2^24) and
- * directions dirs_host[i] (0 = DLT, 1 = IDLT), all of one precision, executed
- * together.  Inputs and outputs are concatenated in the given order: transform
- * i occupies elements [sum_{j<i} Ns[j], sum_{j<=i} Ns[j]) of `in` and `out`
- * (device, element type of `prec`).  Creation groups the transforms by
- * (N, direction), makes one plan per distinct N sized for its largest group,
- * allocates grouped staging buffers and captures every group's batched chain
- * into one CUDA graph (1 <= B <= 65535).  An execution makes the work wait for
- * `cuda_stream`, gathers `in` into the staging buffers, replays the graph,
- * scatters the results into `out` and makes `cuda_stream` wait for them; it
- * allocates nothing.  Executions of one batch object must not overlap. */
+ * a time): B transforms of lengths Ns_host[i] (1..2^24; lengths that are not
+ * powers of two up to 65536, by the direct method) and directions dirs_host[i]
+ * (0 = DLT, 1 = IDLT), all of one precision, executed together.  Inputs and
+ * outputs are concatenated in the given order: transform i occupies elements
+ * [sum_{j<i} Ns[j], sum_{j<=i} Ns[j]) of `in` and `out` (device, element type
+ * of `prec`).  Creation groups the transforms by (N, direction), makes one plan
+ * per group sized for the whole group, spreads the groups over up to 8 internal
+ * streams, picks each group's method and captures every group's batched chain
+ * into one CUDA graph with one branch per stream (1 <= B <= 65535).  With
+ * GBDLT_METHOD_AUTO the method of a group that allows both is chosen by timing
+ * both on the device at creation (the autotuner; see gbdlt_batch_group_info),
+ * so two batch objects over the same lengths may choose differently; FAST or
+ * DIRECT force one method (GBDLT_ERR_UNSUPPORTED_N where a length does not suit
+ * it).  An execution makes the work wait for `cuda_stream`, gathers `in` into
+ * the staging buffers, replays the graph, scatters the results into `out` and
+ * makes `cuda_stream` wait for them; it allocates nothing.  Executions of one
+ * batch object must not overlap.  gbdlt_batch_create = gbdlt_batch_create_ex
+ * with GBDLT_METHOD_AUTO. */
 typedef struct gbdlt_batch_s* gbdlt_batch;
 int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
                        double eps, gbdlt_batch* out);
+int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
+                          double eps, int method, gbdlt_batch* out);
 int gbdlt_batch_exec(gbdlt_batch batch, const void* in, void* out, void* cuda_stream);
+/* Group g (0 <= g < groups, in staging order): its length, direction, number of
+ * transforms, the method it runs, and the autotuner's milliseconds per run of
+ * the whole group by each method (-1 where that method was not timed).  Any
+ * output pointer may be NULL. */
+int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
+                           int32_t* method, double* ms_fast, double* ms_direct);
 /* total elements of the concatenated layout, number of (N, direction) groups,
  * kernel nodes in the captured graph (any pointer may be NULL) */
 int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int64_t* groups,

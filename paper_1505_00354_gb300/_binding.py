@@ -14,6 +14,9 @@ import torch
 
 FP64 = 0
 FP32 = 1
+METHOD_AUTO = 0
+METHOD_FAST = 1
+METHOD_DIRECT = 2
 MAX_BANDS = 32
 
 STATUS = {
@@ -55,6 +58,8 @@ class Params(ctypes.Structure):
         ("bytes_dlt", ctypes.c_double),
         ("bytes_idlt", ctypes.c_double),
         ("workspace_bytes", ctypes.c_size_t),
+        ("method", ctypes.c_int),
+        ("direct_steps", ctypes.c_int64),
     ]
 
     def to_dict(self) -> dict:
@@ -64,16 +69,19 @@ class Params(ctypes.Structure):
             "bands": [(self.band_ns[i], self.band_ka[i], self.band_kb[i]) for i in range(K)],
             "rec_steps": self.rec_steps, "seg_len": self.seg_len, "flops_dlt": self.flops_dlt,
             "bytes_dlt": self.bytes_dlt, "bytes_idlt": self.bytes_idlt,
-            "workspace_bytes": self.workspace_bytes,
+            "workspace_bytes": self.workspace_bytes, "method": self.method,
+            "direct_steps": self.direct_steps,
         }
 
 
 ENTRY_POINTS = (
-    "gbdlt_plan_params", "gbdlt_plan_create", "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
+    "gbdlt_plan_params", "gbdlt_plan_params_ex", "gbdlt_plan_create", "gbdlt_plan_create_ex",
+    "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
     "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
-    "gbdlt_batch_create", "gbdlt_batch_exec", "gbdlt_batch_info", "gbdlt_batch_destroy",
+    "gbdlt_batch_create", "gbdlt_batch_create_ex", "gbdlt_batch_exec", "gbdlt_batch_info",
+    "gbdlt_batch_group_info", "gbdlt_batch_destroy",
     "gbdlt_status_string", "gbdlt_launch_count",
 )
 
@@ -91,7 +99,9 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.gbdlt_plan_params.argtypes = [i64, i32, dbl, ctypes.POINTER(Params)]
+        L.gbdlt_plan_params_ex.argtypes = [i64, i32, dbl, i32, ctypes.POINTER(Params)]
         L.gbdlt_plan_create.argtypes = [i64, i32, dbl, vp, ctypes.POINTER(vp)]
+        L.gbdlt_plan_create_ex.argtypes = [i64, i32, dbl, i32, vp, ctypes.POINTER(vp)]
         L.gbdlt_plan_destroy.argtypes = [vp]
         L.gbdlt_plan_set_stream.argtypes = [vp, vp]
         L.gbdlt_plan_sync.argtypes = [vp]
@@ -103,6 +113,11 @@ def lib():
             getattr(L, name).argtypes = [vp, vp, vp, i64]
         L.gbdlt_batch_create.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                          i64, i32, dbl, ctypes.POINTER(vp)]
+        L.gbdlt_batch_create_ex.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                            i64, i32, dbl, i32, ctypes.POINTER(vp)]
+        L.gbdlt_batch_group_info.argtypes = [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
         L.gbdlt_batch_exec.argtypes = [vp, vp, vp, vp]
         L.gbdlt_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.gbdlt_batch_destroy.argtypes = [vp]
@@ -124,10 +139,10 @@ def _check(status: int, where: str):
         raise GbdltError(status, where)
 
 
-def plan_params(N: int, prec: int = FP64, eps: float = 0.0) -> dict:
-    """Parameters the library derives for (N, prec, eps); host only, no GPU."""
+def plan_params(N: int, prec: int = FP64, eps: float = 0.0, method: int = METHOD_AUTO) -> dict:
+    """Parameters the library derives for (N, prec, eps, method); host only, no GPU."""
     p = Params()
-    _check(lib().gbdlt_plan_params(N, prec, eps, ctypes.byref(p)), "plan_params")
+    _check(lib().gbdlt_plan_params_ex(N, prec, eps, method, ctypes.byref(p)), "plan_params")
     return p.to_dict()
 
 
@@ -148,7 +163,8 @@ class Plan:
     plans, float32 for FP32 plans) and return a new tensor (or write ``out``).
     """
 
-    def __init__(self, N: int, prec: int = FP64, eps: float = 0.0, stream=None, device=None):
+    def __init__(self, N: int, prec: int = FP64, eps: float = 0.0, stream=None, device=None,
+                 method: int = METHOD_AUTO):
         self._h = None
         self.N = int(N)
         self.prec = prec
@@ -158,8 +174,8 @@ class Plan:
             s = torch.cuda.current_stream() if stream is None else stream
             self.stream = s
             h = ctypes.c_void_p()
-            _check(lib().gbdlt_plan_create(self.N, prec, eps, ctypes.c_void_p(s.cuda_stream),
-                                           ctypes.byref(h)), "plan_create")
+            _check(lib().gbdlt_plan_create_ex(self.N, prec, eps, method, ctypes.c_void_p(s.cuda_stream),
+                                              ctypes.byref(h)), "plan_create")
         self._h = h
 
     def close(self):
@@ -252,11 +268,12 @@ class Plan:
 
 
 class Batch:
-    """Uneven batch of DLTs (dir 0) and IDLTs (dir 1) of power-of-two lengths,
-    executed as one CUDA-graph replay (gbdlt_batch_*).  ``run(x)`` takes and
+    """Uneven batch of DLTs (dir 0) and IDLTs (dir 1) executed as one CUDA-graph
+    replay (gbdlt_batch_*); ``method`` METHOD_AUTO lets the library time both
+    methods per (N, direction) group and keep the faster.  ``run(x)`` takes and
     returns the concatenation of the B vectors in the given order."""
 
-    def __init__(self, Ns, dirs, prec: int = FP64, eps: float = 0.0):
+    def __init__(self, Ns, dirs, prec: int = FP64, eps: float = 0.0, method: int = METHOD_AUTO):
         import numpy as np
         Ns = np.ascontiguousarray(Ns, dtype=np.int64)
         dirs = np.ascontiguousarray(dirs, dtype=np.int32)
@@ -266,15 +283,28 @@ class Batch:
         self.Ns, self.dirs, self.prec, self.dtype = Ns, dirs, prec, _dtype(prec)
         self.offsets = np.concatenate([[0], np.cumsum(Ns)])
         h = ctypes.c_void_p()
-        _check(lib().gbdlt_batch_create(Ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                        dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                        Ns.size, prec, eps, ctypes.byref(h)), "batch_create")
+        _check(lib().gbdlt_batch_create_ex(Ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           Ns.size, prec, eps, method, ctypes.byref(h)), "batch_create")
         self._h = h
 
     def info(self) -> dict:
         t, g, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib().gbdlt_batch_info(self._h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(k)), "batch_info")
         return {"total_elements": t.value, "groups": g.value, "graph_kernels": k.value}
+
+    def groups(self) -> list:
+        """Per (N, direction) group: N, dir, count, method and the autotuner's timings."""
+        out = []
+        for g in range(self.info()["groups"]):
+            N, d, c, m = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+            tf, td = ctypes.c_double(), ctypes.c_double()
+            _check(lib().gbdlt_batch_group_info(self._h, g, ctypes.byref(N), ctypes.byref(d), ctypes.byref(c),
+                                                ctypes.byref(m), ctypes.byref(tf), ctypes.byref(td)),
+                   "batch_group_info")
+            out.append({"N": N.value, "dir": d.value, "count": c.value, "method": m.value,
+                        "ms_fast": tf.value, "ms_direct": td.value})
+        return out
 
     def run(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         n = int(self.offsets[-1])
@@ -304,13 +334,13 @@ class Batch:
 _plans: dict = {}
 
 
-def get_plan(N: int, prec: int, device=None) -> Plan:
+def get_plan(N: int, prec: int, device=None, method: int = METHOD_AUTO) -> Plan:
     dev = torch.cuda.current_device() if device is None else torch.device(device).index
     stream = torch.cuda.current_stream(dev)
-    key = (int(N), prec, dev, stream.cuda_stream)
+    key = (int(N), prec, dev, stream.cuda_stream, method)
     p = _plans.get(key)
     if p is None:
-        p = Plan(N, prec, stream=stream, device=dev)
+        p = Plan(N, prec, stream=stream, device=dev, method=method)
         _plans[key] = p
     return p
 

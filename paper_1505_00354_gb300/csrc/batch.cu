@@ -1,16 +1,27 @@
 // Uneven batches: many transforms of different lengths and directions run as
 // one CUDA-graph replay.
 //
-// The transforms are grouped by (N, direction).  Each distinct N gets one plan
-// whose workspace holds the largest group of that N in one pass, so a group is
-// a single batched chain (every stage kernel carries the batch index in
-// blockIdx.y and every FFT launch transforms all vectors of the group).  At
-// creation the group chains are run once (to settle kernel attributes) and then
-// captured from an internal stream into one CUDA graph.  An execution is: wait
-// for the caller's stream, gather the caller's concatenated inputs into the
-// grouped staging layout, replay the graph, scatter the grouped outputs back to
-// the caller's layout, and make the caller's stream wait for the result.
-// Nothing is allocated per execution.
+// The transforms are grouped by (N, direction).  Each group gets its own plan,
+// whose workspace holds the whole group in one pass, so a group is a single
+// batched chain (every kernel carries the batch index in blockIdx.y and every
+// FFT launch transforms all vectors of the group).  Groups are spread over up to
+// kLanes internal streams, so that the graph has independent branches and small
+// groups run side by side.
+//
+// Method per group (the autotuner): with GBDLT_METHOD_AUTO, a group whose N
+// allows both methods is run and timed with CUDA events through the FFT-based
+// chain and through the direct method (three timed runs each after a warm-up
+// run) and keeps the faster; lengths that are not powers of two take the direct
+// method, lengths above its limit the FFT-based chain.  The timings are kept and
+// reported by gbdlt_batch_group_info.
+//
+// At creation the chains are run once more with the chosen methods and then
+// captured from the internal streams into one CUDA graph (fork from the main
+// internal stream, one branch per lane, join).  An execution is: wait for the
+// caller's stream, gather the caller's concatenated inputs into the grouped
+// staging layout, replay the graph, scatter the grouped outputs back to the
+// caller's layout, and make the caller's stream wait for the result.  Nothing is
+// allocated per execution.
 #include <algorithm>
 #include <map>
 #include <new>
@@ -20,18 +31,27 @@
 
 namespace gbdlt {
 
+constexpr int kLanes = 8;
+
 struct BatchGroup {
   int64_t N;
   int dir;  // 0: DLT, 1: IDLT
   int64_t count;
   int64_t stage_off;  // element offset of the group's first vector in the staging buffers
   Plan* plan;
+  int lane;           // internal stream the group runs on
+  int method;         // GBDLT_METHOD_FAST or GBDLT_METHOD_DIRECT
+  double ms_fast = -1.0, ms_direct = -1.0;  // autotuner timings (-1: not timed)
 };
 
 struct Batch {
   int prec = GBDLT_FP64;
   int64_t B = 0, total = 0, maxN = 0;
   cudaStream_t s = nullptr;
+  cudaStream_t lane_s[kLanes] = {};
+  cudaEvent_t lane_ev[kLanes] = {};
+  cudaEvent_t ev_fork = nullptr;
+  int nlanes = 0;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<Plan*> plans;
   std::vector<BatchGroup> groups;
@@ -67,15 +87,47 @@ int move(Batch& b, const void* src, void* dst, bool gather) {
   return check_launch();
 }
 
-int run_groups(Batch& b) {
+int run_group(Batch& b, const BatchGroup& g, int method) {
   const size_t es = b.prec == GBDLT_FP64 ? 8 : 4;
+  const char* in = (const char*)b.stage_in + (size_t)g.stage_off * es;
+  char* out = (char*)b.stage_out + (size_t)g.stage_off * es;
+  return run_op_method(reinterpret_cast<gbdlt_plan>(g.plan), g.dir ? OP_IDLT : OP_DLT, method, in, out, g.count);
+}
+
+// every group on its lane: the lanes wait for b.s, then b.s waits for the lanes
+int run_groups(Batch& b) {
+  if (cudaEventRecord(b.ev_fork, b.s) != cudaSuccess) return GBDLT_ERR_CUDA;
+  for (int l = 0; l < b.nlanes; ++l)
+    if (cudaStreamWaitEvent(b.lane_s[l], b.ev_fork, 0) != cudaSuccess) return GBDLT_ERR_CUDA;
   for (const BatchGroup& g : b.groups) {
-    const char* in = (const char*)b.stage_in + (size_t)g.stage_off * es;
-    char* out = (char*)b.stage_out + (size_t)g.stage_off * es;
-    int st = run_op(reinterpret_cast<gbdlt_plan>(g.plan), g.dir ? OP_IDLT : OP_DLT, in, out, g.count);
+    int st = run_group(b, g, g.method);
     if (st) return st;
   }
+  for (int l = 0; l < b.nlanes; ++l) {
+    if (cudaEventRecord(b.lane_ev[l], b.lane_s[l]) != cudaSuccess) return GBDLT_ERR_CUDA;
+    if (cudaStreamWaitEvent(b.s, b.lane_ev[l], 0) != cudaSuccess) return GBDLT_ERR_CUDA;
+  }
   return GBDLT_OK;
+}
+
+// milliseconds per run of group g with `method`: one warm-up run, three timed
+double time_group(Batch& b, BatchGroup& g, int method, cudaEvent_t e0, cudaEvent_t e1, int* status) {
+  cudaStream_t st = b.lane_s[g.lane];
+  *status = run_group(b, g, method);
+  if (*status) return -1.0;
+  if (cudaEventRecord(e0, st) != cudaSuccess) {
+    *status = GBDLT_ERR_CUDA;
+    return -1.0;
+  }
+  for (int r = 0; r < 3 && !*status; ++r) *status = run_group(b, g, method);
+  if (*status) return -1.0;
+  float ms = 0.f;
+  if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+    *status = GBDLT_ERR_CUDA;
+    return -1.0;
+  }
+  return (double)ms / 3.0;
 }
 
 void free_batch(Batch* b) {
@@ -87,6 +139,11 @@ void free_batch(Batch* b) {
   if (b->stage_in) cudaFree(b->stage_in);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (int l = 0; l < kLanes; ++l) {
+    if (b->lane_ev[l]) cudaEventDestroy(b->lane_ev[l]);
+    if (b->lane_s[l]) cudaStreamDestroy(b->lane_s[l]);
+  }
   if (b->s) cudaStreamDestroy(b->s);
   delete b;
 }
@@ -99,15 +156,20 @@ using namespace gbdlt;
 
 struct gbdlt_batch_s {};  // opaque tag; the pointer is a gbdlt::Batch
 
-extern "C" int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
-                                  double eps, gbdlt_batch* out) {
+extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
+                                     double eps, int method, gbdlt_batch* out) {
   if (!out) return GBDLT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!Ns_host || !dirs_host || B < 1 || B > 65535) return GBDLT_ERR_INVALID_ARG;
   if (prec != GBDLT_FP64 && prec != GBDLT_FP32) return GBDLT_ERR_INVALID_ARG;
+  if (method != GBDLT_METHOD_AUTO && method != GBDLT_METHOD_FAST && method != GBDLT_METHOD_DIRECT)
+    return GBDLT_ERR_INVALID_ARG;
   for (int64_t i = 0; i < B; ++i) {
     const int64_t N = Ns_host[i];
-    if (N < 1 || N > (1ll << 24) || (N & (N - 1))) return GBDLT_ERR_UNSUPPORTED_N;
+    const bool pow2 = N >= 1 && (N & (N - 1)) == 0;
+    if (N < 1 || N > (1ll << 24)) return GBDLT_ERR_UNSUPPORTED_N;
+    if (!pow2 && (method == GBDLT_METHOD_FAST || N > kDirectMax)) return GBDLT_ERR_UNSUPPORTED_N;
+    if (method == GBDLT_METHOD_DIRECT && N > kDirectMax) return GBDLT_ERR_UNSUPPORTED_N;
     if (dirs_host[i] != 0 && dirs_host[i] != 1) return GBDLT_ERR_INVALID_ARG;
   }
   Batch* b = new (std::nothrow) Batch();
@@ -115,14 +177,19 @@ extern "C" int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_ho
   b->prec = prec;
   b->B = B;
   const size_t es = prec == GBDLT_FP64 ? 8 : 4;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
   auto fail = [&](int st) {
     cudaGetLastError();
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
     free_batch(b);
     return st;
   };
   if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
     return fail(GBDLT_ERR_CUDA);
   // groups by (N, dir), staging offsets, per-transform offsets
   std::map<std::pair<int64_t, int>, std::vector<int64_t>> members;
@@ -136,26 +203,41 @@ extern "C" int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_ho
     members[{Ns_host[i], dirs_host[i]}].push_back(i);
   }
   b->total = off;
-  std::map<int64_t, int64_t> max_count;
-  for (auto& kv : members)
-    max_count[kv.first.first] = std::max<int64_t>(max_count[kv.first.first], (int64_t)kv.second.size());
-  std::map<int64_t, Plan*> plan_of;
-  for (auto& kv : max_count) {
+  b->nlanes = (int)std::min<size_t>(kLanes, members.size());
+  for (int l = 0; l < b->nlanes; ++l)
+    if (cudaStreamCreateWithFlags(&b->lane_s[l], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->lane_ev[l], cudaEventDisableTiming) != cudaSuccess)
+      return fail(GBDLT_ERR_CUDA);
+  // one plan per group, on the group's lane; groups go to lanes in order of
+  // decreasing work so that the lanes carry similar loads
+  std::vector<std::pair<double, std::pair<int64_t, int>>> order;
+  for (auto& kv : members) order.push_back({-(double)kv.second.size() * (double)kv.first.first, kv.first});
+  std::sort(order.begin(), order.end());
+  std::vector<double> lane_load(b->nlanes, 0.0);
+  int64_t soff = 0;
+  for (auto& ok : order) {
+    const std::vector<int64_t>& idx = members[ok.second];
+    BatchGroup g;
+    g.N = ok.second.first;
+    g.dir = ok.second.second;
+    g.count = (int64_t)idx.size();
+    g.stage_off = soff;
+    g.lane = (int)(std::min_element(lane_load.begin(), lane_load.end()) - lane_load.begin());
+    lane_load[g.lane] += -ok.first;
+    const bool pow2 = (g.N & (g.N - 1)) == 0;
+    const bool can_direct = g.N > 1 && g.N <= kDirectMax;
+    int m = method;
+    if (!pow2) m = GBDLT_METHOD_DIRECT;
+    if (m == GBDLT_METHOD_AUTO && !can_direct) m = GBDLT_METHOD_FAST;
     Plan* p = nullptr;
-    int st = plan_create_impl(kv.first, prec, eps, b->s, kv.second, &p);
+    const int plan_method = m == GBDLT_METHOD_AUTO ? GBDLT_METHOD_FAST : m;
+    int st = plan_create_impl(g.N, prec, eps, plan_method, b->lane_s[g.lane], g.count,
+                              m == GBDLT_METHOD_AUTO ? 1 : 0, &p);
     if (st) return fail(st);
     b->plans.push_back(p);
-    plan_of[kv.first] = p;
-  }
-  int64_t soff = 0;
-  for (auto& kv : members) {
-    BatchGroup g;
-    g.N = kv.first.first;
-    g.dir = kv.first.second;
-    g.count = (int64_t)kv.second.size();
-    g.stage_off = soff;
-    g.plan = plan_of[g.N];
-    for (size_t q = 0; q < kv.second.size(); ++q) stage[kv.second[q]] = soff + (int64_t)q * g.N;
+    g.plan = p;
+    g.method = m;  // AUTO is resolved by the timing below
+    for (size_t q = 0; q < idx.size(); ++q) stage[idx[q]] = soff + (int64_t)q * g.N;
     soff += g.count * g.N;
     b->groups.push_back(g);
   }
@@ -168,8 +250,19 @@ extern "C" int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_ho
   if (cudaMemcpy(b->d_src, src.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_stage, stage.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_len, len.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemsetAsync(b->stage_in, 0, 2 * es * (size_t)b->total, b->s) != cudaSuccess)
+      cudaMemsetAsync(b->stage_in, 0, 2 * es * (size_t)b->total, b->s) != cudaSuccess ||
+      cudaStreamSynchronize(b->s) != cudaSuccess)
     return fail(GBDLT_ERR_CUDA);
+  // the autotuner: time both methods where both are open, keep the faster
+  for (BatchGroup& g : b->groups) {
+    if (g.method != GBDLT_METHOD_AUTO) continue;
+    int st = GBDLT_OK;
+    g.ms_fast = time_group(*b, g, GBDLT_METHOD_FAST, t0, t1, &st);
+    if (st) return fail(st);
+    g.ms_direct = time_group(*b, g, GBDLT_METHOD_DIRECT, t0, t1, &st);
+    if (st) return fail(st);
+    g.method = g.ms_direct < g.ms_fast ? GBDLT_METHOD_DIRECT : GBDLT_METHOD_FAST;
+  }
   // one plain run (kernel attributes, lazy module loading), then capture
   int st = run_groups(*b);
   if (st) return fail(st);
@@ -194,8 +287,15 @@ extern "C" int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_ho
       if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->graph_kernels;
     }
   }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
   *out = reinterpret_cast<gbdlt_batch>(b);
   return GBDLT_OK;
+}
+
+extern "C" int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
+                                  double eps, gbdlt_batch* out) {
+  return gbdlt_batch_create_ex(Ns_host, dirs_host, B, prec, eps, GBDLT_METHOD_AUTO, out);
 }
 
 extern "C" int gbdlt_batch_exec(gbdlt_batch batch, const void* in, void* out, void* cuda_stream) {
@@ -225,10 +325,26 @@ extern "C" int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int6
   return GBDLT_OK;
 }
 
+extern "C" int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
+                                      int32_t* method, double* ms_fast, double* ms_direct) {
+  if (!batch) return GBDLT_ERR_INVALID_ARG;
+  Batch& b = *reinterpret_cast<Batch*>(batch);
+  if (g < 0 || g >= (int64_t)b.groups.size()) return GBDLT_ERR_INVALID_ARG;
+  const BatchGroup& G = b.groups[(size_t)g];
+  if (N) *N = G.N;
+  if (dir) *dir = G.dir;
+  if (count) *count = G.count;
+  if (method) *method = G.method;
+  if (ms_fast) *ms_fast = G.ms_fast;
+  if (ms_direct) *ms_direct = G.ms_direct;
+  return GBDLT_OK;
+}
+
 extern "C" int gbdlt_batch_destroy(gbdlt_batch batch) {
   if (!batch) return GBDLT_ERR_INVALID_ARG;
   Batch* b = reinterpret_cast<Batch*>(batch);
   cudaStreamSynchronize(b->s);
+  for (int l = 0; l < b->nlanes; ++l) cudaStreamSynchronize(b->lane_s[l]);
   free_batch(b);
   return GBDLT_OK;
 }

@@ -22,7 +22,23 @@
 //    per k2.
 // Twiddles come from tables (no trigonometry in the hot loop): the inner
 // Stockham twiddles from a 4096-entry table e^{2 pi i j/4096}, the inter-pass
-// twiddle from a two-level table of e^{2 pi i e/N}.
+// twiddle from a table of e^{2 pi i e/N} (one entry per e in FP64; in FP32 the
+// product of a two-level table).
+//
+// FP64 stages with twiddles (radix 16, Ns > 1) are written for GB300's FP64
+// pipe, which retires two operations per SM per clock while every other pipe
+// is idle: each radix-16 butterfly is two layers of radix-4 decimation-in-time
+// butterflies whose twiddle products are folded into fused multiply-adds in the
+// cosine/tangent form of Linzer and Feig (IBM J. Res. Dev., 1993):
+//   w b = sigma * ((b_x - tau b_y) + i (b_y + tau b_x)),  sigma = cos, tau = tan,
+// or, where |sin| > |cos|, the same with sigma = sin, tau = cot on the swapped
+// components of b (the swap is a register select, not an FP64 operation).  A
+// radix-4 butterfly with twiddle U,
+//   y_q = sum_r omega_4^{rq} U^r a_r
+//       = (a0 +- U^2 a2) + omega_4^q U (a1 +- U^2 a3),
+// then costs 24 FMAs for 4 points, against 16 additions and 3 complex products
+// (28 operations) in the plain form; a twiddled radix-16 stage drops from
+// 13.75 to 12 FP64 operations per point.
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -49,6 +65,74 @@ template <typename T, int DIR>
 __device__ __forceinline__ C2<T> rot(C2<T> v, T c, T s) {
   const T sd = DIR > 0 ? s : -s;
   return mk<T>(v.x * c - v.y * sd, v.x * sd + v.y * c);
+}
+
+// ---------------------------------------------------------------- cosine/tangent twiddles (FP64)
+// Table entry for angle a: (sx, sy, t, swap) with, if |cos a| >= |sin a|,
+// sx = sy = cos a, t = tan a, swap = 0; otherwise sx = -sin a, sy = sin a,
+// t = cot a, swap = 1.  Then e^{ia} b = (sx R_x, sy R_y) with
+// R = (b'_x - t b'_y, b'_y + t b'_x), b' = b or (b_y, b_x) if swap.
+struct LFTw {
+  double sx, sy, t;
+  bool sw;
+};
+
+__device__ __forceinline__ LFTw lf_load(const double2* __restrict__ tab, int e) {
+  const double2 a = tab[2 * e], b = tab[2 * e + 1];
+  return {a.x, a.y, b.x, __double_as_longlong(b.y) != 0};
+}
+
+__device__ __forceinline__ C2<double> lf_rot(const LFTw& T, const C2<double> b) {
+  const double bx = T.sw ? b.y : b.x;
+  const double by = T.sw ? b.x : b.y;
+  return mk<double>(fma(-T.t, by, bx), fma(T.t, bx, by));
+}
+
+// in place: a_q <- sum_r omega_4^{rq} U^r a_r, omega_4 = e^{DIR i pi/2}; U2 = U^2
+template <int DIR>
+__device__ __forceinline__ void lf_dft4(C2<double>& a0, C2<double>& a1, C2<double>& a2, C2<double>& a3,
+                                        const LFTw& U, const LFTw& U2) {
+  using CD = C2<double>;
+  const CD r2 = lf_rot(U2, a2), r3 = lf_rot(U2, a3);
+  const CD b0 = mk<double>(fma(U2.sx, r2.x, a0.x), fma(U2.sy, r2.y, a0.y));   // a0 + U^2 a2
+  const CD b1 = mk<double>(fma(-U2.sx, r2.x, a0.x), fma(-U2.sy, r2.y, a0.y)); // a0 - U^2 a2
+  const CD c0 = mk<double>(fma(U2.sx, r3.x, a1.x), fma(U2.sy, r3.y, a1.y));   // a1 + U^2 a3
+  const CD c1 = mk<double>(fma(-U2.sx, r3.x, a1.x), fma(-U2.sy, r3.y, a1.y)); // a1 - U^2 a3
+  const CD q0 = lf_rot(U, c0), q1 = lf_rot(U, c1);
+  a0 = mk<double>(fma(U.sx, q0.x, b0.x), fma(U.sy, q0.y, b0.y));    // b0 + U c0
+  a2 = mk<double>(fma(-U.sx, q0.x, b0.x), fma(-U.sy, q0.y, b0.y));  // b0 - U c0
+  // b1 +- omega_4 U c1 with omega_4 (p + iq) = DIR (-q + ip)
+  if (DIR > 0) {
+    a1 = mk<double>(fma(-U.sy, q1.y, b1.x), fma(U.sx, q1.x, b1.y));
+    a3 = mk<double>(fma(U.sy, q1.y, b1.x), fma(-U.sx, q1.x, b1.y));
+  } else {
+    a1 = mk<double>(fma(U.sy, q1.y, b1.x), fma(-U.sx, q1.x, b1.y));
+    a3 = mk<double>(fma(-U.sy, q1.y, b1.x), fma(U.sx, q1.x, b1.y));
+  }
+}
+
+// Radix-16 DIT butterfly with twiddles w^{r k}, w = e^{DIR 2 pi i/(16 Ns)}, as two
+// radix-4 layers (r = r1 + 4 r2, q = q1 + 4 q2):
+//   B_r1(q1)   = sum_r2 omega_4^{r2 q1} W^{r2} x_{r1+4r2},          W = w^{4k}
+//   y_{q1+4q2} = sum_r1 omega_4^{r1 q2} V_q1^{r1} B_r1(q1),  V_q1 = w^{k + Ns q1}
+// On return v[4 q1 + q2] holds y_{q1 + 4 q2}.
+template <int DIR>
+__device__ __forceinline__ void lf_dft16(C2<double>* v, const double2* __restrict__ lf, int k, int Ns) {
+  const int s4 = 1024 / Ns;  // 4096 / (4 Ns): table step of w^4
+  const int s16 = 256 / Ns;  // 4096 / (16 Ns): table step of w
+  const LFTw W = lf_load(lf, k * s4), W2 = lf_load(lf, 2 * k * s4);
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) lf_dft4<DIR>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12], W, W2);
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1) {
+    int e = (k + Ns * q1) * s16;
+    // tie the table index to the data just computed so that the compiler loads
+    // each twiddle pair when it is needed instead of holding all of them in
+    // registers (the 16 values already take 64)
+    asm volatile("" : "+r"(e) : "d"(v[4 * q1].x));
+    const LFTw V = lf_load(lf, e), V2 = lf_load(lf, 2 * e);
+    lf_dft4<DIR>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3], V, V2);
+  }
 }
 
 // ---------------------------------------------------------------- small DFTs in registers
@@ -135,6 +219,45 @@ __device__ __forceinline__ void dftR(C2<T>* v) {
   if constexpr (R == 16) dft16<T, DIR>(v);
 }
 
+// FP64 radix-16 Stockham stage with Ns > 1 on the fused cosine/tangent form
+template <int DIR>
+__device__ __forceinline__ void stage_lf16(C2<double>* sm, int L, int logL, int lines, int LP, int Ns,
+                                           const double2* __restrict__ lf) {
+  using CD = C2<double>;
+  constexpr int PER = FFT_TILE / 16 / FFT_THREADS;
+  const int LR = L >> 4;
+  const int logLR = logL - 4;
+  const int nbf = lines * LR;
+  CD v[PER][16];
+  int dst[PER], ln[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * FFT_THREADS;
+    dst[q] = -1;
+    if (b < nbf) {
+      const int line = b >> logLR;
+      const int j = b & (LR - 1);
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[q][r] = sm[sidx(line, LP, j + r * LR)];
+      lf_dft16<DIR>(v[q], lf, k, Ns);
+      ln[q] = line;
+      dst[q] = (j - k) * 16 + k;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (dst[q] >= 0) {
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) sm[sidx(ln[q], LP, dst[q] + (q1 + 4 * q2) * Ns)] = v[q][4 * q1 + q2];
+    }
+  }
+  __syncthreads();
+}
+
 // One Stockham stage of radix R over `lines` vectors of length L (current
 // sub-transform length Ns): butterfly j reads x[j + r L/R], applies
 // w_{Ns R}^{r (j mod Ns)}, takes the R-point DFT and writes
@@ -143,7 +266,7 @@ __device__ __forceinline__ void dftR(C2<T>* v) {
 // products of them (FP32 arithmetic is cheap, table traffic is not).
 template <typename T, int DIR, int R>
 __device__ __forceinline__ void stage(C2<T>* sm, int L, int logL, int lines, int LP, int Ns,
-                                      const C2<T>* __restrict__ tw) {
+                                      const C2<T>* __restrict__ tw, const double2* __restrict__ lf) {
   using CT = C2<T>;
   constexpr int PER = FFT_TILE / R / FFT_THREADS;
   const int LR = L / R;
@@ -194,28 +317,42 @@ __device__ __forceinline__ void stage(C2<T>* sm, int L, int logL, int lines, int
 // In-place FFT of `lines` vectors of length L held at sidx(line, LP, i):
 // one stage of radix 2^(log2 L mod 4) (if any), then radix-16 stages.
 template <typename T, int DIR>
-__device__ void fft_tile(C2<T>* sm, int L, int logL, int lines, int LP, const C2<T>* __restrict__ tw) {
+__device__ void fft_tile(C2<T>* sm, int L, int logL, int lines, int LP, const C2<T>* __restrict__ tw,
+                         const double2* __restrict__ lf) {
   int Ns = 1;
   const int rem = logL & 3;
   if (rem == 1) {
-    stage<T, DIR, 2>(sm, L, logL, lines, LP, Ns, tw);
+    stage<T, DIR, 2>(sm, L, logL, lines, LP, Ns, tw, lf);
     Ns = 2;
   } else if (rem == 2) {
-    stage<T, DIR, 4>(sm, L, logL, lines, LP, Ns, tw);
+    stage<T, DIR, 4>(sm, L, logL, lines, LP, Ns, tw, lf);
     Ns = 4;
   } else if (rem == 3) {
-    stage<T, DIR, 8>(sm, L, logL, lines, LP, Ns, tw);
+    stage<T, DIR, 8>(sm, L, logL, lines, LP, Ns, tw, lf);
     Ns = 8;
   }
-  while (Ns < L) {
-    stage<T, DIR, 16>(sm, L, logL, lines, LP, Ns, tw);
-    Ns <<= 4;
+  if constexpr (sizeof(T) == 8) {
+    // FP64: the untwiddled first radix-16 stage, then the fused cosine/tangent stages
+    if (Ns == 1 && Ns < L) {
+      stage<T, DIR, 16>(sm, L, logL, lines, LP, 1, tw, lf);
+      Ns = 16;
+    }
+    while (Ns < L) {
+      stage_lf16<DIR>(reinterpret_cast<C2<double>*>(sm), L, logL, lines, LP, Ns, lf);
+      Ns <<= 4;
+    }
+  } else {
+    while (Ns < L) {
+      stage<T, DIR, 16>(sm, L, logL, lines, LP, Ns, tw, lf);
+      Ns <<= 4;
+    }
   }
 }
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
-    k_fft_single(C2<T>* __restrict__ data, int L, int logL, int64_t nvec, const C2<T>* __restrict__ tw4096) {
+    k_fft_single(C2<T>* __restrict__ data, int L, int logL, int64_t nvec, const C2<T>* __restrict__ tw4096,
+                 const double2* __restrict__ lf) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int lines_max = FFT_TILE / L;
@@ -226,7 +363,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
   C2<T>* g = data + v0 * L;
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) sm[sidx(i >> logL, LP, i & (L - 1))] = g[i];
   __syncthreads();
-  fft_tile<T, DIR>(sm, L, logL, lines, LP, tw4096);
+  fft_tile<T, DIR>(sm, L, logL, lines, LP, tw4096, lf);
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) g[i] = sm[sidx(i >> logL, LP, i & (L - 1))];
 }
 
@@ -234,7 +371,7 @@ template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int logL1, int L2, int C, int logC,
                const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
-               const C2<T>* __restrict__ tlo) {
+               const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int c0 = blockIdx.x * C;
@@ -246,13 +383,14 @@ __global__ void __launch_bounds__(FFT_THREADS)
     sm[sidx(c, LP, n1)] = g[(int64_t)n1 * L2 + c0 + c];
   }
   __syncthreads();
-  fft_tile<T, DIR>(sm, L1, logL1, C, LP, tw4096);
+  fft_tile<T, DIR>(sm, L1, logL1, C, LP, tw4096, lf);
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {
     const int k1 = i >> logC, c = i & (C - 1);
     const int64_t e = (int64_t)(c0 + c) * k1;
     C2<T> val = sm[sidx(c, LP, k1)];
     if (e != 0) {
-      const C2<T> w = tw_lookup<T>(thi, tlo, e);
+      // FP64: one table entry per e; FP32: product of the two-level entries
+      const C2<T> w = sizeof(T) == 8 ? tfull[e] : tw_lookup<T>(thi, tlo, e);
       val = cmul<T>(val, mk<T>(w.x, DIR > 0 ? w.y : -w.y));
     }
     g[(int64_t)k1 * L2 + c0 + c] = val;
@@ -262,7 +400,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
-               int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096) {
+               int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096,
+               const double2* __restrict__ lf) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int r0 = blockIdx.x * C2n;
@@ -275,7 +414,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
     sm[sidx(line, LP, n2)] = g[(int64_t)(r0 + line) * L2 + n2];
   }
   __syncthreads();
-  fft_tile<T, DIR>(sm, L2, logL2, C2n, LP, tw4096);
+  fft_tile<T, DIR>(sm, L2, logL2, C2n, LP, tw4096, lf);
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {
     const int k2 = i >> logC2, line = i & (C2n - 1);
     o[(int64_t)(r0 + line) + (int64_t)L1 * k2] = sm[sidx(line, LP, k2)];
@@ -288,6 +427,8 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   const int64_t N = P.p.N;
   if (nvec <= 0 || N <= 1) return a;
   const TwT<T> tw = tw_tables(P, T());
+  // cosine/tangent table of this direction (FP64 only)
+  const double2* lfd = tw.lf ? tw.lf + (DIR > 0 ? 0 : 2 * 4096) : nullptr;
   const size_t smax = (size_t)FFT_SMEM_ELEMS * sizeof(CT);
   static bool attrs = false;  // one flag per (T, DIR) instantiation
   if (!attrs) {
@@ -303,7 +444,7 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
     int lines = FFT_TILE / L;
     int64_t grid = (nvec + lines - 1) / lines;
     size_t sm = (size_t)lines * line_pitch(L) * sizeof(CT);
-    k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, lg, nvec, tw.t4096);
+    k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, lg, nvec, tw.t4096, lfd);
     launched(P, "fft_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
     return a;
   }
@@ -316,11 +457,11 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   int lL1 = p / 2, lL2 = p - p / 2, lC = 12 - lL1, lC2 = 12 - lL2;
   dim3 g1(L2 / C, (unsigned)nvec);
   k_fft_cols<T, DIR><<<g1, FFT_THREADS, (size_t)C * line_pitch(L1) * sizeof(CT), P.stream>>>(
-      (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo);
+      (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo, tw.full, lfd);
   launched(P, "fft_cols", (5.0 * (p / 2) + 6.0) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
   dim3 g2(L1 / C2n, (unsigned)nvec);
   k_fft_rows<T, DIR><<<g2, FFT_THREADS, (size_t)C2n * line_pitch(L2) * sizeof(CT), P.stream>>>(
-      (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096);
+      (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096, lfd);
   launched(P, "fft_rows", 5.0 * (p - p / 2) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
   return b;
 }
@@ -331,6 +472,41 @@ void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir) {
 }
 
 template void* launch_fft<double>(Plan&, void*, void*, int64_t, int);
+
+namespace {
+// cosine/tangent table for both directions: entry e of direction d holds the
+// form of e^{i a}, a = (d ? -1 : +1) 2 pi e / 4096
+__global__ void k_lf_init(double2* __restrict__ tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * 4096) return;
+  const int d = i >> 12, e = i & 4095;
+  double s, c;
+  sincospi(2.0 * (double)e / 4096.0, &s, &c);
+  if (d) s = -s;
+  double sx, sy, t, sw;
+  if (fabs(c) >= fabs(s)) {
+    sx = c;
+    sy = c;
+    t = s / c;
+    sw = 0.0;
+  } else {
+    sx = -s;
+    sy = s;
+    t = c / s;
+    sw = 1.0;
+  }
+  tab[2 * i] = make_double2(sx, sy);
+  tab[2 * i + 1] = make_double2(t, sw);
+}
+}  // namespace
+
+int launch_fft_tables_init(Plan& P) {
+  if (P.lf_tab) {
+    k_lf_init<<<32, 256, 0, P.stream>>>(P.lf_tab);
+    count_launch();
+  }
+  return check_launch();
+}
 template void* launch_fft<float>(Plan&, void*, void*, int64_t, int);
 
 }  // namespace gbdlt

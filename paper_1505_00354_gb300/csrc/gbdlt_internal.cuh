@@ -134,15 +134,25 @@ struct Params {
   int seg = 512;
   int64_t rec_steps = 0;
   double flops_dlt = 0, bytes_dlt = 0, bytes_idlt = 0;
+  int method = GBDLT_METHOD_FAST;  // what gbdlt_dlt/idlt(_t) run (resolved, never AUTO)
+  bool fast = true;                // N is a power of two: the FFT-based chains exist
+  int64_t direct_steps = 0;        // half-row recurrence steps of one direct transform
 };
 
-// Fills Params from (N, prec, eps): Taylor terms, asymptotic terms and bands.
-int derive_params(int64_t N, int prec, double eps, Params* p);
+// Direct method limits: largest N a direct plan accepts, and the largest
+// power-of-two N that GBDLT_METHOD_AUTO sends to the direct method.
+constexpr int64_t kDirectMax = 1 << 16;
+constexpr int64_t kDirectAuto = 256;
+
+// Fills Params from (N, prec, eps, method): Taylor terms, asymptotic terms, bands
+// and the method the plan runs.
+int derive_params(int64_t N, int prec, double eps, int method, Params* p);
 // Host table of C_n = sqrt(4/pi) Gamma(n+1)/Gamma(n+3/2), n = 0..N (double-double recurrence).
 std::vector<double> cn_table(int64_t N);
 
 struct RecLayout {
-  int64_t H = 0;              // half rows (N / 2)
+  int64_t H = 0;              // half rows (ceil(N / 2); row H-1 is its own mirror for odd N)
+  int64_t half_steps = 0;     // recurrence steps over all half rows
   int S = 512;                // segment length
   int64_t nseg_total = 0;     // sum over half rows of nseg(k)
   int64_t n_long = 0;         // rows [0, n_long) have nseg > 64
@@ -156,6 +166,7 @@ struct RecLayout {
   int32_t* cta_j = nullptr;   // [ncta]
   int64_t* toff = nullptr;    // [nblocks] offset of row block partials (length nseg_max*S)
   int32_t* bcutmax = nullptr; // [nblocks] nseg_max(rb) * S (partial array length)
+  double* xm1 = nullptr;      // [H] x_k - 1 of the rows (cheb1 grid, or Legendre nodes)
   double2* state = nullptr;   // [nseg_total] (P, D) at segment starts
   double2* part = nullptr;    // [nseg_total] forward partial sums (E, O)
   double* tbuf = nullptr;     // [tbuf_total] transposed partial sums
@@ -181,8 +192,15 @@ struct Plan {
   // the same tables rounded to float, used by the FP32 form (no FP64 work there)
   float2* tw4096f = nullptr;
   float2 *twNf_lo = nullptr, *twNf_hi = nullptr, *tw4Nf_lo = nullptr, *tw4Nf_hi = nullptr;
+  // FP64 FFT tables: e^{2 pi i e/N} for every e < N (the four-step twiddle; FP64
+  // plans with N > 4096 only), and the cosine/tangent form of e^{+-2 pi i e/4096}
+  // used by the fused radix-4 layers ([2 directions][4096][sx, sy, t, swap])
+  double2* twfull = nullptr;
+  double2* lf_tab = nullptr;
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
-  RecLayout rec;
+  RecLayout rec;    // recurrence region of the fast path (cheb1 rows)
+  RecLayout drec;   // every row and column at the Legendre nodes (direct method)
+  bool has_direct = false;
   // workspace (element type = plan precision)
   void* bufA = nullptr;
   void* bufB = nullptr;
@@ -208,20 +226,27 @@ struct TwT {
   const C2<T>* nhi;
   const C2<T>* flo;    // e^{2 pi i e / (4N)}, two-level
   const C2<T>* fhi;
+  const C2<T>* full;   // e^{2 pi i e / N}, one entry per e (FP64 only, else null)
+  const double2* lf;   // cosine/tangent twiddles (FP64 only, else null)
 };
 inline TwT<double> tw_tables(const Plan& P, double) {
-  return {P.tw4096, P.twN.lo, P.twN.hi, P.tw4N.lo, P.tw4N.hi};
+  return {P.tw4096, P.twN.lo, P.twN.hi, P.tw4N.lo, P.tw4N.hi, P.twfull, P.lf_tab};
 }
 inline TwT<float> tw_tables(const Plan& P, float) {
-  return {P.tw4096f, P.twNf_lo, P.twNf_hi, P.tw4Nf_lo, P.tw4Nf_hi};
+  return {P.tw4096f, P.twNf_lo, P.twNf_hi, P.tw4Nf_lo, P.tw4Nf_hi, nullptr, nullptr};
 }
 
 // plan lifecycle and the operator dispatch shared by the C ABI and the batch
 // executor; max_batch > 0 limits the batch items one workspace pass holds
-int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64_t max_batch, Plan** out);
+// want_direct also builds the direct layout for a fast plan (the batch autotuner
+// times both methods on one plan)
+int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t stream, int64_t max_batch,
+                     int want_direct, Plan** out);
 void free_plan(Plan* P);
 enum Op { OP_L2C, OP_L2C_T, OP_CHEB, OP_CHEB_T, OP_DLT, OP_DLT_T, OP_IDLT, OP_IDLT_T };
 int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch);
+// the same with the method of the four transforms given (GBDLT_METHOD_FAST / _DIRECT)
+int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out, int64_t batch);
 
 // ---------------------------------------------------------------------------
 // launch bookkeeping
@@ -237,6 +262,8 @@ void launched(Plan& P, const char* name, double flops, double bytes);
 // ---------------------------------------------------------------------------
 // tables.cu
 int launch_twiddle_init(Plan& P);
+// fft.cu: the FP64 transform tables (twfull, lf_tab)
+int launch_fft_tables_init(Plan& P);
 // legpts.cu
 int launch_legpts(Plan& P, double CN);
 int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N
@@ -245,11 +272,14 @@ int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N
 template <typename T>
 void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir);
 // rec.cu
-int launch_rec_state_init(Plan& P);
+int launch_rec_state_init(Plan& P, RecLayout& L);
 template <typename T>
-int launch_rec_forward(Plan& P, const T* c, T* vrec, int64_t nb);
+int launch_rec_forward(Plan& P, RecLayout& L, const T* c, T* vrec, int64_t nb);
 template <typename T>
-int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb);
+int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb,
+                         const double* zw = nullptr, int scale_out = 0);
+// x_k - 1 of the cheb1 rows (fast path) or of the Legendre nodes (direct method)
+int launch_rec_xm1(Plan& P, RecLayout& L, int legendre);
 // stages.cu (prologues / epilogues)
 template <typename T>
 int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb);

@@ -213,15 +213,24 @@ static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, doubl
   return best_res;
 }
 
-int derive_params(int64_t N, int prec, double eps, Params* p) {
-  if (N < 1 || N > (1ll << 24) || (N & (N - 1))) return GBDLT_ERR_UNSUPPORTED_N;
+int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
+  if (N < 1 || N > (1ll << 24)) return GBDLT_ERR_UNSUPPORTED_N;
   if (prec != GBDLT_FP64 && prec != GBDLT_FP32) return GBDLT_ERR_INVALID_ARG;
+  if (method != GBDLT_METHOD_AUTO && method != GBDLT_METHOD_FAST && method != GBDLT_METHOD_DIRECT)
+    return GBDLT_ERR_INVALID_ARG;
   if (eps <= 0.0) eps = prec == GBDLT_FP64 ? 1e-14 : 2e-6;
   if (!(eps < 1.0) || !std::isfinite(eps)) return GBDLT_ERR_INVALID_ARG;
+  const bool pow2 = (N & (N - 1)) == 0;
+  if (method == GBDLT_METHOD_AUTO)
+    method = (!pow2 || N <= kDirectAuto) ? GBDLT_METHOD_DIRECT : GBDLT_METHOD_FAST;
+  if (method == GBDLT_METHOD_FAST && !pow2) return GBDLT_ERR_UNSUPPORTED_N;
+  if (method == GBDLT_METHOD_DIRECT && N > kDirectMax) return GBDLT_ERR_UNSUPPORTED_N;
   Params q;
   q.N = N;
   q.prec = prec;
   q.eps = eps;
+  q.method = method;
+  q.fast = pow2;
   // Corollary 2.4 with theta* = theta^cheb1: |f - f_L| <= 0.83845^L / L! ||c||_1
   int L = 1;
   double b = 0.83845;
@@ -235,7 +244,7 @@ int derive_params(int64_t N, int prec, double eps, Params* p) {
   q.K = 0;
   int lg = 0;
   while ((1ll << lg) < N) ++lg;
-  if (N >= 4) {
+  if (pow2 && N >= 4) {
     const double eps_asy = eps / 20.0;
     // costs in picoseconds of GB300 time, fitted to the measured kernels at
     // N = 2^20: one FFT vector of the pipeline (forward and transposed chain)
@@ -264,18 +273,22 @@ int derive_params(int64_t N, int prec, double eps, Params* p) {
     q.K = (int)q.bands.size();
     if (q.K == 0) q.M = 0;
   }
-  // recurrence work
+  // recurrence work of the fast path (cheb1 rows), and of the direct method
+  // (every Legendre node row against every column, mirrored rows shared)
   const int64_t H = N / 2;
   int64_t half_steps = 0;
-  {
+  if (pow2) {
     int64_t k0 = q.K > 0 ? q.bands[0].ka : H;
     half_steps += k0 * N;
     for (const Band& bd : q.bands) half_steps += (bd.kb - bd.ka) * bd.ns;
   }
   q.rec_steps = 2 * half_steps;
+  q.direct_steps = N <= kDirectMax ? ((N + 1) / 2) * N : 0;
   const int npair = (q.L - 1 + 1) / 2;
   const double fft_flops = 5.0 * (double)N * (double)std::max(lg, 1);
-  q.flops_dlt = (double)(q.K * q.M + 1 + npair) * fft_flops + 7.0 * (double)half_steps;
+  q.flops_dlt = method == GBDLT_METHOD_DIRECT
+                    ? 7.0 * (double)q.direct_steps
+                    : (double)(q.K * q.M + 1 + npair) * fft_flops + 7.0 * (double)half_steps;
   const double dsz = prec == GBDLT_FP64 ? 8.0 : 4.0;
   q.bytes_dlt = (2.0 * dsz + 8.0) * (double)N;
   q.bytes_idlt = (2.0 * dsz + 16.0) * (double)N;
@@ -315,6 +328,7 @@ int launch_twiddle_init(Plan& P) {
   twiddle_fill(P, P.twN.hi, std::max<int64_t>(1, P.twN.B / 4096), P.twN.B, 4096);
   twiddle_fill(P, P.tw4N.lo, 4096, P.tw4N.B, 1);
   twiddle_fill(P, P.tw4N.hi, std::max<int64_t>(1, P.tw4N.B / 4096), P.tw4N.B, 4096);
+  if (P.twfull) twiddle_fill(P, P.twfull, P.p.N, P.p.N, 1);
   to_float(P, P.tw4096, P.tw4096f, 4096);
   to_float(P, P.twN.lo, P.twNf_lo, 4096);
   to_float(P, P.twN.hi, P.twNf_hi, std::max<int64_t>(1, P.twN.B / 4096));
@@ -351,9 +365,59 @@ void free_plan(Plan* P) {
 }
 
 
-int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64_t max_batch, Plan** out) {
+namespace {
+
+// Host side of a recurrence layout: rows [0, H) with column cuts `cut`, cut into
+// segments of S columns; CTAs are (row block of 256 half rows, segment) pairs.
+struct LayoutHost {
+  std::vector<int32_t> cut, cta_rb, cta_j, maxcut;
+  std::vector<int64_t> poff, toff;
+};
+
+void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, LayoutHost& h) {
+  R.H = H;
+  R.S = S;
+  h.cut = std::move(cut);
+  h.poff.assign((size_t)std::max<int64_t>(H, 1), 0);
+  int64_t o = 0, steps = 0;
+  R.n_long = 0;
+  for (int64_t k = 0; k < H; ++k) {
+    h.poff[(size_t)k] = o;
+    const int64_t ns = (h.cut[(size_t)k] + S - 1) / S;
+    o += ns;
+    steps += h.cut[(size_t)k];
+    if (ns > 64) R.n_long = k + 1;
+  }
+  R.nseg_total = o;
+  R.half_steps = steps;
+  R.nblocks = (H + 255) / 256;
+  int64_t to = 0;
+  for (int64_t rb = 0; rb < R.nblocks; ++rb) {
+    int32_t mc = 0;
+    for (int64_t k = rb * 256; k < std::min<int64_t>(H, rb * 256 + 256); ++k) mc = std::max(mc, h.cut[(size_t)k]);
+    const int64_t nsm = (mc + S - 1) / S;
+    h.maxcut.push_back(mc);
+    h.toff.push_back(to);
+    to += nsm * S;
+    for (int64_t j = 0; j < nsm; ++j) {
+      h.cta_rb.push_back((int32_t)rb);
+      h.cta_j.push_back((int32_t)j);
+    }
+  }
+  R.tbuf_total = to;
+  R.ncta = (int64_t)h.cta_rb.size();
+}
+
+struct LayoutOff {
+  size_t cut, poff, crb, cj, toff, mc, xm1, state, part, tbuf;
+};
+
+}  // namespace
+
+int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t stream, int64_t max_batch,
+                     int want_direct, Plan** out) {
   Params prm;
-  int st = derive_params(N, prec, eps, &prm);
+  int st = derive_params(N, prec, eps, method, &prm);
   if (st != GBDLT_OK) return st;
   Plan* P = new (std::nothrow) Plan();
   if (!P) return GBDLT_ERR_OOM;
@@ -362,50 +426,29 @@ int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64
   cudaGetDevice(&P->device);
   const size_t ts = prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * ts;
-  const int64_t H = N / 2;
-  // recurrence layout (host)
-  RecLayout& R = P->rec;
-  R.H = H;
-  R.S = prm.seg;
-  std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1));
-  std::vector<int64_t> poff((size_t)std::max<int64_t>(H, 1));
-  std::vector<int32_t> cta_rb, cta_j, maxcut;
-  std::vector<int64_t> toff;
-  if (H > 0) {
-    for (int64_t k = 0; k < H; ++k) cut[(size_t)k] = (int32_t)N;
+  // recurrence layouts (host): the fast path's region on the cheb1 rows, and the
+  // direct method's full rows at the Legendre nodes
+  LayoutHost hf, hd;
+  if (prm.fast) {
+    const int64_t H = N / 2;
+    std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1), (int32_t)N);
     for (const Band& b : prm.bands)
       for (int64_t k = b.ka; k < b.kb; ++k) cut[(size_t)k] = (int32_t)b.ns;
-    int64_t o = 0;
-    R.n_long = 0;
-    for (int64_t k = 0; k < H; ++k) {
-      poff[(size_t)k] = o;
-      int64_t ns = (cut[(size_t)k] + R.S - 1) / R.S;
-      o += ns;
-      if (ns > 64) R.n_long = k + 1;
-    }
-    R.nseg_total = o;
-    R.nblocks = (H + 255) / 256;
-    int64_t to = 0;
-    for (int64_t rb = 0; rb < R.nblocks; ++rb) {
-      int32_t mc = cut[(size_t)(rb * 256)];
-      int64_t nsm = (mc + R.S - 1) / R.S;
-      maxcut.push_back(mc);
-      toff.push_back(to);
-      to += nsm * R.S;
-      for (int64_t j = 0; j < nsm; ++j) {
-        cta_rb.push_back((int32_t)rb);
-        cta_j.push_back((int32_t)j);
-      }
-    }
-    R.tbuf_total = to;
-    R.ncta = (int64_t)cta_rb.size();
+    layout_build(P->rec, H, prm.seg, std::move(cut), hf);
   }
+  P->has_direct = N > 1 && N <= kDirectMax && (prm.method == GBDLT_METHOD_DIRECT || want_direct);
+  if (P->has_direct) {
+    const int64_t H = (N + 1) / 2;
+    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), hd);
+  }
+  RecLayout& R = P->rec;
+  RecLayout& D = P->drec;
   const int npair = (prm.L + 1) / 2;
-  P->nfft_max = std::max<int64_t>({(int64_t)prm.K * prm.M, (int64_t)npair, 1});
+  P->nfft_max = prm.fast ? std::max<int64_t>({(int64_t)prm.K * prm.M, (int64_t)npair, 1}) : 0;
   {
     // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
-    const double per_item = 2.0 * P->nfft_max * N * cs + 5.0 * N * ts + 16.0 * R.nseg_total +
-                            8.0 * R.tbuf_total;
+    const double per_item = 2.0 * P->nfft_max * N * cs + 5.0 * N * ts + 16.0 * (R.nseg_total + D.nseg_total) +
+                            8.0 * (R.tbuf_total + D.tbuf_total);
     P->bcap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(512.0 * (1 << 20) / per_item)));
     if (max_batch > 0) P->bcap = std::min<int64_t>(P->bcap, max_batch);
   }
@@ -424,10 +467,24 @@ int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64
   size_t o_twf = A.take<float2>(4096), o_twNflo = A.take<float2>(4096),
          o_twNfhi = A.take<float2>(std::max<int64_t>(1, N / 4096)), o_tw4flo = A.take<float2>(4096),
          o_tw4fhi = A.take<float2>(std::max<int64_t>(1, 4 * N / 4096));
-  size_t o_cut = A.take<int32_t>(H), o_poff = A.take<int64_t>(H), o_crb = A.take<int32_t>(R.ncta),
-         o_cj = A.take<int32_t>(R.ncta), o_toff = A.take<int64_t>(R.nblocks),
-         o_mc = A.take<int32_t>(R.nblocks), o_state = A.take<double2>(R.nseg_total),
-         o_part = A.take<double2>(BC * R.nseg_total), o_tbuf = A.take<double>(BC * R.tbuf_total);
+  const bool fp64_tabs = prec == GBDLT_FP64 && prm.fast;
+  size_t o_twfull = A.take<double2>(fp64_tabs && N > 4096 ? N : 1);
+  size_t o_lf = A.take<double2>(4 * 4096);
+  auto take_layout = [&](const RecLayout& L) {
+    LayoutOff o;
+    o.cut = A.take<int32_t>(L.H);
+    o.poff = A.take<int64_t>(L.H);
+    o.crb = A.take<int32_t>(L.ncta);
+    o.cj = A.take<int32_t>(L.ncta);
+    o.toff = A.take<int64_t>(L.nblocks);
+    o.mc = A.take<int32_t>(L.nblocks);
+    o.xm1 = A.take<double>(L.H);
+    o.state = A.take<double2>(L.nseg_total);
+    o.part = A.take<double2>(BC * L.nseg_total);
+    o.tbuf = A.take<double>(BC * L.tbuf_total);
+    return o;
+  };
+  const LayoutOff of = take_layout(R), od = take_layout(D);
   auto bytes_block = [&](size_t b) {
     size_t o = A.off;
     A.off += (b + 255) & ~(size_t)255;
@@ -467,15 +524,22 @@ int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64
   P->twNf_hi = (float2*)(base + o_twNfhi);
   P->tw4Nf_lo = (float2*)(base + o_tw4flo);
   P->tw4Nf_hi = (float2*)(base + o_tw4fhi);
-  R.cut = (int32_t*)(base + o_cut);
-  R.poff = (int64_t*)(base + o_poff);
-  R.cta_rb = (int32_t*)(base + o_crb);
-  R.cta_j = (int32_t*)(base + o_cj);
-  R.toff = (int64_t*)(base + o_toff);
-  R.bcutmax = (int32_t*)(base + o_mc);
-  R.state = (double2*)(base + o_state);
-  R.part = (double2*)(base + o_part);
-  R.tbuf = (double*)(base + o_tbuf);
+  P->twfull = fp64_tabs && N > 4096 ? (double2*)(base + o_twfull) : nullptr;
+  P->lf_tab = fp64_tabs ? (double2*)(base + o_lf) : nullptr;
+  auto place_layout = [&](RecLayout& L, const LayoutOff& o) {
+    L.cut = (int32_t*)(base + o.cut);
+    L.poff = (int64_t*)(base + o.poff);
+    L.cta_rb = (int32_t*)(base + o.crb);
+    L.cta_j = (int32_t*)(base + o.cj);
+    L.toff = (int64_t*)(base + o.toff);
+    L.bcutmax = (int32_t*)(base + o.mc);
+    L.xm1 = (double*)(base + o.xm1);
+    L.state = (double2*)(base + o.state);
+    L.part = (double2*)(base + o.part);
+    L.tbuf = (double*)(base + o.tbuf);
+  };
+  place_layout(R, of);
+  place_layout(D, od);
   P->bufA = base + o_bufA;
   P->bufB = base + o_bufB;
   P->v = base + o_v;
@@ -509,14 +573,17 @@ int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64
     up(P->ra_ff, raf.data(), sizeof(float2) * raf.size());
     up(P->rb_ff, rbf.data(), sizeof(float2) * rbf.size());
   }
-  if (H > 0) {
-    up(R.cut, cut.data(), sizeof(int32_t) * (size_t)H);
-    up(R.poff, poff.data(), sizeof(int64_t) * (size_t)H);
-    up(R.cta_rb, cta_rb.data(), sizeof(int32_t) * cta_rb.size());
-    up(R.cta_j, cta_j.data(), sizeof(int32_t) * cta_j.size());
-    up(R.toff, toff.data(), sizeof(int64_t) * toff.size());
-    up(R.bcutmax, maxcut.data(), sizeof(int32_t) * maxcut.size());
-  }
+  auto upload_layout = [&](RecLayout& L, const LayoutHost& h) {
+    if (L.H == 0) return;
+    up(L.cut, h.cut.data(), sizeof(int32_t) * (size_t)L.H);
+    up(L.poff, h.poff.data(), sizeof(int64_t) * (size_t)L.H);
+    up(L.cta_rb, h.cta_rb.data(), sizeof(int32_t) * h.cta_rb.size());
+    up(L.cta_j, h.cta_j.data(), sizeof(int32_t) * h.cta_j.size());
+    up(L.toff, h.toff.data(), sizeof(int64_t) * h.toff.size());
+    up(L.bcutmax, h.maxcut.data(), sizeof(int32_t) * h.maxcut.size());
+  };
+  upload_layout(R, hf);
+  upload_layout(D, hd);
   if (cudaMemsetAsync(P->status, 0, sizeof(int), P->stream) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
@@ -524,8 +591,13 @@ int plan_create_impl(int64_t N, int prec, double eps, cudaStream_t stream, int64
     return GBDLT_ERR_CUDA;
   }
   st = launch_twiddle_init(*P);
-  if (st == GBDLT_OK) st = launch_rec_state_init(*P);
+  if (st == GBDLT_OK) st = launch_fft_tables_init(*P);
+  if (st == GBDLT_OK) st = launch_rec_xm1(*P, R, 0);
+  if (st == GBDLT_OK) st = launch_rec_state_init(*P, R);
   if (st == GBDLT_OK) st = launch_legpts(*P, P->CN);
+  // the direct layout's rows are the Legendre nodes just computed
+  if (st == GBDLT_OK && P->has_direct) st = launch_rec_xm1(*P, D, 1);
+  if (st == GBDLT_OK && P->has_direct) st = launch_rec_state_init(*P, D);
   if (st == GBDLT_OK && cudaStreamSynchronize(P->stream) != cudaSuccess) st = GBDLT_ERR_CUDA;
   if (st == GBDLT_OK) {
     int hs = 0;
@@ -557,7 +629,7 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   T* vrec = (T*)P.tmp;
   T* v = (T*)P.v;
-  int st = launch_rec_forward<T>(P, c, vrec, nb);
+  int st = launch_rec_forward<T>(P, P.rec, c, vrec, nb);
   if (st) return st;
   const C2<T>* Y = nullptr;
   if (KM > 0) {
@@ -610,7 +682,7 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   void* U = Y ? other(P, Y) : P.bufA;
   st = launch_l2ct_pro<T>(P, Y, g, use_w, z, (C2<T>*)U, nb);
   if (st) return st;
-  st = launch_rec_transpose<T>(P, z, rect, nb);
+  st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
   if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), nb * KM, -1);
@@ -629,7 +701,7 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   void* U = other(P, Y);
   st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, nb);
   if (st) return st;
-  st = launch_rec_transpose<T>(P, z, rect, nb);
+  st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
   if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), nb * KM, -1);
@@ -646,8 +718,36 @@ int run_chebeval_t(Plan& P, const T* g, T* out, int64_t nb) {
 }
 
 
+// Direct method: the sums of Eq. (1) and (2) by the recurrence at the Legendre
+// nodes over all columns (rows k and N-1-k share one recurrence).
+//   DLT     f = P c
+//   DLT^T   out = P^T g
+//   IDLT    c = D_s P^T D_w f  (weights on the rows, n + 1/2 on the reduction)
+//   IDLT^T  out = D_w P D_s g
 template <typename T>
-int run_one(Plan& P, int op, const T* in, T* out, int64_t nb) {
+int run_direct(Plan& P, int op, const T* in, T* out, int64_t nb) {
+  RecLayout& D = P.drec;
+  switch (op) {
+    case OP_DLT:
+      return launch_rec_forward<T>(P, D, in, out, nb);
+    case OP_DLT_T:
+      return launch_rec_transpose<T>(P, D, in, out, nb, nullptr, 0);
+    case OP_IDLT:
+      return launch_rec_transpose<T>(P, D, in, out, nb, P.w, 1);
+    case OP_IDLT_T: {
+      T* sg = (T*)P.tmp2;
+      int st = launch_scale<T>(P, in, sg, 1, nb);
+      if (st) return st;
+      st = launch_rec_forward<T>(P, D, sg, out, nb);
+      if (st) return st;
+      return launch_scale<T>(P, out, out, 2, nb);
+    }
+  }
+  return GBDLT_ERR_INVALID_ARG;
+}
+
+template <typename T>
+int run_one(Plan& P, int op, int method, const T* in, T* out, int64_t nb) {
   const int64_t N = P.p.N;
   if (N == 1) {
     // every operator is the identity at N = 1 (P_0 = T_0 = 1, w_0 = 2, s_0 = 1/2)
@@ -655,6 +755,12 @@ int run_one(Plan& P, int op, const T* in, T* out, int64_t nb) {
                ? GBDLT_OK
                : GBDLT_ERR_CUDA;
   }
+  const bool transform = op == OP_DLT || op == OP_DLT_T || op == OP_IDLT || op == OP_IDLT_T;
+  if (transform && method == GBDLT_METHOD_DIRECT) {
+    if (!P.has_direct) return GBDLT_ERR_UNSUPPORTED_N;
+    return run_direct<T>(P, op, in, out, nb);
+  }
+  if (!P.p.fast) return GBDLT_ERR_UNSUPPORTED_N;  // the FFT-based chains need a power of two
   switch (op) {
     case OP_L2C:
       return run_leg2cheb<T>(P, in, out, nb);
@@ -691,7 +797,13 @@ int run_one(Plan& P, int op, const T* in, T* out, int64_t nb) {
 }  // namespace
 
 int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch) {
+  if (!plan) return GBDLT_ERR_INVALID_ARG;
+  return run_op_method(plan, op, reinterpret_cast<Plan*>(plan)->p.method, in, out, batch);
+}
+
+int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out, int64_t batch) {
   if (!plan || batch < 0) return GBDLT_ERR_INVALID_ARG;
+  if (method != GBDLT_METHOD_FAST && method != GBDLT_METHOD_DIRECT) return GBDLT_ERR_INVALID_ARG;
   if (batch == 0) return GBDLT_OK;  // nothing to do; the pointers are not read
   if (!in || !out) return GBDLT_ERR_INVALID_ARG;
   Plan& P = *reinterpret_cast<Plan*>(plan);
@@ -707,9 +819,9 @@ int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch) {
     const int64_t nb = std::min<int64_t>(P.bcap, batch - i);
     int st;
     if (P.p.prec == GBDLT_FP64)
-      st = run_one<double>(P, op, (const double*)in + i * N, (double*)out + i * N, nb);
+      st = run_one<double>(P, op, method, (const double*)in + i * N, (double*)out + i * N, nb);
     else
-      st = run_one<float>(P, op, (const float*)in + i * N, (float*)out + i * N, nb);
+      st = run_one<float>(P, op, method, (const float*)in + i * N, (float*)out + i * N, nb);
     if (st) return st;
   }
   return check_launch();
@@ -746,25 +858,35 @@ static void fill_public(const Params& q, size_t ws, gbdlt_params* out) {
   out->bytes_dlt = q.bytes_dlt;
   out->bytes_idlt = q.bytes_idlt;
   out->workspace_bytes = ws;
+  out->method = q.method;
+  out->direct_steps = q.direct_steps;
 }
 
-int gbdlt_plan_params(int64_t N, int prec, double eps, gbdlt_params* out) {
+int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out) {
   if (!out) return GBDLT_ERR_INVALID_ARG;
   Params q;
-  int st = derive_params(N, prec, eps, &q);
+  int st = derive_params(N, prec, eps, method, &q);
   if (st) return st;
   fill_public(q, 0, out);
   return GBDLT_OK;
 }
 
-int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_plan* out) {
+int gbdlt_plan_params(int64_t N, int prec, double eps, gbdlt_params* out) {
+  return gbdlt_plan_params_ex(N, prec, eps, GBDLT_METHOD_AUTO, out);
+}
+
+int gbdlt_plan_create_ex(int64_t N, int prec, double eps, int method, void* cuda_stream, gbdlt_plan* out) {
   if (!out) return GBDLT_ERR_INVALID_ARG;
   *out = nullptr;
   Plan* P = nullptr;
-  int st = plan_create_impl(N, prec, eps, (cudaStream_t)cuda_stream, 0, &P);
+  int st = plan_create_impl(N, prec, eps, method, (cudaStream_t)cuda_stream, 0, 0, &P);
   if (st) return st;
   *out = reinterpret_cast<gbdlt_plan>(P);
   return GBDLT_OK;
+}
+
+int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_plan* out) {
+  return gbdlt_plan_create_ex(N, prec, eps, GBDLT_METHOD_AUTO, cuda_stream, out);
 }
 
 int gbdlt_plan_destroy(gbdlt_plan plan) {

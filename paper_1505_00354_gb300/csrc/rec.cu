@@ -31,6 +31,7 @@ constexpr int RT = 256;  // threads per CTA = half rows per row block
 
 struct RecArgs {
   int64_t N, H;
+  int64_t mid;         // the half row that is its own mirror (odd N), else -1
   int S;
   int64_t nblocks;
   int64_t nseg_total;  // batch stride of the segment partials
@@ -46,6 +47,9 @@ struct RecArgs {
   const double* rb;
   const float2* raf;
   const float2* rbf;
+  const double* xm1;   // [H] x_k - 1
+  const double* zw;    // transposed input weights (w_k for the direct IDLT), or null
+  int scale_out;       // transposed reduction: 1 multiplies out_n by n + 1/2
 };
 
 // ---------------------------------------------------------------------------
@@ -87,21 +91,25 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
-RecArgs rec_args(const Plan& P) {
+RecArgs rec_args(const Plan& P, const RecLayout& L) {
   RecArgs a;
   a.N = P.p.N;
-  a.H = P.rec.H;
-  a.S = P.rec.S;
-  a.nblocks = P.rec.nblocks;
-  a.nseg_total = P.rec.nseg_total;
-  a.tbuf_total = P.rec.tbuf_total;
-  a.cut = P.rec.cut;
-  a.poff = P.rec.poff;
-  a.state = P.rec.state;
-  a.cta_rb = P.rec.cta_rb;
-  a.cta_j = P.rec.cta_j;
-  a.toff = P.rec.toff;
-  a.maxcut = P.rec.bcutmax;
+  a.H = L.H;
+  a.mid = (P.p.N & 1) ? L.H - 1 : -1;
+  a.S = L.S;
+  a.nblocks = L.nblocks;
+  a.nseg_total = L.nseg_total;
+  a.tbuf_total = L.tbuf_total;
+  a.cut = L.cut;
+  a.poff = L.poff;
+  a.state = L.state;
+  a.cta_rb = L.cta_rb;
+  a.cta_j = L.cta_j;
+  a.toff = L.toff;
+  a.maxcut = L.bcutmax;
+  a.xm1 = L.xm1;
+  a.zw = nullptr;
+  a.scale_out = 0;
   a.ra = P.ra;
   a.rb = P.rb;
   a.raf = P.ra_ff;
@@ -109,9 +117,13 @@ RecArgs rec_args(const Plan& P) {
   return a;
 }
 
-__device__ __forceinline__ double xm1_of(int64_t k, int64_t N) {
-  const double s = sinpi((double)(2 * k + 1) / (double)(4 * N));
-  return -2.0 * s * s;
+// x - 1 = -2 sin^2(theta/2) per half row: theta_k = (k+1/2)pi/N (cheb1 grid of
+// the fast path) or the Legendre node theta_k (direct method)
+__global__ void k_rec_xm1(double* __restrict__ xm1, const double* __restrict__ theta, int64_t H, int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= H) return;
+  const double s = theta ? sin(0.5 * theta[k]) : sinpi((double)(2 * k + 1) / (double)(4 * N));
+  xm1[k] = -2.0 * s * s;
 }
 
 __device__ __forceinline__ int nseg_of(const RecArgs& R, int64_t k) {
@@ -125,7 +137,7 @@ __global__ void k_rec_basis(RecArgs R, double2* __restrict__ Tbuf) {
   const int64_t k = rbk * RT + threadIdx.x;
   if (k >= R.H) return;
   if (j >= nseg_of(R, k) - 1) return;
-  const double xm1 = xm1_of(k, R.N);
+  const double xm1 = R.xm1[k];
   double P1 = 1.0, D1 = 0.0, P2 = 0.0, D2 = 1.0;
   const int64_t n0 = (int64_t)j * R.S;
   for (int64_t n = n0; n < n0 + R.S; ++n) {
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__
   if (j >= (cut + R.S - 1) / R.S) return;
   const int64_t o = R.poff[k] + j;
   const double2 st = R.state[o];
-  const double xm1 = xm1_of(k, R.N);
+  const double xm1 = R.xm1[k];
   double P = st.x, G = st.y / xm1;
   const int64_t n0 = (int64_t)j * R.S;
   const int64_t n1 = min(n0 + R.S, (int64_t)cut);
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __res
   const int64_t o = R.poff[k] + j;
   const double2 st = R.state[o];
   ffv P = ff_from(st.x), D = ff_from(st.y);
-  const ffv xm1 = ff_from(xm1_of(k, R.N));
+  const ffv xm1 = ff_from(R.xm1[k]);
   const int64_t n0 = (int64_t)j * R.S;
   const int64_t n1 = min(n0 + R.S, (int64_t)cut);
   float Es = 0.f, Ec = 0.f, Os = 0.f, Oc = 0.f;
@@ -261,7 +273,7 @@ __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T*
     }
   }
   vrec[k] = (T)(E + O);
-  vrec[R.N - 1 - k] = (T)(E - O);
+  if (k != R.mid) vrec[R.N - 1 - k] = (T)(E - O);
 }
 
 // transposed: out_n = sum_k z_k P_n(x_k) over rows with n < cut(k).  A CTA takes
@@ -298,11 +310,15 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
     active = j < (cut + R.S - 1) / R.S;
   }
   if (active) {
-    const double a = (double)z[k], b = (double)z[R.N - 1 - k];
-    zp = a + b;
-    zm = a - b;
+    double a = (double)z[k], b = (double)z[R.N - 1 - k];
+    if (R.zw) {
+      a *= R.zw[k];
+      b *= R.zw[R.N - 1 - k];
+    }
+    zp = k == R.mid ? a : a + b;
+    zm = k == R.mid ? a : a - b;
     const double2 st = R.state[R.poff[k] + j];
-    xm1 = xm1_of(k, R.N);
+    xm1 = R.xm1[k];
     P = st.x;
     G = st.y / xm1;
   } else {
@@ -364,13 +380,17 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
     active = j < (cut + R.S - 1) / R.S;
   }
   if (active) {
-    const float a = z[k], b = z[R.N - 1 - k];
-    zp = a + b;
-    zm = a - b;
+    float a = z[k], b = z[R.N - 1 - k];
+    if (R.zw) {
+      a = (float)((double)a * R.zw[k]);
+      b = (float)((double)b * R.zw[R.N - 1 - k]);
+    }
+    zp = k == R.mid ? a : a + b;
+    zm = k == R.mid ? a : a - b;
     const double2 st = R.state[R.poff[k] + j];
     P = ff_from(st.x);
     D = ff_from(st.y);
-    xm1 = ff_from(xm1_of(k, R.N));
+    xm1 = ff_from(R.xm1[k]);
   } else {
     cut = 0;
   }
@@ -423,21 +443,28 @@ __global__ void k_rec_t_reduce(RecArgs R, const double* __restrict__ tbuf, T* __
     double t = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) t += red[q][lane];
+    if (R.scale_out) t *= (double)n + 0.5;
     out[n] = (T)t;
   }
 }
 
 }  // namespace
 
-int launch_rec_state_init(Plan& P) {
-  RecLayout& L = P.rec;
+int launch_rec_xm1(Plan& P, RecLayout& L, int legendre) {
+  if (L.H == 0) return GBDLT_OK;
+  k_rec_xm1<<<(unsigned)((L.H + 255) / 256), 256, 0, P.stream>>>(L.xm1, legendre ? P.theta : nullptr, L.H, P.p.N);
+  count_launch();
+  return check_launch();
+}
+
+int launch_rec_state_init(Plan& P, RecLayout& L) {
   if (L.H == 0 || L.nseg_total == 0) return GBDLT_OK;
   double2* Tbuf = nullptr;
   if (cudaMalloc(&Tbuf, sizeof(double2) * 2 * (size_t)L.nseg_total) != cudaSuccess) {
     cudaGetLastError();
     return GBDLT_ERR_OOM;
   }
-  RecArgs R = rec_args(P);
+  RecArgs R = rec_args(P, L);
   k_rec_basis<<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, Tbuf);
   count_launch();
   k_rec_scan<<<(unsigned)((L.H + 127) / 128), 128, 0, P.stream>>>(R, Tbuf, L.state);
@@ -449,16 +476,15 @@ int launch_rec_state_init(Plan& P) {
 }
 
 template <typename T>
-int launch_rec_forward(Plan& P, const T* c, T* vrec, int64_t nb) {
-  RecLayout& L = P.rec;
-  RecArgs R = rec_args(P);
+int launch_rec_forward(Plan& P, RecLayout& L, const T* c, T* vrec, int64_t nb) {
+  RecArgs R = rec_args(P, L);
   if (L.H == 0) return GBDLT_OK;
   if constexpr (sizeof(T) == 4) {
     k_rec_fwd_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, (const float*)c, L.part);
   } else {
     k_rec_fwd<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, c, L.part);
   }
-  launched(P, "rec_fwd", (double)nb * 7.0 * (double)(P.p.rec_steps / 2),
+  launched(P, "rec_fwd", (double)nb * 7.0 * (double)L.half_steps,
            (double)nb * ((double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total));
   if (L.n_long > 0) {
     const int64_t threads = L.n_long * 32;
@@ -477,9 +503,11 @@ int launch_rec_forward(Plan& P, const T* c, T* vrec, int64_t nb) {
 }
 
 template <typename T>
-int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb) {
-  RecLayout& L = P.rec;
-  RecArgs R = rec_args(P);
+int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb, const double* zw,
+                         int scale_out) {
+  RecArgs R = rec_args(P, L);
+  R.zw = zw;
+  R.scale_out = scale_out;
   if (L.H == 0) return GBDLT_OK;
   const size_t smem = sizeof(T) * (8 * 32 * TP + 8 * (size_t)L.S) + (sizeof(T) == 8 ? 16 * RT : 0);
   static bool attr_set = false;
@@ -496,7 +524,7 @@ int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb) {
     }
     k_rec_t<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, z, L.tbuf);
   }
-  launched(P, "rec_t", (double)nb * 7.0 * (double)(P.p.rec_steps / 2),
+  launched(P, "rec_t", (double)nb * 7.0 * (double)L.half_steps,
            (double)nb * ((double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total));
   k_rec_t_reduce<T><<<dim3((unsigned)((P.p.N + 31) / 32), (unsigned)nb), 256, 0, P.stream>>>(R, L.tbuf, out);
   launched(P, "rec_t_reduce", (double)nb * (double)L.tbuf_total,
@@ -504,9 +532,9 @@ int launch_rec_transpose(Plan& P, const T* z, T* out, int64_t nb) {
   return check_launch();
 }
 
-template int launch_rec_forward<double>(Plan&, const double*, double*, int64_t);
-template int launch_rec_forward<float>(Plan&, const float*, float*, int64_t);
-template int launch_rec_transpose<double>(Plan&, const double*, double*, int64_t);
-template int launch_rec_transpose<float>(Plan&, const float*, float*, int64_t);
+template int launch_rec_forward<double>(Plan&, RecLayout&, const double*, double*, int64_t);
+template int launch_rec_forward<float>(Plan&, RecLayout&, const float*, float*, int64_t);
+template int launch_rec_transpose<double>(Plan&, RecLayout&, const double*, double*, int64_t, const double*, int);
+template int launch_rec_transpose<float>(Plan&, RecLayout&, const float*, float*, int64_t, const double*, int);
 
 }  // namespace gbdlt

@@ -59,17 +59,16 @@ def test_uneven_batch(gb, prec):
     y2 = b.run(xd)
     assert torch.equal(y, y2)  # replays are deterministic
     off = b.offsets
-    # every transform against the single-vector call
-    for N in sorted(set(Ns.tolist())):
-        p = gb.get_plan(int(N), prec)
-        for d in (0, 1):
-            idx = np.nonzero((Ns == N) & (dirs == d))[0]
-            if idx.size == 0:
-                continue
-            X = torch.stack([xd[off[i]:off[i + 1]] for i in idx])
-            Y = p.dlt(X) if d == 0 else p.idlt(X)
-            got = torch.stack([y[off[i]:off[i + 1]] for i in idx])
-            assert torch.equal(got, Y), (N, d)
+    # every transform against the single-vector call of the method its group ran
+    # (the autotuner times both methods per group and keeps the faster)
+    for G in b.groups():
+        N, d = G["N"], G["dir"]
+        p = gb.get_plan(int(N), prec, method=G["method"])
+        idx = np.nonzero((Ns == N) & (dirs == d))[0]
+        X = torch.stack([xd[off[i]:off[i + 1]] for i in idx])
+        Y = p.dlt(X) if d == 0 else p.idlt(X)
+        got = torch.stack([y[off[i]:off[i + 1]] for i in idx])
+        assert torch.equal(got, Y), (N, d, G["method"])
     # a seeded sample against the oracle
     rng = np.random.default_rng(41)
     worst = 0.0
@@ -85,6 +84,8 @@ def test_uneven_batch(gb, prec):
             err = np.max(np.abs(yi - ref) / ((np.arange(N) + 0.5) * np.abs(nd.w * xi).sum()))
         worst = max(worst, err)
     print(f"prec={prec} uneven batch: {info}, worst sampled error {worst:.2e}")
+    print("groups (N, dir, method, ms fast, ms direct):",
+          [(G["N"], G["dir"], G["method"], round(G["ms_fast"], 3), round(G["ms_direct"], 3)) for G in b.groups()])
     assert worst <= (1e-12 if prec == 0 else 5e-6)
 
 
@@ -94,7 +95,11 @@ def test_batch_errors(gb):
     h = ctypes.c_void_p()
     Ns = (ctypes.c_int64 * 2)(16, 24)
     dirs = (ctypes.c_int32 * 2)(0, 1)
-    assert L.gbdlt_batch_create(Ns, dirs, 2, 0, 0.0, ctypes.byref(h)) == -2
+    # 24 is open to the direct method only; 65537 to neither
+    assert L.gbdlt_batch_create_ex(Ns, dirs, 2, 0, 0.0, 1, ctypes.byref(h)) == -2
+    big = (ctypes.c_int64 * 2)(16, 65537)
+    assert L.gbdlt_batch_create(big, dirs, 2, 0, 0.0, ctypes.byref(h)) == -2
+    assert L.gbdlt_batch_create_ex(Ns, dirs, 2, 0, 0.0, 5, ctypes.byref(h)) == -1
     Ns = (ctypes.c_int64 * 2)(16, 32)
     bad = (ctypes.c_int32 * 2)(0, 2)
     assert L.gbdlt_batch_create(Ns, bad, 2, 0, 0.0, ctypes.byref(h)) == -1

@@ -98,7 +98,7 @@ def _c(N, seed, decay=0.0):
 def test_leg2cheb_full(gb, N):
     import oracle
     c = _c(N, 1)
-    got = host(gb.Plan(N).leg2cheb(dev(c)))
+    got = host(gb.Plan(N, method=gb.METHOD_FAST).leg2cheb(dev(c)))
     err = np.max(np.abs(got - oracle.leg2cheb(c))) / np.abs(c).sum()
     print(f"N={N} leg2cheb err/||c||1 = {err:.2e}")
     assert err <= TOL64
@@ -108,7 +108,7 @@ def test_leg2cheb_full(gb, N):
 def test_chebeval_full(gb, N):
     import oracle
     c = _c(N, 2)
-    got = host(gb.Plan(N).chebeval(dev(c)))
+    got = host(gb.Plan(N, method=gb.METHOD_FAST).chebeval(dev(c)))
     ref = oracle.ndct_rows(c, onodes(N))
     err = np.max(np.abs(got - ref)) / np.abs(c).sum()
     print(f"N={N} chebeval err/||c||1 = {err:.2e}")
@@ -120,7 +120,7 @@ def test_chebeval_full(gb, N):
 def test_dlt_full(gb, N, decay):
     import oracle
     c = _c(N, 3, decay)
-    got = host(gb.Plan(N).dlt(dev(c)))
+    got = host(gb.Plan(N, method=gb.METHOD_FAST).dlt(dev(c)))
     ref = oracle.dlt_rows(c, onodes(N))
     err = np.max(np.abs(got - ref)) / np.abs(c).sum()
     print(f"N={N} decay={decay} dlt err/||c||1 = {err:.2e}")
@@ -139,7 +139,7 @@ def test_idlt_full(gb, N):
     import paper_1505_00354_gb300.inputs as inp
     f = inp.values(N, 4)
     nd = onodes(N)
-    got = host(gb.Plan(N).idlt(dev(f)))
+    got = host(gb.Plan(N, method=gb.METHOD_FAST).idlt(dev(f)))
     ref = oracle.idlt(f, nd)
     err = _idlt_err(got, ref, nd.w, f)
     print(f"N={N} idlt err = {err:.2e} (abs {np.max(np.abs(got - ref)):.2e})")
@@ -149,7 +149,7 @@ def test_idlt_full(gb, N):
 @pytest.mark.parametrize("N", [16, 256, 1024, 4096])
 def test_idlt_dlt_roundtrip(gb, N):
     c = _c(N, 5)
-    p = gb.Plan(N)
+    p = gb.Plan(N, method=gb.METHOD_FAST)
     back = host(p.idlt(p.dlt(dev(c))))
     err = np.max(np.abs(back - c)) / np.abs(c).sum()
     print(f"N={N} idlt(dlt(c)) - c: {err:.2e}")
@@ -161,7 +161,7 @@ def test_transposes_full(gb, N):
     import oracle
     nd = onodes(N)
     g = _c(N, 6)
-    p = gb.Plan(N)
+    p = gb.Plan(N, method=gb.METHOD_FAST)
     s = np.abs(g).sum()
     e1 = np.max(np.abs(host(p.dlt_t(dev(g))) - oracle.dlt_t(g, nd))) / s
     e2 = np.max(np.abs(host(p.chebeval_t(dev(g))) - oracle.ndct_t(g, nd))) / s
@@ -188,7 +188,7 @@ def test_dlt_sampled(gb, N, nrows, decay):
     p2 = int(math.log2(N))
     c = inp.coeffs(N, (10 if decay else 20) + p2, decay)
     rows = inp.sample_rows(N, nrows, seed=1000 + p2)
-    got = host(gb.Plan(N).dlt(dev(c)))
+    got = host(gb.Plan(N, method=gb.METHOD_FAST).dlt(dev(c)))
     ref = oracle.dlt_rows(c, onodes(N, tuple(rows.tolist())))
     err = np.max(np.abs(got[rows] - ref)) / np.abs(c).sum()
     print(f"N={N} decay={decay} rows={rows.size} dlt err/||c||1 = {err:.2e}")
@@ -204,7 +204,7 @@ def test_idlt_forward_residual(gb, N, nrows):
     p2 = int(math.log2(N))
     f = inp.values(N, 30 + p2)
     rows = inp.sample_rows(N, nrows, seed=2000 + p2)
-    c = host(gb.Plan(N).idlt(dev(f)))
+    c = host(gb.Plan(N, method=gb.METHOD_FAST).idlt(dev(f)))
     resid = oracle.dlt_rows(c, onodes(N, tuple(rows.tolist()))) - f[rows]
     err = np.max(np.abs(resid)) / np.abs(c).sum()
     print(f"N={N} idlt forward residual / ||c||1 = {err:.2e}")
@@ -215,7 +215,7 @@ def test_idlt_forward_residual(gb, N, nrows):
 def test_adjoint_identities(gb, N):
     """<A y, z> = <y, A^T z> for every operator pair, at sizes beyond the oracle."""
     import paper_1505_00354_gb300.inputs as inp
-    p = gb.Plan(N)
+    p = gb.Plan(N, method=gb.METHOD_FAST)
     y, z = dev(inp.coeffs(N, 7)), dev(inp.coeffs(N, 8))
     for fwd, tr in ((p.dlt, p.dlt_t), (p.chebeval, p.chebeval_t), (p.leg2cheb, p.leg2cheb_t),
                     (p.idlt, p.idlt_t)):
@@ -232,7 +232,7 @@ def test_adjoint_identities(gb, N):
 def test_fp32_form_full(gb, N):
     import oracle
     c = _c(N, 9, 1.0)
-    p = gb.Plan(N, gb.FP32)
+    p = gb.Plan(N, gb.FP32, method=gb.METHOD_FAST)
     got = host(p.dlt(dev(c, torch.float32)))
     c32 = c.astype(np.float32).astype(np.float64)
     nd = onodes(N)
@@ -252,7 +252,7 @@ def test_fp32_form_sampled(gb, N, nrows):
     p2 = int(math.log2(N))
     c = inp.coeffs(N, 40 + p2, 1.0).astype(np.float32).astype(np.float64)
     rows = inp.sample_rows(N, nrows, seed=3000 + p2)
-    got = host(gb.Plan(N, gb.FP32).dlt(dev(c, torch.float32)))
+    got = host(gb.Plan(N, gb.FP32, method=gb.METHOD_FAST).dlt(dev(c, torch.float32)))
     ref = oracle.dlt_rows(c, onodes(N, tuple(rows.tolist())))
     err = np.max(np.abs(got[rows] - ref)) / np.abs(c).sum()
     print(f"N={N} fp32 dlt err/||c||1 = {err:.2e}")
@@ -264,7 +264,7 @@ def test_fp32_form_sampled(gb, N, nrows):
 # --------------------------------------------------------------------------
 def test_batch_matches_single(gb):
     N = 1024
-    p = gb.Plan(N)
+    p = gb.Plan(N, method=gb.METHOD_FAST)
     C = dev(np.stack([_c(N, 100 + i) for i in range(3)]))
     Fb = p.dlt(C)
     for i in range(3):
@@ -277,10 +277,20 @@ def test_argument_errors(gb):
     import ctypes
     L = gb.lib()
     h = ctypes.c_void_p()
-    for bad in (0, 3, 1000, 2**25):
+    for bad in (0, 2**25):
         assert L.gbdlt_plan_create(bad, 0, 0.0, None, ctypes.byref(h)) == -2
+    for bad in (3, 1000):
+        assert L.gbdlt_plan_create_ex(bad, 0, 0.0, 1, None, ctypes.byref(h)) == -2
+    assert L.gbdlt_plan_create_ex(2**17, 0, 0.0, 2, None, ctypes.byref(h)) == -2
     assert L.gbdlt_plan_create(64, 7, 0.0, None, ctypes.byref(h)) == -1
-    p = gb.Plan(64)
+    # a plan for a length that is not a power of two runs the direct method; the
+    # FFT-based operators (leg2cheb, chebeval) are not open to it
+    q = gb.Plan(1000)
+    assert q.params()["method"] == 2
+    y = torch.zeros(1000, dtype=torch.float64, device="cuda")
+    with pytest.raises(gb.GbdltError):
+        q.leg2cheb(y)
+    p = gb.Plan(64, method=gb.METHOD_FAST)
     x = torch.zeros(64, dtype=torch.float64, device="cuda")
     assert L.gbdlt_dlt(p.handle, None, ctypes.c_void_p(x.data_ptr()), 1) == -1
     assert L.gbdlt_dlt(p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 1) == -1

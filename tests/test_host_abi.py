@@ -48,14 +48,35 @@ def test_launch_count_is_host_only(gb):
 def test_bad_arguments(gb):
     lib = gb.lib()
     p = gb._binding.Params()
-    for bad in (0, 3, 6, 1000, 2**25):
+    for bad in (0, 2**25):
         assert lib.gbdlt_plan_params(bad, 0, 0.0, ctypes.byref(p)) == -2
+    # the FFT-based chain needs a power of two; the direct method takes N <= 65536
+    for bad in (3, 6, 1000):
+        assert lib.gbdlt_plan_params_ex(bad, 0, 0.0, 1, ctypes.byref(p)) == -2
+    for bad in (65537, 2**17):
+        assert lib.gbdlt_plan_params_ex(bad, 0, 0.0, 2, ctypes.byref(p)) == -2
+    assert lib.gbdlt_plan_params_ex(64, 0, 0.0, 3, ctypes.byref(p)) == -1
     assert lib.gbdlt_plan_params(64, 2, 0.0, ctypes.byref(p)) == -1
     assert lib.gbdlt_plan_params(64, 0, 2.0, ctypes.byref(p)) == -1
     assert lib.gbdlt_plan_params(64, 0, 0.0, None) == -1
     assert lib.gbdlt_plan_destroy(None) == -1
     assert lib.gbdlt_plan_sync(None) == -1
     assert lib.gbdlt_dlt(None, None, None, 1) == -1
+
+
+def test_method_selection(gb):
+    """GBDLT_METHOD_AUTO: the direct method for N that is not a power of two or
+    N <= 256, the FFT-based chain otherwise; the direct method's work is
+    ceil(N/2) rows x N columns of the recurrence."""
+    for N, m in ((1, 2), (3, 2), (256, 2), (257, 2), (1000, 2), (512, 1), (4096, 1), (2**20, 1)):
+        q = gb.plan_params(N)
+        assert q["method"] == m, N
+        if m == 2:
+            assert q["direct_steps"] == ((N + 1) // 2) * N
+            assert q["K"] == 0 and q["M"] == 0
+    assert gb.plan_params(1024, method=2)["method"] == 2
+    assert gb.plan_params(256, method=1)["method"] == 1
+    assert gb.plan_params(2**17, method=1)["direct_steps"] == 0
 
 
 def _taylor_L(eps):
