@@ -109,6 +109,11 @@ __device__ __forceinline__ ddv dd_div_dd(double a, double b) {
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
+// per-row factors of the asymptotic expansion (stages.cu)
+struct alignas(32) RowAR {
+  double ax, ay, rx, ry;
+};
+
 struct Band {
   int64_t ns;  // columns n >= ns use the asymptotic expansion
   int64_t ka;  // rows [ka, kb) and [N-kb, N-ka)
@@ -197,6 +202,10 @@ struct Plan {
   // used by the fused radix-4 layers ([2 directions][4096][sx, sy, t, swap])
   double2* twfull = nullptr;
   double2* lf_tab = nullptr;
+  // FP64 stage tables: C_n h_{m,n} ([M][N], the asymptotic expansion's column
+  // weights) and per cheb1 row {alpha_k, rho_k} (the expansion's row factors)
+  double* Hnm = nullptr;
+  RowAR* row_ar = nullptr;
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
   RecLayout rec;    // recurrence region of the fast path (cheb1 rows)
   RecLayout drec;   // every row and column at the Legendre nodes (direct method)
@@ -264,6 +273,8 @@ void launched(Plan& P, const char* name, double flops, double bytes);
 int launch_twiddle_init(Plan& P);
 // fft.cu: the FP64 transform tables (twfull, lf_tab)
 int launch_fft_tables_init(Plan& P);
+// stages.cu: the FP64 stage tables (Hnm, row_ar)
+int launch_stage_tables_init(Plan& P);
 // legpts.cu
 int launch_legpts(Plan& P, double CN);
 int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N

@@ -19,15 +19,21 @@
 //      P_N(cos t) = C_N sum_m h_{m,N} cos((N+m+1/2)t - (m+1/2)pi/2) / (2 sin t)^{m+1/2},
 //      C_N = sqrt(4/pi) Gamma(N+1)/Gamma(N+3/2),
 //      h_{0,N} = 1, h_{m+1,N} = h_{m,N} (m+1/2)^2 / ((m+1)(N+m+3/2));
-//  * otherwise (the few nodes near theta = 0): the terminating hypergeometric
+//  * otherwise (the 8 nodes nearest theta = 0): the terminating hypergeometric
 //    series P_N(cos t) = sum_j (-N)_j (N+1)_j / (j!)^2 s^j, s = sin^2(t/2),
-//    summed in double-double (its terms reach ~1e10 before they cancel).
+//    summed in double-double (its terms reach ~1e10 before they cancel) by one
+//    warp per node (k_legpts_ends): lane l holds terms 3l..3l+2, obtains the
+//    first of them as a prefix product of the term ratios over the lanes below,
+//    and the sums are reduced across the warp.  These nodes start Newton from
+//    j_{0,k+1}/(N+1/2), the zeros of Hilb's Bessel approximation
+//    P_N(cos t) ~ sqrt(t / sin t) J_0((N+1/2) t).
 // Weight: w_k = 2 / (dP_N/dtheta)^2 at the root (Gauss-Legendre weight written
 // in theta).  Outputs per node: theta_k, x_k = cos theta_k, w_k and
 // t_k = N * (theta_k - (k+1/2)pi/N), the scaled offset from the cheb1 grid used
 // by the Taylor series of Sec. 2.1 (computed from the exact difference
 // theta*_k - theta^cheb1_k = pi (N-2k-1) / (4N(N+1/2)) plus delta, so it keeps
 // full relative accuracy).
+#include <cmath>
 #include <mutex>
 
 #include "gbdlt_internal.cuh"
@@ -74,8 +80,9 @@ __device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, doubl
   const double sg = (k & 1) ? -1.0 : 1.0;
   double cr = -sg * se, ci = sg * ce;  // e^{i phi_0}, phi_0 = (k+1/2)pi + eps
   const double rr = s, ri = -c;        // e^{i(theta - pi/2)}
-  const double g = 0.5 / s;
-  const double cot = c / s;
+  const double inv_s = 1.0 / s;
+  const double g = 0.5 * inv_s;
+  const double cot = c * inv_s;
   const double sg0 = sqrt(g);
   double gm = sg0;  // g^{m+1/2}
   double P = 0.0, dP = 0.0;
@@ -95,47 +102,24 @@ __device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, doubl
   return r;
 }
 
-__device__ PD eval_series(int64_t N, double s, double c, double sh, double ch) {
-  const double sq = sh * sh;  // s = sin^2(theta/2)
-  ddv t = {1.0, 0.0};
-  ddv sp = {1.0, 0.0};
-  ddv sj = {0.0, 0.0};
-  const double Nd = (double)N;
-  for (int j = 0; j < 400 && j < N; ++j) {
-    double num = -(Nd - j) * (Nd + j + 1.0);  // exact in double for N <= 2^26
-    double den = (double)(j + 1) * (double)(j + 1);
-    ddv ratio = dd_div_dd(num, den);
-    t = dd_mul_d(dd_mul(t, ratio), sq);
-    sp = dd_add(sp, t);
-    sj = dd_add(sj, dd_mul_d(t, (double)(j + 1)));
-    if (j > 4 && fabs(t.hi) < 1e-34) break;
-  }
-  PD r;
-  r.p = sp.hi + sp.lo;
-  r.dp = (ch / sh) * (sj.hi + sj.lo);  // dP/dtheta = cot(theta/2) sum_j j t_j
-  return r;
-}
-
-__global__ void k_legpts(int64_t N, double CN, HTab H, double* __restrict__ theta, double* __restrict__ x,
-                         double* __restrict__ w, double* __restrict__ tN, int* __restrict__ status) {
+// nodes k >= kend (k < kend: k_legpts_ends)
+__global__ void k_legpts(int64_t N, int64_t kend, double CN, HTab H, double* __restrict__ theta,
+                         double* __restrict__ x, double* __restrict__ w, double* __restrict__ tN,
+                         int* __restrict__ status) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t half = (N + 1) / 2;
-  if (k >= half) return;
+  if (k >= half || k < kend) return;
   const double Nh = (double)N + 0.5;
-  const double th0 = ((double)k + 0.75) * kPi / Nh;
+  const double inv_Nh = 1.0 / Nh;
+  const double th0 = ((double)k + 0.75) * kPi * inv_Nh;
   double s0, c0;
   sincos(th0, &s0, &c0);
-  int mode;
-  if (N <= 64)
-    mode = 0;
-  else if ((double)N * s0 >= 25.0)
-    mode = 1;
-  else
-    mode = 2;
+  const int mode = N <= 64 ? 0 : 1;
   // interior nodes start from the zero of the first two terms of the expansion:
   // cos(phi_0) + h_1 cos(phi_1) / (2 sin theta) = 0 gives, to first order,
   // (N+1/2) delta = cot(theta) / (8 (N+3/2)), i.e. about 1000 times closer than theta*
-  double d = mode == 1 ? (c0 / s0) / (8.0 * Nh * ((double)N + 1.5)) : 0.0;
+  const double cot0 = c0 / s0;
+  double d = mode == 1 ? cot0 * (0.125 * inv_Nh) / ((double)N + 1.5) : 0.0;
   bool ok = false;
   PD r;
   double s = s0, c = c0, sh = 0, ch = 0, dp_final = 0.0;
@@ -143,26 +127,31 @@ __global__ void k_legpts(int64_t N, double CN, HTab H, double* __restrict__ thet
     // sin/cos of theta = th0 + d by the angle-addition formula; |d| <= 1/(3 pi (2N+1))
     // (Lemma 2.3), so the Taylor polynomials below are exact to < 1e-20
     const double d2 = d * d;
-    const double sd =
-        d * (1.0 - d2 / 6.0 * (1.0 - d2 / 20.0 * (1.0 - d2 / 42.0 * (1.0 - d2 / 72.0))));
+    const double sd = d * (1.0 - d2 * (1.0 / 6.0) *
+                                     (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
     const double cd =
-        1.0 - d2 / 2.0 * (1.0 - d2 / 12.0 * (1.0 - d2 / 30.0 * (1.0 - d2 / 56.0 * (1.0 - d2 / 90.0))));
+        1.0 - d2 * 0.5 *
+                  (1.0 - d2 * (1.0 / 12.0) *
+                             (1.0 - d2 * (1.0 / 30.0) * (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
     s = s0 * cd + c0 * sd;
     c = c0 * cd - s0 * sd;
-    if (mode != 1) {
+    if (mode == 0) {
       double th = th0 + d;
       sincos(0.5 * th, &sh, &ch);
-    }
-    if (mode == 0)
       r = eval_rec(N, s, c, sh);
-    else if (mode == 1)
+    } else {
       r = eval_asy(N, k, d, s, c, CN, H);
-    else
-      r = eval_series(N, s, c, sh, ch);
+    }
     const double step = r.p / r.dp;
     d -= step;
     if (!(fabs(d) < 1.0)) break;  // diverged (NaN or runaway)
-    if (fabs(step) <= 1e-11 / (double)N) {
+    // Newton's error after this step is about (f''/2f') step^2 = (cot(theta)/2) step^2
+    // (at a root Legendre's equation gives P'' = -cot(theta) P').  Stop once that
+    // is far below the rounding floor of the evaluation (~u/N in theta) and the
+    // step is small enough for the one-step derivative update below to keep the
+    // weight to ~1e-17 relative ((step N)^2 / 2).
+    const double a_step = fabs(step);
+    if (a_step * (double)N <= 1e-8 && (0.5 * fabs(c / s) + 1.0) * a_step * a_step * (double)N <= 1e-18) {
       // dP/dtheta at the updated point by one Taylor step, with the second
       // derivative from Legendre's equation in theta:
       //   P'' = -cot(theta) P' - N(N+1) P   (step^2 N^3 is below 1e-20 here)
@@ -179,7 +168,7 @@ __global__ void k_legpts(int64_t N, double CN, HTab H, double* __restrict__ thet
   const double th = th0 + d;
   const double wk = 2.0 / (dp_final * dp_final);
   const double xk = c;
-  const double tk = kPi * (double)(N - 2 * k - 1) / (4.0 * Nh) + (double)N * d;
+  const double tk = kPi * (double)(N - 2 * k - 1) * (0.25 * inv_Nh) + (double)N * d;
   theta[k] = th;
   x[k] = xk;
   w[k] = wk;
@@ -191,6 +180,118 @@ __global__ void k_legpts(int64_t N, double CN, HTab H, double* __restrict__ thet
     w[km] = wk;
     tN[km] = -tk;
   }
+}
+
+// zeros j_{0,m}, m = 1..10, of the Bessel function J_0 (DLMF 10.21)
+__constant__ double kJ0Zeros[10] = {2.404825557695772768622, 5.520078110286310649597, 8.653727912911012216954,
+                                    11.79153443901428161374, 14.93091770848778594776, 18.07106396791092254315,
+                                    21.21163662987925895908, 24.35247153074930273706, 27.49347913204025479588,
+                                    30.63460646843197511755};
+constexpr int kMaxEnds = 10;
+
+__device__ __forceinline__ ddv shfl_up_dd(ddv v, int off) {
+  return {__shfl_up_sync(0xffffffffu, v.hi, off), __shfl_up_sync(0xffffffffu, v.lo, off)};
+}
+__device__ __forceinline__ ddv shfl_xor_dd(ddv v, int m) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+// P_N(cos t) and dP_N/dt from the hypergeometric series by one warp (every lane
+// returns lane 0's values).  Term ratio t_{j+1}/t_j = -(N-j)(N+j+1)/(j+1)^2 s;
+// with N sin t < 25 the terms fall below 1e-90 of the largest before j = 96.
+__device__ PD eval_series_warp(int64_t N, double sh, double ch, int lane) {
+  const double sq = sh * sh;  // s = sin^2(t/2)
+  const double Nd = (double)N;
+  ddv rho[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int j = 3 * lane + q;
+    if ((int64_t)j < N) {
+      const double num = -(Nd - j) * (Nd + j + 1.0);  // exact in double for N <= 2^26
+      const double den = (double)(j + 1) * (double)(j + 1);
+      rho[q] = dd_mul_d(dd_div_dd(num, den), sq);
+    } else {
+      rho[q] = {0.0, 0.0};  // (-N)_j = 0 for j > N
+    }
+  }
+  // inclusive prefix product of the lanes' ratio products, then the exclusive one
+  ddv R = dd_mul(dd_mul(rho[0], rho[1]), rho[2]);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const ddv v = shfl_up_dd(R, off);
+    if (lane >= off) R = dd_mul(v, R);
+  }
+  ddv t0 = shfl_up_dd(R, 1);
+  if (lane == 0) t0 = {1.0, 0.0};
+  const ddv t1 = dd_mul(t0, rho[0]);
+  const ddv t2 = dd_mul(t1, rho[1]);
+  ddv S = dd_add(dd_add(t0, t1), t2);
+  const double j0 = 3.0 * lane;
+  ddv W = dd_add(dd_add(dd_mul_d(t0, j0), dd_mul_d(t1, j0 + 1.0)), dd_mul_d(t2, j0 + 2.0));
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    S = dd_add(S, shfl_xor_dd(S, m));
+    W = dd_add(W, shfl_xor_dd(W, m));
+  }
+  PD r;
+  r.p = __shfl_sync(0xffffffffu, S.hi + S.lo, 0);
+  r.dp = __shfl_sync(0xffffffffu, (ch / sh) * (W.hi + W.lo), 0);  // dP/dt = cot(t/2) sum_j j t_j
+  return r;
+}
+
+// one warp per node k < kend (N sin theta*_k < 25, N > 64)
+__global__ void __launch_bounds__(32) k_legpts_ends(int64_t N, double* __restrict__ theta, double* __restrict__ x,
+                                                    double* __restrict__ w, double* __restrict__ tN,
+                                                    int* __restrict__ status) {
+  const int64_t k = blockIdx.x;
+  const int lane = threadIdx.x;
+  const double Nh = (double)N + 0.5;
+  const double inv_Nh = 1.0 / Nh;
+  const double th0 = ((double)k + 0.75) * kPi * inv_Nh;
+  double d = kJ0Zeros[k] * inv_Nh - th0;
+  bool ok = false;
+  double s = 0.0, c = 1.0, dp_final = 0.0;
+  for (int it = 0; it < 24; ++it) {
+    double sh, ch;
+    sincos(0.5 * (th0 + d), &sh, &ch);
+    s = 2.0 * sh * ch;
+    c = (ch - sh) * (ch + sh);
+    const PD r = eval_series_warp(N, sh, ch, lane);
+    const double step = r.p / r.dp;  // identical on every lane
+    d -= step;
+    if (!(fabs(d) < 1.0)) break;
+    const double a_step = fabs(step);
+    if (a_step * (double)N <= 1e-8 && (0.5 * fabs(c / s) + 1.0) * a_step * a_step * (double)N <= 1e-18) {
+      dp_final = r.dp + step * ((c / s) * r.dp + (double)N * ((double)N + 1.0) * r.p);
+      const double cn = c + s * step;
+      s = s - c * step;
+      c = cn;
+      ok = true;
+      break;
+    }
+  }
+  if (lane != 0) return;
+  if (!ok) atomicOr(status, 1);
+  const double th = th0 + d;
+  const double wk = 2.0 / (dp_final * dp_final);
+  const double tk = kPi * (double)(N - 2 * k - 1) * (0.25 * inv_Nh) + (double)N * d;
+  theta[k] = th;
+  x[k] = c;
+  w[k] = wk;
+  tN[k] = tk;
+  const int64_t km = N - 1 - k;
+  theta[km] = kPi - th;
+  x[km] = -c;
+  w[km] = wk;
+  tN[km] = -tk;
+}
+
+// nodes handled by k_legpts_ends: the first k with N sin theta*_k >= 25 (at most 8)
+int64_t end_nodes(int64_t N) {
+  if (N <= 64) return 0;
+  int64_t k = 0;
+  while (k < kMaxEnds && (double)N * std::sin(((double)k + 0.75) * kPi / ((double)N + 0.5)) < 25.0) ++k;
+  return k;
 }
 
 __global__ void k_dtheta(const double* __restrict__ tN, double* __restrict__ out, int64_t N) {
@@ -207,6 +308,19 @@ HTab htab(int64_t N) {
   return H;
 }
 
+// the node kernels on `stream` (callers count the launches)
+void launch_main_nodes(int64_t N, int64_t kend, double CN, double* theta, double* x, double* w, double* tN,
+                       int* status, cudaStream_t stream) {
+  const int64_t half = (N + 1) / 2;
+  const int threads = 128;
+  k_legpts<<<(unsigned)((half + threads - 1) / threads), threads, 0, stream>>>(N, kend, CN, htab(N), theta, x, w,
+                                                                               tN, status);
+}
+void launch_end_nodes(int64_t N, int64_t kend, double* theta, double* x, double* w, double* tN, int* status,
+                      cudaStream_t stream) {
+  if (kend > 0) k_legpts_ends<<<(unsigned)kend, 32, 0, stream>>>(N, theta, x, w, tN, status);
+}
+
 }  // namespace
 
 int launch_dtheta(Plan& P, double* out) {
@@ -218,11 +332,13 @@ int launch_dtheta(Plan& P, double* out) {
 
 int launch_legpts(Plan& P, double CN) {
   const int64_t N = P.p.N;
-  const int64_t half = (N + 1) / 2;
-  const int threads = 128;
-  const int64_t blocks = (half + threads - 1) / threads;
-  k_legpts<<<(unsigned)blocks, threads, 0, P.stream>>>(N, CN, htab(N), P.theta, P.x, P.w, P.tN, P.status);
+  const int64_t kend = end_nodes(N);
+  launch_main_nodes(N, kend, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream);
   launched(P, "legpts", 0.0, 32.0 * N);
+  if (kend > 0) {
+    launch_end_nodes(N, kend, P.theta, P.x, P.w, P.tN, P.status, P.stream);
+    launched(P, "legpts_ends", 0.0, 64.0 * kend);
+  }
   return check_launch();
 }
 
@@ -320,11 +436,13 @@ extern "C" int gbdlt_legpts_noalloc(int64_t N, double* x, double* theta, double*
     cudaGetLastError();
     return GBDLT_ERR_CUDA;
   }
-  const int64_t half = (N + 1) / 2;
-  const int threads = 128;
-  k_legpts<<<(unsigned)((half + threads - 1) / threads), threads, 0, stream>>>(
-      N, cn_running(N), htab(N), theta, x, w, tN, status);
+  const int64_t kend = end_nodes(N);
+  launch_main_nodes(N, kend, cn_running(N), theta, x, w, tN, status, stream);
   count_launch();
+  if (kend > 0) {
+    launch_end_nodes(N, kend, theta, x, w, tN, status, stream);
+    count_launch();
+  }
   if (dtheta) {
     k_dtheta<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(tN, dtheta, N);
     count_launch();

@@ -252,12 +252,12 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     double c_fft, c_rec;
     int Mmax;
     if (prec == GBDLT_FP64) {
-      c_fft = (5.7 * lg + 21.0) * (double)N;  // ~85 FP64 instructions per point at 2^20
-      c_rec = 10.5;                           // ~6.6 FP64 instructions per step
+      c_fft = (4.33 * lg + 16.0) * (double)N;  // ~64 FP64 instructions per point at 2^20
+      c_rec = 7.7;                             // ~4.8 FP64 instructions per step
       Mmax = 24;
     } else {
-      c_fft = (0.6 * lg + 2.3) * (double)N;   // memory and shared-memory bound FP32 passes
-      c_rec = 4.9;                            // float-float recurrence
+      c_fft = (0.43 * lg + 1.7) * (double)N;   // memory and shared-memory bound FP32 passes
+      c_rec = 3.4;                             // float-float recurrence
       Mmax = 16;
     }
     double best = (double)N * c_rec * (double)(N / 2);  // all recurrence
@@ -470,6 +470,9 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   const bool fp64_tabs = prec == GBDLT_FP64 && prm.fast;
   size_t o_twfull = A.take<double2>(fp64_tabs && N > 4096 ? N : 1);
   size_t o_lf = A.take<double2>(4 * 4096);
+  const bool stage_tabs = fp64_tabs && prm.K > 0 && prm.M > 0;
+  size_t o_hnm = A.take<double>(stage_tabs ? (int64_t)prm.M * N : 1);
+  size_t o_ar = A.take<RowAR>(stage_tabs ? N : 1);
   auto take_layout = [&](const RecLayout& L) {
     LayoutOff o;
     o.cut = A.take<int32_t>(L.H);
@@ -526,6 +529,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   P->tw4Nf_hi = (float2*)(base + o_tw4fhi);
   P->twfull = fp64_tabs && N > 4096 ? (double2*)(base + o_twfull) : nullptr;
   P->lf_tab = fp64_tabs ? (double2*)(base + o_lf) : nullptr;
+  P->Hnm = stage_tabs ? (double*)(base + o_hnm) : nullptr;
+  P->row_ar = stage_tabs ? (RowAR*)(base + o_ar) : nullptr;
   auto place_layout = [&](RecLayout& L, const LayoutOff& o) {
     L.cut = (int32_t*)(base + o.cut);
     L.poff = (int64_t*)(base + o.poff);
@@ -592,6 +597,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   }
   st = launch_twiddle_init(*P);
   if (st == GBDLT_OK) st = launch_fft_tables_init(*P);
+  if (st == GBDLT_OK) st = launch_stage_tables_init(*P);
   if (st == GBDLT_OK) st = launch_rec_xm1(*P, R, 0);
   if (st == GBDLT_OK) st = launch_rec_state_init(*P, R);
   if (st == GBDLT_OK) st = launch_legpts(*P, P->CN);

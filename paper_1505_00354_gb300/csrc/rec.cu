@@ -330,7 +330,14 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
   double* mytile = tile + (w * 32 + lane) * TP;
   double* mysum = wsum + w * R.S;
   const double* zw = reinterpret_cast<const double*>(zt + w * 32) + (lane & 1);
+  // columns past every cut of the warp's rows contribute nothing: the warp skips
+  // them as a whole (a per-lane test would still issue the FP64 instructions)
+  const int wcut = __reduce_max_sync(0xffffffffu, cut);
   for (int64_t n0 = n0s; n0 < seg_end; n0 += 32) {
+    if (n0 >= wcut) {
+      mysum[(n0 - n0s) + lane] = 0.0;
+      continue;
+    }
 #pragma unroll 4
     for (int i = 0; i < 32; ++i) {
       const int64_t n = n0 + i;
@@ -398,7 +405,12 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
   const int64_t seg_end = min(n0s + R.S, (int64_t)R.maxcut[rbk]);
   float* mytile = tile + (w * 32 + lane) * TP;
   float* mysum = wsum + w * R.S;
+  const int wcut = __reduce_max_sync(0xffffffffu, cut);
   for (int64_t n0 = n0s; n0 < seg_end; n0 += 32) {
+    if (n0 >= wcut) {
+      mysum[(n0 - n0s) + lane] = 0.f;
+      continue;
+    }
 #pragma unroll 4
     for (int i = 0; i < 32; ++i) {
       const int64_t n = n0 + i;

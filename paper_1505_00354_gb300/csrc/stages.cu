@@ -78,37 +78,109 @@ __device__ __forceinline__ int band_of(const BandArgs& B, int64_t k, int64_t N) 
   return -1;
 }
 
+// 1/l for the Taylor coefficients t^l / l! (products instead of divisions)
+__constant__ double kInvInt[48] = {
+    0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,  1.0 / 9,
+    1.0 / 10,   1.0 / 11,   1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19,
+    1.0 / 20,   1.0 / 21,   1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29,
+    1.0 / 30,   1.0 / 31,   1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
+    1.0 / 40,   1.0 / 41,   1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47};
+
 // signed Taylor coefficient of the cos part ((-1)^{l/2}, l even) and of the sin
 // part ((-1)^{(l+1)/2}, l odd), Eq. (6)
 __device__ __forceinline__ int sgn_even(int l) { return ((l >> 1) & 1) ? -1 : 1; }
 __device__ __forceinline__ int sgn_odd(int l) { return (((l + 1) >> 1) & 1) ? -1 : 1; }
 
 // ---------------------------------------------------------------- leg2cheb
+// C_n h_{m,n} for term m: from the plan's table in FP64 (Hnm[m N + n]); the FP32
+// form runs the recurrence h_{m+1} = h_m (m+1/2)^2 / ((m+1)(n+m+3/2)) in float
+template <typename T>
+struct HTerm {
+  const double* Hnm;
+  int64_t N, n;
+  T cn, h;
+  __device__ __forceinline__ T at(int m) {
+    if constexpr (sizeof(T) == 8) {
+      return Hnm[(int64_t)m * N + n];
+    } else {
+      const T v = cn * h;
+      const T mh = (T)m + (T)0.5;
+      h = h * (mh * mh) / (((T)m + (T)1) * ((T)n + (T)m + (T)1.5));
+      return v;
+    }
+  }
+};
+
 template <typename T>
 __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, int64_t N, int M,
-                          BandArgs B, const double* __restrict__ Cn, TwArgs<T> tw4N) {
+                          BandArgs B, const double* __restrict__ Cn, const double* __restrict__ Hnm,
+                          TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
   c += bt * N;
   U += bt * (int64_t)B.K * M * N;
-  const T cn = (T)Cn[n] * c[n];
+  const T cv = c[n];
   const C2<T> e = twid<T>(tw4N, n);
-  const T nn = (T)n;
-  T h = (T)1;
+  const C2<T> ce = mk<T>(cv * e.x, cv * e.y);
+  HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
+  const C2<T> zero = mk<T>((T)0, (T)0);
   for (int m = 0; m < M; ++m) {
-    const T a = cn * h;
-    const C2<T> val = mk<T>(a * e.x, a * e.y);
-    const C2<T> zero = mk<T>((T)0, (T)0);
+    const T a = H.at(m);
+    const C2<T> val = mk<T>(a * ce.x, a * ce.y);
     for (int s = 0; s < B.K; ++s) U[(int64_t)(s * M + m) * N + n] = (n >= B.ns[s]) ? val : zero;
-    const T mh = (T)m + (T)0.5;
-    h = h * (mh * mh) / (((T)m + (T)1) * (nn + (T)m + (T)1.5));
+  }
+}
+
+// Per cheb1 row k: alpha_k = e^{i(theta_k/2 - pi/4)} / (2 sin theta_k)^{1/2} and
+// rho_k = e^{i(theta_k - pi/2)} / (2 sin theta_k), so that the term-m factor
+// e^{i(m+1/2)(theta_k - pi/2)} / (2 sin theta_k)^{m+1/2} is alpha_k rho_k^m.  FP64
+// plans read them from a table (AR[k] = {alpha, rho}); the FP32 form computes them.
+template <typename T>
+__device__ __forceinline__ void row_factors(int64_t k, int64_t N, const RowAR* __restrict__ AR, C2<T>& al,
+                                            C2<T>& rho) {
+  if constexpr (sizeof(T) == 8) {
+    const RowAR a = AR[k];
+    al = mk<T>(a.ax, a.ay);
+    rho = mk<T>(a.rx, a.ry);
+  } else {
+    T st, ct, sa, ca;
+    sincospi_t((T)(2 * k + 1) / (T)(2 * N), &st, &ct);      // theta_k
+    sincospi_t((T)(2 * k + 1 - N) / (T)(4 * N), &sa, &ca);  // theta_k/2 - pi/4
+    const T g = (T)0.5 / st;
+    const T sq = sqrt(g);
+    al = mk<T>(ca * sq, sa * sq);
+    rho = mk<T>(st * g, -ct * g);
+  }
+}
+
+__global__ void k_row_factors_init(RowAR* __restrict__ AR, int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double st, ct, sa, ca;
+  sincospi((double)(2 * k + 1) / (double)(2 * N), &st, &ct);
+  sincospi((double)(2 * k + 1 - N) / (double)(4 * N), &sa, &ca);
+  const double g = 0.5 / st;
+  const double sq = sqrt(g);
+  AR[k] = RowAR{ca * sq, sa * sq, st * g, -ct * g};
+}
+
+// Hnm[m N + n] = C_n h_{m,n} (the recurrence in FP64, once per plan)
+__global__ void k_hnm_init(double* __restrict__ Hnm, const double* __restrict__ Cn, int64_t N, int M) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double h = 1.0;
+  const double cn = Cn[n];
+  for (int m = 0; m < M; ++m) {
+    Hnm[(int64_t)m * N + n] = cn * h;
+    const double mh = (double)m + 0.5;
+    h = h * (mh * mh) / (((double)m + 1.0) * ((double)n + (double)m + 1.5));
   }
 }
 
 template <typename T>
 __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const T* __restrict__ vrec, T* __restrict__ v,
-                          int64_t N, int M, BandArgs B) {
+                          int64_t N, int M, BandArgs B, const RowAR* __restrict__ AR) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int64_t bt = blockIdx.y;
@@ -118,13 +190,8 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const T* __restrict__ vre
   T acc = vrec[k];
   const int s = band_of(B, k, N);
   if (s >= 0) {
-    T st, ct, sa, ca;
-    sincospi_t((T)(2 * k + 1) / (T)(2 * N), &st, &ct);            // theta_k
-    sincospi_t((T)(2 * k + 1 - N) / (T)(4 * N), &sa, &ca);        // theta_k/2 - pi/4
-    const T g = (T)0.5 / st;
-    const T sq = sqrt(g);
-    C2<T> al = mk<T>(ca * sq, sa * sq);
-    const C2<T> rho = mk<T>(st * g, -ct * g);
+    C2<T> al, rho;
+    row_factors<T>(k, N, AR, al, rho);
     const bool odd = k & 1;
     const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
     const C2<T>* y = Y + (int64_t)s * M * N + idx;
@@ -197,8 +264,9 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int
   if (n >= N) return;
   chat += (int64_t)blockIdx.y * N;
   U += (int64_t)blockIdx.y * npair * N;
-  const T r = (T)n / (T)N;
-  const T rN = (T)(N - n) / (T)N;
+  const T invN = (T)1 / (T)N;  // exact: N is a power of two
+  const T r = (T)n * invN;
+  const T rN = (T)(N - n) * invN;
   const T cn = chat[n];
   const T cm = n > 0 ? chat[N - n] : (T)0;
   const C2<T> e = twid<T>(tw4N, n);
@@ -240,18 +308,27 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const T* __restrict__ v, 
   const T t = (T)tN[k];
   const bool odd = k & 1;
   const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
-  const T sk = odd ? (T)-1 : (T)1;
+  const T sk = odd ? (T)-0.5 : (T)0.5;
   T acc = inc0 ? (T)0 : v[k];
-  // q_l = t^l / l!
-  T q[2 * 16 + 3];
-  q[0] = (T)1;
-  for (int l = 1; l < L; ++l) q[l] = q[l - 1] * t / (T)l;
+  // q_l = t^l / l! advanced term by term: pair p uses l_b = 2p+1 and l_a = 2p (inc0)
+  // or 2p+2, so l runs upwards through both parts
+  T qa = (T)1;                        // q_{l_a} (inc0: q_0)
+  T qb = t;                           // q_{l_b} = q_1
+  if (!inc0) qa = qb * t * (T)kInvInt[2];
   for (int p = 0; p < npair; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const C2<T> y = Y[(int64_t)p * N + idx];
-    if (la <= L - 1) acc += (T)sgn_even(la) * q[la] * (T)0.5 * y.x;
-    if (lb <= L - 1) acc += (T)sgn_odd(lb) * q[lb] * (T)0.5 * sk * y.y;
+    if (la <= L - 1) acc += (T)sgn_even(la) * (T)0.5 * qa * y.x;
+    if (lb <= L - 1) acc += (T)sgn_odd(lb) * sk * qb * y.y;
+    // next pair: l_b + 2 and l_a + 2
+    if (inc0) {
+      qb = qb * t * (T)kInvInt[lb + 1] * t * (T)kInvInt[lb + 2];
+      qa = qa * t * (T)kInvInt[la + 1] * t * (T)kInvInt[la + 2];
+    } else {
+      qb = qa * t * (T)kInvInt[la + 1];
+      qa = qb * t * (T)kInvInt[la + 2];
+    }
   }
   f[k] = acc;
 }
@@ -301,13 +378,12 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
   F += bt * npair * N;
   if (Q) Q += bt * N;
   if (uout) uout += bt * N;
-  const T r = (T)n / (T)N;
+  const T r = (T)n * ((T)1 / (T)N);  // exact: N is a power of two
   const C2<T> e = twid<T>(tw4N, n);
   const int64_t nm = (N - n) & (N - 1);
-  T q[2 * 16 + 3];
-  q[0] = (T)1;
-  for (int l = 1; l < L; ++l) q[l] = q[l - 1] * r / (T)l;
   T acc = (T)0;
+  T qa = (T)1, qb = r;  // r^l / l! for l_a (inc0: 0) and l_b = 1
+  if (!inc0) qa = qb * r * (T)kInvInt[2];
   for (int p = 0; p < npair; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
@@ -316,12 +392,19 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
     if (la <= L - 1) {
       // U_n = Re[conj(e) (Fn + conj Fm)/2]
       const T vx = (Fn.x + Fm.x) * (T)0.5, vy = (Fn.y - Fm.y) * (T)0.5;
-      acc += (T)sgn_even(la) * q[la] * (e.x * vx + e.y * vy);
+      acc += (T)sgn_even(la) * qa * (e.x * vx + e.y * vy);
     }
     if (lb <= L - 1 && n > 0) {
       // V_n = Re[(-i e) (Fm - conj Fn)/(2i)] = Re[-e (Fm - conj Fn)]/2
       const T wx = Fm.x - Fn.x, wy = Fm.y + Fn.y;
-      acc += (T)sgn_odd(lb) * q[lb] * (T)(-0.5) * (e.x * wx - e.y * wy);
+      acc += (T)sgn_odd(lb) * qb * (T)(-0.5) * (e.x * wx - e.y * wy);
+    }
+    if (inc0) {
+      qb = qb * r * (T)kInvInt[lb + 1] * r * (T)kInvInt[lb + 2];
+      qa = qa * r * (T)kInvInt[la + 1] * r * (T)kInvInt[la + 2];
+    } else {
+      qb = qa * r * (T)kInvInt[la + 1];
+      qa = qb * r * (T)kInvInt[la + 2];
     }
   }
   if (mode == 0) {
@@ -397,10 +480,16 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
   }
 }
 
+// With F the T2-type transform of band s, term m, the DCT-II part minus the
+// DST-II part of the pair, (e.x (Fn.x + Fm.x) + e.y (Fn.y - Fm.y)) +
+// (e.x (Fm.x - Fn.x) - e.y (Fm.y + Fn.y)), is 2 Re(e_n F_{N-n}) (and 2 Re F_0 at
+// n = 0, where e = 1): only the bin N - n is read, and the sum over bands and
+// terms is taken before the rotation,
+//   out_n = rect_n + Re(e_n sum_m C_n h_{m,n} sum_{s: n >= n_s} F^{(s,m)}_{N-n}).
 template <typename T>
 __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ rect, T* __restrict__ out,
-                           int64_t N, int M, BandArgs B, const double* __restrict__ Cn, int scale_s,
-                           TwArgs<T> tw4N) {
+                           int64_t N, int M, BandArgs B, const double* __restrict__ Cn,
+                           const double* __restrict__ Hnm, int scale_s, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
@@ -409,25 +498,20 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ re
   if (F) F += bt * (int64_t)B.K * M * N;
   T acc = rect[n];
   if (B.K > 0 && M > 0) {
-    const C2<T> e = twid<T>(tw4N, n);
     const int64_t nm = (N - n) & (N - 1);
-    const T cn = (T)Cn[n];
-    const T nn = (T)n;
-    T h = (T)1;
-    for (int m = 0; m < M; ++m) {
-      T sum = (T)0;
-      for (int s = 0; s < B.K; ++s) {
-        if (n < B.ns[s]) continue;
-        const C2<T>* f = F + (int64_t)(s * M + m) * N;
-        const C2<T> Fn = f[n], Fm = f[nm];
-        const T U = e.x * (Fn.x + Fm.x) + e.y * (Fn.y - Fm.y);  // 2 * DCT-II part
-        T V = (T)0;
-        if (n > 0) V = -(e.x * (Fm.x - Fn.x) - e.y * (Fm.y + Fn.y));  // 2 * DST-II part
-        sum += (U - V);
+    int s0 = 0;  // bands s >= s0 have n >= n_s (the cuts decrease with s)
+    while (s0 < B.K && n < B.ns[s0]) ++s0;
+    if (s0 < B.K) {
+      HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
+      C2<T> V = mk<T>((T)0, (T)0);
+      for (int m = 0; m < M; ++m) {
+        C2<T> X = F[(int64_t)(s0 * M + m) * N + nm];
+        for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * M + m) * N + nm]);
+        const T hm = H.at(m);
+        V = mk<T>(V.x + hm * X.x, V.y + hm * X.y);
       }
-      acc += (T)0.5 * cn * h * sum;
-      const T mh = (T)m + (T)0.5;
-      h = h * (mh * mh) / (((T)m + (T)1) * (nn + (T)m + (T)1.5));
+      const C2<T> e = twid<T>(tw4N, n);
+      acc += e.x * V.x - e.y * V.y;
     }
   }
   out[n] = scale_s ? ((T)n + (T)0.5) * acc : acc;
@@ -455,7 +539,8 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 template <typename T>
 int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn, tw);
+  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn,
+                                                                       P.Hnm, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -466,7 +551,8 @@ int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb) {
 }
 template <typename T>
 int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v, int64_t nb) {
-  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P));
+  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P),
+                                                                       P.row_ar);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -585,12 +671,12 @@ template <typename T>
 int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
   k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
-                                                     scale_s, tw);
+                                                                        P.Hnm, scale_s, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
-    launched(P, "l2ct_epi", (double)nb * (14.0 * KM * N), (double)nb * (2.0 * KM * N * cs + 2.0 * ts * N));
+    launched(P, "l2ct_epi", (double)nb * (4.0 * KM * N), (double)nb * (KM * N * cs + 2.0 * ts * N));
   }
   return check_launch();
 }
@@ -602,6 +688,19 @@ int launch_scale(Plan& P, const T* in, T* out, int which, int64_t nb) {
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
     launched(P, "scale", (double)nb * (N), (double)nb * (2.0 * ts * N + 8.0 * N));
+  }
+  return check_launch();
+}
+
+int launch_stage_tables_init(Plan& P) {
+  const int64_t N = P.p.N;
+  if (P.row_ar) {
+    k_row_factors_init<<<nblk(N), TPB, 0, P.stream>>>(P.row_ar, N);
+    count_launch();
+  }
+  if (P.Hnm) {
+    k_hnm_init<<<nblk(N), TPB, 0, P.stream>>>(P.Hnm, P.Cn, N, P.p.M);
+    count_launch();
   }
   return check_launch();
 }
