@@ -79,7 +79,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbdlt", choices=["gbdlt", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--n", "--length", dest="n", type=int, default=N_DEFAULT,
+                    help="transform length (--length under torchrun, whose own options --n would abbreviate)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled-row error check")
     ap.add_argument("--quick", action="store_true", help="small sample sizes (for profiling runs)")
@@ -103,13 +104,20 @@ def barrier(world):
 
 
 def max_over_ranks(world, value: float) -> float:
+    """The largest of the ranks' values (the whole job's time is its slowest rank's)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(world, transforms_per_rank: float, ms_this_rank: float) -> float:
+    """Whole-job transforms/s: every rank's transforms over the slowest rank's time."""
+    return transforms_per_rank * world / (max_over_ranks(world, ms_this_rank) / 1e3)
 
 
 # --------------------------------------------------------------------------
@@ -239,8 +247,7 @@ def run_gpu(args, world, rank, local):
     clocks = clk.stop()
     prof = plan64.profile_report()
     t_step = sum(ms64) / len(ms64)
-    t_max = max_over_ranks(world, sum(ms64))
-    value = 2.0 * args.steps * world / (t_max / 1e3)
+    value = job_rate(world, 2.0 * args.steps, sum(ms64))
 
     # ---------------- FP32 form
     plan32, cold32 = make(g.FP32)
@@ -331,8 +338,9 @@ def run_gpu(args, world, rank, local):
         b.record(stream)
         ee.append((a, b))
     torch.cuda.synchronize()
-    t_e2e = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in ee))
-    e2e_value = 2.0 * args.steps * world / (t_e2e / 1e3)
+    t_e2e_rank = sum(a.elapsed_time(b) for a, b in ee)
+    t_e2e = max_over_ranks(world, t_e2e_rank)
+    e2e_value = job_rate(world, 2.0 * args.steps, t_e2e_rank)
 
     out = None
     if rank == 0:
@@ -376,7 +384,7 @@ def run_gpu(args, world, rank, local):
                                 "bands": params["bands"], "rec_steps": params["rec_steps"]}},
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 3), "unit": "transforms/s", "h2d_bytes_per_step": 8 * N,
-                    "d2h_bytes_per_step": 16 * N, "ms_per_step": round(t_e2e / args.steps / world, 4)},
+                    "d2h_bytes_per_step": 16 * N, "ms_per_step": round(t_e2e / args.steps, 4)},
             "roofline": roofline,
             "hbm_algorithmic": {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (t_step / 1e3) / 1e9, 2),
                                 "peak_gbs": hbm, "peak_source": hbm_src, "frac": round(hbm_frac, 6)},

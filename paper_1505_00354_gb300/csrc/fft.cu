@@ -314,6 +314,31 @@ __device__ __forceinline__ void stage(C2<T>* sm, int L, int logL, int lines, int
   __syncthreads();
 }
 
+// Global -> shared tile load, thread i taking elements i, i + 256, ...  In FP32
+// every thread first issues all of its (up to 16) loads into registers and then
+// stores them: the FP32 passes are bound by global-load latency, and this keeps
+// 16 loads in flight per thread.  FP64 passes are bound by the FP64 pipe and keep
+// the plain loop (its registers hold the radix-16 butterflies).
+template <typename T, typename Idx, typename Ld>
+__device__ __forceinline__ void load_tile(C2<T>* sm, int tot, Idx sidx_of, Ld ld) {
+  if constexpr (sizeof(T) == 4) {
+    constexpr int PER = FFT_TILE / FFT_THREADS;
+    C2<T> r[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = threadIdx.x + q * FFT_THREADS;
+      if (i < tot) r[q] = ld(i);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = threadIdx.x + q * FFT_THREADS;
+      if (i < tot) sm[sidx_of(i)] = r[q];
+    }
+  } else {
+    for (int i = threadIdx.x; i < tot; i += FFT_THREADS) sm[sidx_of(i)] = ld(i);
+  }
+}
+
 // In-place FFT of `lines` vectors of length L held at sidx(line, LP, i):
 // one stage of radix 2^(log2 L mod 4) (if any), then radix-16 stages.
 template <typename T, int DIR>
@@ -350,7 +375,7 @@ __device__ void fft_tile(C2<T>* sm, int L, int logL, int lines, int LP, const C2
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     k_fft_single(C2<T>* __restrict__ data, int L, int logL, int64_t nvec, const C2<T>* __restrict__ tw4096,
                  const double2* __restrict__ lf) {
   extern __shared__ unsigned char smraw[];
@@ -361,14 +386,14 @@ __global__ void __launch_bounds__(FFT_THREADS)
   const int LP = line_pitch(L);
   const int tot = lines * L;
   C2<T>* g = data + v0 * L;
-  for (int i = threadIdx.x; i < tot; i += FFT_THREADS) sm[sidx(i >> logL, LP, i & (L - 1))] = g[i];
+  load_tile<T>(sm, tot, [&](int i) { return sidx(i >> logL, LP, i & (L - 1)); }, [&](int i) { return g[i]; });
   __syncthreads();
   fft_tile<T, DIR>(sm, L, logL, lines, LP, tw4096, lf);
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) g[i] = sm[sidx(i >> logL, LP, i & (L - 1))];
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int logL1, int L2, int C, int logC,
                const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
                const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf) {
@@ -378,10 +403,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
   C2<T>* g = data + (int64_t)blockIdx.y * N;
   const int LP = line_pitch(L1);
   const int tot = L1 * C;
-  for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {
-    const int n1 = i >> logC, c = i & (C - 1);
-    sm[sidx(c, LP, n1)] = g[(int64_t)n1 * L2 + c0 + c];
-  }
+  load_tile<T>(sm, tot, [&](int i) { return sidx(i & (C - 1), LP, i >> logC); },
+               [&](int i) { return g[(int64_t)(i >> logC) * L2 + c0 + (i & (C - 1))]; });
   __syncthreads();
   fft_tile<T, DIR>(sm, L1, logL1, C, LP, tw4096, lf);
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {
@@ -398,7 +421,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
                int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096,
                const double2* __restrict__ lf) {
@@ -409,10 +432,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
   C2<T>* o = out + (int64_t)blockIdx.y * N;
   const int LP = line_pitch(L2);
   const int tot = L2 * C2n;
-  for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {
-    const int line = i >> logL2, n2 = i & (L2 - 1);
-    sm[sidx(line, LP, n2)] = g[(int64_t)(r0 + line) * L2 + n2];
-  }
+  load_tile<T>(sm, tot, [&](int i) { return sidx(i >> logL2, LP, i & (L2 - 1)); },
+               [&](int i) { return g[(int64_t)(r0 + (i >> logL2)) * L2 + (i & (L2 - 1))]; });
   __syncthreads();
   fft_tile<T, DIR>(sm, L2, logL2, C2n, LP, tw4096, lf);
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {

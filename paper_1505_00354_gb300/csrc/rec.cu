@@ -447,7 +447,24 @@ __global__ void k_rec_t_reduce(RecArgs R, const double* __restrict__ tbuf, T* __
   const int64_t n = (int64_t)blockIdx.x * 32 + lane;
   double s = 0.0;
   if (n < R.N) {
-    for (int64_t rb = w; rb < R.nblocks && (int64_t)R.maxcut[rb] > n; rb += 8) s += tbuf[R.toff[rb] + n];
+    // row blocks come in order of non-increasing cut: stop at the first that ends
+    // before column n.  Eight blocks per round with independent loads (the few
+    // columns below every cut walk all blocks, and set the kernel's length).
+    constexpr int U = 8;
+    for (int64_t rb0 = w; rb0 < R.nblocks; rb0 += 8 * U) {
+      double v[U];
+      bool more = true;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t rb = rb0 + 8 * u;
+        const bool in = rb < R.nblocks && (int64_t)R.maxcut[rb] > n;
+        v[u] = in ? tbuf[R.toff[rb] + n] : 0.0;
+        if (u == U - 1) more = in;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) s += v[u];
+      if (!more) break;
+    }
   }
   red[w][lane] = s;
   __syncthreads();
