@@ -374,6 +374,16 @@ __device__ void fft_tile(C2<T>* sm, int L, int logL, int lines, int LP, const C2
   }
 }
 
+// Launch-local vector j -> vector (j / count) * stride + first + j % count of the
+// buffer: a launch can cover, for every batch item, a contiguous run of the
+// item's vectors (the bands the pruned kernels do not take).
+struct VecMap {
+  int64_t first, count, stride;
+};
+__device__ __forceinline__ int64_t vec_of(const VecMap& m, int64_t j) {
+  return (j / m.count) * m.stride + m.first + j % m.count;
+}
+
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     k_fft_single(C2<T>* __restrict__ data, int L, int logL, int64_t nvec, const C2<T>* __restrict__ tw4096,
@@ -396,11 +406,12 @@ template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int logL1, int L2, int C, int logC,
                const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
-               const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf) {
+               const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf,
+               VecMap vm) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int c0 = blockIdx.x * C;
-  C2<T>* g = data + (int64_t)blockIdx.y * N;
+  C2<T>* g = data + vec_of(vm, blockIdx.y) * N;
   const int LP = line_pitch(L1);
   const int tot = L1 * C;
   load_tile<T>(sm, tot, [&](int i) { return sidx(i & (C - 1), LP, i >> logC); },
@@ -424,12 +435,13 @@ template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
                int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096,
-               const double2* __restrict__ lf) {
+               const double2* __restrict__ lf, VecMap vm) {
   extern __shared__ unsigned char smraw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
   const int r0 = blockIdx.x * C2n;
-  const C2<T>* g = in + (int64_t)blockIdx.y * N;
-  C2<T>* o = out + (int64_t)blockIdx.y * N;
+  const int64_t v = vec_of(vm, blockIdx.y);
+  const C2<T>* g = in + v * N;
+  C2<T>* o = out + v * N;
   const int LP = line_pitch(L2);
   const int tot = L2 * C2n;
   load_tile<T>(sm, tot, [&](int i) { return sidx(i >> logL2, LP, i & (L2 - 1)); },
@@ -442,6 +454,132 @@ __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
   }
 }
 
+// ---------------------------------------------------------------- pruned passes
+// A band of rows [ka, kb) (and their mirrors) reads the forward transform only at
+// the bins of two windows, |y| < R and |y - N/2| < R cyclically (R = kb/2 + 2),
+// and its transposed transform has nonzero input only there.  With the four-step
+// split y = k1 + L1 k2 (forward) and n = n1 L2 + n2 (input), and 2R <= L1, L2:
+//  * forward: row k1 < R needs k2 in {0, L2/2}, row k1 >= L1 - R needs
+//    k2 in {L2 - 1, L2/2 - 1}, other rows nothing: each needed row is two even/odd
+//    sums (twiddled by e^{-DIR 2 pi i n2/L2} for the high rows) instead of an FFT;
+//  * transposed: column n2 < R has input only at n1 in {0, L1/2}, column
+//    n2 >= L2 - R only at n1 in {L1/2 - 1, L1 - 1}, other columns none: the column
+//    transform is x_a +- x_b times one twiddle, w_N^{n2 k1} or w_N^{k1 (n2 - L2)}.
+
+// forward: grid (2R rows, vectors), 256 threads per row
+template <typename T, int DIR>
+__global__ void __launch_bounds__(FFT_THREADS)
+    k_fft_rows_pruned(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2, int R,
+                      const C2<T>* __restrict__ tw4096, VecMap vm) {
+  __shared__ T red[FFT_THREADS / 32][4];
+  const int r = blockIdx.x;
+  const bool low = r < R;
+  const int k1 = low ? r : L1 - 2 * R + r;
+  const int64_t v = vec_of(vm, blockIdx.y);
+  const C2<T>* g = in + v * N + (int64_t)k1 * L2;
+  C2<T>* o = out + v * N;
+  const int step = FFT_TILE / L2;
+  T ex = 0, ey = 0, ox = 0, oy = 0;
+  for (int n2 = 2 * threadIdx.x; n2 < L2; n2 += 2 * FFT_THREADS) {
+    C2<T> a = g[n2], b = g[n2 + 1];
+    if (!low) {
+      // times e^{-DIR 2 pi i n2 / L2}
+      const C2<T> wa = tw4096[n2 * step], wb = tw4096[(n2 + 1) * step];
+      a = cmul<T>(a, mk<T>(wa.x, DIR > 0 ? -wa.y : wa.y));
+      b = cmul<T>(b, mk<T>(wb.x, DIR > 0 ? -wb.y : wb.y));
+    }
+    ex += a.x;
+    ey += a.y;
+    ox += b.x;
+    oy += b.y;
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    ex += __shfl_xor_sync(0xffffffffu, ex, m);
+    ey += __shfl_xor_sync(0xffffffffu, ey, m);
+    ox += __shfl_xor_sync(0xffffffffu, ox, m);
+    oy += __shfl_xor_sync(0xffffffffu, oy, m);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w][0] = ex;
+    red[w][1] = ey;
+    red[w][2] = ox;
+    red[w][3] = oy;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ex = ey = ox = oy = 0;
+    for (int q = 0; q < FFT_THREADS / 32; ++q) {
+      ex += red[q][0];
+      ey += red[q][1];
+      ox += red[q][2];
+      oy += red[q][3];
+    }
+    const int64_t ka = low ? 0 : L2 - 1, kb = low ? L2 / 2 : L2 / 2 - 1;
+    o[k1 + (int64_t)L1 * ka] = mk<T>(ex + ox, ey + oy);
+    o[k1 + (int64_t)L1 * kb] = mk<T>(ex - ox, ey - oy);
+  }
+}
+
+// transposed: grid (L2 / C column groups, vectors), in place
+template <typename T, int DIR>
+__global__ void __launch_bounds__(FFT_THREADS)
+    k_fft_cols_pruned(C2<T>* __restrict__ data, int64_t N, int L1, int L2, int R, int C, int logC,
+                      const C2<T>* __restrict__ thi, const C2<T>* __restrict__ tlo,
+                      const C2<T>* __restrict__ tfull, VecMap vm) {
+  __shared__ C2<T> xs[2][64];  // C <= 4096 / L1 <= 64 (L1 >= 64 when N > 4096)
+  const int c0 = blockIdx.x * C;
+  C2<T>* g = data + vec_of(vm, blockIdx.y) * N;
+  for (int c = threadIdx.x; c < C; c += FFT_THREADS) {
+    const int n2 = c0 + c;
+    C2<T> a = mk<T>(0, 0), b = mk<T>(0, 0);
+    if (n2 < R) {
+      a = g[n2];
+      b = g[(int64_t)(L1 / 2) * L2 + n2];
+    } else if (n2 >= L2 - R) {
+      a = g[(int64_t)(L1 - 1) * L2 + n2];
+      b = g[(int64_t)(L1 / 2 - 1) * L2 + n2];
+    }
+    xs[0][c] = a;
+    xs[1][c] = b;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < L1 * C; i += FFT_THREADS) {
+    const int k1 = i >> logC, c = i & (C - 1);
+    const int n2 = c0 + c;
+    C2<T> val = mk<T>(0, 0);
+    const bool lowc = n2 < R;
+    if (lowc || n2 >= L2 - R) {
+      const C2<T> a = xs[0][c], b = xs[1][c];
+      val = (k1 & 1) ? csub<T>(a, b) : cadd<T>(a, b);
+      const int64_t e = lowc ? (int64_t)n2 * k1 : (N - (int64_t)k1 * (L2 - n2)) & (N - 1);
+      if (e != 0) {
+        const C2<T> w = sizeof(T) == 8 ? tfull[e] : tw_lookup<T>(thi, tlo, e);
+        val = cmul<T>(val, mk<T>(w.x, DIR > 0 ? w.y : -w.y));
+      }
+    }
+    g[(int64_t)k1 * L2 + n2] = val;
+  }
+}
+
+template <typename T, int DIR>
+static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, int64_t npruned, int R,
+                       int mode);
+
+// the tile kernels use more than 48 KB of dynamic shared memory: raise their
+// limit once per (T, DIR), before the first launch from any entry path
+template <typename T, int DIR>
+static void fft_attrs() {
+  static bool done = false;
+  if (done) return;
+  const int smax = (int)(FFT_SMEM_ELEMS * sizeof(C2<T>));
+  cudaFuncSetAttribute(k_fft_single<T, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  cudaFuncSetAttribute(k_fft_cols<T, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  cudaFuncSetAttribute(k_fft_rows<T, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  done = true;
+}
+
 template <typename T, int DIR>
 static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   using CT = C2<T>;
@@ -450,14 +588,7 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
   const TwT<T> tw = tw_tables(P, T());
   // cosine/tangent table of this direction (FP64 only)
   const double2* lfd = tw.lf ? tw.lf + (DIR > 0 ? 0 : 2 * 4096) : nullptr;
-  const size_t smax = (size_t)FFT_SMEM_ELEMS * sizeof(CT);
-  static bool attrs = false;  // one flag per (T, DIR) instantiation
-  if (!attrs) {
-    cudaFuncSetAttribute(k_fft_single<T, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-    cudaFuncSetAttribute(k_fft_cols<T, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-    cudaFuncSetAttribute(k_fft_rows<T, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-    attrs = true;
-  }
+  fft_attrs<T, DIR>();
   if (N <= FFT_TILE) {
     int L = (int)N;
     int lg = 0;
@@ -469,21 +600,67 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
     launched(P, "fft_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
     return a;
   }
+  return four_step<T, DIR>(P, a, b, nvec, 1, 0, 0, 0);
+}
+
+// Four-step FFT of nb items x per_item vectors; the first npruned vectors of
+// every item are pruned to the windows of half-width R: their row pass (mode 1,
+// forward, output windows) or column pass (mode 2, transposed, input windows)
+// runs in the pruned kernel, all other passes in the full kernels.
+template <typename T, int DIR>
+static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, int64_t npruned, int R,
+                       int mode) {
+  using CT = C2<T>;
+  fft_attrs<T, DIR>();
+  const int64_t N = P.p.N;
+  const TwT<T> tw = tw_tables(P, T());
+  const double2* lfd = tw.lf ? tw.lf + (DIR > 0 ? 0 : 2 * 4096) : nullptr;
   int p = 0;
   while ((1ll << p) < N) ++p;
-  int L1 = 1 << (p / 2);
-  int L2 = (int)(N / L1);
-  int C = FFT_TILE / L1;
-  int C2n = FFT_TILE / L2;
-  int lL1 = p / 2, lL2 = p - p / 2, lC = 12 - lL1, lC2 = 12 - lL2;
-  dim3 g1(L2 / C, (unsigned)nvec);
-  k_fft_cols<T, DIR><<<g1, FFT_THREADS, (size_t)C * line_pitch(L1) * sizeof(CT), P.stream>>>(
-      (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo, tw.full, lfd);
-  launched(P, "fft_cols", (5.0 * (p / 2) + 6.0) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
-  dim3 g2(L1 / C2n, (unsigned)nvec);
-  k_fft_rows<T, DIR><<<g2, FFT_THREADS, (size_t)C2n * line_pitch(L2) * sizeof(CT), P.stream>>>(
-      (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096, lfd);
-  launched(P, "fft_rows", 5.0 * (p - p / 2) * (double)N * nvec, 2.0 * (double)nvec * N * sizeof(CT));
+  const int L1 = 1 << (p / 2);
+  const int L2 = (int)(N / L1);
+  const int C = FFT_TILE / L1;
+  const int C2n = FFT_TILE / L2;
+  const int lL1 = p / 2, lL2 = p - p / 2, lC = 12 - lL1, lC2 = 12 - lL2;
+  if (mode == 0 || 2 * R > L1 || 2 * R > L2 || C > 64) npruned = 0;
+  const int64_t nfull = per_item - npruned;
+  const VecMap all{0, nb * per_item, nb * per_item};
+  const VecMap pruned{0, npruned, per_item};
+  const VecMap rest{npruned, nfull, per_item};
+  const size_t smc = (size_t)C * line_pitch(L1) * sizeof(CT), smr = (size_t)C2n * line_pitch(L2) * sizeof(CT);
+  // column pass
+  if (mode == 2 && npruned > 0) {
+    k_fft_cols_pruned<T, DIR><<<dim3(L2 / C, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
+        (CT*)a, N, L1, L2, R, C, lC, tw.nhi, tw.nlo, tw.full, pruned);
+    launched(P, "fft_cols_pruned", 6.0 * (double)N * nb * npruned * (4.0 * R / L2),
+             (double)nb * npruned * N * sizeof(CT));
+    if (nfull > 0) {
+      k_fft_cols<T, DIR><<<dim3(L2 / C, (unsigned)(nb * nfull)), FFT_THREADS, smc, P.stream>>>(
+          (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo, tw.full, lfd, rest);
+      launched(P, "fft_cols", (5.0 * lL1 + 6.0) * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
+    }
+  } else {
+    k_fft_cols<T, DIR><<<dim3(L2 / C, (unsigned)(nb * per_item)), FFT_THREADS, smc, P.stream>>>(
+        (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo, tw.full, lfd, all);
+    launched(P, "fft_cols", (5.0 * lL1 + 6.0) * (double)N * nb * per_item,
+             2.0 * (double)nb * per_item * N * sizeof(CT));
+  }
+  // row pass
+  if (mode == 1 && npruned > 0) {
+    k_fft_rows_pruned<T, DIR><<<dim3(2 * R, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
+        (const CT*)a, (CT*)b, N, L1, L2, R, tw.t4096, pruned);
+    launched(P, "fft_rows_pruned", 6.0 * 2.0 * R * L2 * (double)nb * npruned,
+             (double)nb * npruned * 2.0 * R * L2 * sizeof(CT));
+    if (nfull > 0) {
+      k_fft_rows<T, DIR><<<dim3(L1 / C2n, (unsigned)(nb * nfull)), FFT_THREADS, smr, P.stream>>>(
+          (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096, lfd, rest);
+      launched(P, "fft_rows", 5.0 * lL2 * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
+    }
+  } else {
+    k_fft_rows<T, DIR><<<dim3(L1 / C2n, (unsigned)(nb * per_item)), FFT_THREADS, smr, P.stream>>>(
+        (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096, lfd, all);
+    launched(P, "fft_rows", 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
+  }
   return b;
 }
 
@@ -492,7 +669,19 @@ void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir) {
   return dir > 0 ? fft_dir<T, 1>(P, a, b, nvec) : fft_dir<T, -1>(P, a, b, nvec);
 }
 
+template <typename T>
+void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int transposed) {
+  const int64_t KM = (int64_t)P.p.K * P.p.M;
+  if (P.p.N <= FFT_TILE || P.prune_bands == 0) return launch_fft<T>(P, a, b, nb * KM, dir);
+  const int64_t np = (int64_t)P.prune_bands * P.p.M;
+  const int mode = transposed ? 2 : 1;
+  return dir > 0 ? four_step<T, 1>(P, a, b, nb, KM, np, P.prune_R, mode)
+                 : four_step<T, -1>(P, a, b, nb, KM, np, P.prune_R, mode);
+}
+
 template void* launch_fft<double>(Plan&, void*, void*, int64_t, int);
+template void* launch_fft_bands<double>(Plan&, void*, void*, int64_t, int, int);
+template void* launch_fft_bands<float>(Plan&, void*, void*, int64_t, int, int);
 
 namespace {
 // cosine/tangent table for both directions: entry e of direction d holds the

@@ -164,6 +164,7 @@ struct RecLayout {
   int64_t nblocks = 0;        // row blocks of 256 half rows
   int64_t ncta = 0;           // (row block, segment) pairs
   int64_t tbuf_total = 0;     // transposed partial buffer length
+  int64_t n_heavy = 0;        // columns n below the cuts of more than 32 row blocks
   // device arrays
   int32_t* cut = nullptr;     // [H] recurrence cut per half row
   int64_t* poff = nullptr;    // [H] offset of row k's segments
@@ -175,6 +176,7 @@ struct RecLayout {
   double2* state = nullptr;   // [nseg_total] (P, D) at segment starts
   double2* part = nullptr;    // [nseg_total] forward partial sums (E, O)
   double* tbuf = nullptr;     // [tbuf_total] transposed partial sums
+  double* rscratch = nullptr; // [ceil(nblocks/64)][n_heavy] chunk sums of the transposed reduction
 };
 
 struct Plan {
@@ -214,6 +216,8 @@ struct Plan {
   void* bufA = nullptr;
   void* bufB = nullptr;
   int64_t nfft_max = 0;  // FFT vectors per transform (per batch item)
+  int prune_bands = 0;   // leading bands whose FFTs are pruned to their row windows
+  int prune_R = 0;       // window half-width of those bands (bins)
   int64_t bcap = 1;      // batch items one pass over the workspace holds
   void* v = nullptr;     // [N]
   void* chat = nullptr;  // [N]
@@ -282,6 +286,11 @@ int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N
 // Input in `a`; result in `a` when N <= 4096, else in `b` (returned pointer).
 template <typename T>
 void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir);
+// the K*M band FFTs of nb items (vectors [item][band][term]); bands
+// [0, prune_bands) read only the windows of their rows (transposed = 0: forward
+// chain, outputs pruned; 1: transposed chain, inputs pruned)
+template <typename T>
+void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int transposed);
 // rec.cu
 int launch_rec_state_init(Plan& P, RecLayout& L);
 template <typename T>

@@ -11,6 +11,7 @@
 //    of candidate cuts, ratio 2^(1/4)) minimise a cost model: each band costs M
 //    FFTs of length N, each recurrence step a fixed cost per half row.
 #include <algorithm>
+#include <functional>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -406,10 +407,15 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, Layo
   }
   R.tbuf_total = to;
   R.ncta = (int64_t)h.cta_rb.size();
+  // the transposed reduction relies on row blocks in order of non-increasing cut
+  // (true by construction: full rows first, then bands of decreasing cut)
+  std::vector<int32_t> mc = h.maxcut;
+  std::sort(mc.begin(), mc.end(), std::greater<int32_t>());
+  R.n_heavy = mc.size() > 32 ? mc[32] : 0;
 }
 
 struct LayoutOff {
-  size_t cut, poff, crb, cj, toff, mc, xm1, state, part, tbuf;
+  size_t cut, poff, crb, cj, toff, mc, xm1, state, part, tbuf, rscr;
 };
 
 }  // namespace
@@ -445,6 +451,19 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   RecLayout& D = P->drec;
   const int npair = (prm.L + 1) / 2;
   P->nfft_max = prm.fast ? std::max<int64_t>({(int64_t)prm.K * prm.M, (int64_t)npair, 1}) : 0;
+  // bands whose rows are few enough that their FFTs only touch two windows of
+  // bins (four-step sizes only; see fft.cu, pruned passes)
+  if (prm.fast && N > 4096) {
+    int p2 = 0;
+    while ((1ll << p2) < N) ++p2;
+    const int64_t L1 = 1ll << (p2 / 2), L2 = N / L1;
+    for (int s = 0; s < prm.K; ++s) {
+      const int64_t Rs = prm.bands[s].kb / 2 + 2;
+      if (2 * Rs > std::min(L1, L2)) break;
+      P->prune_bands = s + 1;
+      P->prune_R = (int)Rs;
+    }
+  }
   {
     // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
     const double per_item = 2.0 * P->nfft_max * N * cs + 5.0 * N * ts + 16.0 * (R.nseg_total + D.nseg_total) +
@@ -485,6 +504,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     o.state = A.take<double2>(L.nseg_total);
     o.part = A.take<double2>(BC * L.nseg_total);
     o.tbuf = A.take<double>(BC * L.tbuf_total);
+    o.rscr = A.take<double>(BC * ((L.nblocks + 63) / 64) * L.n_heavy);
     return o;
   };
   const LayoutOff of = take_layout(R), od = take_layout(D);
@@ -542,6 +562,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     L.state = (double2*)(base + o.state);
     L.part = (double2*)(base + o.part);
     L.tbuf = (double*)(base + o.tbuf);
+    L.rscratch = (double*)(base + o.rscr);
   };
   place_layout(R, of);
   place_layout(D, od);
@@ -641,7 +662,7 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   if (KM > 0) {
     st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, nb);
     if (st) return st;
-    Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * KM, +1);
+    Y = (const C2<T>*)launch_fft_bands<T>(P, P.bufA, P.bufB, nb, +1, 0);
   }
   st = launch_l2c_epi<T>(P, Y, vrec, v, nb);
   if (st) return st;
@@ -691,7 +712,7 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
-  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), nb * KM, -1);
+  if (KM > 0) F2 = (const C2<T>*)launch_fft_bands<T>(P, U, other(P, U), nb, -1, 1);
   return launch_l2ct_epi<T>(P, F2, rect, out, scale_s, nb);
 }
 
@@ -710,7 +731,7 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
-  if (KM > 0) F2 = (const C2<T>*)launch_fft<T>(P, U, other(P, U), nb * KM, -1);
+  if (KM > 0) F2 = (const C2<T>*)launch_fft_bands<T>(P, U, other(P, U), nb, -1, 1);
   return launch_l2ct_epi<T>(P, F2, rect, out, 0, nb);
 }
 

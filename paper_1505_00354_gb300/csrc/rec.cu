@@ -21,6 +21,8 @@
 // (one multiply and two fused multiply-adds).  The FP64 form runs the recurrence in FP64;
 // the FP32 form runs it in float-float (compensated FP32, ~2^-44 per operation)
 // on the FP32 pipe, which is 58 times faster than the FP64 pipe on GB300.
+#include <algorithm>
+
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -49,6 +51,9 @@ struct RecArgs {
   const float2* rbf;
   const double* xm1;   // [H] x_k - 1
   const double* zw;    // transposed input weights (w_k for the direct IDLT), or null
+  int64_t n_heavy;     // columns below the cuts of more than 32 row blocks
+  int64_t rchunks;     // chunks of 64 row blocks
+  double* rscratch;    // [batch][rchunks][n_heavy] chunk sums
   int scale_out;       // transposed reduction: 1 multiplies out_n by n + 1/2
 };
 
@@ -110,6 +115,9 @@ RecArgs rec_args(const Plan& P, const RecLayout& L) {
   a.xm1 = L.xm1;
   a.zw = nullptr;
   a.scale_out = 0;
+  a.n_heavy = L.n_heavy;
+  a.rchunks = (L.nblocks + 63) / 64;
+  a.rscratch = L.rscratch;
   a.ra = P.ra;
   a.rb = P.rb;
   a.raf = P.ra_ff;
@@ -438,25 +446,63 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
   }
 }
 
-template <typename T>
-__global__ void k_rec_t_reduce(RecArgs R, const double* __restrict__ tbuf, T* __restrict__ out) {
+// Column sums of the row blocks' partials: out_n = sum over row blocks with
+// cut > n of tbuf[toff[rb] + n] (row blocks come in order of non-increasing cut,
+// so the contributing blocks are a prefix).  Columns [0, n_heavy) lie below the
+// cuts of more than 32 blocks: k_rec_t_reduce_part sums them in chunks of 64
+// row blocks (grid: column groups x chunks, one round of independent loads per
+// warp) into a small scratch; k_rec_t_reduce_final adds the chunk sums of those
+// columns and sums the other columns' few blocks directly, one thread per column.
+constexpr int RB_CHUNK = 64;
+
+__global__ void k_rec_t_reduce_part(RecArgs R, const double* __restrict__ tbuf) {
   __shared__ double red[8][32];
-  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
-  out += (int64_t)blockIdx.y * R.N;
+  const int64_t bt = blockIdx.z;
+  tbuf += bt * R.tbuf_total;
+  double* scr = R.rscratch + bt * R.rchunks * R.n_heavy;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t rbc = (int64_t)blockIdx.y * RB_CHUNK;
   double s = 0.0;
-  if (n < R.N) {
-    // row blocks come in order of non-increasing cut: stop at the first that ends
-    // before column n.  Eight blocks per round with independent loads (the few
-    // columns below every cut walk all blocks, and set the kernel's length).
-    constexpr int U = 8;
-    for (int64_t rb0 = w; rb0 < R.nblocks; rb0 += 8 * U) {
+  if (n < R.n_heavy) {
+    double v[RB_CHUNK / 8];
+#pragma unroll
+    for (int u = 0; u < RB_CHUNK / 8; ++u) {
+      const int64_t rb = rbc + w + 8 * u;
+      v[u] = (rb < R.nblocks && (int64_t)R.maxcut[rb] > n) ? tbuf[R.toff[rb] + n] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < RB_CHUNK / 8; ++u) s += v[u];
+  }
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && n < R.n_heavy) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    scr[blockIdx.y * R.n_heavy + n] = t;
+  }
+}
+
+template <typename T>
+__global__ void k_rec_t_reduce_final(RecArgs R, const double* __restrict__ tbuf, T* __restrict__ out) {
+  const int64_t bt = blockIdx.y;
+  tbuf += bt * R.tbuf_total;
+  out += bt * R.N;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= R.N) return;
+  double s = 0.0;
+  if (n < R.n_heavy) {
+    const double* scr = R.rscratch + bt * R.rchunks * R.n_heavy + n;
+    for (int64_t c = 0; c < R.rchunks; ++c) s += scr[c * R.n_heavy];
+  } else {
+    constexpr int U = 4;
+    for (int64_t rb0 = 0; rb0 < R.nblocks; rb0 += U) {
       double v[U];
       bool more = true;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t rb = rb0 + 8 * u;
+        const int64_t rb = rb0 + u;
         const bool in = rb < R.nblocks && (int64_t)R.maxcut[rb] > n;
         v[u] = in ? tbuf[R.toff[rb] + n] : 0.0;
         if (u == U - 1) more = in;
@@ -466,15 +512,8 @@ __global__ void k_rec_t_reduce(RecArgs R, const double* __restrict__ tbuf, T* __
       if (!more) break;
     }
   }
-  red[w][lane] = s;
-  __syncthreads();
-  if (w == 0 && n < R.N) {
-    double t = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) t += red[q][lane];
-    if (R.scale_out) t *= (double)n + 0.5;
-    out[n] = (T)t;
-  }
+  if (R.scale_out) s *= (double)n + 0.5;
+  out[n] = (T)s;
 }
 
 }  // namespace
@@ -555,7 +594,11 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb, 
   }
   launched(P, "rec_t", (double)nb * 7.0 * (double)L.half_steps,
            (double)nb * ((double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total));
-  k_rec_t_reduce<T><<<dim3((unsigned)((P.p.N + 31) / 32), (unsigned)nb), 256, 0, P.stream>>>(R, L.tbuf, out);
+  if (R.n_heavy > 0)
+    k_rec_t_reduce_part<<<dim3((unsigned)((R.n_heavy + 31) / 32), (unsigned)R.rchunks, (unsigned)nb), 256, 0,
+                          P.stream>>>(R, L.tbuf);
+  k_rec_t_reduce_final<T><<<dim3((unsigned)((P.p.N + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(R, L.tbuf,
+                                                                                                   out);
   launched(P, "rec_t_reduce", (double)nb * (double)L.tbuf_total,
            (double)nb * (8.0 * (double)L.tbuf_total + (double)sizeof(T) * P.p.N));
   return check_launch();

@@ -436,20 +436,10 @@ __device__ __forceinline__ T row_z(const C2<T>* Y, const T* g, const double* wsc
 }
 
 template <typename T>
-__device__ __forceinline__ void alpha_init(int64_t k, int64_t N, C2<T>* al, C2<T>* rho) {
-  T st, ct, sa, ca;
-  sincospi_t((T)(2 * k + 1) / (T)(2 * N), &st, &ct);
-  sincospi_t((T)(2 * k + 1 - N) / (T)(4 * N), &sa, &ca);
-  const T g = (T)0.5 / st;
-  const T sq = sqrt(g);
-  *al = mk<T>(ca * sq, sa * sq);
-  *rho = mk<T>(st * g, -ct * g);
-}
-
-template <typename T>
 __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
                            const double* __restrict__ wscale, T* __restrict__ zout,
-                           C2<T>* __restrict__ U, int64_t N, int M, BandArgs B) {
+                           C2<T>* __restrict__ U, int64_t N, int M, BandArgs B,
+                           const RowAR* __restrict__ AR) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
   const int64_t bt = blockIdx.y;
@@ -464,8 +454,8 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
   zout[k1] = z1;
   const int s0 = band_of(B, k0, N), s1 = band_of(B, k1, N);
   C2<T> al0 = mk<T>(0, 0), rho0 = mk<T>(0, 0), al1 = mk<T>(0, 0), rho1 = mk<T>(0, 0);
-  if (s0 >= 0) alpha_init<T>(k0, N, &al0, &rho0);
-  if (s1 >= 0) alpha_init<T>(k1, N, &al1, &rho1);
+  if (s0 >= 0) row_factors<T>(k0, N, AR, al0, rho0);
+  if (s1 >= 0) row_factors<T>(k1, N, AR, al1, rho1);
   for (int m = 0; m < M; ++m) {
     // beta = z alpha; a = Re beta, h = (-1)^k Im beta
     const C2<T> v0 = mk<T>(z0 * al0.x, z0 * al0.y);
@@ -658,7 +648,8 @@ int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int n
 template <typename T>
 int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, int64_t nb) {
   const double* w = use_w ? P.w : nullptr;
-  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P));
+  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P),
+                                                                           P.row_ar);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;

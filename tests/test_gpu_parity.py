@@ -296,3 +296,20 @@ def test_argument_errors(gb):
     assert L.gbdlt_dlt(p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 1) == -1
     assert L.gbdlt_dlt(p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), -1) == -1
     assert L.gbdlt_plan_sync(p.handle) == 0
+
+
+@pytest.mark.parametrize("op", ["dlt", "idlt", "dlt_t"])
+def test_first_call_in_fresh_process(gb, op):
+    """The first transform of a process may reach any FFT entry path first (the
+    band FFTs take the four-step launcher directly): every path must set the
+    kernels' shared-memory limits itself."""
+    import subprocess
+    import sys
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import torch, paper_1505_00354_gb300 as g; "
+            "p = g.Plan(8192, method=g.METHOD_FAST); "
+            f"y = p.{op}(torch.ones(8192, dtype=torch.float64, device='cuda')); "
+            "torch.cuda.synchronize(); print(float(y.abs().sum()))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
