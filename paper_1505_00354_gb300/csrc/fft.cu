@@ -466,13 +466,14 @@ __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
 //    n2 >= L2 - R only at n1 in {L1/2 - 1, L1 - 1}, other columns none: the column
 //    transform is x_a +- x_b times one twiddle, w_N^{n2 k1} or w_N^{k1 (n2 - L2)}.
 
-// forward: grid (2R rows, vectors), 256 threads per row
+// forward: one warp per needed row, 8 rows per CTA; grid (ceil(2R / 8), vectors)
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_rows_pruned(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2, int R,
                       const C2<T>* __restrict__ tw4096, VecMap vm) {
-  __shared__ T red[FFT_THREADS / 32][4];
-  const int r = blockIdx.x;
+  const int r = blockIdx.x * (FFT_THREADS / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= 2 * R) return;  // whole warp
   const bool low = r < R;
   const int k1 = low ? r : L1 - 2 * R + r;
   const int64_t v = vec_of(vm, blockIdx.y);
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
   C2<T>* o = out + v * N;
   const int step = FFT_TILE / L2;
   T ex = 0, ey = 0, ox = 0, oy = 0;
-  for (int n2 = 2 * threadIdx.x; n2 < L2; n2 += 2 * FFT_THREADS) {
+  for (int n2 = 2 * lane; n2 < L2; n2 += 64) {
     C2<T> a = g[n2], b = g[n2 + 1];
     if (!low) {
       // times e^{-DIR 2 pi i n2 / L2}
@@ -500,22 +501,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
     ox += __shfl_xor_sync(0xffffffffu, ox, m);
     oy += __shfl_xor_sync(0xffffffffu, oy, m);
   }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[w][0] = ex;
-    red[w][1] = ey;
-    red[w][2] = ox;
-    red[w][3] = oy;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ex = ey = ox = oy = 0;
-    for (int q = 0; q < FFT_THREADS / 32; ++q) {
-      ex += red[q][0];
-      ey += red[q][1];
-      ox += red[q][2];
-      oy += red[q][3];
-    }
+  if (lane == 0) {
     const int64_t ka = low ? 0 : L2 - 1, kb = low ? L2 / 2 : L2 / 2 - 1;
     o[k1 + (int64_t)L1 * ka] = mk<T>(ex + ox, ey + oy);
     o[k1 + (int64_t)L1 * kb] = mk<T>(ex - ox, ey - oy);
@@ -647,7 +633,7 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   }
   // row pass
   if (mode == 1 && npruned > 0) {
-    k_fft_rows_pruned<T, DIR><<<dim3(2 * R, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
+    k_fft_rows_pruned<T, DIR><<<dim3((2 * R + 7) / 8, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
         (const CT*)a, (CT*)b, N, L1, L2, R, tw.t4096, pruned);
     launched(P, "fft_rows_pruned", 6.0 * 2.0 * R * L2 * (double)nb * npruned,
              (double)nb * npruned * 2.0 * R * L2 * sizeof(CT));

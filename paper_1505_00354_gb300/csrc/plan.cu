@@ -135,7 +135,10 @@ struct DPResult {
   std::vector<Band> bands;
 };
 
-static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, double c_rec) {
+// prune_kb: a band whose rows end at kb <= prune_kb has its FFTs pruned to two
+// windows of bins (fft.cu), costing about prune_f of a full band's FFTs
+static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, double c_rec, int64_t prune_kb,
+                           double prune_f) {
   const int64_t H = N / 2;
   DPResult best_res;
   // candidate cuts, descending
@@ -183,7 +186,8 @@ static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, doubl
     for (int j = i + 1; j < nc; ++j) {
       const int64_t kb = Kc[j];
       if (kb <= ka) continue;
-      double c2 = tcost + (double)cands[i] * c_rec * (double)(kb - ka) + best[j];
+      const double bt = kb <= prune_kb ? prune_f * tcost : tcost;
+      double c2 = bt + (double)cands[i] * c_rec * (double)(kb - ka) + best[j];
       if (c2 < opt) {
         opt = c2;
         ch = j;
@@ -262,8 +266,15 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
       Mmax = 16;
     }
     double best = (double)N * c_rec * (double)(N / 2);  // all recurrence
+    int64_t prune_kb = 0;
+    if (N > 4096) {
+      const int64_t L1 = 1ll << (lg / 2), L2 = N / L1;
+      prune_kb = std::min(L1, L2) - 4;  // 2 (kb/2 + 2) <= min(L1, L2)
+    }
     for (int M = 2; M <= Mmax; ++M) {
-      DPResult r = plan_bands(N, M, eps_asy, c_fft, c_rec);
+      // pruned bands save FP64 work; the FP32 passes are bound by memory
+      // latency, where the saving is small
+      DPResult r = plan_bands(N, M, eps_asy, c_fft, c_rec, prune_kb, prec == GBDLT_FP64 ? 0.6 : 1.0);
       if ((int)r.bands.size() > GBDLT_MAX_BANDS) continue;
       if (r.cost < best) {
         best = r.cost;
