@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled-row error check")
     ap.add_argument("--quick", action="store_true", help="small sample sizes (for profiling runs)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the N = 2^12 .. 2^22 sweep of both forms")
     return ap.parse_args()
 
 
@@ -403,6 +404,8 @@ def run_gpu(args, world, rank, local):
         }
         if not args.no_check:
             out["max_err"] = error_check(N, c_np, f64, cb64, f32, cb32, quick=args.quick)
+        if not args.no_sweep and world == 1:
+            out["sweep"] = sweep(stream, flush, check=not args.no_check)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(N, c_np, target_s=5.0 if args.quick else 15.0)
     if world > 1:
@@ -429,6 +432,58 @@ def error_check(N, c, f64, cb64, f32, cb32, quick=False):
         "roundtrip_fp32": float(np.max(np.abs(cb32.double().cpu().numpy() - c)) / c1),
         "rows": int(rows.size), "norm": "max|err| / ||c||_1",
     }
+
+
+def sweep(stream, flush, check=True):
+    """Both forms at N = 2^12 .. 2^22 (every second power): ms per step (legpts +
+    DLT + IDLT, 3 timed steps after 2 warm-up, L2 flushed between steps) and, at
+    8 sampled rows, max |error| / ||c||_1 of the DLT against the oracle (the FP32
+    form against the oracle of its rounded input)."""
+    import torch
+    import oracle
+    import paper_1505_00354_gb300 as g
+    from paper_1505_00354_gb300 import inputs
+    res = {}
+    for p2 in range(12, 23, 2):
+        N = 2**p2
+        c = inputs.coeffs(N, 700 + p2, 0.0)
+        rows = inputs.sample_rows(N, 8, seed=800 + p2, include_ends=2)
+        nd = oracle.legpts(N, rows) if check else None
+        entry = {}
+        for prec, name in ((g.FP64, "fp64"), (g.FP32, "fp32")):
+            dt = torch.float64 if prec == g.FP64 else torch.float32
+            plan = g.Plan(N, prec, stream=stream, method=g.METHOD_FAST)
+            x = torch.tensor(c, dtype=dt, device="cuda")
+            f, cb = torch.empty_like(x), torch.empty_like(x)
+            lib = g.lib()
+
+            def step():
+                lib.gbdlt_legpts(plan.handle, None, None, None, None)
+                plan.dlt(x, out=f)
+                plan.idlt(f, out=cb)
+
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for i in range(3):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            e = {"ms_per_step": round(tot / 3, 4), "transforms_per_s": round(2.0 / (tot / 3 / 1e3), 2)}
+            if check:
+                cc = c if prec == g.FP64 else c.astype(np.float32).astype(np.float64)
+                ref = oracle.dlt_rows(cc, nd)
+                e["dlt_err"] = float(np.max(np.abs(f.double().cpu().numpy()[rows] - ref)) / np.abs(cc).sum())
+            entry[name] = e
+            plan.close()
+            del x, f, cb
+        res[f"2^{p2}"] = entry
+    return res
 
 
 # --------------------------------------------------------------------------

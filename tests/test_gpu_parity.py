@@ -245,6 +245,47 @@ def test_fp32_form_full(gb, N):
     assert err <= TOL32 and ei <= TOL32
 
 
+@pytest.mark.parametrize("p2", list(range(12, 23)))
+@pytest.mark.parametrize("decay", [0.0, 1.0])
+def test_fp32_form_sweep(gb, p2, decay):
+    """The FP32 form across N = 2^12 .. 2^22, decaying and non-decaying c, against
+    the FP64 oracle at sampled rows (all rows up to 2^14)."""
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    N = 2**p2
+    c = inp.coeffs(N, 500 + p2 + int(10 * decay), decay).astype(np.float32).astype(np.float64)
+    p = gb.Plan(N, gb.FP32, method=gb.METHOD_FAST)
+    got = host(p.dlt(dev(c, torch.float32)))
+    if N <= 2**14:
+        rows = np.arange(N)
+        nd = onodes(N)
+    else:
+        rows = inp.sample_rows(N, 32, seed=5000 + p2)
+        nd = onodes(N, tuple(rows.tolist()))
+    err = np.max(np.abs(got[rows] - oracle.dlt_rows(c, nd))) / np.abs(c).sum()
+    print(f"N=2^{p2} decay {decay} fp32 dlt err/||c||1 = {err:.2e}")
+    assert err <= TOL32
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9, 1e-12])
+@pytest.mark.parametrize("N", [4096, 2**16])
+def test_general_eps(gb, eps, N):
+    """A user tolerance (Sec. 3: parameters for an arbitrary eps): fewer Taylor
+    and expansion terms for larger eps, and the DLT within eps * ||c||_1."""
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    p = gb.Plan(N, eps=eps, method=gb.METHOD_FAST)
+    q, q0 = p.params(), gb.plan_params(N, method=gb.METHOD_FAST)
+    assert q["L"] <= q0["L"] and (q["K"] == 0 or q["M"] <= q0["M"] or q["K"] < q0["K"])
+    c = inp.coeffs(N, 600 + N % 97, 0.0)
+    got = host(p.dlt(dev(c)))
+    rows = np.arange(N) if N <= 4096 else inp.sample_rows(N, 128, seed=601)
+    nd = onodes(N) if N <= 4096 else onodes(N, tuple(rows.tolist()))
+    err = np.max(np.abs(got[rows] - oracle.dlt_rows(c, nd))) / np.abs(c).sum()
+    print(f"N={N} eps={eps:g}: L={q['L']} M={q['M']} K={q['K']} err/||c||1 = {err:.2e}")
+    assert err <= eps
+
+
 @pytest.mark.parametrize("N,nrows", [(2**16, 256), (2**20, 128), (2**22, 48)])
 def test_fp32_form_sampled(gb, N, nrows):
     import oracle
