@@ -1,10 +1,15 @@
 // Recurrence region of leg2cheb and of its transpose (Sec. 3; the direct
 // three-term recurrence of Sec. 2.4 / Sec. 4.1 applied where the asymptotic
-// expansion of P_n(cos theta) is not accurate).
+// expansion of P_n(cos theta) is not accurate), and the direct method (the same
+// kernels over every column at the Legendre nodes: Eq. (1), and Eq. (2) with the
+// weights on the rows and n + 1/2 on the reduction).
 //
-// Rows are the cheb1 points theta_k = (k+1/2)pi/N.  Row k uses the recurrence for
-// columns n < cut(k) (cut = N for the rows nearest theta = 0, pi; the band's
-// column cut otherwise).  Rows k and N-1-k share one recurrence because
+// A layout (RecLayout) gives per half row k its x_k - 1 and its column cut.  In the
+// fast path the rows are the cheb1 points theta_k = (k+1/2)pi/N and row k uses the
+// recurrence for columns n < cut(k) (cut = N for the rows nearest theta = 0, pi;
+// the band's column cut otherwise); in the direct method the rows are the
+// Legendre nodes and every cut is N (for odd N the middle row, x = 0, is its own
+// mirror).  Rows k and N-1-k share one recurrence because
 // P_n(-x) = (-1)^n P_n(x): with E = sum over even n and O over odd n of c_n P_n(x_k),
 //   v_k = E + O,  v_{N-1-k} = E - O.
 // The recurrence runs in difference form with x - 1 = -2 sin^2(theta/2) computed

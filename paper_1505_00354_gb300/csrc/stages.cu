@@ -270,6 +270,10 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int
   const T cn = chat[n];
   const T cm = n > 0 ? chat[N - n] : (T)0;
   const C2<T> e = twid<T>(tw4N, n);
+  // U_n = e_n [(a_n + b_n) - i (a_{N-n} - b_{N-n})] with a = r^{l_a} chat, b = r^{l_b} chat:
+  // = (r^{l_a} + r^{l_b}) e chat_n + (rN^{l_b} - rN^{l_a}) i e chat_{N-n}
+  const C2<T> E1 = mk<T>(e.x * cn, e.y * cn);
+  const C2<T> E2 = mk<T>(-e.y * cm, e.x * cm);
   // r^l and rN^l for the current pair, advanced by r^2 per pair
   const T r2 = r * r, rN2 = rN * rN;
   T pa = inc0 ? (T)1 : r2, paN = inc0 ? (T)1 : rN2;  // r^{l_a}
@@ -277,16 +281,14 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int
   for (int p = 0; p < npair; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
-    const T ua = la <= L - 1 ? (T)1 : (T)0;
-    const T ub = lb <= L - 1 ? (T)1 : (T)0;
+    const bool ua = la <= L - 1, ub = lb <= L - 1;
     C2<T> val;
     if (n == 0) {
-      val = mk<T>((T)2 * ua * pa * cn, (T)0);  // 0^0 = 1 for l_a = 0
+      val = mk<T>(ua ? (T)2 * pa * cn : (T)0, (T)0);  // 0^0 = 1 for l_a = 0
     } else {
-      const T a = ua * pa * cn, b = ub * pb * cn;
-      const T aN = ua * paN * cm, bN = ub * pbN * cm;
-      const T re = a + b, im = -(aN - bN);
-      val = mk<T>(re * e.x - im * e.y, re * e.y + im * e.x);
+      const T A = (ua ? pa : (T)0) + (ub ? pb : (T)0);
+      const T Bm = (ub ? pbN : (T)0) - (ua ? paN : (T)0);
+      val = mk<T>(A * E1.x + Bm * E2.x, A * E1.y + Bm * E2.y);
     }
     U[(int64_t)p * N + n] = val;
     pa *= r2;
