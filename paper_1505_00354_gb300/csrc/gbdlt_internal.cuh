@@ -229,6 +229,7 @@ struct Plan {
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel
   struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
+  struct GraphCache* graphs = nullptr;  // replayed transform chains (plan.cu)
 };
 
 // twiddle tables in the precision T of a transform

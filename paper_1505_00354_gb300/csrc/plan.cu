@@ -26,6 +26,8 @@ namespace gbdlt {
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+static uint64_t launches_now() { return g_launches.load(std::memory_order_relaxed); }
+static void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 int check_launch() {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GBDLT_OK : GBDLT_ERR_CUDA;
@@ -366,8 +368,54 @@ struct Arena {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Graph replay of transform chains.  A chain is 10-60 kernel launches; for small
+// N their launch latency is most of a call.  The third and later calls with the
+// same (operator, method, pointers, batch) replay a CUDA graph captured on the
+// plan's internal stream (the first call runs the chain directly, which settles
+// kernel attributes; the second captures and replays).  The internal stream
+// waits for the caller's stream and the caller's stream for the replay, so the
+// calls keep the caller's stream order.  Chains are not replayed while the
+// per-kernel profiler is on or while the caller's stream is itself being
+// captured (the caller's graph then records the kernels).
+// ---------------------------------------------------------------------------
+struct GraphEntry {
+  int op = 0, method = 0;
+  const void* in = nullptr;
+  void* out = nullptr;
+  int64_t batch = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+  uint64_t last = 0;
+  int calls = 0;
+};
+struct GraphCache {
+  cudaStream_t s = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+  std::vector<GraphEntry> e;
+  uint64_t tick = 0;
+  bool broken = false;  // a capture failed: run chains directly from now on
+};
+constexpr size_t kGraphCacheSize = 16;
+
+void free_graphs(Plan* P) {
+  GraphCache* G = P->graphs;
+  if (!G) return;
+  for (GraphEntry& x : G->e)
+    if (x.exec) cudaGraphExecDestroy(x.exec);
+  if (G->in) cudaEventDestroy(G->in);
+  if (G->out) cudaEventDestroy(G->out);
+  if (G->s) cudaStreamDestroy(G->s);
+  delete G;
+  P->graphs = nullptr;
+}
+
 void free_plan(Plan* P) {
   if (!P) return;
+  if (P->graphs) {
+    cudaStreamSynchronize(P->graphs->s);
+    free_graphs(P);
+  }
   if (P->arena) cudaFree(P->arena);
   if (P->prof) {
     for (cudaEvent_t e : P->prof->ev) cudaEventDestroy(e);
@@ -839,20 +887,116 @@ int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch) {
   return run_op_method(plan, op, reinterpret_cast<Plan*>(plan)->p.method, in, out, batch);
 }
 
+static int run_chain(Plan& P, int op, int method, const void* in, void* out, int64_t batch);
+
 int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out, int64_t batch) {
   if (!plan || batch < 0) return GBDLT_ERR_INVALID_ARG;
   if (method != GBDLT_METHOD_FAST && method != GBDLT_METHOD_DIRECT) return GBDLT_ERR_INVALID_ARG;
   if (batch == 0) return GBDLT_OK;  // nothing to do; the pointers are not read
   if (!in || !out) return GBDLT_ERR_INVALID_ARG;
   Plan& P = *reinterpret_cast<Plan*>(plan);
-  const int64_t N = P.p.N;
   const size_t es = P.p.prec == GBDLT_FP64 ? 8 : 4;
   if (((uintptr_t)in % es) || ((uintptr_t)out % es)) return GBDLT_ERR_INVALID_ARG;
-  const char* a = (const char*)in;
-  const char* ae = a + (size_t)batch * N * es;
-  const char* b = (const char*)out;
-  const char* be = b + (size_t)batch * N * es;
-  if (batch > 0 && a < be && b < ae) return GBDLT_ERR_INVALID_ARG;  // overlap
+  {
+    const char* a = (const char*)in;
+    const char* ae = a + (size_t)batch * P.p.N * es;
+    const char* b = (const char*)out;
+    const char* be = b + (size_t)batch * P.p.N * es;
+    if (a < be && b < ae) return GBDLT_ERR_INVALID_ARG;  // overlap
+  }
+  // direct execution: profiling, a capturing caller stream, or a broken cache
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(P.stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;  // cannot tell: do not capture
+  }
+  if ((P.prof && P.prof->on) || cs != cudaStreamCaptureStatusNone || (P.graphs && P.graphs->broken))
+    return run_chain(P, op, method, in, out, batch);
+  if (!P.graphs) {
+    GraphCache* G = new (std::nothrow) GraphCache();
+    if (!G) return run_chain(P, op, method, in, out, batch);
+    P.graphs = G;
+    if (cudaStreamCreateWithFlags(&G->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      G->broken = true;
+      return run_chain(P, op, method, in, out, batch);
+    }
+  }
+  GraphCache& G = *P.graphs;
+  ++G.tick;
+  GraphEntry* E = nullptr;
+  for (GraphEntry& x : G.e)
+    if (x.op == op && x.method == method && x.in == in && x.out == out && x.batch == batch) E = &x;
+  if (!E) {
+    if (G.e.size() >= kGraphCacheSize) {
+      size_t lru = 0;
+      for (size_t i = 1; i < G.e.size(); ++i)
+        if (G.e[i].last < G.e[lru].last) lru = i;
+      if (G.e[lru].exec) cudaGraphExecDestroy(G.e[lru].exec);
+      G.e.erase(G.e.begin() + (long)lru);
+    }
+    GraphEntry x;
+    x.op = op;
+    x.method = method;
+    x.in = in;
+    x.out = out;
+    x.batch = batch;
+    G.e.push_back(x);
+    E = &G.e.back();
+  }
+  E->last = G.tick;
+  if (++E->calls < 2) return run_chain(P, op, method, in, out, batch);
+  // fork onto the internal stream
+  if (cudaEventRecord(G.in, P.stream) != cudaSuccess || cudaStreamWaitEvent(G.s, G.in, 0) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  if (!E->exec) {
+    cudaStream_t user = P.stream;
+    P.stream = G.s;
+    int st = GBDLT_OK;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(G.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = GBDLT_ERR_CUDA;
+    } else {
+      // kernels recorded into the graph are counted when the graph is launched
+      const uint64_t c0 = launches_now();
+      st = run_chain(P, op, method, in, out, batch);
+      uncount_launches(launches_now() - c0);
+      if (cudaStreamEndCapture(G.s, &graph) != cudaSuccess) st = st ? st : GBDLT_ERR_CUDA;
+    }
+    P.stream = user;
+    if (st == GBDLT_OK && graph && cudaGraphInstantiate(&E->exec, graph, 0) == cudaSuccess) {
+      size_t n = 0;
+      if (cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (n && cudaGraphGetNodes(graph, nodes.data(), &n) == cudaSuccess)
+          for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++E->kernels;
+          }
+      }
+    } else {
+      E->exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (!E->exec) {
+      // capture did not work: the work was not done; run it directly from now on
+      cudaGetLastError();
+      G.broken = true;
+      if (cudaEventRecord(G.out, G.s) == cudaSuccess) cudaStreamWaitEvent(P.stream, G.out, 0);
+      return st ? st : run_chain(P, op, method, in, out, batch);
+    }
+  }
+  if (cudaGraphLaunch(E->exec, G.s) != cudaSuccess) return GBDLT_ERR_CUDA;
+  count_launch((int)E->kernels);
+  if (cudaEventRecord(G.out, G.s) != cudaSuccess || cudaStreamWaitEvent(P.stream, G.out, 0) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  return GBDLT_OK;
+}
+
+static int run_chain(Plan& P, int op, int method, const void* in, void* out, int64_t batch) {
+  const int64_t N = P.p.N;
   for (int64_t i = 0; i < batch; i += P.bcap) {
     const int64_t nb = std::min<int64_t>(P.bcap, batch - i);
     int st;

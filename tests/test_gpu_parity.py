@@ -354,3 +354,58 @@ def test_first_call_in_fresh_process(gb, op):
             "torch.cuda.synchronize(); print(float(y.abs().sum()))")
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
+
+
+def test_max_n(gb):
+    """The largest N a plan accepts (2^24, FP64): sampled rows of the DLT against
+    the oracle, and the IDLT's forward residual there."""
+    import oracle
+    import paper_1505_00354_gb300.inputs as inp
+    N = 2**24
+    p = gb.Plan(N, method=gb.METHOD_FAST)
+    c = inp.coeffs(N, 924, 1.0)
+    f = p.dlt(dev(c))
+    # interior rows: the oracle's double-double Newton cannot settle the nodes
+    # nearest x = +-1 at this N (its recurrence's rounding floor is above its stop
+    # threshold there); those rows are checked at N <= 2^22
+    rows = inp.sample_rows(N, 16, seed=925, include_ends=0)
+    nd = onodes(N, tuple(rows.tolist()))
+    err = np.max(np.abs(host(f)[rows] - oracle.dlt_rows(c, nd))) / np.abs(c).sum()
+    cb = host(p.idlt(f))
+    res = np.max(np.abs(oracle.dlt_rows(cb, nd) - host(f)[rows])) / np.abs(cb).sum()
+    print(f"N=2^24: dlt {err:.2e}, idlt forward residual {res:.2e}")
+    assert err <= TOL64 and res <= TOL64
+    with pytest.raises(gb.GbdltError):
+        gb.Plan(2 * N)
+
+
+def test_graph_replay(gb):
+    """Repeated calls with the same pointers replay a captured chain: results are
+    bitwise those of the direct run, on the default stream and on a side stream,
+    and the launch count of a replay is the graph's kernel count."""
+    N = 512
+    for method in (gb.METHOD_FAST, gb.METHOD_DIRECT):
+        p = gb.Plan(N, method=method)
+        x = dev(_c(N, 77))
+        y = torch.empty_like(x)
+        outs = []
+        for _ in range(5):
+            p.dlt(x, out=y)
+            outs.append(y.clone())
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+        c0 = gb.launch_count()
+        p.dlt(x, out=y)
+        torch.cuda.synchronize()
+        assert gb.launch_count() > c0
+        assert torch.equal(y, outs[0])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = gb.Plan(N, method=gb.METHOD_FAST, stream=s)
+        x = dev(_c(N, 78))
+        ref = p.idlt(x).clone()
+        y = torch.empty_like(x)
+        for _ in range(4):
+            p.idlt(x, out=y)
+        s.synchronize()
+        assert torch.equal(y, ref)
