@@ -549,6 +549,193 @@ __global__ void __launch_bounds__(FFT_THREADS)
   }
 }
 
+// ---------------------------------------------------------------- FP32 passes, compile-time lines
+// The FP32 passes issue every instruction the FP32 pipe does not hide, and in the
+// generic stage most of them are shared-memory index arithmetic (line length and
+// sub-transform length are run-time values there).  These kernels take log2 of
+// the line length as a template parameter: the stage sequence, strides and masks
+// are constants, the 16 elements of a butterfly sit at immediate offsets from
+// one base whenever the stride is a multiple of 16, and the tile is always full
+// (four-step passes), so no bounds tests remain.
+__host__ __device__ constexpr int line_pitch_ct(int L) { return L + (L >> 4) + (L >= 16 ? 1 : 0); }
+
+template <int DIR, int R, int LOGL, int LOGNS>
+__device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
+  using CT = C2<float>;
+  constexpr int L = 1 << LOGL;
+  constexpr int LOGR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+  constexpr int LR = L / R, LOGLR = LOGL - LOGR;
+  constexpr int NS = 1 << LOGNS;
+  constexpr int LP = line_pitch_ct(L);
+  constexpr int PER = FFT_TILE / R / FFT_THREADS;
+  constexpr int SRD = LR + (LR >> 4), SWR = NS + (NS >> 4);
+  CT v[PER][R];
+  int lnq[PER], dq[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * FFT_THREADS;
+    const int line = b >> LOGLR;
+    const int j = b & (LR - 1);
+    const int k = j & (NS - 1);
+    if constexpr ((LR & 15) == 0) {
+      const CT* p = sm + line * LP + j + (j >> 4);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = p[r * SRD];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = sm[sidx(line, LP, j + r * LR)];
+    }
+    if constexpr (NS > 1) {
+      const int ks = k * (FFT_TILE / (NS * R));
+      CT w[R];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        if ((r & (r - 1)) == 0) {
+          w[r] = tw[r * ks];
+        } else {
+          w[r] = cmul<float>(w[r & (r - 1)], w[r & -r]);
+        }
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q][r] = cmul<float>(v[q][r], mk<float>(w[r].x, DIR > 0 ? w[r].y : -w[r].y));
+    }
+    lnq[q] = line;
+    dq[q] = (j - k) * R + k;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    dftR<float, DIR, R>(v[q]);
+    if constexpr ((NS & 15) == 0) {
+      CT* p = sm + lnq[q] * LP + dq[q] + (dq[q] >> 4);
+#pragma unroll
+      for (int r = 0; r < R; ++r) p[r * SWR] = v[q][r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[sidx(lnq[q], LP, dq[q] + r * NS)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIR, int LOGL, int LOGNS>
+__device__ __forceinline__ void r16_stages_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
+  if constexpr (LOGNS < LOGL) {
+    stage_ct<DIR, 16, LOGL, LOGNS>(sm, tw);
+    r16_stages_ct<DIR, LOGL, LOGNS + 4>(sm, tw);
+  }
+}
+
+template <int DIR, int LOGL>
+__device__ __forceinline__ void fft_tile_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
+  constexpr int REM = LOGL & 3;
+  if constexpr (REM == 1) stage_ct<DIR, 2, LOGL, 0>(sm, tw);
+  if constexpr (REM == 2) stage_ct<DIR, 4, LOGL, 0>(sm, tw);
+  if constexpr (REM == 3) stage_ct<DIR, 8, LOGL, 0>(sm, tw);
+  r16_stages_ct<DIR, LOGL, REM>(sm, tw);
+}
+
+template <int DIR, int LOGL1>
+__global__ void __launch_bounds__(FFT_THREADS, 4)
+    k_fft32_cols(C2<float>* __restrict__ data, int64_t N, int L2, const C2<float>* __restrict__ tw4096,
+                 const C2<float>* __restrict__ thi, const C2<float>* __restrict__ tlo, VecMap vm) {
+  using CT = C2<float>;
+  constexpr int L1 = 1 << LOGL1, LOGC = 12 - LOGL1, C = 1 << LOGC, LP = line_pitch_ct(L1);
+  constexpr int PER = FFT_TILE / FFT_THREADS;
+  __shared__ CT sm[C * LP];
+  const int c0 = blockIdx.x * C;
+  CT* g = data + vec_of(vm, blockIdx.y) * N;
+#pragma unroll
+  for (int q0 = 0; q0 < PER; q0 += 8) {
+    CT r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = threadIdx.x + (q0 + q) * FFT_THREADS;
+      r[q] = g[(int64_t)(i >> LOGC) * L2 + c0 + (i & (C - 1))];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = threadIdx.x + (q0 + q) * FFT_THREADS;
+      sm[sidx(i & (C - 1), LP, i >> LOGC)] = r[q];
+    }
+  }
+  __syncthreads();
+  fft_tile_ct<DIR, LOGL1>(sm, tw4096);
+#pragma unroll 4
+  for (int q = 0; q < PER; ++q) {
+    const int i = threadIdx.x + q * FFT_THREADS;
+    const int k1 = i >> LOGC, c = i & (C - 1);
+    const int64_t e = (int64_t)(c0 + c) * k1;
+    CT val = sm[sidx(c, LP, k1)];
+    if (e != 0) {
+      const CT w = tw_lookup<float>(thi, tlo, e);
+      val = cmul<float>(val, mk<float>(w.x, DIR > 0 ? w.y : -w.y));
+    }
+    g[(int64_t)k1 * L2 + c0 + c] = val;
+  }
+}
+
+template <int DIR, int LOGL2>
+__global__ void __launch_bounds__(FFT_THREADS, 4)
+    k_fft32_rows(const C2<float>* __restrict__ in, C2<float>* __restrict__ out, int64_t N, int L1,
+                 const C2<float>* __restrict__ tw4096, VecMap vm) {
+  using CT = C2<float>;
+  constexpr int L2 = 1 << LOGL2, LOGC2 = 12 - LOGL2, C2n = 1 << LOGC2, LP = line_pitch_ct(L2);
+  constexpr int PER = FFT_TILE / FFT_THREADS;
+  __shared__ CT sm[C2n * LP];
+  const int r0 = blockIdx.x * C2n;
+  const int64_t v = vec_of(vm, blockIdx.y);
+  const CT* g = in + v * N + (int64_t)r0 * L2;
+  CT* o = out + v * N;
+#pragma unroll
+  for (int q0 = 0; q0 < PER; q0 += 8) {
+    CT r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = g[threadIdx.x + (q0 + q) * FFT_THREADS];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = threadIdx.x + (q0 + q) * FFT_THREADS;
+      sm[sidx(i >> LOGL2, LP, i & (L2 - 1))] = r[q];
+    }
+  }
+  __syncthreads();
+  fft_tile_ct<DIR, LOGL2>(sm, tw4096);
+#pragma unroll 4
+  for (int q = 0; q < PER; ++q) {
+    const int i = threadIdx.x + q * FFT_THREADS;
+    const int k2 = i >> LOGC2, line = i & (C2n - 1);
+    o[(int64_t)(r0 + line) + (int64_t)L1 * k2] = sm[sidx(line, LP, k2)];
+  }
+}
+
+// launch the FP32 compile-time pass for log2 L in [6, 12]; false if none applies
+template <int DIR>
+static bool launch_fft32_cols(int logL1, dim3 grid, cudaStream_t s, C2<float>* a, int64_t N, int L2,
+                              const C2<float>* tw, const C2<float>* thi, const C2<float>* tlo, VecMap vm) {
+  switch (logL1) {
+#define GBDLT_C32(LG) \
+  case LG:            \
+    k_fft32_cols<DIR, LG><<<grid, FFT_THREADS, 0, s>>>(a, N, L2, tw, thi, tlo, vm); \
+    return true;
+    GBDLT_C32(6) GBDLT_C32(7) GBDLT_C32(8) GBDLT_C32(9) GBDLT_C32(10) GBDLT_C32(11) GBDLT_C32(12)
+#undef GBDLT_C32
+  }
+  return false;
+}
+template <int DIR>
+static bool launch_fft32_rows(int logL2, dim3 grid, cudaStream_t s, const C2<float>* a, C2<float>* b, int64_t N,
+                              int L1, const C2<float>* tw, VecMap vm) {
+  switch (logL2) {
+#define GBDLT_R32(LG) \
+  case LG:            \
+    k_fft32_rows<DIR, LG><<<grid, FFT_THREADS, 0, s>>>(a, b, N, L1, tw, vm); \
+    return true;
+    GBDLT_R32(6) GBDLT_R32(7) GBDLT_R32(8) GBDLT_R32(9) GBDLT_R32(10) GBDLT_R32(11) GBDLT_R32(12)
+#undef GBDLT_R32
+  }
+  return false;
+}
+
 template <typename T, int DIR>
 static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, int64_t npruned, int R,
                        int mode);
@@ -614,6 +801,28 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   const VecMap pruned{0, npruned, per_item};
   const VecMap rest{npruned, nfull, per_item};
   const size_t smc = (size_t)C * line_pitch(L1) * sizeof(CT), smr = (size_t)C2n * line_pitch(L2) * sizeof(CT);
+  // full column / row passes over a vector map: the FP32 compile-time kernels
+  // where the line length has one, else the generic ones
+  auto cols = [&](VecMap vm, int64_t nv) {
+    const dim3 grid(L2 / C, (unsigned)nv);
+    if constexpr (sizeof(T) == 4) {
+      if (launch_fft32_cols<DIR>(lL1, grid, P.stream, (C2<float>*)a, N, L2, (const C2<float>*)tw.t4096,
+                                 (const C2<float>*)tw.nhi, (const C2<float>*)tw.nlo, vm))
+        return;
+    }
+    k_fft_cols<T, DIR><<<grid, FFT_THREADS, smc, P.stream>>>((CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi,
+                                                              tw.nlo, tw.full, lfd, vm);
+  };
+  auto rows = [&](VecMap vm, int64_t nv) {
+    const dim3 grid(L1 / C2n, (unsigned)nv);
+    if constexpr (sizeof(T) == 4) {
+      if (launch_fft32_rows<DIR>(lL2, grid, P.stream, (const C2<float>*)a, (C2<float>*)b, N, L1,
+                                 (const C2<float>*)tw.t4096, vm))
+        return;
+    }
+    k_fft_rows<T, DIR><<<grid, FFT_THREADS, smr, P.stream>>>((const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2,
+                                                              tw.t4096, lfd, vm);
+  };
   // column pass
   if (mode == 2 && npruned > 0) {
     k_fft_cols_pruned<T, DIR><<<dim3(L2 / C, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
@@ -621,13 +830,11 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
     launched(P, "fft_cols_pruned", 6.0 * (double)N * nb * npruned * (4.0 * R / L2),
              (double)nb * npruned * N * sizeof(CT));
     if (nfull > 0) {
-      k_fft_cols<T, DIR><<<dim3(L2 / C, (unsigned)(nb * nfull)), FFT_THREADS, smc, P.stream>>>(
-          (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo, tw.full, lfd, rest);
+      cols(rest, nb * nfull);
       launched(P, "fft_cols", (5.0 * lL1 + 6.0) * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
     }
   } else {
-    k_fft_cols<T, DIR><<<dim3(L2 / C, (unsigned)(nb * per_item)), FFT_THREADS, smc, P.stream>>>(
-        (CT*)a, N, L1, lL1, L2, C, lC, tw.t4096, tw.nhi, tw.nlo, tw.full, lfd, all);
+    cols(all, nb * per_item);
     launched(P, "fft_cols", (5.0 * lL1 + 6.0) * (double)N * nb * per_item,
              2.0 * (double)nb * per_item * N * sizeof(CT));
   }
@@ -638,13 +845,11 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
     launched(P, "fft_rows_pruned", 6.0 * 2.0 * R * L2 * (double)nb * npruned,
              (double)nb * npruned * 2.0 * R * L2 * sizeof(CT));
     if (nfull > 0) {
-      k_fft_rows<T, DIR><<<dim3(L1 / C2n, (unsigned)(nb * nfull)), FFT_THREADS, smr, P.stream>>>(
-          (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096, lfd, rest);
+      rows(rest, nb * nfull);
       launched(P, "fft_rows", 5.0 * lL2 * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
     }
   } else {
-    k_fft_rows<T, DIR><<<dim3(L1 / C2n, (unsigned)(nb * per_item)), FFT_THREADS, smr, P.stream>>>(
-        (const CT*)a, (CT*)b, N, L1, L2, lL2, C2n, lC2, tw.t4096, lfd, all);
+    rows(all, nb * per_item);
     launched(P, "fft_rows", 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
   }
   return b;

@@ -383,7 +383,12 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
   const T r = (T)n * ((T)1 / (T)N);  // exact: N is a power of two
   const C2<T> e = twid<T>(tw4N, n);
   const int64_t nm = (N - n) & (N - 1);
-  T acc = (T)0;
+  // with U_n = Re[conj(e) (Fn + conj Fm)]/2 (DCT-II part) and
+  // V_n = Re[-e (Fm - conj Fn)]/2 (DST-II part, 0 at n = 0), the sum over pairs of
+  // sgn_a q_a U - sgn_b q_b V is e.x Ax + e.y Ay with
+  //   Ax = sum (ca (Fn.x + Fm.x) - cb (Fm.x - Fn.x)),  Ay = sum (ca (Fn.y - Fm.y) + cb (Fm.y + Fn.y)),
+  // ca = sgn_a q_a / 2, cb = sgn_b q_b / 2
+  T Ax = (T)0, Ay = (T)0;
   T qa = (T)1, qb = r;  // r^l / l! for l_a (inc0: 0) and l_b = 1
   if (!inc0) qa = qb * r * (T)kInvInt[2];
   for (int p = 0; p < npair; ++p) {
@@ -391,16 +396,11 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
     const int lb = 2 * p + 1;
     const C2<T> Fn = F[(int64_t)p * N + n];
     const C2<T> Fm = F[(int64_t)p * N + nm];
-    if (la <= L - 1) {
-      // U_n = Re[conj(e) (Fn + conj Fm)/2]
-      const T vx = (Fn.x + Fm.x) * (T)0.5, vy = (Fn.y - Fm.y) * (T)0.5;
-      acc += (T)sgn_even(la) * qa * (e.x * vx + e.y * vy);
-    }
-    if (lb <= L - 1 && n > 0) {
-      // V_n = Re[(-i e) (Fm - conj Fn)/(2i)] = Re[-e (Fm - conj Fn)]/2
-      const T wx = Fm.x - Fn.x, wy = Fm.y + Fn.y;
-      acc += (T)sgn_odd(lb) * qb * (T)(-0.5) * (e.x * wx - e.y * wy);
-    }
+    const T ha = la <= L - 1 ? (sgn_even(la) > 0 ? (T)0.5 : (T)-0.5) : (T)0;
+    const T hb = (lb <= L - 1 && n > 0) ? (sgn_odd(lb) > 0 ? (T)0.5 : (T)-0.5) : (T)0;
+    const T ca = ha * qa, cb = hb * qb;
+    Ax += ca * (Fn.x + Fm.x) - cb * (Fm.x - Fn.x);
+    Ay += ca * (Fn.y - Fm.y) + cb * (Fm.y + Fn.y);
     if (inc0) {
       qb = qb * r * (T)kInvInt[lb + 1] * r * (T)kInvInt[lb + 2];
       qa = qa * r * (T)kInvInt[la + 1] * r * (T)kInvInt[la + 2];
@@ -409,6 +409,7 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
       qa = qb * r * (T)kInvInt[la + 2];
     }
   }
+  const T acc = e.x * Ax + e.y * Ay;
   if (mode == 0) {
     const T d = (n == 0 ? (T)1 : (T)2) / (T)N;
     const T a = d * acc;
