@@ -88,6 +88,16 @@ __device__ __forceinline__ ffv ff_mul(ffv a, ffv b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return ff_quick(p, e);
 }
+// the same product left unnormalised (|lo| may exceed half an ulp of hi): for
+// operands that go straight into ff_mul or ff_add, whose error-free steps take
+// hi and lo as they come and renormalise at the end
+__device__ __forceinline__ ffv ff_mul_raw(ffv a, ffv b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return {p, e};
+}
 __device__ __forceinline__ ffv ff_from(double v) {
   const float h = (float)v;
   return {h, (float)(v - (double)h)};
@@ -238,10 +248,10 @@ __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __res
   int64_t n = n0;
   for (; n + 1 < n1; n += 2) {
     kahan_add(Es, Ec, __fmul_rn(c[n], P.hi));
-    D = ff_add(ff_mul(ff_mul(ff_ld(R.raf[n]), xm1), P), ff_mul(ff_ld(R.rbf[n]), D));
+    D = ff_add(ff_mul_raw(ff_mul_raw(ff_ld(R.raf[n]), xm1), P), ff_mul_raw(ff_ld(R.rbf[n]), D));
     P = ff_add(P, D);
     kahan_add(Os, Oc, __fmul_rn(c[n + 1], P.hi));
-    D = ff_add(ff_mul(ff_mul(ff_ld(R.raf[n + 1]), xm1), P), ff_mul(ff_ld(R.rbf[n + 1]), D));
+    D = ff_add(ff_mul_raw(ff_mul_raw(ff_ld(R.raf[n + 1]), xm1), P), ff_mul_raw(ff_ld(R.rbf[n + 1]), D));
     P = ff_add(P, D);
   }
   if (n < n1) kahan_add(Es, Ec, __fmul_rn(c[n], P.hi));
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
       float val = 0.f;
       if (n < cut) {
         val = ((n & 1) ? zm : zp) * P.hi;
-        D = ff_add(ff_mul(ff_mul(ff_ld(R.raf[n]), xm1), P), ff_mul(ff_ld(R.rbf[n]), D));
+        D = ff_add(ff_mul_raw(ff_mul_raw(ff_ld(R.raf[n]), xm1), P), ff_mul_raw(ff_ld(R.rbf[n]), D));
         P = ff_add(P, D);
       }
       mytile[i] = val;
