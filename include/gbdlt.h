@@ -90,6 +90,8 @@ typedef struct {
   size_t workspace_bytes; /* device workspace the plan allocates              */
   int method;          /* GBDLT_METHOD_FAST or GBDLT_METHOD_DIRECT (resolved)  */
   int64_t direct_steps; /* half-row recurrence steps of one direct transform   */
+  int64_t head;        /* fast path: columns n < head come from the dense block
+                          M[0:head, 0:head] (Sec. 3); 0 = none                 */
 } gbdlt_params;
 
 /* Host-only parameter derivation: no GPU, no allocation.  eps <= 0 selects the

@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("method", ctypes.c_int),
         ("direct_steps", ctypes.c_int64),
+        ("head", ctypes.c_int64),
     ]
 
     def to_dict(self) -> dict:
@@ -70,7 +71,7 @@ class Params(ctypes.Structure):
             "rec_steps": self.rec_steps, "seg_len": self.seg_len, "flops_dlt": self.flops_dlt,
             "bytes_dlt": self.bytes_dlt, "bytes_idlt": self.bytes_idlt,
             "workspace_bytes": self.workspace_bytes, "method": self.method,
-            "direct_steps": self.direct_steps,
+            "direct_steps": self.direct_steps, "head": self.head,
         }
 
 

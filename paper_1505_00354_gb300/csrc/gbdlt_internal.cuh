@@ -142,12 +142,15 @@ struct Params {
   int method = GBDLT_METHOD_FAST;  // what gbdlt_dlt/idlt(_t) run (resolved, never AUTO)
   bool fast = true;                // N is a power of two: the FFT-based chains exist
   int64_t direct_steps = 0;        // half-row recurrence steps of one direct transform
+  int64_t head = 0;                // columns n < head come from the dense block M[0:head, 0:head]
 };
 
 // Direct method limits: largest N a direct plan accepts, and the largest
 // power-of-two N that GBDLT_METHOD_AUTO sends to the direct method.
 constexpr int64_t kDirectMax = 1 << 16;
 constexpr int64_t kDirectAuto = 256;
+// largest dense head block a fast plan uses (h^2/4 terms per transform)
+constexpr int64_t kHeadMax = 1 << 16;
 
 // Fills Params from (N, prec, eps, method): Taylor terms, asymptotic terms, bands
 // and the method the plan runs.
@@ -159,6 +162,7 @@ struct RecLayout {
   int64_t H = 0;              // half rows (ceil(N / 2); row H-1 is its own mirror for odd N)
   int64_t half_steps = 0;     // recurrence steps over all half rows
   int S = 512;                // segment length
+  int j0 = 0;                 // first segment run (columns below j0 S are the dense head's)
   int64_t nseg_total = 0;     // sum over half rows of nseg(k)
   int64_t n_long = 0;         // rows [0, n_long) have nseg > 64
   int64_t nblocks = 0;        // row blocks of 256 half rows
@@ -208,6 +212,9 @@ struct Plan {
   // weights) and per cheb1 row {alpha_k, rho_k} (the expansion's row factors)
   double* Hnm = nullptr;
   RowAR* row_ar = nullptr;
+  // dense head block: Lam'_j = sqrt(2/pi) Gamma(j+1/2)/Gamma(j+1), j < head
+  double* head_lam = nullptr;
+  float* head_lamf = nullptr;
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
   RecLayout rec;    // recurrence region of the fast path (cheb1 rows)
   RecLayout drec;   // every row and column at the Legendre nodes (direct method)
@@ -319,7 +326,8 @@ int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npai
 template <typename T>
 int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb);
+int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb,
+                    int64_t nu = -1);
 template <typename T>
 int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, int64_t nb);
 template <typename T>
@@ -328,5 +336,11 @@ template <typename T>
 int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb);
 template <typename T>
 int launch_scale(Plan& P, const T* in, T* out, int which, int64_t nb);
+// head.cu: the dense head block, chat[0:h] += M[0:h, 0:h] c[0:h], and its
+// transpose, out[0:h] += D M[0:h, 0:h]^T y[0:h] (D = diag(n + 1/2) when scale_s)
+template <typename T>
+int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb);
+template <typename T>
+int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb);
 
 }  // namespace gbdlt

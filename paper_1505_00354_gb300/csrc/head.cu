@@ -1,0 +1,134 @@
+// Dense head block of leg2cheb (Sec. 3, the matrix M with chat = M c) and of its
+// transpose.  The first h Legendre columns map to the first h Chebyshev
+// coefficients only (M is upper triangular), through
+//   M_{0n} = Lam'_{n/2}^2 / 2,   M_{kn} = Lam'_{(n-k)/2} Lam'_{(n+k)/2}   (0 < k <= n, n - k even),
+// with Lam'_j = sqrt(2/pi) Gamma(j+1/2)/Gamma(j+1) (the plan's table, computed
+// in double-double on the host).  A fast plan with head h takes columns n < h
+// from this block, so no asymptotic band cuts below h and every recurrence row
+// starts at n = h.
+//   forward     chat_k += sum_{j : k+2j < h} Lam'_j Lam'_{j+k} c_{k+2j}       (halved at k = 0)
+//   transposed  out_n  += s_n sum_{j <= n/2} Lam'_j Lam'_{n-j} y_{n-2j}      (halved where n = 2j),
+//               s_n = n + 1/2 when the chain scales its output, else 1.
+// One warp per output: lanes stride over j, so the table and input reads of a
+// warp are contiguous; the sum is a plain FP64 fused multiply-add chain in the
+// FP64 form and a Kahan-compensated FP32 sum in the FP32 form (FP32 arithmetic
+// runs on a pipe 64 times wider than FP64 on GB300).  Per term: one product of
+// two table entries and one multiply-add, so FP64 issue bounds the FP64 form.
+#include "gbdlt_internal.cuh"
+
+namespace gbdlt {
+
+namespace {
+
+constexpr int HW = 8;  // warps (outputs) per CTA
+
+__device__ __forceinline__ void kahan_acc(float& s, float& c, float v) {
+  const float y = __fsub_rn(v, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+// sum over lanes of a lane partial, in double
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// lane partial of sum_{j in [0, J), j = lane mod 32} lam[a0 + j] lam[b0 + s_b j] x[x0 + s_x j]
+template <typename T>
+struct HeadSum;
+
+template <>
+struct HeadSum<double> {
+  __device__ __forceinline__ static double run(const double* __restrict__ lam, const double* __restrict__ x,
+                                               int64_t b0, int sb, int64_t x0, int sx, int64_t J, int lane) {
+    double a0 = 0.0, a1 = 0.0;
+    int64_t j = lane;
+    for (; j + 32 < J; j += 64) {
+      a0 = fma(lam[j] * lam[b0 + sb * j], x[x0 + sx * j], a0);
+      const int64_t j2 = j + 32;
+      a1 = fma(lam[j2] * lam[b0 + sb * j2], x[x0 + sx * j2], a1);
+    }
+    if (j < J) a0 = fma(lam[j] * lam[b0 + sb * j], x[x0 + sx * j], a0);
+    return a0 + a1;
+  }
+};
+
+template <>
+struct HeadSum<float> {
+  __device__ __forceinline__ static double run(const float* __restrict__ lam, const float* __restrict__ x,
+                                               int64_t b0, int sb, int64_t x0, int sx, int64_t J, int lane) {
+    float s = 0.f, c = 0.f;
+    for (int64_t j = lane; j < J; j += 32) kahan_acc(s, c, lam[j] * lam[b0 + sb * j] * x[x0 + sx * j]);
+    return (double)s - (double)c;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(HW * 32) k_head_fwd(const T* __restrict__ c, T* __restrict__ chat,
+                                                      const T* __restrict__ lam, int64_t N, int64_t h) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * HW + (threadIdx.x >> 5);
+  if (k >= h) return;  // whole warp
+  c += (int64_t)blockIdx.y * N;
+  chat += (int64_t)blockIdx.y * N;
+  const int64_t J = (h - k + 1) / 2;  // j < J  <=>  k + 2j < h
+  // term j: lam[j] lam[k + j] c[k + 2j]
+  double s = warp_sum(HeadSum<T>::run(lam, c, k, 1, k, 2, J, lane));
+  if (k == 0) s *= 0.5;
+  if (lane == 0) chat[k] = (T)((double)chat[k] + s);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(HW * 32) k_head_t(const T* __restrict__ y, T* __restrict__ out,
+                                                    const T* __restrict__ lam, int64_t N, int64_t h, int scale_s) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * HW + (threadIdx.x >> 5);
+  if (q >= h) return;  // whole warp
+  const int64_t n = h - 1 - q;  // longest sums first
+  y += (int64_t)blockIdx.y * N;
+  out += (int64_t)blockIdx.y * N;
+  // terms j with n - 2j > 0 in the loop; the k = 0 term (n even) halved after it
+  const int64_t J = (n + 1) / 2;
+  // term j: lam[j] lam[n - j] y[n - 2j]
+  double s = warp_sum(HeadSum<T>::run(lam, y, n, -1, n, -2, J, lane));
+  if (lane == 0) {
+    if (!(n & 1)) s += 0.5 * (double)lam[n / 2] * (double)lam[n / 2] * (double)y[0];
+    if (scale_s) s *= (double)n + 0.5;
+    out[n] = (T)((double)out[n] + s);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb) {
+  const int64_t h = P.p.head;
+  if (h == 0) return GBDLT_OK;
+  const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
+  k_head_fwd<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(c, chat, lam,
+                                                                                               P.p.N, h);
+  launched(P, "head", (double)nb * 0.5 * (double)h * (double)h,
+           (double)nb * (double)sizeof(T) * 3.0 * (double)h);
+  return check_launch();
+}
+
+template <typename T>
+int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb) {
+  const int64_t h = P.p.head;
+  if (h == 0) return GBDLT_OK;
+  const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
+  k_head_t<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(y, out, lam, P.p.N,
+                                                                                             h, scale_s);
+  launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h,
+           (double)nb * (double)sizeof(T) * 3.0 * (double)h);
+  return check_launch();
+}
+
+template int launch_head_fwd<double>(Plan&, const double*, double*, int64_t);
+template int launch_head_fwd<float>(Plan&, const float*, float*, int64_t);
+template int launch_head_t<double>(Plan&, const double*, double*, int, int64_t);
+template int launch_head_t<float>(Plan&, const float*, float*, int, int64_t);
+
+}  // namespace gbdlt

@@ -121,6 +121,17 @@ std::vector<double> cn_table(int64_t N) {
   return C;
 }
 
+static std::vector<double> head_table(int64_t h) {
+  // Lam'_0 = sqrt(2/pi) Gamma(1/2) = sqrt(2); Lam'_{j+1} = Lam'_j (j+1/2)/(j+1)
+  std::vector<double> L((size_t)h);
+  hdd v = {1.4142135623730951, -9.667293313452913e-17};  // sqrt(2) to double-double
+  for (int64_t j = 0; j < h; ++j) {
+    L[(size_t)j] = v.hi + v.lo;
+    v = h_div_d(h_mul_d(v, (double)j + 0.5), (double)(j + 1));
+  }
+  return L;
+}
+
 // ---------------------------------------------------------------------------
 // parameter derivation
 // ---------------------------------------------------------------------------
@@ -138,20 +149,24 @@ struct DPResult {
 };
 
 // prune_kb: a band whose rows end at kb <= prune_kb has its FFTs pruned to two
-// windows of bins (fft.cu), costing about prune_f of a full band's FFTs
+// windows of bins (fft.cu), costing about prune_f of a full band's FFTs.
+// head: columns n < head come from the dense head block M[0:head, 0:head]
+// (head.cu), so no band cuts below it and every row's recurrence starts there.
 static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, double c_rec, int64_t prune_kb,
-                           double prune_f) {
+                           double prune_f, int64_t head) {
   const int64_t H = N / 2;
   DPResult best_res;
-  // candidate cuts, descending
+  // candidate cuts, descending (none below the head; the head itself is one)
   std::vector<int64_t> cands;
   int lg = 0;
   while ((1ll << lg) < N) ++lg;
   for (int i = 4 * lg; i >= 4; --i) {
     int64_t v = (int64_t)std::llround(std::pow(2.0, i / 4.0));
     v = std::min<int64_t>(v, N);
+    if (head > 0 && v < head) break;
     if (v >= 2 && (cands.empty() || cands.back() != v)) cands.push_back(v);
   }
+  if (head > 0 && (cands.empty() || cands.back() != head)) cands.push_back(head);
   const int nc = (int)cands.size();
   // first half row whose n_cut <= cand
   std::vector<int64_t> Kc(nc);
@@ -183,13 +198,14 @@ static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, doubl
       choice[i] = -2;  // empty
       continue;
     }
-    double opt = tcost + (double)cands[i] * c_rec * (double)(H - ka);
+    const double rows_rec = (double)(cands[i] - head) * c_rec;  // per row of the band
+    double opt = tcost + rows_rec * (double)(H - ka);
     int ch = -1;
     for (int j = i + 1; j < nc; ++j) {
       const int64_t kb = Kc[j];
       if (kb <= ka) continue;
       const double bt = kb <= prune_kb ? prune_f * tcost : tcost;
-      double c2 = bt + (double)cands[i] * c_rec * (double)(kb - ka) + best[j];
+      double c2 = bt + rows_rec * (double)(kb - ka) + best[j];
       if (c2 < opt) {
         opt = c2;
         ch = j;
@@ -198,11 +214,12 @@ static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, doubl
     best[i] = opt;
     choice[i] = ch;
   }
-  double top = (double)N * c_rec * (double)H;
+  const double full_rec = (double)(N - head) * c_rec;  // per row below the first band
+  double top = full_rec * (double)H;
   int topi = -1;
   for (int i = 0; i < nc; ++i) {
     if (choice[i] == -2) continue;
-    double c0 = (double)N * c_rec * (double)Kc[i] + best[i];
+    double c0 = full_rec * (double)Kc[i] + best[i];
     if (c0 < top) {
       top = c0;
       topi = i;
@@ -256,15 +273,19 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     // costs in picoseconds of GB300 time, fitted to the measured kernels at
     // N = 2^20: one FFT vector of the pipeline (forward and transposed chain)
     // per point, and one recurrence step of a half row (both directions averaged)
-    double c_fft, c_rec;
+    // c_head: one term M_kn c_n of the dense head block (two FP64 instructions
+    // in the FP64 form; FP32 arithmetic with a compensated sum in the FP32 form)
+    double c_fft, c_rec, c_head;
     int Mmax;
     if (prec == GBDLT_FP64) {
       c_fft = (4.33 * lg + 16.0) * (double)N;  // ~64 FP64 instructions per point at 2^20
       c_rec = 7.7;                             // ~4.8 FP64 instructions per step
+      c_head = 4.0;
       Mmax = 24;
     } else {
       c_fft = (0.43 * lg + 1.7) * (double)N;   // memory and shared-memory bound FP32 passes
       c_rec = 3.4;                             // float-float recurrence
+      c_head = 0.25;
       Mmax = 16;
     }
     double best = (double)N * c_rec * (double)(N / 2);  // all recurrence
@@ -273,15 +294,23 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
       const int64_t L1 = 1ll << (lg / 2), L2 = N / L1;
       prune_kb = std::min(L1, L2) - 4;  // 2 (kb/2 + 2) <= min(L1, L2)
     }
-    for (int M = 2; M <= Mmax; ++M) {
-      // pruned bands save FP64 work; the FP32 passes are bound by memory
-      // latency, where the saving is small
-      DPResult r = plan_bands(N, M, eps_asy, c_fft, c_rec, prune_kb, prec == GBDLT_FP64 ? 0.6 : 1.0);
-      if ((int)r.bands.size() > GBDLT_MAX_BANDS) continue;
-      if (r.cost < best) {
-        best = r.cost;
-        q.M = M;
-        q.bands = r.bands;
+    // head sizes: 0 or a power-of-two multiple of the segment length, at most
+    // N/4 and kHeadMax
+    std::vector<int64_t> heads = {0};
+    for (int64_t h = q.seg; h <= std::min<int64_t>(N / 4, kHeadMax); h *= 2) heads.push_back(h);
+    for (int64_t h : heads) {
+      const double head_cost = c_head * 0.25 * (double)h * (double)h;  // h^2/4 terms
+      for (int M = 2; M <= Mmax; ++M) {
+        // pruned bands save FP64 work; the FP32 passes are bound by memory
+        // latency, where the saving is small
+        DPResult r = plan_bands(N, M, eps_asy, c_fft, c_rec, prune_kb, prec == GBDLT_FP64 ? 0.6 : 1.0, h);
+        if ((int)r.bands.size() > GBDLT_MAX_BANDS) continue;
+        if (r.cost + head_cost < best) {
+          best = r.cost + head_cost;
+          q.M = M;
+          q.bands = r.bands;
+          q.head = h;
+        }
       }
     }
     q.K = (int)q.bands.size();
@@ -293,8 +322,8 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
   int64_t half_steps = 0;
   if (pow2) {
     int64_t k0 = q.K > 0 ? q.bands[0].ka : H;
-    half_steps += k0 * N;
-    for (const Band& bd : q.bands) half_steps += (bd.kb - bd.ka) * bd.ns;
+    half_steps += k0 * (N - q.head);
+    for (const Band& bd : q.bands) half_steps += (bd.kb - bd.ka) * (bd.ns - q.head);
   }
   q.rec_steps = 2 * half_steps;
   q.direct_steps = N <= kDirectMax ? ((N + 1) / 2) * N : 0;
@@ -302,7 +331,8 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
   const double fft_flops = 5.0 * (double)N * (double)std::max(lg, 1);
   q.flops_dlt = method == GBDLT_METHOD_DIRECT
                     ? 7.0 * (double)q.direct_steps
-                    : (double)(q.K * q.M + 1 + npair) * fft_flops + 7.0 * (double)half_steps;
+                    : (double)(q.K * q.M + 1 + npair) * fft_flops + 7.0 * (double)half_steps +
+                          0.5 * (double)q.head * (double)q.head;
   const double dsz = prec == GBDLT_FP64 ? 8.0 : 4.0;
   q.bytes_dlt = (2.0 * dsz + 8.0) * (double)N;
   q.bytes_idlt = (2.0 * dsz + 16.0) * (double)N;
@@ -429,23 +459,28 @@ namespace {
 
 // Host side of a recurrence layout: rows [0, H) with column cuts `cut`, cut into
 // segments of S columns; CTAs are (row block of 256 half rows, segment) pairs.
+// Segments below j0 (the columns of the dense head block) are not run: a row
+// stores its segments j0 .. nseg-1, and a row block's transposed partials cover
+// columns [j0 S, nseg_max S).
 struct LayoutHost {
   std::vector<int32_t> cut, cta_rb, cta_j, maxcut;
   std::vector<int64_t> poff, toff;
 };
 
-void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, LayoutHost& h) {
+void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int j0, LayoutHost& h) {
   R.H = H;
   R.S = S;
+  R.j0 = j0;
   h.cut = std::move(cut);
   h.poff.assign((size_t)std::max<int64_t>(H, 1), 0);
   int64_t o = 0, steps = 0;
   R.n_long = 0;
+  const int64_t n_lo = (int64_t)j0 * S;
   for (int64_t k = 0; k < H; ++k) {
     h.poff[(size_t)k] = o;
-    const int64_t ns = (h.cut[(size_t)k] + S - 1) / S;
+    const int64_t ns = std::max<int64_t>(0, (h.cut[(size_t)k] + S - 1) / S - j0);
     o += ns;
-    steps += h.cut[(size_t)k];
+    steps += std::max<int64_t>(0, h.cut[(size_t)k] - n_lo);
     if (ns > 64) R.n_long = k + 1;
   }
   R.nseg_total = o;
@@ -458,8 +493,8 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, Layo
     const int64_t nsm = (mc + S - 1) / S;
     h.maxcut.push_back(mc);
     h.toff.push_back(to);
-    to += nsm * S;
-    for (int64_t j = 0; j < nsm; ++j) {
+    to += std::max<int64_t>(0, nsm - j0) * S;
+    for (int64_t j = j0; j < nsm; ++j) {
       h.cta_rb.push_back((int32_t)rb);
       h.cta_j.push_back((int32_t)j);
     }
@@ -499,12 +534,12 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1), (int32_t)N);
     for (const Band& b : prm.bands)
       for (int64_t k = b.ka; k < b.kb; ++k) cut[(size_t)k] = (int32_t)b.ns;
-    layout_build(P->rec, H, prm.seg, std::move(cut), hf);
+    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), hf);
   }
   P->has_direct = N > 1 && N <= kDirectMax && (prm.method == GBDLT_METHOD_DIRECT || want_direct);
   if (P->has_direct) {
     const int64_t H = (N + 1) / 2;
-    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), hd);
+    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, hd);
   }
   RecLayout& R = P->rec;
   RecLayout& D = P->drec;
@@ -551,6 +586,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   const bool stage_tabs = fp64_tabs && prm.K > 0 && prm.M > 0;
   size_t o_hnm = A.take<double>(stage_tabs ? (int64_t)prm.M * N : 1);
   size_t o_ar = A.take<RowAR>(stage_tabs ? N : 1);
+  const int64_t nhead = prm.fast ? prm.head : 0;
+  size_t o_lam = A.take<double>(std::max<int64_t>(nhead, 1)), o_lamf = A.take<float>(std::max<int64_t>(nhead, 1));
   auto take_layout = [&](const RecLayout& L) {
     LayoutOff o;
     o.cut = A.take<int32_t>(L.H);
@@ -610,6 +647,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   P->lf_tab = fp64_tabs ? (double2*)(base + o_lf) : nullptr;
   P->Hnm = stage_tabs ? (double*)(base + o_hnm) : nullptr;
   P->row_ar = stage_tabs ? (RowAR*)(base + o_ar) : nullptr;
+  P->head_lam = nhead > 0 ? (double*)(base + o_lam) : nullptr;
+  P->head_lamf = nhead > 0 ? (float*)(base + o_lamf) : nullptr;
   auto place_layout = [&](RecLayout& L, const LayoutOff& o) {
     L.cut = (int32_t*)(base + o.cut);
     L.poff = (int64_t*)(base + o.poff);
@@ -657,6 +696,12 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     }
     up(P->ra_ff, raf.data(), sizeof(float2) * raf.size());
     up(P->rb_ff, rbf.data(), sizeof(float2) * rbf.size());
+  }
+  if (nhead > 0) {
+    std::vector<double> lam = head_table(nhead);
+    std::vector<float> lamf(lam.begin(), lam.end());
+    up(P->head_lam, lam.data(), sizeof(double) * lam.size());
+    up(P->head_lamf, lamf.data(), sizeof(float) * lamf.size());
   }
   auto upload_layout = [&](RecLayout& L, const LayoutHost& h) {
     if (L.H == 0) return;
@@ -728,7 +773,24 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA, nb);
   if (st) return st;
   const C2<T>* F = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb, -1);
-  return launch_a4_epi<T>(P, F, chat, nb);
+  st = launch_a4_epi<T>(P, F, chat, nb);
+  if (st) return st;
+  // columns below the head: P.v lacks them, so chains that go on to the Taylor
+  // NDCT take its l = 0 term from chat (run_dlt_tail)
+  return launch_head_fwd<T>(P, c, chat, nb);
+}
+
+// forward declaration (defined below)
+template <typename T>
+int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb);
+
+// f = Taylor NDCT of P.chat after run_leg2cheb: the l = 0 term is v itself
+// (values on the cheb1 grid) when the plan has no head block, else it is one
+// more transformed term of chat (for even L the pair count is the same)
+template <typename T>
+int run_dlt_tail(Plan& P, T* out, int64_t nb) {
+  if (P.p.head > 0) return run_taylor<T>(P, (const T*)P.chat, nullptr, out, 1, nb);
+  return run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0, nb);
 }
 
 // Taylor NDCT (Sec. 2): f = [v] + sum_{l} ...; inc0 = 1 includes l = 0 (standalone chebeval)
@@ -747,32 +809,40 @@ int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb) {
   return launch_tay_epi<T>(P, Y, v, f, inc0, npair, nb);
 }
 
-// transposed chain: out = [D_s] P^T [D_w] g (idlt when weighted), Sec. 4
+// transposed chain: out = [D_s] P^T [D_w] g (idlt when weighted), Sec. 4.
+// Without a head block the l = 0 Taylor term enters in value space (z = g + ...);
+// with one, every term goes through the coefficient-space sum u = T^T-type
+// transposed Taylor sum, whose first `head` entries feed the transposed head block.
 template <typename T>
 int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
-  const int npair = P.p.L / 2;  // l = 1..L-1
+  const int64_t head = P.p.head;
+  const int inc0 = head > 0 ? 1 : 0;
+  const int npair = inc0 ? (P.p.L + 1) / 2 : P.p.L / 2;  // l = 0..L-1, or 1..L-1
   T* z = (T*)P.z;
   T* rect = (T*)P.tmp;
+  T* uhead = (T*)P.chat;  // first `head` coefficients of u (batch stride N)
   int st;
   const C2<T>* Y = nullptr;  // A4^T FFT output
   if (npair > 0) {
-    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, 0, npair, nb);
+    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, inc0, npair, nb);
     if (st) return st;
     const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * npair, -1);
     void* q = other(P, F);
-    st = launch_tayt_epi<T>(P, (const C2<T>*)F, (C2<T>*)q, nullptr, 0, npair, nb);
+    st = launch_tayt_epi<T>(P, (const C2<T>*)F, (C2<T>*)q, head > 0 ? uhead : nullptr, inc0, npair, nb, head);
     if (st) return st;
     Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), nb, +1);
   }
   void* U = Y ? other(P, Y) : P.bufA;
-  st = launch_l2ct_pro<T>(P, Y, g, use_w, z, (C2<T>*)U, nb);
+  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, nb);
   if (st) return st;
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
   if (KM > 0) F2 = (const C2<T>*)launch_fft_bands<T>(P, U, other(P, U), nb, -1, 1);
-  return launch_l2ct_epi<T>(P, F2, rect, out, scale_s, nb);
+  st = launch_l2ct_epi<T>(P, F2, rect, out, scale_s, nb);
+  if (st) return st;
+  return launch_head_t<T>(P, uhead, out, scale_s, nb);
 }
 
 // out = M^T y: z = A4^T y, then P_cheb^T z
@@ -791,7 +861,9 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   if (st) return st;
   const C2<T>* F2 = nullptr;
   if (KM > 0) F2 = (const C2<T>*)launch_fft_bands<T>(P, U, other(P, U), nb, -1, 1);
-  return launch_l2ct_epi<T>(P, F2, rect, out, 0, nb);
+  st = launch_l2ct_epi<T>(P, F2, rect, out, 0, nb);
+  if (st) return st;
+  return launch_head_t<T>(P, y, out, 0, nb);
 }
 
 template <typename T>
@@ -859,7 +931,7 @@ int run_one(Plan& P, int op, int method, const T* in, T* out, int64_t nb) {
     case OP_DLT: {
       int st = run_leg2cheb<T>(P, in, (T*)P.chat, nb);
       if (st) return st;
-      return run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0, nb);
+      return run_dlt_tail<T>(P, out, nb);
     }
     case OP_DLT_T:
       return run_transposed<T>(P, in, out, 0, 0, nb);
@@ -872,7 +944,7 @@ int run_one(Plan& P, int op, int method, const T* in, T* out, int64_t nb) {
       if (st) return st;
       st = run_leg2cheb<T>(P, sg, (T*)P.chat, nb);
       if (st) return st;
-      st = run_taylor<T>(P, (const T*)P.chat, (const T*)P.v, out, 0, nb);
+      st = run_dlt_tail<T>(P, out, nb);
       if (st) return st;
       return launch_scale<T>(P, out, out, 2, nb);
     }
@@ -1042,6 +1114,7 @@ static void fill_public(const Params& q, size_t ws, gbdlt_params* out) {
   out->workspace_bytes = ws;
   out->method = q.method;
   out->direct_steps = q.direct_steps;
+  out->head = q.head;
 }
 
 int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out) {

@@ -60,6 +60,8 @@ struct RecArgs {
   int64_t rchunks;     // chunks of 64 row blocks
   double* rscratch;    // [batch][rchunks][n_heavy] chunk sums
   int scale_out;       // transposed reduction: 1 multiplies out_n by n + 1/2
+  int j0;              // first segment run (the dense head block covers n < n_lo)
+  int64_t n_lo;        // j0 * S
 };
 
 // ---------------------------------------------------------------------------
@@ -133,6 +135,8 @@ RecArgs rec_args(const Plan& P, const RecLayout& L) {
   a.n_heavy = L.n_heavy;
   a.rchunks = (L.nblocks + 63) / 64;
   a.rscratch = L.rscratch;
+  a.j0 = L.j0;
+  a.n_lo = (int64_t)L.j0 * L.S;
   a.ra = P.ra;
   a.rb = P.rb;
   a.raf = P.ra_ff;
@@ -151,6 +155,25 @@ __global__ void k_rec_xm1(double* __restrict__ xm1, const double* __restrict__ t
 
 __device__ __forceinline__ int nseg_of(const RecArgs& R, int64_t k) {
   return (R.cut[k] + R.S - 1) / R.S;
+}
+// segments a row stores and runs: j0 .. nseg-1
+__device__ __forceinline__ int nstored_of(const RecArgs& R, int64_t k) {
+  return max(0, nseg_of(R, k) - R.j0);
+}
+
+// state (P, D) at n = n_lo of every row that runs segments past the head: the
+// recurrence from n = 0 in the difference form, one thread per half row
+__global__ void k_rec_lead(RecArgs R, double2* __restrict__ state) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= R.H) return;
+  if (nstored_of(R, k) == 0) return;
+  const double xm1 = R.xm1[k];
+  double P = 1.0, D = 1.0;
+  for (int64_t n = 0; n < R.n_lo; ++n) {
+    D = fma(R.ra[n] * xm1, P, R.rb[n] * D);
+    P += D;
+  }
+  state[R.poff[k]] = make_double2(P, D);
 }
 
 // transfer matrix of one full segment: images of the basis states (1,0), (0,1)
@@ -171,7 +194,7 @@ __global__ void k_rec_basis(RecArgs R, double2* __restrict__ Tbuf) {
     D2 = fma(t, P2, b * D2);
     P2 += D2;
   }
-  const int64_t o = 2 * (R.poff[k] + j);
+  const int64_t o = 2 * (R.poff[k] + j - R.j0);
   Tbuf[o] = make_double2(P1, D1);
   Tbuf[o + 1] = make_double2(P2, D2);
 }
@@ -179,10 +202,15 @@ __global__ void k_rec_basis(RecArgs R, double2* __restrict__ Tbuf) {
 __global__ void k_rec_scan(RecArgs R, const double2* __restrict__ Tbuf, double2* __restrict__ state) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= R.H) return;
-  const int ns = nseg_of(R, k);
+  const int ns = nstored_of(R, k);
   if (ns == 0) return;
   const int64_t o = R.poff[k];
   double P = 1.0, D = 1.0;
+  if (R.j0 > 0) {
+    const double2 s0 = state[o];  // from k_rec_lead
+    P = s0.x;
+    D = s0.y;
+  }
   state[o] = make_double2(P, D);
   for (int j = 0; j + 1 < ns; ++j) {
     const double2 a = Tbuf[2 * (o + j)], b = Tbuf[2 * (o + j) + 1];
@@ -206,7 +234,7 @@ __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__
   if (k >= R.H) return;
   const int cut = R.cut[k];
   if (j >= (cut + R.S - 1) / R.S) return;
-  const int64_t o = R.poff[k] + j;
+  const int64_t o = R.poff[k] + j - R.j0;
   const double2 st = R.state[o];
   const double xm1 = R.xm1[k];
   double P = st.x, G = st.y / xm1;
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __res
   if (k >= R.H) return;
   const int cut = R.cut[k];
   if (j >= (cut + R.S - 1) / R.S) return;
-  const int64_t o = R.poff[k] + j;
+  const int64_t o = R.poff[k] + j - R.j0;
   const double2 st = R.state[o];
   ffv P = ff_from(st.x), D = ff_from(st.y);
   const ffv xm1 = ff_from(R.xm1[k]);
@@ -272,7 +300,7 @@ __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T*
     k = r0 + gt / 32;
     const int lane = threadIdx.x & 31;
     if (k >= r1) return;  // whole warp leaves together
-    const int ns = nseg_of(R, k);
+    const int ns = nstored_of(R, k);
     const int64_t o = R.poff[k];
     for (int j = lane; j < ns; j += 32) {
       const double2 p = part[o + j];
@@ -287,7 +315,7 @@ __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T*
   } else {
     k = r0 + gt;
     if (k >= r1) return;
-    const int ns = nseg_of(R, k);
+    const int ns = nstored_of(R, k);
     const int64_t o = R.poff[k];
     for (int j = 0; j < ns; ++j) {
       const double2 p = part[o + j];
@@ -340,7 +368,7 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
     }
     zp = k == R.mid ? a : a + b;
     zm = k == R.mid ? a : a - b;
-    const double2 st = R.state[R.poff[k] + j];
+    const double2 st = R.state[R.poff[k] + j - R.j0];
     xm1 = R.xm1[k];
     P = st.x;
     G = st.y / xm1;
@@ -384,7 +412,7 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) s += wsum[q * R.S + c];
-    tbuf[R.toff[rbk] + n0s + c] = s;
+    tbuf[R.toff[rbk] + (n0s - R.n_lo) + c] = s;
   }
 }
 
@@ -417,7 +445,7 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
     }
     zp = k == R.mid ? a : a + b;
     zm = k == R.mid ? a : a - b;
-    const double2 st = R.state[R.poff[k] + j];
+    const double2 st = R.state[R.poff[k] + j - R.j0];
     P = ff_from(st.x);
     D = ff_from(st.y);
     xm1 = ff_from(R.xm1[k]);
@@ -457,13 +485,14 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) s += (double)wsum[q * R.S + c];
-    tbuf[R.toff[rbk] + n0s + c] = s;
+    tbuf[R.toff[rbk] + (n0s - R.n_lo) + c] = s;
   }
 }
 
 // Column sums of the row blocks' partials: out_n = sum over row blocks with
-// cut > n of tbuf[toff[rb] + n] (row blocks come in order of non-increasing cut,
-// so the contributing blocks are a prefix).  Columns [0, n_heavy) lie below the
+// cut > n of tbuf[toff[rb] + n - n_lo] (row blocks come in order of non-increasing
+// cut, so the contributing blocks are a prefix; columns below n_lo belong to the
+// dense head block and get 0 here).  Columns [n_lo, n_heavy) lie below the
 // cuts of more than 32 blocks: k_rec_t_reduce_part sums them in chunks of 64
 // row blocks (grid: column groups x chunks, one round of independent loads per
 // warp) into a small scratch; k_rec_t_reduce_final adds the chunk sums of those
@@ -476,7 +505,7 @@ __global__ void k_rec_t_reduce_part(RecArgs R, const double* __restrict__ tbuf) 
   tbuf += bt * R.tbuf_total;
   double* scr = R.rscratch + bt * R.rchunks * R.n_heavy;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t n = R.n_lo + (int64_t)blockIdx.x * 32 + lane;
   const int64_t rbc = (int64_t)blockIdx.y * RB_CHUNK;
   double s = 0.0;
   if (n < R.n_heavy) {
@@ -484,7 +513,7 @@ __global__ void k_rec_t_reduce_part(RecArgs R, const double* __restrict__ tbuf) 
 #pragma unroll
     for (int u = 0; u < RB_CHUNK / 8; ++u) {
       const int64_t rb = rbc + w + 8 * u;
-      v[u] = (rb < R.nblocks && (int64_t)R.maxcut[rb] > n) ? tbuf[R.toff[rb] + n] : 0.0;
+      v[u] = (rb < R.nblocks && (int64_t)R.maxcut[rb] > n) ? tbuf[R.toff[rb] + n - R.n_lo] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < RB_CHUNK / 8; ++u) s += v[u];
@@ -507,7 +536,9 @@ __global__ void k_rec_t_reduce_final(RecArgs R, const double* __restrict__ tbuf,
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= R.N) return;
   double s = 0.0;
-  if (n < R.n_heavy) {
+  if (n < R.n_lo) {
+    // the dense head block's columns: no recurrence contributions
+  } else if (n < R.n_heavy) {
     const double* scr = R.rscratch + bt * R.rchunks * R.n_heavy + n;
     for (int64_t c = 0; c < R.rchunks; ++c) s += scr[c * R.n_heavy];
   } else {
@@ -519,7 +550,7 @@ __global__ void k_rec_t_reduce_final(RecArgs R, const double* __restrict__ tbuf,
       for (int u = 0; u < U; ++u) {
         const int64_t rb = rb0 + u;
         const bool in = rb < R.nblocks && (int64_t)R.maxcut[rb] > n;
-        v[u] = in ? tbuf[R.toff[rb] + n] : 0.0;
+        v[u] = in ? tbuf[R.toff[rb] + n - R.n_lo] : 0.0;
         if (u == U - 1) more = in;
       }
 #pragma unroll
@@ -548,8 +579,14 @@ int launch_rec_state_init(Plan& P, RecLayout& L) {
     return GBDLT_ERR_OOM;
   }
   RecArgs R = rec_args(P, L);
-  k_rec_basis<<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, Tbuf);
-  count_launch();
+  if (L.j0 > 0) {
+    k_rec_lead<<<(unsigned)((L.H + 127) / 128), 128, 0, P.stream>>>(R, L.state);
+    count_launch();
+  }
+  if (L.ncta > 0) {
+    k_rec_basis<<<(unsigned)L.ncta, RT, 0, P.stream>>>(R, Tbuf);
+    count_launch();
+  }
   k_rec_scan<<<(unsigned)((L.H + 127) / 128), 128, 0, P.stream>>>(R, Tbuf, L.state);
   count_launch();
   int st = check_launch();
@@ -562,13 +599,16 @@ template <typename T>
 int launch_rec_forward(Plan& P, RecLayout& L, const T* c, T* vrec, int64_t nb) {
   RecArgs R = rec_args(P, L);
   if (L.H == 0) return GBDLT_OK;
-  if constexpr (sizeof(T) == 4) {
-    k_rec_fwd_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, (const float*)c, L.part);
-  } else {
-    k_rec_fwd<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, c, L.part);
+  // (no segments at all when the head block and the bands cover every column)
+  if (L.ncta > 0) {
+    if constexpr (sizeof(T) == 4) {
+      k_rec_fwd_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, (const float*)c, L.part);
+    } else {
+      k_rec_fwd<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, c, L.part);
+    }
+    launched(P, "rec_fwd", (double)nb * 7.0 * (double)L.half_steps,
+             (double)nb * ((double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total));
   }
-  launched(P, "rec_fwd", (double)nb * 7.0 * (double)L.half_steps,
-           (double)nb * ((double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total));
   if (L.n_long > 0) {
     const int64_t threads = L.n_long * 32;
     k_rec_fwd_reduce<T><<<dim3((unsigned)((threads + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
@@ -594,24 +634,28 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb, 
   if (L.H == 0) return GBDLT_OK;
   const size_t smem = sizeof(T) * (8 * 32 * TP + 8 * (size_t)L.S) + (sizeof(T) == 8 ? 16 * RT : 0);
   static bool attr_set = false;
-  if constexpr (sizeof(T) == 4) {
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_rec_t_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set = true;
+  if (L.ncta > 0) {
+    if constexpr (sizeof(T) == 4) {
+      if (!attr_set) {
+        cudaFuncSetAttribute(k_rec_t_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+      }
+      k_rec_t_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, (const float*)z, L.tbuf);
+    } else {
+      if (!attr_set) {
+        cudaFuncSetAttribute(k_rec_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+      }
+      k_rec_t<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, z, L.tbuf);
     }
-    k_rec_t_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, (const float*)z, L.tbuf);
-  } else {
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_rec_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set = true;
-    }
-    k_rec_t<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, smem, P.stream>>>(R, z, L.tbuf);
+    launched(P, "rec_t", (double)nb * 7.0 * (double)L.half_steps,
+             (double)nb * ((double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total));
   }
-  launched(P, "rec_t", (double)nb * 7.0 * (double)L.half_steps,
-           (double)nb * ((double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total + 8.0 * (double)L.tbuf_total));
-  if (R.n_heavy > 0)
-    k_rec_t_reduce_part<<<dim3((unsigned)((R.n_heavy + 31) / 32), (unsigned)R.rchunks, (unsigned)nb), 256, 0,
-                          P.stream>>>(R, L.tbuf);
+  if (R.n_heavy > R.n_lo) {
+    k_rec_t_reduce_part<<<dim3((unsigned)((R.n_heavy - R.n_lo + 31) / 32), (unsigned)R.rchunks, (unsigned)nb), 256,
+                          0, P.stream>>>(R, L.tbuf);
+    count_launch();
+  }
   k_rec_t_reduce_final<T><<<dim3((unsigned)((P.p.N + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(R, L.tbuf,
                                                                                                    out);
   launched(P, "rec_t_reduce", (double)nb * (double)L.tbuf_total,

@@ -369,11 +369,12 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
   }
 }
 
-// mode 0: write the FCS input of A4^T, Q_n = d_n u'_n e^{i pi n/(2N)};
-// mode 1: write u_n to uout.
+// Q != null: write the FCS input of A4^T, Q_n = d_n u'_n e^{i pi n/(2N)};
+// uout != null: write u_n to uout for n < nu (both when the chain also needs the
+// first nu coefficients of u, for the dense head block).
 template <typename T>
 __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T* __restrict__ uout,
-                           int64_t N, int L, int inc0, int npair, int mode, TwArgs<T> tw4N) {
+                           int64_t N, int L, int inc0, int npair, int64_t nu, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
@@ -410,13 +411,12 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
     }
   }
   const T acc = e.x * Ax + e.y * Ay;
-  if (mode == 0) {
+  if (Q) {
     const T d = (n == 0 ? (T)1 : (T)2) / (T)N;
     const T a = d * acc;
     Q[n] = mk<T>(a * e.x, a * e.y);
-  } else {
-    uout[n] = acc;
   }
+  if (uout && n < nu) uout[n] = acc;
 }
 
 // ---------------------------------------------------------------- leg2cheb (transposed)
@@ -636,10 +636,10 @@ int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npai
   return check_launch();
 }
 template <typename T>
-int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb) {
+int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb, int64_t nu) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  const int mode = Q ? 0 : 1;
-  k_tayt_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, mode, tw);
+  if (nu < 0) nu = P.p.N;
+  k_tayt_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, nu, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -709,7 +709,7 @@ int launch_stage_tables_init(Plan& P) {
   template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, int, int, int64_t);                         \
   template int launch_tay_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int, int64_t);                   \
   template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, int, int, int64_t);                   \
-  template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int, int64_t);                \
+  template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int, int64_t, int64_t);                \
   template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, int64_t);           \
   template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int64_t);                   \
   template int launch_scale<T>(Plan&, const T*, T*, int, int64_t);

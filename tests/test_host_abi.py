@@ -115,9 +115,14 @@ def test_band_layout_is_consistent(gb, N, prec):
     if bands:
         assert bands[-1][2] == H
         assert 1 <= p["M"] <= 24
-    # recurrence work matches the layout
+    # dense head block: a multiple of the segment length, at most N/4, and no
+    # band cuts below it
+    h = p["head"]
+    assert h == 0 or (h % p["seg_len"] == 0 and h <= N // 4)
+    assert all(ns >= h for ns, _, _ in bands)
+    # recurrence work matches the layout (every row starts at n = head)
     k0 = bands[0][1] if bands else H
-    steps = k0 * N + sum((kb - ka) * ns for ns, ka, kb in bands)
+    steps = k0 * (N - h) + sum((kb - ka) * (ns - h) for ns, ka, kb in bands)
     assert p["rec_steps"] == 2 * steps
     # algorithmic bytes: c, dtheta in; f out (+ w for the IDLT)
     ds = 8 if prec == 0 else 4
