@@ -92,6 +92,8 @@ typedef struct {
   int64_t direct_steps; /* half-row recurrence steps of one direct transform   */
   int64_t head;        /* fast path: columns n < head come from the dense block
                           M[0:head, 0:head] (Sec. 3); 0 = none                 */
+  int M_fp32;          /* FP64 plans: the last M_fp32 expansion terms have their
+                          band FFTs in FP32 (their size bounds the error)       */
 } gbdlt_params;
 
 /* Host-only parameter derivation: no GPU, no allocation.  eps <= 0 selects the

@@ -61,6 +61,7 @@ class Params(ctypes.Structure):
         ("method", ctypes.c_int),
         ("direct_steps", ctypes.c_int64),
         ("head", ctypes.c_int64),
+        ("M_fp32", ctypes.c_int),
     ]
 
     def to_dict(self) -> dict:
@@ -72,6 +73,7 @@ class Params(ctypes.Structure):
             "bytes_dlt": self.bytes_dlt, "bytes_idlt": self.bytes_idlt,
             "workspace_bytes": self.workspace_bytes, "method": self.method,
             "direct_steps": self.direct_steps, "head": self.head,
+            "M_fp32": self.M_fp32,
         }
 
 

@@ -770,7 +770,7 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
     int64_t grid = (nvec + lines - 1) / lines;
     size_t sm = (size_t)lines * line_pitch(L) * sizeof(CT);
     k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, lg, nvec, tw.t4096, lfd);
-    launched(P, "fft_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
+    launched(P, sizeof(T) == 8 ? "fft_single" : "fft32_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
     return a;
   }
   return four_step<T, DIR>(P, a, b, nvec, 1, 0, 0, 0);
@@ -827,30 +827,30 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   if (mode == 2 && npruned > 0) {
     k_fft_cols_pruned<T, DIR><<<dim3(L2 / C, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
         (CT*)a, N, L1, L2, R, C, lC, tw.nhi, tw.nlo, tw.full, pruned);
-    launched(P, "fft_cols_pruned", 6.0 * (double)N * nb * npruned * (4.0 * R / L2),
+    launched(P, sizeof(T) == 8 ? "fft_cols_pruned" : "fft32_cols_pruned", 6.0 * (double)N * nb * npruned * (4.0 * R / L2),
              (double)nb * npruned * N * sizeof(CT));
     if (nfull > 0) {
       cols(rest, nb * nfull);
-      launched(P, "fft_cols", (5.0 * lL1 + 6.0) * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
+      launched(P, sizeof(T) == 8 ? "fft_cols" : "fft32_cols", (5.0 * lL1 + 6.0) * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
     }
   } else {
     cols(all, nb * per_item);
-    launched(P, "fft_cols", (5.0 * lL1 + 6.0) * (double)N * nb * per_item,
+    launched(P, sizeof(T) == 8 ? "fft_cols" : "fft32_cols", (5.0 * lL1 + 6.0) * (double)N * nb * per_item,
              2.0 * (double)nb * per_item * N * sizeof(CT));
   }
   // row pass
   if (mode == 1 && npruned > 0) {
     k_fft_rows_pruned<T, DIR><<<dim3((2 * R + 7) / 8, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
         (const CT*)a, (CT*)b, N, L1, L2, R, tw.t4096, pruned);
-    launched(P, "fft_rows_pruned", 6.0 * 2.0 * R * L2 * (double)nb * npruned,
+    launched(P, sizeof(T) == 8 ? "fft_rows_pruned" : "fft32_rows_pruned", 6.0 * 2.0 * R * L2 * (double)nb * npruned,
              (double)nb * npruned * 2.0 * R * L2 * sizeof(CT));
     if (nfull > 0) {
       rows(rest, nb * nfull);
-      launched(P, "fft_rows", 5.0 * lL2 * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
+      launched(P, sizeof(T) == 8 ? "fft_rows" : "fft32_rows", 5.0 * lL2 * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
     }
   } else {
     rows(all, nb * per_item);
-    launched(P, "fft_rows", 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
+    launched(P, sizeof(T) == 8 ? "fft_rows" : "fft32_rows", 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
   }
   return b;
 }
@@ -861,18 +861,18 @@ void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir) {
 }
 
 template <typename T>
-void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int transposed) {
-  const int64_t KM = (int64_t)P.p.K * P.p.M;
+void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int transposed, int terms) {
+  const int64_t KM = (int64_t)P.p.K * terms;
   if (P.p.N <= FFT_TILE || P.prune_bands == 0) return launch_fft<T>(P, a, b, nb * KM, dir);
-  const int64_t np = (int64_t)P.prune_bands * P.p.M;
+  const int64_t np = (int64_t)P.prune_bands * terms;
   const int mode = transposed ? 2 : 1;
   return dir > 0 ? four_step<T, 1>(P, a, b, nb, KM, np, P.prune_R, mode)
                  : four_step<T, -1>(P, a, b, nb, KM, np, P.prune_R, mode);
 }
 
 template void* launch_fft<double>(Plan&, void*, void*, int64_t, int);
-template void* launch_fft_bands<double>(Plan&, void*, void*, int64_t, int, int);
-template void* launch_fft_bands<float>(Plan&, void*, void*, int64_t, int, int);
+template void* launch_fft_bands<double>(Plan&, void*, void*, int64_t, int, int, int);
+template void* launch_fft_bands<float>(Plan&, void*, void*, int64_t, int, int, int);
 
 namespace {
 // cosine/tangent table for both directions: entry e of direction d holds the

@@ -143,6 +143,8 @@ struct Params {
   bool fast = true;                // N is a power of two: the FFT-based chains exist
   int64_t direct_steps = 0;        // half-row recurrence steps of one direct transform
   int64_t head = 0;                // columns n < head come from the dense block M[0:head, 0:head]
+  int Mh = 0;                      // expansion terms whose band FFTs run in the plan's precision;
+                                   // terms Mh..M-1 of an FP64 plan run in FP32
 };
 
 // Direct method limits: largest N a direct plan accepts, and the largest
@@ -223,6 +225,13 @@ struct Plan {
   void* bufA = nullptr;
   void* bufB = nullptr;
   int64_t nfft_max = 0;  // FFT vectors per transform (per batch item)
+  // the FP32 band vectors of an FP64 plan ([item][band][term Mh..M-1][N] float2)
+  void* bufA32 = nullptr;
+  void* bufB32 = nullptr;
+  // their power-of-two scales: per (band, term) exponents [2][K][M] (forward,
+  // transposed) and per batch item the bits of max |chain input|
+  int* b32exp = nullptr;
+  unsigned long long* absmax = nullptr;
   int prune_bands = 0;   // leading bands whose FFTs are pruned to their row windows
   int prune_R = 0;       // window half-width of those bands (bins)
   int64_t bcap = 1;      // batch items one pass over the workspace holds
@@ -298,7 +307,7 @@ void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir);
 // [0, prune_bands) read only the windows of their rows (transposed = 0: forward
 // chain, outputs pruned; 1: transposed chain, inputs pruned)
 template <typename T>
-void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int transposed);
+void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int transposed, int terms);
 // rec.cu
 int launch_rec_state_init(Plan& P, RecLayout& L);
 template <typename T>
@@ -309,10 +318,15 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb,
 // x_k - 1 of the cheb1 rows (fast path) or of the Legendre nodes (direct method)
 int launch_rec_xm1(Plan& P, RecLayout& L, int legendre);
 // stages.cu (prologues / epilogues)
+// band vectors of terms m < Mh in U / Y / F (precision T), of terms m >= Mh in
+// U32 / Y32 / F32 (FP32; FP64 plans only)
 template <typename T>
-int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb);
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, float2* U32, int64_t nb);
+// max |x| per batch item into P.absmax (FP64 plans with FP32 band vectors)
 template <typename T>
-int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v, int64_t nb);
+int launch_absmax(Plan& P, const T* x, int64_t nb);
+template <typename T>
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const float2* Y32, const T* vrec, T* v, int64_t nb);
 template <typename T>
 int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb);
 template <typename T>
@@ -329,9 +343,9 @@ template <typename T>
 int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb,
                     int64_t nu = -1);
 template <typename T>
-int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, int64_t nb);
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, float2* U32, int64_t nb);
 template <typename T>
-int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s, int64_t nb);
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const float2* F32, const T* rect, T* out, int scale_s, int64_t nb);
 template <typename T>
 int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb);
 template <typename T>

@@ -148,11 +148,51 @@ struct DPResult {
   std::vector<Band> bands;
 };
 
-// prune_kb: a band whose rows end at kb <= prune_kb has its FFTs pruned to two
-// windows of bins (fft.cu), costing about prune_f of a full band's FFTs.
+// first half row k (theta_k = (k+1/2) pi/N) at which the M-term remainder bound
+// of columns n >= ns is below eps_asy, or H when none is
+static int64_t first_row(int64_t N, int M, double eps_asy, int64_t ns) {
+  const int64_t H = N / 2;
+  double lgm = log_gM(M, (double)ns);
+  double lsmin = (lgm - std::log(eps_asy)) / (M + 0.5) - std::log(2.0);
+  double smin = std::exp(lsmin);
+  if (smin >= 1.0) return H;
+  double kk = (double)N * std::asin(smin) / M_PI - 0.5;
+  int64_t k = (int64_t)std::ceil(kk);
+  if (k < 0) k = 0;
+  // guard against rounding of asin: move to the first row that satisfies the bound
+  while (k < H && std::sin((k + 0.5) * M_PI / N) < smin) ++k;
+  while (k > 0 && std::sin((k - 0.5) * M_PI / N) >= smin) --k;
+  return std::min(k, H);
+}
+
+// FP64 plans: how many leading expansion terms of a band must have FP64 FFTs.
+// At the band's first row, term m of columns n >= ns is at most
+// T_m = 2 C_ns h_{m,ns} / (2 sin theta_ka)^{m+1/2} ||c||_1 (the remainder bound
+// with m terms), and an FFT in FP32 of its vector errs by at most about
+// 2 log2(N) u_32 T_m; the terms run in FP32 are the tail m >= Mh whose errors
+// sum to at most eps/20.
+static int fp64_terms(int64_t N, int M, double eps, int64_t ns, int64_t ka) {
+  int lg = 0;
+  while ((1ll << lg) < N) ++lg;
+  const double s2 = 2.0 * std::sin(((double)ka + 0.5) * M_PI / (double)N);
+  const double ferr = 2.0 * std::max(lg, 1) * std::ldexp(1.0, -24);
+  double err = 0.0;
+  int Mh = M;
+  while (Mh > 1) {
+    const double Tm = std::exp(log_gM(Mh - 1, (double)ns) - (Mh - 0.5) * std::log(s2));
+    if (err + ferr * Tm > eps / 20.0) break;
+    err += ferr * Tm;
+    --Mh;
+  }
+  return Mh;
+}
+
+// tcost: the FFTs of one band (all its terms); prune_kb: a band whose rows end at
+// kb <= prune_kb has its FFTs pruned to two windows of bins (fft.cu), costing
+// about prune_f of a full band's FFTs.
 // head: columns n < head come from the dense head block M[0:head, 0:head]
 // (head.cu), so no band cuts below it and every row's recurrence starts there.
-static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, double c_rec, int64_t prune_kb,
+static DPResult plan_bands(int64_t N, int M, double eps_asy, double tcost, double c_rec, int64_t prune_kb,
                            double prune_f, int64_t head) {
   const int64_t H = N / 2;
   DPResult best_res;
@@ -170,25 +210,7 @@ static DPResult plan_bands(int64_t N, int M, double eps_asy, double c_fft, doubl
   const int nc = (int)cands.size();
   // first half row whose n_cut <= cand
   std::vector<int64_t> Kc(nc);
-  for (int i = 0; i < nc; ++i) {
-    double lgm = log_gM(M, (double)cands[i]);
-    double lsmin = (lgm - std::log(eps_asy)) / (M + 0.5) - std::log(2.0);
-    double smin = std::exp(lsmin);
-    int64_t k;
-    if (smin >= 1.0) {
-      k = H;
-    } else {
-      double kk = (double)N * std::asin(smin) / M_PI - 0.5;
-      k = (int64_t)std::ceil(kk);
-      if (k < 0) k = 0;
-      // guard against rounding of asin: move to the first row that satisfies the bound
-      while (k < H && std::sin((k + 0.5) * M_PI / N) < smin) ++k;
-      while (k > 0 && std::sin((k - 0.5) * M_PI / N) >= smin) --k;
-      if (k > H) k = H;
-    }
-    Kc[i] = k;
-  }
-  const double tcost = (double)M * c_fft;
+  for (int i = 0; i < nc; ++i) Kc[i] = first_row(N, M, eps_asy, cands[i]);
   std::vector<double> best(nc, 0.0);
   std::vector<int> choice(nc, -1);
   for (int i = nc - 1; i >= 0; --i) {
@@ -275,6 +297,9 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     // per point, and one recurrence step of a half row (both directions averaged)
     // c_head: one term M_kn c_n of the dense head block (two FP64 instructions
     // in the FP64 form; FP32 arithmetic with a compensated sum in the FP32 form)
+    // c_fft32: an FP32 FFT vector (the FP32 form's, and the FP32 tail terms of
+    // an FP64 plan's bands)
+    const double c_fft32 = (0.43 * lg + 1.7) * (double)N;  // memory and shared-memory bound FP32 passes
     double c_fft, c_rec, c_head;
     int Mmax;
     if (prec == GBDLT_FP64) {
@@ -283,7 +308,7 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
       c_head = 4.0;
       Mmax = 24;
     } else {
-      c_fft = (0.43 * lg + 1.7) * (double)N;   // memory and shared-memory bound FP32 passes
+      c_fft = c_fft32;
       c_rec = 3.4;                             // float-float recurrence
       c_head = 0.25;
       Mmax = 16;
@@ -301,9 +326,18 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     for (int64_t h : heads) {
       const double head_cost = c_head * 0.25 * (double)h * (double)h;  // h^2/4 terms
       for (int M = 2; M <= Mmax; ++M) {
+        // FP64 plans: the FP64 share of a band's terms, estimated on a band
+        // with cut max(h, sqrt N) at its first row (the split is nearly the same
+        // for every band: each starts where its own bound meets eps/20)
+        int Mh = M;
+        if (prec == GBDLT_FP64) {
+          const int64_t ns_rep = std::max<int64_t>(h, 1ll << (lg / 2));
+          Mh = fp64_terms(N, M, eps, ns_rep, first_row(N, M, eps_asy, ns_rep));
+        }
+        const double tcost = (double)Mh * c_fft + (double)(M - Mh) * c_fft32;
         // pruned bands save FP64 work; the FP32 passes are bound by memory
         // latency, where the saving is small
-        DPResult r = plan_bands(N, M, eps_asy, c_fft, c_rec, prune_kb, prec == GBDLT_FP64 ? 0.6 : 1.0, h);
+        DPResult r = plan_bands(N, M, eps_asy, tcost, c_rec, prune_kb, prec == GBDLT_FP64 ? 0.6 : 1.0, h);
         if ((int)r.bands.size() > GBDLT_MAX_BANDS) continue;
         if (r.cost + head_cost < best) {
           best = r.cost + head_cost;
@@ -315,6 +349,12 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     }
     q.K = (int)q.bands.size();
     if (q.K == 0) q.M = 0;
+    // the split of the chosen bands: every band's FP32 tail within its budget
+    q.Mh = q.M;
+    if (prec == GBDLT_FP64 && q.K > 0) {
+      q.Mh = 1;
+      for (const Band& bd : q.bands) q.Mh = std::max(q.Mh, fp64_terms(N, q.M, eps, bd.ns, bd.ka));
+    }
   }
   // recurrence work of the fast path (cheb1 rows), and of the direct method
   // (every Legendre node row against every column, mirrored rows shared)
@@ -544,7 +584,9 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   RecLayout& R = P->rec;
   RecLayout& D = P->drec;
   const int npair = (prm.L + 1) / 2;
-  P->nfft_max = prm.fast ? std::max<int64_t>({(int64_t)prm.K * prm.M, (int64_t)npair, 1}) : 0;
+  P->nfft_max = prm.fast ? std::max<int64_t>({(int64_t)prm.K * prm.Mh, (int64_t)npair, 1}) : 0;
+  // FP32 band vectors of an FP64 plan (terms Mh..M-1)
+  const int64_t nfft32 = prm.fast && prec == GBDLT_FP64 ? (int64_t)prm.K * (prm.M - prm.Mh) : 0;
   // bands whose rows are few enough that their FFTs only touch two windows of
   // bins (four-step sizes only; see fft.cu, pruned passes)
   if (prm.fast && N > 4096) {
@@ -560,7 +602,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   }
   {
     // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
-    const double per_item = 2.0 * P->nfft_max * N * cs + 5.0 * N * ts + 16.0 * (R.nseg_total + D.nseg_total) +
+    const double per_item = 2.0 * P->nfft_max * N * cs + 2.0 * nfft32 * N * 8.0 + 5.0 * N * ts +
+                            16.0 * (R.nseg_total + D.nseg_total) +
                             8.0 * (R.tbuf_total + D.tbuf_total);
     P->bcap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(512.0 * (1 << 20) / per_item)));
     if (max_batch > 0) P->bcap = std::min<int64_t>(P->bcap, max_batch);
@@ -611,6 +654,10 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   };
   size_t o_bufA = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
   size_t o_bufB = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
+  size_t o_bufA32 = bytes_block((size_t)BC * nfft32 * (size_t)N * sizeof(float2));
+  size_t o_b32exp = A.take<int>(std::max<int64_t>(1, 2 * (int64_t)prm.K * prm.M));
+  size_t o_absmax = A.take<unsigned long long>(BC);
+  size_t o_bufB32 = bytes_block((size_t)BC * nfft32 * (size_t)N * sizeof(float2));
   size_t o_v = bytes_block((size_t)BC * N * ts);
   size_t o_chat = bytes_block((size_t)BC * N * ts);
   size_t o_z = bytes_block((size_t)BC * N * ts);
@@ -666,6 +713,10 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   place_layout(D, od);
   P->bufA = base + o_bufA;
   P->bufB = base + o_bufB;
+  P->bufA32 = nfft32 > 0 ? base + o_bufA32 : nullptr;
+  P->bufB32 = nfft32 > 0 ? base + o_bufB32 : nullptr;
+  P->b32exp = nfft32 > 0 ? (int*)(base + o_b32exp) : nullptr;
+  P->absmax = nfft32 > 0 ? (unsigned long long*)(base + o_absmax) : nullptr;
   P->v = base + o_v;
   P->chat = base + o_chat;
   P->z = base + o_z;
@@ -696,6 +747,23 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     }
     up(P->ra_ff, raf.data(), sizeof(float2) * raf.size());
     up(P->rb_ff, rbf.data(), sizeof(float2) * rbf.size());
+  }
+  if (nfft32 > 0) {
+    // power-of-two scales of the FP32 band vectors: forward, the largest weight
+    // C_n h_{m,n} (n >= ns, at n = ns) times 2^e <= 1; transposed, the largest
+    // row factor (2 sin theta)^{-(m+1/2)} (at the band's first row) times 2^e <= 1
+    const int K = prm.K, M = prm.M;
+    std::vector<int> e((size_t)2 * K * M);
+    for (int sb = 0; sb < K; ++sb) {
+      const Band& bd = prm.bands[(size_t)sb];
+      const double l2s = std::log2(2.0 * std::sin(((double)bd.ka + 0.5) * M_PI / (double)N));
+      for (int m = 0; m < M; ++m) {
+        const double l2w = (log_gM(m, (double)bd.ns) - std::log(2.0)) / std::log(2.0);
+        e[(size_t)(sb * M + m)] = -(int)std::ceil(l2w);
+        e[(size_t)(K * M + sb * M + m)] = (int)std::floor((m + 0.5) * l2s);
+      }
+    }
+    up(P->b32exp, e.data(), sizeof(int) * e.size());
   }
   if (nhead > 0) {
     std::vector<double> lam = head_table(nhead);
@@ -754,6 +822,20 @@ namespace {
 // the FFT buffer that does not hold `p`
 inline void* other(Plan& P, const void* p) { return p == P.bufA ? P.bufB : P.bufA; }
 
+// The band FFTs: terms m < Mh in precision T from `a` (result returned), terms
+// m >= Mh (FP64 plans) in FP32 from the plan's FP32 band buffers (result in *y32).
+template <typename T>
+const C2<T>* band_ffts(Plan& P, void* a, int64_t nb, int dir, int transposed, const float2** y32) {
+  const int Ml = P.p.M - P.p.Mh;
+  *y32 = nullptr;
+  const C2<T>* y = nullptr;
+  if (P.p.K > 0 && P.p.Mh > 0)
+    y = (const C2<T>*)launch_fft_bands<T>(P, a, other(P, a), nb, dir, transposed, P.p.Mh);
+  if (P.p.K > 0 && Ml > 0 && P.bufA32)
+    *y32 = (const float2*)launch_fft_bands<float>(P, P.bufA32, P.bufB32, nb, dir, transposed, Ml);
+  return y;
+}
+
 // chat = M c (Sec. 3); also leaves v (values on the cheb1 grid) in P.v
 template <typename T>
 int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
@@ -763,12 +845,15 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   int st = launch_rec_forward<T>(P, P.rec, c, vrec, nb);
   if (st) return st;
   const C2<T>* Y = nullptr;
+  const float2* Y32 = nullptr;
   if (KM > 0) {
-    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, nb);
+    st = launch_absmax<T>(P, c, nb);
     if (st) return st;
-    Y = (const C2<T>*)launch_fft_bands<T>(P, P.bufA, P.bufB, nb, +1, 0);
+    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, (float2*)P.bufA32, nb);
+    if (st) return st;
+    Y = band_ffts<T>(P, P.bufA, nb, +1, 0, &Y32);
   }
-  st = launch_l2c_epi<T>(P, Y, vrec, v, nb);
+  st = launch_l2c_epi<T>(P, Y, Y32, vrec, v, nb);
   if (st) return st;
   st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA, nb);
   if (st) return st;
@@ -822,7 +907,8 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   T* z = (T*)P.z;
   T* rect = (T*)P.tmp;
   T* uhead = (T*)P.chat;  // first `head` coefficients of u (batch stride N)
-  int st;
+  int st = KM > 0 ? launch_absmax<T>(P, g, nb) : GBDLT_OK;
+  if (st) return st;
   const C2<T>* Y = nullptr;  // A4^T FFT output
   if (npair > 0) {
     st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, inc0, npair, nb);
@@ -834,13 +920,14 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
     Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), nb, +1);
   }
   void* U = Y ? other(P, Y) : P.bufA;
-  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, nb);
+  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, (float2*)P.bufA32, nb);
   if (st) return st;
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
-  if (KM > 0) F2 = (const C2<T>*)launch_fft_bands<T>(P, U, other(P, U), nb, -1, 1);
-  st = launch_l2ct_epi<T>(P, F2, rect, out, scale_s, nb);
+  const float2* F32 = nullptr;
+  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &F32);
+  st = launch_l2ct_epi<T>(P, F2, F32, rect, out, scale_s, nb);
   if (st) return st;
   return launch_head_t<T>(P, uhead, out, scale_s, nb);
 }
@@ -851,17 +938,20 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   T* z = (T*)P.z;
   T* rect = (T*)P.tmp;
-  int st = launch_fcs_pro<T>(P, y, (C2<T>*)P.bufA, 1, nb);
+  int st = KM > 0 ? launch_absmax<T>(P, y, nb) : GBDLT_OK;
+  if (st) return st;
+  st = launch_fcs_pro<T>(P, y, (C2<T>*)P.bufA, 1, nb);
   if (st) return st;
   const void* Y = launch_fft<T>(P, P.bufA, P.bufB, nb, +1);
   void* U = other(P, Y);
-  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, nb);
+  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, (float2*)P.bufA32, nb);
   if (st) return st;
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
-  if (KM > 0) F2 = (const C2<T>*)launch_fft_bands<T>(P, U, other(P, U), nb, -1, 1);
-  st = launch_l2ct_epi<T>(P, F2, rect, out, 0, nb);
+  const float2* F32 = nullptr;
+  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &F32);
+  st = launch_l2ct_epi<T>(P, F2, F32, rect, out, 0, nb);
   if (st) return st;
   return launch_head_t<T>(P, y, out, 0, nb);
 }
@@ -1115,6 +1205,7 @@ static void fill_public(const Params& q, size_t ws, gbdlt_params* out) {
   out->method = q.method;
   out->direct_steps = q.direct_steps;
   out->head = q.head;
+  out->M_fp32 = q.M - q.Mh;
 }
 
 int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out) {

@@ -26,6 +26,8 @@
 //                      Z_l = FCS((n/N)^l chat), t_k = N dtheta_k; terms paired (F2)
 //  tayt_pro / tayt_epi transposed Taylor sum (Sec. 4 item 2), pairs through T2
 //  l2ct_pro / l2ct_epi transposed asymptotic part (Sec. 4 item 3)
+#include <algorithm>
+
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -78,6 +80,23 @@ __device__ __forceinline__ int band_of(const BandArgs& B, int64_t k, int64_t N) 
   return -1;
 }
 
+// FP32 band vectors of FP64 plans are scaled by exact powers of two: 2^{e_sm - E}
+// with e_sm a per-(band, term) exponent of the plan (so that the largest entry
+// of the vector is about 1 for unit input) and E the exponent of the item's
+// largest input magnitude; the epilogues undo it in FP64.
+struct Scale32 {
+  const int* e;                         // [2][K][M]: forward, transposed
+  const unsigned long long* amax;       // [item] bits of max |input| (a non-negative double)
+};
+__device__ __forceinline__ double pow2i(int e) {
+  e = max(-1022, min(1023, e));
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ int item_exp(const Scale32& S, int64_t bt) {
+  const unsigned long long b = S.amax[bt];
+  return b == 0ull ? 0 : (int)((b >> 52) & 0x7ff) - 1023;
+}
+
 // 1/l for the Taylor coefficients t^l / l! (products instead of divisions)
 __constant__ double kInvInt[48] = {
     0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,  1.0 / 9,
@@ -111,15 +130,20 @@ struct HTerm {
   }
 };
 
+// terms m < Mh go to U ([band][m][N], precision T), terms m >= Mh to U32
+// ([band][m - Mh][N], FP32)
 template <typename T>
-__global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, int64_t N, int M,
-                          BandArgs B, const double* __restrict__ Cn, const double* __restrict__ Hnm,
-                          TwArgs<T> tw4N) {
+__global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, float2* __restrict__ U32, int64_t N,
+                          int M, int Mh, BandArgs B, const double* __restrict__ Cn,
+                          const double* __restrict__ Hnm, TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
+  const int Ml = M - Mh;
+  const int E = U32 ? item_exp(S, bt) : 0;
   c += bt * N;
-  U += bt * (int64_t)B.K * M * N;
+  U += bt * (int64_t)B.K * Mh * N;
+  if (U32) U32 += bt * (int64_t)B.K * Ml * N;
   const T cv = c[n];
   const C2<T> e = twid<T>(tw4N, n);
   const C2<T> ce = mk<T>(cv * e.x, cv * e.y);
@@ -128,7 +152,15 @@ __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, int64_
   for (int m = 0; m < M; ++m) {
     const T a = H.at(m);
     const C2<T> val = mk<T>(a * ce.x, a * ce.y);
-    for (int s = 0; s < B.K; ++s) U[(int64_t)(s * M + m) * N + n] = (n >= B.ns[s]) ? val : zero;
+    if (m < Mh) {
+      for (int s = 0; s < B.K; ++s) U[(int64_t)(s * Mh + m) * N + n] = (n >= B.ns[s]) ? val : zero;
+    } else {
+      for (int s = 0; s < B.K; ++s) {
+        const double sc = pow2i(S.e[s * M + m] - E);
+        U32[(int64_t)(s * Ml + m - Mh) * N + n] =
+            (n >= B.ns[s]) ? make_float2((float)(val.x * sc), (float)(val.y * sc)) : make_float2(0.f, 0.f);
+      }
+    }
   }
 }
 
@@ -179,14 +211,17 @@ __global__ void k_hnm_init(double* __restrict__ Hnm, const double* __restrict__ 
 }
 
 template <typename T>
-__global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const T* __restrict__ vrec, T* __restrict__ v,
-                          int64_t N, int M, BandArgs B, const RowAR* __restrict__ AR) {
+__global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const float2* __restrict__ Y32, const T* __restrict__ vrec,
+                          T* __restrict__ v, int64_t N, int M, int Mh, BandArgs B, const RowAR* __restrict__ AR,
+                          Scale32 S) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int64_t bt = blockIdx.y;
+  const int Ml = M - Mh;
   vrec += bt * N;
   v += bt * N;
-  if (Y) Y += bt * (int64_t)B.K * M * N;
+  if (Y) Y += bt * (int64_t)B.K * Mh * N;
+  if (Y32) Y32 += bt * (int64_t)B.K * Ml * N;
   T acc = vrec[k];
   const int s = band_of(B, k, N);
   if (s >= 0) {
@@ -194,9 +229,16 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const T* __restrict__ vre
     row_factors<T>(k, N, AR, al, rho);
     const bool odd = k & 1;
     const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
-    const C2<T>* y = Y + (int64_t)s * M * N + idx;
+    const C2<T>* y = Y + (int64_t)s * Mh * N + idx;
     for (int m = 0; m < M; ++m) {
-      C2<T> z = y[(int64_t)m * N];
+      C2<T> z;
+      if (m < Mh) {
+        z = y[(int64_t)m * N];
+      } else {
+        const float2 w = Y32[(int64_t)(s * Ml + m - Mh) * N + idx];
+        const double sc = pow2i(item_exp(S, bt) - S.e[s * M + m]);
+        z = mk<T>((T)(w.x * sc), (T)(w.y * sc));
+      }
       if (odd) z.y = -z.y;
       acc += al.x * z.x - al.y * z.y;
       al = cmul<T>(al, rho);
@@ -441,15 +483,17 @@ __device__ __forceinline__ T row_z(const C2<T>* Y, const T* g, const double* wsc
 template <typename T>
 __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
                            const double* __restrict__ wscale, T* __restrict__ zout,
-                           C2<T>* __restrict__ U, int64_t N, int M, BandArgs B,
-                           const RowAR* __restrict__ AR) {
+                           C2<T>* __restrict__ U, float2* __restrict__ U32, int64_t N, int M, int Mh, BandArgs B,
+                           const RowAR* __restrict__ AR, Scale32 S) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
   const int64_t bt = blockIdx.y;
+  const int Ml = M - Mh;
   if (Y) Y += bt * N;
   if (g) g += bt * N;
   zout += bt * N;
-  U += bt * (int64_t)B.K * M * N;
+  U += bt * (int64_t)B.K * Mh * N;
+  if (U32) U32 += bt * (int64_t)B.K * Ml * N;
   const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
   const T z0 = row_z<T>(Y, g, wscale, k0, N);
   const T z1 = row_z<T>(Y, g, wscale, k1, N);
@@ -463,10 +507,24 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
     // beta = z alpha; a = Re beta, h = (-1)^k Im beta
     const C2<T> v0 = mk<T>(z0 * al0.x, z0 * al0.y);
     const C2<T> v1 = mk<T>(z1 * al1.x, -z1 * al1.y);
-    for (int s = 0; s < B.K; ++s) {
-      C2<T>* u = U + (int64_t)(s * M + m) * N;
-      u[kp] = (s == s0) ? v0 : mk<T>(0, 0);
-      u[N - 1 - kp] = (s == s1) ? v1 : mk<T>(0, 0);
+    if (m < Mh) {
+      for (int s = 0; s < B.K; ++s) {
+        C2<T>* u = U + (int64_t)(s * Mh + m) * N;
+        u[kp] = (s == s0) ? v0 : mk<T>(0, 0);
+        u[N - 1 - kp] = (s == s1) ? v1 : mk<T>(0, 0);
+      }
+    } else {
+      const int E = item_exp(S, bt);
+      const int* et = S.e + B.K * M;
+      const double sc0 = s0 >= 0 ? pow2i(et[s0 * M + m] - E) : 0.0;
+      const double sc1 = s1 >= 0 ? pow2i(et[s1 * M + m] - E) : 0.0;
+      const float2 w0 = make_float2((float)(v0.x * sc0), (float)(v0.y * sc0));
+      const float2 w1 = make_float2((float)(v1.x * sc1), (float)(v1.y * sc1));
+      for (int s = 0; s < B.K; ++s) {
+        float2* u = U32 + (int64_t)(s * Ml + m - Mh) * N;
+        u[kp] = (s == s0) ? w0 : make_float2(0.f, 0.f);
+        u[N - 1 - kp] = (s == s1) ? w1 : make_float2(0.f, 0.f);
+      }
     }
     if (s0 >= 0) al0 = cmul<T>(al0, rho0);
     if (s1 >= 0) al1 = cmul<T>(al1, rho1);
@@ -480,15 +538,17 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
 // terms is taken before the rotation,
 //   out_n = rect_n + Re(e_n sum_m C_n h_{m,n} sum_{s: n >= n_s} F^{(s,m)}_{N-n}).
 template <typename T>
-__global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ rect, T* __restrict__ out,
-                           int64_t N, int M, BandArgs B, const double* __restrict__ Cn,
-                           const double* __restrict__ Hnm, int scale_s, TwArgs<T> tw4N) {
+__global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const float2* __restrict__ F32, const T* __restrict__ rect,
+                           T* __restrict__ out, int64_t N, int M, int Mh, BandArgs B, const double* __restrict__ Cn,
+                           const double* __restrict__ Hnm, int scale_s, TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
+  const int Ml = M - Mh;
   rect += bt * N;
   out += bt * N;
-  if (F) F += bt * (int64_t)B.K * M * N;
+  if (F) F += bt * (int64_t)B.K * Mh * N;
+  if (F32) F32 += bt * (int64_t)B.K * Ml * N;
   T acc = rect[n];
   if (B.K > 0 && M > 0) {
     const int64_t nm = (N - n) & (N - 1);
@@ -498,8 +558,23 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const T* __restrict__ re
       HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
       C2<T> V = mk<T>((T)0, (T)0);
       for (int m = 0; m < M; ++m) {
-        C2<T> X = F[(int64_t)(s0 * M + m) * N + nm];
-        for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * M + m) * N + nm]);
+        C2<T> X;
+        if (m < Mh) {
+          X = F[(int64_t)(s0 * Mh + m) * N + nm];
+          for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * Mh + m) * N + nm]);
+        } else {
+          // bands carry their own scales: undo each in FP64 before the sum
+          const int E = item_exp(S, bt);
+          const int* et = S.e + B.K * M;
+          double wx = 0.0, wy = 0.0;
+          for (int s = s0; s < B.K; ++s) {
+            const float2 q = F32[(int64_t)(s * Ml + m - Mh) * N + nm];
+            const double sc = pow2i(E - et[s * M + m]);
+            wx += (double)q.x * sc;
+            wy += (double)q.y * sc;
+          }
+          X = mk<T>((T)wx, (T)wy);
+        }
         const T hm = H.at(m);
         V = mk<T>(V.x + hm * X.x, V.y + hm * X.y);
       }
@@ -527,13 +602,28 @@ __global__ void k_scale(const T* __restrict__ in, T* __restrict__ out, const dou
 constexpr int TPB = 256;
 inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
+Scale32 scale32(const Plan& P) { return Scale32{P.b32exp, P.absmax}; }
+
+// amax[item] = max over n of |x_n| as the bits of a non-negative double (their
+// integer order is the order of the values); amax is zeroed before the launch
+template <typename T>
+__global__ void k_absmax(const T* __restrict__ x, int64_t N, unsigned long long* __restrict__ amax) {
+  x += (int64_t)blockIdx.y * N;
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs((double)x[i]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(amax + blockIdx.y, (unsigned long long)__double_as_longlong(m));
+}
+
 }  // namespace
 
 template <typename T>
-int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb) {
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, float2* U32, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(c, U, P.p.N, P.p.M, band_args(P), P.Cn,
-                                                                       P.Hnm, tw);
+  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(c, U, U32, P.p.N, P.p.M, P.p.Mh, band_args(P),
+                                                                       P.Cn, P.Hnm, tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -543,9 +633,9 @@ int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, int64_t nb) {
   return check_launch();
 }
 template <typename T>
-int launch_l2c_epi(Plan& P, const C2<T>* Y, const T* vrec, T* v, int64_t nb) {
-  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, vrec, v, P.p.N, P.p.M, band_args(P),
-                                                                       P.row_ar);
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const float2* Y32, const T* vrec, T* v, int64_t nb) {
+  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, Y32, vrec, v, P.p.N, P.p.M, P.p.Mh,
+                                                                       band_args(P), P.row_ar, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -649,10 +739,10 @@ int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int n
   return check_launch();
 }
 template <typename T>
-int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, int64_t nb) {
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, float2* U32, int64_t nb) {
   const double* w = use_w ? P.w : nullptr;
-  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(Y, g, w, z, U, P.p.N, P.p.M, band_args(P),
-                                                                           P.row_ar);
+  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(Y, g, w, z, U, U32, P.p.N, P.p.M, P.p.Mh,
+                                                                           band_args(P), P.row_ar, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -662,16 +752,27 @@ int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>*
   return check_launch();
 }
 template <typename T>
-int launch_l2ct_epi(Plan& P, const C2<T>* F, const T* rect, T* out, int scale_s, int64_t nb) {
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const float2* F32, const T* rect, T* out, int scale_s, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, rect, out, P.p.N, P.p.M, band_args(P), P.Cn,
-                                                                        P.Hnm, scale_s, tw);
+  k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, F32, rect, out, P.p.N, P.p.M, P.p.Mh,
+                                                                        band_args(P), P.Cn, P.Hnm, scale_s, tw,
+                                                                        scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
     (void)KM;
     launched(P, "l2ct_epi", (double)nb * (4.0 * KM * N), (double)nb * (KM * N * cs + 2.0 * ts * N));
   }
+  return check_launch();
+}
+template <typename T>
+int launch_absmax(Plan& P, const T* x, int64_t nb) {
+  if (!P.absmax) return GBDLT_OK;
+  if (cudaMemsetAsync(P.absmax, 0, sizeof(unsigned long long) * (size_t)nb, P.stream) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  const int64_t blocks = std::min<int64_t>(nblk(P.p.N), 2 * 152);
+  k_absmax<T><<<dim3((unsigned)blocks, (unsigned)nb), TPB, 0, P.stream>>>(x, P.p.N, P.absmax);
+  launched(P, "absmax", (double)nb * P.p.N, (double)nb * sizeof(T) * P.p.N);
   return check_launch();
 }
 template <typename T>
@@ -700,8 +801,9 @@ int launch_stage_tables_init(Plan& P) {
 }
 
 #define INST(T)                                                                              \
-  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*, int64_t);                                   \
-  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const T*, T*, int64_t);                         \
+  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*, float2*, int64_t);                          \
+  template int launch_absmax<T>(Plan&, const T*, int64_t);                                            \
+  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const float2*, const T*, T*, int64_t);          \
   template int launch_a4_pro<T>(Plan&, const T*, C2<T>*, int64_t);                                    \
   template int launch_a4_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                    \
   template int launch_fcs_pro<T>(Plan&, const T*, C2<T>*, int, int64_t);                              \
@@ -710,8 +812,8 @@ int launch_stage_tables_init(Plan& P) {
   template int launch_tay_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int, int64_t);                   \
   template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, int, int, int64_t);                   \
   template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int, int64_t, int64_t);                \
-  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, int64_t);           \
-  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int64_t);                   \
+  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, float2*, int64_t);  \
+  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const float2*, const T*, T*, int, int64_t);    \
   template int launch_scale<T>(Plan&, const T*, T*, int, int64_t);
 INST(double)
 INST(float)
