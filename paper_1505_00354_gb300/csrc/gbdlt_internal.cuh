@@ -210,8 +210,9 @@ struct Plan {
   // used by the fused radix-4 layers ([2 directions][4096][sx, sy, t, swap])
   double2* twfull = nullptr;
   double2* lf_tab = nullptr;
-  // FP64 stage tables: C_n h_{m,n} ([M][N], the asymptotic expansion's column
-  // weights) and per cheb1 row {alpha_k, rho_k} (the expansion's row factors)
+  // FP64 stage tables: C_n h_{m,n} ([Mh][N], the asymptotic expansion's column
+  // weights of the FP64 terms) and per cheb1 row {alpha_k, rho_k} (the expansion's
+  // row factors)
   double* Hnm = nullptr;
   RowAR* row_ar = nullptr;
   // dense head block: Lam'_j = sqrt(2/pi) Gamma(j+1/2)/Gamma(j+1), j < head
@@ -232,6 +233,7 @@ struct Plan {
   // transposed) and per batch item the bits of max |chain input|
   int* b32exp = nullptr;
   unsigned long long* absmax = nullptr;
+  float* H32 = nullptr;  // [M - Mh][N] C_n h_{m,n} 2^{e_{K-1,m}} of the FP32 terms (stages.cu)
   int prune_bands = 0;   // leading bands whose FFTs are pruned to their row windows
   int prune_R = 0;       // window half-width of those bands (bins)
   int64_t bcap = 1;      // batch items one pass over the workspace holds

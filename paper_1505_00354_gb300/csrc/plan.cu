@@ -627,7 +627,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   size_t o_twfull = A.take<double2>(fp64_tabs && N > 4096 ? N : 1);
   size_t o_lf = A.take<double2>(4 * 4096);
   const bool stage_tabs = fp64_tabs && prm.K > 0 && prm.M > 0;
-  size_t o_hnm = A.take<double>(stage_tabs ? (int64_t)prm.M * N : 1);
+  size_t o_hnm = A.take<double>(stage_tabs ? (int64_t)prm.Mh * N : 1);
   size_t o_ar = A.take<RowAR>(stage_tabs ? N : 1);
   const int64_t nhead = prm.fast ? prm.head : 0;
   size_t o_lam = A.take<double>(std::max<int64_t>(nhead, 1)), o_lamf = A.take<float>(std::max<int64_t>(nhead, 1));
@@ -656,6 +656,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   size_t o_bufB = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
   size_t o_bufA32 = bytes_block((size_t)BC * nfft32 * (size_t)N * sizeof(float2));
   size_t o_b32exp = A.take<int>(std::max<int64_t>(1, 2 * (int64_t)prm.K * prm.M));
+  size_t o_h32 = A.take<float>(std::max<int64_t>(1, nfft32 > 0 ? (int64_t)(prm.M - prm.Mh) * N : 1));
   size_t o_absmax = A.take<unsigned long long>(BC);
   size_t o_bufB32 = bytes_block((size_t)BC * nfft32 * (size_t)N * sizeof(float2));
   size_t o_v = bytes_block((size_t)BC * N * ts);
@@ -716,6 +717,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   P->bufA32 = nfft32 > 0 ? base + o_bufA32 : nullptr;
   P->bufB32 = nfft32 > 0 ? base + o_bufB32 : nullptr;
   P->b32exp = nfft32 > 0 ? (int*)(base + o_b32exp) : nullptr;
+  P->H32 = nfft32 > 0 ? (float*)(base + o_h32) : nullptr;
   P->absmax = nfft32 > 0 ? (unsigned long long*)(base + o_absmax) : nullptr;
   P->v = base + o_v;
   P->chat = base + o_chat;

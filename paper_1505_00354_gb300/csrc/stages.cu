@@ -87,10 +87,19 @@ __device__ __forceinline__ int band_of(const BandArgs& B, int64_t k, int64_t N) 
 struct Scale32 {
   const int* e;                         // [2][K][M]: forward, transposed
   const unsigned long long* amax;       // [item] bits of max |input| (a non-negative double)
+  const float* H32;                     // [M - Mh][N]: C_n h_{m,n} 2^{e_{K-1,m}} (0 below the last cut)
 };
 __device__ __forceinline__ double pow2i(int e) {
   e = max(-1022, min(1023, e));
   return __longlong_as_double((long long)(1023 + e) << 52);
+}
+// 2^e as a float (e clamped to the normal range)
+__device__ __forceinline__ float pow2f(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((127 + e) << 23);
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ int item_exp(const Scale32& S, int64_t bt) {
   const unsigned long long b = S.amax[bt];
@@ -149,16 +158,23 @@ __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, float2
   const C2<T> ce = mk<T>(cv * e.x, cv * e.y);
   HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
   const C2<T> zero = mk<T>((T)0, (T)0);
-  for (int m = 0; m < M; ++m) {
+  for (int m = 0; m < Mh; ++m) {
     const T a = H.at(m);
     const C2<T> val = mk<T>(a * ce.x, a * ce.y);
-    if (m < Mh) {
-      for (int s = 0; s < B.K; ++s) U[(int64_t)(s * Mh + m) * N + n] = (n >= B.ns[s]) ? val : zero;
-    } else {
+    for (int s = 0; s < B.K; ++s) U[(int64_t)(s * Mh + m) * N + n] = (n >= B.ns[s]) ? val : zero;
+  }
+  if (Ml > 0) {
+    // FP32 terms: C_n h_{m,n} 2^{e_{s,m}} c_n e_n 2^{-E} from the float table
+    // H32 = C_n h_{m,n} 2^{e_{K-1,m}} times the band's exact 2^{e_{s,m} - e_{K-1,m}}
+    const double sE = pow2i(-E);
+    const float2 cf = make_float2((float)((double)ce.x * sE), (float)((double)ce.y * sE));
+    const int* eK = S.e + (B.K - 1) * M;
+    for (int m = Mh; m < M; ++m) {
+      const float h32 = S.H32[(int64_t)(m - Mh) * N + n];
       for (int s = 0; s < B.K; ++s) {
-        const double sc = pow2i(S.e[s * M + m] - E);
+        const float a = h32 * pow2f(S.e[s * M + m] - eK[m]);
         U32[(int64_t)(s * Ml + m - Mh) * N + n] =
-            (n >= B.ns[s]) ? make_float2((float)(val.x * sc), (float)(val.y * sc)) : make_float2(0.f, 0.f);
+            (n >= B.ns[s]) ? make_float2(a * cf.x, a * cf.y) : make_float2(0.f, 0.f);
       }
     }
   }
@@ -197,14 +213,20 @@ __global__ void k_row_factors_init(RowAR* __restrict__ AR, int64_t N) {
   AR[k] = RowAR{ca * sq, sa * sq, st * g, -ct * g};
 }
 
-// Hnm[m N + n] = C_n h_{m,n} (the recurrence in FP64, once per plan)
-__global__ void k_hnm_init(double* __restrict__ Hnm, const double* __restrict__ Cn, int64_t N, int M) {
+// Hnm[m N + n] = C_n h_{m,n} for m < Mh (the recurrence in FP64, once per plan);
+// for the FP32 terms m >= Mh, H32[(m - Mh) N + n] = C_n h_{m,n} 2^{eK[m]} as a
+// float, 0 below the smallest band cut ns_min (never read there)
+__global__ void k_hnm_init(double* __restrict__ Hnm, float* __restrict__ H32, const double* __restrict__ Cn,
+                           int64_t N, int M, int Mh, const int* __restrict__ eK, int64_t ns_min) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   double h = 1.0;
   const double cn = Cn[n];
   for (int m = 0; m < M; ++m) {
-    Hnm[(int64_t)m * N + n] = cn * h;
+    if (m < Mh)
+      Hnm[(int64_t)m * N + n] = cn * h;
+    else
+      H32[(int64_t)(m - Mh) * N + n] = n >= ns_min ? (float)(cn * h * pow2i(eK[m])) : 0.f;
     const double mh = (double)m + 0.5;
     h = h * (mh * mh) / (((double)m + 1.0) * ((double)n + (double)m + 1.5));
   }
@@ -230,18 +252,31 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const float2* __restrict_
     const bool odd = k & 1;
     const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
     const C2<T>* y = Y + (int64_t)s * Mh * N + idx;
-    for (int m = 0; m < M; ++m) {
-      C2<T> z;
-      if (m < Mh) {
-        z = y[(int64_t)m * N];
-      } else {
-        const float2 w = Y32[(int64_t)(s * Ml + m - Mh) * N + idx];
-        const double sc = pow2i(item_exp(S, bt) - S.e[s * M + m]);
-        z = mk<T>((T)(w.x * sc), (T)(w.y * sc));
-      }
+    for (int m = 0; m < Mh; ++m) {
+      C2<T> z = y[(int64_t)m * N];
       if (odd) z.y = -z.y;
       acc += al.x * z.x - al.y * z.y;
       al = cmul<T>(al, rho);
+    }
+    if (Ml > 0) {
+      // FP32 terms: with the band's FFT output scaled by 2^{e_{s,m} - E}, term m
+      // adds 2^E Re(b_m z_m), b_m = alpha rho^m 2^{-e_{s,m}} (al = alpha rho^Mh here)
+      const int* e = S.e + s * M;
+      const double b0 = pow2i(-e[Mh]);
+      float2 b = make_float2((float)((double)al.x * b0), (float)((double)al.y * b0));
+      const float2 r = make_float2((float)rho.x, (float)rho.y);
+      const float2* y32 = Y32 + (int64_t)s * Ml * N + idx;
+      float a32 = 0.f;
+      for (int m = Mh; m < M; ++m) {
+        float2 z = y32[(int64_t)(m - Mh) * N];
+        if (odd) z.y = -z.y;
+        a32 = fmaf(b.x, z.x, fmaf(-b.y, z.y, a32));
+        if (m + 1 < M) {
+          const float p = pow2f(e[m] - e[m + 1]);
+          b = cmulf(b, make_float2(r.x * p, r.y * p));
+        }
+      }
+      acc += (T)((double)a32 * pow2i(item_exp(S, bt)));
     }
   }
   v[k] = acc;
@@ -503,31 +538,51 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
   C2<T> al0 = mk<T>(0, 0), rho0 = mk<T>(0, 0), al1 = mk<T>(0, 0), rho1 = mk<T>(0, 0);
   if (s0 >= 0) row_factors<T>(k0, N, AR, al0, rho0);
   if (s1 >= 0) row_factors<T>(k1, N, AR, al1, rho1);
-  for (int m = 0; m < M; ++m) {
+  for (int m = 0; m < Mh; ++m) {
     // beta = z alpha; a = Re beta, h = (-1)^k Im beta
     const C2<T> v0 = mk<T>(z0 * al0.x, z0 * al0.y);
     const C2<T> v1 = mk<T>(z1 * al1.x, -z1 * al1.y);
-    if (m < Mh) {
-      for (int s = 0; s < B.K; ++s) {
-        C2<T>* u = U + (int64_t)(s * Mh + m) * N;
-        u[kp] = (s == s0) ? v0 : mk<T>(0, 0);
-        u[N - 1 - kp] = (s == s1) ? v1 : mk<T>(0, 0);
-      }
-    } else {
-      const int E = item_exp(S, bt);
-      const int* et = S.e + B.K * M;
-      const double sc0 = s0 >= 0 ? pow2i(et[s0 * M + m] - E) : 0.0;
-      const double sc1 = s1 >= 0 ? pow2i(et[s1 * M + m] - E) : 0.0;
-      const float2 w0 = make_float2((float)(v0.x * sc0), (float)(v0.y * sc0));
-      const float2 w1 = make_float2((float)(v1.x * sc1), (float)(v1.y * sc1));
+    for (int s = 0; s < B.K; ++s) {
+      C2<T>* u = U + (int64_t)(s * Mh + m) * N;
+      u[kp] = (s == s0) ? v0 : mk<T>(0, 0);
+      u[N - 1 - kp] = (s == s1) ? v1 : mk<T>(0, 0);
+    }
+    if (s0 >= 0) al0 = cmul<T>(al0, rho0);
+    if (s1 >= 0) al1 = cmul<T>(al1, rho1);
+  }
+  if (Ml > 0) {
+    // FP32 terms: beta 2^{g_{s,m} - E} = (z 2^{-E}) gamma_m with gamma_m =
+    // alpha rho^m 2^{g_{s,m}}, advanced in FP32 by rho 2^{g_{s,m+1} - g_{s,m}}
+    // (al = alpha rho^Mh here)
+    const double sE = pow2i(-item_exp(S, bt));
+    const float f0 = (float)((double)z0 * sE), f1 = (float)((double)z1 * sE);
+    const int* g0 = S.e + B.K * M + max(s0, 0) * M;
+    const int* g1 = S.e + B.K * M + max(s1, 0) * M;
+    float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f), r0 = c0, r1 = c0;
+    if (s0 >= 0) {
+      const double q = pow2i(g0[Mh]);
+      c0 = make_float2((float)((double)al0.x * q), (float)((double)al0.y * q));
+      r0 = make_float2((float)rho0.x, (float)rho0.y);
+    }
+    if (s1 >= 0) {
+      const double q = pow2i(g1[Mh]);
+      c1 = make_float2((float)((double)al1.x * q), (float)((double)al1.y * q));
+      r1 = make_float2((float)rho1.x, (float)rho1.y);
+    }
+    for (int m = Mh; m < M; ++m) {
+      const float2 w0 = make_float2(f0 * c0.x, f0 * c0.y);
+      const float2 w1 = make_float2(f1 * c1.x, -f1 * c1.y);
       for (int s = 0; s < B.K; ++s) {
         float2* u = U32 + (int64_t)(s * Ml + m - Mh) * N;
         u[kp] = (s == s0) ? w0 : make_float2(0.f, 0.f);
         u[N - 1 - kp] = (s == s1) ? w1 : make_float2(0.f, 0.f);
       }
+      if (m + 1 < M) {
+        const float p0 = pow2f(g0[m + 1] - g0[m]), p1 = pow2f(g1[m + 1] - g1[m]);
+        c0 = cmulf(c0, make_float2(r0.x * p0, r0.y * p0));
+        c1 = cmulf(c1, make_float2(r1.x * p1, r1.y * p1));
+      }
     }
-    if (s0 >= 0) al0 = cmul<T>(al0, rho0);
-    if (s1 >= 0) al1 = cmul<T>(al1, rho1);
   }
 }
 
@@ -557,26 +612,32 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const float2* __restrict
     if (s0 < B.K) {
       HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
       C2<T> V = mk<T>((T)0, (T)0);
-      for (int m = 0; m < M; ++m) {
-        C2<T> X;
-        if (m < Mh) {
-          X = F[(int64_t)(s0 * Mh + m) * N + nm];
-          for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * Mh + m) * N + nm]);
-        } else {
-          // bands carry their own scales: undo each in FP64 before the sum
-          const int E = item_exp(S, bt);
-          const int* et = S.e + B.K * M;
-          double wx = 0.0, wy = 0.0;
-          for (int s = s0; s < B.K; ++s) {
-            const float2 q = F32[(int64_t)(s * Ml + m - Mh) * N + nm];
-            const double sc = pow2i(E - et[s * M + m]);
-            wx += (double)q.x * sc;
-            wy += (double)q.y * sc;
-          }
-          X = mk<T>((T)wx, (T)wy);
-        }
+      for (int m = 0; m < Mh; ++m) {
+        C2<T> X = F[(int64_t)(s0 * Mh + m) * N + nm];
+        for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * Mh + m) * N + nm]);
         const T hm = H.at(m);
         V = mk<T>(V.x + hm * X.x, V.y + hm * X.y);
+      }
+      if (Ml > 0) {
+        // FP32 terms: band s's output is scaled by 2^{g_{s,m} - E}; with
+        // H32 = C_n h_{m,n} 2^{e_{K-1,m}} the term is 2^E H32 sum_s 2^{-e_{K-1,m} - g_{s,m}} F32
+        const int* eK = S.e + (B.K - 1) * M;
+        const int* et = S.e + B.K * M;
+        float vx = 0.f, vy = 0.f;
+        for (int m = Mh; m < M; ++m) {
+          float xx = 0.f, xy = 0.f;
+          for (int s = s0; s < B.K; ++s) {
+            const float2 q = F32[(int64_t)(s * Ml + m - Mh) * N + nm];
+            const float p = pow2f(-eK[m] - et[s * M + m]);
+            xx = fmaf(p, q.x, xx);
+            xy = fmaf(p, q.y, xy);
+          }
+          const float h32 = S.H32[(int64_t)(m - Mh) * N + n];
+          vx = fmaf(h32, xx, vx);
+          vy = fmaf(h32, xy, vy);
+        }
+        const double sE = pow2i(item_exp(S, bt));
+        V = mk<T>(V.x + (T)((double)vx * sE), V.y + (T)((double)vy * sE));
       }
       const C2<T> e = twid<T>(tw4N, n);
       acc += e.x * V.x - e.y * V.y;
@@ -602,7 +663,7 @@ __global__ void k_scale(const T* __restrict__ in, T* __restrict__ out, const dou
 constexpr int TPB = 256;
 inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
-Scale32 scale32(const Plan& P) { return Scale32{P.b32exp, P.absmax}; }
+Scale32 scale32(const Plan& P) { return Scale32{P.b32exp, P.absmax, P.H32}; }
 
 // amax[item] = max over n of |x_n| as the bits of a non-negative double (their
 // integer order is the order of the values); amax is zeroed before the launch
@@ -794,7 +855,10 @@ int launch_stage_tables_init(Plan& P) {
     count_launch();
   }
   if (P.Hnm) {
-    k_hnm_init<<<nblk(N), TPB, 0, P.stream>>>(P.Hnm, P.Cn, N, P.p.M);
+    const int Mt = P.H32 ? P.p.M : P.p.Mh;  // FP32 tail entries only with their table
+    const int* eK = P.H32 ? P.b32exp + (P.p.K - 1) * P.p.M : nullptr;
+    const int64_t ns_min = P.p.K > 0 ? P.p.bands[(size_t)P.p.K - 1].ns : N;
+    k_hnm_init<<<nblk(N), TPB, 0, P.stream>>>(P.Hnm, P.H32, P.Cn, N, Mt, P.p.Mh, eK, ns_min);
     count_launch();
   }
   return check_launch();
