@@ -175,7 +175,7 @@ struct RecLayout {
   int32_t* cut = nullptr;     // [H] recurrence cut per half row
   int64_t* poff = nullptr;    // [H] offset of row k's segments
   int32_t* cta_rb = nullptr;  // [ncta]
-  int32_t* cta_j = nullptr;   // [ncta]
+  int32_t* cta_j = nullptr;   // [ncta] first segment j, A - 1 << 16, q - 1 << 20 (rec.cu, RecTask)
   int64_t* toff = nullptr;    // [nblocks] offset of row block partials (length nseg_max*S)
   int32_t* bcutmax = nullptr; // [nblocks] nseg_max(rb) * S (partial array length)
   double* xm1 = nullptr;      // [H] x_k - 1 of the rows (cheb1 grid, or Legendre nodes)

@@ -507,7 +507,9 @@ struct LayoutHost {
   std::vector<int64_t> poff, toff;
 };
 
-void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int j0, LayoutHost& h) {
+void build_ctas(RecLayout& R, int64_t H, int S, int j0, int pack, LayoutHost& h);
+
+void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int j0, int sms, LayoutHost& h) {
   R.H = H;
   R.S = S;
   R.j0 = j0;
@@ -526,26 +528,52 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
   R.nseg_total = o;
   R.half_steps = steps;
   R.nblocks = (H + 255) / 256;
-  int64_t to = 0;
-  for (int64_t rb = 0; rb < R.nblocks; ++rb) {
-    int32_t mc = 0;
-    for (int64_t k = rb * 256; k < std::min<int64_t>(H, rb * 256 + 256); ++k) mc = std::max(mc, h.cut[(size_t)k]);
-    const int64_t nsm = (mc + S - 1) / S;
-    h.maxcut.push_back(mc);
-    h.toff.push_back(to);
-    to += std::max<int64_t>(0, nsm - j0) * S;
-    for (int64_t j = j0; j < nsm; ++j) {
-      h.cta_rb.push_back((int32_t)rb);
-      h.cta_j.push_back((int32_t)j);
-    }
+  // CTAs: segments of a row block, several per CTA when their active rows fill
+  // only A < 8 warps (A warps per segment, q = 8 / A segments), provided the
+  // packed launch still has two CTAs per SM (small transforms need the SMs more
+  // than full CTAs)
+  for (int pack = 1; pack >= 0; --pack) {
+    h.cta_rb.clear();
+    h.cta_j.clear();
+    h.maxcut.clear();
+    h.toff.clear();
+    build_ctas(R, H, S, j0, pack, h);
+    if (!pack || (int64_t)h.cta_rb.size() >= 2 * (int64_t)sms) break;
   }
-  R.tbuf_total = to;
   R.ncta = (int64_t)h.cta_rb.size();
   // the transposed reduction relies on row blocks in order of non-increasing cut
   // (true by construction: full rows first, then bands of decreasing cut)
   std::vector<int32_t> mc = h.maxcut;
   std::sort(mc.begin(), mc.end(), std::greater<int32_t>());
   R.n_heavy = mc.size() > 32 ? mc[32] : 0;
+}
+
+void build_ctas(RecLayout& R, int64_t H, int S, int j0, int pack, LayoutHost& h) {
+  int64_t to = 0;
+  std::vector<int> lastr;  // per segment: last row of the block that runs it
+  for (int64_t rb = 0; rb < R.nblocks; ++rb) {
+    const int64_t r0 = rb * 256, r1 = std::min<int64_t>(H, rb * 256 + 256);
+    int32_t mc = 0;
+    for (int64_t k = r0; k < r1; ++k) mc = std::max(mc, h.cut[(size_t)k]);
+    const int64_t nsm = (mc + S - 1) / S;
+    h.maxcut.push_back(mc);
+    h.toff.push_back(to);
+    to += std::max<int64_t>(0, nsm - j0) * S;
+    lastr.assign((size_t)std::max<int64_t>(nsm, 1), -1);
+    for (int64_t k = r0; k < r1; ++k) {
+      const int64_t ns = (h.cut[(size_t)k] + S - 1) / S;
+      if (ns > 0) lastr[(size_t)ns - 1] = std::max(lastr[(size_t)ns - 1], (int)(k - r0));
+    }
+    for (int64_t j = nsm - 2; j >= 0; --j) lastr[(size_t)j] = std::max(lastr[(size_t)j], lastr[(size_t)j + 1]);
+    for (int64_t j = j0; j < nsm;) {
+      const int A = lastr[(size_t)j] / 32 + 1;
+      const int q = pack ? (int)std::min<int64_t>(8 / A, nsm - j) : 1;
+      h.cta_rb.push_back((int32_t)rb);
+      h.cta_j.push_back((int32_t)(j | ((A - 1) << 16) | ((q - 1) << 20)));
+      j += q;
+    }
+  }
+  R.tbuf_total = to;
 }
 
 struct LayoutOff {
@@ -566,6 +594,11 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   cudaGetDevice(&P->device);
   const size_t ts = prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * ts;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 1;
+  }
   // recurrence layouts (host): the fast path's region on the cheb1 rows, and the
   // direct method's full rows at the Legendre nodes
   LayoutHost hf, hd;
@@ -574,12 +607,12 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1), (int32_t)N);
     for (const Band& b : prm.bands)
       for (int64_t k = b.ka; k < b.kb; ++k) cut[(size_t)k] = (int32_t)b.ns;
-    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), hf);
+    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), sms, hf);
   }
   P->has_direct = N > 1 && N <= kDirectMax && (prm.method == GBDLT_METHOD_DIRECT || want_direct);
   if (P->has_direct) {
     const int64_t H = (N + 1) / 2;
-    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, hd);
+    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, sms, hd);
   }
   RecLayout& R = P->rec;
   RecLayout& D = P->drec;

@@ -156,6 +156,33 @@ __global__ void k_rec_xm1(double* __restrict__ xm1, const double* __restrict__ t
 __device__ __forceinline__ int nseg_of(const RecArgs& R, int64_t k) {
   return (R.cut[k] + R.S - 1) / R.S;
 }
+// A CTA's work: row block rb and q consecutive segments j, j+1, ..., j+q-1, each
+// run by A warps (A = the warps that hold the rows of the block still active at
+// segment j; rows are ordered by non-increasing cut, so later segments need no
+// more).  Warp w takes segment j + w / A and the rows (w mod A) * 32 + lane of
+// the block; A * q <= 8.  Blocks whose long rows fill only a few warps (the rows
+// nearest theta = 0) so pack several segments into one full CTA.
+// cta_j packs j (bits 0-15), A - 1 (bits 16-19) and q - 1 (bits 20-23).
+struct RecTask {
+  int64_t rb, k;  // row block, half row of this thread
+  int j;          // segment of this warp
+  int jj, A, q;   // segment slot within the CTA, warps per segment, segments
+  bool in;        // this warp has a segment
+};
+__device__ __forceinline__ RecTask rec_task(const RecArgs& R) {
+  const int code = R.cta_j[blockIdx.x];
+  RecTask t;
+  t.A = ((code >> 16) & 15) + 1;
+  t.q = ((code >> 20) & 15) + 1;
+  const int w = threadIdx.x >> 5;
+  t.jj = w / t.A;
+  t.j = (code & 0xffff) + t.jj;
+  t.in = t.jj < t.q;
+  t.rb = R.cta_rb[blockIdx.x];
+  t.k = t.rb * RT + (w - t.jj * t.A) * 32 + (threadIdx.x & 31);
+  return t;
+}
+
 // segments a row stores and runs: j0 .. nseg-1
 __device__ __forceinline__ int nstored_of(const RecArgs& R, int64_t k) {
   return max(0, nseg_of(R, k) - R.j0);
@@ -178,10 +205,10 @@ __global__ void k_rec_lead(RecArgs R, double2* __restrict__ state) {
 
 // transfer matrix of one full segment: images of the basis states (1,0), (0,1)
 __global__ void k_rec_basis(RecArgs R, double2* __restrict__ Tbuf) {
-  const int64_t rbk = R.cta_rb[blockIdx.x];
-  const int j = R.cta_j[blockIdx.x];
-  const int64_t k = rbk * RT + threadIdx.x;
-  if (k >= R.H) return;
+  const RecTask t = rec_task(R);
+  const int64_t k = t.k;
+  const int j = t.j;
+  if (!t.in || k >= R.H) return;
   if (j >= nseg_of(R, k) - 1) return;
   const double xm1 = R.xm1[k];
   double P1 = 1.0, D1 = 0.0, P2 = 0.0, D2 = 1.0;
@@ -228,10 +255,10 @@ __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__
                                                 double2* __restrict__ part) {
   c += (int64_t)blockIdx.y * R.N;
   part += (int64_t)blockIdx.y * R.nseg_total;
-  const int64_t rbk = R.cta_rb[blockIdx.x];
-  const int j = R.cta_j[blockIdx.x];
-  const int64_t k = rbk * RT + threadIdx.x;
-  if (k >= R.H) return;
+  const RecTask t = rec_task(R);
+  const int64_t k = t.k;
+  const int j = t.j;
+  if (!t.in || k >= R.H) return;
   const int cut = R.cut[k];
   if (j >= (cut + R.S - 1) / R.S) return;
   const int64_t o = R.poff[k] + j - R.j0;
@@ -260,10 +287,10 @@ __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __res
                                                    double2* __restrict__ part) {
   c += (int64_t)blockIdx.y * R.N;
   part += (int64_t)blockIdx.y * R.nseg_total;
-  const int64_t rbk = R.cta_rb[blockIdx.x];
-  const int j = R.cta_j[blockIdx.x];
-  const int64_t k = rbk * RT + threadIdx.x;
-  if (k >= R.H) return;
+  const RecTask t = rec_task(R);
+  const int64_t k = t.k;
+  const int j = t.j;
+  if (!t.in || k >= R.H) return;
   const int cut = R.cut[k];
   if (j >= (cut + R.S - 1) / R.S) return;
   const int64_t o = R.poff[k] + j - R.j0;
@@ -349,11 +376,12 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
   double* tile = sm;                  // [8][32][TP]
   double* wsum = sm + 8 * 32 * TP;    // [8][S] per-warp column partials
   double2* zt = reinterpret_cast<double2*>(wsum + 8 * R.S);  // [8][32] (z+, z-)
-  const int64_t rbk = R.cta_rb[blockIdx.x];
-  const int j = R.cta_j[blockIdx.x];
+  const RecTask t = rec_task(R);
+  const int64_t rbk = t.rb;
+  const int j = t.j;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k = rbk * RT + threadIdx.x;
-  bool active = k < R.H;
+  const int64_t k = t.k;
+  bool active = t.in && k < R.H;
   int cut = 0;
   double zp = 0.0, zm = 0.0, P = 0.0, G = 0.0, xm1 = 0.0;
   if (active) {
@@ -408,11 +436,15 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
     __syncwarp();
   }
   __syncthreads();
-  for (int64_t c = threadIdx.x; c < seg_end - n0s; c += RT) {
+  // per segment of the CTA, the sum of its A warps' column partials
+  const int jf = t.j - t.jj;
+  for (int idx = threadIdx.x; idx < t.q * R.S; idx += RT) {
+    const int sl = idx / R.S, c = idx - sl * R.S;
+    const int64_t n0c = (int64_t)(jf + sl) * R.S;
+    if (n0c + c >= (int64_t)R.maxcut[rbk]) continue;
     double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s += wsum[q * R.S + c];
-    tbuf[R.toff[rbk] + (n0s - R.n_lo) + c] = s;
+    for (int a = 0; a < t.A; ++a) s += wsum[(sl * t.A + a) * R.S + c];
+    tbuf[R.toff[rbk] + (n0c - R.n_lo) + c] = s;
   }
 }
 
@@ -425,11 +457,12 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
   extern __shared__ float smf[];
   float* tile = smf;                 // [8][32][TP]
   float* wsum = smf + 8 * 32 * TP;   // [8][S]
-  const int64_t rbk = R.cta_rb[blockIdx.x];
-  const int j = R.cta_j[blockIdx.x];
+  const RecTask t = rec_task(R);
+  const int64_t rbk = t.rb;
+  const int j = t.j;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k = rbk * RT + threadIdx.x;
-  bool active = k < R.H;
+  const int64_t k = t.k;
+  bool active = t.in && k < R.H;
   int cut = 0;
   float zp = 0.f, zm = 0.f;
   ffv P = {0.f, 0.f}, D = {0.f, 0.f}, xm1 = {0.f, 0.f};
@@ -481,11 +514,14 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
     __syncwarp();
   }
   __syncthreads();
-  for (int64_t c = threadIdx.x; c < seg_end - n0s; c += RT) {
+  const int jf = t.j - t.jj;
+  for (int idx = threadIdx.x; idx < t.q * R.S; idx += RT) {
+    const int sl = idx / R.S, c = idx - sl * R.S;
+    const int64_t n0c = (int64_t)(jf + sl) * R.S;
+    if (n0c + c >= (int64_t)R.maxcut[rbk]) continue;
     double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s += (double)wsum[q * R.S + c];
-    tbuf[R.toff[rbk] + (n0s - R.n_lo) + c] = s;
+    for (int a = 0; a < t.A; ++a) s += (double)wsum[(sl * t.A + a) * R.S + c];
+    tbuf[R.toff[rbk] + (n0c - R.n_lo) + c] = s;
   }
 }
 
