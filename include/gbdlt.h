@@ -94,6 +94,10 @@ typedef struct {
                           M[0:head, 0:head] (Sec. 3); 0 = none                 */
   int M_fp32;          /* FP64 plans: the last M_fp32 expansion terms have their
                           band FFTs in FP32 (their size bounds the error)       */
+  int M_ff;            /* FP64 plans: the M_ff terms before those run their band
+                          FFTs in float-float arithmetic (FP32 pipe)            */
+  int L_ff;            /* FP64 plans: the last L_ff Taylor terms run their FFTs
+                          and combines in float-float                           */
 } gbdlt_params;
 
 /* Host-only parameter derivation: no GPU, no allocation.  eps <= 0 selects the

@@ -62,6 +62,8 @@ class Params(ctypes.Structure):
         ("direct_steps", ctypes.c_int64),
         ("head", ctypes.c_int64),
         ("M_fp32", ctypes.c_int),
+        ("M_ff", ctypes.c_int),
+        ("L_ff", ctypes.c_int),
     ]
 
     def to_dict(self) -> dict:
@@ -73,7 +75,8 @@ class Params(ctypes.Structure):
             "bytes_dlt": self.bytes_dlt, "bytes_idlt": self.bytes_idlt,
             "workspace_bytes": self.workspace_bytes, "method": self.method,
             "direct_steps": self.direct_steps, "head": self.head,
-            "M_fp32": self.M_fp32,
+            "M_fp32": self.M_fp32, "M_ff": self.M_ff,
+            "L_ff": self.L_ff,
         }
 
 

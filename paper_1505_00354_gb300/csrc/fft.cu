@@ -64,7 +64,22 @@ __device__ __forceinline__ C2<T> tw_lookup(const C2<T>* __restrict__ hi, const C
 template <typename T, int DIR>
 __device__ __forceinline__ C2<T> rot(C2<T> v, T c, T s) {
   const T sd = DIR > 0 ? s : -s;
-  return mk<T>(v.x * c - v.y * sd, v.x * sd + v.y * c);
+  return cmul<T>(v, mk<T>(c, sd));
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor_t(T v, int m) {
+  if constexpr (std::is_same<T, ffd>::value) {
+    return ffd(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+  } else {
+    return __shfl_xor_sync(0xffffffffu, v, m);
+  }
+}
+
+// kernel names for the profiler: FP64, FP32 and float-float launches apart
+template <typename T>
+constexpr const char* kname(const char* d, const char* f, const char* ff) {
+  return is_f64<T> ? d : is_f32<T> ? f : ff;
 }
 
 // ---------------------------------------------------------------- cosine/tangent twiddles (FP64)
@@ -289,7 +304,7 @@ __device__ __forceinline__ void stage(C2<T>* sm, int L, int logL, int lines, int
         CT w[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          if (sizeof(T) == 8 || (r & (r - 1)) == 0) {
+          if (!is_f32<T> || (r & (r - 1)) == 0) {
             w[r] = tw[r * k * step];
           } else {
             w[r] = cmul<T>(w[r & (r - 1)], w[r & -r]);
@@ -321,7 +336,7 @@ __device__ __forceinline__ void stage(C2<T>* sm, int L, int logL, int lines, int
 // the plain loop (its registers hold the radix-16 butterflies).
 template <typename T, typename Idx, typename Ld>
 __device__ __forceinline__ void load_tile(C2<T>* sm, int tot, Idx sidx_of, Ld ld) {
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (is_f32<T>) {
     constexpr int PER = FFT_TILE / FFT_THREADS;
     C2<T> r[PER];
 #pragma unroll
@@ -356,7 +371,7 @@ __device__ void fft_tile(C2<T>* sm, int L, int logL, int lines, int LP, const C2
     stage<T, DIR, 8>(sm, L, logL, lines, LP, Ns, tw, lf);
     Ns = 8;
   }
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (is_f64<T>) {
     // FP64: the untwiddled first radix-16 stage, then the fused cosine/tangent stages
     if (Ns == 1 && Ns < L) {
       stage<T, DIR, 16>(sm, L, logL, lines, LP, 1, tw, lf);
@@ -385,7 +400,7 @@ __device__ __forceinline__ int64_t vec_of(const VecMap& m, int64_t j) {
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
     k_fft_single(C2<T>* __restrict__ data, int L, int logL, int64_t nvec, const C2<T>* __restrict__ tw4096,
                  const double2* __restrict__ lf) {
   extern __shared__ unsigned char smraw[];
@@ -403,7 +418,7 @@ __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
     k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int logL1, int L2, int C, int logC,
                const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
                const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf,
@@ -423,8 +438,8 @@ __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
     const int64_t e = (int64_t)(c0 + c) * k1;
     C2<T> val = sm[sidx(c, LP, k1)];
     if (e != 0) {
-      // FP64: one table entry per e; FP32: product of the two-level entries
-      const C2<T> w = sizeof(T) == 8 ? tfull[e] : tw_lookup<T>(thi, tlo, e);
+      // FP64 and float-float: one table entry per e; FP32: product of the two-level entries
+      const C2<T> w = !is_f32<T> ? tfull[e] : tw_lookup<T>(thi, tlo, e);
       val = cmul<T>(val, mk<T>(w.x, DIR > 0 ? w.y : -w.y));
     }
     g[(int64_t)k1 * L2 + c0 + c] = val;
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
     k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
                int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096,
                const double2* __restrict__ lf, VecMap vm) {
@@ -496,10 +511,10 @@ __global__ void __launch_bounds__(FFT_THREADS)
   }
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) {
-    ex += __shfl_xor_sync(0xffffffffu, ex, m);
-    ey += __shfl_xor_sync(0xffffffffu, ey, m);
-    ox += __shfl_xor_sync(0xffffffffu, ox, m);
-    oy += __shfl_xor_sync(0xffffffffu, oy, m);
+    ex += shfl_xor_t(ex, m);
+    ey += shfl_xor_t(ey, m);
+    ox += shfl_xor_t(ox, m);
+    oy += shfl_xor_t(oy, m);
   }
   if (lane == 0) {
     const int64_t ka = low ? 0 : L2 - 1, kb = low ? L2 / 2 : L2 / 2 - 1;
@@ -541,7 +556,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
       val = (k1 & 1) ? csub<T>(a, b) : cadd<T>(a, b);
       const int64_t e = lowc ? (int64_t)n2 * k1 : (N - (int64_t)k1 * (L2 - n2)) & (N - 1);
       if (e != 0) {
-        const C2<T> w = sizeof(T) == 8 ? tfull[e] : tw_lookup<T>(thi, tlo, e);
+        const C2<T> w = !is_f32<T> ? tfull[e] : tw_lookup<T>(thi, tlo, e);
         val = cmul<T>(val, mk<T>(w.x, DIR > 0 ? w.y : -w.y));
       }
     }
@@ -770,7 +785,7 @@ static void* fft_dir(Plan& P, void* a, void* b, int64_t nvec) {
     int64_t grid = (nvec + lines - 1) / lines;
     size_t sm = (size_t)lines * line_pitch(L) * sizeof(CT);
     k_fft_single<T, DIR><<<(unsigned)grid, FFT_THREADS, sm, P.stream>>>((CT*)a, L, lg, nvec, tw.t4096, lfd);
-    launched(P, sizeof(T) == 8 ? "fft_single" : "fft32_single", 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
+    launched(P, kname<T>("fft_single", "fft32_single", "fftff_single"), 5.0 * (double)N * lg * nvec, 2.0 * (double)nvec * N * sizeof(CT));
     return a;
   }
   return four_step<T, DIR>(P, a, b, nvec, 1, 0, 0, 0);
@@ -805,7 +820,7 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   // where the line length has one, else the generic ones
   auto cols = [&](VecMap vm, int64_t nv) {
     const dim3 grid(L2 / C, (unsigned)nv);
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (is_f32<T>) {
       if (launch_fft32_cols<DIR>(lL1, grid, P.stream, (C2<float>*)a, N, L2, (const C2<float>*)tw.t4096,
                                  (const C2<float>*)tw.nhi, (const C2<float>*)tw.nlo, vm))
         return;
@@ -815,7 +830,7 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   };
   auto rows = [&](VecMap vm, int64_t nv) {
     const dim3 grid(L1 / C2n, (unsigned)nv);
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (is_f32<T>) {
       if (launch_fft32_rows<DIR>(lL2, grid, P.stream, (const C2<float>*)a, (C2<float>*)b, N, L1,
                                  (const C2<float>*)tw.t4096, vm))
         return;
@@ -827,30 +842,30 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   if (mode == 2 && npruned > 0) {
     k_fft_cols_pruned<T, DIR><<<dim3(L2 / C, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
         (CT*)a, N, L1, L2, R, C, lC, tw.nhi, tw.nlo, tw.full, pruned);
-    launched(P, sizeof(T) == 8 ? "fft_cols_pruned" : "fft32_cols_pruned", 6.0 * (double)N * nb * npruned * (4.0 * R / L2),
+    launched(P, kname<T>("fft_cols_pruned", "fft32_cols_pruned", "fftff_cols_pruned"), 6.0 * (double)N * nb * npruned * (4.0 * R / L2),
              (double)nb * npruned * N * sizeof(CT));
     if (nfull > 0) {
       cols(rest, nb * nfull);
-      launched(P, sizeof(T) == 8 ? "fft_cols" : "fft32_cols", (5.0 * lL1 + 6.0) * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
+      launched(P, kname<T>("fft_cols", "fft32_cols", "fftff_cols"), (5.0 * lL1 + 6.0) * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
     }
   } else {
     cols(all, nb * per_item);
-    launched(P, sizeof(T) == 8 ? "fft_cols" : "fft32_cols", (5.0 * lL1 + 6.0) * (double)N * nb * per_item,
+    launched(P, kname<T>("fft_cols", "fft32_cols", "fftff_cols"), (5.0 * lL1 + 6.0) * (double)N * nb * per_item,
              2.0 * (double)nb * per_item * N * sizeof(CT));
   }
   // row pass
   if (mode == 1 && npruned > 0) {
     k_fft_rows_pruned<T, DIR><<<dim3((2 * R + 7) / 8, (unsigned)(nb * npruned)), FFT_THREADS, 0, P.stream>>>(
         (const CT*)a, (CT*)b, N, L1, L2, R, tw.t4096, pruned);
-    launched(P, sizeof(T) == 8 ? "fft_rows_pruned" : "fft32_rows_pruned", 6.0 * 2.0 * R * L2 * (double)nb * npruned,
+    launched(P, kname<T>("fft_rows_pruned", "fft32_rows_pruned", "fftff_rows_pruned"), 6.0 * 2.0 * R * L2 * (double)nb * npruned,
              (double)nb * npruned * 2.0 * R * L2 * sizeof(CT));
     if (nfull > 0) {
       rows(rest, nb * nfull);
-      launched(P, sizeof(T) == 8 ? "fft_rows" : "fft32_rows", 5.0 * lL2 * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
+      launched(P, kname<T>("fft_rows", "fft32_rows", "fftff_rows"), 5.0 * lL2 * (double)N * nb * nfull, 2.0 * (double)nb * nfull * N * sizeof(CT));
     }
   } else {
     rows(all, nb * per_item);
-    launched(P, sizeof(T) == 8 ? "fft_rows" : "fft32_rows", 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
+    launched(P, kname<T>("fft_rows", "fft32_rows", "fftff_rows"), 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
   }
   return b;
 }
@@ -873,6 +888,7 @@ void* launch_fft_bands(Plan& P, void* a, void* b, int64_t nb, int dir, int trans
 template void* launch_fft<double>(Plan&, void*, void*, int64_t, int);
 template void* launch_fft_bands<double>(Plan&, void*, void*, int64_t, int, int, int);
 template void* launch_fft_bands<float>(Plan&, void*, void*, int64_t, int, int, int);
+template void* launch_fft_bands<ffd>(Plan&, void*, void*, int64_t, int, int, int);
 
 namespace {
 // cosine/tangent table for both directions: entry e of direction d holds the
@@ -901,13 +917,36 @@ __global__ void k_lf_init(double2* __restrict__ tab) {
 }
 }  // namespace
 
+namespace {
+// float-float copies of FP64 twiddles: hi = fl(v), lo = fl(v - hi)
+__global__ void k_tw_to_ff(const double2* __restrict__ in, ffc* __restrict__ out, int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double2 v = in[i];
+  const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+  ffc w;
+  w.x = ffd(xh, __double2float_rn(v.x - (double)xh));
+  w.y = ffd(yh, __double2float_rn(v.y - (double)yh));
+  out[i] = w;
+}
+}  // namespace
+
 int launch_fft_tables_init(Plan& P) {
   if (P.lf_tab) {
     k_lf_init<<<32, 256, 0, P.stream>>>(P.lf_tab);
     count_launch();
   }
+  if (P.tw4096_ff) {
+    k_tw_to_ff<<<16, 256, 0, P.stream>>>(P.tw4096, P.tw4096_ff, 4096);
+    count_launch();
+  }
+  if (P.twfull_ff && P.twfull) {
+    k_tw_to_ff<<<(unsigned)((P.p.N + 255) / 256), 256, 0, P.stream>>>(P.twfull, P.twfull_ff, P.p.N);
+    count_launch();
+  }
   return check_launch();
 }
 template void* launch_fft<float>(Plan&, void*, void*, int64_t, int);
+template void* launch_fft<ffd>(Plan&, void*, void*, int64_t, int);
 
 }  // namespace gbdlt

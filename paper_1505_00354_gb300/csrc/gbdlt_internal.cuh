@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "gbdlt.h"
@@ -15,6 +16,66 @@ namespace gbdlt {
 // ---------------------------------------------------------------------------
 // complex helpers (float2 / double2)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// float-float scalar: value hi + lo (|lo| <= ulp(hi)/2 after normalisation), the
+// arithmetic of the FFTs of mid-sized terms in FP64 plans, run on the FP32 pipe
+// (64 times the FP64 rate on GB300) with about 2^-47 relative error per
+// operation and the exponent range of float.  Operations are explicitly rounded
+// so nothing is contracted.  Additions use the cheap form (TwoSum of the heads,
+// tails added), whose error is about 2^-47 (|a| + |b|): the transforms need
+// norm-wise accuracy, not accuracy relative to each cancelling sum.
+struct ffd {
+  float hi, lo;
+  ffd() = default;
+  __host__ __device__ constexpr ffd(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr ffd(int v) : hi((float)v), lo(0.f) {}
+  // compile-time constants only (two roundings of a double literal)
+  __host__ __device__ constexpr ffd(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+__device__ __forceinline__ ffd ff_norm(float s, float e) {
+  const float t = __fadd_rn(s, e);
+  return ffd(t, __fsub_rn(e, __fsub_rn(t, s)));
+}
+__device__ __forceinline__ ffd operator+(ffd a, ffd b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ffd operator-(ffd a) { return ffd(-a.hi, -a.lo); }
+__device__ __forceinline__ ffd operator-(ffd a, ffd b) { return a + (-b); }
+__device__ __forceinline__ ffd operator*(ffd a, ffd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ ffd& operator+=(ffd& a, ffd b) {
+  a = a + b;
+  return a;
+}
+// a.x b.x - a.y b.y (sign = -1) or a.x b.y + a.y b.x style dot of two products,
+// one normalisation: p1 + sign p2 with both product errors carried in the tail
+__device__ __forceinline__ ffd ff_dot2(ffd a1, ffd b1, ffd a2, ffd b2, float sign) {
+  const float p1 = __fmul_rn(a1.hi, b1.hi);
+  float e1 = __fmaf_rn(a1.hi, b1.hi, -p1);
+  e1 = __fmaf_rn(a1.hi, b1.lo, e1);
+  e1 = __fmaf_rn(a1.lo, b1.hi, e1);
+  const float h2 = sign * a2.hi, l2 = sign * a2.lo;  // exact
+  const float p2 = __fmul_rn(h2, b2.hi);
+  float e2 = __fmaf_rn(h2, b2.hi, -p2);
+  e2 = __fmaf_rn(h2, b2.lo, e2);
+  e2 = __fmaf_rn(l2, b2.hi, e2);
+  const float s = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(s, p1);
+  const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  return ff_norm(s, __fadd_rn(es, __fadd_rn(e1, e2)));
+}
+struct alignas(16) ffc {
+  ffd x, y;
+};
+
 template <typename T>
 struct Cx;
 template <>
@@ -25,6 +86,18 @@ template <>
 struct Cx<float> {
   using type = float2;
 };
+template <>
+struct Cx<ffd> {
+  using type = ffc;
+};
+template <typename T>
+constexpr bool is_f64 = false;
+template <>
+constexpr bool is_f64<double> = true;
+template <typename T>
+constexpr bool is_f32 = false;
+template <>
+constexpr bool is_f32<float> = true;
 template <typename T>
 using C2 = typename Cx<T>::type;
 
@@ -45,7 +118,11 @@ __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) {
 }
 template <typename T>
 __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  if constexpr (std::is_same<T, ffd>::value) {
+    return mk<T>(ff_dot2(a.x, b.x, a.y, b.y, -1.f), ff_dot2(a.x, b.y, a.y, b.x, 1.f));
+  } else {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  }
 }
 template <typename T>
 __device__ __forceinline__ C2<T> cconj(C2<T> a) {
@@ -145,6 +222,8 @@ struct Params {
   int64_t head = 0;                // columns n < head come from the dense block M[0:head, 0:head]
   int Mh = 0;                      // expansion terms whose band FFTs run in the plan's precision;
                                    // terms Mh..M-1 of an FP64 plan run in FP32
+  int M64 = 0;                     // of those, terms M64..Mh-1 of an FP64 plan run in float-float
+  int Lff = 0;                     // Taylor terms l >= Lff of an FP64 plan run in float-float
 };
 
 // Direct method limits: largest N a direct plan accepts, and the largest
@@ -210,6 +289,10 @@ struct Plan {
   // used by the fused radix-4 layers ([2 directions][4096][sx, sy, t, swap])
   double2* twfull = nullptr;
   double2* lf_tab = nullptr;
+  // the same e^{2 pi i j/4096} and e^{2 pi i e/N} as float-float pairs, for the
+  // float-float FFTs of FP64 plans
+  ffc* tw4096_ff = nullptr;
+  ffc* twfull_ff = nullptr;
   // FP64 stage tables: C_n h_{m,n} ([Mh][N], the asymptotic expansion's column
   // weights of the FP64 terms) and per cheb1 row {alpha_k, rho_k} (the expansion's
   // row factors)
@@ -229,11 +312,15 @@ struct Plan {
   // the FP32 band vectors of an FP64 plan ([item][band][term Mh..M-1][N] float2)
   void* bufA32 = nullptr;
   void* bufB32 = nullptr;
+  // the float-float band vectors of an FP64 plan ([item][band][term M64..Mh-1][N] ffc)
+  void* bufAff = nullptr;
+  void* bufBff = nullptr;
   // their power-of-two scales: per (band, term) exponents [2][K][M] (forward,
   // transposed) and per batch item the bits of max |chain input|
   int* b32exp = nullptr;
   unsigned long long* absmax = nullptr;
   float* H32 = nullptr;  // [M - Mh][N] C_n h_{m,n} 2^{e_{K-1,m}} of the FP32 terms (stages.cu)
+  ffd* Hff = nullptr;    // [Mh - M64][N] the same for the float-float terms
   int prune_bands = 0;   // leading bands whose FFTs are pruned to their row windows
   int prune_R = 0;       // window half-width of those bands (bins)
   int64_t bcap = 1;      // batch items one pass over the workspace holds
@@ -249,6 +336,14 @@ struct Plan {
   struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
   struct GraphCache* graphs = nullptr;  // replayed transform chains (plan.cu)
 };
+
+// Taylor pairs whose FFTs run in the plan's precision: pair p holds terms
+// 2p + (inc0 ? 0 : 2) and 2p + 1; it runs in float-float when both are >= Lff
+inline int taylor_p64(const Params& p, int inc0, int npair) {
+  const int lo = p.Lff;
+  const int q = inc0 ? (lo + 1) / 2 : lo / 2;  // first pair whose smaller term is >= Lff
+  return q < npair ? q : npair;
+}
 
 // twiddle tables in the precision T of a transform
 template <typename T>
@@ -266,6 +361,9 @@ inline TwT<double> tw_tables(const Plan& P, double) {
 }
 inline TwT<float> tw_tables(const Plan& P, float) {
   return {P.tw4096f, P.twNf_lo, P.twNf_hi, P.tw4Nf_lo, P.tw4Nf_hi, nullptr, nullptr};
+}
+inline TwT<ffd> tw_tables(const Plan& P, ffd) {
+  return {P.tw4096_ff, nullptr, nullptr, nullptr, nullptr, P.twfull_ff, nullptr};
 }
 
 // plan lifecycle and the operator dispatch shared by the C ABI and the batch
@@ -320,34 +418,39 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb,
 // x_k - 1 of the cheb1 rows (fast path) or of the Legendre nodes (direct method)
 int launch_rec_xm1(Plan& P, RecLayout& L, int legendre);
 // stages.cu (prologues / epilogues)
-// band vectors of terms m < Mh in U / Y / F (precision T), of terms m >= Mh in
-// U32 / Y32 / F32 (FP32; FP64 plans only)
+// band vectors of terms m < M64 in U / Y / F (precision T), of terms
+// M64 <= m < Mh in Uff / Yff / Fff (float-float) and of terms m >= Mh in U32 /
+// Y32 / F32 (FP32); the last two exist in FP64 plans only
 template <typename T>
-int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, float2* U32, int64_t nb);
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, ffc* Uff, float2* U32, int64_t nb);
 // max |x| per batch item into P.absmax (FP64 plans with FP32 band vectors)
 template <typename T>
 int launch_absmax(Plan& P, const T* x, int64_t nb);
 template <typename T>
-int launch_l2c_epi(Plan& P, const C2<T>* Y, const float2* Y32, const T* vrec, T* v, int64_t nb);
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const float2* Y32, const T* vrec, T* v, int64_t nb);
 template <typename T>
 int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb);
 template <typename T>
 int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb);
 template <typename T>
 int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d, int64_t nb);
+// Taylor pairs: p < taylor_p64 in U / Y / F (precision T, [item][P64][N]); with
+// Uff / Yff / Fff given (FP64 plans), pairs p >= P64 there in float-float
 template <typename T>
-int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair, int64_t nb);
+int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair, int64_t nb);
+int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair, int64_t nb);
+int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb);
 template <typename T>
-int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb,
+int launch_tayt_epi(Plan& P, const C2<T>* F, const ffc* Fff, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb,
                     int64_t nu = -1);
 template <typename T>
-int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, float2* U32, int64_t nb);
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, ffc* Uff, float2* U32,
+                    int64_t nb);
 template <typename T>
-int launch_l2ct_epi(Plan& P, const C2<T>* F, const float2* F32, const T* rect, T* out, int scale_s, int64_t nb);
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const ffc* Fff, const float2* F32, const T* rect, T* out, int scale_s,
+                    int64_t nb);
 template <typename T>
 int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb);
 template <typename T>

@@ -171,11 +171,14 @@ static int64_t first_row(int64_t N, int M, double eps_asy, int64_t ns) {
 // with m terms), and an FFT in FP32 of its vector errs by at most about
 // 2 log2(N) u_32 T_m; the terms run in FP32 are the tail m >= Mh whose errors
 // sum to at most eps/20.
-static int fp64_terms(int64_t N, int M, double eps, int64_t ns, int64_t ka) {
+// unit: the relative error per operation of the cheaper arithmetic (2^-24 for
+// FP32; 2^-46 for float-float, two bits above its significand for the cheap
+// additions).
+static int fp64_terms(int64_t N, int M, double eps, int64_t ns, int64_t ka, double unit = 0x1p-24) {
   int lg = 0;
   while ((1ll << lg) < N) ++lg;
   const double s2 = 2.0 * std::sin(((double)ka + 0.5) * M_PI / (double)N);
-  const double ferr = 2.0 * std::max(lg, 1) * std::ldexp(1.0, -24);
+  const double ferr = 2.0 * std::max(lg, 1) * unit;
   double err = 0.0;
   int Mh = M;
   while (Mh > 1) {
@@ -285,6 +288,24 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     b *= 0.83845 / L;
   }
   q.L = L;
+  // Taylor terms l >= Lff run their FFTs and combines in float-float in FP64
+  // plans: term l is at most 0.83845^l / l! ||c||_1 (Corollary 2.4) and a
+  // float-float FFT of it errs by about 2 log2(N) 2^-46 of that; the tail
+  // l >= Lff keeps the sum of those errors within eps/20
+  q.Lff = L;
+  if (prec == GBDLT_FP64) {
+    int lgN = 0;
+    while ((1ll << lgN) < N) ++lgN;
+    const double ferr = 2.0 * std::max(lgN, 1) * 0x1p-46;
+    double err = 0.0;
+    for (int l = L - 1; l >= 1; --l) {
+      double tl = 1.0;
+      for (int i = 1; i <= l; ++i) tl *= 0.83845 / i;
+      if (err + ferr * tl > eps / 20.0) break;
+      err += ferr * tl;
+      q.Lff = l;
+    }
+  }
   q.seg = 512;
   q.M = 0;
   q.K = 0;
@@ -298,8 +319,10 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     // c_head: one term M_kn c_n of the dense head block (two FP64 instructions
     // in the FP64 form; FP32 arithmetic with a compensated sum in the FP32 form)
     // c_fft32: an FP32 FFT vector (the FP32 form's, and the FP32 tail terms of
-    // an FP64 plan's bands)
-    const double c_fft32 = (0.43 * lg + 1.7) * (double)N;  // memory and shared-memory bound FP32 passes
+    // an FP64 plan's bands); c_fftff: a float-float FFT vector (the mid terms)
+    // (each with its term's share of the prologue/epilogue kernels)
+    const double c_fft32 = (0.8 * lg + 10.0) * (double)N;  // memory and shared-memory bound FP32 passes
+    const double c_fftff = (2.0 * lg + 13.0) * (double)N;  // FP32-pipe bound
     double c_fft, c_rec, c_head;
     int Mmax;
     if (prec == GBDLT_FP64) {
@@ -308,7 +331,7 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
       c_head = 4.0;
       Mmax = 24;
     } else {
-      c_fft = c_fft32;
+      c_fft = (0.43 * lg + 1.7) * (double)N;  // the FP32 form's passes and combines
       c_rec = 3.4;                             // float-float recurrence
       c_head = 0.25;
       Mmax = 16;
@@ -329,12 +352,14 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
         // FP64 plans: the FP64 share of a band's terms, estimated on a band
         // with cut max(h, sqrt N) at its first row (the split is nearly the same
         // for every band: each starts where its own bound meets eps/20)
-        int Mh = M;
+        int Mh = M, M64 = M;
         if (prec == GBDLT_FP64) {
           const int64_t ns_rep = std::max<int64_t>(h, 1ll << (lg / 2));
-          Mh = fp64_terms(N, M, eps, ns_rep, first_row(N, M, eps_asy, ns_rep));
+          const int64_t ka_rep = first_row(N, M, eps_asy, ns_rep);
+          Mh = fp64_terms(N, M, eps, ns_rep, ka_rep);
+          M64 = fp64_terms(N, Mh, eps, ns_rep, ka_rep, 0x1p-46);
         }
-        const double tcost = (double)Mh * c_fft + (double)(M - Mh) * c_fft32;
+        const double tcost = (double)M64 * c_fft + (double)(Mh - M64) * c_fftff + (double)(M - Mh) * c_fft32;
         // pruned bands save FP64 work; the FP32 passes are bound by memory
         // latency, where the saving is small
         DPResult r = plan_bands(N, M, eps_asy, tcost, c_rec, prune_kb, prec == GBDLT_FP64 ? 0.6 : 1.0, h);
@@ -351,9 +376,12 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     if (q.K == 0) q.M = 0;
     // the split of the chosen bands: every band's FP32 tail within its budget
     q.Mh = q.M;
+    q.M64 = q.M;
     if (prec == GBDLT_FP64 && q.K > 0) {
       q.Mh = 1;
       for (const Band& bd : q.bands) q.Mh = std::max(q.Mh, fp64_terms(N, q.M, eps, bd.ns, bd.ka));
+      q.M64 = 1;
+      for (const Band& bd : q.bands) q.M64 = std::max(q.M64, fp64_terms(N, q.Mh, eps, bd.ns, bd.ka, 0x1p-46));
     }
   }
   // recurrence work of the fast path (cheb1 rows), and of the direct method
@@ -617,9 +645,19 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   RecLayout& R = P->rec;
   RecLayout& D = P->drec;
   const int npair = (prm.L + 1) / 2;
-  P->nfft_max = prm.fast ? std::max<int64_t>({(int64_t)prm.K * prm.Mh, (int64_t)npair, 1}) : 0;
-  // FP32 band vectors of an FP64 plan (terms Mh..M-1)
+  // Taylor pairs in the plan's precision and in float-float, for either choice of
+  // the l = 0 term (pairs of l = 0..L-1 or of l = 1..L-1)
+  const int np1 = (prm.L + 1) / 2, np0 = prm.L / 2;
+  const int p64max = std::max(taylor_p64(prm, 1, np1), taylor_p64(prm, 0, np0));
+  const int pffmax = prec == GBDLT_FP64 ? std::max(np1 - taylor_p64(prm, 1, np1), np0 - taylor_p64(prm, 0, np0)) : 0;
+  P->nfft_max = prm.fast ? std::max<int64_t>({(int64_t)prm.K * prm.M64, (int64_t)p64max, 1}) : 0;
+  // FP32 band vectors of an FP64 plan (terms Mh..M-1); float-float vectors (band
+  // terms M64..Mh-1, or the float-float Taylor pairs)
   const int64_t nfft32 = prm.fast && prec == GBDLT_FP64 ? (int64_t)prm.K * (prm.M - prm.Mh) : 0;
+  const int64_t nfftff = prm.fast && prec == GBDLT_FP64
+                             ? std::max<int64_t>((int64_t)prm.K * (prm.Mh - prm.M64), (int64_t)pffmax)
+                             : 0;
+  const bool scaled = nfft32 > 0 || nfftff > 0;
   // bands whose rows are few enough that their FFTs only touch two windows of
   // bins (four-step sizes only; see fft.cu, pruned passes)
   if (prm.fast && N > 4096) {
@@ -635,7 +673,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   }
   {
     // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
-    const double per_item = 2.0 * P->nfft_max * N * cs + 2.0 * nfft32 * N * 8.0 + 5.0 * N * ts +
+    const double per_item = 2.0 * P->nfft_max * N * cs + 2.0 * nfft32 * N * 8.0 + 2.0 * nfftff * N * 16.0 +
+                            5.0 * N * ts +
                             16.0 * (R.nseg_total + D.nseg_total) +
                             8.0 * (R.tbuf_total + D.tbuf_total);
     P->bcap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(512.0 * (1 << 20) / per_item)));
@@ -660,7 +699,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   size_t o_twfull = A.take<double2>(fp64_tabs && N > 4096 ? N : 1);
   size_t o_lf = A.take<double2>(4 * 4096);
   const bool stage_tabs = fp64_tabs && prm.K > 0 && prm.M > 0;
-  size_t o_hnm = A.take<double>(stage_tabs ? (int64_t)prm.Mh * N : 1);
+  size_t o_hnm = A.take<double>(stage_tabs ? (int64_t)prm.M64 * N : 1);
   size_t o_ar = A.take<RowAR>(stage_tabs ? N : 1);
   const int64_t nhead = prm.fast ? prm.head : 0;
   size_t o_lam = A.take<double>(std::max<int64_t>(nhead, 1)), o_lamf = A.take<float>(std::max<int64_t>(nhead, 1));
@@ -688,8 +727,13 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   size_t o_bufA = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
   size_t o_bufB = bytes_block((size_t)BC * P->nfft_max * (size_t)N * cs);
   size_t o_bufA32 = bytes_block((size_t)BC * nfft32 * (size_t)N * sizeof(float2));
+  size_t o_bufAff = bytes_block((size_t)BC * nfftff * (size_t)N * sizeof(ffc));
+  size_t o_bufBff = bytes_block((size_t)BC * nfftff * (size_t)N * sizeof(ffc));
+  size_t o_tw4096ff = bytes_block(nfftff > 0 ? 4096 * sizeof(ffc) : 0);
+  size_t o_twfullff = bytes_block(nfftff > 0 && N > 4096 ? (size_t)N * sizeof(ffc) : 0);
   size_t o_b32exp = A.take<int>(std::max<int64_t>(1, 2 * (int64_t)prm.K * prm.M));
   size_t o_h32 = A.take<float>(std::max<int64_t>(1, nfft32 > 0 ? (int64_t)(prm.M - prm.Mh) * N : 1));
+  size_t o_hff = A.take<ffd>(std::max<int64_t>(1, nfftff > 0 ? (int64_t)(prm.Mh - prm.M64) * N : 1));
   size_t o_absmax = A.take<unsigned long long>(BC);
   size_t o_bufB32 = bytes_block((size_t)BC * nfft32 * (size_t)N * sizeof(float2));
   size_t o_v = bytes_block((size_t)BC * N * ts);
@@ -749,9 +793,14 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   P->bufB = base + o_bufB;
   P->bufA32 = nfft32 > 0 ? base + o_bufA32 : nullptr;
   P->bufB32 = nfft32 > 0 ? base + o_bufB32 : nullptr;
-  P->b32exp = nfft32 > 0 ? (int*)(base + o_b32exp) : nullptr;
+  P->b32exp = scaled ? (int*)(base + o_b32exp) : nullptr;
   P->H32 = nfft32 > 0 ? (float*)(base + o_h32) : nullptr;
-  P->absmax = nfft32 > 0 ? (unsigned long long*)(base + o_absmax) : nullptr;
+  P->Hff = nfftff > 0 ? (ffd*)(base + o_hff) : nullptr;
+  P->bufAff = nfftff > 0 ? base + o_bufAff : nullptr;
+  P->bufBff = nfftff > 0 ? base + o_bufBff : nullptr;
+  P->tw4096_ff = nfftff > 0 ? (ffc*)(base + o_tw4096ff) : nullptr;
+  P->twfull_ff = nfftff > 0 && N > 4096 ? (ffc*)(base + o_twfullff) : nullptr;
+  P->absmax = scaled ? (unsigned long long*)(base + o_absmax) : nullptr;
   P->v = base + o_v;
   P->chat = base + o_chat;
   P->z = base + o_z;
@@ -783,8 +832,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     up(P->ra_ff, raf.data(), sizeof(float2) * raf.size());
     up(P->rb_ff, rbf.data(), sizeof(float2) * rbf.size());
   }
-  if (nfft32 > 0) {
-    // power-of-two scales of the FP32 band vectors: forward, the largest weight
+  if (scaled) {
+    // power-of-two scales of the FP32 and float-float band vectors: forward, the largest weight
     // C_n h_{m,n} (n >= ns, at n = ns) times 2^e <= 1; transposed, the largest
     // row factor (2 sin theta)^{-(m+1/2)} (at the band's first row) times 2^e <= 1
     const int K = prm.K, M = prm.M;
@@ -857,15 +906,20 @@ namespace {
 // the FFT buffer that does not hold `p`
 inline void* other(Plan& P, const void* p) { return p == P.bufA ? P.bufB : P.bufA; }
 
-// The band FFTs: terms m < Mh in precision T from `a` (result returned), terms
-// m >= Mh (FP64 plans) in FP32 from the plan's FP32 band buffers (result in *y32).
+// The band FFTs: terms m < M64 in precision T from `a` (result returned); in
+// FP64 plans terms M64 <= m < Mh in float-float from the plan's float-float band
+// buffers (result in *yff) and terms m >= Mh in FP32 from its FP32 ones (*y32).
 template <typename T>
-const C2<T>* band_ffts(Plan& P, void* a, int64_t nb, int dir, int transposed, const float2** y32) {
-  const int Ml = P.p.M - P.p.Mh;
+const C2<T>* band_ffts(Plan& P, void* a, int64_t nb, int dir, int transposed, const ffc** yff,
+                       const float2** y32) {
+  const int Ml = P.p.M - P.p.Mh, Mf = P.p.Mh - P.p.M64;
   *y32 = nullptr;
+  *yff = nullptr;
   const C2<T>* y = nullptr;
-  if (P.p.K > 0 && P.p.Mh > 0)
-    y = (const C2<T>*)launch_fft_bands<T>(P, a, other(P, a), nb, dir, transposed, P.p.Mh);
+  if (P.p.K > 0 && P.p.M64 > 0)
+    y = (const C2<T>*)launch_fft_bands<T>(P, a, other(P, a), nb, dir, transposed, P.p.M64);
+  if (P.p.K > 0 && Mf > 0 && P.bufAff)
+    *yff = (const ffc*)launch_fft_bands<ffd>(P, P.bufAff, P.bufBff, nb, dir, transposed, Mf);
   if (P.p.K > 0 && Ml > 0 && P.bufA32)
     *y32 = (const float2*)launch_fft_bands<float>(P, P.bufA32, P.bufB32, nb, dir, transposed, Ml);
   return y;
@@ -880,15 +934,16 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   int st = launch_rec_forward<T>(P, P.rec, c, vrec, nb);
   if (st) return st;
   const C2<T>* Y = nullptr;
+  const ffc* Yff = nullptr;
   const float2* Y32 = nullptr;
   if (KM > 0) {
     st = launch_absmax<T>(P, c, nb);
     if (st) return st;
-    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, (float2*)P.bufA32, nb);
+    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, (ffc*)P.bufAff, (float2*)P.bufA32, nb);
     if (st) return st;
-    Y = band_ffts<T>(P, P.bufA, nb, +1, 0, &Y32);
+    Y = band_ffts<T>(P, P.bufA, nb, +1, 0, &Yff, &Y32);
   }
-  st = launch_l2c_epi<T>(P, Y, Y32, vrec, v, nb);
+  st = launch_l2c_epi<T>(P, Y, Yff, Y32, vrec, v, nb);
   if (st) return st;
   st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA, nb);
   if (st) return st;
@@ -923,10 +978,17 @@ int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb) {
                           ? GBDLT_OK
                           : GBDLT_ERR_CUDA;
   }
-  int st = launch_tay_pro<T>(P, chat, (C2<T>*)P.bufA, inc0, npair, nb);
+  // pairs of small terms in float-float (FP64 plans), scaled by the input's exponent
+  ffc* Uff = (ffc*)P.bufAff;
+  const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
+  if (P64 == npair) Uff = nullptr;
+  int st = Uff ? launch_absmax<T>(P, chat, nb) : GBDLT_OK;
   if (st) return st;
-  const C2<T>* Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * npair, +1);
-  return launch_tay_epi<T>(P, Y, v, f, inc0, npair, nb);
+  st = launch_tay_pro<T>(P, chat, (C2<T>*)P.bufA, Uff, inc0, npair, nb);
+  if (st) return st;
+  const C2<T>* Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * P64, +1);
+  const ffc* Yff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), +1) : nullptr;
+  return launch_tay_epi<T>(P, Y, Yff, v, f, inc0, npair, nb);
 }
 
 // transposed chain: out = [D_s] P^T [D_w] g (idlt when weighted), Sec. 4.
@@ -942,27 +1004,34 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   T* z = (T*)P.z;
   T* rect = (T*)P.tmp;
   T* uhead = (T*)P.chat;  // first `head` coefficients of u (batch stride N)
-  int st = KM > 0 ? launch_absmax<T>(P, g, nb) : GBDLT_OK;
+  ffc* Uff = (ffc*)P.bufAff;
+  const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
+  if (P64 == npair) Uff = nullptr;
+  int st = (KM > 0 || Uff) ? launch_absmax<T>(P, g, nb) : GBDLT_OK;
   if (st) return st;
   const C2<T>* Y = nullptr;  // A4^T FFT output
   if (npair > 0) {
-    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, inc0, npair, nb);
+    st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, Uff, inc0, npair, nb);
     if (st) return st;
-    const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * npair, -1);
+    const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
+    const ffc* Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
     void* q = other(P, F);
-    st = launch_tayt_epi<T>(P, (const C2<T>*)F, (C2<T>*)q, head > 0 ? uhead : nullptr, inc0, npair, nb, head);
+    st = launch_tayt_epi<T>(P, (const C2<T>*)F, Fff, (C2<T>*)q, head > 0 ? uhead : nullptr, inc0, npair, nb,
+                            head);
     if (st) return st;
     Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), nb, +1);
   }
   void* U = Y ? other(P, Y) : P.bufA;
-  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, (float2*)P.bufA32, nb);
+  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, (ffc*)P.bufAff,
+                          (float2*)P.bufA32, nb);
   if (st) return st;
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
+  const ffc* Fff = nullptr;
   const float2* F32 = nullptr;
-  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &F32);
-  st = launch_l2ct_epi<T>(P, F2, F32, rect, out, scale_s, nb);
+  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &Fff, &F32);
+  st = launch_l2ct_epi<T>(P, F2, Fff, F32, rect, out, scale_s, nb);
   if (st) return st;
   return launch_head_t<T>(P, uhead, out, scale_s, nb);
 }
@@ -979,14 +1048,15 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   if (st) return st;
   const void* Y = launch_fft<T>(P, P.bufA, P.bufB, nb, +1);
   void* U = other(P, Y);
-  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, (float2*)P.bufA32, nb);
+  st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, (ffc*)P.bufAff, (float2*)P.bufA32, nb);
   if (st) return st;
   st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
+  const ffc* Fff = nullptr;
   const float2* F32 = nullptr;
-  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &F32);
-  st = launch_l2ct_epi<T>(P, F2, F32, rect, out, 0, nb);
+  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &Fff, &F32);
+  st = launch_l2ct_epi<T>(P, F2, Fff, F32, rect, out, 0, nb);
   if (st) return st;
   return launch_head_t<T>(P, y, out, 0, nb);
 }
@@ -994,10 +1064,16 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
 template <typename T>
 int run_chebeval_t(Plan& P, const T* g, T* out, int64_t nb) {
   const int npair = (P.p.L + 1) / 2;  // l = 0..L-1
-  int st = launch_tayt_pro<T>(P, g, 0, (C2<T>*)P.bufA, 1, npair, nb);
+  ffc* Uff = (ffc*)P.bufAff;
+  const int P64 = Uff ? taylor_p64(P.p, 1, npair) : npair;
+  if (P64 == npair) Uff = nullptr;
+  int st = Uff ? launch_absmax<T>(P, g, nb) : GBDLT_OK;
   if (st) return st;
-  const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * npair, -1);
-  return launch_tayt_epi<T>(P, (const C2<T>*)F, nullptr, out, 1, npair, nb);
+  st = launch_tayt_pro<T>(P, g, 0, (C2<T>*)P.bufA, Uff, 1, npair, nb);
+  if (st) return st;
+  const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
+  const ffc* Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
+  return launch_tayt_epi<T>(P, (const C2<T>*)F, Fff, nullptr, out, 1, npair, nb);
 }
 
 
@@ -1241,6 +1317,8 @@ static void fill_public(const Params& q, size_t ws, gbdlt_params* out) {
   out->direct_steps = q.direct_steps;
   out->head = q.head;
   out->M_fp32 = q.M - q.Mh;
+  out->M_ff = q.Mh - q.M64;
+  out->L_ff = q.L - q.Lff;
 }
 
 int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out) {

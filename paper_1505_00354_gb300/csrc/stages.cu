@@ -88,11 +88,25 @@ struct Scale32 {
   const int* e;                         // [2][K][M]: forward, transposed
   const unsigned long long* amax;       // [item] bits of max |input| (a non-negative double)
   const float* H32;                     // [M - Mh][N]: C_n h_{m,n} 2^{e_{K-1,m}} (0 below the last cut)
+  const ffd* Hff;                       // [Mh - M64][N]: the same for the float-float terms
 };
 __device__ __forceinline__ double pow2i(int e) {
   e = max(-1022, min(1023, e));
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
+// float-float from double (hi = fl(v), lo = fl(v - hi)) and back
+__device__ __forceinline__ ffd ffd_of(double v) {
+  const float h = __double2float_rn(v);
+  return ffd(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ ffc ffc_of(double x, double y) {
+  ffc r;
+  r.x = ffd_of(x);
+  r.y = ffd_of(y);
+  return r;
+}
+__device__ __forceinline__ double dbl_of(ffd a) { return (double)a.hi + (double)a.lo; }
+
 // 2^e as a float (e clamped to the normal range)
 __device__ __forceinline__ float pow2f(int e) {
   e = max(-126, min(127, e));
@@ -113,6 +127,20 @@ __constant__ double kInvInt[48] = {
     1.0 / 20,   1.0 / 21,   1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29,
     1.0 / 30,   1.0 / 31,   1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
     1.0 / 40,   1.0 / 41,   1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47};
+
+// the same 1/l as float-float pairs (the float-float Taylor pairs)
+#define GB_FFINV(l) ffd(1.0 / (l))
+__constant__ ffd kInvIntFF[48] = {
+    ffd(0.f, 0.f), GB_FFINV(1),  GB_FFINV(2),  GB_FFINV(3),  GB_FFINV(4),  GB_FFINV(5),  GB_FFINV(6),
+    GB_FFINV(7),   GB_FFINV(8),  GB_FFINV(9),  GB_FFINV(10), GB_FFINV(11), GB_FFINV(12), GB_FFINV(13),
+    GB_FFINV(14),  GB_FFINV(15), GB_FFINV(16), GB_FFINV(17), GB_FFINV(18), GB_FFINV(19), GB_FFINV(20),
+    GB_FFINV(21),  GB_FFINV(22), GB_FFINV(23), GB_FFINV(24), GB_FFINV(25), GB_FFINV(26), GB_FFINV(27),
+    GB_FFINV(28),  GB_FFINV(29), GB_FFINV(30), GB_FFINV(31), GB_FFINV(32), GB_FFINV(33), GB_FFINV(34),
+    GB_FFINV(35),  GB_FFINV(36), GB_FFINV(37), GB_FFINV(38), GB_FFINV(39), GB_FFINV(40), GB_FFINV(41),
+    GB_FFINV(42),  GB_FFINV(43), GB_FFINV(44), GB_FFINV(45), GB_FFINV(46), GB_FFINV(47)};
+#undef GB_FFINV
+// x times an exact power-of-two float (no rounding)
+__device__ __forceinline__ ffd ff_scale(ffd x, float p) { return ffd(x.hi * p, x.lo * p); }
 
 // signed Taylor coefficient of the cos part ((-1)^{l/2}, l even) and of the sin
 // part ((-1)^{(l+1)/2}, l odd), Eq. (6)
@@ -142,26 +170,47 @@ struct HTerm {
 // terms m < Mh go to U ([band][m][N], precision T), terms m >= Mh to U32
 // ([band][m - Mh][N], FP32)
 template <typename T>
-__global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, float2* __restrict__ U32, int64_t N,
-                          int M, int Mh, BandArgs B, const double* __restrict__ Cn,
-                          const double* __restrict__ Hnm, TwArgs<T> tw4N, Scale32 S) {
+__global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, ffc* __restrict__ Uff,
+                          float2* __restrict__ U32, int64_t N, int M, int Mh, int M64, BandArgs B,
+                          const double* __restrict__ Cn, const double* __restrict__ Hnm, TwArgs<T> tw4N,
+                          Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
-  const int Ml = M - Mh;
-  const int E = U32 ? item_exp(S, bt) : 0;
+  const int Ml = M - Mh, Mf = Mh - M64;
+  const int E = (U32 || Uff) ? item_exp(S, bt) : 0;
   c += bt * N;
-  U += bt * (int64_t)B.K * Mh * N;
+  U += bt * (int64_t)B.K * M64 * N;
+  if (Uff) Uff += bt * (int64_t)B.K * Mf * N;
   if (U32) U32 += bt * (int64_t)B.K * Ml * N;
   const T cv = c[n];
   const C2<T> e = twid<T>(tw4N, n);
   const C2<T> ce = mk<T>(cv * e.x, cv * e.y);
   HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
   const C2<T> zero = mk<T>((T)0, (T)0);
-  for (int m = 0; m < Mh; ++m) {
+  for (int m = 0; m < M64; ++m) {
     const T a = H.at(m);
     const C2<T> val = mk<T>(a * ce.x, a * ce.y);
-    for (int s = 0; s < B.K; ++s) U[(int64_t)(s * Mh + m) * N + n] = (n >= B.ns[s]) ? val : zero;
+    for (int s = 0; s < B.K; ++s) U[(int64_t)(s * M64 + m) * N + n] = (n >= B.ns[s]) ? val : zero;
+  }
+  if (Mf > 0) {
+    // float-float terms: Hff = C_n h_{m,n} 2^{e_{K-1,m}} times c_n e_n 2^{-E} in
+    // float-float, then the band's exact 2^{e_{s,m} - e_{K-1,m}}
+    const double sE = pow2i(-E);
+    const ffc cf = ffc_of((double)ce.x * sE, (double)ce.y * sE);
+    const int* eK = S.e + (B.K - 1) * M;
+    const ffc zz = ffc_of(0.0, 0.0);
+    for (int m = M64; m < Mh; ++m) {
+      const ffd h = S.Hff[(int64_t)(m - M64) * N + n];
+      const ffd vx = h * cf.x, vy = h * cf.y;
+      for (int s = 0; s < B.K; ++s) {
+        const float p = pow2f(S.e[s * M + m] - eK[m]);
+        ffc w;
+        w.x = ffd(vx.hi * p, vx.lo * p);
+        w.y = ffd(vy.hi * p, vy.lo * p);
+        Uff[(int64_t)(s * Mf + m - M64) * N + n] = (n >= B.ns[s]) ? w : zz;
+      }
+    }
   }
   if (Ml > 0) {
     // FP32 terms: C_n h_{m,n} 2^{e_{s,m}} c_n e_n 2^{-E} from the float table
@@ -213,18 +262,22 @@ __global__ void k_row_factors_init(RowAR* __restrict__ AR, int64_t N) {
   AR[k] = RowAR{ca * sq, sa * sq, st * g, -ct * g};
 }
 
-// Hnm[m N + n] = C_n h_{m,n} for m < Mh (the recurrence in FP64, once per plan);
-// for the FP32 terms m >= Mh, H32[(m - Mh) N + n] = C_n h_{m,n} 2^{eK[m]} as a
-// float, 0 below the smallest band cut ns_min (never read there)
-__global__ void k_hnm_init(double* __restrict__ Hnm, float* __restrict__ H32, const double* __restrict__ Cn,
-                           int64_t N, int M, int Mh, const int* __restrict__ eK, int64_t ns_min) {
+// Hnm[m N + n] = C_n h_{m,n} for the FP64 terms m < M64 (the recurrence in FP64,
+// once per plan); for the float-float terms M64 <= m < Mh and the FP32 terms
+// m >= Mh, Hff[(m - M64) N + n] and H32[(m - Mh) N + n] = C_n h_{m,n} 2^{eK[m]},
+// 0 below the smallest band cut ns_min (never read there)
+__global__ void k_hnm_init(double* __restrict__ Hnm, ffd* __restrict__ Hff, float* __restrict__ H32,
+                           const double* __restrict__ Cn, int64_t N, int M, int Mh, int M64,
+                           const int* __restrict__ eK, int64_t ns_min) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   double h = 1.0;
   const double cn = Cn[n];
   for (int m = 0; m < M; ++m) {
-    if (m < Mh)
+    if (m < M64)
       Hnm[(int64_t)m * N + n] = cn * h;
+    else if (m < Mh)
+      Hff[(int64_t)(m - M64) * N + n] = n >= ns_min ? ffd_of(cn * h * pow2i(eK[m])) : ffd(0.f, 0.f);
     else
       H32[(int64_t)(m - Mh) * N + n] = n >= ns_min ? (float)(cn * h * pow2i(eK[m])) : 0.f;
     const double mh = (double)m + 0.5;
@@ -233,16 +286,17 @@ __global__ void k_hnm_init(double* __restrict__ Hnm, float* __restrict__ H32, co
 }
 
 template <typename T>
-__global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const float2* __restrict__ Y32, const T* __restrict__ vrec,
-                          T* __restrict__ v, int64_t N, int M, int Mh, BandArgs B, const RowAR* __restrict__ AR,
-                          Scale32 S) {
+__global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Yff, const float2* __restrict__ Y32,
+                          const T* __restrict__ vrec, T* __restrict__ v, int64_t N, int M, int Mh, int M64,
+                          BandArgs B, const RowAR* __restrict__ AR, Scale32 S) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int64_t bt = blockIdx.y;
-  const int Ml = M - Mh;
+  const int Ml = M - Mh, Mf = Mh - M64;
   vrec += bt * N;
   v += bt * N;
-  if (Y) Y += bt * (int64_t)B.K * Mh * N;
+  if (Y) Y += bt * (int64_t)B.K * M64 * N;
+  if (Yff) Yff += bt * (int64_t)B.K * Mf * N;
   if (Y32) Y32 += bt * (int64_t)B.K * Ml * N;
   T acc = vrec[k];
   const int s = band_of(B, k, N);
@@ -251,19 +305,49 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const float2* __restrict_
     row_factors<T>(k, N, AR, al, rho);
     const bool odd = k & 1;
     const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
-    const C2<T>* y = Y + (int64_t)s * Mh * N + idx;
-    for (int m = 0; m < Mh; ++m) {
+    const C2<T>* y = Y + (int64_t)s * M64 * N + idx;
+    for (int m = 0; m < M64; ++m) {
       C2<T> z = y[(int64_t)m * N];
       if (odd) z.y = -z.y;
       acc += al.x * z.x - al.y * z.y;
       al = cmul<T>(al, rho);
     }
+    // al = alpha rho^M64 here
+    ffc bff;  // float-float b_m = alpha rho^m 2^{-e_{s,m}}
+    if (Mf > 0) {
+      // float-float terms: with the band's FFT output scaled by 2^{e_{s,m} - E},
+      // term m adds 2^E Re(b_m z_m); b advances by rho 2^{e_{s,m} - e_{s,m+1}}
+      const int* e = S.e + s * M;
+      const double b0 = pow2i(-e[M64]);
+      bff = ffc_of((double)al.x * b0, (double)al.y * b0);
+      const ffc r = ffc_of((double)rho.x, (double)rho.y);
+      ffd aff(0.f, 0.f);
+      for (int m = M64; m < Mh; ++m) {
+        ffc z = Yff[(int64_t)(s * Mf + m - M64) * N + idx];
+        if (odd) z.y = -z.y;
+        aff = aff + ff_dot2(bff.x, z.x, bff.y, z.y, -1.f);
+        if (m + 1 < M) {
+          const float p = pow2f(e[m] - e[m + 1]);
+          ffc rp;
+          rp.x = ffd(r.x.hi * p, r.x.lo * p);
+          rp.y = ffd(r.y.hi * p, r.y.lo * p);
+          bff = cmul<ffd>(bff, rp);
+        }
+      }
+      acc += (T)(dbl_of(aff) * pow2i(item_exp(S, bt)));
+    }
     if (Ml > 0) {
       // FP32 terms: with the band's FFT output scaled by 2^{e_{s,m} - E}, term m
-      // adds 2^E Re(b_m z_m), b_m = alpha rho^m 2^{-e_{s,m}} (al = alpha rho^Mh here)
+      // adds 2^E Re(b_m z_m), b_m = alpha rho^m 2^{-e_{s,m}}, continued from the
+      // float-float terms (or from al = alpha rho^Mh when there are none)
       const int* e = S.e + s * M;
-      const double b0 = pow2i(-e[Mh]);
-      float2 b = make_float2((float)((double)al.x * b0), (float)((double)al.y * b0));
+      float2 b;
+      if (Mf > 0) {
+        b = make_float2(bff.x.hi, bff.y.hi);
+      } else {
+        const double b0 = pow2i(-e[Mh]);
+        b = make_float2((float)((double)al.x * b0), (float)((double)al.y * b0));
+      }
       const float2 r = make_float2((float)rho.x, (float)rho.y);
       const float2* y32 = Y32 + (int64_t)s * Ml * N + idx;
       float a32 = 0.f;
@@ -334,13 +418,17 @@ __global__ void k_fcs_re_epi(const C2<T>* __restrict__ Y, T* __restrict__ out, i
 // ---------------------------------------------------------------- Taylor (forward)
 // pair p: X part l_a = 2p + (inc0 ? 0 : 2), Y part l_b = 2p + 1; a term is used
 // only when its l <= L-1.
+// pairs p < P64 go to U ([item][P64][N], precision T), pairs p >= P64 to Uff
+// ([item][npair - P64][N], float-float, scaled by 2^{-E})
 template <typename T>
-__global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int64_t N, int L,
-                          int inc0, int npair, TwArgs<T> tw4N) {
+__global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, ffc* __restrict__ Uff, int64_t N,
+                          int L, int inc0, int npair, int P64, TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  chat += (int64_t)blockIdx.y * N;
-  U += (int64_t)blockIdx.y * npair * N;
+  const int64_t bt = blockIdx.y;
+  chat += bt * N;
+  U += bt * P64 * N;
+  if (Uff) Uff += bt * (npair - P64) * N;
   const T invN = (T)1 / (T)N;  // exact: N is a power of two
   const T r = (T)n * invN;
   const T rN = (T)(N - n) * invN;
@@ -355,7 +443,7 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int
   const T r2 = r * r, rN2 = rN * rN;
   T pa = inc0 ? (T)1 : r2, paN = inc0 ? (T)1 : rN2;  // r^{l_a}
   T pb = r, pbN = rN;                               // r^{l_b}
-  for (int p = 0; p < npair; ++p) {
+  for (int p = 0; p < P64; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const bool ua = la <= L - 1, ub = lb <= L - 1;
@@ -373,15 +461,49 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, int
     pb *= r2;
     pbN *= rN2;
   }
+  if (P64 < npair) {
+    // float-float pairs: the same sums, continued from the powers reached above
+    // (r = n/N and rN are exact floats, so r^2 and rN^2 are exact float-float)
+    const double sE = pow2i(-item_exp(S, bt));
+    const ffc e1 = ffc_of((double)E1.x * sE, (double)E1.y * sE);
+    const ffc e2 = ffc_of((double)E2.x * sE, (double)E2.y * sE);
+    const ffd c0 = ffd_of((double)cn * sE);
+    const ffd fr((float)r, 0.f), frN((float)rN, 0.f);
+    const ffd fr2 = fr * fr, frN2 = frN * frN;
+    ffd fa = ffd_of((double)pa), faN = ffd_of((double)paN), fb = ffd_of((double)pb), fbN = ffd_of((double)pbN);
+    const ffd z(0.f, 0.f);
+    for (int p = P64; p < npair; ++p) {
+      const int la = 2 * p + (inc0 ? 0 : 2);
+      const int lb = 2 * p + 1;
+      const bool ua = la <= L - 1, ub = lb <= L - 1;
+      ffc val;
+      if (n == 0) {
+        val.x = ua ? ff_scale(fa * c0, 2.f) : z;
+        val.y = z;
+      } else {
+        const ffd A = (ua ? fa : z) + (ub ? fb : z);
+        const ffd Bm = (ub ? fbN : z) - (ua ? faN : z);
+        val.x = ff_dot2(A, e1.x, Bm, e2.x, 1.f);
+        val.y = ff_dot2(A, e1.y, Bm, e2.y, 1.f);
+      }
+      Uff[(int64_t)(p - P64) * N + n] = val;
+      fa = fa * fr2;
+      faN = faN * frN2;
+      fb = fb * fr2;
+      fbN = fbN * frN2;
+    }
+  }
 }
 
 template <typename T>
-__global__ void k_tay_epi(const C2<T>* __restrict__ Y, const T* __restrict__ v, T* __restrict__ f,
-                          const double* __restrict__ tN, int64_t N, int L, int inc0, int npair) {
+__global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Yff, const T* __restrict__ v,
+                          T* __restrict__ f, const double* __restrict__ tN, int64_t N, int L, int inc0, int npair,
+                          int P64, Scale32 S) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int64_t bt = blockIdx.y;
-  Y += bt * npair * N;
+  Y += bt * P64 * N;
+  if (Yff) Yff += bt * (npair - P64) * N;
   f += bt * N;
   if (v) v += bt * N;
   const T t = (T)tN[k];
@@ -394,7 +516,7 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const T* __restrict__ v, 
   T qa = (T)1;                        // q_{l_a} (inc0: q_0)
   T qb = t;                           // q_{l_b} = q_1
   if (!inc0) qa = qb * t * (T)kInvInt[2];
-  for (int p = 0; p < npair; ++p) {
+  for (int p = 0; p < P64; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const C2<T> y = Y[(int64_t)p * N + idx];
@@ -409,18 +531,41 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const T* __restrict__ v, 
       qa = qb * t * (T)kInvInt[la + 2];
     }
   }
+  if (P64 < npair) {
+    // float-float pairs, continued from q reached above; outputs scaled by 2^{-E}
+    const ffd ft = ffd_of((double)t);
+    ffd fqa = ffd_of((double)qa), fqb = ffd_of((double)qb), aff(0.f, 0.f);
+    const float fsk = (float)sk;
+    for (int p = P64; p < npair; ++p) {
+      const int la = 2 * p + (inc0 ? 0 : 2);
+      const int lb = 2 * p + 1;
+      const ffc y = Yff[(int64_t)(p - P64) * N + idx];
+      if (la <= L - 1) aff = aff + ff_scale(fqa * y.x, sgn_even(la) * 0.5f);
+      if (lb <= L - 1) aff = aff + ff_scale(fqb * y.y, sgn_odd(lb) * fsk);
+      if (inc0) {
+        fqb = fqb * ft * kInvIntFF[lb + 1] * ft * kInvIntFF[lb + 2];
+        fqa = fqa * ft * kInvIntFF[la + 1] * ft * kInvIntFF[la + 2];
+      } else {
+        fqb = fqa * ft * kInvIntFF[la + 1];
+        fqa = fqb * ft * kInvIntFF[la + 2];
+      }
+    }
+    acc += (T)(dbl_of(aff) * pow2i(item_exp(S, bt)));
+  }
   f[k] = acc;
 }
 
 // ---------------------------------------------------------------- Taylor (transposed)
 template <typename T>
 __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__ wscale,
-                           const double* __restrict__ tN, C2<T>* __restrict__ U, int64_t N, int L,
-                           int inc0, int npair) {
+                           const double* __restrict__ tN, C2<T>* __restrict__ U, ffc* __restrict__ Uff, int64_t N,
+                           int L, int inc0, int npair, int P64, Scale32 S) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
-  fin += (int64_t)blockIdx.y * N;
-  U += (int64_t)blockIdx.y * npair * N;
+  const int64_t bt = blockIdx.y;
+  fin += bt * N;
+  U += bt * P64 * N;
+  if (Uff) Uff += bt * (npair - P64) * N;
   const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
   T g0 = fin[k0], g1 = fin[k1];
   if (wscale) {
@@ -431,7 +576,7 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
   const T t02 = t0 * t0, t12 = t1 * t1;
   T pa0 = inc0 ? (T)1 : t02, pa1 = inc0 ? (T)1 : t12;
   T pb0 = t0, pb1 = t1;
-  for (int p = 0; p < npair; ++p) {
+  for (int p = 0; p < P64; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const T ua = la <= L - 1 ? (T)1 : (T)0;
@@ -444,18 +589,45 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
     pb0 *= t02;
     pb1 *= t12;
   }
+  if (P64 < npair) {
+    // float-float pairs, continued from the powers reached above, scaled by 2^{-E}
+    const double sE = pow2i(-item_exp(S, bt));
+    const ffd fg0 = ffd_of((double)g0 * sE), fg1 = ffd_of((double)g1 * sE);
+    const ffd ft0 = ffd_of((double)t0), ft1 = ffd_of((double)t1);
+    const ffd ft02 = ft0 * ft0, ft12 = ft1 * ft1;
+    ffd fa0 = ffd_of((double)pa0), fa1 = ffd_of((double)pa1), fb0 = ffd_of((double)pb0), fb1 = ffd_of((double)pb1);
+    const ffd z(0.f, 0.f);
+    for (int p = P64; p < npair; ++p) {
+      const int la = 2 * p + (inc0 ? 0 : 2);
+      const int lb = 2 * p + 1;
+      const bool ua = la <= L - 1, ub = lb <= L - 1;
+      ffc w0, w1;
+      w0.x = ua ? fa0 * fg0 : z;
+      w0.y = ub ? fb0 * fg0 : z;
+      w1.x = ua ? fa1 * fg1 : z;
+      w1.y = ub ? -(fb1 * fg1) : z;
+      Uff[(int64_t)(p - P64) * N + kp] = w0;
+      Uff[(int64_t)(p - P64) * N + N - 1 - kp] = w1;
+      fa0 = fa0 * ft02;
+      fa1 = fa1 * ft12;
+      fb0 = fb0 * ft02;
+      fb1 = fb1 * ft12;
+    }
+  }
 }
 
 // Q != null: write the FCS input of A4^T, Q_n = d_n u'_n e^{i pi n/(2N)};
 // uout != null: write u_n to uout for n < nu (both when the chain also needs the
 // first nu coefficients of u, for the dense head block).
 template <typename T>
-__global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T* __restrict__ uout,
-                           int64_t N, int L, int inc0, int npair, int64_t nu, TwArgs<T> tw4N) {
+__global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ Fff, C2<T>* __restrict__ Q,
+                           T* __restrict__ uout, int64_t N, int L, int inc0, int npair, int P64, int64_t nu,
+                           TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
-  F += bt * npair * N;
+  F += bt * P64 * N;
+  if (Fff) Fff += bt * (npair - P64) * N;
   if (Q) Q += bt * N;
   if (uout) uout += bt * N;
   const T r = (T)n * ((T)1 / (T)N);  // exact: N is a power of two
@@ -469,7 +641,7 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
   T Ax = (T)0, Ay = (T)0;
   T qa = (T)1, qb = r;  // r^l / l! for l_a (inc0: 0) and l_b = 1
   if (!inc0) qa = qb * r * (T)kInvInt[2];
-  for (int p = 0; p < npair; ++p) {
+  for (int p = 0; p < P64; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const C2<T> Fn = F[(int64_t)p * N + n];
@@ -486,6 +658,33 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, C2<T>* __restrict__ Q, T
       qb = qa * r * (T)kInvInt[la + 1];
       qa = qb * r * (T)kInvInt[la + 2];
     }
+  }
+  if (P64 < npair) {
+    // float-float pairs (outputs scaled by 2^{-E}), continued from q reached above
+    const ffd fr((float)r, 0.f);  // n/N: exact
+    ffd fqa = ffd_of((double)qa), fqb = ffd_of((double)qb);
+    ffd ax(0.f, 0.f), ay(0.f, 0.f);
+    for (int p = P64; p < npair; ++p) {
+      const int la = 2 * p + (inc0 ? 0 : 2);
+      const int lb = 2 * p + 1;
+      const ffc Fn = Fff[(int64_t)(p - P64) * N + n];
+      const ffc Fm = Fff[(int64_t)(p - P64) * N + nm];
+      const float ha = la <= L - 1 ? (sgn_even(la) > 0 ? 0.5f : -0.5f) : 0.f;
+      const float hb = (lb <= L - 1 && n > 0) ? (sgn_odd(lb) > 0 ? 0.5f : -0.5f) : 0.f;
+      const ffd ca = ff_scale(fqa, ha), cb = ff_scale(fqb, hb);
+      ax = ax + ff_dot2(ca, Fn.x + Fm.x, cb, Fm.x - Fn.x, -1.f);
+      ay = ay + ff_dot2(ca, Fn.y - Fm.y, cb, Fm.y + Fn.y, 1.f);
+      if (inc0) {
+        fqb = fqb * fr * kInvIntFF[lb + 1] * fr * kInvIntFF[lb + 2];
+        fqa = fqa * fr * kInvIntFF[la + 1] * fr * kInvIntFF[la + 2];
+      } else {
+        fqb = fqa * fr * kInvIntFF[la + 1];
+        fqa = fqb * fr * kInvIntFF[la + 2];
+      }
+    }
+    const double sE = pow2i(item_exp(S, bt));
+    Ax += (T)(dbl_of(ax) * sE);
+    Ay += (T)(dbl_of(ay) * sE);
   }
   const T acc = e.x * Ax + e.y * Ay;
   if (Q) {
@@ -518,16 +717,17 @@ __device__ __forceinline__ T row_z(const C2<T>* Y, const T* g, const double* wsc
 template <typename T>
 __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
                            const double* __restrict__ wscale, T* __restrict__ zout,
-                           C2<T>* __restrict__ U, float2* __restrict__ U32, int64_t N, int M, int Mh, BandArgs B,
-                           const RowAR* __restrict__ AR, Scale32 S) {
+                           C2<T>* __restrict__ U, ffc* __restrict__ Uff, float2* __restrict__ U32, int64_t N,
+                           int M, int Mh, int M64, BandArgs B, const RowAR* __restrict__ AR, Scale32 S) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= N / 2) return;
   const int64_t bt = blockIdx.y;
-  const int Ml = M - Mh;
+  const int Ml = M - Mh, Mf = Mh - M64;
   if (Y) Y += bt * N;
   if (g) g += bt * N;
   zout += bt * N;
-  U += bt * (int64_t)B.K * Mh * N;
+  U += bt * (int64_t)B.K * M64 * N;
+  if (Uff) Uff += bt * (int64_t)B.K * Mf * N;
   if (U32) U32 += bt * (int64_t)B.K * Ml * N;
   const int64_t k0 = 2 * kp, k1 = 2 * kp + 1;
   const T z0 = row_z<T>(Y, g, wscale, k0, N);
@@ -538,49 +738,97 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
   C2<T> al0 = mk<T>(0, 0), rho0 = mk<T>(0, 0), al1 = mk<T>(0, 0), rho1 = mk<T>(0, 0);
   if (s0 >= 0) row_factors<T>(k0, N, AR, al0, rho0);
   if (s1 >= 0) row_factors<T>(k1, N, AR, al1, rho1);
-  for (int m = 0; m < Mh; ++m) {
+  for (int m = 0; m < M64; ++m) {
     // beta = z alpha; a = Re beta, h = (-1)^k Im beta
     const C2<T> v0 = mk<T>(z0 * al0.x, z0 * al0.y);
     const C2<T> v1 = mk<T>(z1 * al1.x, -z1 * al1.y);
     for (int s = 0; s < B.K; ++s) {
-      C2<T>* u = U + (int64_t)(s * Mh + m) * N;
+      C2<T>* u = U + (int64_t)(s * M64 + m) * N;
       u[kp] = (s == s0) ? v0 : mk<T>(0, 0);
       u[N - 1 - kp] = (s == s1) ? v1 : mk<T>(0, 0);
     }
     if (s0 >= 0) al0 = cmul<T>(al0, rho0);
     if (s1 >= 0) al1 = cmul<T>(al1, rho1);
   }
-  if (Ml > 0) {
-    // FP32 terms: beta 2^{g_{s,m} - E} = (z 2^{-E}) gamma_m with gamma_m =
-    // alpha rho^m 2^{g_{s,m}}, advanced in FP32 by rho 2^{g_{s,m+1} - g_{s,m}}
-    // (al = alpha rho^Mh here)
+  // al = alpha rho^M64 here.  The float-float and FP32 terms write
+  // beta 2^{g_{s,m} - E} = (z 2^{-E}) gamma_m with gamma_m = alpha rho^m 2^{g_{s,m}},
+  // advanced by rho 2^{g_{s,m+1} - g_{s,m}} (float-float, then FP32)
+  if (Mf > 0 || Ml > 0) {
     const double sE = pow2i(-item_exp(S, bt));
-    const float f0 = (float)((double)z0 * sE), f1 = (float)((double)z1 * sE);
     const int* g0 = S.e + B.K * M + max(s0, 0) * M;
     const int* g1 = S.e + B.K * M + max(s1, 0) * M;
-    float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f), r0 = c0, r1 = c0;
-    if (s0 >= 0) {
-      const double q = pow2i(g0[Mh]);
-      c0 = make_float2((float)((double)al0.x * q), (float)((double)al0.y * q));
-      r0 = make_float2((float)rho0.x, (float)rho0.y);
-    }
-    if (s1 >= 0) {
-      const double q = pow2i(g1[Mh]);
-      c1 = make_float2((float)((double)al1.x * q), (float)((double)al1.y * q));
-      r1 = make_float2((float)rho1.x, (float)rho1.y);
-    }
-    for (int m = Mh; m < M; ++m) {
-      const float2 w0 = make_float2(f0 * c0.x, f0 * c0.y);
-      const float2 w1 = make_float2(f1 * c1.x, -f1 * c1.y);
-      for (int s = 0; s < B.K; ++s) {
-        float2* u = U32 + (int64_t)(s * Ml + m - Mh) * N;
-        u[kp] = (s == s0) ? w0 : make_float2(0.f, 0.f);
-        u[N - 1 - kp] = (s == s1) ? w1 : make_float2(0.f, 0.f);
+    ffc c0ff = ffc_of(0.0, 0.0), c1ff = c0ff;
+    if (Mf > 0) {
+      const ffd f0 = ffd_of((double)z0 * sE), f1 = ffd_of((double)z1 * sE);
+      ffc r0 = c0ff, r1 = c0ff;
+      if (s0 >= 0) {
+        const double q = pow2i(g0[M64]);
+        c0ff = ffc_of((double)al0.x * q, (double)al0.y * q);
+        r0 = ffc_of((double)rho0.x, (double)rho0.y);
       }
-      if (m + 1 < M) {
-        const float p0 = pow2f(g0[m + 1] - g0[m]), p1 = pow2f(g1[m + 1] - g1[m]);
-        c0 = cmulf(c0, make_float2(r0.x * p0, r0.y * p0));
-        c1 = cmulf(c1, make_float2(r1.x * p1, r1.y * p1));
+      if (s1 >= 0) {
+        const double q = pow2i(g1[M64]);
+        c1ff = ffc_of((double)al1.x * q, (double)al1.y * q);
+        r1 = ffc_of((double)rho1.x, (double)rho1.y);
+      }
+      const ffc zz = ffc_of(0.0, 0.0);
+      for (int m = M64; m < Mh; ++m) {
+        ffc w0, w1;
+        w0.x = f0 * c0ff.x;
+        w0.y = f0 * c0ff.y;
+        w1.x = f1 * c1ff.x;
+        w1.y = -(f1 * c1ff.y);
+        for (int s = 0; s < B.K; ++s) {
+          ffc* u = Uff + (int64_t)(s * Mf + m - M64) * N;
+          u[kp] = (s == s0) ? w0 : zz;
+          u[N - 1 - kp] = (s == s1) ? w1 : zz;
+        }
+        if (m + 1 < M) {
+          const float p0 = pow2f(g0[m + 1] - g0[m]), p1 = pow2f(g1[m + 1] - g1[m]);
+          ffc q0, q1;
+          q0.x = ffd(r0.x.hi * p0, r0.x.lo * p0);
+          q0.y = ffd(r0.y.hi * p0, r0.y.lo * p0);
+          q1.x = ffd(r1.x.hi * p1, r1.x.lo * p1);
+          q1.y = ffd(r1.y.hi * p1, r1.y.lo * p1);
+          c0ff = cmul<ffd>(c0ff, q0);
+          c1ff = cmul<ffd>(c1ff, q1);
+        }
+      }
+    }
+    if (Ml > 0) {
+      const float f0 = (float)((double)z0 * sE), f1 = (float)((double)z1 * sE);
+      float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f), r0 = c0, r1 = c0;
+      if (s0 >= 0) {
+        if (Mf > 0) {
+          c0 = make_float2(c0ff.x.hi, c0ff.y.hi);
+        } else {
+          const double q = pow2i(g0[Mh]);
+          c0 = make_float2((float)((double)al0.x * q), (float)((double)al0.y * q));
+        }
+        r0 = make_float2((float)rho0.x, (float)rho0.y);
+      }
+      if (s1 >= 0) {
+        if (Mf > 0) {
+          c1 = make_float2(c1ff.x.hi, c1ff.y.hi);
+        } else {
+          const double q = pow2i(g1[Mh]);
+          c1 = make_float2((float)((double)al1.x * q), (float)((double)al1.y * q));
+        }
+        r1 = make_float2((float)rho1.x, (float)rho1.y);
+      }
+      for (int m = Mh; m < M; ++m) {
+        const float2 w0 = make_float2(f0 * c0.x, f0 * c0.y);
+        const float2 w1 = make_float2(f1 * c1.x, -f1 * c1.y);
+        for (int s = 0; s < B.K; ++s) {
+          float2* u = U32 + (int64_t)(s * Ml + m - Mh) * N;
+          u[kp] = (s == s0) ? w0 : make_float2(0.f, 0.f);
+          u[N - 1 - kp] = (s == s1) ? w1 : make_float2(0.f, 0.f);
+        }
+        if (m + 1 < M) {
+          const float p0 = pow2f(g0[m + 1] - g0[m]), p1 = pow2f(g1[m + 1] - g1[m]);
+          c0 = cmulf(c0, make_float2(r0.x * p0, r0.y * p0));
+          c1 = cmulf(c1, make_float2(r1.x * p1, r1.y * p1));
+        }
       }
     }
   }
@@ -593,16 +841,18 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
 // terms is taken before the rotation,
 //   out_n = rect_n + Re(e_n sum_m C_n h_{m,n} sum_{s: n >= n_s} F^{(s,m)}_{N-n}).
 template <typename T>
-__global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const float2* __restrict__ F32, const T* __restrict__ rect,
-                           T* __restrict__ out, int64_t N, int M, int Mh, BandArgs B, const double* __restrict__ Cn,
+__global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ Fff,
+                           const float2* __restrict__ F32, const T* __restrict__ rect, T* __restrict__ out, int64_t N,
+                           int M, int Mh, int M64, BandArgs B, const double* __restrict__ Cn,
                            const double* __restrict__ Hnm, int scale_s, TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
-  const int Ml = M - Mh;
+  const int Ml = M - Mh, Mf = Mh - M64;
   rect += bt * N;
   out += bt * N;
-  if (F) F += bt * (int64_t)B.K * Mh * N;
+  if (F) F += bt * (int64_t)B.K * M64 * N;
+  if (Fff) Fff += bt * (int64_t)B.K * Mf * N;
   if (F32) F32 += bt * (int64_t)B.K * Ml * N;
   T acc = rect[n];
   if (B.K > 0 && M > 0) {
@@ -612,11 +862,33 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const float2* __restrict
     if (s0 < B.K) {
       HTerm<T> H{Hnm, N, n, sizeof(T) == 8 ? (T)0 : (T)Cn[n], (T)1};
       C2<T> V = mk<T>((T)0, (T)0);
-      for (int m = 0; m < Mh; ++m) {
-        C2<T> X = F[(int64_t)(s0 * Mh + m) * N + nm];
-        for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * Mh + m) * N + nm]);
+      for (int m = 0; m < M64; ++m) {
+        C2<T> X = F[(int64_t)(s0 * M64 + m) * N + nm];
+        for (int s = s0 + 1; s < B.K; ++s) X = cadd<T>(X, F[(int64_t)(s * M64 + m) * N + nm]);
         const T hm = H.at(m);
         V = mk<T>(V.x + hm * X.x, V.y + hm * X.y);
+      }
+      if (Mf > 0) {
+        // float-float terms: band s's output is scaled by 2^{g_{s,m} - E}; with
+        // Hff = C_n h_{m,n} 2^{e_{K-1,m}} the term is
+        // 2^E Hff sum_s 2^{-e_{K-1,m} - g_{s,m}} Fff, summed in float-float
+        const int* eK = S.e + (B.K - 1) * M;
+        const int* et = S.e + B.K * M;
+        ffd vx(0.f, 0.f), vy(0.f, 0.f);
+        for (int m = M64; m < Mh; ++m) {
+          ffd xx(0.f, 0.f), xy(0.f, 0.f);
+          for (int s = s0; s < B.K; ++s) {
+            const ffc q = Fff[(int64_t)(s * Mf + m - M64) * N + nm];
+            const float p = pow2f(-eK[m] - et[s * M + m]);
+            xx = xx + ffd(q.x.hi * p, q.x.lo * p);
+            xy = xy + ffd(q.y.hi * p, q.y.lo * p);
+          }
+          const ffd h = S.Hff[(int64_t)(m - M64) * N + n];
+          vx = vx + h * xx;
+          vy = vy + h * xy;
+        }
+        const double sE = pow2i(item_exp(S, bt));
+        V = mk<T>(V.x + (T)(dbl_of(vx) * sE), V.y + (T)(dbl_of(vy) * sE));
       }
       if (Ml > 0) {
         // FP32 terms: band s's output is scaled by 2^{g_{s,m} - E}; with
@@ -663,7 +935,7 @@ __global__ void k_scale(const T* __restrict__ in, T* __restrict__ out, const dou
 constexpr int TPB = 256;
 inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
-Scale32 scale32(const Plan& P) { return Scale32{P.b32exp, P.absmax, P.H32}; }
+Scale32 scale32(const Plan& P) { return Scale32{P.b32exp, P.absmax, P.H32, P.Hff}; }
 
 // amax[item] = max over n of |x_n| as the bits of a non-negative double (their
 // integer order is the order of the values); amax is zeroed before the launch
@@ -681,10 +953,10 @@ __global__ void k_absmax(const T* __restrict__ x, int64_t N, unsigned long long*
 }  // namespace
 
 template <typename T>
-int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, float2* U32, int64_t nb) {
+int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, ffc* Uff, float2* U32, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(c, U, U32, P.p.N, P.p.M, P.p.Mh, band_args(P),
-                                                                       P.Cn, P.Hnm, tw, scale32(P));
+  k_l2c_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(
+      c, U, Uff, U32, P.p.N, P.p.M, P.p.Mh, P.p.M64, band_args(P), P.Cn, P.Hnm, tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -694,9 +966,9 @@ int launch_l2c_pro(Plan& P, const T* c, C2<T>* U, float2* U32, int64_t nb) {
   return check_launch();
 }
 template <typename T>
-int launch_l2c_epi(Plan& P, const C2<T>* Y, const float2* Y32, const T* vrec, T* v, int64_t nb) {
-  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, Y32, vrec, v, P.p.N, P.p.M, P.p.Mh,
-                                                                       band_args(P), P.row_ar, scale32(P));
+int launch_l2c_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const float2* Y32, const T* vrec, T* v, int64_t nb) {
+  k_l2c_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(
+      Y, Yff, Y32, vrec, v, P.p.N, P.p.M, P.p.Mh, P.p.M64, band_args(P), P.row_ar, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -752,9 +1024,11 @@ int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb) {
   return check_launch();
 }
 template <typename T>
-int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair, int64_t nb) {
+int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_tay_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(chat, U, P.p.N, P.p.L, inc0, npair, tw);
+  const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
+  k_tay_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(chat, U, Uff, P.p.N, P.p.L, inc0, npair, P64,
+                                                                       tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -764,8 +1038,10 @@ int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, int inc0, int npair, int64_
   return check_launch();
 }
 template <typename T>
-int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npair, int64_t nb) {
-  k_tay_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, v, f, P.tN, P.p.N, P.p.L, inc0, npair);
+int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, int inc0, int npair, int64_t nb) {
+  const int P64 = Yff ? taylor_p64(P.p, inc0, npair) : npair;
+  k_tay_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, Yff, v, f, P.tN, P.p.N, P.p.L, inc0, npair,
+                                                                       P64, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -775,9 +1051,11 @@ int launch_tay_epi(Plan& P, const C2<T>* Y, const T* v, T* f, int inc0, int npai
   return check_launch();
 }
 template <typename T>
-int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npair, int64_t nb) {
+int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb) {
   const double* w = use_w ? P.w : nullptr;
-  k_tayt_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(f, w, P.tN, U, P.p.N, P.p.L, inc0, npair);
+  const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
+  k_tayt_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(f, w, P.tN, U, Uff, P.p.N, P.p.L, inc0,
+                                                                           npair, P64, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -787,10 +1065,13 @@ int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, int inc0, int npai
   return check_launch();
 }
 template <typename T>
-int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb, int64_t nu) {
+int launch_tayt_epi(Plan& P, const C2<T>* F, const ffc* Fff, C2<T>* Q, T* u_out, int inc0, int npair, int64_t nb,
+                    int64_t nu) {
   const TwArgs<T> tw = tw4n_args<T>(P);
   if (nu < 0) nu = P.p.N;
-  k_tayt_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, Q, u_out, P.p.N, P.p.L, inc0, npair, nu, tw);
+  const int P64 = Fff ? taylor_p64(P.p, inc0, npair) : npair;
+  k_tayt_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, Fff, Q, u_out, P.p.N, P.p.L, inc0, npair,
+                                                                        P64, nu, tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -800,10 +1081,11 @@ int launch_tayt_epi(Plan& P, const C2<T>* F, C2<T>* Q, T* u_out, int inc0, int n
   return check_launch();
 }
 template <typename T>
-int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, float2* U32, int64_t nb) {
+int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, ffc* Uff, float2* U32,
+                    int64_t nb) {
   const double* w = use_w ? P.w : nullptr;
-  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(Y, g, w, z, U, U32, P.p.N, P.p.M, P.p.Mh,
-                                                                           band_args(P), P.row_ar, scale32(P));
+  k_l2ct_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(
+      Y, g, w, z, U, Uff, U32, P.p.N, P.p.M, P.p.Mh, P.p.M64, band_args(P), P.row_ar, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -813,11 +1095,11 @@ int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>*
   return check_launch();
 }
 template <typename T>
-int launch_l2ct_epi(Plan& P, const C2<T>* F, const float2* F32, const T* rect, T* out, int scale_s, int64_t nb) {
+int launch_l2ct_epi(Plan& P, const C2<T>* F, const ffc* Fff, const float2* F32, const T* rect, T* out, int scale_s,
+                    int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, F32, rect, out, P.p.N, P.p.M, P.p.Mh,
-                                                                        band_args(P), P.Cn, P.Hnm, scale_s, tw,
-                                                                        scale32(P));
+  k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(
+      F, Fff, F32, rect, out, P.p.N, P.p.M, P.p.Mh, P.p.M64, band_args(P), P.Cn, P.Hnm, scale_s, tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -855,29 +1137,31 @@ int launch_stage_tables_init(Plan& P) {
     count_launch();
   }
   if (P.Hnm) {
-    const int Mt = P.H32 ? P.p.M : P.p.Mh;  // FP32 tail entries only with their table
-    const int* eK = P.H32 ? P.b32exp + (P.p.K - 1) * P.p.M : nullptr;
+    // entries of the float-float and FP32 terms only with their tables
+    const int Mh = P.Hff ? P.p.Mh : P.p.M64;
+    const int Mt = P.H32 ? P.p.M : Mh;
+    const int* eK = P.b32exp ? P.b32exp + (P.p.K - 1) * P.p.M : nullptr;
     const int64_t ns_min = P.p.K > 0 ? P.p.bands[(size_t)P.p.K - 1].ns : N;
-    k_hnm_init<<<nblk(N), TPB, 0, P.stream>>>(P.Hnm, P.H32, P.Cn, N, Mt, P.p.Mh, eK, ns_min);
+    k_hnm_init<<<nblk(N), TPB, 0, P.stream>>>(P.Hnm, P.Hff, P.H32, P.Cn, N, Mt, Mh, P.p.M64, eK, ns_min);
     count_launch();
   }
   return check_launch();
 }
 
 #define INST(T)                                                                              \
-  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*, float2*, int64_t);                          \
+  template int launch_l2c_pro<T>(Plan&, const T*, C2<T>*, ffc*, float2*, int64_t);                    \
   template int launch_absmax<T>(Plan&, const T*, int64_t);                                            \
-  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const float2*, const T*, T*, int64_t);          \
+  template int launch_l2c_epi<T>(Plan&, const C2<T>*, const ffc*, const float2*, const T*, T*, int64_t); \
   template int launch_a4_pro<T>(Plan&, const T*, C2<T>*, int64_t);                                    \
   template int launch_a4_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                    \
   template int launch_fcs_pro<T>(Plan&, const T*, C2<T>*, int, int64_t);                              \
   template int launch_fcs_re_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                \
-  template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, int, int, int64_t);                         \
-  template int launch_tay_epi<T>(Plan&, const C2<T>*, const T*, T*, int, int, int64_t);                   \
-  template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, int, int, int64_t);                   \
-  template int launch_tayt_epi<T>(Plan&, const C2<T>*, C2<T>*, T*, int, int, int64_t, int64_t);                \
-  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, float2*, int64_t);  \
-  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const float2*, const T*, T*, int, int64_t);    \
+  template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, ffc*, int, int, int64_t);                   \
+  template int launch_tay_epi<T>(Plan&, const C2<T>*, const ffc*, const T*, T*, int, int, int64_t);   \
+  template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, ffc*, int, int, int64_t);             \
+  template int launch_tayt_epi<T>(Plan&, const C2<T>*, const ffc*, C2<T>*, T*, int, int, int64_t, int64_t); \
+  template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, ffc*, float2*, int64_t); \
+  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const ffc*, const float2*, const T*, T*, int, int64_t); \
   template int launch_scale<T>(Plan&, const T*, T*, int, int64_t);
 INST(double)
 INST(float)
