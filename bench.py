@@ -76,7 +76,7 @@ def src_hash(files) -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbdlt", choices=["gbdlt", "reference"])
     ap.add_argument("--n", "--length", dest="n", type=int, default=N_DEFAULT,
@@ -125,28 +125,54 @@ def job_rate(world, transforms_per_rank: float, ms_this_rank: float) -> float:
 # clocks during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling every 100 ms; only the samples taken between mark()
+    and stop() (the timed region, host clock) are kept, plus the first one after
+    it when the region is shorter than the sampling period."""
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, uuid: str | None):
         self.uuid = uuid
         self.proc = None
+        self.t0 = self.t1 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling and wait (up to 5 s) for the first sample."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def mark(self):
+        """The timed region starts now."""
+        self.t0 = time.time()
+
+    @staticmethod
+    def _when(stamp: str) -> float | None:
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp.strip(), fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self) -> dict | None:
+        """End of the timed region: stop sampling and summarise its samples."""
+        self.t1 = time.time()
         if self.proc is None:
             return None
+        time.sleep(0.15)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -156,24 +182,38 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
-            if self.uuid and self.uuid not in parts[0]:
+            if self.uuid and self.uuid not in parts[1]:
                 continue
-            rows.append(parts)
-        if not rows:
+            rows.append((self._when(parts[0]), parts[2:]))
+        t0 = self.t0 if self.t0 is not None else 0.0
+        inside = [r for t, r in rows if t is not None and t0 <= t <= self.t1]
+        if not inside:  # region shorter than the period: the first sample after it
+            after = [r for t, r in rows if t is not None and t >= t0]
+            inside = after[:1]
+        if not inside:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in inside if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[4 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside),
+                "window_ms": round((self.t1 - t0) * 1e3, 1)}
 
 
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def workload_config(N, world):
+    """The workload both arms report: one FP64 vector, legpts + DLT + IDLT."""
+    return {"workload": f"FP64 legpts + DLT + IDLT of one vector, N=2^{int(math.log2(N))}",
+            "N": N, "batch": 1, "transforms_per_step": 2,
+            "l2": "flushed between timed steps (256 MiB write outside the step events)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def peaks():
     try:
         d = json.load(open(MEASURED_PEAKS))
@@ -203,7 +243,7 @@ def run_gpu(args, world, rank, local):
         torch.cuda.synchronize()
         return p, time.perf_counter() - t0
 
-    def timed_loop(plan, x, K, W, profile):
+    def timed_loop(plan, x, K, W, profile, sampler=None):
         lib = g.lib()
         f = torch.empty_like(x)
         cb = torch.empty_like(x)
@@ -223,6 +263,8 @@ def run_gpu(args, world, rank, local):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         barrier(world)
         torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.mark()
         n0 = g.launch_count()
         for i in range(K):
             flush.fill_(float(i))
@@ -244,7 +286,7 @@ def run_gpu(args, world, rank, local):
     clk = ClockSampler(getattr(torch.cuda.get_device_properties(local), "uuid", None))
     clk.uuid = str(clk.uuid) if clk.uuid is not None else None
     clk.start()
-    ms64, launches, f64, cb64 = timed_loop(plan64, c, args.steps, args.warmup, True)
+    ms64, launches, f64, cb64 = timed_loop(plan64, c, args.steps, args.warmup, True, clk)
     clocks = clk.stop()
     prof = plan64.profile_report()
     t_step = sum(ms64) / len(ms64)
@@ -377,12 +419,9 @@ def run_gpu(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded c_n ~ N(0,1), numpy PCG64)",
-            "config": {"workload": f"FP64 legpts + DLT + IDLT of one vector, N=2^{int(math.log2(N))}",
-                       "N": N, "batch": 1, "transforms_per_step": 2,
-                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "plan": {"L": params["L"], "M": params["M"], "K": params["K"],
-                                "bands": params["bands"], "rec_steps": params["rec_steps"]}},
+            "config": workload_config(N, world),
+            "plan": {"L": params["L"], "M": params["M"], "K": params["K"],
+                     "bands": params["bands"], "rec_steps": params["rec_steps"]},
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 3), "unit": "transforms/s", "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 16 * N, "ms_per_step": round(t_e2e / args.steps, 4)},
@@ -537,8 +576,8 @@ def run_reference(args, world, rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "dd (f64 pairs)",
             "data": "synthetic (seeded c_n ~ N(0,1), numpy PCG64)",
-            "config": {"workload": f"CPU oracle legpts + DLT + IDLT of one vector, N=2^{int(math.log2(N))}",
-                       "N": N, "transforms_per_step": 2},
+            "config": workload_config(N, world),
+            "timing": "host wall clock of the CPU oracle on sampled rows, extrapolated to all N rows",
             "cpu_baseline": {"value": round(value, 8), "unit": "transforms/s", "cores": cores, "kind": "oracle",
                              "sample": f"{nrows} of {N} rows per step, extrapolated x{N / nrows:.0f}"},
             "e2e": {"value": round(value, 8), "unit": "transforms/s", "h2d_bytes_per_step": 0,
