@@ -329,28 +329,26 @@ __device__ __forceinline__ void stage(C2<T>* sm, int L, int logL, int lines, int
   __syncthreads();
 }
 
-// Global -> shared tile load, thread i taking elements i, i + 256, ...  In FP32
-// every thread first issues all of its (up to 16) loads into registers and then
-// stores them: the FP32 passes are bound by global-load latency, and this keeps
-// 16 loads in flight per thread.  FP64 passes are bound by the FP64 pipe and keep
-// the plain loop (its registers hold the radix-16 butterflies).
+// Global -> shared tile load, thread i taking elements i, i + 256, ...  Every
+// thread issues a batch of loads into registers before it stores them, so each
+// thread keeps several global loads in flight: all 16 of its elements in FP32
+// (those passes are bound by global-load latency), 8 in FP64 and float-float,
+// whose butterflies need the registers only after the load phase.
 template <typename T, typename Idx, typename Ld>
 __device__ __forceinline__ void load_tile(C2<T>* sm, int tot, Idx sidx_of, Ld ld) {
-  if constexpr (is_f32<T>) {
-    constexpr int PER = FFT_TILE / FFT_THREADS;
-    C2<T> r[PER];
+  constexpr int B = is_f32<T> ? FFT_TILE / FFT_THREADS : 8;
+  for (int i0 = 0; i0 < tot; i0 += B * FFT_THREADS) {
+    C2<T> r[B];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int i = threadIdx.x + q * FFT_THREADS;
+    for (int q = 0; q < B; ++q) {
+      const int i = i0 + threadIdx.x + q * FFT_THREADS;
       if (i < tot) r[q] = ld(i);
     }
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int i = threadIdx.x + q * FFT_THREADS;
+    for (int q = 0; q < B; ++q) {
+      const int i = i0 + threadIdx.x + q * FFT_THREADS;
       if (i < tot) sm[sidx_of(i)] = r[q];
     }
-  } else {
-    for (int i = threadIdx.x; i < tot; i += FFT_THREADS) sm[sidx_of(i)] = ld(i);
   }
 }
 
@@ -433,6 +431,7 @@ __global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
                [&](int i) { return g[(int64_t)(i >> logC) * L2 + c0 + (i & (C - 1))]; });
   __syncthreads();
   fft_tile<T, DIR>(sm, L1, logL1, C, LP, tw4096, lf);
+#pragma unroll 4
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) {
     const int k1 = i >> logC, c = i & (C - 1);
     const int64_t e = (int64_t)(c0 + c) * k1;

@@ -333,6 +333,11 @@ struct Plan {
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel
+  // side stream for FP32-pipe work (float-float and FP32 transforms) that runs
+  // beside FP64 work of the same chain; created on first use
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_broken = false;  // creation failed: everything on the plan stream
   struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
   struct GraphCache* graphs = nullptr;  // replayed transform chains (plan.cu)
 };

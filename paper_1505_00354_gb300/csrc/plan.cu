@@ -514,6 +514,12 @@ void free_plan(Plan* P) {
     cudaStreamSynchronize(P->graphs->s);
     free_graphs(P);
   }
+  if (P->side) {
+    cudaStreamSynchronize(P->side);
+    cudaStreamDestroy(P->side);
+  }
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   if (P->arena) cudaFree(P->arena);
   if (P->prof) {
     for (cudaEvent_t e : P->prof->ev) cudaEventDestroy(e);
@@ -906,11 +912,60 @@ namespace {
 // the FFT buffer that does not hold `p`
 inline void* other(Plan& P, const void* p) { return p == P.bufA ? P.bufB : P.bufA; }
 
+// A branch of a chain on the plan's side stream.  GB300 retires 2 FP64 operations
+// per SM and clock against 128 FP32 ones, and the FP64 kernels issue an
+// instruction in about one cycle of ten; the float-float and FP32 transforms of a
+// stage (independent of its FP64 transforms and recurrence, disjoint buffers)
+// therefore run on the side stream beside the FP64 work, and the stage's
+// epilogue waits for both.  Not while profiling (the per-kernel events assume one
+// stream).  Inside a capture the side stream joins the caller's graph as a branch.
+struct Side {
+  Plan& P;
+  cudaStream_t main;
+  bool on = false;
+  Side(Plan& p, bool want) : P(p), main(p.stream) {
+    if (!want || (P.prof && P.prof->on)) return;
+    if (!P.side && !P.side_broken) {
+      if (cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        P.side_broken = true;
+      }
+    }
+    if (P.side_broken || !P.side) return;
+    if (cudaEventRecord(P.ev_fork, main) != cudaSuccess || cudaStreamWaitEvent(P.side, P.ev_fork, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    on = true;
+  }
+  // launches between enter() and leave() go to the side stream
+  void enter() {
+    if (on) P.stream = P.side;
+  }
+  void leave() { P.stream = main; }
+  // the plan stream waits for the side branch
+  int join() {
+    P.stream = main;
+    if (!on) return GBDLT_OK;
+    on = false;
+    if (cudaEventRecord(P.ev_join, P.side) != cudaSuccess || cudaStreamWaitEvent(main, P.ev_join, 0) != cudaSuccess)
+      return GBDLT_ERR_CUDA;
+    return GBDLT_OK;
+  }
+  ~Side() { join(); }
+};
+
 // The band FFTs: terms m < M64 in precision T from `a` (result returned); in
 // FP64 plans terms M64 <= m < Mh in float-float from the plan's float-float band
 // buffers (result in *yff) and terms m >= Mh in FP32 from its FP32 ones (*y32).
+// The float-float and FP32 ones go to the side branch `sd` (joined by the caller).
+inline bool side_bands(const Plan& P) {
+  return P.p.K > 0 && ((P.p.Mh > P.p.M64 && P.bufAff) || (P.p.M > P.p.Mh && P.bufA32));
+}
 template <typename T>
-const C2<T>* band_ffts(Plan& P, void* a, int64_t nb, int dir, int transposed, const ffc** yff,
+const C2<T>* band_ffts(Plan& P, Side& sd, void* a, int64_t nb, int dir, int transposed, const ffc** yff,
                        const float2** y32) {
   const int Ml = P.p.M - P.p.Mh, Mf = P.p.Mh - P.p.M64;
   *y32 = nullptr;
@@ -918,10 +973,12 @@ const C2<T>* band_ffts(Plan& P, void* a, int64_t nb, int dir, int transposed, co
   const C2<T>* y = nullptr;
   if (P.p.K > 0 && P.p.M64 > 0)
     y = (const C2<T>*)launch_fft_bands<T>(P, a, other(P, a), nb, dir, transposed, P.p.M64);
+  sd.enter();
   if (P.p.K > 0 && Mf > 0 && P.bufAff)
     *yff = (const ffc*)launch_fft_bands<ffd>(P, P.bufAff, P.bufBff, nb, dir, transposed, Mf);
   if (P.p.K > 0 && Ml > 0 && P.bufA32)
     *y32 = (const float2*)launch_fft_bands<float>(P, P.bufA32, P.bufB32, nb, dir, transposed, Ml);
+  sd.leave();
   return y;
 }
 
@@ -931,17 +988,24 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   T* vrec = (T*)P.tmp;
   T* v = (T*)P.v;
-  int st = launch_rec_forward<T>(P, P.rec, c, vrec, nb);
-  if (st) return st;
+  int st = GBDLT_OK;
   const C2<T>* Y = nullptr;
   const ffc* Yff = nullptr;
   const float2* Y32 = nullptr;
-  if (KM > 0) {
-    st = launch_absmax<T>(P, c, nb);
+  {
+    if (KM > 0) {
+      st = launch_absmax<T>(P, c, nb);
+      if (st) return st;
+      st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, (ffc*)P.bufAff, (float2*)P.bufA32, nb);
+      if (st) return st;
+    }
+    // band FFTs (FP32-pipe ones on the side branch) beside the recurrence region
+    Side sd(P, KM > 0 && side_bands(P));
+    if (KM > 0) Y = band_ffts<T>(P, sd, P.bufA, nb, +1, 0, &Yff, &Y32);
+    st = launch_rec_forward<T>(P, P.rec, c, vrec, nb);
+    const int sj = sd.join();
     if (st) return st;
-    st = launch_l2c_pro<T>(P, c, (C2<T>*)P.bufA, (ffc*)P.bufAff, (float2*)P.bufA32, nb);
-    if (st) return st;
-    Y = band_ffts<T>(P, P.bufA, nb, +1, 0, &Yff, &Y32);
+    if (sj) return sj;
   }
   st = launch_l2c_epi<T>(P, Y, Yff, Y32, vrec, v, nb);
   if (st) return st;
@@ -986,8 +1050,16 @@ int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb) {
   if (st) return st;
   st = launch_tay_pro<T>(P, chat, (C2<T>*)P.bufA, Uff, inc0, npair, nb);
   if (st) return st;
-  const C2<T>* Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * P64, +1);
-  const ffc* Yff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), +1) : nullptr;
+  const C2<T>* Y = nullptr;
+  const ffc* Yff = nullptr;
+  {
+    Side sd(P, Uff != nullptr);
+    Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * P64, +1);
+    sd.enter();
+    Yff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), +1) : nullptr;
+    st = sd.join();
+    if (st) return st;
+  }
   return launch_tay_epi<T>(P, Y, Yff, v, f, inc0, npair, nb);
 }
 
@@ -1013,8 +1085,16 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   if (npair > 0) {
     st = launch_tayt_pro<T>(P, g, use_w, (C2<T>*)P.bufA, Uff, inc0, npair, nb);
     if (st) return st;
-    const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
-    const ffc* Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
+    const void* F = nullptr;
+    const ffc* Fff = nullptr;
+    {
+      Side sd(P, Uff != nullptr);
+      F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
+      sd.enter();
+      Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
+      st = sd.join();
+      if (st) return st;
+    }
     void* q = other(P, F);
     st = launch_tayt_epi<T>(P, (const C2<T>*)F, Fff, (C2<T>*)q, head > 0 ? uhead : nullptr, inc0, npair, nb,
                             head);
@@ -1025,12 +1105,17 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, (ffc*)P.bufAff,
                           (float2*)P.bufA32, nb);
   if (st) return st;
-  st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
-  if (st) return st;
   const C2<T>* F2 = nullptr;
   const ffc* Fff = nullptr;
   const float2* F32 = nullptr;
-  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &Fff, &F32);
+  {
+    Side sd(P, KM > 0 && side_bands(P));
+    if (KM > 0) F2 = band_ffts<T>(P, sd, U, nb, -1, 1, &Fff, &F32);
+    st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
+    const int sj = sd.join();
+    if (st) return st;
+    if (sj) return sj;
+  }
   st = launch_l2ct_epi<T>(P, F2, Fff, F32, rect, out, scale_s, nb);
   if (st) return st;
   return launch_head_t<T>(P, uhead, out, scale_s, nb);
@@ -1050,12 +1135,17 @@ int run_leg2cheb_t(Plan& P, const T* y, T* out, int64_t nb) {
   void* U = other(P, Y);
   st = launch_l2ct_pro<T>(P, (const C2<T>*)Y, nullptr, 0, z, (C2<T>*)U, (ffc*)P.bufAff, (float2*)P.bufA32, nb);
   if (st) return st;
-  st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
-  if (st) return st;
   const C2<T>* F2 = nullptr;
   const ffc* Fff = nullptr;
   const float2* F32 = nullptr;
-  if (KM > 0) F2 = band_ffts<T>(P, U, nb, -1, 1, &Fff, &F32);
+  {
+    Side sd(P, KM > 0 && side_bands(P));
+    if (KM > 0) F2 = band_ffts<T>(P, sd, U, nb, -1, 1, &Fff, &F32);
+    st = launch_rec_transpose<T>(P, P.rec, z, rect, nb);
+    const int sj = sd.join();
+    if (st) return st;
+    if (sj) return sj;
+  }
   st = launch_l2ct_epi<T>(P, F2, Fff, F32, rect, out, 0, nb);
   if (st) return st;
   return launch_head_t<T>(P, y, out, 0, nb);
@@ -1071,8 +1161,16 @@ int run_chebeval_t(Plan& P, const T* g, T* out, int64_t nb) {
   if (st) return st;
   st = launch_tayt_pro<T>(P, g, 0, (C2<T>*)P.bufA, Uff, 1, npair, nb);
   if (st) return st;
-  const void* F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
-  const ffc* Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
+  const void* F = nullptr;
+  const ffc* Fff = nullptr;
+  {
+    Side sd(P, Uff != nullptr);
+    F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
+    sd.enter();
+    Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
+    st = sd.join();
+    if (st) return st;
+  }
   return launch_tayt_epi<T>(P, (const C2<T>*)F, Fff, nullptr, out, 1, npair, nb);
 }
 

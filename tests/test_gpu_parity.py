@@ -399,6 +399,37 @@ def test_max_n(gb):
         gb.Plan(2 * N)
 
 
+@pytest.mark.parametrize("N", [1024, 1 << 16, 1 << 20])
+def test_side_branch_bitwise(gb, N):
+    """FP64 plans run their float-float and FP32 transforms on a side stream beside
+    the FP64 work of the same stage.  The results are bitwise those of the serial
+    order (while the per-kernel profiler is on, every launch stays on one stream),
+    for every operator, on the first (direct) call, the capturing call and graph
+    replays, on the default stream and on a non-default one."""
+    x = dev(_c(N, 91))
+    ops = ["leg2cheb", "leg2cheb_t", "chebeval", "chebeval_t", "dlt", "dlt_t", "idlt", "idlt_t"]
+    p = gb.Plan(N, method=gb.METHOD_FAST)
+    p.profile(1)
+    ref = {op: getattr(p, op)(x).clone() for op in ops}
+    p.profile(0)
+    torch.cuda.synchronize()
+    for op in ops:
+        y = torch.empty_like(x)
+        for _ in range(4):
+            getattr(p, op)(x, out=y)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref[op]), op
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        q = gb.Plan(N, method=gb.METHOD_FAST, stream=s)
+        for op in ("dlt", "idlt"):
+            y = torch.empty_like(x)
+            for _ in range(3):
+                getattr(q, op)(x, out=y)
+            s.synchronize()
+            assert torch.equal(y, ref[op]), op
+
+
 def test_graph_replay(gb):
     """Repeated calls with the same pointers replay a captured chain: results are
     bitwise those of the direct run, on the default stream and on a side stream,
