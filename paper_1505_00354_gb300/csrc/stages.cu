@@ -94,10 +94,58 @@ __device__ __forceinline__ double pow2i(int e) {
   e = max(-1022, min(1023, e));
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
-// float-float from double (hi = fl(v), lo = fl(v - hi)) and back
+// Conversions between double and float built from the bit patterns.  On GB300 a
+// double <-> float conversion instruction issues on the FP64 pipe (measured 595
+// G/s, the DFMA rate, against 11 T/s for int -> float), and the stage kernels of
+// FP64 plans convert at every boundary between their FP64 and FP32-pipe tiers, so
+// they assemble the IEEE 754 fields with integer operations instead.  Values are
+// scaled to magnitudes near 1 by exact powers of two before they are converted;
+// floats below the normal range (2^-126) are flushed to zero.
+
+// v 2^e by exponent-field arithmetic (exact); zero stays zero, results below the
+// double normal range flush to zero (|v 2^e| < 2^1024 is the caller's)
+__device__ __forceinline__ double scale2(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0 || E + e <= 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
+  return __longlong_as_double(b + ((long long)e << 52));
+}
+// float nearest to v (ties away from zero); |v| >= 2^128 gives infinity
+__device__ __forceinline__ float f32_of(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long a = b & 0x7fffffffffffffffull;
+  const unsigned int sg = (unsigned int)(b >> 32) & 0x80000000u;
+  if (a < (897ull << 52)) return __uint_as_float(sg);
+  if (a >= (1151ull << 52)) return __uint_as_float(sg | 0x7f800000u);
+  return __uint_as_float(sg | (unsigned int)(((a + (1ull << 28)) >> 29) - (896ull << 23)));
+}
+// double of a float (exact; subnormal floats give zero)
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned long long a = u & 0x7fffffffu;
+  const unsigned long long sg = (unsigned long long)(u & 0x80000000u) << 32;
+  if (a < 0x00800000ull) return __longlong_as_double((long long)sg);
+  return __longlong_as_double((long long)(sg | ((a + (896ull << 23)) << 29)));
+}
+// float-float pair of a double: hi = v rounded to float, lo = v - hi (an integer
+// of at most 29 bits in units of 2^(E-1075), E the biased exponent of v) rounded
+// to float; the pair carries v to 2^-48 relative
 __device__ __forceinline__ ffd ffd_of(double v) {
-  const float h = __double2float_rn(v);
-  return ffd(h, __double2float_rn(v - (double)h));
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long a = b & 0x7fffffffffffffffull;
+  const unsigned int sg = (unsigned int)(b >> 32) & 0x80000000u;
+  if (a < (897ull << 52)) return ffd(0.f, 0.f);
+  if (a >= (1151ull << 52)) return ffd(__uint_as_float(sg | 0x7f800000u), 0.f);
+  const unsigned long long up = (a >> 28) & 1ull;
+  const unsigned int hb = (unsigned int)((a >> 29) + up - (896ull << 23));
+  const int rem = (int)(a & ((1ull << 29) - 1ull)) - (int)(up << 29);  // |rem| <= 2^28
+  const int E = (int)(a >> 52);  // 897 <= E <= 1150 here
+  // rem 2^(E-1075); below E = 949 that power is not a normal float, so it is
+  // applied as 2^(E-1011) 2^-64
+  const bool big = E >= 949;
+  const float sc = __uint_as_float((unsigned int)(big ? E - 948 : E - 884) << 23);
+  const float lo = __int2float_rn(rem) * sc * (big ? 1.f : 0x1p-64f);
+  return ffd(__uint_as_float(sg | hb), sg ? -lo : lo);
 }
 __device__ __forceinline__ ffc ffc_of(double x, double y) {
   ffc r;
@@ -105,7 +153,8 @@ __device__ __forceinline__ ffc ffc_of(double x, double y) {
   r.y = ffd_of(y);
   return r;
 }
-__device__ __forceinline__ double dbl_of(ffd a) { return (double)a.hi + (double)a.lo; }
+// hi + lo in double: one FP64 addition
+__device__ __forceinline__ double dbl_of(ffd a) { return f64_of(a.hi) + f64_of(a.lo); }
 
 // 2^e as a float (e clamped to the normal range)
 __device__ __forceinline__ float pow2f(int e) {
@@ -196,10 +245,9 @@ __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, ffc* _
   if (Mf > 0) {
     // float-float terms: Hff = C_n h_{m,n} 2^{e_{K-1,m}} times c_n e_n 2^{-E} in
     // float-float, then the band's exact 2^{e_{s,m} - e_{K-1,m}}
-    const double sE = pow2i(-E);
-    const ffc cf = ffc_of((double)ce.x * sE, (double)ce.y * sE);
+    const ffc cf = ffc_of(scale2((double)ce.x, -E), scale2((double)ce.y, -E));
     const int* eK = S.e + (B.K - 1) * M;
-    const ffc zz = ffc_of(0.0, 0.0);
+    const ffc zz = {ffd(0.f, 0.f), ffd(0.f, 0.f)};
     for (int m = M64; m < Mh; ++m) {
       const ffd h = S.Hff[(int64_t)(m - M64) * N + n];
       const ffd vx = h * cf.x, vy = h * cf.y;
@@ -215,8 +263,7 @@ __global__ void k_l2c_pro(const T* __restrict__ c, C2<T>* __restrict__ U, ffc* _
   if (Ml > 0) {
     // FP32 terms: C_n h_{m,n} 2^{e_{s,m}} c_n e_n 2^{-E} from the float table
     // H32 = C_n h_{m,n} 2^{e_{K-1,m}} times the band's exact 2^{e_{s,m} - e_{K-1,m}}
-    const double sE = pow2i(-E);
-    const float2 cf = make_float2((float)((double)ce.x * sE), (float)((double)ce.y * sE));
+    const float2 cf = make_float2(f32_of(scale2((double)ce.x, -E)), f32_of(scale2((double)ce.y, -E)));
     const int* eK = S.e + (B.K - 1) * M;
     for (int m = Mh; m < M; ++m) {
       const float h32 = S.H32[(int64_t)(m - Mh) * N + n];
@@ -318,8 +365,7 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
       // float-float terms: with the band's FFT output scaled by 2^{e_{s,m} - E},
       // term m adds 2^E Re(b_m z_m); b advances by rho 2^{e_{s,m} - e_{s,m+1}}
       const int* e = S.e + s * M;
-      const double b0 = pow2i(-e[M64]);
-      bff = ffc_of((double)al.x * b0, (double)al.y * b0);
+      bff = ffc_of(scale2((double)al.x, -e[M64]), scale2((double)al.y, -e[M64]));
       const ffc r = ffc_of((double)rho.x, (double)rho.y);
       ffd aff(0.f, 0.f);
       for (int m = M64; m < Mh; ++m) {
@@ -334,7 +380,7 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
           bff = cmul<ffd>(bff, rp);
         }
       }
-      acc += (T)(dbl_of(aff) * pow2i(item_exp(S, bt)));
+      acc += (T)scale2(dbl_of(aff), item_exp(S, bt));
     }
     if (Ml > 0) {
       // FP32 terms: with the band's FFT output scaled by 2^{e_{s,m} - E}, term m
@@ -345,10 +391,9 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
       if (Mf > 0) {
         b = make_float2(bff.x.hi, bff.y.hi);
       } else {
-        const double b0 = pow2i(-e[Mh]);
-        b = make_float2((float)((double)al.x * b0), (float)((double)al.y * b0));
+        b = make_float2(f32_of(scale2((double)al.x, -e[Mh])), f32_of(scale2((double)al.y, -e[Mh])));
       }
-      const float2 r = make_float2((float)rho.x, (float)rho.y);
+      const float2 r = make_float2(f32_of((double)rho.x), f32_of((double)rho.y));
       const float2* y32 = Y32 + (int64_t)s * Ml * N + idx;
       float a32 = 0.f;
       for (int m = Mh; m < M; ++m) {
@@ -360,7 +405,7 @@ __global__ void k_l2c_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
           b = cmulf(b, make_float2(r.x * p, r.y * p));
         }
       }
-      acc += (T)((double)a32 * pow2i(item_exp(S, bt)));
+      acc += (T)scale2(f64_of(a32), item_exp(S, bt));
     }
   }
   v[k] = acc;
@@ -464,11 +509,11 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, ffc
   if (P64 < npair) {
     // float-float pairs: the same sums, continued from the powers reached above
     // (r = n/N and rN are exact floats, so r^2 and rN^2 are exact float-float)
-    const double sE = pow2i(-item_exp(S, bt));
-    const ffc e1 = ffc_of((double)E1.x * sE, (double)E1.y * sE);
-    const ffc e2 = ffc_of((double)E2.x * sE, (double)E2.y * sE);
-    const ffd c0 = ffd_of((double)cn * sE);
-    const ffd fr((float)r, 0.f), frN((float)rN, 0.f);
+    const int E = item_exp(S, bt);
+    const ffc e1 = ffc_of(scale2((double)E1.x, -E), scale2((double)E1.y, -E));
+    const ffc e2 = ffc_of(scale2((double)E2.x, -E), scale2((double)E2.y, -E));
+    const ffd c0 = ffd_of(scale2((double)cn, -E));
+    const ffd fr(f32_of((double)r), 0.f), frN(f32_of((double)rN), 0.f);
     const ffd fr2 = fr * fr, frN2 = frN * frN;
     ffd fa = ffd_of((double)pa), faN = ffd_of((double)paN), fb = ffd_of((double)pb), fbN = ffd_of((double)pbN);
     const ffd z(0.f, 0.f);
@@ -535,7 +580,7 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
     // float-float pairs, continued from q reached above; outputs scaled by 2^{-E}
     const ffd ft = ffd_of((double)t);
     ffd fqa = ffd_of((double)qa), fqb = ffd_of((double)qb), aff(0.f, 0.f);
-    const float fsk = (float)sk;
+    const float fsk = odd ? -0.5f : 0.5f;
     for (int p = P64; p < npair; ++p) {
       const int la = 2 * p + (inc0 ? 0 : 2);
       const int lb = 2 * p + 1;
@@ -550,7 +595,7 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
         fqa = fqb * ft * kInvIntFF[la + 2];
       }
     }
-    acc += (T)(dbl_of(aff) * pow2i(item_exp(S, bt)));
+    acc += (T)scale2(dbl_of(aff), item_exp(S, bt));
   }
   f[k] = acc;
 }
@@ -591,8 +636,8 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
   }
   if (P64 < npair) {
     // float-float pairs, continued from the powers reached above, scaled by 2^{-E}
-    const double sE = pow2i(-item_exp(S, bt));
-    const ffd fg0 = ffd_of((double)g0 * sE), fg1 = ffd_of((double)g1 * sE);
+    const int E = item_exp(S, bt);
+    const ffd fg0 = ffd_of(scale2((double)g0, -E)), fg1 = ffd_of(scale2((double)g1, -E));
     const ffd ft0 = ffd_of((double)t0), ft1 = ffd_of((double)t1);
     const ffd ft02 = ft0 * ft0, ft12 = ft1 * ft1;
     ffd fa0 = ffd_of((double)pa0), fa1 = ffd_of((double)pa1), fb0 = ffd_of((double)pb0), fb1 = ffd_of((double)pb1);
@@ -661,7 +706,7 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
   }
   if (P64 < npair) {
     // float-float pairs (outputs scaled by 2^{-E}), continued from q reached above
-    const ffd fr((float)r, 0.f);  // n/N: exact
+    const ffd fr(f32_of((double)r), 0.f);  // n/N: exact
     ffd fqa = ffd_of((double)qa), fqb = ffd_of((double)qb);
     ffd ax(0.f, 0.f), ay(0.f, 0.f);
     for (int p = P64; p < npair; ++p) {
@@ -682,9 +727,9 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
         fqa = fqb * fr * kInvIntFF[la + 2];
       }
     }
-    const double sE = pow2i(item_exp(S, bt));
-    Ax += (T)(dbl_of(ax) * sE);
-    Ay += (T)(dbl_of(ay) * sE);
+    const int E = item_exp(S, bt);
+    Ax += (T)scale2(dbl_of(ax), E);
+    Ay += (T)scale2(dbl_of(ay), E);
   }
   const T acc = e.x * Ax + e.y * Ay;
   if (Q) {
@@ -754,24 +799,22 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
   // beta 2^{g_{s,m} - E} = (z 2^{-E}) gamma_m with gamma_m = alpha rho^m 2^{g_{s,m}},
   // advanced by rho 2^{g_{s,m+1} - g_{s,m}} (float-float, then FP32)
   if (Mf > 0 || Ml > 0) {
-    const double sE = pow2i(-item_exp(S, bt));
+    const int E = item_exp(S, bt);
     const int* g0 = S.e + B.K * M + max(s0, 0) * M;
     const int* g1 = S.e + B.K * M + max(s1, 0) * M;
-    ffc c0ff = ffc_of(0.0, 0.0), c1ff = c0ff;
+    const ffc zz = {ffd(0.f, 0.f), ffd(0.f, 0.f)};
+    ffc c0ff = zz, c1ff = zz;
     if (Mf > 0) {
-      const ffd f0 = ffd_of((double)z0 * sE), f1 = ffd_of((double)z1 * sE);
-      ffc r0 = c0ff, r1 = c0ff;
+      const ffd f0 = ffd_of(scale2((double)z0, -E)), f1 = ffd_of(scale2((double)z1, -E));
+      ffc r0 = zz, r1 = zz;
       if (s0 >= 0) {
-        const double q = pow2i(g0[M64]);
-        c0ff = ffc_of((double)al0.x * q, (double)al0.y * q);
+        c0ff = ffc_of(scale2((double)al0.x, g0[M64]), scale2((double)al0.y, g0[M64]));
         r0 = ffc_of((double)rho0.x, (double)rho0.y);
       }
       if (s1 >= 0) {
-        const double q = pow2i(g1[M64]);
-        c1ff = ffc_of((double)al1.x * q, (double)al1.y * q);
+        c1ff = ffc_of(scale2((double)al1.x, g1[M64]), scale2((double)al1.y, g1[M64]));
         r1 = ffc_of((double)rho1.x, (double)rho1.y);
       }
-      const ffc zz = ffc_of(0.0, 0.0);
       for (int m = M64; m < Mh; ++m) {
         ffc w0, w1;
         w0.x = f0 * c0ff.x;
@@ -796,25 +839,23 @@ __global__ void k_l2ct_pro(const C2<T>* __restrict__ Y, const T* __restrict__ g,
       }
     }
     if (Ml > 0) {
-      const float f0 = (float)((double)z0 * sE), f1 = (float)((double)z1 * sE);
+      const float f0 = f32_of(scale2((double)z0, -E)), f1 = f32_of(scale2((double)z1, -E));
       float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f), r0 = c0, r1 = c0;
       if (s0 >= 0) {
         if (Mf > 0) {
           c0 = make_float2(c0ff.x.hi, c0ff.y.hi);
         } else {
-          const double q = pow2i(g0[Mh]);
-          c0 = make_float2((float)((double)al0.x * q), (float)((double)al0.y * q));
+          c0 = make_float2(f32_of(scale2((double)al0.x, g0[Mh])), f32_of(scale2((double)al0.y, g0[Mh])));
         }
-        r0 = make_float2((float)rho0.x, (float)rho0.y);
+        r0 = make_float2(f32_of((double)rho0.x), f32_of((double)rho0.y));
       }
       if (s1 >= 0) {
         if (Mf > 0) {
           c1 = make_float2(c1ff.x.hi, c1ff.y.hi);
         } else {
-          const double q = pow2i(g1[Mh]);
-          c1 = make_float2((float)((double)al1.x * q), (float)((double)al1.y * q));
+          c1 = make_float2(f32_of(scale2((double)al1.x, g1[Mh])), f32_of(scale2((double)al1.y, g1[Mh])));
         }
-        r1 = make_float2((float)rho1.x, (float)rho1.y);
+        r1 = make_float2(f32_of((double)rho1.x), f32_of((double)rho1.y));
       }
       for (int m = Mh; m < M; ++m) {
         const float2 w0 = make_float2(f0 * c0.x, f0 * c0.y);
@@ -887,8 +928,8 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
           vx = vx + h * xx;
           vy = vy + h * xy;
         }
-        const double sE = pow2i(item_exp(S, bt));
-        V = mk<T>(V.x + (T)(dbl_of(vx) * sE), V.y + (T)(dbl_of(vy) * sE));
+        const int E = item_exp(S, bt);
+        V = mk<T>(V.x + (T)scale2(dbl_of(vx), E), V.y + (T)scale2(dbl_of(vy), E));
       }
       if (Ml > 0) {
         // FP32 terms: band s's output is scaled by 2^{g_{s,m} - E}; with
@@ -908,8 +949,8 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
           vx = fmaf(h32, xx, vx);
           vy = fmaf(h32, xy, vy);
         }
-        const double sE = pow2i(item_exp(S, bt));
-        V = mk<T>(V.x + (T)((double)vx * sE), V.y + (T)((double)vy * sE));
+        const int E = item_exp(S, bt);
+        V = mk<T>(V.x + (T)scale2(f64_of(vx), E), V.y + (T)scale2(f64_of(vy), E));
       }
       const C2<T> e = twid<T>(tw4N, n);
       acc += e.x * V.x - e.y * V.y;
