@@ -155,6 +155,16 @@ __device__ __forceinline__ ffc ffc_of(double x, double y) {
 }
 // hi + lo in double: one FP64 addition
 __device__ __forceinline__ double dbl_of(ffd a) { return f64_of(a.hi) + f64_of(a.lo); }
+// an index 0 <= n <= 2^24 (every N of a plan) in precision T; exact, and for
+// double without the FP64-pipe conversion instruction
+template <typename T>
+__device__ __forceinline__ T idx_t(int64_t n) {
+  if constexpr (is_f64<T>) {
+    return f64_of(__int2float_rn((int)n));
+  } else {
+    return (T)n;
+  }
+}
 
 // 2^e as a float (e clamped to the normal range)
 __device__ __forceinline__ float pow2f(int e) {
@@ -176,6 +186,17 @@ __constant__ double kInvInt[48] = {
     1.0 / 20,   1.0 / 21,   1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29,
     1.0 / 30,   1.0 / 31,   1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
     1.0 / 40,   1.0 / 41,   1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47};
+
+// 1/((l+1)(l+2)): q_{l+2} = q_l t^2 / ((l+1)(l+2)) in one product per term
+#define GB_INVP(l) 1.0 / (((l) + 1.0) * ((l) + 2.0))
+__constant__ double kInvPair[46] = {
+    GB_INVP(0),  GB_INVP(1),  GB_INVP(2),  GB_INVP(3),  GB_INVP(4),  GB_INVP(5),  GB_INVP(6),  GB_INVP(7),
+    GB_INVP(8),  GB_INVP(9),  GB_INVP(10), GB_INVP(11), GB_INVP(12), GB_INVP(13), GB_INVP(14), GB_INVP(15),
+    GB_INVP(16), GB_INVP(17), GB_INVP(18), GB_INVP(19), GB_INVP(20), GB_INVP(21), GB_INVP(22), GB_INVP(23),
+    GB_INVP(24), GB_INVP(25), GB_INVP(26), GB_INVP(27), GB_INVP(28), GB_INVP(29), GB_INVP(30), GB_INVP(31),
+    GB_INVP(32), GB_INVP(33), GB_INVP(34), GB_INVP(35), GB_INVP(36), GB_INVP(37), GB_INVP(38), GB_INVP(39),
+    GB_INVP(40), GB_INVP(41), GB_INVP(42), GB_INVP(43), GB_INVP(44), GB_INVP(45)};
+#undef GB_INVP
 
 // the same 1/l as float-float pairs (the float-float Taylor pairs)
 #define GB_FFINV(l) ffd(1.0 / (l))
@@ -423,7 +444,7 @@ __global__ void k_a4_pro(const T* __restrict__ v, C2<T>* __restrict__ U, int64_t
 }
 
 template <typename T>
-__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, TwArgs<T> tw4N) {
+__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, T invN, TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   F += (int64_t)blockIdx.y * N;
@@ -433,19 +454,19 @@ __global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int6
   const C2<T> Vh = mk<T>((Fn.x + Fm.x) * (T)0.5, (Fn.y - Fm.y) * (T)0.5);
   const C2<T> e = twid<T>(tw4N, n);  // conj(e) = e^{-i pi n/(2N)}
   const T U = e.x * Vh.x + e.y * Vh.y;
-  chat[n] = (n == 0 ? (T)1 / (T)N : (T)2 / (T)N) * U;
+  chat[n] = (n == 0 ? invN : (T)2 * invN) * U;
 }
 
 // ---------------------------------------------------------------- FCS helpers
 template <typename T>
-__global__ void k_fcs_pro(const T* __restrict__ a, C2<T>* __restrict__ U, int64_t N, int scale_d,
+__global__ void k_fcs_pro(const T* __restrict__ a, C2<T>* __restrict__ U, int64_t N, int scale_d, T invN,
                           TwArgs<T> tw4N) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   a += (int64_t)blockIdx.y * N;
   U += (int64_t)blockIdx.y * N;
   T an = a[n];
-  if (scale_d) an *= (n == 0 ? (T)1 : (T)2) / (T)N;
+  if (scale_d) an *= n == 0 ? invN : (T)2 * invN;
   const C2<T> e = twid<T>(tw4N, n);
   U[n] = mk<T>(an * e.x, an * e.y);
 }
@@ -467,16 +488,15 @@ __global__ void k_fcs_re_epi(const C2<T>* __restrict__ Y, T* __restrict__ out, i
 // ([item][npair - P64][N], float-float, scaled by 2^{-E})
 template <typename T>
 __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, ffc* __restrict__ Uff, int64_t N,
-                          int L, int inc0, int npair, int P64, TwArgs<T> tw4N, Scale32 S) {
+                          int L, int inc0, int npair, int P64, T invN, TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
   chat += bt * N;
   U += bt * P64 * N;
   if (Uff) Uff += bt * (npair - P64) * N;
-  const T invN = (T)1 / (T)N;  // exact: N is a power of two
-  const T r = (T)n * invN;
-  const T rN = (T)(N - n) * invN;
+  const T r = idx_t<T>(n) * invN;  // exact: N is a power of two
+  const T rN = idx_t<T>(N - n) * invN;
   const T cn = chat[n];
   const T cm = n > 0 ? chat[N - n] : (T)0;
   const C2<T> e = twid<T>(tw4N, n);
@@ -554,28 +574,30 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
   const T t = (T)tN[k];
   const bool odd = k & 1;
   const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
-  const T sk = odd ? (T)-0.5 : (T)0.5;
-  T acc = inc0 ? (T)0 : v[k];
+  T acc2 = (T)0;  // twice the sum of the pairs in the plan's precision
   // q_l = t^l / l! advanced term by term: pair p uses l_b = 2p+1 and l_a = 2p (inc0)
   // or 2p+2, so l runs upwards through both parts
   T qa = (T)1;                        // q_{l_a} (inc0: q_0)
   T qb = t;                           // q_{l_b} = q_1
+  const T t2 = t * t;
   if (!inc0) qa = qb * t * (T)kInvInt[2];
   for (int p = 0; p < P64; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const C2<T> y = Y[(int64_t)p * N + idx];
-    if (la <= L - 1) acc += (T)sgn_even(la) * (T)0.5 * qa * y.x;
-    if (lb <= L - 1) acc += (T)sgn_odd(lb) * sk * qb * y.y;
+    if (la <= L - 1) acc2 = fma(sgn_even(la) > 0 ? qa : -qa, y.x, acc2);
+    if (lb <= L - 1) acc2 = fma((sgn_odd(lb) > 0) != odd ? qb : -qb, y.y, acc2);
     // next pair: l_b + 2 and l_a + 2
     if (inc0) {
-      qb = qb * t * (T)kInvInt[lb + 1] * t * (T)kInvInt[lb + 2];
-      qa = qa * t * (T)kInvInt[la + 1] * t * (T)kInvInt[la + 2];
+      qb = qb * (t2 * (T)kInvPair[lb]);
+      qa = qa * (t2 * (T)kInvPair[la]);
     } else {
       qb = qa * t * (T)kInvInt[la + 1];
       qa = qb * t * (T)kInvInt[la + 2];
     }
   }
+  T acc = inc0 ? (T)0 : v[k];
+  acc = fma((T)0.5, acc2, acc);
   if (P64 < npair) {
     // float-float pairs, continued from q reached above; outputs scaled by 2^{-E}
     const ffd ft = ffd_of((double)t);
@@ -666,7 +688,7 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
 // first nu coefficients of u, for the dense head block).
 template <typename T>
 __global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ Fff, C2<T>* __restrict__ Q,
-                           T* __restrict__ uout, int64_t N, int L, int inc0, int npair, int P64, int64_t nu,
+                           T* __restrict__ uout, int64_t N, int L, int inc0, int npair, int P64, int64_t nu, T invN,
                            TwArgs<T> tw4N, Scale32 S) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
@@ -675,7 +697,7 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
   if (Fff) Fff += bt * (npair - P64) * N;
   if (Q) Q += bt * N;
   if (uout) uout += bt * N;
-  const T r = (T)n * ((T)1 / (T)N);  // exact: N is a power of two
+  const T r = idx_t<T>(n) * invN;  // exact: N is a power of two
   const C2<T> e = twid<T>(tw4N, n);
   const int64_t nm = (N - n) & (N - 1);
   // with U_n = Re[conj(e) (Fn + conj Fm)]/2 (DCT-II part) and
@@ -685,25 +707,30 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
   // ca = sgn_a q_a / 2, cb = sgn_b q_b / 2
   T Ax = (T)0, Ay = (T)0;
   T qa = (T)1, qb = r;  // r^l / l! for l_a (inc0: 0) and l_b = 1
+  const T r2 = r * r;
   if (!inc0) qa = qb * r * (T)kInvInt[2];
   for (int p = 0; p < P64; ++p) {
     const int la = 2 * p + (inc0 ? 0 : 2);
     const int lb = 2 * p + 1;
     const C2<T> Fn = F[(int64_t)p * N + n];
     const C2<T> Fm = F[(int64_t)p * N + nm];
-    const T ha = la <= L - 1 ? (sgn_even(la) > 0 ? (T)0.5 : (T)-0.5) : (T)0;
-    const T hb = (lb <= L - 1 && n > 0) ? (sgn_odd(lb) > 0 ? (T)0.5 : (T)-0.5) : (T)0;
-    const T ca = ha * qa, cb = hb * qb;
-    Ax += ca * (Fn.x + Fm.x) - cb * (Fm.x - Fn.x);
-    Ay += ca * (Fn.y - Fm.y) + cb * (Fm.y + Fn.y);
+    // 2 ca and 2 cb (the halving is applied once, after the loop); then
+    // Ax += (ca + cb) Fn.x + (ca - cb) Fm.x,  Ay += (ca + cb) Fn.y - (ca - cb) Fm.y
+    const T ca2 = la <= L - 1 ? (sgn_even(la) > 0 ? qa : -qa) : (T)0;
+    const T cb2 = (lb <= L - 1 && n > 0) ? (sgn_odd(lb) > 0 ? qb : -qb) : (T)0;
+    const T al = ca2 + cb2, be = ca2 - cb2;
+    Ax = fma(al, Fn.x, fma(be, Fm.x, Ax));
+    Ay = fma(al, Fn.y, fma(-be, Fm.y, Ay));
     if (inc0) {
-      qb = qb * r * (T)kInvInt[lb + 1] * r * (T)kInvInt[lb + 2];
-      qa = qa * r * (T)kInvInt[la + 1] * r * (T)kInvInt[la + 2];
+      qb = qb * (r2 * (T)kInvPair[lb]);
+      qa = qa * (r2 * (T)kInvPair[la]);
     } else {
       qb = qa * r * (T)kInvInt[la + 1];
       qa = qb * r * (T)kInvInt[la + 2];
     }
   }
+  Ax *= (T)0.5;
+  Ay *= (T)0.5;
   if (P64 < npair) {
     // float-float pairs (outputs scaled by 2^{-E}), continued from q reached above
     const ffd fr(f32_of((double)r), 0.f);  // n/N: exact
@@ -733,7 +760,7 @@ __global__ void k_tayt_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
   }
   const T acc = e.x * Ax + e.y * Ay;
   if (Q) {
-    const T d = (n == 0 ? (T)1 : (T)2) / (T)N;
+    const T d = n == 0 ? invN : (T)2 * invN;
     const T a = d * acc;
     Q[n] = mk<T>(a * e.x, a * e.y);
   }
@@ -956,7 +983,7 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
       acc += e.x * V.x - e.y * V.y;
     }
   }
-  out[n] = scale_s ? ((T)n + (T)0.5) * acc : acc;
+  out[n] = scale_s ? (idx_t<T>(n) + (T)0.5) * acc : acc;
 }
 
 // which: 0 copy, 1 multiply by (n + 1/2), 2 multiply by w_k, 3 dtheta = tN / N (double out)
@@ -968,7 +995,7 @@ __global__ void k_scale(const T* __restrict__ in, T* __restrict__ out, const dou
   in += (int64_t)blockIdx.y * N;
   out += (int64_t)blockIdx.y * N;
   T v = in[n];
-  if (which == 1) v *= ((T)n + (T)0.5);
+  if (which == 1) v *= (idx_t<T>(n) + (T)0.5);
   if (which == 2) v *= (T)w[n];
   out[n] = v;
 }
@@ -1032,7 +1059,7 @@ int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb) {
 template <typename T>
 int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_a4_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, chat, P.p.N, tw);
+  k_a4_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, chat, P.p.N, (T)1 / (T)P.p.N, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -1044,7 +1071,7 @@ int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb) {
 template <typename T>
 int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d, int64_t nb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_fcs_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, tw);
+  k_fcs_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(a, U, P.p.N, scale_d, (T)1 / (T)P.p.N, tw);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -1069,7 +1096,7 @@ int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, ffc* Uff, int inc0, int npa
   const TwArgs<T> tw = tw4n_args<T>(P);
   const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
   k_tay_pro<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(chat, U, Uff, P.p.N, P.p.L, inc0, npair, P64,
-                                                                       tw, scale32(P));
+                                                                       (T)1 / (T)P.p.N, tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -1112,7 +1139,7 @@ int launch_tayt_epi(Plan& P, const C2<T>* F, const ffc* Fff, C2<T>* Q, T* u_out,
   if (nu < 0) nu = P.p.N;
   const int P64 = Fff ? taylor_p64(P.p, inc0, npair) : npair;
   k_tayt_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, Fff, Q, u_out, P.p.N, P.p.L, inc0, npair,
-                                                                        P64, nu, tw, scale32(P));
+                                                                        P64, nu, (T)1 / (T)P.p.N, tw, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
