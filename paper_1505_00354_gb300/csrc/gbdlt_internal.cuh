@@ -232,6 +232,8 @@ constexpr int64_t kDirectMax = 1 << 16;
 constexpr int64_t kDirectAuto = 256;
 // largest dense head block a fast plan uses (h^2/4 terms per transform)
 constexpr int64_t kHeadMax = 1 << 16;
+// largest head block whose products an FP64 plan stores (h^2/4 doubles: 2.1 GB)
+constexpr int64_t kHeadTabMax = 1 << 15;
 
 // Fills Params from (N, prec, eps, method): Taylor terms, asymptotic terms, bands
 // and the method the plan runs.
@@ -301,6 +303,10 @@ struct Plan {
   // dense head block: Lam'_j = sqrt(2/pi) Gamma(j+1/2)/Gamma(j+1), j < head
   double* head_lam = nullptr;
   float* head_lamf = nullptr;
+  // FP64 plans with head <= kHeadTabMax: the products M_{k,n} of the head block,
+  // row k (n = k, k+2, ..., < head) from offset head_off[k] (head.cu)
+  double* head_tab = nullptr;
+  int64_t* head_off = nullptr;
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
   RecLayout rec;    // recurrence region of the fast path (cheb1 rows)
   RecLayout drec;   // every row and column at the Legendre nodes (direct method)
@@ -466,5 +472,7 @@ template <typename T>
 int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb);
 template <typename T>
 int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb);
+// fills P.head_tab from P.head_lam (plan creation)
+int launch_head_tab_init(Plan& P);
 
 }  // namespace gbdlt

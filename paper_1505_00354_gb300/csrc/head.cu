@@ -100,13 +100,117 @@ __global__ void __launch_bounds__(HW * 32) k_head_t(const T* __restrict__ y, T* 
   }
 }
 
+// ---------------------------------------------------------------- stored products
+// FP64 plans with h <= kHeadTabMax keep the products M_{k,n} = Lam'_j Lam'_{j+k}
+// (n = k + 2j) in a table, row k holding n = k, k+2, ..., < h from offset off[k]
+// (h^2/4 doubles: 537 MB at h = 16384).  Each term then costs one FP64 fused
+// multiply-add and 8 bytes of HBM instead of a product and a fused multiply-add:
+// the block moves from the FP64 pipe towards the HBM roofline.  The stored
+// product is the rounded product the on-the-fly kernel forms, so the forward
+// block is bitwise the same.
+__global__ void k_head_tab_init(const double* __restrict__ lam, const int64_t* __restrict__ off,
+                                double* __restrict__ tab, int64_t h) {
+  const int64_t k = blockIdx.x;
+  const int64_t J = (h - k + 1) / 2;
+  double* row = tab + off[k];
+  for (int64_t j = threadIdx.x; j < J; j += blockDim.x) row[j] = lam[j] * lam[k + j];
+}
+
+// forward: one warp per output k, lanes over j (the on-the-fly kernel's order)
+__global__ void __launch_bounds__(HW * 32) k_head_fwd_tab(const double* __restrict__ c, double* __restrict__ chat,
+                                                          const double* __restrict__ tab,
+                                                          const int64_t* __restrict__ off, int64_t N, int64_t h) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * HW + (threadIdx.x >> 5);
+  if (k >= h) return;  // whole warp
+  c += (int64_t)blockIdx.y * N;
+  chat += (int64_t)blockIdx.y * N;
+  const int64_t J = (h - k + 1) / 2;
+  const double* __restrict__ row = tab + off[k];
+  const double* __restrict__ x = c + k;
+  double a0 = 0.0, a1 = 0.0;
+  int64_t j = lane;
+#pragma unroll 4
+  for (; j + 32 < J; j += 64) {
+    a0 = fma(row[j], x[2 * j], a0);
+    a1 = fma(row[j + 32], x[2 * (j + 32)], a1);
+  }
+  if (j < J) a0 = fma(row[j], x[2 * j], a0);
+  double s = warp_sum(a0 + a1);
+  if (k == 0) s *= 0.5;
+  if (lane == 0) chat[k] = chat[k] + s;
+}
+
+// transposed: a CTA takes 32 columns n = 64 g + par + 2 lane of one parity and its
+// TW warps split the rows k = par, par + 2, ... <= n among them (row k's entry for
+// column n sits at off[k] + (n - k)/2, so a warp's loads are contiguous); the
+// row k = 0 term is halved; the warps' partial sums are added in shared memory
+constexpr int TW = 16;
+__global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict__ y, double* __restrict__ out,
+                                                        const double* __restrict__ tab,
+                                                        const int64_t* __restrict__ off, int64_t N, int64_t h,
+                                                        int scale_s) {
+  __shared__ double red[TW][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t ng = (h + 63) / 64;
+  const int64_t g = ng - 1 - (int64_t)(blockIdx.x >> 1);  // longest sums first
+  const int par = blockIdx.x & 1;
+  const int64_t n = 64 * g + par + 2 * lane;
+  y += (int64_t)blockIdx.y * N;
+  out += (int64_t)blockIdx.y * N;
+  const int64_t R = 32 * g + 32;  // rows k = par + 2 i, i < R, cover k <= 64 g + par + 62
+  const int64_t i0 = (int64_t)w * R / TW, i1 = (int64_t)(w + 1) * R / TW;
+  // batches of 8 rows: their 8 (independent) loads are in flight together
+  constexpr int B8 = 8;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t ib = i0; ib < i1; ib += B8) {
+    double m[B8], yv[B8];
+#pragma unroll
+    for (int q = 0; q < B8; ++q) {
+      const int64_t i = ib + q;
+      const int64_t k = par + 2 * i;
+      const bool live = i < i1 && n < h && k <= n;
+      m[q] = live ? tab[off[k] + ((n - k) >> 1)] : 0.0;
+      yv[q] = live ? (k == 0 ? 0.5 * y[0] : y[k]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < B8; ++q) a[q & 3] = fma(m[q], yv[q], a[q & 3]);
+  }
+  const double a0 = a[0] + a[1], a1 = a[2] + a[3];
+  red[w][lane] = a0 + a1;
+  __syncthreads();
+  if (w == 0 && n < h) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < TW; ++q) s += red[q][lane];
+    if (scale_s) s *= (double)n + 0.5;
+    out[n] = out[n] + s;
+  }
+}
+
 }  // namespace
+
+int launch_head_tab_init(Plan& P) {
+  const int64_t h = P.p.head;
+  if (!P.head_tab || h == 0) return GBDLT_OK;
+  k_head_tab_init<<<(unsigned)h, 256, 0, P.stream>>>(P.head_lam, P.head_off, P.head_tab, h);
+  count_launch();
+  return check_launch();
+}
 
 template <typename T>
 int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb) {
   const int64_t h = P.p.head;
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
+  if constexpr (sizeof(T) == 8) {
+    if (P.head_tab) {
+      k_head_fwd_tab<<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(
+          c, chat, P.head_tab, P.head_off, P.p.N, h);
+      launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 8.0 * 0.25 * (double)h * (double)h);
+      return check_launch();
+    }
+  }
   k_head_fwd<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(c, chat, lam,
                                                                                                P.p.N, h);
   launched(P, "head", (double)nb * 0.5 * (double)h * (double)h,
@@ -119,6 +223,14 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb) {
   const int64_t h = P.p.head;
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
+  if constexpr (sizeof(T) == 8) {
+    if (P.head_tab) {
+      k_head_t_tab<<<dim3((unsigned)(2 * ((h + 63) / 64)), (unsigned)nb), TW * 32, 0, P.stream>>>(
+          y, out, P.head_tab, P.head_off, P.p.N, h, scale_s);
+      launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 8.0 * 0.25 * (double)h * (double)h);
+      return check_launch();
+    }
+  }
   k_head_t<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(y, out, lam, P.p.N,
                                                                                              h, scale_s);
   launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h,

@@ -709,6 +709,19 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   size_t o_ar = A.take<RowAR>(stage_tabs ? N : 1);
   const int64_t nhead = prm.fast ? prm.head : 0;
   size_t o_lam = A.take<double>(std::max<int64_t>(nhead, 1)), o_lamf = A.take<float>(std::max<int64_t>(nhead, 1));
+  // stored head products (FP64 plans): row k holds (nhead - k + 1) / 2 entries
+  const bool head_tab = prec == GBDLT_FP64 && nhead > 0 && nhead <= kHeadTabMax;
+  std::vector<int64_t> hoff;
+  int64_t htab_n = 0;
+  if (head_tab) {
+    hoff.resize((size_t)nhead);
+    for (int64_t k = 0; k < nhead; ++k) {
+      hoff[(size_t)k] = htab_n;
+      htab_n += (nhead - k + 1) / 2;
+    }
+  }
+  size_t o_hoff = A.take<int64_t>(head_tab ? nhead : 1);
+  size_t o_htab = A.take<double>(head_tab ? htab_n : 1);
   auto take_layout = [&](const RecLayout& L) {
     LayoutOff o;
     o.cut = A.take<int32_t>(L.H);
@@ -780,6 +793,8 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   P->row_ar = stage_tabs ? (RowAR*)(base + o_ar) : nullptr;
   P->head_lam = nhead > 0 ? (double*)(base + o_lam) : nullptr;
   P->head_lamf = nhead > 0 ? (float*)(base + o_lamf) : nullptr;
+  P->head_off = head_tab ? (int64_t*)(base + o_hoff) : nullptr;
+  P->head_tab = head_tab ? (double*)(base + o_htab) : nullptr;
   auto place_layout = [&](RecLayout& L, const LayoutOff& o) {
     L.cut = (int32_t*)(base + o.cut);
     L.poff = (int64_t*)(base + o.poff);
@@ -860,6 +875,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
     std::vector<float> lamf(lam.begin(), lam.end());
     up(P->head_lam, lam.data(), sizeof(double) * lam.size());
     up(P->head_lamf, lamf.data(), sizeof(float) * lamf.size());
+    if (P->head_tab) up(P->head_off, hoff.data(), sizeof(int64_t) * hoff.size());
   }
   auto upload_layout = [&](RecLayout& L, const LayoutHost& h) {
     if (L.H == 0) return;
@@ -881,6 +897,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   st = launch_twiddle_init(*P);
   if (st == GBDLT_OK) st = launch_fft_tables_init(*P);
   if (st == GBDLT_OK) st = launch_stage_tables_init(*P);
+  if (st == GBDLT_OK) st = launch_head_tab_init(*P);
   if (st == GBDLT_OK) st = launch_rec_xm1(*P, R, 0);
   if (st == GBDLT_OK) st = launch_rec_state_init(*P, R);
   if (st == GBDLT_OK) st = launch_legpts(*P, P->CN);
