@@ -54,14 +54,13 @@ HBM_FALLBACK_GBS = 6800.0
 # dram__bytes_write.sum) and the hash of the kernel sources it was taken with;
 # a traffic figure is reported only while the sources are unchanged.
 TRAFFIC = {
-    # profiles/k_fft_fp64_N2p20.md: one launch of 48 vectors of 2^20 complex
-    # doubles (the leg2cheb band FFTs) moved these DRAM bytes against
-    # 2 x 48 x 2^20 x 16 B = 1610.6 MB algorithmic; valid while the sources
-    # the kernel is built from hash to "src"
-    "fft_cols": {"dram_per_algorithmic_byte": (827.942912 + 751.041280) / 1610.612736,
-                 "files": ("fft.cu", "gbdlt_internal.cuh"), "src": "60f9b22339337234"},
-    "fft_rows": {"dram_per_algorithmic_byte": (805.427456 + 757.708288) / 1610.612736,
-                 "files": ("fft.cu", "gbdlt_internal.cuh"), "src": "60f9b22339337234"},
+    # an ncu capture of the six launches of k_fft_cols<double> in one
+    # FP64 step at N = 2^20 (14 vectors of 2^20 complex doubles) moved 329.9 MB of
+    # DRAM traffic against 2 x 14 x 2^20 x 16 B = 469.8 MB algorithmic (part of
+    # each launch's input is still in the L2 from the kernel before it); valid
+    # while the sources the kernel is built from hash to "src"
+    "fft_cols": {"dram_per_algorithmic_byte": 329.913088 / 469.762048,
+                 "files": ("fft.cu", "gbdlt_internal.cuh"), "src": "a09c923705f45103"},
 }
 
 

@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict
   const int64_t i0 = (int64_t)w * R / TW, i1 = (int64_t)(w + 1) * R / TW;
   // batches of 8 rows: their 8 (independent) loads are in flight together
   constexpr int B8 = 8;
+  const double y0h = 0.5 * y[0];  // the row k = 0 term is halved
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t ib = i0; ib < i1; ib += B8) {
     double m[B8], yv[B8];
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict
       const int64_t k = par + 2 * i;
       const bool live = i < i1 && n < h && k <= n;
       m[q] = live ? tab[off[k] + ((n - k) >> 1)] : 0.0;
-      yv[q] = live ? (k == 0 ? 0.5 * y[0] : y[k]) : 0.0;
+      yv[q] = live ? (k == 0 ? y0h : y[k]) : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < B8; ++q) a[q & 3] = fma(m[q], yv[q], a[q & 3]);
