@@ -25,8 +25,14 @@
  *     caller owns every input/output buffer, the plan owns its node cache,
  *     tables and workspace.  gbdlt_plan_sync() waits for the stream and reports
  *     device-side failures (for instance a node iteration that did not settle).
- *   - N is the transform length: a power of two with 1 <= N <= 2^24.  Any
- *     other N makes gbdlt_plan_create return GBDLT_ERR_UNSUPPORTED_N.
+ *     FP64 plans run the float-float and FP32 transforms of a stage on a
+ *     plan-owned side stream that is forked from and joined back into the plan
+ *     stream within the call, so a call's work stays ordered on the plan stream
+ *     (inside a stream capture the side stream becomes a branch of the graph).
+ *   - N is the transform length, 1 <= N <= 2^24: a power of two for the
+ *     FFT-based chain, any N <= 65536 for the direct method (see
+ *     GBDLT_METHOD_*).  Other N make plan creation return
+ *     GBDLT_ERR_UNSUPPORTED_N.
  *   - A plan is not thread-safe: calls on one plan must be serialised.
  */
 #ifndef GBDLT_H
@@ -41,10 +47,14 @@ extern "C" {
 
 typedef struct gbdlt_plan_s* gbdlt_plan;
 
-/* Arithmetic form.  GBDLT_FP64: every transform step in double.  GBDLT_FP32:
- * DCT/DST transforms, asymptotic and Taylor combines in float; the recurrence
- * region in float-float (compensated float, ~2^-44 per operation) with
- * compensated sums; nodes, weights and delta-theta are computed in double.
+/* Arithmetic form.  GBDLT_FP64: double data in/out and FP64 accuracy: the
+ * nodes, the recurrence region, the head block and the leading expansion and
+ * Taylor terms in double; the terms whose size bounds their rounding error
+ * within eps/20 (gbdlt_params M_ff, M_fp32, L_ff) have their transforms and
+ * combines in float-float or FP32 arithmetic, scaled by exact powers of two.
+ * GBDLT_FP32: DCT/DST transforms, asymptotic and Taylor combines in float; the
+ * recurrence region in float-float (compensated float, ~2^-44 per operation)
+ * with compensated sums; nodes, weights and delta-theta are computed in double.
  * Float data in/out. */
 enum { GBDLT_FP64 = 0, GBDLT_FP32 = 1 };
 
