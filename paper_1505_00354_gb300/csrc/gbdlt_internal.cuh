@@ -441,8 +441,9 @@ template <typename T>
 int launch_l2c_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const float2* Y32, const T* vrec, T* v, int64_t nb);
 template <typename T>
 int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb);
+// hb != null: add the head block's written result (launch_head_fwd with hout)
 template <typename T>
-int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb);
+int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb, const double* hb = nullptr);
 template <typename T>
 int launch_fcs_pro(Plan& P, const T* a, C2<T>* U, int scale_d, int64_t nb);
 // Taylor pairs: p < taylor_p64 in U / Y / F (precision T, [item][P64][N]); with
@@ -459,19 +460,23 @@ int launch_tayt_epi(Plan& P, const C2<T>* F, const ffc* Fff, C2<T>* Q, T* u_out,
 template <typename T>
 int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>* U, ffc* Uff, float2* U32,
                     int64_t nb);
+// hb != null: add the transposed head block's written result (launch_head_t with hout)
 template <typename T>
 int launch_l2ct_epi(Plan& P, const C2<T>* F, const ffc* Fff, const float2* F32, const T* rect, T* out, int scale_s,
-                    int64_t nb);
+                    int64_t nb, const double* hb = nullptr);
 template <typename T>
 int launch_fcs_re_epi(Plan& P, const C2<T>* Y, T* out, int64_t nb);
 template <typename T>
 int launch_scale(Plan& P, const T* in, T* out, int which, int64_t nb);
 // head.cu: the dense head block, chat[0:h] += M[0:h, 0:h] c[0:h], and its
 // transpose, out[0:h] += D M[0:h, 0:h]^T y[0:h] (D = diag(n + 1/2) when scale_s)
+// With hout given, the block's result is written (double; item stride N sizeof(T)/8
+// doubles, so it fits in an N-element buffer of the plan's precision) instead of
+// being added; the A4 / transposed leg2cheb epilogues then add it (hb below).
 template <typename T>
-int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb);
+int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb, double* hout = nullptr);
 template <typename T>
-int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb);
+int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* hout = nullptr);
 // fills P.head_tab from P.head_lam (plan creation)
 int launch_head_tab_init(Plan& P);
 

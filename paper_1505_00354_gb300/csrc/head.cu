@@ -65,9 +65,12 @@ struct HeadSum<float> {
   }
 };
 
+// hout != null: the block's sum goes to hout[k] (double, item stride hs) instead
+// of being added to chat (the chain adds it in the A4 epilogue)
 template <typename T>
 __global__ void __launch_bounds__(HW * 32) k_head_fwd(const T* __restrict__ c, T* __restrict__ chat,
-                                                      const T* __restrict__ lam, int64_t N, int64_t h) {
+                                                      const T* __restrict__ lam, int64_t N, int64_t h,
+                                                      double* __restrict__ hout, int64_t hs) {
   const int lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * HW + (threadIdx.x >> 5);
   if (k >= h) return;  // whole warp
@@ -77,12 +80,20 @@ __global__ void __launch_bounds__(HW * 32) k_head_fwd(const T* __restrict__ c, T
   // term j: lam[j] lam[k + j] c[k + 2j]
   double s = warp_sum(HeadSum<T>::run(lam, c, k, 1, k, 2, J, lane));
   if (k == 0) s *= 0.5;
-  if (lane == 0) chat[k] = (T)((double)chat[k] + s);
+  if (lane == 0) {
+    if (hout)
+      hout[(int64_t)blockIdx.y * hs + k] = s;
+    else
+      chat[k] = (T)((double)chat[k] + s);
+  }
 }
 
+// hout != null: the scaled sum goes to hout[n] (double, item stride hs) instead of
+// being added to out (the chain adds it in the transposed leg2cheb epilogue)
 template <typename T>
 __global__ void __launch_bounds__(HW * 32) k_head_t(const T* __restrict__ y, T* __restrict__ out,
-                                                    const T* __restrict__ lam, int64_t N, int64_t h, int scale_s) {
+                                                    const T* __restrict__ lam, int64_t N, int64_t h, int scale_s,
+                                                    double* __restrict__ hout, int64_t hs) {
   const int lane = threadIdx.x & 31;
   const int64_t q = (int64_t)blockIdx.x * HW + (threadIdx.x >> 5);
   if (q >= h) return;  // whole warp
@@ -96,7 +107,10 @@ __global__ void __launch_bounds__(HW * 32) k_head_t(const T* __restrict__ y, T* 
   if (lane == 0) {
     if (!(n & 1)) s += 0.5 * (double)lam[n / 2] * (double)lam[n / 2] * (double)y[0];
     if (scale_s) s *= (double)n + 0.5;
-    out[n] = (T)((double)out[n] + s);
+    if (hout)
+      hout[(int64_t)blockIdx.y * hs + n] = s;
+    else
+      out[n] = (T)((double)out[n] + s);
   }
 }
 
@@ -200,48 +214,48 @@ int launch_head_tab_init(Plan& P) {
 }
 
 template <typename T>
-int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb) {
+int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb, double* hout) {
   const int64_t h = P.p.head;
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
   if constexpr (sizeof(T) == 8) {
-    if (P.head_tab) {
+    if (P.head_tab && !hout) {
       k_head_fwd_tab<<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(
           c, chat, P.head_tab, P.head_off, P.p.N, h);
       launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 8.0 * 0.25 * (double)h * (double)h);
       return check_launch();
     }
   }
-  k_head_fwd<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(c, chat, lam,
-                                                                                               P.p.N, h);
+  k_head_fwd<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(
+      c, chat, lam, P.p.N, h, hout, P.p.N * (int64_t)sizeof(T) / 8);
   launched(P, "head", (double)nb * 0.5 * (double)h * (double)h,
            (double)nb * (double)sizeof(T) * 3.0 * (double)h);
   return check_launch();
 }
 
 template <typename T>
-int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb) {
+int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* hout) {
   const int64_t h = P.p.head;
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
   if constexpr (sizeof(T) == 8) {
-    if (P.head_tab) {
+    if (P.head_tab && !hout) {
       k_head_t_tab<<<dim3((unsigned)(2 * ((h + 63) / 64)), (unsigned)nb), TW * 32, 0, P.stream>>>(
           y, out, P.head_tab, P.head_off, P.p.N, h, scale_s);
       launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 8.0 * 0.25 * (double)h * (double)h);
       return check_launch();
     }
   }
-  k_head_t<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(y, out, lam, P.p.N,
-                                                                                             h, scale_s);
+  k_head_t<T><<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(
+      y, out, lam, P.p.N, h, scale_s, hout, P.p.N * (int64_t)sizeof(T) / 8);
   launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h,
            (double)nb * (double)sizeof(T) * 3.0 * (double)h);
   return check_launch();
 }
 
-template int launch_head_fwd<double>(Plan&, const double*, double*, int64_t);
-template int launch_head_fwd<float>(Plan&, const float*, float*, int64_t);
-template int launch_head_t<double>(Plan&, const double*, double*, int, int64_t);
-template int launch_head_t<float>(Plan&, const float*, float*, int, int64_t);
+template int launch_head_fwd<double>(Plan&, const double*, double*, int64_t, double*);
+template int launch_head_fwd<float>(Plan&, const float*, float*, int64_t, double*);
+template int launch_head_t<double>(Plan&, const double*, double*, int, int64_t, double*);
+template int launch_head_t<float>(Plan&, const float*, float*, int, int64_t, double*);
 
 }  // namespace gbdlt

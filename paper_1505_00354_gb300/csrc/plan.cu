@@ -1000,12 +1000,25 @@ const C2<T>* band_ffts(Plan& P, Side& sd, void* a, int64_t nb, int dir, int tran
 }
 
 // chat = M c (Sec. 3); also leaves v (values on the cheb1 grid) in P.v
+// In FP32 plans the dense head block (FP32-pipe work that reads only c) runs on the
+// side stream beside the rest of leg2cheb and writes its columns to P.z as
+// doubles; the A4 epilogue adds them.  (FP64 plans add it in place at the end: it
+// is FP64 work like the rest of the chain.)
 template <typename T>
 int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   const int64_t KM = (int64_t)P.p.K * P.p.M;
   T* vrec = (T*)P.tmp;
   T* v = (T*)P.v;
   int st = GBDLT_OK;
+  const bool head_side = is_f32<T> && P.p.head > 0;
+  double* hb = head_side ? (double*)P.z : nullptr;
+  Side hs(P, head_side);
+  if (head_side) {
+    hs.enter();
+    st = launch_head_fwd<T>(P, c, chat, nb, hb);
+    hs.leave();
+    if (st) return st;
+  }
   const C2<T>* Y = nullptr;
   const ffc* Yff = nullptr;
   const float2* Y32 = nullptr;
@@ -1029,11 +1042,13 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   st = launch_a4_pro<T>(P, v, (C2<T>*)P.bufA, nb);
   if (st) return st;
   const C2<T>* F = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb, -1);
-  st = launch_a4_epi<T>(P, F, chat, nb);
+  st = hs.join();
+  if (st) return st;
+  st = launch_a4_epi<T>(P, F, chat, nb, hb);
   if (st) return st;
   // columns below the head: P.v lacks them, so chains that go on to the Taylor
   // NDCT take its l = 0 term from chat (run_dlt_tail)
-  return launch_head_fwd<T>(P, c, chat, nb);
+  return head_side ? GBDLT_OK : launch_head_fwd<T>(P, c, chat, nb);
 }
 
 // forward declaration (defined below)
@@ -1118,6 +1133,18 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
     if (st) return st;
     Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), nb, +1);
   }
+  // FP32 plans: the transposed head block (reads u[0:head], FP32-pipe work) on the
+  // side stream beside the rest of the chain, its scaled columns into P.tmp2 as
+  // doubles; the transposed leg2cheb epilogue adds them
+  const bool head_side = is_f32<T> && head > 0 && npair > 0;
+  double* hb = head_side ? (double*)P.tmp2 : nullptr;
+  Side hsd(P, head_side);
+  if (head_side) {
+    hsd.enter();
+    st = launch_head_t<T>(P, uhead, out, scale_s, nb, hb);
+    hsd.leave();
+    if (st) return st;
+  }
   void* U = Y ? other(P, Y) : P.bufA;
   st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, (ffc*)P.bufAff,
                           (float2*)P.bufA32, nb);
@@ -1133,9 +1160,11 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
     if (st) return st;
     if (sj) return sj;
   }
-  st = launch_l2ct_epi<T>(P, F2, Fff, F32, rect, out, scale_s, nb);
+  st = hsd.join();
   if (st) return st;
-  return launch_head_t<T>(P, uhead, out, scale_s, nb);
+  st = launch_l2ct_epi<T>(P, F2, Fff, F32, rect, out, scale_s, nb, hb);
+  if (st) return st;
+  return head_side ? GBDLT_OK : launch_head_t<T>(P, uhead, out, scale_s, nb);
 }
 
 // out = M^T y: z = A4^T y, then P_cheb^T z

@@ -444,7 +444,8 @@ __global__ void k_a4_pro(const T* __restrict__ v, C2<T>* __restrict__ U, int64_t
 }
 
 template <typename T>
-__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, T invN, TwArgs<T> tw4N) {
+__global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int64_t N, T invN, TwArgs<T> tw4N,
+                         const double* __restrict__ hb, int64_t h, int64_t hs) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   F += (int64_t)blockIdx.y * N;
@@ -454,7 +455,9 @@ __global__ void k_a4_epi(const C2<T>* __restrict__ F, T* __restrict__ chat, int6
   const C2<T> Vh = mk<T>((Fn.x + Fm.x) * (T)0.5, (Fn.y - Fm.y) * (T)0.5);
   const C2<T> e = twid<T>(tw4N, n);  // conj(e) = e^{-i pi n/(2N)}
   const T U = e.x * Vh.x + e.y * Vh.y;
-  chat[n] = (n == 0 ? invN : (T)2 * invN) * U;
+  const T a = (n == 0 ? invN : (T)2 * invN) * U;
+  // the head block's columns (when it ran beside this chain): added in double
+  chat[n] = (hb && n < h) ? (T)((double)a + hb[(int64_t)blockIdx.y * hs + n]) : a;
 }
 
 // ---------------------------------------------------------------- FCS helpers
@@ -912,7 +915,8 @@ template <typename T>
 __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ Fff,
                            const float2* __restrict__ F32, const T* __restrict__ rect, T* __restrict__ out, int64_t N,
                            int M, int Mh, int M64, BandArgs B, const double* __restrict__ Cn,
-                           const double* __restrict__ Hnm, int scale_s, TwArgs<T> tw4N, Scale32 S) {
+                           const double* __restrict__ Hnm, int scale_s, TwArgs<T> tw4N, Scale32 S,
+                           const double* __restrict__ hb, int64_t hh, int64_t hs) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t bt = blockIdx.y;
@@ -983,7 +987,9 @@ __global__ void k_l2ct_epi(const C2<T>* __restrict__ F, const ffc* __restrict__ 
       acc += e.x * V.x - e.y * V.y;
     }
   }
-  out[n] = scale_s ? (idx_t<T>(n) + (T)0.5) * acc : acc;
+  const T val = scale_s ? (idx_t<T>(n) + (T)0.5) * acc : acc;
+  // the head block's columns (when it ran beside this chain): added in double
+  out[n] = (hb && n < hh) ? (T)((double)val + hb[bt * hs + n]) : val;
 }
 
 // which: 0 copy, 1 multiply by (n + 1/2), 2 multiply by w_k, 3 dtheta = tN / N (double out)
@@ -1057,9 +1063,10 @@ int launch_a4_pro(Plan& P, const T* v, C2<T>* U, int64_t nb) {
   return check_launch();
 }
 template <typename T>
-int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb) {
+int launch_a4_epi(Plan& P, const C2<T>* F, T* chat, int64_t nb, const double* hb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
-  k_a4_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, chat, P.p.N, (T)1 / (T)P.p.N, tw);
+  k_a4_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(F, chat, P.p.N, (T)1 / (T)P.p.N, tw, hb,
+                                                                     P.p.head, P.p.N * (int64_t)sizeof(T) / 8);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -1164,10 +1171,11 @@ int launch_l2ct_pro(Plan& P, const C2<T>* Y, const T* g, int use_w, T* z, C2<T>*
 }
 template <typename T>
 int launch_l2ct_epi(Plan& P, const C2<T>* F, const ffc* Fff, const float2* F32, const T* rect, T* out, int scale_s,
-                    int64_t nb) {
+                    int64_t nb, const double* hb) {
   const TwArgs<T> tw = tw4n_args<T>(P);
   k_l2ct_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(
-      F, Fff, F32, rect, out, P.p.N, P.p.M, P.p.Mh, P.p.M64, band_args(P), P.Cn, P.Hnm, scale_s, tw, scale32(P));
+      F, Fff, F32, rect, out, P.p.N, P.p.M, P.p.Mh, P.p.M64, band_args(P), P.Cn, P.Hnm, scale_s, tw, scale32(P), hb,
+      P.p.head, P.p.N * (int64_t)sizeof(T) / 8);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -1221,7 +1229,7 @@ int launch_stage_tables_init(Plan& P) {
   template int launch_absmax<T>(Plan&, const T*, int64_t);                                            \
   template int launch_l2c_epi<T>(Plan&, const C2<T>*, const ffc*, const float2*, const T*, T*, int64_t); \
   template int launch_a4_pro<T>(Plan&, const T*, C2<T>*, int64_t);                                    \
-  template int launch_a4_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                    \
+  template int launch_a4_epi<T>(Plan&, const C2<T>*, T*, int64_t, const double*);                     \
   template int launch_fcs_pro<T>(Plan&, const T*, C2<T>*, int, int64_t);                              \
   template int launch_fcs_re_epi<T>(Plan&, const C2<T>*, T*, int64_t);                                \
   template int launch_tay_pro<T>(Plan&, const T*, C2<T>*, ffc*, int, int, int64_t);                   \
@@ -1229,7 +1237,8 @@ int launch_stage_tables_init(Plan& P) {
   template int launch_tayt_pro<T>(Plan&, const T*, int, C2<T>*, ffc*, int, int, int64_t);             \
   template int launch_tayt_epi<T>(Plan&, const C2<T>*, const ffc*, C2<T>*, T*, int, int, int64_t, int64_t); \
   template int launch_l2ct_pro<T>(Plan&, const C2<T>*, const T*, int, T*, C2<T>*, ffc*, float2*, int64_t); \
-  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const ffc*, const float2*, const T*, T*, int, int64_t); \
+  template int launch_l2ct_epi<T>(Plan&, const C2<T>*, const ffc*, const float2*, const T*, T*, int, int64_t, \
+                                  const double*);                                                      \
   template int launch_scale<T>(Plan&, const T*, T*, int, int64_t);
 INST(double)
 INST(float)

@@ -399,16 +399,19 @@ def test_max_n(gb):
         gb.Plan(2 * N)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("N", [1024, 1 << 16, 1 << 20])
-def test_side_branch_bitwise(gb, N):
+def test_side_branch_bitwise(gb, N, prec):
     """FP64 plans run their float-float and FP32 transforms on a side stream beside
-    the FP64 work of the same stage.  The results are bitwise those of the serial
-    order (while the per-kernel profiler is on, every launch stays on one stream),
-    for every operator, on the first (direct) call, the capturing call and graph
-    replays, on the default stream and on a non-default one."""
-    x = dev(_c(N, 91))
+    the FP64 work of the same stage; FP32 plans run their dense head blocks there.
+    The results are bitwise those of the serial order (while the per-kernel
+    profiler is on, every launch stays on one stream), for every operator, on the
+    first (direct) call, the capturing call and graph replays, on the default
+    stream and on a non-default one."""
+    fp = gb.FP64 if prec == "fp64" else gb.FP32
+    x = dev(_c(N, 91), torch.float64 if prec == "fp64" else torch.float32)
     ops = ["leg2cheb", "leg2cheb_t", "chebeval", "chebeval_t", "dlt", "dlt_t", "idlt", "idlt_t"]
-    p = gb.Plan(N, method=gb.METHOD_FAST)
+    p = gb.Plan(N, fp, method=gb.METHOD_FAST)
     p.profile(1)
     ref = {op: getattr(p, op)(x).clone() for op in ops}
     p.profile(0)
@@ -421,7 +424,7 @@ def test_side_branch_bitwise(gb, N):
             assert torch.equal(y, ref[op]), op
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        q = gb.Plan(N, method=gb.METHOD_FAST, stream=s)
+        q = gb.Plan(N, fp, method=gb.METHOD_FAST, stream=s)
         for op in ("dlt", "idlt"):
             y = torch.empty_like(x)
             for _ in range(3):
