@@ -46,6 +46,7 @@ constexpr double kPi = 3.141592653589793238;
 
 struct PD {
   double p, dp;
+  double cot;  // cot(theta) at the evaluation point
 };
 
 // h_{m,N} of the expansion for m < kMaxTerms; the same for every node of a plan,
@@ -68,11 +69,13 @@ __device__ PD eval_rec(int64_t N, double s, double c, double sh) {
   PD r;
   r.p = P;
   r.dp = (double)N * (xm1 * P + D) / s;
+  r.cot = c / s;
   return r;
 }
 
-__device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, double CN, const HTab& H) {
-  const double eps = ((double)N + 0.5) * d;
+// Nh = N + 1/2
+__device__ PD eval_asy(double Nh, int64_t k, double d, double s, double c, double CN, const HTab& H) {
+  const double eps = Nh * d;
   const double e2 = eps * eps;
   // sin/cos of |eps| <= 0.06 by Taylor polynomials (error < 1e-19)
   double se = eps * (1.0 + e2 * (-1.0 / 6 + e2 * (1.0 / 120 + e2 * (-1.0 / 5040 + e2 * (1.0 / 362880)))));
@@ -86,10 +89,13 @@ __device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, doubl
   const double sg0 = sqrt(g);
   double gm = sg0;  // g^{m+1/2}
   double P = 0.0, dP = 0.0;
+  double mh = 0.5, nmh = Nh;  // m + 1/2 and N + m + 1/2, exact
   for (int m = 0; m < kMaxTerms - 1; ++m) {
     const double term = H.h[m] * gm;
     P += term * cr;
-    dP += term * (-((double)N + m + 0.5) * ci - (m + 0.5) * cot * cr);
+    dP += term * (-nmh * ci - mh * cot * cr);
+    mh += 1.0;
+    nmh += 1.0;
     gm *= g;
     const double ncr = cr * rr - ci * ri;
     ci = cr * ri + ci * rr;
@@ -99,6 +105,7 @@ __device__ PD eval_asy(int64_t N, int64_t k, double d, double s, double c, doubl
   PD r;
   r.p = CN * P;
   r.dp = CN * dP;
+  r.cot = cot;
   return r;
 }
 
@@ -140,7 +147,7 @@ __global__ void k_legpts(int64_t N, int64_t kend, double CN, HTab H, double* __r
       sincos(0.5 * th, &sh, &ch);
       r = eval_rec(N, s, c, sh);
     } else {
-      r = eval_asy(N, k, d, s, c, CN, H);
+      r = eval_asy(Nh, k, d, s, c, CN, H);
     }
     const double step = r.p / r.dp;
     d -= step;
@@ -151,11 +158,11 @@ __global__ void k_legpts(int64_t N, int64_t kend, double CN, HTab H, double* __r
     // step is small enough for the one-step derivative update below to keep the
     // weight to ~1e-17 relative ((step N)^2 / 2).
     const double a_step = fabs(step);
-    if (a_step * (double)N <= 1e-8 && (0.5 * fabs(c / s) + 1.0) * a_step * a_step * (double)N <= 1e-18) {
+    if (a_step * (double)N <= 1e-8 && (0.5 * fabs(r.cot) + 1.0) * a_step * a_step * (double)N <= 1e-18) {
       // dP/dtheta at the updated point by one Taylor step, with the second
       // derivative from Legendre's equation in theta:
       //   P'' = -cot(theta) P' - N(N+1) P   (step^2 N^3 is below 1e-20 here)
-      dp_final = r.dp + step * ((c / s) * r.dp + (double)N * ((double)N + 1.0) * r.p);
+      dp_final = r.dp + step * (r.cot * r.dp + (double)N * ((double)N + 1.0) * r.p);
       // cos/sin at the updated point (theta decreased by step)
       const double cn = c + s * step;
       s = s - c * step;
