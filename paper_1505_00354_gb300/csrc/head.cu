@@ -163,7 +163,7 @@ constexpr int TW = 16;
 __global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict__ y, double* __restrict__ out,
                                                         const double* __restrict__ tab,
                                                         const int64_t* __restrict__ off, int64_t N, int64_t h,
-                                                        int scale_s) {
+                                                        int scale_s, double* __restrict__ hout, int64_t hs) {
   __shared__ double red[TW][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t ng = (h + 63) / 64;
@@ -199,7 +199,10 @@ __global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict
 #pragma unroll
     for (int q = 0; q < TW; ++q) s += red[q][lane];
     if (scale_s) s *= (double)n + 0.5;
-    out[n] = out[n] + s;
+    if (hout)
+      hout[(int64_t)blockIdx.y * hs + n] = s;
+    else
+      out[n] = out[n] + s;
   }
 }
 
@@ -239,9 +242,9 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* 
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
   if constexpr (sizeof(T) == 8) {
-    if (P.head_tab && !hout) {
+    if (P.head_tab) {
       k_head_t_tab<<<dim3((unsigned)(2 * ((h + 63) / 64)), (unsigned)nb), TW * 32, 0, P.stream>>>(
-          y, out, P.head_tab, P.head_off, P.p.N, h, scale_s);
+          y, out, P.head_tab, P.head_off, P.p.N, h, scale_s, hout, P.p.N);
       launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 8.0 * 0.25 * (double)h * (double)h);
       return check_launch();
     }

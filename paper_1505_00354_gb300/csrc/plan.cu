@@ -1133,10 +1133,12 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
     if (st) return st;
     Y = (const C2<T>*)launch_fft<T>(P, q, other(P, q), nb, +1);
   }
-  // FP32 plans: the transposed head block (reads u[0:head], FP32-pipe work) on the
-  // side stream beside the rest of the chain, its scaled columns into P.tmp2 as
-  // doubles; the transposed leg2cheb epilogue adds them
-  const bool head_side = is_f32<T> && head > 0 && npair > 0;
+  // The transposed head block (reads u[0:head]) on the side stream beside the rest
+  // of the chain, its scaled columns into P.tmp2 as doubles; the transposed
+  // leg2cheb epilogue adds them.  FP32 plans: FP32-pipe work.  FP64 plans with the
+  // stored products: a latency-bound kernel (about 70 % of the FP64 pipe) that
+  // fills gaps of the FP64 work beside it.
+  const bool head_side = (is_f32<T> || P.head_tab) && head > 0 && npair > 0;
   double* hb = head_side ? (double*)P.tmp2 : nullptr;
   Side hsd(P, head_side);
   if (head_side) {
