@@ -9,8 +9,10 @@ distributed coefficients; no dataset is involved).
 
 GPU arm (default): W warm-up steps, then K timed steps; each step is bracketed by
 CUDA events on the plan's stream and preceded (outside the events) by a 256 MiB
-write that flushes the 129 MB L2.  The per-kernel timing behind the roofline
-object is taken in the same timed steps.  Also reported: the FP32 form on the
+write that flushes the 129 MB L2.  The timed steps run as a user's calls do
+(side-stream transforms, graph replays).  The per-kernel timing behind the
+roofline object comes from K more steps with the plan's profiler on, which keeps
+every launch on the plan stream (serial order).  Also reported: the FP32 form on the
 same workload, the error of both forms against the oracle on sampled rows, an
 end-to-end number through the public API with host buffers, and the oracle timed
 on the host cores on a bounded sample (cpu_baseline).
