@@ -13,7 +13,8 @@
 // warp are contiguous; the sum is a plain FP64 fused multiply-add chain in the
 // FP64 form and a Kahan-compensated FP32 sum in the FP32 form (FP32 arithmetic
 // runs on a pipe 64 times wider than FP64 on GB300).  Per term: one product of
-// two table entries and one multiply-add, so FP64 issue bounds the FP64 form.
+// two table entries and one multiply-add, so FP64 issue bounds the FP64 form;
+// FP64 plans with h <= kHeadTabMax use the stored products below instead.
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__(HW * 32) k_head_t(const T* __restrict__ y, T* 
 // (n = k + 2j) in a table, row k holding n = k, k+2, ..., < h from offset off[k]
 // (h^2/4 doubles: 537 MB at h = 16384).  Each term then costs one FP64 fused
 // multiply-add and 8 bytes of HBM instead of a product and a fused multiply-add:
-// the block moves from the FP64 pipe towards the HBM roofline.  The stored
-// product is the rounded product the on-the-fly kernel forms, so the forward
-// block is bitwise the same.
+// the FP64 work halves, and the table streams from HBM at about 4 TB/s beside
+// it.  The stored product is the rounded product the on-the-fly kernel forms, so
+// the forward block is bitwise the same.
 __global__ void k_head_tab_init(const double* __restrict__ lam, const int64_t* __restrict__ off,
                                 double* __restrict__ tab, int64_t h) {
   const int64_t k = blockIdx.x;
