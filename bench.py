@@ -188,28 +188,34 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 10:
-                continue
-            if self.uuid and self.uuid not in parts[1]:
-                continue
-            rows.append((self._when(parts[0]), parts[2:]))
-        t0 = self.t0 if self.t0 is not None else 0.0
-        inside = [r for t, r in rows if t is not None and t0 <= t <= self.t1]
-        if not inside:  # region shorter than the period: the first sample after it
-            after = [r for t, r in rows if t is not None and t >= t0]
-            inside = after[:1]
-        if not inside:
-            return None
-        sm = [float(r[0]) for r in inside if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in inside for i in range(4) if r[4 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(inside),
-                "window_ms": round((self.t1 - t0) * 1e3, 1)}
+        with open(self.path) as fh:
+            return summarize_clocks(fh, self.uuid, self.t0 if self.t0 is not None else 0.0, self.t1)
+
+
+def summarize_clocks(lines, uuid: str | None, t0: float, t1: float) -> dict | None:
+    """Median SM clock, maximum clock and active throttle reasons of the
+    nvidia-smi samples (ClockSampler.FIELDS, CSV without header or units) taken
+    between host times t0 and t1; when none falls inside (a region shorter than
+    the sampling period), the first sample after t0."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        if uuid and uuid not in parts[1]:
+            continue
+        rows.append((ClockSampler._when(parts[0]), parts[2:]))
+    inside = [r for t, r in rows if t is not None and t0 <= t <= t1]
+    if not inside:
+        inside = [r for t, r in rows if t is not None and t >= t0][:1]
+    if not inside:
+        return None
+    sm = [float(r[0]) for r in inside if r[0].replace(".", "").isdigit()]
+    mx = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in inside for i in range(4) if r[4 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(inside), "window_ms": round((t1 - t0) * 1e3, 1)}
 
 
 # --------------------------------------------------------------------------
