@@ -144,3 +144,38 @@ def test_bands_respect_asymptotic_bound(gb):
             lh = sum(2 * math.log(j - 0.5) - math.log(j) - math.log(ns + j + 0.5) for j in range(1, M + 1))
             bound = 2 * math.exp(lc + lh) / (2 * s) ** (M + 0.5)
             assert bound <= eps / 20 * (1 + 1e-9), (N, ns, ka, bound)
+
+
+@pytest.mark.parametrize("N", [1024, 2**16, 2**20, 2**22])
+def test_precision_tiers_within_budget(gb, N):
+    """FP64 plans run the tail of each band's expansion in FP32 and the terms
+    before it in float-float: on every band the FFT rounding of those terms,
+    2 log2(N) u T_m with T_m = 2 C_ns h_{m,ns} / (2 sin theta_ka)^{m+1/2} (the
+    term's bound at the band's first row; u = 2^-24 for FP32, 2^-46 for
+    float-float), sums to at most eps/20 per tier; likewise the float-float
+    Taylor terms l >= L - L_ff with T_l = 0.83845^l / l! (Corollary 2.4)."""
+    p = gb.plan_params(N, 0)
+    M, eps = p["M"], p["eps"]
+    Mh = M - p["M_fp32"]
+    M64 = Mh - p["M_ff"]
+    assert 1 <= M64 <= Mh <= M
+    lg = int(round(math.log2(N)))
+    for ns, ka, kb in p["bands"]:
+        s2 = 2 * math.sin((ka + 0.5) * math.pi / N)
+        lc = 0.5 * math.log(4 / math.pi) + math.lgamma(ns + 1) - math.lgamma(ns + 1.5)
+
+        def T(m):
+            lh = sum(2 * math.log(j - 0.5) - math.log(j) - math.log(ns + j + 0.5) for j in range(1, m + 1))
+            return 2 * math.exp(lc + lh) / s2 ** (m + 0.5)
+
+        e32 = sum(2 * lg * 2.0**-24 * T(m) for m in range(Mh, M))
+        eff = sum(2 * lg * 2.0**-46 * T(m) for m in range(M64, Mh))
+        assert e32 <= eps / 20 * (1 + 1e-9), (N, ns, e32)
+        assert eff <= eps / 20 * (1 + 1e-9), (N, ns, eff)
+    L = p["L"]
+    Lff = L - p["L_ff"]
+    eL = sum(2 * lg * 2.0**-46 * 0.83845**l / math.factorial(l) for l in range(Lff, L))
+    assert eL <= eps / 20 * (1 + 1e-9)
+    # FP32 plans have no tiers
+    q = gb.plan_params(N, 1)
+    assert q["M_fp32"] == 0 and q["M_ff"] == 0 and q["L_ff"] == 0
