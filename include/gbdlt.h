@@ -136,6 +136,15 @@ int gbdlt_plan_set_stream(gbdlt_plan plan, void* cuda_stream);
  * iteration failed since the last sync, GBDLT_ERR_CUDA on a CUDA error. */
 int gbdlt_plan_sync(gbdlt_plan plan);
 int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out);
+/* Newton iterations a node may take in this plan's later gbdlt_legpts calls
+ * (0 <= max_iter <= 24, the default and the largest value; the node solve of
+ * Sec. 2.2 settles in 2-4).  A node that has not settled within the cap is
+ * flagged and the next gbdlt_plan_sync returns GBDLT_ERR_NOT_CONVERGED (and
+ * clears the flag); its theta, x, w and dtheta are then unspecified until a
+ * gbdlt_legpts with a sufficient cap recomputes them.  A failure-path hook: it
+ * lets a caller or a test reach the not-converged status without a fault.
+ * GBDLT_ERR_INVALID_ARG for other values. */
+int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
 
 /* Legendre nodes and weights (Eq. 1 and Eq. 2; Sec. 2.1-2.2): recomputes the
  * plan's node cache on the GPU and copies any requested array out.  Ordering:
@@ -154,14 +163,17 @@ int gbdlt_legpts(gbdlt_plan plan, double* x, double* theta, double* w, double* d
  *   x, theta, w (device, N doubles each, required) and dtheta (device, N
  *   doubles, may be NULL): the same arrays and ordering as gbdlt_legpts.
  *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream).
- * Allocates no memory.  Its scratch (N doubles and a status word) is a
- * 512 KB array in the library's device memory, present on every GPU that loads
- * the library until the process exits.  The first call on each device looks up
- * that array's device address (make that first call before any stream capture
- * on that device).  Every call uses the same array, so calls that overlap on
- * the GPU (different streams, different host threads) race and must be
- * serialised by the caller.  Synchronises `cuda_stream` before returning and
- * returns GBDLT_ERR_NOT_CONVERGED if a node iteration did not settle. */
+ * Allocates no memory (gbdlt_device_alloc_count does not change).  Its scratch
+ * (N doubles and a status word) is a 512 KB array in the library's device
+ * memory, present on every GPU that loads the library until the process exits.
+ * Every call looks up that array's device address in the current device's
+ * context (the first call on a device may load the library's device code there:
+ * make that first call before any stream capture on that device); a call after
+ * cudaDeviceReset therefore uses the array of the new context.  Every call uses
+ * the same array, so calls that overlap on the GPU (different streams,
+ * different host threads) race and must be serialised by the caller.
+ * Synchronises `cuda_stream` before returning and returns
+ * GBDLT_ERR_NOT_CONVERGED if a node iteration did not settle. */
 int gbdlt_legpts_noalloc(int64_t N, double* x, double* theta, double* w, double* dtheta,
                          void* cuda_stream);
 
@@ -238,6 +250,10 @@ const char* gbdlt_status_string(int status);
 /* Number of kernels this library has launched since it was loaded (all plans,
  * all threads). */
 uint64_t gbdlt_launch_count(void);
+/* Number of device allocations (cudaMalloc calls) this library has made since
+ * it was loaded: plan workspaces, plan-creation scratch and batch staging
+ * buffers (all plans and batches, all threads). */
+uint64_t gbdlt_device_alloc_count(void);
 
 #ifdef __cplusplus
 }

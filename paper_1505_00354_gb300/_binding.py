@@ -83,12 +83,12 @@ class Params(ctypes.Structure):
 ENTRY_POINTS = (
     "gbdlt_plan_params", "gbdlt_plan_params_ex", "gbdlt_plan_create", "gbdlt_plan_create_ex",
     "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
-    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
+    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_plan_set_node_iterations", "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
     "gbdlt_batch_create", "gbdlt_batch_create_ex", "gbdlt_batch_exec", "gbdlt_batch_info",
     "gbdlt_batch_group_info", "gbdlt_batch_destroy",
-    "gbdlt_status_string", "gbdlt_launch_count",
+    "gbdlt_status_string", "gbdlt_launch_count", "gbdlt_device_alloc_count",
 )
 
 
@@ -112,6 +112,7 @@ def lib():
         L.gbdlt_plan_set_stream.argtypes = [vp, vp]
         L.gbdlt_plan_sync.argtypes = [vp]
         L.gbdlt_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.gbdlt_plan_set_node_iterations.argtypes = [vp, i32]
         L.gbdlt_legpts.argtypes = [vp, vp, vp, vp, vp]
         L.gbdlt_legpts_noalloc.argtypes = [i64, vp, vp, vp, vp, vp]
         for name in ("gbdlt_leg2cheb", "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t",
@@ -132,8 +133,9 @@ def lib():
         L.gbdlt_status_string.argtypes = [i32]
         L.gbdlt_status_string.restype = ctypes.c_char_p
         L.gbdlt_launch_count.restype = ctypes.c_uint64
+        L.gbdlt_device_alloc_count.restype = ctypes.c_uint64
         for name in ENTRY_POINTS:
-            if name not in ("gbdlt_status_string", "gbdlt_launch_count"):
+            if name not in ("gbdlt_status_string", "gbdlt_launch_count", "gbdlt_device_alloc_count"):
                 getattr(L, name).restype = i32
         L.gbdlt_plan_profile_read.restype = i64
         _lib = L
@@ -155,6 +157,11 @@ def plan_params(N: int, prec: int = FP64, eps: float = 0.0, method: int = METHOD
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(lib().gbdlt_launch_count())
+
+
+def device_alloc_count() -> int:
+    """Device allocations (cudaMalloc calls) the library has made since it was loaded."""
+    return int(lib().gbdlt_device_alloc_count())
 
 
 def _dtype(prec: int):
@@ -206,6 +213,10 @@ class Plan:
 
     def sync(self):
         _check(lib().gbdlt_plan_sync(self._h), "plan_sync")
+
+    def set_node_iterations(self, max_iter: int):
+        """Cap the Newton iterations of later legpts() calls (0..24; 24 is the default)."""
+        _check(lib().gbdlt_plan_set_node_iterations(self._h, int(max_iter)), "set_node_iterations")
 
     def set_stream(self, stream):
         self.stream = stream

@@ -242,10 +242,10 @@ extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs
     b->groups.push_back(g);
   }
   // device tables and staging
-  if (cudaMalloc(&b->d_src, sizeof(int64_t) * 3 * (size_t)B) != cudaSuccess) return fail(GBDLT_ERR_OOM);
+  if (dev_malloc((void**)&b->d_src, sizeof(int64_t) * 3 * (size_t)B) != cudaSuccess) return fail(GBDLT_ERR_OOM);
   b->d_stage = b->d_src + B;
   b->d_len = b->d_src + 2 * B;
-  if (cudaMalloc(&b->stage_in, 2 * es * (size_t)b->total) != cudaSuccess) return fail(GBDLT_ERR_OOM);
+  if (dev_malloc((void**)&b->stage_in, 2 * es * (size_t)b->total) != cudaSuccess) return fail(GBDLT_ERR_OOM);
   b->stage_out = (char*)b->stage_in + es * (size_t)b->total;
   if (cudaMemcpy(b->d_src, src.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_stage, stage.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||

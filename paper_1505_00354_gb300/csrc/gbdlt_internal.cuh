@@ -266,6 +266,10 @@ struct RecLayout {
   double* rscratch = nullptr; // [ceil(nblocks/64)][n_heavy] chunk sums of the transposed reduction
 };
 
+// Newton iterations a node may take before the node kernels flag it as not
+// converged (the cap a plan uses unless gbdlt_plan_set_node_iterations lowers it)
+constexpr int kNodeIterMax = 24;
+
 struct Plan {
   Params p;
   int device = 0;
@@ -336,6 +340,7 @@ struct Plan {
   void* tmp = nullptr;   // [N]
   void* tmp2 = nullptr;  // [N]
   int* status = nullptr; // device status word
+  int node_iter_max = kNodeIterMax;  // Newton iterations a node may take (legpts.cu)
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel
@@ -394,6 +399,8 @@ int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out
 // ---------------------------------------------------------------------------
 void count_launch(int n = 1);
 int check_launch();  // GBDLT_OK or GBDLT_ERR_CUDA after a launch
+// cudaMalloc that counts the library's device allocations (gbdlt_device_alloc_count)
+cudaError_t dev_malloc(void** p, size_t bytes);
 // Counts one launch and, when the plan's profiler is on, records an event after
 // it tagged with the kernel name and its algorithmic flops and bytes.
 void launched(Plan& P, const char* name, double flops, double bytes);

@@ -34,7 +34,6 @@
 // theta*_k - theta^cheb1_k = pi (N-2k-1) / (4N(N+1/2)) plus delta, so it keeps
 // full relative accuracy).
 #include <cmath>
-#include <mutex>
 
 #include "gbdlt_internal.cuh"
 
@@ -112,7 +111,7 @@ __device__ PD eval_asy(double Nh, int64_t k, double d, double s, double c, doubl
 // nodes k >= kend (k < kend: k_legpts_ends)
 __global__ void k_legpts(int64_t N, int64_t kend, double CN, HTab H, double* __restrict__ theta,
                          double* __restrict__ x, double* __restrict__ w, double* __restrict__ tN,
-                         int* __restrict__ status) {
+                         int* __restrict__ status, int max_iter) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t half = (N + 1) / 2;
   if (k >= half || k < kend) return;
@@ -130,7 +129,7 @@ __global__ void k_legpts(int64_t N, int64_t kend, double CN, HTab H, double* __r
   bool ok = false;
   PD r;
   double s = s0, c = c0, sh = 0, ch = 0, dp_final = 0.0;
-  for (int it = 0; it < 24; ++it) {
+  for (int it = 0; it < max_iter; ++it) {
     // sin/cos of theta = th0 + d by the angle-addition formula; |d| <= 1/(3 pi (2N+1))
     // (Lemma 2.3), so the Taylor polynomials below are exact to < 1e-20
     const double d2 = d * d;
@@ -249,7 +248,7 @@ __device__ PD eval_series_warp(int64_t N, double sh, double ch, int lane) {
 // one warp per node k < kend (N sin theta*_k < 25, N > 64)
 __global__ void __launch_bounds__(32) k_legpts_ends(int64_t N, double* __restrict__ theta, double* __restrict__ x,
                                                     double* __restrict__ w, double* __restrict__ tN,
-                                                    int* __restrict__ status) {
+                                                    int* __restrict__ status, int max_iter) {
   const int64_t k = blockIdx.x;
   const int lane = threadIdx.x;
   const double Nh = (double)N + 0.5;
@@ -258,7 +257,7 @@ __global__ void __launch_bounds__(32) k_legpts_ends(int64_t N, double* __restric
   double d = kJ0Zeros[k] * inv_Nh - th0;
   bool ok = false;
   double s = 0.0, c = 1.0, dp_final = 0.0;
-  for (int it = 0; it < 24; ++it) {
+  for (int it = 0; it < max_iter; ++it) {
     double sh, ch;
     sincos(0.5 * (th0 + d), &sh, &ch);
     s = 2.0 * sh * ch;
@@ -303,7 +302,8 @@ int64_t end_nodes(int64_t N) {
 
 __global__ void k_dtheta(const double* __restrict__ tN, double* __restrict__ out, int64_t N) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < N) out[k] = tN[k] / (double)N;  // exact: N is a power of two
+  // exact for N a power of two (the FFT-based chain), correctly rounded otherwise
+  if (k < N) out[k] = tN[k] / (double)N;
 }
 
 // h_{0,N} = 1, h_{m+1,N} = h_{m,N} (m+1/2)^2 / ((m+1)(N+m+3/2))
@@ -317,15 +317,15 @@ HTab htab(int64_t N) {
 
 // the node kernels on `stream` (callers count the launches)
 void launch_main_nodes(int64_t N, int64_t kend, double CN, double* theta, double* x, double* w, double* tN,
-                       int* status, cudaStream_t stream) {
+                       int* status, cudaStream_t stream, int max_iter = kNodeIterMax) {
   const int64_t half = (N + 1) / 2;
   const int threads = 128;
   k_legpts<<<(unsigned)((half + threads - 1) / threads), threads, 0, stream>>>(N, kend, CN, htab(N), theta, x, w,
-                                                                               tN, status);
+                                                                               tN, status, max_iter);
 }
 void launch_end_nodes(int64_t N, int64_t kend, double* theta, double* x, double* w, double* tN, int* status,
-                      cudaStream_t stream) {
-  if (kend > 0) k_legpts_ends<<<(unsigned)kend, 32, 0, stream>>>(N, theta, x, w, tN, status);
+                      cudaStream_t stream, int max_iter = kNodeIterMax) {
+  if (kend > 0) k_legpts_ends<<<(unsigned)kend, 32, 0, stream>>>(N, theta, x, w, tN, status, max_iter);
 }
 
 }  // namespace
@@ -340,10 +340,10 @@ int launch_dtheta(Plan& P, double* out) {
 int launch_legpts(Plan& P, double CN) {
   const int64_t N = P.p.N;
   const int64_t kend = end_nodes(N);
-  launch_main_nodes(N, kend, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream);
+  launch_main_nodes(N, kend, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max);
   launched(P, "legpts", 0.0, 32.0 * N);
   if (kend > 0) {
-    launch_end_nodes(N, kend, P.theta, P.x, P.w, P.tN, P.status, P.stream);
+    launch_end_nodes(N, kend, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max);
     launched(P, "legpts_ends", 0.0, 64.0 * kend);
   }
   return check_launch();
@@ -373,29 +373,19 @@ constexpr int64_t kNoAllocMaxN = 65536;
 // 512 KB per GPU that loads the library, held until the process exits.
 static __device__ __align__(256) double g_legpts_scratch[kNoAllocMaxN + 32];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device; looked up once per
-// device with that device current (a host-side reference to the symbol is not
-// a device address).
+// Device address of the scratch array in the current device's context.  Looked
+// up on every call with that device current: a host-side reference to the
+// symbol is not a device address, and an address kept from an earlier call
+// would dangle once the context is destroyed (cudaDeviceReset, or the primary
+// context released and made again), because the array then lives in the newly
+// loaded module.  Once the module is loaded the lookup is a host-side query.
 int scratch_on_current_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_legpts_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
     return GBDLT_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_legpts_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return GBDLT_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = (double*)p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = (double*)p;
   return GBDLT_OK;
 }
 

@@ -25,7 +25,12 @@
 namespace gbdlt {
 
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_allocs{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return cudaMalloc(p, bytes);
+}
 static uint64_t launches_now() { return g_launches.load(std::memory_order_relaxed); }
 static void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 int check_launch() {
@@ -762,7 +767,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   size_t o_tmp2 = bytes_block((size_t)BC * N * ts);
   size_t o_status = A.take<int>(1);
   P->ws_bytes = A.off;
-  if (cudaMalloc(&P->arena, A.off) != cudaSuccess) {
+  if (dev_malloc(&P->arena, A.off) != cudaSuccess) {
     cudaGetLastError();
     free_plan(P);
     return GBDLT_ERR_OOM;
@@ -1554,6 +1559,12 @@ int gbdlt_plan_set_stream(gbdlt_plan plan, void* cuda_stream) {
   return GBDLT_OK;
 }
 
+int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter) {
+  if (!plan || max_iter < 0 || max_iter > kNodeIterMax) return GBDLT_ERR_INVALID_ARG;
+  reinterpret_cast<Plan*>(plan)->node_iter_max = max_iter;
+  return GBDLT_OK;
+}
+
 int gbdlt_plan_sync(gbdlt_plan plan) {
   if (!plan) return GBDLT_ERR_INVALID_ARG;
   Plan* P = reinterpret_cast<Plan*>(plan);
@@ -1628,5 +1639,6 @@ const char* gbdlt_status_string(int s) {
 }
 
 uint64_t gbdlt_launch_count(void) { return g_launches.load(); }
+uint64_t gbdlt_device_alloc_count(void) { return g_allocs.load(); }
 
 }  // extern "C"

@@ -610,7 +610,7 @@ int launch_rec_xm1(Plan& P, RecLayout& L, int legendre) {
 int launch_rec_state_init(Plan& P, RecLayout& L) {
   if (L.H == 0 || L.nseg_total == 0) return GBDLT_OK;
   double2* Tbuf = nullptr;
-  if (cudaMalloc(&Tbuf, sizeof(double2) * 2 * (size_t)L.nseg_total) != cudaSuccess) {
+  if (dev_malloc((void**)&Tbuf, sizeof(double2) * 2 * (size_t)L.nseg_total) != cudaSuccess) {
     cudaGetLastError();
     return GBDLT_ERR_OOM;
   }
