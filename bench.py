@@ -18,9 +18,11 @@ end-to-end number through the public API with host buffers, and the oracle timed
 on the host cores on a bounded sample (cpu_baseline).
 
 Reference arm (--impl reference): there is no reference implementation to run;
-the baseline is the CPU oracle itself (double-double direct sums), timed on a
-bounded sample of the same workload per step and extrapolated to the full
-transform.
+the baseline is the CPU oracle's plain FP64 direct method (nodes by Newton on
+the FP64 recurrence, Eq. 1 and Eq. 2 by the recurrence in double, OpenMP over
+rows), timed on a bounded sample of the same workload per step and
+extrapolated to the full transform.  The double-double oracle is used for
+accuracy only.
 
 Multi-GPU: the path does not shard; N > 1 runs independent replicas (one per
 rank) and reports the whole-job rate.
@@ -35,6 +37,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -145,12 +148,12 @@ class ClockSampler:
         self.uuid = uuid
         self.proc = None
         self.t0 = self.t1 = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="gbdlt_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         """Start sampling and wait (up to 5 s) for the first sample."""
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -189,7 +192,12 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         with open(self.path) as fh:
-            return summarize_clocks(fh, self.uuid, self.t0 if self.t0 is not None else 0.0, self.t1)
+            res = summarize_clocks(fh, self.uuid, self.t0 if self.t0 is not None else 0.0, self.t1)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return res
 
 
 def summarize_clocks(lines, uuid: str | None, t0: float, t1: float) -> dict | None:
@@ -568,15 +576,20 @@ def sweep(stream, flush, check=True):
 # CPU oracle timing (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
 def oracle_sample(N, c, rows):
-    """The oracle's work for the listed rows of one DLT + IDLT: the nodes
-    (Newton on the recurrence), the DLT row sums and the rows' IDLT
-    contributions; returns seconds."""
+    """The plain FP64 direct method's work for the listed rows of one DLT +
+    IDLT: the nodes (Newton on the FP64 recurrence), the DLT row sums (Eq. 1)
+    and the rows' contributions to the IDLT (Eq. 2); returns seconds."""
     import oracle
     t0 = time.perf_counter()
-    nd = oracle.legpts(N, rows)
-    f = oracle.dlt_rows(c, nd)
-    oracle.idlt_rows(f, nd, N)
+    nd = oracle.legpts_f64(N, rows)
+    f = oracle.dlt_rows_f64(c, nd["x"])
+    oracle.idlt_rows_f64(f, nd["x"], nd["w"], N)
     return time.perf_counter() - t0
+
+
+BASELINE_KIND = ("plain FP64 direct method (oracle/): nodes by Newton on the FP64 three-term recurrence, "
+                 "Eq. 1 and Eq. 2 row sums by the recurrence in double, OpenMP over rows; the "
+                 "double-double oracle is used for accuracy only")
 
 
 def cpu_baseline(N, c, target_s=15.0):
@@ -590,8 +603,9 @@ def cpu_baseline(N, c, target_s=15.0):
     t = oracle_sample(N, c, rows)
     t_full = t * N / rows.size
     return {"value": round(2.0 / t_full, 8), "unit": "transforms/s", "cores": cores, "kind": "oracle",
-            "sample": f"{rows.size} of {N} rows of one DLT+IDLT (double-double nodes, row sums, row "
-                      f"contributions to the IDLT) in {t:.1f} s, extrapolated x{N / rows.size:.0f}"}
+            "method": BASELINE_KIND,
+            "sample": f"{rows.size} of {N} rows of one DLT+IDLT (FP64 nodes, row sums, row contributions "
+                      f"to the IDLT) in {t:.1f} s, extrapolated x{N / rows.size:.0f}"}
 
 
 def run_reference(args, world, rank):
@@ -602,7 +616,10 @@ def run_reference(args, world, rank):
     N = args.n
     c = inputs.coeffs(N, 20 + int(math.log2(N)))
     cores = oracle.num_threads()
-    nrows = max(cores, 2 * cores)
+    # rows per step: about 2 s of host work per step, so that W + K steps end in
+    # a few minutes (one probe step sizes it)
+    t_probe = oracle_sample(N, c, inputs.sample_rows(N, cores, seed=99, include_ends=0))
+    nrows = int(min(N, max(cores, cores * round(2.0 / max(t_probe, 1e-3)))))
     ts = []
     for i in range(args.warmup + args.steps):
         rows = inputs.sample_rows(N, nrows, seed=100 + i, include_ends=0)
@@ -613,11 +630,12 @@ def run_reference(args, world, rank):
     value = 2.0 / t_full
     return {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "transforms/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "dd (f64 pairs)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded c_n ~ N(0,1), numpy PCG64)",
             "config": workload_config(N, world),
             "timing": "host wall clock of the CPU oracle on sampled rows, extrapolated to all N rows",
             "cpu_baseline": {"value": round(value, 8), "unit": "transforms/s", "cores": cores, "kind": "oracle",
+                             "method": BASELINE_KIND,
                              "sample": f"{nrows} of {N} rows per step, extrapolated x{N / nrows:.0f}"},
             "e2e": {"value": round(value, 8), "unit": "transforms/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

@@ -69,6 +69,10 @@ def _load():
         lib.orc_leg2cheb.argtypes = [i64, _D, _D]
         lib.orc_leg2cheb_t.argtypes = [i64, _D, _D]
         lib.orc_leg2cheb_matrix.argtypes = [i64, _D]
+        lib.orc_legpts_f64.argtypes = [i64, _I64, i64, _D, _D, _D]
+        lib.orc_legpts_f64.restype = i64
+        lib.orc_dlt_rows_f64.argtypes = [i64, _D, i64, _D, _D]
+        lib.orc_idlt_rows_f64.argtypes = [i64, _D, i64, _D, _D, _D]
         lib.orc_two_prod.argtypes = [d, d, _D, _D]
         lib.orc_two_sum.argtypes = [d, d, _D, _D]
         lib.orc_dd_div.argtypes = [d, d, d, d, _D, _D]
@@ -244,6 +248,41 @@ def leg2cheb_matrix(N: int) -> np.ndarray:
     m = np.empty((N, N))
     _load().orc_leg2cheb_matrix(N, _dp(m))
     return m
+
+
+# --------------------------------------------------------------------------
+# plain FP64 direct method (the timed CPU baseline; the dd functions above are
+# the reference for accuracy)
+# --------------------------------------------------------------------------
+def legpts_f64(N: int, ks=None) -> dict:
+    """Nodes (theta ascending), x and weights by Newton in double on the FP64
+    recurrence; raises if a node did not settle."""
+    ks = np.arange(N, dtype=np.int64) if ks is None else np.ascontiguousarray(ks, dtype=np.int64)
+    out = {k: np.empty(ks.size) for k in ("theta", "x", "w")}
+    bad = _load().orc_legpts_f64(N, ks.ctypes.data_as(_I64), ks.size, _dp(out["theta"]), _dp(out["x"]),
+                                 _dp(out["w"]))
+    if bad:
+        raise RuntimeError(f"oracle legpts_f64: {bad} node(s) did not settle (N={N})")
+    out["k"] = ks
+    out["N"] = N
+    return out
+
+
+def dlt_rows_f64(c, x) -> np.ndarray:
+    """Eq. 1 at the nodes x, every operation in double."""
+    c, x = _f64(c), _f64(x)
+    f = np.empty(x.size)
+    _load().orc_dlt_rows_f64(c.size, _dp(c), x.size, _dp(x), _dp(f))
+    return f
+
+
+def idlt_rows_f64(f_rows, x, w, N: int) -> np.ndarray:
+    """The rows' contribution to Eq. 2, every operation in double; summed over
+    all N rows it is the plain FP64 IDLT."""
+    f_rows, x, w = _f64(f_rows), _f64(x), _f64(w)
+    out = np.empty(N)
+    _load().orc_idlt_rows_f64(N, _dp(f_rows), f_rows.size, _dp(x), _dp(w), _dp(out))
+    return out
 
 
 # --------------------------------------------------------------------------

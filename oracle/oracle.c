@@ -37,6 +37,15 @@
  *   orc_leg2cheb_t   M^T y
  *   orc_cos_dd       cos/sin of a dd angle (argument reduction by dd pi/2 and
  *                    Taylor series), used for x_k = cos(theta_k)
+ *   orc_legpts_f64,  the plain FP64 direct method (no double-double anywhere):
+ *   orc_dlt_rows_f64, nodes by Newton on P_N from the cheb* point, Eq. 1 rows
+ *   orc_idlt_rows_f64 and the rows' contributions to Eq. 2, every sum by the
+ *                    three-term recurrence in double.  This is the baseline the
+ *                    GPU path is timed against (the paper's direct approach,
+ *                    Sec. 2.4 and Sec. 4.1); its error grows like N^2 u near
+ *                    x = +-1 (the rounding of x_k alone moves P_n by up to
+ *                    n^2 u / 2 there), so the dd functions above stay the
+ *                    reference for accuracy.
  *
  * Reading of the matrix M (Sec. 3): with Lambda(z) = Gamma(z+1/2)/Gamma(z+1),
  *   M_{0n} = (1/pi) Lambda(n/2)^2                       n even,
@@ -576,6 +585,107 @@ void orc_leg2cheb_t(int64_t N, const double* y, double* out) {
     out[n] = acc.hi + acc.lo;
   }
   free(lam);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plain FP64 direct method (the timed CPU baseline)                        */
+/* ------------------------------------------------------------------------ */
+/* P_N(x) and P_{N-1}(x) by (m+1) P_{m+1} = (2m+1) x P_m - m P_{m-1} in double. */
+static void legendre_pair_f64(int64_t N, double x, double* pn, double* pnm1) {
+  double pm1 = 0.0, p = 1.0;
+  for (int64_t m = 0; m < N; ++m) {
+    double next = ((double)(2 * m + 1) * x * p - (double)m * pm1) / (double)(m + 1);
+    pm1 = p;
+    p = next;
+  }
+  *pn = p;
+  *pnm1 = pm1;
+}
+
+/* Nodes and weights in double: Newton in theta on P_N(cos theta) from the
+ * cheb* point (k+3/4)pi/(N+1/2) (Sec. 2.2), derivative dP_N/dtheta =
+ * -N (P_{N-1} - x P_N)/sin(theta).  Lemma 2.3 puts the start within
+ * 1/(3 pi (2N+1)) of the root, about 1/60 of the node spacing ~pi/N, and Newton
+ * converges quadratically from there (errors ~1e-2, 1e-4, 1e-8, 1e-16 of the
+ * spacing), so five steps reach the rounding floor of the double recurrence
+ * (near x = +-1 that floor is about N^2 u of the spacing).  A node whose fifth
+ * step is still above 1e-6 of the spacing did not settle.  w = 2/(dP_N/dtheta)^2
+ * at the final iterate.  Returns the number of nodes that did not settle. */
+int64_t orc_legpts_f64(int64_t N, const int64_t* ks, int64_t nk, double* theta, double* x, double* w) {
+  int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+  for (int64_t i = 0; i < nk; ++i) {
+    double th = ((double)ks[i] + 0.75) * M_PI / ((double)N + 0.5);
+    double step = 0.0;
+    for (int it = 0; it < 5; ++it) {
+      double pn, pnm1;
+      double c = cos(th), s = sin(th);
+      legendre_pair_f64(N, c, &pn, &pnm1);
+      double dp = -(double)N * (pnm1 - c * pn) / s;
+      step = pn / dp;
+      th -= step;
+    }
+    double pn, pnm1;
+    double c = cos(th), s = sin(th);
+    legendre_pair_f64(N, c, &pn, &pnm1);
+    double dp = -(double)N * (pnm1 - c * pn) / s;
+    if (!(fabs(step) * (double)N <= 1e-6)) bad += 1;
+    if (theta) theta[i] = th;
+    if (x) x[i] = c;
+    if (w) w[i] = 2.0 / (dp * dp);
+  }
+  return bad;
+}
+
+/* Eq. 1 at the given rows, in double: f_i = sum_n c_n P_n(x_i). */
+void orc_dlt_rows_f64(int64_t N, const double* c, int64_t nk, const double* x, double* f) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < nk; ++i) {
+    double pm1 = 0.0, p = 1.0, acc = 0.0;
+    for (int64_t m = 0; m < N; ++m) {
+      acc += c[m] * p;
+      double next = ((double)(2 * m + 1) * x[i] * p - (double)m * pm1) / (double)(m + 1);
+      pm1 = p;
+      p = next;
+    }
+    f[i] = acc;
+  }
+}
+
+/* The given rows' contribution to Eq. 2, in double:
+ * out_n = (n+1/2) sum_i w_i f_i P_n(x_i).  Each thread sums its rows into its
+ * own length-N vector; the vectors are added at the end. */
+void orc_idlt_rows_f64(int64_t N, const double* f, int64_t nk, const double* x, const double* w, double* out) {
+  int nthr = 1;
+#ifdef _OPENMP
+  nthr = omp_get_max_threads();
+#endif
+  double* acc = (double*)calloc((size_t)nthr * (size_t)N, sizeof(double));
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* my = acc + (size_t)tid * (size_t)N;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nk; ++i) {
+      double g = w[i] * f[i];
+      double pm1 = 0.0, p = 1.0;
+      for (int64_t m = 0; m < N; ++m) {
+        my[m] += g * p;
+        double next = ((double)(2 * m + 1) * x[i] * p - (double)m * pm1) / (double)(m + 1);
+        pm1 = p;
+        p = next;
+      }
+    }
+  }
+  for (int64_t m = 0; m < N; ++m) {
+    double s = 0.0;
+    for (int t = 0; t < nthr; ++t) s += acc[(size_t)t * (size_t)N + m];
+    out[m] = s * ((double)m + 0.5);
+  }
+  free(acc);
 }
 
 /* ------------------------------------------------------------------------ */

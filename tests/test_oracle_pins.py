@@ -364,3 +364,90 @@ def test_table1_values():
             ulp = 10.0 ** (math.floor(math.log10(printed)) - 1)
             assert abs(val - printed) <= 1.01 * ulp, (L, printed, val)
     assert round((3 * math.pi**2 + 2) / (12 * math.pi), 5) == 0.83845
+
+
+# --------------------------------------------------------------------------
+# plain FP64 direct method (the timed CPU baseline)
+# --------------------------------------------------------------------------
+U64 = 2.0**-53
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_f64_legpts_closed_forms(orc, N):
+    """Nodes and weights of the FP64 Newton solve against the closed forms."""
+    closed = {2: ([1 / math.sqrt(3), -1 / math.sqrt(3)], [1.0, 1.0]),
+              3: ([math.sqrt(0.6), 0.0, -math.sqrt(0.6)], [5 / 9, 8 / 9, 5 / 9]),
+              5: ([math.sqrt(5 + 2 * math.sqrt(10 / 7)) / 3, math.sqrt(5 - 2 * math.sqrt(10 / 7)) / 3, 0.0,
+                   -math.sqrt(5 - 2 * math.sqrt(10 / 7)) / 3, -math.sqrt(5 + 2 * math.sqrt(10 / 7)) / 3],
+                  [(322 - 13 * math.sqrt(70)) / 900, (322 + 13 * math.sqrt(70)) / 900, 128 / 225,
+                   (322 + 13 * math.sqrt(70)) / 900, (322 - 13 * math.sqrt(70)) / 900])}
+    nd = orc.legpts_f64(N)
+    x, w = closed[N]
+    assert np.max(np.abs(nd["x"] - x)) <= 4 * U64
+    assert np.max(np.abs(nd["w"] - w)) <= 16 * U64
+
+
+@pytest.mark.parametrize("N", [7, 64, 255, 1000])
+def test_f64_legpts_vs_scipy_and_dd(orc, N):
+    """The FP64 solve against scipy's nodes and the dd oracle: x to a few u,
+    theta to N u, w to N^2 u relative (x_k rounded to double moves P'_N by up to
+    N^2 u near the ends, which is the plain FP64 method's error, not a defect).
+    scipy's weights are not used: they differ from the mpmath-pinned dd weights
+    by ~1e-8 at N = 1000."""
+    sp = pytest.importorskip("scipy.special")
+    nd = orc.legpts_f64(N)
+    xs, _ = sp.roots_legendre(N)
+    assert np.max(np.abs(nd["x"] - xs[::-1])) <= 1e-14
+    dd = orc.legpts(N)
+    assert np.max(np.abs(nd["x"] - dd.x)) <= 4 * U64
+    assert np.max(np.abs(nd["theta"] - dd.theta)) <= (N + 16) * U64
+    assert np.max(np.abs(nd["w"] - dd.w) / dd.w) <= (N * N + 64) * U64
+    assert np.all(np.diff(nd["theta"]) > 0)
+
+
+def test_f64_dlt_unit_vectors(orc):
+    """c = e_n gives P_n at the nodes (scipy's Legendre values); c = e_0 gives 1."""
+    sp = pytest.importorskip("scipy.special")
+    N = 200
+    x = orc.legpts_f64(N)["x"]
+    for n in (0, 1, 2, 17, 100, N - 1):
+        c = np.zeros(N)
+        c[n] = 1.0
+        f = orc.dlt_rows_f64(c, x)
+        assert np.max(np.abs(f - sp.eval_legendre(n, x))) <= (n * n + 16) * U64
+    c = np.zeros(N)
+    c[0] = 1.0
+    assert np.all(orc.dlt_rows_f64(c, x) == 1.0)
+
+
+@pytest.mark.parametrize("N", [16, 512, 4096])
+def test_f64_direct_vs_dd(orc, N):
+    """Eq. 1 and Eq. 2 in plain FP64 against the dd oracle on the same (dd)
+    nodes, within the FP64 method's bound N^2 u (the sensitivity of P_n to the
+    rounding of x_k, |P'_n| <= n(n+1)/2, dominates the recurrence's own rounding)."""
+    r = np.random.default_rng(N)
+    c = r.standard_normal(N)
+    nd = orc.legpts(N)
+    f_dd = orc.dlt_rows(c, nd)
+    f_64 = orc.dlt_rows_f64(c, nd.x)
+    assert np.max(np.abs(f_64 - f_dd)) <= N * N * U64 * np.abs(c).sum()
+    c_dd = orc.idlt(f_dd, nd)
+    c_64 = orc.idlt_rows_f64(f_dd, nd.x, nd.w, N)
+    scale = (np.arange(N) + 0.5) * np.abs(nd.w * f_dd).sum()
+    assert np.max(np.abs(c_64 - c_dd) / scale) <= N * N * U64
+
+
+@pytest.mark.parametrize("N", [8, 333, 2048])
+def test_f64_direct_roundtrip(orc, N):
+    """IDLT(DLT(c)) = c with the FP64 method's own nodes and weights, and the
+    row partition: contributions of disjoint row sets add up to the whole."""
+    r = np.random.default_rng(7 * N)
+    c = r.standard_normal(N)
+    nd = orc.legpts_f64(N)
+    f = orc.dlt_rows_f64(c, nd["x"])
+    back = orc.idlt_rows_f64(f, nd["x"], nd["w"], N)
+    assert np.max(np.abs(back - c)) <= N * N * U64 * np.abs(c).sum()
+    half = N // 2
+    a = orc.idlt_rows_f64(f[:half], nd["x"][:half], nd["w"][:half], N)
+    b = orc.idlt_rows_f64(f[half:], nd["x"][half:], nd["w"][half:], N)
+    assert np.max(np.abs(a + b - back)) <= 64 * U64 * np.abs(back).max() + 1e-300
