@@ -56,6 +56,7 @@ def _load():
         lib = ctypes.CDLL(build())
         i64, d = ctypes.c_int64, ctypes.c_double
         lib.orc_legendre_p.argtypes = [i64, _D, i64, _D]
+        lib.orc_legendre_p_dd.argtypes = [i64, _D, _D, i64, _D]
         lib.orc_chebyshev_t.argtypes = [i64, _D, i64, _D]
         lib.orc_sincos_dd.argtypes = [d, d, _D, _D, _D, _D]
         lib.orc_legpts.argtypes = [i64, _I64, i64, _D, _D, _D, _D, _D, _D, _D]
@@ -69,6 +70,10 @@ def _load():
         lib.orc_leg2cheb.argtypes = [i64, _D, _D]
         lib.orc_leg2cheb_t.argtypes = [i64, _D, _D]
         lib.orc_leg2cheb_matrix.argtypes = [i64, _D]
+        lib.orc_dlt_t_rows.argtypes = [i64, _D, i64, _D, _D, _D]
+        lib.orc_ndct_t_rows.argtypes = [i64, _D, i64, _D, _D, _D]
+        lib.orc_leg2cheb_rows.argtypes = [i64, _D, _I64, i64, _D]
+        lib.orc_leg2cheb_t_rows.argtypes = [i64, _D, _I64, i64, _D]
         lib.orc_legpts_f64.argtypes = [i64, _I64, i64, _D, _D, _D]
         lib.orc_legpts_f64.restype = i64
         lib.orc_dlt_rows_f64.argtypes = [i64, _D, i64, _D, _D]
@@ -102,6 +107,14 @@ def legendre_p(n: int, x) -> np.ndarray:
     x = _f64(x).ravel()
     out = np.empty_like(x)
     _load().orc_legendre_p(n, _dp(x), x.size, _dp(out))
+    return out
+
+
+def legendre_p_at(n: int, nodes) -> np.ndarray:
+    """P_n at the double-double points held in ``nodes`` (x_hi + x_lo)."""
+    xh, xl = _f64(nodes["x_hi"]).ravel(), _f64(nodes["x_lo"]).ravel()
+    out = np.empty_like(xh)
+    _load().orc_legendre_p_dd(n, _dp(xh), _dp(xl), xh.size, _dp(out))
     return out
 
 
@@ -241,6 +254,43 @@ def leg2cheb_t(y) -> np.ndarray:
     y = _f64(y)
     out = np.empty_like(y)
     _load().orc_leg2cheb_t(y.size, _dp(y), _dp(out))
+    return out
+
+
+def dlt_t_rows(g_rows, nodes: Nodes, N: int) -> np.ndarray:
+    """(P^T g)_n for n < N when g vanishes off the rows held in ``nodes``
+    (g_rows are its values there)."""
+    g_rows = _f64(g_rows)
+    out = np.empty(N)
+    _load().orc_dlt_t_rows(N, _dp(g_rows), g_rows.size, _dp(_f64(nodes["x_hi"])), _dp(_f64(nodes["x_lo"])),
+                           _dp(out))
+    return out
+
+
+def ndct_t_rows(g_rows, nodes: Nodes, N: int) -> np.ndarray:
+    """(T^T g)_n for n < N when g vanishes off the rows held in ``nodes``."""
+    g_rows = _f64(g_rows)
+    out = np.empty(N)
+    _load().orc_ndct_t_rows(N, _dp(g_rows), g_rows.size, _dp(_f64(nodes["x_hi"])), _dp(_f64(nodes["x_lo"])),
+                            _dp(out))
+    return out
+
+
+def leg2cheb_rows(c, ks) -> np.ndarray:
+    """(M c)_k at the listed k."""
+    c = _f64(c)
+    ks = np.ascontiguousarray(ks, dtype=np.int64)
+    out = np.empty(ks.size)
+    _load().orc_leg2cheb_rows(c.size, _dp(c), ks.ctypes.data_as(_I64), ks.size, _dp(out))
+    return out
+
+
+def leg2cheb_t_rows(y, ns) -> np.ndarray:
+    """(M^T y)_n at the listed n."""
+    y = _f64(y)
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    out = np.empty(ns.size)
+    _load().orc_leg2cheb_t_rows(y.size, _dp(y), ns.ctypes.data_as(_I64), ns.size, _dp(out))
     return out
 
 

@@ -35,6 +35,10 @@
  *                    read with the Lambda-product entries (the printed
  *                    entries drop two Gamma factors; see the reading below)
  *   orc_leg2cheb_t   M^T y
+ *   *_rows variants  the same sums restricted to listed output indices
+ *                    (orc_leg2cheb_rows, orc_leg2cheb_t_rows) or to listed
+ *                    nodes (orc_dlt_t_rows, orc_ndct_t_rows: the transposes
+ *                    of an input that vanishes off those nodes)
  *   orc_cos_dd       cos/sin of a dd angle (argument reduction by dd pi/2 and
  *                    Taylor series), used for x_k = cos(theta_k)
  *   orc_legpts_f64,  the plain FP64 direct method (no double-double anywhere):
@@ -208,15 +212,34 @@ void orc_sincos_dd(double th_hi, double th_lo, double* s_hi, double* s_lo,
 /* ------------------------------------------------------------------------ */
 /* Legendre polynomials by the three-term recurrence (dd)                   */
 /* ------------------------------------------------------------------------ */
-/* Returns P_n(x) and P_{n-1}(x) (P_{-1} := 0).  Recurrence
- * (m+1) P_{m+1} = (2m+1) x P_m - m P_{m-1}. */
-static void legendre_pair_dd(int64_t n, dd x, dd* pn, dd* pnm1) {
+/* Coefficients of the recurrence (m+1) P_{m+1} = (2m+1) x P_m - m P_{m-1},
+ * written as P_{m+1} = alpha_m x P_m - beta_m P_{m-1} with
+ * alpha_m = (2m+1)/(m+1) and beta_m = m/(m+1) in dd, for m < n: entry 2m is
+ * alpha_m, entry 2m+1 is beta_m.  Tabulating them once per call replaces a dd
+ * division per step by two dd products (the same recurrence; results agree to
+ * the dd rounding).  The caller frees the table. */
+static dd* rec_coef(int64_t n) {
+  dd* t = (dd*)malloc(sizeof(dd) * (size_t)(2 * (n > 0 ? n : 1)));
+#pragma omp parallel for schedule(static)
+  for (int64_t m = 0; m < n; ++m) {
+    t[2 * m] = dd_div_d(dd_from((double)(2 * m + 1)), (double)(m + 1));
+    t[2 * m + 1] = dd_div_d(dd_from((double)m), (double)(m + 1));
+  }
+  return t;
+}
+
+/* One step of the recurrence: P_{m+1} from P_m and P_{m-1}. */
+static inline dd rec_step(const dd* coef, int64_t m, dd x, dd p, dd pm1) {
+  return dd_sub(dd_mul(dd_mul(x, p), coef[2 * m]), dd_mul(pm1, coef[2 * m + 1]));
+}
+
+/* Returns P_n(x) and P_{n-1}(x) (P_{-1} := 0) by the recurrence above; coef
+ * holds at least n coefficient pairs. */
+static void legendre_pair_dd(int64_t n, dd x, const dd* coef, dd* pn, dd* pnm1) {
   dd pm1 = dd_from(0.0);
   dd p = dd_from(1.0);
   for (int64_t m = 0; m < n; ++m) {
-    dd a = dd_mul_d(dd_mul(x, p), (double)(2 * m + 1));
-    dd b = dd_mul_d(pm1, (double)m);
-    dd next = dd_div_d(dd_sub(a, b), (double)(m + 1));
+    dd next = rec_step(coef, m, x, p, pm1);
     pm1 = p;
     p = next;
   }
@@ -226,12 +249,26 @@ static void legendre_pair_dd(int64_t n, dd x, dd* pn, dd* pnm1) {
 
 /* P_n at m double points (dd recurrence, rounded). */
 void orc_legendre_p(int64_t n, const double* x, int64_t m, double* out) {
+  dd* coef = rec_coef(n);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < m; ++i) {
     dd pn, pnm1;
-    legendre_pair_dd(n, dd_from(x[i]), &pn, &pnm1);
+    legendre_pair_dd(n, dd_from(x[i]), coef, &pn, &pnm1);
     out[i] = pn.hi + pn.lo;
   }
+  free(coef);
+}
+
+/* P_n at m dd points (x_hi + x_lo, e.g. the oracle's own nodes), rounded. */
+void orc_legendre_p_dd(int64_t n, const double* x_hi, const double* x_lo, int64_t m, double* out) {
+  dd* coef = rec_coef(n);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    dd pn, pnm1;
+    legendre_pair_dd(n, dd_make(x_hi[i], x_lo[i]), coef, &pn, &pnm1);
+    out[i] = pn.hi + pn.lo;
+  }
+  free(coef);
 }
 
 /* Chebyshev T_n at m double points by T_{j+1} = 2x T_j - T_{j-1} (dd). */
@@ -268,7 +305,7 @@ void orc_chebyshev_t(int64_t n, const double* x, int64_t m, double* out) {
  * of cos(theta)).  The weight is 2/(dP_N/dtheta)^2 evaluated
  * at the final theta.  Returns the number of dd iterations used, or -1 when the
  * iteration did not settle. */
-static int legpts_one(int64_t N, int64_t k, dd* theta_out, dd* x_out, dd* w_out) {
+static int legpts_one(int64_t N, int64_t k, const dd* coef, dd* theta_out, dd* x_out, dd* w_out) {
   double th = ((double)k + 0.75) * M_PI / ((double)N + 0.5);
   /* double-precision Newton (the recurrence in double) */
   for (int it = 0; it < 3; ++it) {
@@ -289,7 +326,7 @@ static int legpts_one(int64_t N, int64_t k, dd* theta_out, dd* x_out, dd* w_out)
     orc_sincos_dd(t.hi, t.lo, &sh, &sl, &ch, &cl);
     dd s = dd_make(sh, sl), x = dd_make(ch, cl);
     dd pn, pnm1;
-    legendre_pair_dd(N, x, &pn, &pnm1);
+    legendre_pair_dd(N, x, coef, &pn, &pnm1);
     dd dp = dd_div(dd_mul_d(dd_sub(pnm1, dd_mul(x, pn)), -(double)N), s);
     dd delta = dd_div(pn, dp);
     t = dd_sub(t, delta);
@@ -303,7 +340,7 @@ static int legpts_one(int64_t N, int64_t k, dd* theta_out, dd* x_out, dd* w_out)
   orc_sincos_dd(t.hi, t.lo, &sh, &sl, &ch, &cl);
   dd s = dd_make(sh, sl), x = dd_make(ch, cl);
   dd pn, pnm1;
-  legendre_pair_dd(N, x, &pn, &pnm1);
+  legendre_pair_dd(N, x, coef, &pn, &pnm1);
   dd dp = dd_div(dd_mul_d(dd_sub(pnm1, dd_mul(x, pn)), -(double)N), s);
   *w_out = dd_div(dd_from(2.0), dd_mul(dp, dp));
   *theta_out = t;
@@ -319,10 +356,11 @@ int64_t orc_legpts(int64_t N, const int64_t* ks, int64_t nk, double* th_hi,
                    double* th_lo, double* x_hi, double* x_lo, double* w_hi,
                    double* w_lo, double* dtheta) {
   int64_t bad = 0;
+  dd* coef = rec_coef(N);
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
   for (int64_t i = 0; i < nk; ++i) {
     dd th, x, w;
-    int used = legpts_one(N, ks[i], &th, &x, &w);
+    int used = legpts_one(N, ks[i], coef, &th, &x, &w);
     if (used < 0) bad += 1;
     if (th_hi) th_hi[i] = th.hi;
     if (th_lo) th_lo[i] = th.lo;
@@ -336,6 +374,7 @@ int64_t orc_legpts(int64_t N, const int64_t* ks, int64_t nk, double* th_hi,
       dtheta[i] = d.hi + d.lo;
     }
   }
+  free(coef);
   return bad;
 }
 
@@ -345,6 +384,7 @@ int64_t orc_legpts(int64_t N, const int64_t* ks, int64_t nk, double* th_hi,
 /* Eq. 1 at selected rows: f_i = sum_{n<N} c_n P_n(x_i) with x_i given in dd. */
 void orc_dlt_rows(int64_t N, const double* c, int64_t nk, const double* x_hi,
                   const double* x_lo, double* f) {
+  dd* coef = rec_coef(N);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t i = 0; i < nk; ++i) {
     dd x = dd_make(x_hi[i], x_lo[i]);
@@ -352,27 +392,30 @@ void orc_dlt_rows(int64_t N, const double* c, int64_t nk, const double* x_hi,
     dd acc = dd_from(0.0);
     for (int64_t m = 0; m < N; ++m) {
       acc = dd_add(acc, dd_mul_d(p, c[m]));
-      dd a = dd_mul_d(dd_mul(x, p), (double)(2 * m + 1));
-      dd b = dd_mul_d(pm1, (double)m);
-      dd next = dd_div_d(dd_sub(a, b), (double)(m + 1));
+      dd next = rec_step(coef, m, x, p, pm1);
       pm1 = p;
       p = next;
     }
     f[i] = acc.hi + acc.lo;
   }
+  free(coef);
 }
 
-/* (P^T g)_n = sum_k g_k P_n(x_k) over all N nodes (the transpose used in Sec. 4),
- * with optional per-node weights wk (dd; NULL = 1) and output scale by (n+1/2)
- * when scale_s is nonzero.  With the weights and scale this is the IDLT, Eq. 2.
- * Parallel over blocks of nodes with private dd accumulators. */
-static void dlt_t_impl(int64_t N, const double* g, const double* x_hi,
-                       const double* x_lo, const double* w_hi, const double* w_lo,
-                       int scale_s, double* out) {
+/* Transposed sums over a list of nodes (Sec. 4 matrix form):
+ * out_n = s_n sum_{i<nk} g_i w_i P_n(x_i) for n < N, with x_i (and the optional
+ * weights w_i; NULL = 1) in dd and s_n = n + 1/2 when scale_s is nonzero, else 1.
+ * Over all N nodes with weights and the scale it is the IDLT, Eq. 2; without
+ * them it is P^T g; over a subset of nodes it is the contribution of those rows
+ * (equivalently, the transform of an input that vanishes off them).  Each
+ * thread sums its rows into a private dd vector; the vectors are added in
+ * thread order at the end. */
+static void rows_t_impl(int64_t N, const double* g, int64_t nk, const double* x_hi, const double* x_lo,
+                        const double* w_hi, const double* w_lo, int scale_s, double* out) {
   int nthr = 1;
 #ifdef _OPENMP
   nthr = omp_get_max_threads();
 #endif
+  dd* coef = rec_coef(N);
   dd* acc = (dd*)calloc((size_t)nthr * (size_t)N, sizeof(dd));
 #pragma omp parallel
   {
@@ -381,17 +424,15 @@ static void dlt_t_impl(int64_t N, const double* g, const double* x_hi,
     tid = omp_get_thread_num();
 #endif
     dd* my = acc + (size_t)tid * (size_t)N;
-#pragma omp for schedule(dynamic, 4)
-    for (int64_t k = 0; k < N; ++k) {
-      dd x = dd_make(x_hi[k], x_lo[k]);
-      dd gk = dd_from(g[k]);
-      if (w_hi) gk = dd_mul(gk, dd_make(w_hi[k], w_lo ? w_lo[k] : 0.0));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nk; ++i) {
+      dd x = dd_make(x_hi[i], x_lo[i]);
+      dd gk = dd_from(g[i]);
+      if (w_hi) gk = dd_mul(gk, dd_make(w_hi[i], w_lo ? w_lo[i] : 0.0));
       dd pm1 = dd_from(0.0), p = dd_from(1.0);
       for (int64_t m = 0; m < N; ++m) {
         my[m] = dd_add(my[m], dd_mul(p, gk));
-        dd a = dd_mul_d(dd_mul(x, p), (double)(2 * m + 1));
-        dd b = dd_mul_d(pm1, (double)m);
-        dd next = dd_div_d(dd_sub(a, b), (double)(m + 1));
+        dd next = rec_step(coef, m, x, p, pm1);
         pm1 = p;
         p = next;
       }
@@ -404,58 +445,34 @@ static void dlt_t_impl(int64_t N, const double* g, const double* x_hi,
     out[m] = s.hi + s.lo;
   }
   free(acc);
+  free(coef);
 }
 
+/* (P^T g)_n = sum_k g_k P_n(x_k) over all N nodes. */
 void orc_dlt_t(int64_t N, const double* g, const double* x_hi, const double* x_lo,
                double* out) {
-  dlt_t_impl(N, g, x_hi, x_lo, NULL, NULL, 0, out);
+  rows_t_impl(N, g, N, x_hi, x_lo, NULL, NULL, 0, out);
+}
+
+/* The same over the listed nodes only: out_n = sum_{i<nk} g_i P_n(x_i), i.e.
+ * P^T of an input that is zero off those rows. */
+void orc_dlt_t_rows(int64_t N, const double* g, int64_t nk, const double* x_hi, const double* x_lo,
+                    double* out) {
+  rows_t_impl(N, g, nk, x_hi, x_lo, NULL, NULL, 0, out);
 }
 
 /* Contribution of a subset of rows to Eq. 2: out_n = (n+1/2) sum_{i<nk} w_i f_i
  * P_n(x_i) for the listed nodes (x_i, w_i in dd).  Summing it over a partition
- * of all N rows gives the IDLT; used to time the oracle on a sample of rows. */
+ * of all N rows gives the IDLT. */
 void orc_idlt_rows(int64_t N, const double* f, int64_t nk, const double* x_hi,
                    const double* x_lo, const double* w_hi, const double* w_lo, double* out) {
-  int nthr = 1;
-#ifdef _OPENMP
-  nthr = omp_get_max_threads();
-#endif
-  dd* acc = (dd*)calloc((size_t)nthr * (size_t)N, sizeof(dd));
-#pragma omp parallel
-  {
-    int tid = 0;
-#ifdef _OPENMP
-    tid = omp_get_thread_num();
-#endif
-    dd* my = acc + (size_t)tid * (size_t)N;
-#pragma omp for schedule(dynamic, 1)
-    for (int64_t i = 0; i < nk; ++i) {
-      dd x = dd_make(x_hi[i], x_lo[i]);
-      dd gk = dd_mul(dd_from(f[i]), dd_make(w_hi[i], w_lo[i]));
-      dd pm1 = dd_from(0.0), p = dd_from(1.0);
-      for (int64_t m = 0; m < N; ++m) {
-        my[m] = dd_add(my[m], dd_mul(p, gk));
-        dd a = dd_mul_d(dd_mul(x, p), (double)(2 * m + 1));
-        dd b = dd_mul_d(pm1, (double)m);
-        dd next = dd_div_d(dd_sub(a, b), (double)(m + 1));
-        pm1 = p;
-        p = next;
-      }
-    }
-  }
-  for (int64_t m = 0; m < N; ++m) {
-    dd s = dd_from(0.0);
-    for (int t = 0; t < nthr; ++t) s = dd_add(s, acc[(size_t)t * (size_t)N + m]);
-    s = dd_mul_d(s, (double)m + 0.5);
-    out[m] = s.hi + s.lo;
-  }
-  free(acc);
+  rows_t_impl(N, f, nk, x_hi, x_lo, w_hi, w_lo, 1, out);
 }
 
 /* Eq. 2: c_n = (n+1/2) sum_k w_k f_k P_n(x_k). */
 void orc_idlt(int64_t N, const double* f, const double* x_hi, const double* x_lo,
               const double* w_hi, const double* w_lo, double* c) {
-  dlt_t_impl(N, f, x_hi, x_lo, w_hi, w_lo, 1, c);
+  rows_t_impl(N, f, N, x_hi, x_lo, w_hi, w_lo, 1, c);
 }
 
 /* Eq. 3 at selected rows: f_i = sum_n c_n T_n(x_i), Chebyshev recurrence
@@ -484,9 +501,10 @@ void orc_ndct_rows(int64_t N, const double* c, int64_t nk, const double* x_hi,
   }
 }
 
-/* (T^T g)_n = sum_k g_k T_n(x_k) over all N nodes (Sec. 4 item 2). */
-void orc_ndct_t(int64_t N, const double* g, const double* x_hi, const double* x_lo,
-                double* out) {
+/* (T^T g)_n = sum_{i<nk} g_i T_n(x_i) for n < N over the listed nodes (Sec. 4
+ * item 2); over all N nodes it is the transposed NDCT. */
+void orc_ndct_t_rows(int64_t N, const double* g, int64_t nk, const double* x_hi, const double* x_lo,
+                     double* out) {
   int nthr = 1;
 #ifdef _OPENMP
   nthr = omp_get_max_threads();
@@ -499,8 +517,8 @@ void orc_ndct_t(int64_t N, const double* g, const double* x_hi, const double* x_
     tid = omp_get_thread_num();
 #endif
     dd* my = acc + (size_t)tid * (size_t)N;
-#pragma omp for schedule(dynamic, 4)
-    for (int64_t k = 0; k < N; ++k) {
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nk; ++k) {
       dd x = dd_make(x_hi[k], x_lo[k]);
       dd gk = dd_from(g[k]);
       dd tm1 = dd_from(1.0), t = dd_from(1.0);
@@ -525,6 +543,11 @@ void orc_ndct_t(int64_t N, const double* g, const double* x_hi, const double* x_
     out[m] = s.hi + s.lo;
   }
   free(acc);
+}
+
+void orc_ndct_t(int64_t N, const double* g, const double* x_hi, const double* x_lo,
+                double* out) {
+  orc_ndct_t_rows(N, g, N, x_hi, x_lo, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -561,30 +584,47 @@ void orc_leg2cheb_matrix(int64_t N, double* m) {
   free(lam);
 }
 
-/* chat = M c (Sec. 3, Eq. 14 context). */
-void orc_leg2cheb(int64_t N, const double* c, double* chat) {
+/* chat_k = sum_n M_{kn} c_n (Sec. 3, Eq. 14 context) for the listed k. */
+void orc_leg2cheb_rows(int64_t N, const double* c, const int64_t* ks, int64_t nk, double* chat) {
   dd* lam = lambda_table(N);
   dd inv_pi = dd_div(dd_from(1.0), dd_pi());
 #pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t k = 0; k < N; ++k) {
+  for (int64_t i = 0; i < nk; ++i) {
+    const int64_t k = ks[i];
     dd acc = dd_from(0.0);
     for (int64_t n = k; n < N; n += 2) acc = dd_add(acc, dd_mul_d(m_entry(lam, k, n, inv_pi), c[n]));
-    chat[k] = acc.hi + acc.lo;
+    chat[i] = acc.hi + acc.lo;
   }
   free(lam);
 }
 
-/* out = M^T y. */
-void orc_leg2cheb_t(int64_t N, const double* y, double* out) {
+/* (M^T y)_n = sum_k M_{kn} y_k for the listed n. */
+void orc_leg2cheb_t_rows(int64_t N, const double* y, const int64_t* ns, int64_t nn, double* out) {
   dd* lam = lambda_table(N);
   dd inv_pi = dd_div(dd_from(1.0), dd_pi());
 #pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t n = 0; n < N; ++n) {
+  for (int64_t i = 0; i < nn; ++i) {
+    const int64_t n = ns[i];
     dd acc = dd_from(0.0);
     for (int64_t k = n & 1; k <= n; k += 2) acc = dd_add(acc, dd_mul_d(m_entry(lam, k, n, inv_pi), y[k]));
-    out[n] = acc.hi + acc.lo;
+    out[i] = acc.hi + acc.lo;
   }
   free(lam);
+}
+
+/* chat = M c and out = M^T y over every index. */
+void orc_leg2cheb(int64_t N, const double* c, double* chat) {
+  int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  for (int64_t i = 0; i < N; ++i) all[i] = i;
+  orc_leg2cheb_rows(N, c, all, N, chat);
+  free(all);
+}
+
+void orc_leg2cheb_t(int64_t N, const double* y, double* out) {
+  int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  for (int64_t i = 0; i < N; ++i) all[i] = i;
+  orc_leg2cheb_t_rows(N, y, all, N, out);
+  free(all);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -96,3 +96,34 @@ def test_gradcheck_small(ag):
     assert torch.autograd.gradcheck(ag.dlt, (c,), eps=1e-6, atol=1e-8, rtol=1e-7)
     f = torch.tensor(np.random.default_rng(71).standard_normal((2, 32)), device="cuda", requires_grad=True)
     assert torch.autograd.gradcheck(ag.idlt, (f,), eps=1e-6, atol=1e-8, rtol=1e-7)
+
+
+def test_fp32_gradients_vs_oracle(ag):
+    """The FP32 form through autograd: the DLT's gradient 2 P^T r and the IDLT's
+    vector-Jacobian product D_w P D_s g against the oracle, at the FP32 form's
+    bar (5e-6 in the spec normalisation)."""
+    import oracle
+    N, B = 4096, 4
+    nd = oracle.legpts(N)
+    c = torch.tensor(_batch(B, N, 80), dtype=torch.float32, device="cuda", requires_grad=True)
+    y = torch.tensor(_batch(B, N, 81, decay=0.0), dtype=torch.float32, device="cuda")
+    loss = ((ag.dlt(c) - y) ** 2).sum()
+    loss.backward()
+    with torch.no_grad():
+        r = (ag.dlt(c) - y).double().cpu().numpy()
+    grad = c.grad.double().cpu().numpy()
+    for b in range(B):
+        rb = r[b].astype(np.float32).astype(np.float64)
+        ref = 2.0 * oracle.dlt_t(rb, nd)
+        err = np.max(np.abs(grad[b] - ref)) / np.abs(2.0 * rb).sum()
+        assert err <= 5e-6, (b, err)
+    f = torch.tensor(np.random.default_rng(82).standard_normal((B, N)), dtype=torch.float32, device="cuda",
+                     requires_grad=True)
+    g = torch.tensor(np.random.default_rng(83).standard_normal((B, N)), dtype=torch.float32, device="cuda")
+    (ag.idlt(f) * g).sum().backward()
+    gd = g.double().cpu().numpy()
+    for b in range(B):
+        sg = (np.arange(N) + 0.5) * gd[b]
+        ref = nd.w * oracle.dlt_rows(sg, nd)
+        err = np.max(np.abs(f.grad[b].double().cpu().numpy() - ref)) / np.abs(sg).sum()
+        assert err <= 5e-6, (b, err)

@@ -451,3 +451,58 @@ def test_f64_direct_roundtrip(orc, N):
     a = orc.idlt_rows_f64(f[:half], nd["x"][:half], nd["w"][:half], N)
     b = orc.idlt_rows_f64(f[half:], nd["x"][half:], nd["w"][half:], N)
     assert np.max(np.abs(a + b - back)) <= 64 * U64 * np.abs(back).max() + 1e-300
+
+
+# --------------------------------------------------------------------------
+# restrictions to listed indices (the sampled-row and sparse-input checks)
+# --------------------------------------------------------------------------
+def test_rows_restrictions_match_full(orc):
+    """Every *_rows function equals its full counterpart at the listed indices
+    (leg2cheb), or on an input that is zero off the listed nodes (transposes),
+    and contributions of a partition of the nodes add up to the full sum."""
+    N = 300
+    r = np.random.default_rng(3)
+    nd = orc.legpts(N)
+    ks = np.sort(r.choice(N, 37, replace=False))
+    sub = orc.legpts(N, ks)
+    g = r.standard_normal(ks.size)
+    dense = np.zeros(N)
+    dense[ks] = g
+    for part, full in ((orc.dlt_t_rows(g, sub, N), orc.dlt_t(dense, nd)),
+                       (orc.ndct_t_rows(g, sub, N), orc.ndct_t(dense, nd))):
+        assert np.max(np.abs(part - full)) <= 1e-14 * np.abs(full).max()
+    rest = np.setdiff1d(np.arange(N), ks)
+    gr = r.standard_normal(rest.size)
+    both = np.zeros(N)
+    both[ks], both[rest] = g, gr
+    s = orc.dlt_t_rows(g, sub, N) + orc.dlt_t_rows(gr, orc.legpts(N, rest), N)
+    assert np.max(np.abs(s - orc.dlt_t(both, nd))) <= 1e-14 * np.abs(s).max()
+    c = r.standard_normal(N)
+    assert np.max(np.abs(orc.leg2cheb_rows(c, ks) - orc.leg2cheb(c)[ks])) <= 1e-15 * np.abs(c).sum()
+    assert np.max(np.abs(orc.leg2cheb_t_rows(c, ks) - orc.leg2cheb_t(c)[ks])) <= 1e-15 * np.abs(c).sum()
+
+
+def test_recurrence_coefficient_form(orc):
+    """The dd recurrence with tabulated (2m+1)/(m+1), m/(m+1) keeps P_n exact
+    at the closed forms and the end points for large n (P_n(1) = 1,
+    P_n(-1) = (-1)^n, P_{2m}(0) = (-1)^m (2m)!/(4^m m!^2))."""
+    for n in (1, 2, 3, 1000, 4097):
+        assert orc.legendre_p(n, [1.0])[0] == 1.0
+        assert orc.legendre_p(n, [-1.0])[0] == (-1.0) ** n
+    for m in (1, 5, 50, 500):
+        exact = Fraction((-1) ** m * math.comb(2 * m, m), 4**m)
+        assert abs(orc.legendre_p(2 * m, [0.0])[0] - float(exact)) <= 2e-16 * abs(float(exact))
+
+
+def test_legendre_p_at_dd_points(orc):
+    """P_n at dd points: equals the double-point routine when x_lo = 0, and at
+    the dd Gauss-Legendre nodes P_N vanishes to dd rounding (they are its
+    roots) while P_{N-1} does not."""
+    x = np.linspace(-1, 1, 41)
+    for n in (0, 1, 7, 300):
+        got = orc.legendre_p_at(n, {"x_hi": x, "x_lo": np.zeros_like(x)})
+        assert np.array_equal(got, orc.legendre_p(n, x))
+    N = 257
+    nd = orc.legpts(N)
+    assert np.max(np.abs(orc.legendre_p_at(N, nd))) <= 1e-25
+    assert np.min(np.abs(orc.legendre_p_at(N - 1, nd))) >= 1e-3
