@@ -145,6 +145,17 @@ int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out);
  * lets a caller or a test reach the not-converged status without a fault.
  * GBDLT_ERR_INVALID_ARG for other values. */
 int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
+/* How the plan's FP32 FFT passes (the FP32 form's transforms, and the FP32
+ * tier of FP64 plans) move their tiles: enable = 1 (the default) uses the
+ * persistent passes that copy each tile into shared memory with the tensor
+ * memory accelerator while the previous tile is transformed (Remark 2.2's
+ * FFTs; 2^13 <= N <= 2^23), enable = 0 the passes in which every thread loads
+ * its part of the tile itself.  Both compute the same butterflies in the same
+ * order, so results are bitwise identical; the choice only changes speed.
+ * Clears the plan's replayed graphs.  GBDLT_ERR_INVALID_ARG for other values.
+ * A staged copy that has not landed after about two seconds makes the next
+ * gbdlt_plan_sync return GBDLT_ERR_CUDA. */
+int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable);
 
 /* Legendre nodes and weights (Eq. 1 and Eq. 2; Sec. 2.1-2.2): recomputes the
  * plan's node cache on the GPU and copies any requested array out.  Ordering:

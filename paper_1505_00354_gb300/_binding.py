@@ -83,7 +83,8 @@ class Params(ctypes.Structure):
 ENTRY_POINTS = (
     "gbdlt_plan_params", "gbdlt_plan_params_ex", "gbdlt_plan_create", "gbdlt_plan_create_ex",
     "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
-    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_plan_set_node_iterations", "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
+    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_plan_set_node_iterations", "gbdlt_plan_set_fft_staging",
+    "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
     "gbdlt_batch_create", "gbdlt_batch_create_ex", "gbdlt_batch_exec", "gbdlt_batch_info",
@@ -113,6 +114,7 @@ def lib():
         L.gbdlt_plan_sync.argtypes = [vp]
         L.gbdlt_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
         L.gbdlt_plan_set_node_iterations.argtypes = [vp, i32]
+        L.gbdlt_plan_set_fft_staging.argtypes = [vp, i32]
         L.gbdlt_legpts.argtypes = [vp, vp, vp, vp, vp]
         L.gbdlt_legpts_noalloc.argtypes = [i64, vp, vp, vp, vp, vp]
         for name in ("gbdlt_leg2cheb", "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t",
@@ -217,6 +219,10 @@ class Plan:
     def set_node_iterations(self, max_iter: int):
         """Cap the Newton iterations of later legpts() calls (0..24; 24 is the default)."""
         _check(lib().gbdlt_plan_set_node_iterations(self._h, int(max_iter)), "set_node_iterations")
+
+    def set_fft_staging(self, enable: bool):
+        """FP32 FFT passes staged by the tensor memory accelerator (default) or not."""
+        _check(lib().gbdlt_plan_set_fft_staging(self._h, 1 if enable else 0), "set_fft_staging")
 
     def set_stream(self, stream):
         self.stream = stream

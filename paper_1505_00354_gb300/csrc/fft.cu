@@ -39,6 +39,12 @@
 // then costs 24 FMAs for 4 points, against 16 additions and 3 complex products
 // (28 operations) in the plain form; a twiddled radix-16 stage drops from
 // 13.75 to 12 FP64 operations per point.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched from the driver at run time)
+
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -396,6 +402,7 @@ struct VecMap {
 __device__ __forceinline__ int64_t vec_of(const VecMap& m, int64_t j) {
   return (j / m.count) * m.stride + m.first + j % m.count;
 }
+inline int64_t vec_of_host(const VecMap& m, int64_t j) { return (j / m.count) * m.stride + m.first + j % m.count; }
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
@@ -750,6 +757,366 @@ static bool launch_fft32_rows(int logL2, dim3 grid, cudaStream_t s, const C2<flo
   return false;
 }
 
+// ---------------------------------------------------------------- FP32 passes staged by TMA
+// The compile-time FP32 passes above load each tile with per-thread global loads
+// before the first butterfly and store it after the last, so while a CTA
+// computes it has nothing in flight, and the 3-4 CTAs an SM holds leave the
+// memory system idle much of the time.  The passes below are persistent (a grid
+// of 3 CTAs per SM stepping over the tiles) and move each tile with the tensor
+// memory accelerator into a staging buffer of its own:
+//   * column pass: a 3-D tensor map over the buffer viewed as
+//     [vector][row n1 < L1][2 L2 floats]; one tile (C = 4096/L1 adjacent
+//     columns of one vector) is L1/256 boxes of 256 rows x 2C floats
+//     (cp.async.bulk.tensor), landing unpadded as [n1][c];
+//   * row pass: a tile is C2 = 4096/L2 whole rows, one contiguous 32 KB run,
+//     moved by one bulk copy (cp.async.bulk).
+// The first Stockham stage (no twiddles) reads the staging buffer and writes the
+// padded work tile of the generic kernels; once every thread has passed it, one
+// thread issues the copy of the CTA's next tile into the staging buffer, so that
+// copy runs under the remaining stages, the inter-pass twiddle and the stores of
+// the current tile.  In the column pass the first stage takes the column index
+// as the fastest-varying thread index: it then reads the unpadded [n1][c] tile
+// and writes the padded one without bank conflicts for every line length of
+// 2^13 <= N <= 2^23 (a model of the 16 bank pairs of 8-byte accesses).
+// Completion is an mbarrier with a transaction count.  Every wait is bounded
+// (about 2 s of SM clock): a copy that has not landed by then sets bit 2 of the
+// plan's status word (gbdlt_plan_sync reports a CUDA error) and the CTA returns.
+namespace tma {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this CTA's earlier generic-proxy accesses of shared memory before later
+// async-proxy (TMA) accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once phase `parity` of the barrier has completed; false after ~2^32 SM
+// cycles without completion
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+}  // namespace tma
+
+// First Stockham stage (radix R, sub-transform length 1, no twiddles) of `lines`
+// lines of length L = 2^LOGL held unpadded in the staging buffer S, written to
+// the padded work tile W.  COLS: S is [i][line] (column-pass tile) and the line
+// index varies fastest over the threads; otherwise S is [line][i].
+template <int DIR, int R, int LOGL, bool COLS>
+__device__ __forceinline__ void stage_first_ct(const C2<float>* __restrict__ S, C2<float>* __restrict__ W) {
+  using CT = C2<float>;
+  constexpr int L = 1 << LOGL;
+  constexpr int LOGR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+  constexpr int LR = L / R, LOGLR = LOGL - LOGR;
+  constexpr int LOGC = 12 - LOGL, C = 1 << LOGC;
+  constexpr int LP = line_pitch_ct(L);
+  constexpr int PER = FFT_TILE / R / FFT_THREADS;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = threadIdx.x + q * FFT_THREADS;
+    const int line = COLS ? (b & (C - 1)) : (b >> LOGLR);
+    const int j = COLS ? (b >> LOGC) : (b & (LR - 1));
+    CT v[R];
+    if constexpr (COLS) {
+      const CT* p = S + j * C + line;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = p[r * LR * C];
+    } else {
+      const CT* p = S + line * L + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = p[r * LR];
+    }
+    dftR<float, DIR, R>(v);
+    // outputs j R + r, r < R: one base plus immediate offsets (R divides 16)
+    CT* o = W + line * LP + j * R + ((j * R) >> 4);
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = v[r];
+  }
+  __syncthreads();
+}
+
+template <int DIR, int LOGL, bool COLS>
+__device__ __forceinline__ void fft_tile_staged(const C2<float>* S, C2<float>* W, const C2<float>* __restrict__ tw,
+                                                uint64_t* bar, bool issue_next, const void* next_src,
+                                                const CUtensorMap* map, int nx, int ny, int nz) {
+  constexpr int REM = LOGL & 3;
+  constexpr int R0 = REM == 1 ? 2 : REM == 2 ? 4 : REM == 3 ? 8 : 16;
+  stage_first_ct<DIR, R0, LOGL, COLS>(S, W);
+  // every thread has read S: refill it with the CTA's next tile
+  if (issue_next && threadIdx.x == 0) {
+    tma::fence_proxy_async();
+    tma::mbar_expect_tx(bar, FFT_TILE * sizeof(C2<float>));
+    if constexpr (COLS) {
+      constexpr int L = 1 << LOGL, BOXR = L < 256 ? L : 256;
+#pragma unroll 1
+      for (int r = 0; r < L; r += BOXR) tma::load_3d((char*)S + (size_t)r * (FFT_TILE / L) * sizeof(C2<float>), map,
+                                                     nx, ny + r, nz, bar);
+    } else {
+      tma::load_1d((void*)S, next_src, FFT_TILE * sizeof(C2<float>), bar);
+    }
+  }
+  r16_stages_ct<DIR, LOGL, (REM == 0 ? 4 : REM)>(W, tw);
+}
+
+template <int DIR, int LOGL1>
+__global__ void __launch_bounds__(FFT_THREADS, 3)
+    k_fft32_cols_tma(const __grid_constant__ CUtensorMap map, C2<float>* __restrict__ data, int64_t N, int L2,
+                     const C2<float>* __restrict__ tw4096, const C2<float>* __restrict__ thi,
+                     const C2<float>* __restrict__ tlo, VecMap vm, int64_t ntiles, int* __restrict__ status) {
+  using CT = C2<float>;
+  constexpr int L1 = 1 << LOGL1, LOGC = 12 - LOGL1, C = 1 << LOGC, LP = line_pitch_ct(L1);
+  constexpr int PER = FFT_TILE / FFT_THREADS;
+  constexpr int BOXR = L1 < 256 ? L1 : 256;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  CT* S = reinterpret_cast<CT*>(smraw);
+  CT* W = S + FFT_TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(W + C * LP + 1);
+  const int nblk = L2 / C;
+  int64_t t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(bar, 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int64_t v = vec_of(vm, t / nblk);
+    const int c0 = (int)(t % nblk) * C;
+    tma::mbar_expect_tx(bar, FFT_TILE * sizeof(CT));
+#pragma unroll 1
+    for (int r = 0; r < L1; r += BOXR)
+      tma::load_3d((char*)S + (size_t)r * C * sizeof(CT), &map, 2 * c0, r, (int)v, bar);
+  }
+  uint32_t phase = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const bool ok = tma::mbar_wait(bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(status, 2);
+      return;
+    }
+    phase ^= 1;
+    const int64_t v = vec_of(vm, t / nblk);
+    const int c0 = (int)(t % nblk) * C;
+    const int64_t tn = t + gridDim.x;
+    const bool more = tn < ntiles;
+    fft_tile_staged<DIR, LOGL1, true>(S, W, tw4096, bar, more, nullptr, &map,
+                                      more ? 2 * (int)(tn % nblk) * C : 0, 0, more ? (int)vec_of(vm, tn / nblk) : 0);
+    CT* g = data + v * N;
+#pragma unroll 4
+    for (int q = 0; q < PER; ++q) {
+      const int i = threadIdx.x + q * FFT_THREADS;
+      const int k1 = i >> LOGC, c = i & (C - 1);
+      const int64_t e = (int64_t)(c0 + c) * k1;
+      CT val = W[sidx(c, LP, k1)];
+      if (e != 0) {
+        const CT w = tw_lookup<float>(thi, tlo, e);
+        val = cmul<float>(val, mk<float>(w.x, DIR > 0 ? w.y : -w.y));
+      }
+      g[(int64_t)k1 * L2 + c0 + c] = val;
+    }
+    __syncthreads();  // W is rewritten by the next tile's first stage
+  }
+}
+
+template <int DIR, int LOGL2>
+__global__ void __launch_bounds__(FFT_THREADS, 3)
+    k_fft32_rows_tma(const C2<float>* __restrict__ in, C2<float>* __restrict__ out, int64_t N, int L1,
+                     const C2<float>* __restrict__ tw4096, VecMap vm, int64_t ntiles, int* __restrict__ status) {
+  using CT = C2<float>;
+  constexpr int L2 = 1 << LOGL2, LOGC2 = 12 - LOGL2, C2n = 1 << LOGC2, LP = line_pitch_ct(L2);
+  constexpr int PER = FFT_TILE / FFT_THREADS;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  CT* S = reinterpret_cast<CT*>(smraw);
+  CT* W = S + FFT_TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(W + C2n * LP + 1);
+  const int nblk = L1 / C2n;
+  int64_t t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(bar, 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  auto src_of = [&](int64_t tt) {
+    return in + vec_of(vm, tt / nblk) * N + (int64_t)(tt % nblk) * C2n * L2;
+  };
+  if (threadIdx.x == 0) {
+    tma::mbar_expect_tx(bar, FFT_TILE * sizeof(CT));
+    tma::load_1d(S, src_of(t), FFT_TILE * sizeof(CT), bar);
+  }
+  uint32_t phase = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const bool ok = tma::mbar_wait(bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(status, 2);
+      return;
+    }
+    phase ^= 1;
+    const int64_t v = vec_of(vm, t / nblk);
+    const int r0 = (int)(t % nblk) * C2n;
+    const int64_t tn = t + gridDim.x;
+    const bool more = tn < ntiles;
+    fft_tile_staged<DIR, LOGL2, false>(S, W, tw4096, bar, more, more ? (const void*)src_of(tn) : nullptr, nullptr,
+                                       0, 0, 0);
+    CT* o = out + v * N;
+#pragma unroll 4
+    for (int q = 0; q < PER; ++q) {
+      const int i = threadIdx.x + q * FFT_THREADS;
+      const int k2 = i >> LOGC2, line = i & (C2n - 1);
+      o[(int64_t)(r0 + line) + (int64_t)L1 * k2] = W[sidx(line, LP, k2)];
+    }
+    __syncthreads();
+  }
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// the driver's tensor-map encoder, looked up once (null if the driver has none)
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiled) nullptr;
+    }
+    return (EncodeTiled)f;
+  }();
+  return fn;
+}
+
+int sm_count() {
+  static int count[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!count[dev]) {
+    int c = 0;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) {
+      cudaGetLastError();
+      c = 148;
+    }
+    count[dev] = c;
+  }
+  return count[dev];
+}
+
+// raise a staged kernel's dynamic shared-memory limit once (before the first
+// launch of any call, which runs uncaptured)
+std::mutex g_smem_mu;
+std::vector<const void*> g_smem_set;
+template <typename K>
+bool set_smem(K kernel, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  const void* key = (const void*)kernel;
+  for (const void* k : g_smem_set)
+    if (k == key) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  g_smem_set.push_back(key);
+  return true;
+}
+}  // namespace
+
+// dynamic shared memory of a staged FP32 pass over lines of length L
+constexpr size_t tma_smem_bytes(int L) {
+  return (size_t)(FFT_TILE + (FFT_TILE / L) * line_pitch_ct(L) + 1) * sizeof(C2<float>) + 16;
+}
+
+// The staged FP32 column pass for log2 L1 in [7, 11] (2 <= C <= 32, so a box row
+// is 16..256 bytes); false (nothing launched) where it does not apply.
+template <int DIR>
+static bool launch_fft32_cols_tma(int logL1, Plan& P, C2<float>* a, int64_t N, int L2, const C2<float>* tw,
+                                  const C2<float>* thi, const C2<float>* tlo, VecMap vm, int64_t nv) {
+  if (logL1 < 7 || logL1 > 11 || P.no_tma) return false;
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return false;
+  const int L1 = 1 << logL1, C = FFT_TILE / L1;
+  const int64_t vmax = vec_of_host(vm, nv - 1);
+  CUtensorMap map;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * L2, (cuuint64_t)L1, (cuuint64_t)(vmax + 1)};
+  const cuuint64_t strides[2] = {(cuuint64_t)L2 * sizeof(C2<float>), (cuuint64_t)N * sizeof(C2<float>)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * C), (cuuint32_t)(L1 < 256 ? L1 : 256), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)a, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return false;
+  const int64_t ntiles = nv * (L2 / C);
+  const int64_t grid = std::min<int64_t>(ntiles, 3 * (int64_t)sm_count());
+  const size_t smem = tma_smem_bytes(L1);
+  switch (logL1) {
+#define GBDLT_C32T(LG)                                                                                        \
+  case LG:                                                                                                    \
+    if (!set_smem(k_fft32_cols_tma<DIR, LG>, smem)) return false;                                             \
+    k_fft32_cols_tma<DIR, LG><<<(unsigned)grid, FFT_THREADS, smem, P.stream>>>(map, a, N, L2, tw, thi, tlo, vm, \
+                                                                               ntiles, P.status);             \
+    return true;
+    GBDLT_C32T(7) GBDLT_C32T(8) GBDLT_C32T(9) GBDLT_C32T(10) GBDLT_C32T(11)
+#undef GBDLT_C32T
+  }
+  return false;
+}
+
+// The staged FP32 row pass for log2 L2 in [6, 12].
+template <int DIR>
+static bool launch_fft32_rows_tma(int logL2, Plan& P, const C2<float>* a, C2<float>* b, int64_t N, int L1,
+                                  const C2<float>* tw, VecMap vm, int64_t nv) {
+  if (logL2 < 6 || logL2 > 12 || P.no_tma) return false;
+  const int L2 = 1 << logL2, C2n = FFT_TILE / L2;
+  const int64_t ntiles = nv * (L1 / C2n);
+  const int64_t grid = std::min<int64_t>(ntiles, 3 * (int64_t)sm_count());
+  const size_t smem = tma_smem_bytes(L2);
+  switch (logL2) {
+#define GBDLT_R32T(LG)                                                                                              \
+  case LG:                                                                                                          \
+    if (!set_smem(k_fft32_rows_tma<DIR, LG>, smem)) return false;                                                   \
+    k_fft32_rows_tma<DIR, LG><<<(unsigned)grid, FFT_THREADS, smem, P.stream>>>(a, b, N, L1, tw, vm, ntiles, P.status); \
+    return true;
+    GBDLT_R32T(6) GBDLT_R32T(7) GBDLT_R32T(8) GBDLT_R32T(9) GBDLT_R32T(10) GBDLT_R32T(11) GBDLT_R32T(12)
+#undef GBDLT_R32T
+  }
+  return false;
+}
+
 template <typename T, int DIR>
 static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, int64_t npruned, int R,
                        int mode);
@@ -820,6 +1187,9 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   auto cols = [&](VecMap vm, int64_t nv) {
     const dim3 grid(L2 / C, (unsigned)nv);
     if constexpr (is_f32<T>) {
+      if (launch_fft32_cols_tma<DIR>(lL1, P, (C2<float>*)a, N, L2, (const C2<float>*)tw.t4096,
+                                     (const C2<float>*)tw.nhi, (const C2<float>*)tw.nlo, vm, nv))
+        return;
       if (launch_fft32_cols<DIR>(lL1, grid, P.stream, (C2<float>*)a, N, L2, (const C2<float>*)tw.t4096,
                                  (const C2<float>*)tw.nhi, (const C2<float>*)tw.nlo, vm))
         return;
@@ -830,6 +1200,9 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
   auto rows = [&](VecMap vm, int64_t nv) {
     const dim3 grid(L1 / C2n, (unsigned)nv);
     if constexpr (is_f32<T>) {
+      if (launch_fft32_rows_tma<DIR>(lL2, P, (const C2<float>*)a, (C2<float>*)b, N, L1, (const C2<float>*)tw.t4096,
+                                     vm, nv))
+        return;
       if (launch_fft32_rows<DIR>(lL2, grid, P.stream, (const C2<float>*)a, (C2<float>*)b, N, L1,
                                  (const C2<float>*)tw.t4096, vm))
         return;

@@ -341,6 +341,7 @@ struct Plan {
   void* tmp2 = nullptr;  // [N]
   int* status = nullptr; // device status word
   int node_iter_max = kNodeIterMax;  // Newton iterations a node may take (legpts.cu)
+  bool no_tma = false;   // FP32 FFT passes without the TMA-staged kernels (fft.cu)
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel

@@ -1574,8 +1574,22 @@ int gbdlt_plan_sync(gbdlt_plan plan) {
   if (hs) {
     cudaMemset(P->status, 0, sizeof(int));
     if (hs & 1) return GBDLT_ERR_NOT_CONVERGED;
+    if (hs & 2) return GBDLT_ERR_CUDA;  // an asynchronous tile copy did not complete in time
   }
   return check_launch();
+}
+
+int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable) {
+  if (!plan || (enable != 0 && enable != 1)) return GBDLT_ERR_INVALID_ARG;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (P->no_tma == (enable == 0)) return GBDLT_OK;
+  // replayed chains hold the kernels they were captured with
+  if (P->graphs) {
+    if (cudaStreamSynchronize(P->graphs->s) != cudaSuccess) return GBDLT_ERR_CUDA;
+    free_graphs(P);
+  }
+  P->no_tma = enable == 0;
+  return GBDLT_OK;
 }
 
 int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out) {

@@ -477,3 +477,27 @@ def test_graph_replay(gb):
             p.idlt(x, out=y)
         s.synchronize()
         assert torch.equal(y, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("N", [1 << 13, 1 << 16, 1 << 19, 1 << 20, 1 << 22])
+def test_fft_staging_bitwise(gb, N, prec):
+    """The FP32 FFT passes staged by the tensor memory accelerator compute the
+    same butterflies in the same order as the per-thread-load passes: every
+    operator's result is bitwise identical with staging on and off, for FP32
+    plans and for the FP32 tier of FP64 plans (replays included)."""
+    fp = gb.FP64 if prec == "fp64" else gb.FP32
+    x = dev(_c(N, 93, 1.0), torch.float64 if prec == "fp64" else torch.float32)
+    ops = ["leg2cheb", "leg2cheb_t", "chebeval", "chebeval_t", "dlt", "dlt_t", "idlt", "idlt_t"]
+    p = gb.Plan(N, fp, method=gb.METHOD_FAST)
+    p.set_fft_staging(False)
+    ref = {op: getattr(p, op)(x).clone() for op in ops}
+    p.set_fft_staging(True)
+    for op in ops:
+        y = torch.empty_like(x)
+        for _ in range(3):
+            getattr(p, op)(x, out=y)
+            assert torch.equal(y, ref[op]), op
+    assert gb.lib().gbdlt_plan_sync(p.handle) == 0
+    with pytest.raises(gb.GbdltError):
+        gb._binding._check(gb.lib().gbdlt_plan_set_fft_staging(p.handle, 2), "set_fft_staging")
