@@ -146,11 +146,13 @@ int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out);
  * GBDLT_ERR_INVALID_ARG for other values. */
 int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
 /* How the plan's FP32 FFT passes (the FP32 form's transforms, and the FP32
- * tier of FP64 plans) move their tiles: enable = 1 (the default) uses the
- * persistent passes that copy each tile into shared memory with the tensor
- * memory accelerator while the previous tile is transformed (Remark 2.2's
- * FFTs; 2^13 <= N <= 2^23), enable = 0 the passes in which every thread loads
- * its part of the tile itself.  Both compute the same butterflies in the same
+ * tier of FP64 plans) move their tiles: enable = 1 uses the persistent passes
+ * that copy each tile into shared memory with the tensor memory accelerator
+ * while the previous tile is transformed (Remark 2.2's FFTs; column passes for
+ * 2^13 <= N <= 2^23, row passes for N <= 2^21), enable = 0 the passes in which
+ * every thread loads its part of the tile itself.  Default: 1 for GBDLT_FP32
+ * plans, 0 for GBDLT_FP64 plans (their FP32 transforms run beside FP64 kernels,
+ * which a persistent grid would crowd out).  Both compute the same butterflies in the same
  * order, so results are bitwise identical; the choice only changes speed.
  * Clears the plan's replayed graphs.  GBDLT_ERR_INVALID_ARG for other values.
  * A staged copy that has not landed after about two seconds makes the next

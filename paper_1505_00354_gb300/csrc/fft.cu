@@ -66,6 +66,16 @@ __device__ __forceinline__ C2<T> tw_lookup(const C2<T>* __restrict__ hi, const C
   return cmul<T>(hi[e >> 12], lo[e & 4095]);
 }
 
+// e^{2 pi i e / N} in FP32 for 0 <= e < N <= 2^24, N a power of two: sincospif
+// of the argument 2e/N, which is exact in float (e fits the significand and 2/N
+// is a power of two), so the only rounding is the function's own (no table
+// loads: the FP32 passes are bound by the latency of their global loads)
+__device__ __forceinline__ C2<float> tw_pow2_f32(int64_t e, float two_over_n) {
+  float s, c;
+  sincospif((float)e * two_over_n, &s, &c);
+  return mk<float>(c, s);
+}
+
 // multiply by e^{DIR i a} given (cos a, sin a)
 template <typename T, int DIR>
 __device__ __forceinline__ C2<T> rot(C2<T> v, T c, T s) {
@@ -580,7 +590,10 @@ __global__ void __launch_bounds__(FFT_THREADS)
 // (four-step passes), so no bounds tests remain.
 __host__ __device__ constexpr int line_pitch_ct(int L) { return L + (L >> 4) + (L >= 16 ? 1 : 0); }
 
-template <int DIR, int R, int LOGL, int LOGNS>
+// tw holds e^{2 pi i j / TABN} at tw[j]: the 4096-entry global table (TABN =
+// 4096) or a shared-memory copy of the first L/2 entries of e^{2 pi i j / L}
+// (TABN = L), which holds every twiddle a line of length L needs
+template <int DIR, int R, int LOGL, int LOGNS, int TABN = FFT_TILE>
 __device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
   using CT = C2<float>;
   constexpr int L = 1 << LOGL;
@@ -607,7 +620,7 @@ __device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restr
       for (int r = 0; r < R; ++r) v[q][r] = sm[sidx(line, LP, j + r * LR)];
     }
     if constexpr (NS > 1) {
-      const int ks = k * (FFT_TILE / (NS * R));
+      const int ks = k * (TABN / (NS * R));
       CT w[R];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -639,11 +652,11 @@ __device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restr
   __syncthreads();
 }
 
-template <int DIR, int LOGL, int LOGNS>
+template <int DIR, int LOGL, int LOGNS, int TABN = FFT_TILE>
 __device__ __forceinline__ void r16_stages_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
   if constexpr (LOGNS < LOGL) {
-    stage_ct<DIR, 16, LOGL, LOGNS>(sm, tw);
-    r16_stages_ct<DIR, LOGL, LOGNS + 4>(sm, tw);
+    stage_ct<DIR, 16, LOGL, LOGNS, TABN>(sm, tw);
+    r16_stages_ct<DIR, LOGL, LOGNS + 4, TABN>(sm, tw);
   }
 }
 
@@ -689,7 +702,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4)
     const int64_t e = (int64_t)(c0 + c) * k1;
     CT val = sm[sidx(c, LP, k1)];
     if (e != 0) {
-      const CT w = tw_lookup<float>(thi, tlo, e);
+      const CT w = tw_pow2_f32(e, 2.0f / (float)N);
       val = cmul<float>(val, mk<float>(w.x, DIR > 0 ? w.y : -w.y));
     }
     g[(int64_t)k1 * L2 + c0 + c] = val;
@@ -867,6 +880,7 @@ __device__ __forceinline__ void stage_first_ct(const C2<float>* __restrict__ S, 
   __syncthreads();
 }
 
+// tw: the shared-memory table e^{2 pi i j / L}, j < L/2 (tw_fill)
 template <int DIR, int LOGL, bool COLS>
 __device__ __forceinline__ void fft_tile_staged(const C2<float>* S, C2<float>* W, const C2<float>* __restrict__ tw,
                                                 uint64_t* bar, bool issue_next, const void* next_src,
@@ -887,7 +901,16 @@ __device__ __forceinline__ void fft_tile_staged(const C2<float>* S, C2<float>* W
       tma::load_1d((void*)S, next_src, FFT_TILE * sizeof(C2<float>), bar);
     }
   }
-  r16_stages_ct<DIR, LOGL, (REM == 0 ? 4 : REM)>(W, tw);
+  r16_stages_ct<DIR, LOGL, (REM == 0 ? 4 : REM), (1 << LOGL)>(W, tw);
+}
+
+// T[j] = e^{2 pi i j / L} = tw4096[j 4096 / L] for j < L/2: the same rounded
+// values as the global table, so the staged passes stay bitwise equal to the
+// others
+template <int LOGL>
+__device__ __forceinline__ void tw_fill(C2<float>* T, const C2<float>* __restrict__ tw4096) {
+  constexpr int L = 1 << LOGL;
+  for (int j = threadIdx.x; j < L / 2; j += FFT_THREADS) T[j] = tw4096[j * (FFT_TILE / L)];
 }
 
 template <int DIR, int LOGL1>
@@ -902,7 +925,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   extern __shared__ __align__(1024) unsigned char smraw[];
   CT* S = reinterpret_cast<CT*>(smraw);
   CT* W = S + FFT_TILE;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(W + C * LP + 1);
+  CT* T = W + C * LP;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(T + L1 / 2);
   const int nblk = L2 / C;
   int64_t t = blockIdx.x;
   if (t >= ntiles) return;
@@ -910,6 +934,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
     tma::mbar_init(bar, 1);
     tma::fence_mbar_init();
   }
+  tw_fill<LOGL1>(T, tw4096);
   __syncthreads();
   if (threadIdx.x == 0) {
     const int64_t v = vec_of(vm, t / nblk);
@@ -931,7 +956,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
     const int c0 = (int)(t % nblk) * C;
     const int64_t tn = t + gridDim.x;
     const bool more = tn < ntiles;
-    fft_tile_staged<DIR, LOGL1, true>(S, W, tw4096, bar, more, nullptr, &map,
+    fft_tile_staged<DIR, LOGL1, true>(S, W, T, bar, more, nullptr, &map,
                                       more ? 2 * (int)(tn % nblk) * C : 0, 0, more ? (int)vec_of(vm, tn / nblk) : 0);
     CT* g = data + v * N;
 #pragma unroll 4
@@ -941,7 +966,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
       const int64_t e = (int64_t)(c0 + c) * k1;
       CT val = W[sidx(c, LP, k1)];
       if (e != 0) {
-        const CT w = tw_lookup<float>(thi, tlo, e);
+        const CT w = tw_pow2_f32(e, 2.0f / (float)N);
         val = cmul<float>(val, mk<float>(w.x, DIR > 0 ? w.y : -w.y));
       }
       g[(int64_t)k1 * L2 + c0 + c] = val;
@@ -960,7 +985,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   extern __shared__ __align__(1024) unsigned char smraw[];
   CT* S = reinterpret_cast<CT*>(smraw);
   CT* W = S + FFT_TILE;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(W + C2n * LP + 1);
+  CT* T = W + C2n * LP;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(T + L2 / 2);
   const int nblk = L1 / C2n;
   int64_t t = blockIdx.x;
   if (t >= ntiles) return;
@@ -968,6 +994,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
     tma::mbar_init(bar, 1);
     tma::fence_mbar_init();
   }
+  tw_fill<LOGL2>(T, tw4096);
   __syncthreads();
   auto src_of = [&](int64_t tt) {
     return in + vec_of(vm, tt / nblk) * N + (int64_t)(tt % nblk) * C2n * L2;
@@ -988,7 +1015,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
     const int r0 = (int)(t % nblk) * C2n;
     const int64_t tn = t + gridDim.x;
     const bool more = tn < ntiles;
-    fft_tile_staged<DIR, LOGL2, false>(S, W, tw4096, bar, more, more ? (const void*)src_of(tn) : nullptr, nullptr,
+    fft_tile_staged<DIR, LOGL2, false>(S, W, T, bar, more, more ? (const void*)src_of(tn) : nullptr, nullptr,
                                        0, 0, 0);
     CT* o = out + v * N;
 #pragma unroll 4
@@ -1056,9 +1083,10 @@ bool set_smem(K kernel, size_t bytes) {
 }
 }  // namespace
 
-// dynamic shared memory of a staged FP32 pass over lines of length L
+// dynamic shared memory of a staged FP32 pass over lines of length L: staging
+// tile, padded work tile, twiddle table (L/2 entries), mbarrier
 constexpr size_t tma_smem_bytes(int L) {
-  return (size_t)(FFT_TILE + (FFT_TILE / L) * line_pitch_ct(L) + 1) * sizeof(C2<float>) + 16;
+  return (size_t)(FFT_TILE + (FFT_TILE / L) * line_pitch_ct(L) + L / 2) * sizeof(C2<float>) + 16;
 }
 
 // The staged FP32 column pass for log2 L1 in [7, 11] (2 <= C <= 32, so a box row
@@ -1096,11 +1124,14 @@ static bool launch_fft32_cols_tma(int logL1, Plan& P, C2<float>* a, int64_t N, i
   return false;
 }
 
-// The staged FP32 row pass for log2 L2 in [6, 12].
+// The staged FP32 row pass for log2 L2 in [6, 10]; at L2 = 2048 (N = 2^22,
+// 2^23), where a tile is two rows and its stores 16-byte pieces, the staged pass
+// measured slower than the per-thread-load pass (1.18 against 0.81 ms for the
+// FP32 form's six launches at 2^22) and is not used.
 template <int DIR>
 static bool launch_fft32_rows_tma(int logL2, Plan& P, const C2<float>* a, C2<float>* b, int64_t N, int L1,
                                   const C2<float>* tw, VecMap vm, int64_t nv) {
-  if (logL2 < 6 || logL2 > 12 || P.no_tma) return false;
+  if (logL2 < 6 || logL2 > 10 || P.no_tma) return false;
   const int L2 = 1 << logL2, C2n = FFT_TILE / L2;
   const int64_t ntiles = nv * (L1 / C2n);
   const int64_t grid = std::min<int64_t>(ntiles, 3 * (int64_t)sm_count());
@@ -1111,7 +1142,7 @@ static bool launch_fft32_rows_tma(int logL2, Plan& P, const C2<float>* a, C2<flo
     if (!set_smem(k_fft32_rows_tma<DIR, LG>, smem)) return false;                                                   \
     k_fft32_rows_tma<DIR, LG><<<(unsigned)grid, FFT_THREADS, smem, P.stream>>>(a, b, N, L1, tw, vm, ntiles, P.status); \
     return true;
-    GBDLT_R32T(6) GBDLT_R32T(7) GBDLT_R32T(8) GBDLT_R32T(9) GBDLT_R32T(10) GBDLT_R32T(11) GBDLT_R32T(12)
+    GBDLT_R32T(6) GBDLT_R32T(7) GBDLT_R32T(8) GBDLT_R32T(9) GBDLT_R32T(10)
 #undef GBDLT_R32T
   }
   return false;

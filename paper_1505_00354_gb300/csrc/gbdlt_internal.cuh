@@ -341,7 +341,10 @@ struct Plan {
   void* tmp2 = nullptr;  // [N]
   int* status = nullptr; // device status word
   int node_iter_max = kNodeIterMax;  // Newton iterations a node may take (legpts.cu)
-  bool no_tma = false;   // FP32 FFT passes without the TMA-staged kernels (fft.cu)
+  // FP32 FFT passes without the TMA-staged kernels (fft.cu): the default of FP64
+  // plans, whose FP32 transforms run on the side stream beside FP64 kernels and
+  // there leave more room to them as ordinary (non-persistent) grids
+  bool no_tma = false;
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel

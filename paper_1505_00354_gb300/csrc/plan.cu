@@ -630,6 +630,7 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   if (!P) return GBDLT_ERR_OOM;
   P->p = prm;
   P->stream = stream;
+  P->no_tma = prm.prec == GBDLT_FP64;
   cudaGetDevice(&P->device);
   const size_t ts = prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * ts;

@@ -493,6 +493,7 @@ def test_fft_staging_bitwise(gb, N, prec):
     p.set_fft_staging(False)
     ref = {op: getattr(p, op)(x).clone() for op in ops}
     p.set_fft_staging(True)
+    # the default stays whatever the plan chose; both settings agree bitwise
     for op in ops:
         y = torch.empty_like(x)
         for _ in range(3):
