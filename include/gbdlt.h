@@ -151,8 +151,10 @@ int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
  * while the previous tile is transformed (Remark 2.2's FFTs; column passes for
  * 2^13 <= N <= 2^23, row passes for N <= 2^21), enable = 0 the passes in which
  * every thread loads its part of the tile itself.  Default: 1 for GBDLT_FP32
- * plans, 0 for GBDLT_FP64 plans (their FP32 transforms run beside FP64 kernels,
- * which a persistent grid would crowd out).  Both compute the same butterflies in the same
+ * plans with 2^18 <= N <= 2^21, where the whole DLT + IDLT measured faster
+ * with it; 0 otherwise (neutral at smaller N, slower where the persistent
+ * grid keeps kernels of the plan's side stream, or the FP64 kernels beside an
+ * FP64 plan's FP32 transforms, off the SMs).  Both compute the same butterflies in the same
  * order, so results are bitwise identical; the choice only changes speed.
  * Clears the plan's replayed graphs.  GBDLT_ERR_INVALID_ARG for other values.
  * A staged copy that has not landed after about two seconds makes the next

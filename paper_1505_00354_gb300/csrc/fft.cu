@@ -669,6 +669,40 @@ __device__ __forceinline__ void fft_tile_ct(C2<float>* sm, const C2<float>* __re
   r16_stages_ct<DIR, LOGL, REM>(sm, tw);
 }
 
+// Epilogue element of the i-th (thread, step) slot of a transposed tile write:
+// row k of line c of a tile of C = 2^LOGC lines.  Each half-warp takes C lines
+// x 16/C rows spaced C apart, so its reads of the padded tile (c LP + k + k/16,
+// LP = 1 mod 16) hit 16 distinct bank pairs, while every warp still writes
+// whole C-element row segments; slot tid + 256 q keeps the thread's line c and
+// takes row k0 + (256/C) q.
+template <int LOGC>
+__device__ __forceinline__ void epi_slot(int i, int& k, int& c) {
+  constexpr int C = 1 << LOGC;
+  if constexpr (C >= 16) {
+    k = i >> LOGC;
+    c = i & (C - 1);
+  } else {
+    const int hw = i >> 4, l16 = i & 15;
+    c = l16 & (C - 1);
+    k = 16 * (hw >> LOGC) + (hw & (C - 1)) + C * (l16 >> LOGC);
+  }
+}
+
+// Inter-pass twiddles of a column tile (columns c0 + c, c < C):
+// T[c][q] = e^{2 pi i (256/C)(c0 + c) q / N}, q < 16, filled by the CTA; the
+// thread with line c and first row k0 multiplies B = e^{2 pi i (c0 + c) k0 / N}
+// by T[c][q] for row k0 + (256/C) q.  Two rounded factors and one product, as
+// with a two-level table, but only 16 C + 256 sines and cosines per tile and no
+// global loads.
+template <int LOGC>
+__device__ __forceinline__ void tw_tile_fill(C2<float>* T, int c0, float two_over_n) {
+  constexpr int C = 1 << LOGC;
+  for (int j = threadIdx.x; j < 16 * C; j += FFT_THREADS) {
+    const int c = j >> 4, q = j & 15;
+    T[j] = tw_pow2_f32((int64_t)(256 / C) * (c0 + c) * q, two_over_n);
+  }
+}
+
 template <int DIR, int LOGL1>
 __global__ void __launch_bounds__(FFT_THREADS, 4)
     k_fft32_cols(C2<float>* __restrict__ data, int64_t N, int L2, const C2<float>* __restrict__ tw4096,
@@ -677,6 +711,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4)
   constexpr int L1 = 1 << LOGL1, LOGC = 12 - LOGL1, C = 1 << LOGC, LP = line_pitch_ct(L1);
   constexpr int PER = FFT_TILE / FFT_THREADS;
   __shared__ CT sm[C * LP];
+  __shared__ CT tws[16 * C];
   const int c0 = blockIdx.x * C;
   CT* g = data + vec_of(vm, blockIdx.y) * N;
 #pragma unroll
@@ -693,18 +728,18 @@ __global__ void __launch_bounds__(FFT_THREADS, 4)
       sm[sidx(i & (C - 1), LP, i >> LOGC)] = r[q];
     }
   }
+  const float ton = 2.0f / (float)N;
+  tw_tile_fill<LOGC>(tws, c0, ton);
   __syncthreads();
   fft_tile_ct<DIR, LOGL1>(sm, tw4096);
+  int k0, c;
+  epi_slot<LOGC>(threadIdx.x, k0, c);
+  const CT B = tw_pow2_f32((int64_t)(c0 + c) * k0, ton);
 #pragma unroll 4
   for (int q = 0; q < PER; ++q) {
-    const int i = threadIdx.x + q * FFT_THREADS;
-    const int k1 = i >> LOGC, c = i & (C - 1);
-    const int64_t e = (int64_t)(c0 + c) * k1;
-    CT val = sm[sidx(c, LP, k1)];
-    if (e != 0) {
-      const CT w = tw_pow2_f32(e, 2.0f / (float)N);
-      val = cmul<float>(val, mk<float>(w.x, DIR > 0 ? w.y : -w.y));
-    }
+    const int k1 = k0 + (256 / C) * q;
+    const CT w = cmul<float>(B, tws[16 * c + q]);
+    const CT val = cmul<float>(sm[sidx(c, LP, k1)], mk<float>(w.x, DIR > 0 ? w.y : -w.y));
     g[(int64_t)k1 * L2 + c0 + c] = val;
   }
 }
@@ -736,8 +771,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 4)
   fft_tile_ct<DIR, LOGL2>(sm, tw4096);
 #pragma unroll 4
   for (int q = 0; q < PER; ++q) {
-    const int i = threadIdx.x + q * FFT_THREADS;
-    const int k2 = i >> LOGC2, line = i & (C2n - 1);
+    int k2, line;
+    epi_slot<LOGC2>(threadIdx.x + q * FFT_THREADS, k2, line);
     o[(int64_t)(r0 + line) + (int64_t)L1 * k2] = sm[sidx(line, LP, k2)];
   }
 }
@@ -926,7 +961,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   CT* S = reinterpret_cast<CT*>(smraw);
   CT* W = S + FFT_TILE;
   CT* T = W + C * LP;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(T + L1 / 2);
+  CT* tws = T + L1 / 2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + 16 * C);
+  const float ton = 2.0f / (float)N;
   const int nblk = L2 / C;
   int64_t t = blockIdx.x;
   if (t >= ntiles) return;
@@ -956,22 +993,21 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
     const int c0 = (int)(t % nblk) * C;
     const int64_t tn = t + gridDim.x;
     const bool more = tn < ntiles;
+    tw_tile_fill<LOGC>(tws, c0, ton);  // read after the stages' barriers
     fft_tile_staged<DIR, LOGL1, true>(S, W, T, bar, more, nullptr, &map,
                                       more ? 2 * (int)(tn % nblk) * C : 0, 0, more ? (int)vec_of(vm, tn / nblk) : 0);
     CT* g = data + v * N;
+    int k0, c;
+    epi_slot<LOGC>(threadIdx.x, k0, c);
+    const CT B = tw_pow2_f32((int64_t)(c0 + c) * k0, ton);
 #pragma unroll 4
     for (int q = 0; q < PER; ++q) {
-      const int i = threadIdx.x + q * FFT_THREADS;
-      const int k1 = i >> LOGC, c = i & (C - 1);
-      const int64_t e = (int64_t)(c0 + c) * k1;
-      CT val = W[sidx(c, LP, k1)];
-      if (e != 0) {
-        const CT w = tw_pow2_f32(e, 2.0f / (float)N);
-        val = cmul<float>(val, mk<float>(w.x, DIR > 0 ? w.y : -w.y));
-      }
+      const int k1 = k0 + (256 / C) * q;
+      const CT w = cmul<float>(B, tws[16 * c + q]);
+      const CT val = cmul<float>(W[sidx(c, LP, k1)], mk<float>(w.x, DIR > 0 ? w.y : -w.y));
       g[(int64_t)k1 * L2 + c0 + c] = val;
     }
-    __syncthreads();  // W is rewritten by the next tile's first stage
+    __syncthreads();  // W and the tile twiddles are rewritten for the next tile
   }
 }
 
@@ -1020,8 +1056,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
     CT* o = out + v * N;
 #pragma unroll 4
     for (int q = 0; q < PER; ++q) {
-      const int i = threadIdx.x + q * FFT_THREADS;
-      const int k2 = i >> LOGC2, line = i & (C2n - 1);
+      int k2, line;
+      epi_slot<LOGC2>(threadIdx.x + q * FFT_THREADS, k2, line);
       o[(int64_t)(r0 + line) + (int64_t)L1 * k2] = W[sidx(line, LP, k2)];
     }
     __syncthreads();
@@ -1084,9 +1120,11 @@ bool set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 // dynamic shared memory of a staged FP32 pass over lines of length L: staging
-// tile, padded work tile, twiddle table (L/2 entries), mbarrier
+// tile, padded work tile, twiddle table (L/2 entries), the column pass's tile
+// twiddles (16 C entries), mbarrier
 constexpr size_t tma_smem_bytes(int L) {
-  return (size_t)(FFT_TILE + (FFT_TILE / L) * line_pitch_ct(L) + L / 2) * sizeof(C2<float>) + 16;
+  return (size_t)(FFT_TILE + (FFT_TILE / L) * line_pitch_ct(L) + L / 2 + 16 * (FFT_TILE / L)) * sizeof(C2<float>) +
+         16;
 }
 
 // The staged FP32 column pass for log2 L1 in [7, 11] (2 <= C <= 32, so a box row

@@ -630,7 +630,10 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   if (!P) return GBDLT_ERR_OOM;
   P->p = prm;
   P->stream = stream;
-  P->no_tma = prm.prec == GBDLT_FP64;
+  // staged FP32 FFT passes where they measured faster over a whole DLT + IDLT
+  // (FP32 plans, 2^18 <= N <= 2^21; elsewhere neutral, or slower where their
+  // persistent grid keeps the side stream's kernels off the SMs)
+  P->no_tma = !(prm.prec == GBDLT_FP32 && N >= (1 << 18) && N <= (1 << 21));
   cudaGetDevice(&P->device);
   const size_t ts = prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * ts;
