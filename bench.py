@@ -351,6 +351,11 @@ def run_gpu(args, world, rank, local):
     ms32, _, f32, cb32 = timed_loop(plan32, c32, args.steps, args.warmup)
     t32 = sum(ms32) / len(ms32)
     prof32, _ = profiled_loop(plan32, c32, args.steps)
+    # the FP32 FFT passes with the TMA-staged kernels switched off, for comparison
+    plan32.set_fft_staging(False)
+    ms32u, _, _, _ = timed_loop(plan32, c32, args.steps, args.warmup)
+    prof32u, _ = profiled_loop(plan32, c32, args.steps)
+    plan32.set_fft_staging(True)
 
     # ---------------- uneven batch (4096 transforms, N log-uniform in [16, 8192], 50/50)
     def time_batch(prec):
@@ -485,6 +490,10 @@ def run_gpu(args, world, rank, local):
                                 "peak_gbs": hbm, "peak_source": hbm_src, "frac": round(hbm_frac, 6)},
             "fp32_form": {"value": round(2.0 * world / (t32 / 1e3), 3), "unit": "transforms/s",
                           "ms_per_step": round(t32, 4), "speedup_vs_fp64": round(t_step / t32, 3),
+                          "roofline": fft_roofline(prof32, args.steps, hbm, hbm_src),
+                          "fft_passes": {"staged": fft_passes(prof32, args.steps, hbm),
+                                         "per_thread_loads": dict(fft_passes(prof32u, args.steps, hbm),
+                                                                  ms_per_step=round(sum(ms32u) / len(ms32u), 4))},
                           "dtype": "f32 transforms and combines, float-float recurrence, f64 nodes",
                           "breakdown": {k: round(v["ms"] / args.steps, 4)
                                         for k, v in sorted(prof32.items(), key=lambda kv: -kv[1]["ms"])}},
@@ -514,6 +523,29 @@ def run_gpu(args, world, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return out
+
+
+def fft_passes(prof, steps, hbm):
+    """ms per step, launches and achieved algorithmic GB/s (2 x N x 8 bytes per
+    vector and pass) of the FP32 FFT passes in a profiled run."""
+    out = {}
+    for k in ("fft32_cols", "fft32_rows"):
+        v = prof.get(k)
+        if v:
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            out[k] = {"ms_per_step": round(v["ms"] / steps, 4), "launches_per_step": v["launches"] / steps,
+                      "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4)}
+    return out
+
+
+def fft_roofline(prof, steps, hbm, hbm_src):
+    """Roofline object of the FP32 form's dominant FFT pass (HBM-bound: its
+    algorithmic bytes are one read and one write of every vector)."""
+    name, v = max(((k, v) for k, v in prof.items() if k in ("fft32_cols", "fft32_rows")), key=lambda kv: kv[1]["ms"])
+    achieved = v["bytes"] / (v["ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "launches_per_step": v["launches"] / steps,
+            "ms_per_launch": round(v["ms"] / v["launches"], 4), "peak_source": hbm_src}
 
 
 def golden_rows(N, c):

@@ -590,10 +590,13 @@ __global__ void __launch_bounds__(FFT_THREADS)
 // (four-step passes), so no bounds tests remain.
 __host__ __device__ constexpr int line_pitch_ct(int L) { return L + (L >> 4) + (L >= 16 ? 1 : 0); }
 
-// tw holds e^{2 pi i j / TABN} at tw[j]: the 4096-entry global table (TABN =
-// 4096) or a shared-memory copy of the first L/2 entries of e^{2 pi i j / L}
-// (TABN = L), which holds every twiddle a line of length L needs
-template <int DIR, int R, int LOGL, int LOGNS, int TABN = FFT_TILE>
+// Twiddles: with R0 = 0, tw is the 4096-entry global table e^{2 pi i j/4096};
+// with R0 > 0 (the radix of the line's first stage), tw is the shared-memory
+// table of tw_fill: for each twiddled radix-16 stage (sub-transform length NS =
+// R0, 16 R0, ...) four rows of NS entries, row b holding the twiddles of
+// r = 2^b, w^{r k} for k < NS, so that the lanes of a warp read consecutive
+// entries (the same rounded values as the global table)
+template <int DIR, int R, int LOGL, int LOGNS, int R0 = 0>
 __device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
   using CT = C2<float>;
   constexpr int L = 1 << LOGL;
@@ -620,12 +623,18 @@ __device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restr
       for (int r = 0; r < R; ++r) v[q][r] = sm[sidx(line, LP, j + r * LR)];
     }
     if constexpr (NS > 1) {
-      const int ks = k * (TABN / (NS * R));
+      const int ks = k * (FFT_TILE / (NS * R));
+      // rows of this stage's shared table (R0 > 0: 4 (NS - R0) / 15 entries precede)
+      const C2<float>* ts = tw + (R0 > 0 ? 4 * (NS - R0) / 15 : 0);
       CT w[R];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         if ((r & (r - 1)) == 0) {
-          w[r] = tw[r * ks];
+          if constexpr (R0 > 0) {
+            w[r] = ts[(r == 1 ? 0 : r == 2 ? 1 : r == 4 ? 2 : 3) * NS + k];
+          } else {
+            w[r] = tw[r * ks];
+          }
         } else {
           w[r] = cmul<float>(w[r & (r - 1)], w[r & -r]);
         }
@@ -652,11 +661,11 @@ __device__ __forceinline__ void stage_ct(C2<float>* sm, const C2<float>* __restr
   __syncthreads();
 }
 
-template <int DIR, int LOGL, int LOGNS, int TABN = FFT_TILE>
+template <int DIR, int LOGL, int LOGNS, int R0 = 0>
 __device__ __forceinline__ void r16_stages_ct(C2<float>* sm, const C2<float>* __restrict__ tw) {
   if constexpr (LOGNS < LOGL) {
-    stage_ct<DIR, 16, LOGL, LOGNS, TABN>(sm, tw);
-    r16_stages_ct<DIR, LOGL, LOGNS + 4, TABN>(sm, tw);
+    stage_ct<DIR, 16, LOGL, LOGNS, R0>(sm, tw);
+    r16_stages_ct<DIR, LOGL, LOGNS + 4, R0>(sm, tw);
   }
 }
 
@@ -689,16 +698,17 @@ __device__ __forceinline__ void epi_slot(int i, int& k, int& c) {
 }
 
 // Inter-pass twiddles of a column tile (columns c0 + c, c < C):
-// T[c][q] = e^{2 pi i (256/C)(c0 + c) q / N}, q < 16, filled by the CTA; the
-// thread with line c and first row k0 multiplies B = e^{2 pi i (c0 + c) k0 / N}
-// by T[c][q] for row k0 + (256/C) q.  Two rounded factors and one product, as
+// T[q][c] = e^{2 pi i (256/C)(c0 + c) q / N}, q < 16, filled by the CTA (the
+// lines of a half-warp read consecutive entries); the thread with line c and
+// first row k0 multiplies B = e^{2 pi i (c0 + c) k0 / N} by T[q][c] for row
+// k0 + (256/C) q.  Two rounded factors and one product, as
 // with a two-level table, but only 16 C + 256 sines and cosines per tile and no
 // global loads.
 template <int LOGC>
 __device__ __forceinline__ void tw_tile_fill(C2<float>* T, int c0, float two_over_n) {
   constexpr int C = 1 << LOGC;
   for (int j = threadIdx.x; j < 16 * C; j += FFT_THREADS) {
-    const int c = j >> 4, q = j & 15;
+    const int q = j >> LOGC, c = j & (C - 1);
     T[j] = tw_pow2_f32((int64_t)(256 / C) * (c0 + c) * q, two_over_n);
   }
 }
@@ -738,7 +748,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4)
 #pragma unroll 4
   for (int q = 0; q < PER; ++q) {
     const int k1 = k0 + (256 / C) * q;
-    const CT w = cmul<float>(B, tws[16 * c + q]);
+    const CT w = cmul<float>(B, tws[q * C + c]);
     const CT val = cmul<float>(sm[sidx(c, LP, k1)], mk<float>(w.x, DIR > 0 ? w.y : -w.y));
     g[(int64_t)k1 * L2 + c0 + c] = val;
   }
@@ -915,7 +925,7 @@ __device__ __forceinline__ void stage_first_ct(const C2<float>* __restrict__ S, 
   __syncthreads();
 }
 
-// tw: the shared-memory table e^{2 pi i j / L}, j < L/2 (tw_fill)
+// tw: the shared-memory twiddle rows of tw_fill
 template <int DIR, int LOGL, bool COLS>
 __device__ __forceinline__ void fft_tile_staged(const C2<float>* S, C2<float>* W, const C2<float>* __restrict__ tw,
                                                 uint64_t* bar, bool issue_next, const void* next_src,
@@ -936,16 +946,33 @@ __device__ __forceinline__ void fft_tile_staged(const C2<float>* S, C2<float>* W
       tma::load_1d((void*)S, next_src, FFT_TILE * sizeof(C2<float>), bar);
     }
   }
-  r16_stages_ct<DIR, LOGL, (REM == 0 ? 4 : REM), (1 << LOGL)>(W, tw);
+  r16_stages_ct<DIR, LOGL, (REM == 0 ? 4 : REM), (REM == 0 ? 16 : (1 << REM))>(W, tw);
 }
 
-// T[j] = e^{2 pi i j / L} = tw4096[j 4096 / L] for j < L/2: the same rounded
-// values as the global table, so the staged passes stay bitwise equal to the
-// others
+// Shared-memory twiddles of the radix-16 stages of a line of length L = 2^LOGL
+// (first stage radix R0, untwiddled): stage NS = R0 16^s (NS < L) holds four
+// rows [b][k], k < NS, with tw4096[2^b k 4096 / (16 NS)] = e^{2 pi i 2^b k /
+// (16 NS)}, the same rounded values the global table gives, so the staged passes
+// stay bitwise equal to the others.  Entries: 4 (L - R0) / 15.
+template <int LOGL>
+__host__ __device__ constexpr int tw_rows_r0() {
+  return (LOGL & 3) == 0 ? 16 : 1 << (LOGL & 3);
+}
+template <int LOGL>
+__host__ __device__ constexpr int tw_rows_len() {
+  return 4 * ((1 << LOGL) - tw_rows_r0<LOGL>()) / 15;
+}
 template <int LOGL>
 __device__ __forceinline__ void tw_fill(C2<float>* T, const C2<float>* __restrict__ tw4096) {
-  constexpr int L = 1 << LOGL;
-  for (int j = threadIdx.x; j < L / 2; j += FFT_THREADS) T[j] = tw4096[j * (FFT_TILE / L)];
+  constexpr int R0 = tw_rows_r0<LOGL>(), L = 1 << LOGL;
+  for (int e = threadIdx.x; e < tw_rows_len<LOGL>(); e += FFT_THREADS) {
+    // stage of entry e: offsets 4 (NS - R0) / 15 for NS = R0, 16 R0, ...
+    int NS = R0;
+    while (NS * 16 < L && e >= 4 * (NS * 16 - R0) / 15) NS *= 16;
+    const int o = e - 4 * (NS - R0) / 15;
+    const int b = o / NS, k = o % NS;
+    T[e] = tw4096[(1 << b) * k * (FFT_TILE / (16 * NS))];
+  }
 }
 
 template <int DIR, int LOGL1>
@@ -961,7 +988,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   CT* S = reinterpret_cast<CT*>(smraw);
   CT* W = S + FFT_TILE;
   CT* T = W + C * LP;
-  CT* tws = T + L1 / 2;
+  CT* tws = T + tw_rows_len<LOGL1>();
   uint64_t* bar = reinterpret_cast<uint64_t*>(tws + 16 * C);
   const float ton = 2.0f / (float)N;
   const int nblk = L2 / C;
@@ -1003,7 +1030,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
 #pragma unroll 4
     for (int q = 0; q < PER; ++q) {
       const int k1 = k0 + (256 / C) * q;
-      const CT w = cmul<float>(B, tws[16 * c + q]);
+      const CT w = cmul<float>(B, tws[q * C + c]);
       const CT val = cmul<float>(W[sidx(c, LP, k1)], mk<float>(w.x, DIR > 0 ? w.y : -w.y));
       g[(int64_t)k1 * L2 + c0 + c] = val;
     }
@@ -1022,7 +1049,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   CT* S = reinterpret_cast<CT*>(smraw);
   CT* W = S + FFT_TILE;
   CT* T = W + C2n * LP;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(T + L2 / 2);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(T + tw_rows_len<LOGL2>());
   const int nblk = L1 / C2n;
   int64_t t = blockIdx.x;
   if (t >= ntiles) return;
@@ -1120,8 +1147,8 @@ bool set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 // dynamic shared memory of a staged FP32 pass over lines of length L: staging
-// tile, padded work tile, twiddle table (L/2 entries), the column pass's tile
-// twiddles (16 C entries), mbarrier
+// tile, padded work tile, twiddle rows (at most L/2 entries), the column pass's
+// tile twiddles (16 C entries), mbarrier
 constexpr size_t tma_smem_bytes(int L) {
   return (size_t)(FFT_TILE + (FFT_TILE / L) * line_pitch_ct(L) + L / 2 + 16 * (FFT_TILE / L)) * sizeof(C2<float>) +
          16;
