@@ -15,6 +15,8 @@
 // runs on a pipe 64 times wider than FP64 on GB300).  Per term: one product of
 // two table entries and one multiply-add, so FP64 issue bounds the FP64 form;
 // FP64 plans with h <= kHeadTabMax use the stored products below instead.
+#include <type_traits>
+
 #include "gbdlt_internal.cuh"
 
 namespace gbdlt {
@@ -207,6 +209,97 @@ __global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict
   }
 }
 
+// ---------------------------------------------------------------- tiled product (h <= kHeadMM)
+// FP32 plans with a small head block (h <= kHeadMM, N <= 8192) run both
+// directions as one tiled product over the batch, for single and batched calls
+// alike (FP64 plans keep the per-warp kernels with stored products, which
+// measured faster: 0.26 against 0.31 ms for 246 items at N = 4096).  Per
+// parity p the block is G_p[a][m] = Lam'_{m-a} Lam'_{m+a+p} (a <= m, halved at
+// a = 0 when p = 0; a exact power-of-two scaling), k = p + 2a, n = p + 2m:
+//   forward     chat_{p+2a} += sum_{m >= a} G_p[a][m] c_{p+2m}
+//   transposed  out_{p+2m}  += s_n sum_{a <= m} G_p[a][m] y_{p+2a}.
+// A CTA computes 64 outputs of one parity for 32 batch items; the reduction
+// index runs through chunks of 32 staged in shared memory (G entries formed
+// there from the table, the inputs gathered), and each output is summed in
+// ascending reduction order, sequentially (an FP64 fused multiply-add chain, a
+// Kahan-compensated FP32 sum), so the result of an item does not depend on how
+// many items a call carries.  Thread t: item t mod 32, outputs 8 (t / 32) + i.
+constexpr int64_t kHeadMM = 2048;
+constexpr int MMO = 64, MMB = 32, MMR = 32;
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_head_mm(const T* __restrict__ x, T* __restrict__ out,
+                                                 const T* __restrict__ lam, int64_t N, int64_t h, int scale_s,
+                                                 double* __restrict__ hout, int64_t hs, int64_t nb) {
+  __shared__ T Gs[MMR][MMO];
+  __shared__ T Xs[MMR][MMB];
+  const int par = blockIdx.x & 1;
+  const int64_t H = (h - par + 1) / 2;  // indices of this parity below h
+  const int64_t o0 = (int64_t)(blockIdx.x >> 1) * MMO;
+  const int64_t b0 = (int64_t)blockIdx.y * MMB;
+  if (o0 >= H) return;  // whole CTA
+  const int tb = threadIdx.x & 31, og = threadIdx.x >> 5;
+  // reduction range: forward r = m in [o0, H), transposed r = a in [0, min(o0 + MMO, H))
+  const int64_t r_lo = TRANS ? 0 : o0;
+  const int64_t r_hi = TRANS ? min(o0 + MMO, H) : H;
+  T acc[8], cmp[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = cmp[i] = (T)0;
+  for (int64_t r0 = r_lo; r0 < r_hi; r0 += MMR) {
+    // G tile: entry (rr, oo) for reduction index r0 + rr and output o0 + oo
+    for (int e = threadIdx.x; e < MMR * MMO; e += 256) {
+      const int rr = e / MMO, oo = e % MMO;
+      const int64_t r = r0 + rr, o = o0 + oo;
+      const int64_t a = TRANS ? r : o, m = TRANS ? o : r;
+      T g = (T)0;
+      if (r < r_hi && o < H && a <= m) {
+        g = lam[m - a] * lam[m + a + par];
+        if (par == 0 && a == 0) g *= (T)0.5;
+      }
+      Gs[rr][oo] = g;
+    }
+    for (int e = threadIdx.x; e < MMR * MMB; e += 256) {
+      const int rr = e / MMB, bb = e % MMB;
+      const int64_t r = r0 + rr, b = b0 + bb;
+      Xs[rr][bb] = (r < r_hi && b < nb) ? x[b * N + par + 2 * r] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < MMR; ++rr) {
+      const T xv = Xs[rr][tb];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const T g = Gs[rr][og * 8 + i];
+        if constexpr (std::is_same<T, double>::value) {
+          acc[i] = fma(g, xv, acc[i]);
+        } else {
+          // Kahan step on the product g x (the per-warp kernels' arithmetic)
+          const float v = __fmul_rn(g, xv);
+          const float y = __fsub_rn(v, cmp[i]);
+          const float t = __fadd_rn(acc[i], y);
+          cmp[i] = __fsub_rn(__fsub_rn(t, acc[i]), y);
+          acc[i] = t;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t b = b0 + tb;
+  if (b >= nb) return;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t o = o0 + og * 8 + i;
+    if (o >= H) break;
+    const int64_t idx = par + 2 * o;  // output coefficient k (forward) or n (transposed)
+    double s = std::is_same<T, double>::value ? (double)acc[i] : (double)acc[i] - (double)cmp[i];
+    if (TRANS && scale_s) s *= (double)idx + 0.5;
+    if (hout)
+      hout[b * hs + idx] = s;
+    else
+      out[b * N + idx] = (T)((double)out[b * N + idx] + s);
+  }
+}
+
 }  // namespace
 
 int launch_head_tab_init(Plan& P) {
@@ -217,11 +310,22 @@ int launch_head_tab_init(Plan& P) {
   return check_launch();
 }
 
+// grid of k_head_mm: (output tiles x 2 parities, item tiles)
+inline dim3 head_mm_grid(int64_t h, int64_t nb) {
+  return dim3((unsigned)(2 * (((h + 1) / 2 + MMO - 1) / MMO)), (unsigned)((nb + MMB - 1) / MMB));
+}
+
 template <typename T>
 int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb, double* hout) {
   const int64_t h = P.p.head;
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
+  if (sizeof(T) == 4 && h <= kHeadMM) {
+    k_head_mm<T, false><<<head_mm_grid(h, nb), 256, 0, P.stream>>>(c, chat, lam, P.p.N, h, 0, hout,
+                                                                   P.p.N * (int64_t)sizeof(T) / 8, nb);
+    launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * (double)sizeof(T) * 2.0 * (double)h);
+    return check_launch();
+  }
   if constexpr (sizeof(T) == 8) {
     if (P.head_tab && !hout) {
       k_head_fwd_tab<<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(
@@ -242,6 +346,13 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* 
   const int64_t h = P.p.head;
   if (h == 0) return GBDLT_OK;
   const T* lam = sizeof(T) == 8 ? (const T*)P.head_lam : (const T*)P.head_lamf;
+  if (sizeof(T) == 4 && h <= kHeadMM) {
+    k_head_mm<T, true><<<head_mm_grid(h, nb), 256, 0, P.stream>>>(y, out, lam, P.p.N, h, scale_s, hout,
+                                                                  P.p.N * (int64_t)sizeof(T) / 8, nb);
+    launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h,
+             (double)nb * (double)sizeof(T) * 2.0 * (double)h);
+    return check_launch();
+  }
   if constexpr (sizeof(T) == 8) {
     if (P.head_tab) {
       k_head_t_tab<<<dim3((unsigned)(2 * ((h + 63) / 64)), (unsigned)nb), TW * 32, 0, P.stream>>>(
