@@ -548,7 +548,8 @@ struct LayoutHost {
 
 void build_ctas(RecLayout& R, int64_t H, int S, int j0, int pack, LayoutHost& h);
 
-void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int j0, int sms, LayoutHost& h) {
+void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int j0, int sms, int64_t batch,
+                  LayoutHost& h) {
   R.H = H;
   R.S = S;
   R.j0 = j0;
@@ -569,15 +570,16 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
   R.nblocks = (H + 255) / 256;
   // CTAs: segments of a row block, several per CTA when their active rows fill
   // only A < 8 warps (A warps per segment, q = 8 / A segments), provided the
-  // packed launch still has two CTAs per SM (small transforms need the SMs more
-  // than full CTAs)
+  // packed launch still has two CTAs per SM over the batch the plan is made for
+  // (small transforms need the SMs more than full CTAs; the per-segment
+  // arithmetic is the same either way)
   for (int pack = 1; pack >= 0; --pack) {
     h.cta_rb.clear();
     h.cta_j.clear();
     h.maxcut.clear();
     h.toff.clear();
     build_ctas(R, H, S, j0, pack, h);
-    if (!pack || (int64_t)h.cta_rb.size() >= 2 * (int64_t)sms) break;
+    if (!pack || (int64_t)h.cta_rb.size() * batch >= 2 * (int64_t)sms) break;
   }
   R.ncta = (int64_t)h.cta_rb.size();
   // the transposed reduction relies on row blocks in order of non-increasing cut
@@ -644,18 +646,19 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   }
   // recurrence layouts (host): the fast path's region on the cheb1 rows, and the
   // direct method's full rows at the Legendre nodes
+  const int64_t batch_hint = max_batch > 0 ? max_batch : 1;
   LayoutHost hf, hd;
   if (prm.fast) {
     const int64_t H = N / 2;
     std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1), (int32_t)N);
     for (const Band& b : prm.bands)
       for (int64_t k = b.ka; k < b.kb; ++k) cut[(size_t)k] = (int32_t)b.ns;
-    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), sms, hf);
+    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), sms, batch_hint, hf);
   }
   P->has_direct = N > 1 && N <= kDirectMax && (prm.method == GBDLT_METHOD_DIRECT || want_direct);
   if (P->has_direct) {
     const int64_t H = (N + 1) / 2;
-    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, sms, hd);
+    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, sms, batch_hint, hd);
   }
   RecLayout& R = P->rec;
   RecLayout& D = P->drec;
