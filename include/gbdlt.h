@@ -160,6 +160,15 @@ int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
  * A staged copy that has not landed after about two seconds makes the next
  * gbdlt_plan_sync return GBDLT_ERR_CUDA. */
 int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable);
+/* SM clock cycles a staged FFT pass of this plan waits for a tile copy before
+ * it gives up (0 <= sm_cycles <= 2^32; default 2^32, about two seconds).  A pass
+ * that gives up records it (the next gbdlt_plan_sync returns GBDLT_ERR_CUDA and
+ * clears the record), waits once more with the default limit for its own copy
+ * in flight, and ends without finishing its tiles (that call's results are
+ * unspecified).  A failure-path hook: a small limit reaches this status with no
+ * fault.  Clears the plan's replayed graphs.  GBDLT_ERR_INVALID_ARG for other
+ * values. */
+int gbdlt_plan_set_wait_limit(gbdlt_plan plan, int64_t sm_cycles);
 
 /* Legendre nodes and weights (Eq. 1 and Eq. 2; Sec. 2.1-2.2): recomputes the
  * plan's node cache on the GPU and copies any requested array out.  Ordering:

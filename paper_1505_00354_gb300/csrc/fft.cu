@@ -862,15 +862,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// true once phase `parity` of the barrier has completed; false after ~2^32 SM
-// cycles without completion
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+// SM cycles a staged pass waits for a tile copy before it gives up (about 2 s)
+constexpr long long kWaitCycles = 1ll << 32;
+// non-blocking test of phase `parity` (try_wait may suspend the thread for a
+// while before it answers)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once phase `parity` of the barrier has completed; false after `limit` SM
+// cycles without completion (limit 0: unless it has completed already)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  if (mbar_test_wait(bar, parity)) return true;
+  if (limit <= 0) return false;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 32)) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+// A wait that ran out: record it in the plan status (bit 2) and wait once more,
+// with the full limit, for the CTA's own copy in flight before the CTA returns,
+// so that no copy lands in shared memory the CTA no longer owns.
+__device__ __forceinline__ void give_up(uint64_t* bar, uint32_t parity, int* status) {
+  if (threadIdx.x == 0) {
+    atomicOr(status, 2);
+    mbar_wait(bar, parity, kWaitCycles);
+  }
+  __syncthreads();
 }
 __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
@@ -979,7 +1003,8 @@ template <int DIR, int LOGL1>
 __global__ void __launch_bounds__(FFT_THREADS, 3)
     k_fft32_cols_tma(const __grid_constant__ CUtensorMap map, C2<float>* __restrict__ data, int64_t N, int L2,
                      const C2<float>* __restrict__ tw4096, const C2<float>* __restrict__ thi,
-                     const C2<float>* __restrict__ tlo, VecMap vm, int64_t ntiles, int* __restrict__ status) {
+                     const C2<float>* __restrict__ tlo, VecMap vm, int64_t ntiles, int* __restrict__ status,
+                     long long wait_limit) {
   using CT = C2<float>;
   constexpr int L1 = 1 << LOGL1, LOGC = 12 - LOGL1, C = 1 << LOGC, LP = line_pitch_ct(L1);
   constexpr int PER = FFT_TILE / FFT_THREADS;
@@ -1010,9 +1035,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   }
   uint32_t phase = 0;
   for (; t < ntiles; t += gridDim.x) {
-    const bool ok = tma::mbar_wait(bar, phase);
+    const bool ok = tma::mbar_wait(bar, phase, wait_limit);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(status, 2);
+      tma::give_up(bar, phase, status);
       return;
     }
     phase ^= 1;
@@ -1041,7 +1066,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
 template <int DIR, int LOGL2>
 __global__ void __launch_bounds__(FFT_THREADS, 3)
     k_fft32_rows_tma(const C2<float>* __restrict__ in, C2<float>* __restrict__ out, int64_t N, int L1,
-                     const C2<float>* __restrict__ tw4096, VecMap vm, int64_t ntiles, int* __restrict__ status) {
+                     const C2<float>* __restrict__ tw4096, VecMap vm, int64_t ntiles, int* __restrict__ status,
+                     long long wait_limit) {
   using CT = C2<float>;
   constexpr int L2 = 1 << LOGL2, LOGC2 = 12 - LOGL2, C2n = 1 << LOGC2, LP = line_pitch_ct(L2);
   constexpr int PER = FFT_TILE / FFT_THREADS;
@@ -1068,9 +1094,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 3)
   }
   uint32_t phase = 0;
   for (; t < ntiles; t += gridDim.x) {
-    const bool ok = tma::mbar_wait(bar, phase);
+    const bool ok = tma::mbar_wait(bar, phase, wait_limit);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(status, 2);
+      tma::give_up(bar, phase, status);
       return;
     }
     phase ^= 1;
@@ -1181,7 +1207,7 @@ static bool launch_fft32_cols_tma(int logL1, Plan& P, C2<float>* a, int64_t N, i
   case LG:                                                                                                    \
     if (!set_smem(k_fft32_cols_tma<DIR, LG>, smem)) return false;                                             \
     k_fft32_cols_tma<DIR, LG><<<(unsigned)grid, FFT_THREADS, smem, P.stream>>>(map, a, N, L2, tw, thi, tlo, vm, \
-                                                                               ntiles, P.status);             \
+                                                                               ntiles, P.status, P.tma_wait); \
     return true;
     GBDLT_C32T(7) GBDLT_C32T(8) GBDLT_C32T(9) GBDLT_C32T(10) GBDLT_C32T(11)
 #undef GBDLT_C32T
@@ -1205,7 +1231,8 @@ static bool launch_fft32_rows_tma(int logL2, Plan& P, const C2<float>* a, C2<flo
 #define GBDLT_R32T(LG)                                                                                              \
   case LG:                                                                                                          \
     if (!set_smem(k_fft32_rows_tma<DIR, LG>, smem)) return false;                                                   \
-    k_fft32_rows_tma<DIR, LG><<<(unsigned)grid, FFT_THREADS, smem, P.stream>>>(a, b, N, L1, tw, vm, ntiles, P.status); \
+    k_fft32_rows_tma<DIR, LG><<<(unsigned)grid, FFT_THREADS, smem, P.stream>>>(a, b, N, L1, tw, vm, ntiles, P.status, \
+                                                                               P.tma_wait);                    \
     return true;
     GBDLT_R32T(6) GBDLT_R32T(7) GBDLT_R32T(8) GBDLT_R32T(9) GBDLT_R32T(10)
 #undef GBDLT_R32T

@@ -345,6 +345,7 @@ struct Plan {
   // plans, whose FP32 transforms run on the side stream beside FP64 kernels and
   // there leave more room to them as ordinary (non-persistent) grids
   bool no_tma = false;
+  long long tma_wait = 1ll << 32;  // SM cycles a staged pass waits for a tile copy
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
   double CN = 0;         // C_N for the node kernel

@@ -1586,6 +1586,19 @@ int gbdlt_plan_sync(gbdlt_plan plan) {
   return check_launch();
 }
 
+int gbdlt_plan_set_wait_limit(gbdlt_plan plan, int64_t sm_cycles) {
+  if (!plan || sm_cycles < 0 || sm_cycles > (1ll << 32)) return GBDLT_ERR_INVALID_ARG;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (P->tma_wait == sm_cycles) return GBDLT_OK;
+  // replayed chains hold the limit they were captured with
+  if (P->graphs) {
+    if (cudaStreamSynchronize(P->graphs->s) != cudaSuccess) return GBDLT_ERR_CUDA;
+    free_graphs(P);
+  }
+  P->tma_wait = sm_cycles;
+  return GBDLT_OK;
+}
+
 int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable) {
   if (!plan || (enable != 0 && enable != 1)) return GBDLT_ERR_INVALID_ARG;
   Plan* P = reinterpret_cast<Plan*>(plan);

@@ -86,3 +86,28 @@ def test_sync_reports_before_clearing_once(gb):
     assert L.gbdlt_plan_sync(p.handle) == NOT_CONVERGED
     assert L.gbdlt_plan_sync(p.handle) == 0
     assert ctypes.c_int(L.gbdlt_plan_sync(p.handle)).value == 0
+
+
+def test_staged_copy_wait_limit_reports_error(gb):
+    """A staged FFT pass whose tile-copy wait runs out (a limit of 0 cycles)
+    records it: the next sync returns GBDLT_ERR_CUDA once, the context stays
+    usable, and with the default limit the plan's results are again bitwise
+    those of the per-thread-load passes."""
+    import paper_1505_00354_gb300.inputs as inp
+    L = gb.lib()
+    N = 1 << 20
+    p = gb.Plan(N, gb.FP32, method=gb.METHOD_FAST)
+    x = torch.tensor(inp.coeffs(N, 5), dtype=torch.float32, device="cuda")
+    p.set_fft_staging(False)
+    ref = p.dlt(x).clone()
+    p.set_fft_staging(True)
+    p.set_wait_limit(0)
+    p.dlt(x)
+    assert L.gbdlt_plan_sync(p.handle) == -3
+    assert L.gbdlt_plan_sync(p.handle) == 0
+    p.set_wait_limit(1 << 32)
+    y = p.dlt(x)
+    assert L.gbdlt_plan_sync(p.handle) == 0
+    assert torch.equal(y, ref)
+    for bad in (-1, (1 << 32) + 1):
+        assert L.gbdlt_plan_set_wait_limit(p.handle, bad) == -1
