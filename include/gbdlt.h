@@ -236,8 +236,12 @@ int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
  * it).  An execution makes the work wait for `cuda_stream`, gathers `in` into
  * the staging buffers, replays the graph, scatters the results into `out` and
  * makes `cuda_stream` wait for them; it allocates nothing.  Executions of one
- * batch object must not overlap.  gbdlt_batch_create = gbdlt_batch_create_ex
- * with GBDLT_METHOD_AUTO. */
+ * batch object must not overlap.  Direct-method groups whose transforms each
+ * fit one thread block (N <= 512) do not get a chain of their own: all such
+ * transforms of one direction run in a single persistent launch that strides
+ * over a job table fixed at creation (longest transforms first), with results
+ * bitwise those of the group's single-plan calls.  gbdlt_batch_create =
+ * gbdlt_batch_create_ex with GBDLT_METHOD_AUTO. */
 typedef struct gbdlt_batch_s* gbdlt_batch;
 int gbdlt_batch_create(const int64_t* Ns_host, const int32_t* dirs_host, int64_t B, int prec,
                        double eps, gbdlt_batch* out);
@@ -250,6 +254,10 @@ int gbdlt_batch_exec(gbdlt_batch batch, const void* in, void* out, void* cuda_st
  * output pointer may be NULL. */
 int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
                            int32_t* method, double* ms_fast, double* ms_direct);
+/* As gbdlt_batch_group_info, and *fused = 1 where the group runs inside its
+ * direction's persistent direct launch, else 0. */
+int gbdlt_batch_group_info_ex(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
+                              int32_t* method, double* ms_fast, double* ms_direct, int32_t* fused);
 /* total elements of the concatenated layout, number of (N, direction) groups,
  * kernel nodes in the captured graph (any pointer may be NULL) */
 int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int64_t* groups,

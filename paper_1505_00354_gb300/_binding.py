@@ -88,7 +88,7 @@ ENTRY_POINTS = (
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
     "gbdlt_batch_create", "gbdlt_batch_create_ex", "gbdlt_batch_exec", "gbdlt_batch_info",
-    "gbdlt_batch_group_info", "gbdlt_batch_destroy",
+    "gbdlt_batch_group_info", "gbdlt_batch_group_info_ex", "gbdlt_batch_destroy",
     "gbdlt_status_string", "gbdlt_launch_count", "gbdlt_device_alloc_count",
 )
 
@@ -128,6 +128,10 @@ def lib():
         L.gbdlt_batch_group_info.argtypes = [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        L.gbdlt_batch_group_info_ex.argtypes = [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                                ctypes.POINTER(ctypes.c_int32)]
         L.gbdlt_batch_exec.argtypes = [vp, vp, vp, vp]
         L.gbdlt_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.gbdlt_batch_destroy.argtypes = [vp]
@@ -322,16 +326,18 @@ class Batch:
         return {"total_elements": t.value, "groups": g.value, "graph_kernels": k.value}
 
     def groups(self) -> list:
-        """Per (N, direction) group: N, dir, count, method and the autotuner's timings."""
+        """Per (N, direction) group: N, dir, count, method, the autotuner's timings
+        and whether it runs inside its direction's persistent direct launch."""
         out = []
         for g in range(self.info()["groups"]):
             N, d, c, m = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
-            tf, td = ctypes.c_double(), ctypes.c_double()
-            _check(lib().gbdlt_batch_group_info(self._h, g, ctypes.byref(N), ctypes.byref(d), ctypes.byref(c),
-                                                ctypes.byref(m), ctypes.byref(tf), ctypes.byref(td)),
+            tf, td, fu = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+            _check(lib().gbdlt_batch_group_info_ex(self._h, g, ctypes.byref(N), ctypes.byref(d), ctypes.byref(c),
+                                                   ctypes.byref(m), ctypes.byref(tf), ctypes.byref(td),
+                                                   ctypes.byref(fu)),
                    "batch_group_info")
             out.append({"N": N.value, "dir": d.value, "count": c.value, "method": m.value,
-                        "ms_fast": tf.value, "ms_direct": td.value})
+                        "ms_fast": tf.value, "ms_direct": td.value, "fused": bool(fu.value)})
         return out
 
     def run(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

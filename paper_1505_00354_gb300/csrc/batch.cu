@@ -42,6 +42,7 @@ struct BatchGroup {
   int lane;           // internal stream the group runs on
   int method;         // GBDLT_METHOD_FAST or GBDLT_METHOD_DIRECT
   double ms_fast = -1.0, ms_direct = -1.0;  // autotuner timings (-1: not timed)
+  bool fused = false;  // runs inside the direction's persistent direct launch
 };
 
 struct Batch {
@@ -60,6 +61,8 @@ struct Batch {
   int64_t* d_len = nullptr;    // [B] N_i
   void* stage_in = nullptr;
   void* stage_out = nullptr;
+  DirectMulti* direct[2] = {};  // persistent direct launches (DLT, IDLT) over the small groups
+  int direct_lane[2] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;  // kernel nodes one replay launches
@@ -99,7 +102,12 @@ int run_groups(Batch& b) {
   if (cudaEventRecord(b.ev_fork, b.s) != cudaSuccess) return GBDLT_ERR_CUDA;
   for (int l = 0; l < b.nlanes; ++l)
     if (cudaStreamWaitEvent(b.lane_s[l], b.ev_fork, 0) != cudaSuccess) return GBDLT_ERR_CUDA;
+  for (int d = 0; d < 2; ++d) {
+    int st = direct_multi_launch(b.direct[d], b.lane_s[b.direct_lane[d]]);
+    if (st) return st;
+  }
   for (const BatchGroup& g : b.groups) {
+    if (g.fused) continue;
     int st = run_group(b, g, g.method);
     if (st) return st;
   }
@@ -134,6 +142,7 @@ void free_batch(Batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (DirectMulti* d : b->direct) direct_multi_free(d);
   for (Plan* p : b->plans) free_plan(p);
   if (b->d_src) cudaFree(b->d_src);
   if (b->stage_in) cudaFree(b->stage_in);
@@ -263,6 +272,23 @@ extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs
     if (st) return fail(st);
     g.method = g.ms_direct < g.ms_fast ? GBDLT_METHOD_DIRECT : GBDLT_METHOD_FAST;
   }
+  // direct-method groups whose transforms each fit one CTA run as one persistent
+  // launch per direction, on the lane of the largest such group
+  for (int d = 0; d < 2; ++d) {
+    std::vector<DirectGroupRef> refs;
+    int lane = -1;
+    for (BatchGroup& g : b->groups) {
+      if (g.dir != d || g.method != GBDLT_METHOD_DIRECT || !direct_fusable(*g.plan)) continue;
+      refs.push_back({g.plan, g.count, (const char*)b->stage_in + (size_t)g.stage_off * es,
+                      (char*)b->stage_out + (size_t)g.stage_off * es});
+      g.fused = true;
+      if (lane < 0) lane = g.lane;  // groups are in order of decreasing work
+    }
+    if (refs.empty()) continue;
+    int st = direct_multi_create(refs, prec, d, &b->direct[d]);
+    if (st) return fail(st);
+    b->direct_lane[d] = lane;
+  }
   // one plain run (kernel attributes, lazy module loading), then capture
   int st = run_groups(*b);
   if (st) return fail(st);
@@ -327,6 +353,11 @@ extern "C" int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int6
 
 extern "C" int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
                                       int32_t* method, double* ms_fast, double* ms_direct) {
+  return gbdlt_batch_group_info_ex(batch, g, N, dir, count, method, ms_fast, ms_direct, nullptr);
+}
+
+extern "C" int gbdlt_batch_group_info_ex(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
+                                         int32_t* method, double* ms_fast, double* ms_direct, int32_t* fused) {
   if (!batch) return GBDLT_ERR_INVALID_ARG;
   Batch& b = *reinterpret_cast<Batch*>(batch);
   if (g < 0 || g >= (int64_t)b.groups.size()) return GBDLT_ERR_INVALID_ARG;
@@ -337,6 +368,7 @@ extern "C" int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, 
   if (method) *method = G.method;
   if (ms_fast) *ms_fast = G.ms_fast;
   if (ms_direct) *ms_direct = G.ms_direct;
+  if (fused) *fused = G.fused ? 1 : 0;
   return GBDLT_OK;
 }
 

@@ -440,6 +440,23 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb,
                          const double* zw = nullptr, int scale_out = 0);
 // x_k - 1 of the cheb1 rows (fast path) or of the Legendre nodes (direct method)
 int launch_rec_xm1(Plan& P, RecLayout& L, int legendre);
+// Many small direct-method transforms in one persistent launch (uneven batches):
+// the groups' transforms, `count` vectors of length N each, contiguous from
+// `in` / `out`, all of one direction (0: DLT, 1: IDLT).  Only plans whose direct
+// layout is one CTA (direct_fusable) take part; results are bitwise those of
+// run_op_method with GBDLT_METHOD_DIRECT.
+struct DirectGroupRef {
+  Plan* plan;
+  int64_t count;
+  const void* in;
+  void* out;
+};
+struct DirectMulti;
+bool direct_fusable(const Plan& P);
+int direct_multi_create(const std::vector<DirectGroupRef>& groups, int prec, int dir, DirectMulti** out);
+int direct_multi_launch(DirectMulti* d, cudaStream_t s);
+int64_t direct_multi_jobs(const DirectMulti* d);
+void direct_multi_free(DirectMulti* d);
 // stages.cu (prologues / epilogues)
 // band vectors of terms m < M64 in U / Y / F (precision T), of terms
 // M64 <= m < Mh in Uff / Yff / Fff (float-float) and of terms m >= Mh in U32 /

@@ -27,6 +27,8 @@
 // the FP32 form runs it in float-float (compensated FP32, ~2^-44 per operation)
 // on the FP32 pipe, which is 58 times faster than the FP64 pipe on GB300.
 #include <algorithm>
+#include <new>
+#include <vector>
 
 #include "gbdlt_internal.cuh"
 
@@ -169,8 +171,8 @@ struct RecTask {
   int jj, A, q;   // segment slot within the CTA, warps per segment, segments
   bool in;        // this warp has a segment
 };
-__device__ __forceinline__ RecTask rec_task(const RecArgs& R) {
-  const int code = R.cta_j[blockIdx.x];
+__device__ __forceinline__ RecTask rec_task(const RecArgs& R, int64_t cta) {
+  const int code = R.cta_j[cta];
   RecTask t;
   t.A = ((code >> 16) & 15) + 1;
   t.q = ((code >> 20) & 15) + 1;
@@ -178,7 +180,7 @@ __device__ __forceinline__ RecTask rec_task(const RecArgs& R) {
   t.jj = w / t.A;
   t.j = (code & 0xffff) + t.jj;
   t.in = t.jj < t.q;
-  t.rb = R.cta_rb[blockIdx.x];
+  t.rb = R.cta_rb[cta];
   t.k = t.rb * RT + (w - t.jj * t.A) * 32 + (threadIdx.x & 31);
   return t;
 }
@@ -205,7 +207,7 @@ __global__ void k_rec_lead(RecArgs R, double2* __restrict__ state) {
 
 // transfer matrix of one full segment: images of the basis states (1,0), (0,1)
 __global__ void k_rec_basis(RecArgs R, double2* __restrict__ Tbuf) {
-  const RecTask t = rec_task(R);
+  const RecTask t = rec_task(R, blockIdx.x);
   const int64_t k = t.k;
   const int j = t.j;
   if (!t.in || k >= R.H) return;
@@ -249,19 +251,19 @@ __global__ void k_rec_scan(RecArgs R, const double2* __restrict__ Tbuf, double2*
   }
 }
 
-// forward: per (half row, segment) the partial sums E (even n) and O (odd n)
+// forward: per (half row, segment) the partial sums E (even n) and O (odd n) of
+// the thread's row in CTA `cta` of the layout; false when the thread has none
+// (o: its slot in the partial array)
 template <typename T>
-__global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__ c,
-                                                double2* __restrict__ part) {
-  c += (int64_t)blockIdx.y * R.N;
-  part += (int64_t)blockIdx.y * R.nseg_total;
-  const RecTask t = rec_task(R);
+__device__ __forceinline__ bool rec_fwd_body(const RecArgs& R, int64_t cta, const T* __restrict__ c, int64_t& o,
+                                             double2& EO) {
+  const RecTask t = rec_task(R, cta);
   const int64_t k = t.k;
   const int j = t.j;
-  if (!t.in || k >= R.H) return;
+  if (!t.in || k >= R.H) return false;
   const int cut = R.cut[k];
-  if (j >= (cut + R.S - 1) / R.S) return;
-  const int64_t o = R.poff[k] + j - R.j0;
+  if (j >= (cut + R.S - 1) / R.S) return false;
+  o = R.poff[k] + j - R.j0;
   const double2 st = R.state[o];
   const double xm1 = R.xm1[k];
   double P = st.x, G = st.y / xm1;
@@ -278,22 +280,21 @@ __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__
     P = fma(xm1, G, P);
   }
   if (n < n1) E = fma((double)c[n], P, E);
-  part[o] = make_double2(E, O);
+  EO = make_double2(E, O);
+  return true;
 }
 
 // FP32 form: the same segment sums with the recurrence in float-float and the
 // products c_n P_n accumulated in Kahan-compensated float
-__global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __restrict__ c,
-                                                   double2* __restrict__ part) {
-  c += (int64_t)blockIdx.y * R.N;
-  part += (int64_t)blockIdx.y * R.nseg_total;
-  const RecTask t = rec_task(R);
+__device__ __forceinline__ bool rec_fwd_body_ff(const RecArgs& R, int64_t cta, const float* __restrict__ c,
+                                                int64_t& o, double2& EO) {
+  const RecTask t = rec_task(R, cta);
   const int64_t k = t.k;
   const int j = t.j;
-  if (!t.in || k >= R.H) return;
+  if (!t.in || k >= R.H) return false;
   const int cut = R.cut[k];
-  if (j >= (cut + R.S - 1) / R.S) return;
-  const int64_t o = R.poff[k] + j - R.j0;
+  if (j >= (cut + R.S - 1) / R.S) return false;
+  o = R.poff[k] + j - R.j0;
   const double2 st = R.state[o];
   ffv P = ff_from(st.x), D = ff_from(st.y);
   const ffv xm1 = ff_from(R.xm1[k]);
@@ -310,7 +311,27 @@ __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __res
     P = ff_add(P, D);
   }
   if (n < n1) kahan_add(Es, Ec, __fmul_rn(c[n], P.hi));
-  part[o] = make_double2((double)Es - (double)Ec, (double)Os - (double)Oc);
+  EO = make_double2((double)Es - (double)Ec, (double)Os - (double)Oc);
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__ c,
+                                                double2* __restrict__ part) {
+  c += (int64_t)blockIdx.y * R.N;
+  part += (int64_t)blockIdx.y * R.nseg_total;
+  int64_t o;
+  double2 EO;
+  if (rec_fwd_body<T>(R, blockIdx.x, c, o, EO)) part[o] = EO;
+}
+
+__global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __restrict__ c,
+                                                   double2* __restrict__ part) {
+  c += (int64_t)blockIdx.y * R.N;
+  part += (int64_t)blockIdx.y * R.nseg_total;
+  int64_t o;
+  double2 EO;
+  if (rec_fwd_body_ff(R, blockIdx.x, c, o, EO)) part[o] = EO;
 }
 
 // sum of a half row's segment partials; warp per row for rows [r0, r1) when
@@ -367,16 +388,14 @@ __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T*
 // lane i's column is that of i.
 constexpr int TP = 33;  // tile pitch
 
+// The column partials of CTA `cta`: on return (after a CTA barrier) wsum[w][c]
+// (sm + 8 * 32 * TP) holds warp w's sum of column c of its segment.
 template <typename T>
-__global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z,
-                                              double* __restrict__ tbuf) {
-  z += (int64_t)blockIdx.y * R.N;
-  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
-  extern __shared__ double sm[];
+__device__ __forceinline__ RecTask rec_t_body(const RecArgs& R, int64_t cta, const T* __restrict__ z, double* sm) {
   double* tile = sm;                  // [8][32][TP]
   double* wsum = sm + 8 * 32 * TP;    // [8][S] per-warp column partials
   double2* zt = reinterpret_cast<double2*>(wsum + 8 * R.S);  // [8][32] (z+, z-)
-  const RecTask t = rec_task(R);
+  const RecTask t = rec_task(R, cta);
   const int64_t rbk = t.rb;
   const int j = t.j;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -436,6 +455,18 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
     __syncwarp();
   }
   __syncthreads();
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z,
+                                              double* __restrict__ tbuf) {
+  z += (int64_t)blockIdx.y * R.N;
+  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
+  extern __shared__ double sm[];
+  const RecTask t = rec_t_body<T>(R, blockIdx.x, z, sm);
+  const double* wsum = sm + 8 * 32 * TP;
+  const int64_t rbk = t.rb;
   // per segment of the CTA, the sum of its A warps' column partials
   const int jf = t.j - t.jj;
   for (int idx = threadIdx.x; idx < t.q * R.S; idx += RT) {
@@ -449,15 +480,13 @@ __global__ void __launch_bounds__(RT) k_rec_t(RecArgs R, const T* __restrict__ z
 }
 
 // FP32 form of k_rec_t: recurrence in float-float, products and the tile /
-// warp sums in float, row-block partials stored in double
-__global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restrict__ z,
-                                                 double* __restrict__ tbuf) {
-  z += (int64_t)blockIdx.y * R.N;
-  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
-  extern __shared__ float smf[];
+// warp sums in float, row-block partials stored in double.  On return (after a
+// CTA barrier) wsum[w][c] (smf + 8 * 32 * TP) holds warp w's column sums.
+__device__ __forceinline__ RecTask rec_t_body_ff(const RecArgs& R, int64_t cta, const float* __restrict__ z,
+                                                 float* smf) {
   float* tile = smf;                 // [8][32][TP]
   float* wsum = smf + 8 * 32 * TP;   // [8][S]
-  const RecTask t = rec_task(R);
+  const RecTask t = rec_task(R, cta);
   const int64_t rbk = t.rb;
   const int j = t.j;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -514,6 +543,17 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
     __syncwarp();
   }
   __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restrict__ z,
+                                                 double* __restrict__ tbuf) {
+  z += (int64_t)blockIdx.y * R.N;
+  tbuf += (int64_t)blockIdx.y * R.tbuf_total;
+  extern __shared__ float smf[];
+  const RecTask t = rec_t_body_ff(R, blockIdx.x, z, smf);
+  const float* wsum = smf + 8 * 32 * TP;
+  const int64_t rbk = t.rb;
   const int jf = t.j - t.jj;
   for (int idx = threadIdx.x; idx < t.q * R.S; idx += RT) {
     const int sl = idx / R.S, c = idx - sl * R.S;
@@ -596,6 +636,79 @@ __global__ void k_rec_t_reduce_final(RecArgs R, const double* __restrict__ tbuf,
   }
   if (R.scale_out) s *= (double)n + 0.5;
   out[n] = (T)s;
+}
+
+// Direct method over many small transforms in one launch: each job is one
+// transform whose direct layout is a single CTA (one row block, one segment per
+// row: N <= S), so the CTA finishes the whole transform, reductions included.
+// A persistent grid strides over the job table fixed at batch creation.  The
+// arithmetic is that of the per-plan chain step for step (partial sums added
+// from 0.0 in the same order, the same casts), so the outputs are bitwise those
+// of single-plan calls.
+struct DirectJob {
+  int32_t arg;  // index of the transform's RecArgs
+  int32_t pad;
+  const void* in;
+  void* out;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_direct_fwd_multi(const RecArgs* __restrict__ args,
+                                                         const DirectJob* __restrict__ jobs, int64_t njobs) {
+  for (int64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    const DirectJob J = jobs[jb];
+    const RecArgs& R = args[J.arg];
+    int64_t o;
+    double2 EO;
+    bool have;
+    if constexpr (sizeof(T) == 4)
+      have = rec_fwd_body_ff(R, 0, (const float*)J.in, o, EO);
+    else
+      have = rec_fwd_body<T>(R, 0, (const T*)J.in, o, EO);
+    const RecTask t = rec_task(R, 0);
+    if (t.in && t.k < R.H) {
+      // the row's one partial, added from 0.0 as the row reduction does
+      const double E = 0.0 + (have ? EO.x : 0.0), O = 0.0 + (have ? EO.y : 0.0);
+      T* f = (T*)J.out;
+      f[t.k] = (T)(E + O);
+      if (t.k != R.mid) f[R.N - 1 - t.k] = (T)(E - O);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_direct_t_multi(const RecArgs* __restrict__ args,
+                                                       const DirectJob* __restrict__ jobs, int64_t njobs) {
+  extern __shared__ double sm[];
+  for (int64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    const DirectJob J = jobs[jb];
+    const RecArgs& R = args[J.arg];
+    RecTask t;
+    if constexpr (sizeof(T) == 4)
+      t = rec_t_body_ff(R, 0, (const float*)J.in, reinterpret_cast<float*>(sm));
+    else
+      t = rec_t_body<T>(R, 0, (const T*)J.in, sm);
+    const int64_t mc = R.maxcut[0];
+    T* out = (T*)J.out;
+    for (int c = threadIdx.x; c < R.N; c += RT) {
+      // the block partial (warp partials from 0.0), then the column reduction
+      // over the one row block (from 0.0) and the output scale
+      double s = 0.0;
+      if (c < mc) {
+        if constexpr (sizeof(T) == 4) {
+          const float* wsum = reinterpret_cast<const float*>(sm) + 8 * 32 * TP;
+          for (int a = 0; a < t.A; ++a) s += (double)wsum[a * R.S + c];
+        } else {
+          const double* wsum = sm + 8 * 32 * TP;
+          for (int a = 0; a < t.A; ++a) s += wsum[a * R.S + c];
+        }
+      }
+      double v = 0.0 + s;
+      if (R.scale_out) v *= (double)c + 0.5;
+      out[c] = (T)v;
+    }
+    __syncthreads();  // the next job rewrites the tiles and partials
+  }
 }
 
 }  // namespace
@@ -697,6 +810,127 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb, 
   launched(P, "rec_t_reduce", (double)nb * (double)L.tbuf_total,
            (double)nb * (8.0 * (double)L.tbuf_total + (double)sizeof(T) * P.p.N));
   return check_launch();
+}
+
+struct DirectMulti {
+  int prec = GBDLT_FP64;
+  int dir = 0;
+  int64_t njobs = 0;
+  RecArgs* args = nullptr;  // device [groups]
+  DirectJob* jobs = nullptr;
+  unsigned grid = 0;
+  size_t smem = 0;
+};
+
+bool direct_fusable(const Plan& P) {
+  const RecLayout& L = P.drec;
+  return P.has_direct && P.p.N > 1 && L.H > 0 && L.ncta == 1 && L.nblocks == 1 && L.j0 == 0 &&
+         L.nseg_total == L.H && L.n_heavy <= 0 && P.p.N <= L.S;
+}
+
+int direct_multi_create(const std::vector<DirectGroupRef>& groups, int prec, int dir, DirectMulti** out) {
+  *out = nullptr;
+  if (groups.empty()) return GBDLT_OK;
+  DirectMulti* d = new (std::nothrow) DirectMulti();
+  if (!d) return GBDLT_ERR_OOM;
+  d->prec = prec;
+  d->dir = dir;
+  const size_t es = prec == GBDLT_FP64 ? 8 : 4;
+  std::vector<RecArgs> args;
+  std::vector<std::pair<int64_t, DirectJob>> jobs;  // (N, job), longest first
+  for (const DirectGroupRef& g : groups) {
+    if (!direct_fusable(*g.plan)) {
+      direct_multi_free(d);
+      return GBDLT_ERR_INVALID_ARG;
+    }
+    RecArgs R = rec_args(*g.plan, g.plan->drec);
+    if (dir == 1) {
+      R.zw = g.plan->w;
+      R.scale_out = 1;
+    }
+    const int64_t N = g.plan->p.N;
+    for (int64_t i = 0; i < g.count; ++i) {
+      DirectJob J;
+      J.arg = (int32_t)args.size();
+      J.pad = 0;
+      J.in = (const char*)g.in + (size_t)(i * N) * es;
+      J.out = (char*)g.out + (size_t)(i * N) * es;
+      jobs.push_back({N, J});
+    }
+    args.push_back(R);
+  }
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [](const std::pair<int64_t, DirectJob>& a, const std::pair<int64_t, DirectJob>& b) {
+                     return a.first > b.first;
+                   });
+  std::vector<DirectJob> table;
+  for (auto& j : jobs) table.push_back(j.second);
+  d->njobs = (int64_t)table.size();
+  if (dev_malloc((void**)&d->args, sizeof(RecArgs) * args.size()) != cudaSuccess ||
+      dev_malloc((void**)&d->jobs, sizeof(DirectJob) * table.size()) != cudaSuccess) {
+    cudaGetLastError();
+    direct_multi_free(d);
+    return GBDLT_ERR_OOM;
+  }
+  if (cudaMemcpy(d->args, args.data(), sizeof(RecArgs) * args.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d->jobs, table.data(), sizeof(DirectJob) * table.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    direct_multi_free(d);
+    return GBDLT_ERR_CUDA;
+  }
+  // persistent grid: the CTAs the SMs hold at once, or one per job
+  const void* fn = nullptr;
+  int S = 0;
+  for (const DirectGroupRef& g : groups) S = std::max(S, g.plan->drec.S);
+  if (dir == 0) {
+    fn = prec == GBDLT_FP64 ? (const void*)k_direct_fwd_multi<double> : (const void*)k_direct_fwd_multi<float>;
+  } else {
+    d->smem = es * (8 * 32 * TP + 8 * (size_t)S) + (es == 8 ? 16 * RT : 0);
+    fn = prec == GBDLT_FP64 ? (const void*)k_direct_t_multi<double> : (const void*)k_direct_t_multi<float>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) != cudaSuccess) {
+      direct_multi_free(d);
+      return GBDLT_ERR_CUDA;
+    }
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RT, d->smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  d->grid = (unsigned)std::min<int64_t>(d->njobs, (int64_t)per_sm * sms);
+  *out = d;
+  return GBDLT_OK;
+}
+
+int direct_multi_launch(DirectMulti* d, cudaStream_t s) {
+  if (!d || d->njobs == 0) return GBDLT_OK;
+  if (d->dir == 0) {
+    if (d->prec == GBDLT_FP64)
+      k_direct_fwd_multi<double><<<d->grid, RT, 0, s>>>(d->args, d->jobs, d->njobs);
+    else
+      k_direct_fwd_multi<float><<<d->grid, RT, 0, s>>>(d->args, d->jobs, d->njobs);
+  } else {
+    if (d->prec == GBDLT_FP64)
+      k_direct_t_multi<double><<<d->grid, RT, d->smem, s>>>(d->args, d->jobs, d->njobs);
+    else
+      k_direct_t_multi<float><<<d->grid, RT, d->smem, s>>>(d->args, d->jobs, d->njobs);
+  }
+  count_launch();
+  return check_launch();
+}
+
+int64_t direct_multi_jobs(const DirectMulti* d) { return d ? d->njobs : 0; }
+
+void direct_multi_free(DirectMulti* d) {
+  if (!d) return;
+  if (d->args) cudaFree(d->args);
+  if (d->jobs) cudaFree(d->jobs);
+  delete d;
 }
 
 template int launch_rec_forward<double>(Plan&, RecLayout&, const double*, double*, int64_t);

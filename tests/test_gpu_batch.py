@@ -89,6 +89,52 @@ def test_uneven_batch(gb, prec):
     assert worst <= (1e-12 if prec == 0 else 5e-6)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_small_direct_groups_one_launch(gb, prec):
+    """Lengths 1..600 drawn without rounding (odd and even, many groups): the
+    direct-method groups with N <= 512 run in one persistent launch per
+    direction, bitwise equal to single-plan calls, and sampled rows match the
+    oracle."""
+    import oracle
+    from paper_1505_00354_gb300 import inputs
+    rng = np.random.default_rng(7)
+    B = 700
+    Ns = rng.integers(1, 601, B).astype(np.int64)
+    Ns[:4] = [1, 2, 3, 512]
+    dirs = rng.integers(0, 2, B).astype(np.int32)
+    x = np.concatenate([inputs.coeffs(int(N), 5000 + i, 1.0) for i, N in enumerate(Ns)])
+    dt = torch.float64 if prec == 0 else torch.float32
+    b = gb.Batch(Ns, dirs, prec)
+    groups = b.groups()
+    fused = [G for G in groups if G["fused"]]
+    assert fused and all(G["method"] == gb.METHOD_DIRECT and 1 < G["N"] <= 512 for G in fused)
+    # every direct group of N in 2..512 is fused: two launches replace their chains
+    assert all(G["fused"] for G in groups if G["method"] == gb.METHOD_DIRECT and 1 < G["N"] <= 512)
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    y = b.run(xd)
+    off = b.offsets
+    for G in groups:
+        N, d = G["N"], G["dir"]
+        p = gb.get_plan(int(N), prec, method=G["method"])
+        idx = np.nonzero((Ns == N) & (dirs == d))[0]
+        X = torch.stack([xd[off[i]:off[i + 1]] for i in idx])
+        Y = p.dlt(X) if d == 0 else p.idlt(X)
+        got = torch.stack([y[off[i]:off[i + 1]] for i in idx])
+        assert torch.equal(got, Y), (N, d, G["method"], G["fused"])
+    worst = 0.0
+    for i in rng.choice(B, 16, replace=False):
+        N = int(Ns[i])
+        xi = xd[off[i]:off[i + 1]].double().cpu().numpy()
+        yi = y[off[i]:off[i + 1]].double().cpu().numpy()
+        nd = oracle.legpts(N)
+        if dirs[i] == 0:
+            err = np.max(np.abs(yi - oracle.dlt_rows(xi, nd))) / np.abs(xi).sum()
+        else:
+            err = np.max(np.abs(yi - oracle.idlt(xi, nd)) / ((np.arange(N) + 0.5) * np.abs(nd.w * xi).sum()))
+        worst = max(worst, err)
+    assert worst <= (1e-12 if prec == 0 else 5e-6)
+
+
 def test_batch_errors(gb):
     import ctypes
     L = gb.lib()
