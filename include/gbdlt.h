@@ -69,13 +69,19 @@ enum {
 };
 
 /* How a plan computes gbdlt_dlt, gbdlt_idlt and their transposes.
- * GBDLT_METHOD_FAST: the FFT-based chain of Sec. 2-4 (N a power of two).
+ * GBDLT_METHOD_FAST: the FFT-based chain of Sec. 2-4.  For N a power of two it
+ *   runs on the N-point Chebyshev grid; for other N on the grid of the next
+ *   power of two G (gbdlt_params.grid_n): coefficient vectors are zero-padded
+ *   to G, the rows are the N-point Gauss-Legendre rule, each row's Taylor
+ *   expansion (Sec. 2.1-2.3) is taken about its nearest grid point, and L
+ *   follows from Corollary 2.4 with |n dtheta| <= (N-1) pi / (2G) in place of
+ *   0.83845; the cost is close to that of a plan for G.
  * GBDLT_METHOD_DIRECT: the O(N^2) sums of Eq. (1) and (2) evaluated by the
  *   three-term recurrence at the Legendre nodes (any N <= 65536); the direct
  *   approach the paper compares against, and faster on GB300 for small N.
- * GBDLT_METHOD_AUTO: DIRECT when N is not a power of two or N <= 256, FAST
- *   otherwise.  leg2cheb and chebeval always run the FFT-based chain and need
- *   N to be a power of two. */
+ * GBDLT_METHOD_AUTO: DIRECT when N <= 256, FAST otherwise.  leg2cheb and
+ *   chebeval always run the FFT-based chain (a DIRECT plan whose N is not a
+ *   power of two has none: GBDLT_ERR_UNSUPPORTED_N). */
 enum { GBDLT_METHOD_AUTO = 0, GBDLT_METHOD_FAST = 1, GBDLT_METHOD_DIRECT = 2 };
 
 /* Parameters the plan derives from (N, precision, eps) by the error bounds of
@@ -108,6 +114,9 @@ typedef struct {
                           FFTs in float-float arithmetic (FP32 pipe)            */
   int L_ff;            /* FP64 plans: the last L_ff Taylor terms run their FFTs
                           and combines in float-float                           */
+  int64_t grid_n;      /* fast path: length of the Chebyshev grid and of its FFTs
+                          (N for a power of two, else the next power of two);
+                          0 for a DIRECT plan with N not a power of two        */
 } gbdlt_params;
 
 /* Host-only parameter derivation: no GPU, no allocation.  eps <= 0 selects the
@@ -115,7 +124,7 @@ typedef struct {
  * GBDLT_ERR_UNSUPPORTED_N or GBDLT_ERR_INVALID_ARG on bad input. */
 int gbdlt_plan_params(int64_t N, int prec, double eps, gbdlt_params* out);
 /* The same for a given method (GBDLT_METHOD_*); GBDLT_ERR_UNSUPPORTED_N if N
- * does not suit it (FAST: not a power of two; DIRECT: N > 65536). */
+ * does not suit it (N outside 1..2^24; DIRECT: N > 65536). */
 int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out);
 
 /* Create a plan on the current CUDA device.  `cuda_stream` is a cudaStream_t
@@ -220,8 +229,7 @@ int gbdlt_idlt(gbdlt_plan plan, const void* f, void* c, int64_t batch);
 int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
 
 /* Uneven batches (no counterpart in the paper, which transforms one vector at
- * a time): B transforms of lengths Ns_host[i] (1..2^24; lengths that are not
- * powers of two up to 65536, by the direct method) and directions dirs_host[i]
+ * a time): B transforms of lengths Ns_host[i] (1..2^24) and directions dirs_host[i]
  * (0 = DLT, 1 = IDLT), all of one precision, executed together.  Inputs and
  * outputs are concatenated in the given order: transform i occupies elements
  * [sum_{j<i} Ns[j], sum_{j<=i} Ns[j]) of `in` and `out` (device, element type

@@ -64,6 +64,7 @@ class Params(ctypes.Structure):
         ("M_fp32", ctypes.c_int),
         ("M_ff", ctypes.c_int),
         ("L_ff", ctypes.c_int),
+        ("grid_n", ctypes.c_int64),
     ]
 
     def to_dict(self) -> dict:
@@ -76,7 +77,7 @@ class Params(ctypes.Structure):
             "workspace_bytes": self.workspace_bytes, "method": self.method,
             "direct_steps": self.direct_steps, "head": self.head,
             "M_fp32": self.M_fp32, "M_ff": self.M_ff,
-            "L_ff": self.L_ff,
+            "L_ff": self.L_ff, "grid_n": self.grid_n,
         }
 
 

@@ -11,8 +11,8 @@
 // Method per group (the autotuner): with GBDLT_METHOD_AUTO, a group whose N
 // allows both methods is run and timed with CUDA events through the FFT-based
 // chain and through the direct method (three timed runs each after a warm-up
-// run) and keeps the faster; lengths that are not powers of two take the direct
-// method, lengths above its limit the FFT-based chain.  The timings are kept and
+// run) and keeps the faster; lengths above the direct method's limit take the
+// FFT-based chain (on the next power-of-two grid when N is not a power of two).  The timings are kept and
 // reported by gbdlt_batch_group_info.
 //
 // At creation the chains are run once more with the chosen methods and then
@@ -175,9 +175,7 @@ extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs
     return GBDLT_ERR_INVALID_ARG;
   for (int64_t i = 0; i < B; ++i) {
     const int64_t N = Ns_host[i];
-    const bool pow2 = N >= 1 && (N & (N - 1)) == 0;
     if (N < 1 || N > (1ll << 24)) return GBDLT_ERR_UNSUPPORTED_N;
-    if (!pow2 && (method == GBDLT_METHOD_FAST || N > kDirectMax)) return GBDLT_ERR_UNSUPPORTED_N;
     if (method == GBDLT_METHOD_DIRECT && N > kDirectMax) return GBDLT_ERR_UNSUPPORTED_N;
     if (dirs_host[i] != 0 && dirs_host[i] != 1) return GBDLT_ERR_INVALID_ARG;
   }
@@ -233,10 +231,8 @@ extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs
     g.stage_off = soff;
     g.lane = (int)(std::min_element(lane_load.begin(), lane_load.end()) - lane_load.begin());
     lane_load[g.lane] += -ok.first;
-    const bool pow2 = (g.N & (g.N - 1)) == 0;
     const bool can_direct = g.N > 1 && g.N <= kDirectMax;
     int m = method;
-    if (!pow2) m = GBDLT_METHOD_DIRECT;
     if (m == GBDLT_METHOD_AUTO && !can_direct) m = GBDLT_METHOD_FAST;
     Plan* p = nullptr;
     const int plan_method = m == GBDLT_METHOD_AUTO ? GBDLT_METHOD_FAST : m;

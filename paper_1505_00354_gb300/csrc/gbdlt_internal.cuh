@@ -224,6 +224,9 @@ struct Params {
                                    // terms Mh..M-1 of an FP64 plan run in FP32
   int M64 = 0;                     // of those, terms M64..Mh-1 of an FP64 plan run in float-float
   int Lff = 0;                     // Taylor terms l >= Lff of an FP64 plan run in float-float
+  int64_t grid = 0;                // fast path: length G of the Chebyshev grid and FFTs (N for a
+                                   // power of two, the next power of two otherwise); 0: direct only
+  double taylor_b = 0.83845;       // bound on |n dtheta_k| behind L and Lff (Corollary 2.4)
 };
 
 // Direct method limits: largest N a direct plan accepts, and the largest
@@ -236,8 +239,10 @@ constexpr int64_t kHeadMax = 1 << 16;
 constexpr int64_t kHeadTabMax = 1 << 15;
 
 // Fills Params from (N, prec, eps, method): Taylor terms, asymptotic terms, bands
-// and the method the plan runs.
-int derive_params(int64_t N, int prec, double eps, int method, Params* p);
+// and the method the plan runs.  taylor_b bounds |n dtheta_k| over the columns
+// and rows the Taylor step serves (0.83845 for the Legendre nodes against the
+// cheb1 grid of the same N, Lemma 2.3).
+int derive_params(int64_t N, int prec, double eps, int method, Params* p, double taylor_b = 0.83845);
 // Host table of C_n = sqrt(4/pi) Gamma(n+1)/Gamma(n+3/2), n = 0..N (double-double recurrence).
 std::vector<double> cn_table(int64_t N);
 
@@ -356,6 +361,20 @@ struct Plan {
   bool side_broken = false;  // creation failed: everything on the plan stream
   struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
   struct GraphCache* graphs = nullptr;  // replayed transform chains (plan.cu)
+  // N not a power of two (grid.cu): the fast path is the chain of `inner`, a plan
+  // on the power-of-two grid G > N, fed with inputs zero-padded to G; this plan
+  // keeps the N-point rule (and the direct method's layout)
+  Plan* inner = nullptr;
+  void* rg_in = nullptr;   // [bcap][G] padded inputs
+  void* rg_out = nullptr;  // [bcap][G] chain outputs before truncation to N
+  // on an inner plan: the rows of the outer N-point rule on this plan's grid
+  int64_t rg_n = 0;              // N of the outer rule (0: the rows are this plan's own nodes)
+  int32_t* rg_j = nullptr;       // [rg_n] grid point j(k) nearest theta_k
+  int32_t* rg_kf = nullptr;      // [G + 1] first row k with j(k) >= j
+  double* rg_t = nullptr;        // [rg_n] G (theta_k - (j(k) + 1/2) pi / G)
+  const double* rg_w = nullptr;  // [rg_n] the outer rule's weights
+  void* rg_g = nullptr;          // [bcap][G] rows summed onto their grid points
+  void* rg_block = nullptr;      // the allocation holding rg_j .. rg_g
 };
 
 // Taylor pairs whose FFTs run in the plan's precision: pair p holds terms
@@ -445,6 +464,19 @@ int launch_rec_xm1(Plan& P, RecLayout& L, int legendre);
 // `in` / `out`, all of one direction (0: DLT, 1: IDLT).  Only plans whose direct
 // layout is one CTA (direct_fusable) take part; results are bitwise those of
 // run_op_method with GBDLT_METHOD_DIRECT.
+// grid.cu: plans for N that is not a power of two.  grid_attach builds the
+// row-to-grid maps of the outer plan's rule on its inner plan; launch_grid_pad
+// copies [nb][N] into [nb][G] with zeros past N, launch_grid_cut the first N of
+// each [G] row back; launch_grid_scatter sums the rows (times w_k when use_w)
+// onto their grid points (the l = 0 Taylor term of the transposed chain).
+int grid_attach(Plan& O, Plan& I);
+template <typename T>
+int launch_grid_pad(Plan& P, const T* in, T* out, int64_t N, int64_t G, int64_t nb);
+template <typename T>
+int launch_grid_cut(Plan& P, const T* in, T* out, int64_t N, int64_t G, int64_t nb);
+template <typename T>
+int launch_grid_scatter(Plan& I, const T* g, int use_w, T* out, int64_t nb);
+
 struct DirectGroupRef {
   Plan* plan;
   int64_t count;

@@ -267,7 +267,7 @@ static DPResult plan_bands(int64_t N, int M, double eps_asy, double tcost, doubl
   return best_res;
 }
 
-int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
+int derive_params(int64_t N, int prec, double eps, int method, Params* p, double taylor_b) {
   if (N < 1 || N > (1ll << 24)) return GBDLT_ERR_UNSUPPORTED_N;
   if (prec != GBDLT_FP64 && prec != GBDLT_FP32) return GBDLT_ERR_INVALID_ARG;
   if (method != GBDLT_METHOD_AUTO && method != GBDLT_METHOD_FAST && method != GBDLT_METHOD_DIRECT)
@@ -275,26 +275,49 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
   if (eps <= 0.0) eps = prec == GBDLT_FP64 ? 1e-14 : 2e-6;
   if (!(eps < 1.0) || !std::isfinite(eps)) return GBDLT_ERR_INVALID_ARG;
   const bool pow2 = (N & (N - 1)) == 0;
-  if (method == GBDLT_METHOD_AUTO)
-    method = (!pow2 || N <= kDirectAuto) ? GBDLT_METHOD_DIRECT : GBDLT_METHOD_FAST;
-  if (method == GBDLT_METHOD_FAST && !pow2) return GBDLT_ERR_UNSUPPORTED_N;
+  if (method == GBDLT_METHOD_AUTO) method = N <= kDirectAuto ? GBDLT_METHOD_DIRECT : GBDLT_METHOD_FAST;
   if (method == GBDLT_METHOD_DIRECT && N > kDirectMax) return GBDLT_ERR_UNSUPPORTED_N;
+  if (method == GBDLT_METHOD_FAST && !pow2) {
+    // The chain on the power-of-two grid G > N (FFT length G): the coefficients
+    // are zero-padded to G (leg2cheb of the padded vector gives the same
+    // Chebyshev coefficients: the Legendre series has degree N - 1 < G) and every
+    // row theta_k of the N-point rule takes its Taylor expansion about the
+    // nearest point (j + 1/2) pi / G of the grid, |theta_k - theta'_j| <= pi/(2G).
+    // Over the columns n < N, |n dtheta_k| <= (N - 1) pi / (2G): the bound of
+    // Corollary 2.4 with that in place of 0.83845 fixes L.
+    int64_t G = 1;
+    while (G < N) G <<= 1;
+    const double b = (double)(N - 1) * M_PI / (2.0 * (double)G) * (1.0 + 1e-9);
+    Params q;
+    int st = derive_params(G, prec, eps, GBDLT_METHOD_FAST, &q, b);
+    if (st) return st;
+    q.N = N;
+    q.direct_steps = N <= kDirectMax ? ((N + 1) / 2) * N : 0;
+    const double dsz = prec == GBDLT_FP64 ? 8.0 : 4.0;
+    q.bytes_dlt = (2.0 * dsz + 8.0) * (double)N;
+    q.bytes_idlt = (2.0 * dsz + 16.0) * (double)N;
+    *p = q;
+    return GBDLT_OK;
+  }
   Params q;
   q.N = N;
   q.prec = prec;
   q.eps = eps;
   q.method = method;
   q.fast = pow2;
-  // Corollary 2.4 with theta* = theta^cheb1: |f - f_L| <= 0.83845^L / L! ||c||_1
+  q.grid = pow2 ? N : 0;
+  q.taylor_b = taylor_b;
+  // Corollary 2.4 with theta* = theta^cheb1: |f - f_L| <= b^L / L! ||c||_1,
+  // b = 0.83845 (or the bound of a grid plan's rows)
   int L = 1;
-  double b = 0.83845;
+  double b = taylor_b;
   while (b > 0.5 * eps && L < 24) {
     ++L;
-    b *= 0.83845 / L;
+    b *= taylor_b / L;
   }
   q.L = L;
   // Taylor terms l >= Lff run their FFTs and combines in float-float in FP64
-  // plans: term l is at most 0.83845^l / l! ||c||_1 (Corollary 2.4) and a
+  // plans: term l is at most b^l / l! ||c||_1 (Corollary 2.4) and a
   // float-float FFT of it errs by about 2 log2(N) 2^-46 of that; the tail
   // l >= Lff keeps the sum of those errors within eps/20
   q.Lff = L;
@@ -305,7 +328,7 @@ int derive_params(int64_t N, int prec, double eps, int method, Params* p) {
     double err = 0.0;
     for (int l = L - 1; l >= 1; --l) {
       double tl = 1.0;
-      for (int i = 1; i <= l; ++i) tl *= 0.83845 / i;
+      for (int i = 1; i <= l; ++i) tl *= taylor_b / i;
       if (err + ferr * tl > eps / 20.0) break;
       err += ferr * tl;
       q.Lff = l;
@@ -526,6 +549,9 @@ void free_plan(Plan* P) {
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
   if (P->arena) cudaFree(P->arena);
+  if (P->inner) free_plan(P->inner);
+  if (P->rg_in) cudaFree(P->rg_in);
+  if (P->rg_block) cudaFree(P->rg_block);
   if (P->prof) {
     for (cudaEvent_t e : P->prof->ev) cudaEventDestroy(e);
     delete P->prof;
@@ -623,11 +649,57 @@ struct LayoutOff {
 
 }  // namespace
 
+static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch, int want_direct, Plan** out);
+
 int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t stream, int64_t max_batch,
                      int want_direct, Plan** out) {
   Params prm;
   int st = derive_params(N, prec, eps, method, &prm);
   if (st != GBDLT_OK) return st;
+  if (!(prm.method == GBDLT_METHOD_FAST && prm.grid != N)) return plan_build(prm, stream, max_batch, want_direct, out);
+  // N not a power of two (grid.cu): the chain of a plan on the grid G > N, and
+  // this plan's own arena for the N-point rule (and the direct layout)
+  Params pi;
+  st = derive_params(prm.grid, prec, eps, GBDLT_METHOD_FAST, &pi, prm.taylor_b);
+  if (st != GBDLT_OK) return st;
+  Plan* I = nullptr;
+  st = plan_build(pi, stream, max_batch, 0, &I);
+  if (st != GBDLT_OK) return st;
+  Params po = prm;
+  po.fast = false;
+  Plan* O = nullptr;
+  st = plan_build(po, stream, max_batch, want_direct, &O);
+  if (st != GBDLT_OK) {
+    free_plan(I);
+    return st;
+  }
+  O->p = prm;
+  O->inner = I;
+  O->no_tma = I->no_tma;
+  O->bcap = std::min(O->bcap, I->bcap);
+  O->ws_bytes += I->ws_bytes;
+  const size_t ts = prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
+  const size_t rg = ts * (size_t)O->bcap * (size_t)prm.grid;
+  if (dev_malloc(&O->rg_in, 2 * rg) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(O);
+    return GBDLT_ERR_OOM;
+  }
+  O->rg_out = (char*)O->rg_in + rg;
+  O->ws_bytes += 2 * rg;
+  st = grid_attach(*O, *I);
+  if (st != GBDLT_OK) {
+    free_plan(O);
+    return st;
+  }
+  *out = O;
+  return GBDLT_OK;
+}
+
+static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch, int want_direct, Plan** out) {
+  const int64_t N = prm.N;
+  const int prec = prm.prec;
+  int st = GBDLT_OK;
   Plan* P = new (std::nothrow) Plan();
   if (!P) return GBDLT_ERR_OOM;
   P->p = prm;
@@ -1160,7 +1232,17 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
     if (st) return st;
   }
   void* U = Y ? other(P, Y) : P.bufA;
-  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g, inc0 ? 0 : use_w, z, (C2<T>*)U, (ffc*)P.bufAff,
+  // the l = 0 term in value space: the rows themselves, or (rows of an outer
+  // rule, grid.cu) the rows summed onto their grid points
+  const T* g0 = g;
+  int w0 = use_w;
+  if (!inc0 && P.rg_n > 0) {
+    st = launch_grid_scatter<T>(P, g, use_w, (T*)P.rg_g, nb);
+    if (st) return st;
+    g0 = (const T*)P.rg_g;
+    w0 = 0;
+  }
+  st = launch_l2ct_pro<T>(P, Y, inc0 ? nullptr : g0, inc0 ? 0 : w0, z, (C2<T>*)U, (ffc*)P.bufAff,
                           (float2*)P.bufA32, nb);
   if (st) return st;
   const C2<T>* F2 = nullptr;
@@ -1263,6 +1345,60 @@ int run_direct(Plan& P, int op, const T* in, T* out, int64_t nb) {
   return GBDLT_ERR_INVALID_ARG;
 }
 
+// A plan whose N is not a power of two (grid.cu): pad the inputs to the inner
+// plan's grid G, run its chain (rows: this plan's N-point rule), keep the first
+// N outputs of each item.
+template <typename T>
+int run_grid(Plan& O, int op, const T* in, T* out, int64_t nb) {
+  Plan& I = *O.inner;
+  I.stream = O.stream;
+  I.prof = O.prof;
+  const int64_t N = O.p.N, G = I.p.N;
+  T* xi = (T*)O.rg_in;
+  T* xo = (T*)O.rg_out;
+  int st = launch_grid_pad<T>(O, in, xi, N, G, nb);
+  if (st == GBDLT_OK) {
+    switch (op) {
+      case OP_L2C:
+        st = run_leg2cheb<T>(I, xi, xo, nb);
+        break;
+      case OP_L2C_T:
+        st = run_leg2cheb_t<T>(I, xi, xo, nb);
+        break;
+      case OP_CHEB:
+        st = run_taylor<T>(I, xi, nullptr, xo, 1, nb);
+        break;
+      case OP_CHEB_T:
+        st = run_chebeval_t<T>(I, xi, xo, nb);
+        break;
+      case OP_DLT:
+        st = run_leg2cheb<T>(I, xi, (T*)I.chat, nb);
+        if (st == GBDLT_OK) st = run_dlt_tail<T>(I, xo, nb);
+        break;
+      case OP_DLT_T:
+        st = run_transposed<T>(I, xi, xo, 0, 0, nb);
+        break;
+      case OP_IDLT:
+        st = run_transposed<T>(I, xi, xo, 1, 1, nb);
+        break;
+      case OP_IDLT_T: {
+        // out = D_w P D_s g: D_s on the padded vector, D_w (this rule's weights) at the end
+        T* sg = (T*)I.tmp2;
+        st = launch_scale<T>(I, xi, sg, 1, nb);
+        if (st == GBDLT_OK) st = run_leg2cheb<T>(I, sg, (T*)I.chat, nb);
+        if (st == GBDLT_OK) st = run_dlt_tail<T>(I, xo, nb);
+        break;
+      }
+      default:
+        st = GBDLT_ERR_INVALID_ARG;
+    }
+  }
+  if (st == GBDLT_OK) st = launch_grid_cut<T>(O, xo, out, N, G, nb);
+  if (st == GBDLT_OK && op == OP_IDLT_T) st = launch_scale<T>(O, out, out, 2, nb);
+  I.prof = nullptr;
+  return st;
+}
+
 template <typename T>
 int run_one(Plan& P, int op, int method, const T* in, T* out, int64_t nb) {
   const int64_t N = P.p.N;
@@ -1277,7 +1413,8 @@ int run_one(Plan& P, int op, int method, const T* in, T* out, int64_t nb) {
     if (!P.has_direct) return GBDLT_ERR_UNSUPPORTED_N;
     return run_direct<T>(P, op, in, out, nb);
   }
-  if (!P.p.fast) return GBDLT_ERR_UNSUPPORTED_N;  // the FFT-based chains need a power of two
+  if (P.inner) return run_grid<T>(P, op, in, out, nb);
+  if (!P.p.fast) return GBDLT_ERR_UNSUPPORTED_N;  // a direct-method plan for N that is not a power of two
   switch (op) {
     case OP_L2C:
       return run_leg2cheb<T>(P, in, out, nb);
@@ -1477,6 +1614,7 @@ static void fill_public(const Params& q, size_t ws, gbdlt_params* out) {
   out->M_fp32 = q.M - q.Mh;
   out->M_ff = q.Mh - q.M64;
   out->L_ff = q.L - q.Lff;
+  out->grid_n = q.grid;
 }
 
 int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_params* out) {
@@ -1576,8 +1714,13 @@ int gbdlt_plan_sync(gbdlt_plan plan) {
   if (!plan) return GBDLT_ERR_INVALID_ARG;
   Plan* P = reinterpret_cast<Plan*>(plan);
   if (cudaStreamSynchronize(P->stream) != cudaSuccess) return GBDLT_ERR_CUDA;
-  int hs = 0;
+  int hs = 0, hi = 0;
   if (cudaMemcpy(&hs, P->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBDLT_ERR_CUDA;
+  // the chain of a plan for N that is not a power of two runs on its inner plan
+  if (P->inner && cudaMemcpy(&hi, P->inner->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return GBDLT_ERR_CUDA;
+  if (hi) cudaMemset(P->inner->status, 0, sizeof(int));
+  hs |= hi;
   if (hs) {
     cudaMemset(P->status, 0, sizeof(int));
     if (hs & 1) return GBDLT_ERR_NOT_CONVERGED;
@@ -1596,6 +1739,7 @@ int gbdlt_plan_set_wait_limit(gbdlt_plan plan, int64_t sm_cycles) {
     free_graphs(P);
   }
   P->tma_wait = sm_cycles;
+  if (P->inner) P->inner->tma_wait = sm_cycles;
   return GBDLT_OK;
 }
 
@@ -1609,6 +1753,7 @@ int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable) {
     free_graphs(P);
   }
   P->no_tma = enable == 0;
+  if (P->inner) P->inner->no_tma = enable == 0;
   return GBDLT_OK;
 }
 

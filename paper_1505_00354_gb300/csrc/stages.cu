@@ -563,20 +563,25 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, ffc
   }
 }
 
-template <typename T>
+// GRID: the rows are those of an outer rule of nout < N nodes (a plan whose N
+// is not a power of two runs its chain on this grid of N points): row k reads
+// the sums at its grid point j = jmap[k] and tN[k] is its offset N (theta_k -
+// theta'_j) from that point; f keeps the grid's batch stride N.
+template <typename T, bool GRID = false>
 __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Yff, const T* __restrict__ v,
                           T* __restrict__ f, const double* __restrict__ tN, int64_t N, int L, int inc0, int npair,
-                          int P64, Scale32 S) {
+                          int P64, Scale32 S, const int32_t* __restrict__ jmap = nullptr, int64_t nout = 0) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
+  if (k >= (GRID ? nout : N)) return;
   const int64_t bt = blockIdx.y;
   Y += bt * P64 * N;
   if (Yff) Yff += bt * (npair - P64) * N;
   f += bt * N;
   if (v) v += bt * N;
   const T t = (T)tN[k];
-  const bool odd = k & 1;
-  const int64_t idx = odd ? N - 1 - (k >> 1) : (k >> 1);
+  const int64_t j = GRID ? (int64_t)jmap[k] : k;
+  const bool odd = j & 1;
+  const int64_t idx = odd ? N - 1 - (j >> 1) : (j >> 1);
   T acc2 = (T)0;  // twice the sum of the pairs in the plan's precision
   // q_l = t^l / l! advanced term by term: pair p uses l_b = 2p+1 and l_a = 2p (inc0)
   // or 2p+2, so l runs upwards through both parts
@@ -599,7 +604,7 @@ __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Y
       qa = qb * t * (T)kInvInt[la + 2];
     }
   }
-  T acc = inc0 ? (T)0 : v[k];
+  T acc = inc0 ? (T)0 : v[j];
   acc = fma((T)0.5, acc2, acc);
   if (P64 < npair) {
     // float-float pairs, continued from q reached above; outputs scaled by 2^{-E}
@@ -682,6 +687,86 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
       fa1 = fa1 * ft12;
       fb0 = fb0 * ft02;
       fb1 = fb1 * ft12;
+    }
+  }
+}
+
+// k_tayt_pro for the rows of an outer rule on this plan's grid of N points:
+// grid point j collects the rows k with j(k) = j (kf[j] <= k < kf[j+1]; at most
+// two, checked when the maps are built), each with its own offset t_k; the
+// thread of pair jp writes grid points 2jp (to U[jp]) and 2jp + 1 (to
+// U[N-1-jp], with the sign (-1)^j of its sine part) as k_tayt_pro does.
+template <typename T>
+__global__ void k_tayt_pro_grid(const T* __restrict__ fin, const double* __restrict__ wscale,
+                                const double* __restrict__ tr, const int32_t* __restrict__ kf,
+                                C2<T>* __restrict__ U, ffc* __restrict__ Uff, int64_t N, int L, int inc0, int npair,
+                                int P64, Scale32 S) {
+  const int64_t jp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (jp >= N / 2) return;
+  const int64_t bt = blockIdx.y;
+  fin += bt * N;
+  U += bt * P64 * N;
+  if (Uff) Uff += bt * (npair - P64) * N;
+  // slots 0, 1: the rows of grid point 2jp; slots 2, 3: those of 2jp + 1
+  const int64_t ka = kf[2 * jp], kb = kf[2 * jp + 1], kc = kf[2 * jp + 2];
+  T g[4], t[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int64_t k = (s < 2 ? ka : kb) + (s & 1);
+    const bool in = k < (s < 2 ? kb : kc);
+    g[s] = in ? fin[k] : (T)0;
+    if (in && wscale) g[s] *= (T)wscale[k];
+    t[s] = in ? (T)tr[k] : (T)0;
+  }
+  T pa[4], pb[4], t2[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    t2[s] = t[s] * t[s];
+    pa[s] = inc0 ? (T)1 : t2[s];
+    pb[s] = t[s];
+  }
+  for (int p = 0; p < P64; ++p) {
+    const int la = 2 * p + (inc0 ? 0 : 2);
+    const int lb = 2 * p + 1;
+    const T ua = la <= L - 1 ? (T)1 : (T)0;
+    const T ub = lb <= L - 1 ? (T)1 : (T)0;
+    U[(int64_t)p * N + jp] = mk<T>(ua * (pa[0] * g[0] + pa[1] * g[1]), ub * (pb[0] * g[0] + pb[1] * g[1]));
+    U[(int64_t)p * N + N - 1 - jp] = mk<T>(ua * (pa[2] * g[2] + pa[3] * g[3]), -ub * (pb[2] * g[2] + pb[3] * g[3]));
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      pa[s] *= t2[s];
+      pb[s] *= t2[s];
+    }
+  }
+  if (P64 < npair) {
+    // float-float pairs, continued from the powers reached above, scaled by 2^{-E}
+    const int E = item_exp(S, bt);
+    ffd fg[4], ft2[4], fa[4], fb[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      fg[s] = ffd_of(scale2((double)g[s], -E));
+      const ffd ft = ffd_of((double)t[s]);
+      ft2[s] = ft * ft;
+      fa[s] = ffd_of((double)pa[s]);
+      fb[s] = ffd_of((double)pb[s]);
+    }
+    const ffd z(0.f, 0.f);
+    for (int p = P64; p < npair; ++p) {
+      const int la = 2 * p + (inc0 ? 0 : 2);
+      const int lb = 2 * p + 1;
+      const bool ua = la <= L - 1, ub = lb <= L - 1;
+      ffc w0, w1;
+      w0.x = ua ? fa[0] * fg[0] + fa[1] * fg[1] : z;
+      w0.y = ub ? fb[0] * fg[0] + fb[1] * fg[1] : z;
+      w1.x = ua ? fa[2] * fg[2] + fa[3] * fg[3] : z;
+      w1.y = ub ? -(fb[2] * fg[2] + fb[3] * fg[3]) : z;
+      Uff[(int64_t)(p - P64) * N + jp] = w0;
+      Uff[(int64_t)(p - P64) * N + N - 1 - jp] = w1;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        fa[s] = fa[s] * ft2[s];
+        fb[s] = fb[s] * ft2[s];
+      }
     }
   }
 }
@@ -1115,8 +1200,12 @@ int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, ffc* Uff, int inc0, int npa
 template <typename T>
 int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, int inc0, int npair, int64_t nb) {
   const int P64 = Yff ? taylor_p64(P.p, inc0, npair) : npair;
-  k_tay_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, Yff, v, f, P.tN, P.p.N, P.p.L, inc0, npair,
-                                                                       P64, scale32(P));
+  if (P.rg_n > 0)
+    k_tay_epi<T, true><<<dim3(nblk(P.rg_n), (unsigned)nb), TPB, 0, P.stream>>>(
+        Y, Yff, v, f, P.rg_t, P.p.N, P.p.L, inc0, npair, P64, scale32(P), P.rg_j, P.rg_n);
+  else
+    k_tay_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, Yff, v, f, P.tN, P.p.N, P.p.L, inc0,
+                                                                         npair, P64, scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;
@@ -1127,10 +1216,14 @@ int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, in
 }
 template <typename T>
 int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb) {
-  const double* w = use_w ? P.w : nullptr;
   const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
-  k_tayt_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(f, w, P.tN, U, Uff, P.p.N, P.p.L, inc0,
-                                                                           npair, P64, scale32(P));
+  if (P.rg_n > 0)
+    k_tayt_pro_grid<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(
+        f, use_w ? P.rg_w : nullptr, P.rg_t, P.rg_kf, U, Uff, P.p.N, P.p.L, inc0, npair, P64, scale32(P));
+  else
+    k_tayt_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(f, use_w ? P.w : nullptr, P.tN, U, Uff,
+                                                                             P.p.N, P.p.L, inc0, npair, P64,
+                                                                             scale32(P));
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
     const double KM = (double)P.p.K * P.p.M;

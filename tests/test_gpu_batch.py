@@ -139,14 +139,14 @@ def test_batch_errors(gb):
     import ctypes
     L = gb.lib()
     h = ctypes.c_void_p()
-    Ns = (ctypes.c_int64 * 2)(16, 24)
     dirs = (ctypes.c_int32 * 2)(0, 1)
-    # 24 is open to the direct method only; 65537 to neither
-    assert L.gbdlt_batch_create_ex(Ns, dirs, 2, 0, 0.0, 1, ctypes.byref(h)) == -2
+    # 65537 is beyond the direct method; 2^24 + 1 beyond both
     big = (ctypes.c_int64 * 2)(16, 65537)
-    assert L.gbdlt_batch_create(big, dirs, 2, 0, 0.0, ctypes.byref(h)) == -2
-    assert L.gbdlt_batch_create_ex(Ns, dirs, 2, 0, 0.0, 5, ctypes.byref(h)) == -1
+    assert L.gbdlt_batch_create_ex(big, dirs, 2, 0, 0.0, 2, ctypes.byref(h)) == -2
+    huge = (ctypes.c_int64 * 2)(16, 2**24 + 1)
+    assert L.gbdlt_batch_create(huge, dirs, 2, 0, 0.0, ctypes.byref(h)) == -2
     Ns = (ctypes.c_int64 * 2)(16, 32)
+    assert L.gbdlt_batch_create_ex(Ns, dirs, 2, 0, 0.0, 5, ctypes.byref(h)) == -1
     bad = (ctypes.c_int32 * 2)(0, 2)
     assert L.gbdlt_batch_create(Ns, bad, 2, 0, 0.0, ctypes.byref(h)) == -1
     assert L.gbdlt_batch_create(Ns, dirs, 0, 0, 0.0, ctypes.byref(h)) == -1

@@ -121,7 +121,7 @@ def test_direct_matches_fast(gb, N):
 def test_direct_batched_bitwise(gb):
     from paper_1505_00354_gb300 import inputs
     N = 1000
-    p = gb.Plan(N)
+    p = gb.Plan(N, method=gb.METHOD_DIRECT)
     C = dev(np.stack([inputs.coeffs(N, 800 + i, 1.0) for i in range(9)]))
     for op in ("dlt", "dlt_t", "idlt", "idlt_t"):
         full = getattr(p, op)(C)
@@ -137,18 +137,14 @@ def test_batch_methods(gb, method):
     from paper_1505_00354_gb300 import inputs
     rng = np.random.default_rng(90)
     Ns = (2 ** np.round(rng.uniform(4, 12, 600))).astype(np.int64)
-    if method != 1:  # lengths that are not powers of two go to the direct method
-        Ns[::7] = rng.integers(3, 3000, Ns[::7].size)
+    Ns[::7] = rng.integers(3, 3000, Ns[::7].size)  # and lengths that are not powers of two
     dirs = rng.integers(0, 2, Ns.size).astype(np.int32)
     x = np.concatenate([inputs.coeffs(int(n), 91000 + i, 1.0) for i, n in enumerate(Ns)])
     b = gb.Batch(Ns, dirs, gb.FP64, method=method)
     groups = b.groups()
     assert len(groups) == len(set(zip(Ns.tolist(), dirs.tolist())))
     for G in groups:
-        pow2 = (G["N"] & (G["N"] - 1)) == 0
-        if not pow2:
-            assert G["method"] == 2
-        elif method in (1, 2):
+        if method in (1, 2):
             assert G["method"] == method
         elif G["N"] > 1:
             assert G["ms_fast"] > 0 and G["ms_direct"] > 0

@@ -50,8 +50,8 @@ def test_bad_arguments(gb):
     p = gb._binding.Params()
     for bad in (0, 2**25):
         assert lib.gbdlt_plan_params(bad, 0, 0.0, ctypes.byref(p)) == -2
-    # the FFT-based chain needs a power of two; the direct method takes N <= 65536
-    for bad in (3, 6, 1000):
+    # the FFT-based chain takes any N in 1..2^24; the direct method N <= 65536
+    for bad in (0, 2**24 + 1):
         assert lib.gbdlt_plan_params_ex(bad, 0, 0.0, 1, ctypes.byref(p)) == -2
     for bad in (65537, 2**17):
         assert lib.gbdlt_plan_params_ex(bad, 0, 0.0, 2, ctypes.byref(p)) == -2
@@ -65,19 +65,46 @@ def test_bad_arguments(gb):
 
 
 def test_method_selection(gb):
-    """GBDLT_METHOD_AUTO: the direct method for N that is not a power of two or
-    N <= 256, the FFT-based chain otherwise; the direct method's work is
-    ceil(N/2) rows x N columns of the recurrence."""
-    for N, m in ((1, 2), (3, 2), (256, 2), (257, 2), (1000, 2), (512, 1), (4096, 1), (2**20, 1)):
+    """GBDLT_METHOD_AUTO: the direct method for N <= 256, the FFT-based chain
+    otherwise (on the next power-of-two grid when N is not a power of two); the
+    direct method's work is ceil(N/2) rows x N columns of the recurrence."""
+    for N, m in ((1, 2), (3, 2), (256, 2), (257, 1), (1000, 1), (512, 1), (4096, 1), (2**20, 1), (10**6, 1)):
         q = gb.plan_params(N)
         assert q["method"] == m, N
         if m == 2:
             assert q["direct_steps"] == ((N + 1) // 2) * N
-        if N & (N - 1):  # no FFT-based chain: no bands
-            assert q["K"] == 0 and q["M"] == 0
+        if m == 2 and N & (N - 1):  # no FFT-based chain: no bands, no grid
+            assert q["K"] == 0 and q["M"] == 0 and q["grid_n"] == 0
+        if m == 1:
+            assert q["grid_n"] == 1 << (N - 1).bit_length()
     assert gb.plan_params(1024, method=2)["method"] == 2
+    assert gb.plan_params(1000, method=2)["grid_n"] == 0
     assert gb.plan_params(256, method=1)["method"] == 1
     assert gb.plan_params(2**17, method=1)["direct_steps"] == 0
+
+
+@pytest.mark.parametrize("N", [3, 5, 100, 1000, 1025, 3000, 12345, 100000, 10**6, 2**20 - 1, 2**24 - 3])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grid_plan_params(gb, N, prec):
+    """N not a power of two: the chain of the grid G = 2^ceil(log2 N), whose band
+    layout and head block are those of a plan for G; L from Corollary 2.4 with
+    |n dtheta| <= (N-1) pi / (2G) (rows expanded about their nearest grid point)
+    in place of 0.83845."""
+    G = 1 << (N - 1).bit_length()
+    q = gb.plan_params(N, prec, method=gb.METHOD_FAST)
+    qG = gb.plan_params(G, prec, method=gb.METHOD_FAST)
+    assert q["N"] == N and q["grid_n"] == G and q["method"] == gb.METHOD_FAST
+    for key in ("K", "M", "bands", "head", "M_fp32", "M_ff"):
+        assert q[key] == qG[key], key
+    b = (N - 1) * math.pi / (2 * G) * (1 + 1e-9)
+    eps = q["eps"]
+    L = 1
+    while b**L / math.factorial(L) > eps / 2 and L < 24:
+        L += 1
+    assert q["L"] == L
+    # the worst row sits half a grid cell from its point: b is attained up to (N-1)/N
+    assert q["L"] >= qG["L"] or b < 0.83845
+    assert q["direct_steps"] == (((N + 1) // 2) * N if N <= 65536 else 0)
 
 
 def _taylor_L(eps):
