@@ -358,9 +358,12 @@ def run_gpu(args, world, rank, local):
     plan32.set_fft_staging(True)
 
     # ---------------- uneven batch (4096 transforms, N log-uniform in [16, 8192], 50/50)
-    def time_batch(prec):
+    def time_batch(prec, rounded=False):
+        # 4096 transforms, N log-uniform in [16, 8192] (rounded: to the nearest
+        # power of two), 50/50 DLT / IDLT, c ~ N(0,1) (n+1)^-1
         rng = np.random.default_rng(40)
-        Ns = (2 ** np.round(rng.uniform(4, 13, 4096))).astype(np.int64)
+        Nf = 2 ** rng.uniform(4, 13, 4096)
+        Ns = (2 ** np.round(np.log2(Nf)) if rounded else np.round(Nf)).astype(np.int64)
         dirs = rng.integers(0, 2, 4096).astype(np.int32)
         x = np.concatenate([inputs.coeffs(int(n), 4000000 + i, 1.0) for i, n in enumerate(Ns)])
         t0 = time.perf_counter()
@@ -384,11 +387,14 @@ def run_gpu(args, world, rank, local):
         inf = bt.info()
         bt.close()
         return {"value": round(4096 / (ms / 1e3), 1), "unit": "transforms/s", "ms_per_batch": round(ms, 4),
-                "transforms": 4096, "elements": int(Ns.sum()), "groups": inf["groups"],
-                "graph_kernels": inf["graph_kernels"], "create_s": round(t_create, 3)}
+                "transforms": 4096, "lengths": "rounded to powers of two" if rounded else "log-uniform",
+                "distinct_lengths": int(len(set(Ns.tolist()))), "elements": int(Ns.sum()),
+                "groups": inf["groups"], "graph_kernels": inf["graph_kernels"], "create_s": round(t_create, 3)}
 
     batch64 = time_batch(g.FP64)
     batch32 = time_batch(g.FP32)
+    batch64r = time_batch(g.FP64, rounded=True)
+    batch32r = time_batch(g.FP32, rounded=True)
 
     # ---------------- differentiation: loss ||DLT(c) - y||^2, batch 256 x N = 4096
     from paper_1505_00354_gb300 import autograd as gag
@@ -504,8 +510,10 @@ def run_gpu(args, world, rank, local):
                                         "M_ff": params12["M_ff"], "M_fp32": params12["M_fp32"],
                                         "L_ff": params12["L_ff"]}},
             "cold_plan_ms": {"fp64": round(cold64 * 1e3, 2), "fp32": round(cold32 * 1e3, 2)},
-            "batch_uneven": {"workload": "4096 transforms, N = 2^round(U(4,13)), DLT/IDLT 50/50, one graph replay",
-                             "fp64": batch64, "fp32": batch32},
+            "batch_uneven": {"workload": "4096 transforms, N = round(2^U(4,13)) (log-uniform on [16, 8192]), "
+                                         "DLT/IDLT 50/50, one graph replay",
+                             "fp64": batch64, "fp32": batch32,
+                             "rounded_to_powers_of_two": {"fp64": batch64r, "fp32": batch32r}},
             "autograd": {"workload": "loss ||DLT(c) - y||^2, batch 256 x N=4096 FP64, forward + backward",
                          "ms_per_step": round(ms_ag, 4),
                          "transforms_per_s": round(2 * 256 / (ms_ag / 1e3), 1)},

@@ -233,8 +233,13 @@ int gbdlt_idlt_t(gbdlt_plan plan, const void* g, void* out, int64_t batch);
  * (0 = DLT, 1 = IDLT), all of one precision, executed together.  Inputs and
  * outputs are concatenated in the given order: transform i occupies elements
  * [sum_{j<i} Ns[j], sum_{j<=i} Ns[j]) of `in` and `out` (device, element type
- * of `prec`).  Creation groups the transforms by (N, direction), makes one plan
- * per group sized for the whole group, spreads the groups over up to 8 internal
+ * of `prec`).  Creation buckets the transforms by (G, direction), G the power
+ * of two with G/2 < N <= G.  A bucket of one length is one group (N, direction)
+ * with its own plan.  A bucket of several lengths is one grid group (one chain
+ * on the grid G for all its transforms, each with its own N-point rule; see
+ * GBDLT_METHOD_FAST) or, under DIRECT (or AUTO with G <= 512), one direct group
+ * per length.  Every group's plan is sized for the whole group; creation spreads the
+ * groups over up to 8 internal
  * streams, picks each group's method and captures every group's batched chain
  * into one CUDA graph with one branch per stream (1 <= B <= 65535).  With
  * GBDLT_METHOD_AUTO the method of a group that allows both is chosen by timing
@@ -263,9 +268,12 @@ int gbdlt_batch_exec(gbdlt_batch batch, const void* in, void* out, void* cuda_st
 int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
                            int32_t* method, double* ms_fast, double* ms_direct);
 /* As gbdlt_batch_group_info, and *fused = 1 where the group runs inside its
- * direction's persistent direct launch, else 0. */
+ * direction's persistent direct launch, else 0; *lengths = the number of
+ * distinct lengths the group holds (1, or for a grid group, whose *N is the grid
+ * G, its lengths in (G/2, G]). */
 int gbdlt_batch_group_info_ex(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
-                              int32_t* method, double* ms_fast, double* ms_direct, int32_t* fused);
+                              int32_t* method, double* ms_fast, double* ms_direct, int32_t* fused,
+                              int64_t* lengths);
 /* total elements of the concatenated layout, number of (N, direction) groups,
  * kernel nodes in the captured graph (any pointer may be NULL) */
 int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int64_t* groups,

@@ -132,7 +132,7 @@ def lib():
         L.gbdlt_batch_group_info_ex.argtypes = [vp, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                                 ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                                                 ctypes.POINTER(dbl), ctypes.POINTER(dbl),
-                                                ctypes.POINTER(ctypes.c_int32)]
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i64)]
         L.gbdlt_batch_exec.argtypes = [vp, vp, vp, vp]
         L.gbdlt_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.gbdlt_batch_destroy.argtypes = [vp]
@@ -327,18 +327,20 @@ class Batch:
         return {"total_elements": t.value, "groups": g.value, "graph_kernels": k.value}
 
     def groups(self) -> list:
-        """Per (N, direction) group: N, dir, count, method, the autotuner's timings
-        and whether it runs inside its direction's persistent direct launch."""
+        """Per group: N (a grid group's grid G), dir, count, method, the
+        autotuner's timings, whether it runs inside its direction's persistent
+        direct launch, and its number of distinct lengths."""
         out = []
         for g in range(self.info()["groups"]):
             N, d, c, m = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
-            tf, td, fu = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+            tf, td, fu, nl = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64()
             _check(lib().gbdlt_batch_group_info_ex(self._h, g, ctypes.byref(N), ctypes.byref(d), ctypes.byref(c),
                                                    ctypes.byref(m), ctypes.byref(tf), ctypes.byref(td),
-                                                   ctypes.byref(fu)),
+                                                   ctypes.byref(fu), ctypes.byref(nl)),
                    "batch_group_info")
             out.append({"N": N.value, "dir": d.value, "count": c.value, "method": m.value,
-                        "ms_fast": tf.value, "ms_direct": td.value, "fused": bool(fu.value)})
+                        "ms_fast": tf.value, "ms_direct": td.value, "fused": bool(fu.value),
+                        "lengths": nl.value})
         return out
 
     def run(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

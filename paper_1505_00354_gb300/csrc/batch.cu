@@ -32,6 +32,9 @@
 namespace gbdlt {
 
 constexpr int kLanes = 8;
+// buckets of several lengths with G up to this run the direct method under AUTO
+// (the fused persistent launch; per-length timings favour it up to N = 512)
+constexpr int64_t kBatchDirectG = 512;
 
 struct BatchGroup {
   int64_t N;
@@ -43,11 +46,16 @@ struct BatchGroup {
   int method;         // GBDLT_METHOD_FAST or GBDLT_METHOD_DIRECT
   double ms_fast = -1.0, ms_direct = -1.0;  // autotuner timings (-1: not timed)
   bool fused = false;  // runs inside the direction's persistent direct launch
+  int64_t stride = 0;  // staging elements per transform: N, or G for a grid group
+  int64_t lengths = 1; // distinct lengths (a grid group's rules)
+  GridRules* rules = nullptr;  // grid group: the rule of every length
+  int32_t* d_item = nullptr;   // grid group: rule of each item (device)
 };
 
 struct Batch {
   int prec = GBDLT_FP64;
   int64_t B = 0, total = 0, maxN = 0;
+  int64_t stage_total = 0;  // staging elements (grid groups take G per transform)
   cudaStream_t s = nullptr;
   cudaStream_t lane_s[kLanes] = {};
   cudaEvent_t lane_ev[kLanes] = {};
@@ -144,6 +152,10 @@ void free_batch(Batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (DirectMulti* d : b->direct) direct_multi_free(d);
   for (Plan* p : b->plans) free_plan(p);
+  for (BatchGroup& g : b->groups) {
+    if (g.rules) grid_rules_free(g.rules);
+    if (g.d_item) cudaFree(g.d_item);
+  }
   if (b->d_src) cudaFree(b->d_src);
   if (b->stage_in) cudaFree(b->stage_in);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -198,8 +210,13 @@ extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
     return fail(GBDLT_ERR_CUDA);
-  // groups by (N, dir), staging offsets, per-transform offsets
-  std::map<std::pair<int64_t, int>, std::vector<int64_t>> members;
+  // Groups.  Transforms are bucketed by (G, dir), G the power of two with
+  // G/2 < N <= G.  A bucket of one length is one group (N, dir) as it stands.
+  // A bucket of several lengths is either one grid group (one chain on the grid
+  // G for all its transforms, each item with its own rule: grid.cu), or, under
+  // the direct method (forced, or AUTO with G <= kBatchDirectG, where the
+  // per-length autotuner timings favoured it), one direct group per length.
+  std::map<std::pair<int64_t, int>, std::vector<int64_t>> buckets;
   std::vector<int64_t> src(B), stage(B), len(B);
   int64_t off = 0;
   for (int64_t i = 0; i < B; ++i) {
@@ -207,55 +224,120 @@ extern "C" int gbdlt_batch_create_ex(const int64_t* Ns_host, const int32_t* dirs
     len[i] = Ns_host[i];
     off += Ns_host[i];
     b->maxN = std::max(b->maxN, Ns_host[i]);
-    members[{Ns_host[i], dirs_host[i]}].push_back(i);
+    int64_t G = 1;
+    while (G < Ns_host[i]) G <<= 1;
+    buckets[{G, dirs_host[i]}].push_back(i);
   }
   b->total = off;
-  b->nlanes = (int)std::min<size_t>(kLanes, members.size());
+  struct Proto {
+    int64_t N, G;
+    int dir;
+    bool grid;
+    std::vector<int64_t> idx;
+  };
+  std::vector<Proto> protos;
+  for (auto& kv : buckets) {
+    const int64_t G = kv.first.first;
+    const int dir = kv.first.second;
+    std::map<int64_t, std::vector<int64_t>> byN;
+    for (int64_t i : kv.second) byN[Ns_host[i]].push_back(i);
+    const bool direct = method == GBDLT_METHOD_DIRECT || (method == GBDLT_METHOD_AUTO && G <= kBatchDirectG);
+    if (byN.size() > 1 && !direct) {
+      protos.push_back(Proto{G, G, dir, true, kv.second});
+    } else {
+      for (auto& nv : byN) protos.push_back(Proto{nv.first, G, dir, false, nv.second});
+    }
+  }
+  b->nlanes = (int)std::min<size_t>(kLanes, protos.size());
   for (int l = 0; l < b->nlanes; ++l)
     if (cudaStreamCreateWithFlags(&b->lane_s[l], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->lane_ev[l], cudaEventDisableTiming) != cudaSuccess)
       return fail(GBDLT_ERR_CUDA);
   // one plan per group, on the group's lane; groups go to lanes in order of
   // decreasing work so that the lanes carry similar loads
-  std::vector<std::pair<double, std::pair<int64_t, int>>> order;
-  for (auto& kv : members) order.push_back({-(double)kv.second.size() * (double)kv.first.first, kv.first});
+  std::vector<std::pair<double, size_t>> order;
+  for (size_t q = 0; q < protos.size(); ++q)
+    order.push_back({-(double)protos[q].idx.size() * (double)(protos[q].grid ? protos[q].G : protos[q].N), q});
   std::sort(order.begin(), order.end());
   std::vector<double> lane_load(b->nlanes, 0.0);
   int64_t soff = 0;
   for (auto& ok : order) {
-    const std::vector<int64_t>& idx = members[ok.second];
+    const Proto& pr = protos[ok.second];
+    const std::vector<int64_t>& idx = pr.idx;
     BatchGroup g;
-    g.N = ok.second.first;
-    g.dir = ok.second.second;
+    g.N = pr.N;
+    g.dir = pr.dir;
     g.count = (int64_t)idx.size();
     g.stage_off = soff;
+    g.stride = pr.N;
     g.lane = (int)(std::min_element(lane_load.begin(), lane_load.end()) - lane_load.begin());
     lane_load[g.lane] += -ok.first;
-    const bool can_direct = g.N > 1 && g.N <= kDirectMax;
-    int m = method;
-    if (m == GBDLT_METHOD_AUTO && !can_direct) m = GBDLT_METHOD_FAST;
     Plan* p = nullptr;
-    const int plan_method = m == GBDLT_METHOD_AUTO ? GBDLT_METHOD_FAST : m;
-    int st = plan_create_impl(g.N, prec, eps, plan_method, b->lane_s[g.lane], g.count,
-                              m == GBDLT_METHOD_AUTO ? 1 : 0, &p);
-    if (st) return fail(st);
-    b->plans.push_back(p);
+    if (pr.grid) {
+      // one node plan per length (its rule), the chain of a plan for G
+      std::map<int64_t, int32_t> rule_of;
+      std::vector<Plan*> nodes;
+      double bmax = 0.0;
+      for (int64_t i : idx) {
+        if (rule_of.count(Ns_host[i])) continue;
+        Plan* np = nullptr;
+        int st = plan_create_nodes(Ns_host[i], prec, b->lane_s[g.lane], &np);
+        if (st) return fail(st);
+        b->plans.push_back(np);
+        rule_of[Ns_host[i]] = (int32_t)nodes.size();
+        nodes.push_back(np);
+        bmax = std::max(bmax, grid_bound(Ns_host[i], pr.G));
+      }
+      int st = plan_create_grid(pr.G, prec, eps, bmax, b->lane_s[g.lane], g.count, &p);
+      if (st) return fail(st);
+      b->plans.push_back(p);
+      st = grid_rules_create(pr.G, nodes, b->lane_s[g.lane], &g.rules);
+      if (st) return fail(st);
+      std::vector<int32_t> item(idx.size());
+      for (size_t q = 0; q < idx.size(); ++q) item[q] = rule_of[Ns_host[idx[q]]];
+      if (dev_malloc((void**)&g.d_item, sizeof(int32_t) * item.size()) != cudaSuccess ||
+          cudaMemcpy(g.d_item, item.data(), sizeof(int32_t) * item.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        b->groups.push_back(g);  // freed with the batch
+        return fail(GBDLT_ERR_CUDA);
+      }
+      st = grid_attach(*p, g.rules, g.d_item, false);
+      if (st) {
+        b->groups.push_back(g);
+        return fail(st);
+      }
+      g.stride = pr.G;
+      g.lengths = (int64_t)nodes.size();
+      g.method = GBDLT_METHOD_FAST;
+    } else {
+      const bool can_direct = g.N > 1 && g.N <= kDirectMax;
+      int m = method;
+      if (m == GBDLT_METHOD_AUTO && !can_direct) m = GBDLT_METHOD_FAST;
+      // several lengths of one bucket under AUTO: the direct method, untimed
+      if (m == GBDLT_METHOD_AUTO && buckets[{pr.G, pr.dir}].size() != idx.size()) m = GBDLT_METHOD_DIRECT;
+      const int plan_method = m == GBDLT_METHOD_AUTO ? GBDLT_METHOD_FAST : m;
+      int st = plan_create_impl(g.N, prec, eps, plan_method, b->lane_s[g.lane], g.count,
+                                m == GBDLT_METHOD_AUTO ? 1 : 0, &p);
+      if (st) return fail(st);
+      b->plans.push_back(p);
+      g.method = m;  // AUTO is resolved by the timing below
+    }
     g.plan = p;
-    g.method = m;  // AUTO is resolved by the timing below
-    for (size_t q = 0; q < idx.size(); ++q) stage[idx[q]] = soff + (int64_t)q * g.N;
-    soff += g.count * g.N;
+    for (size_t q = 0; q < idx.size(); ++q) stage[idx[q]] = soff + (int64_t)q * g.stride;
+    soff += g.count * g.stride;
     b->groups.push_back(g);
   }
-  // device tables and staging
+  b->stage_total = soff;
+  // device tables and staging (zeroed once: a grid group's slots keep zeros past
+  // each transform's length, which the gather never writes)
   if (dev_malloc((void**)&b->d_src, sizeof(int64_t) * 3 * (size_t)B) != cudaSuccess) return fail(GBDLT_ERR_OOM);
   b->d_stage = b->d_src + B;
   b->d_len = b->d_src + 2 * B;
-  if (dev_malloc((void**)&b->stage_in, 2 * es * (size_t)b->total) != cudaSuccess) return fail(GBDLT_ERR_OOM);
-  b->stage_out = (char*)b->stage_in + es * (size_t)b->total;
+  if (dev_malloc((void**)&b->stage_in, 2 * es * (size_t)b->stage_total) != cudaSuccess) return fail(GBDLT_ERR_OOM);
+  b->stage_out = (char*)b->stage_in + es * (size_t)b->stage_total;
   if (cudaMemcpy(b->d_src, src.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_stage, stage.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_len, len.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemsetAsync(b->stage_in, 0, 2 * es * (size_t)b->total, b->s) != cudaSuccess ||
+      cudaMemsetAsync(b->stage_in, 0, 2 * es * (size_t)b->stage_total, b->s) != cudaSuccess ||
       cudaStreamSynchronize(b->s) != cudaSuccess)
     return fail(GBDLT_ERR_CUDA);
   // the autotuner: time both methods where both are open, keep the faster
@@ -349,11 +431,12 @@ extern "C" int gbdlt_batch_info(gbdlt_batch batch, int64_t* total_elements, int6
 
 extern "C" int gbdlt_batch_group_info(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
                                       int32_t* method, double* ms_fast, double* ms_direct) {
-  return gbdlt_batch_group_info_ex(batch, g, N, dir, count, method, ms_fast, ms_direct, nullptr);
+  return gbdlt_batch_group_info_ex(batch, g, N, dir, count, method, ms_fast, ms_direct, nullptr, nullptr);
 }
 
 extern "C" int gbdlt_batch_group_info_ex(gbdlt_batch batch, int64_t g, int64_t* N, int32_t* dir, int64_t* count,
-                                         int32_t* method, double* ms_fast, double* ms_direct, int32_t* fused) {
+                                         int32_t* method, double* ms_fast, double* ms_direct, int32_t* fused,
+                                         int64_t* lengths) {
   if (!batch) return GBDLT_ERR_INVALID_ARG;
   Batch& b = *reinterpret_cast<Batch*>(batch);
   if (g < 0 || g >= (int64_t)b.groups.size()) return GBDLT_ERR_INVALID_ARG;
@@ -365,6 +448,7 @@ extern "C" int gbdlt_batch_group_info_ex(gbdlt_batch batch, int64_t g, int64_t* 
   if (ms_fast) *ms_fast = G.ms_fast;
   if (ms_direct) *ms_direct = G.ms_direct;
   if (fused) *fused = G.fused ? 1 : 0;
+  if (lengths) *lengths = G.lengths;
   return GBDLT_OK;
 }
 

@@ -367,14 +367,25 @@ struct Plan {
   Plan* inner = nullptr;
   void* rg_in = nullptr;   // [bcap][G] padded inputs
   void* rg_out = nullptr;  // [bcap][G] chain outputs before truncation to N
-  // on an inner plan: the rows of the outer N-point rule on this plan's grid
-  int64_t rg_n = 0;              // N of the outer rule (0: the rows are this plan's own nodes)
-  int32_t* rg_j = nullptr;       // [rg_n] grid point j(k) nearest theta_k
-  int32_t* rg_kf = nullptr;      // [G + 1] first row k with j(k) >= j
-  double* rg_t = nullptr;        // [rg_n] G (theta_k - (j(k) + 1/2) pi / G)
-  const double* rg_w = nullptr;  // [rg_n] the outer rule's weights
-  void* rg_g = nullptr;          // [bcap][G] rows summed onto their grid points
-  void* rg_block = nullptr;      // the allocation holding rg_j .. rg_g
+  // on an inner plan: the rows are those of other rules (N-point Gauss-Legendre
+  // rules with N <= G) placed on this plan's grid, one rule per batch item
+  const struct GridRule* rg_rules = nullptr;  // device [rules]; null: this plan's own nodes
+  const int32_t* rg_item = nullptr;  // device [items] rule of each item (null: rule 0 for all)
+  int64_t rg_item0 = 0;              // first item of the pass run_chain is running
+  int64_t rg_nmax = 0;               // longest rule (launch sizes)
+  void* rg_g = nullptr;              // [bcap][G] rows summed onto their grid points
+  struct GridRules* rg_own = nullptr;  // rules this plan owns (a plan for N not a power of two)
+};
+
+// An N-point rule on a grid of G >= N points (grid.cu): row k's nearest grid
+// point j[k], its offset t[k] = G (theta_k - (j[k] + 1/2) pi / G), the first row
+// kf[jj] of grid point jj (jj = 0..G), and the rule's weights.
+struct GridRule {
+  int64_t n;
+  const int32_t* j;
+  const double* t;
+  const int32_t* kf;
+  const double* w;
 };
 
 // Taylor pairs whose FFTs run in the plan's precision: pair p holds terms
@@ -412,6 +423,13 @@ inline TwT<ffd> tw_tables(const Plan& P, ffd) {
 // times both methods on one plan)
 int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t stream, int64_t max_batch,
                      int want_direct, Plan** out);
+// a plan holding only the N-point rule (nodes, weights, N dtheta): the rules of
+// a batch's grid groups
+int plan_create_nodes(int64_t N, int prec, cudaStream_t stream, Plan** out);
+// a fast plan for the power-of-two G whose Taylor step serves rows with
+// |n dtheta| <= taylor_b (rules placed on its grid)
+int plan_create_grid(int64_t G, int prec, double eps, double taylor_b, cudaStream_t stream, int64_t max_batch,
+                     Plan** out);
 void free_plan(Plan* P);
 enum Op { OP_L2C, OP_L2C_T, OP_CHEB, OP_CHEB_T, OP_DLT, OP_DLT_T, OP_IDLT, OP_IDLT_T };
 int run_op(gbdlt_plan plan, int op, const void* in, void* out, int64_t batch);
@@ -464,12 +482,23 @@ int launch_rec_xm1(Plan& P, RecLayout& L, int legendre);
 // `in` / `out`, all of one direction (0: DLT, 1: IDLT).  Only plans whose direct
 // layout is one CTA (direct_fusable) take part; results are bitwise those of
 // run_op_method with GBDLT_METHOD_DIRECT.
-// grid.cu: plans for N that is not a power of two.  grid_attach builds the
-// row-to-grid maps of the outer plan's rule on its inner plan; launch_grid_pad
-// copies [nb][N] into [nb][G] with zeros past N, launch_grid_cut the first N of
-// each [G] row back; launch_grid_scatter sums the rows (times w_k when use_w)
-// onto their grid points (the l = 0 Taylor term of the transposed chain).
-int grid_attach(Plan& O, Plan& I);
+// grid.cu: rules on a power-of-two grid.  grid_rules_create places the rules of
+// the given node plans (their theta, N dtheta and weights) on a grid of G
+// points and checks that no grid point holds more than two rows; the device
+// table has one GridRule per node plan, in order.  grid_bound is the bound b on
+// |n dtheta| over the rules (Corollary 2.4): (N-1) pi / (2G) for N < G, 0.83845
+// for N = G.  grid_attach gives inner plan I the rules `R` (I.rg_*), with
+// `item` the rule of each batch item (device, or null for rule 0).
+// launch_grid_pad copies [nb][N] into [nb][G] with zeros past N,
+// launch_grid_cut the first N of each [G] row back; launch_grid_scatter sums the
+// rows (times w_k when use_w) onto their grid points (the l = 0 Taylor term of
+// the transposed chain).
+struct GridRules;
+double grid_bound(int64_t N, int64_t G);
+int grid_rules_create(int64_t G, const std::vector<Plan*>& nodes, cudaStream_t s, GridRules** out);
+void grid_rules_free(GridRules* r);
+size_t grid_rules_bytes(const GridRules* r);
+int grid_attach(Plan& I, GridRules* R, const int32_t* item, bool own);
 template <typename T>
 int launch_grid_pad(Plan& P, const T* in, T* out, int64_t N, int64_t G, int64_t nb);
 template <typename T>

@@ -18,11 +18,18 @@
 //   t_k = (G/N) tN_k + pi ((2k + 1) G - (2j + 1) N) / (2N),
 // the integer in the second term exact, so t_k carries no cancellation error.
 //
+// An inner plan may carry several rules at once (one per batch item): the batch
+// executor runs every transform whose length lies in (G/2, G] through one chain
+// on the grid G, each item with its own rule.
+//
 // The transposed Taylor prologue sums, per grid point, the rows mapped to it.
 // Rows lie at least 3.11/(N + 1/2) apart in theta (the first gap, between the
 // two smallest Bessel zeros scaled, is the narrowest) and grid cells are pi/G <
 // pi/N wide, so a cell holds at most two rows; grid_attach checks it.
+#include <algorithm>
 #include <cmath>
+#include <new>
+#include <vector>
 
 #include "gbdlt_internal.cuh"
 
@@ -98,57 +105,122 @@ __global__ void k_grid_cut(const T* __restrict__ in, T* __restrict__ out, int64_
   out[bt * N + i] = in[bt * G + i];
 }
 
-// out_j = sum over the rows k of grid point j of g_k (w_k g_k when w), 0 where
-// no row falls; g and out have the grid's batch stride G
+// out_j = sum over the rows k of grid point j of g_k (w_k g_k when use_w), 0
+// where no row falls; g and out have the grid's batch stride G
 template <typename T>
-__global__ void k_grid_scatter(const T* __restrict__ g, const double* __restrict__ w, const int32_t* __restrict__ kf,
-                               T* __restrict__ out, int64_t G) {
+__global__ void k_grid_scatter(const T* __restrict__ g, int use_w, const GridRule* __restrict__ rules,
+                               const int32_t* __restrict__ item, T* __restrict__ out, int64_t G) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= G) return;
   const int64_t bt = blockIdx.y;
+  const GridRule R = rules[item ? item[bt] : 0];
   g += bt * G;
   T s = (T)0;
-  for (int64_t k = kf[j]; k < kf[j + 1]; ++k) s += w ? (T)((double)g[k] * w[k]) : g[k];
+  for (int64_t k = R.kf[j]; k < R.kf[j + 1]; ++k) s += use_w ? (T)((double)g[k] * R.w[k]) : g[k];
   out[bt * G + j] = s;
 }
 
 }  // namespace
 
-int grid_attach(Plan& O, Plan& I) {
-  const int64_t N = O.p.N, G = I.p.N;
-  if (G <= N || G % 2) return GBDLT_ERR_INVALID_ARG;
-  const size_t ts = O.p.prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
+struct GridRules {
+  int64_t G = 0;
+  std::vector<int64_t> n;
+  void* block = nullptr;       // maps of every rule
+  GridRule* dev = nullptr;     // [rules] (inside block)
+  size_t bytes = 0;
+};
+
+double grid_bound(int64_t N, int64_t G) {
+  return N == G ? 0.83845 : (double)(N - 1) * M_PI / (2.0 * (double)G) * (1.0 + 1e-9);
+}
+
+int grid_rules_create(int64_t G, const std::vector<Plan*>& nodes, cudaStream_t s, GridRules** out) {
+  *out = nullptr;
+  if (nodes.empty() || G < 2 || (G & (G - 1))) return GBDLT_ERR_INVALID_ARG;
+  GridRules* R = new (std::nothrow) GridRules();
+  if (!R) return GBDLT_ERR_OOM;
+  R->G = G;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t o_j = 0, o_kf = o_j + al(sizeof(int32_t) * N), o_t = o_kf + al(sizeof(int32_t) * (G + 1)),
-               o_chk = o_t + al(sizeof(double) * N), o_g = o_chk + al(sizeof(int)),
-               bytes = o_g + al(ts * (size_t)I.bcap * G);
-  if (dev_malloc(&I.rg_block, bytes) != cudaSuccess) {
+  const size_t nr = nodes.size();
+  std::vector<size_t> oj(nr), ot(nr), okf(nr);
+  size_t off = al(sizeof(GridRule) * nr) + al(sizeof(int));
+  for (size_t r = 0; r < nr; ++r) {
+    const int64_t N = nodes[r]->p.N;
+    if (N < 1 || N > G) {
+      delete R;
+      return GBDLT_ERR_INVALID_ARG;
+    }
+    R->n.push_back(N);
+    oj[r] = off;
+    off += al(sizeof(int32_t) * N);
+    ot[r] = off;
+    off += al(sizeof(double) * N);
+    okf[r] = off;
+    off += al(sizeof(int32_t) * (G + 1));
+  }
+  R->bytes = off;
+  if (dev_malloc(&R->block, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete R;
+    return GBDLT_ERR_OOM;
+  }
+  char* base = (char*)R->block;
+  R->dev = (GridRule*)base;
+  int* chk = (int*)(base + al(sizeof(GridRule) * nr));
+  std::vector<GridRule> host(nr);
+  bool ok = cudaMemsetAsync(chk, 0, sizeof(int), s) == cudaSuccess;
+  for (size_t r = 0; r < nr && ok; ++r) {
+    const Plan& P = *nodes[r];
+    const int64_t N = P.p.N;
+    int32_t* jm = (int32_t*)(base + oj[r]);
+    double* tr = (double*)(base + ot[r]);
+    int32_t* kf = (int32_t*)(base + okf[r]);
+    host[r] = GridRule{N, jm, tr, kf, P.w};
+    k_grid_map<<<nblk(N), TPB, 0, s>>>(P.theta, P.tN, N, G, jm, tr);
+    k_grid_first<<<nblk(G + 1), TPB, 0, s>>>(jm, N, G, kf);
+    k_grid_check<<<nblk(std::max(G, N)), TPB, 0, s>>>(jm, kf, N, G, chk);
+    count_launch(3);
+    ok = check_launch() == GBDLT_OK;
+  }
+  int worst = 0;
+  if (!ok || cudaMemcpyAsync(R->dev, host.data(), sizeof(GridRule) * nr, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess ||
+      cudaMemcpy(&worst, chk, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    grid_rules_free(R);
+    return GBDLT_ERR_CUDA;
+  }
+  // more than two rows on a grid point (or rows out of order) would break the
+  // transposed prologue's two slots per point
+  if (worst > 2) {
+    grid_rules_free(R);
+    return GBDLT_ERR_UNIMPLEMENTED;
+  }
+  *out = R;
+  return GBDLT_OK;
+}
+
+void grid_rules_free(GridRules* r) {
+  if (!r) return;
+  if (r->block) cudaFree(r->block);
+  delete r;
+}
+
+size_t grid_rules_bytes(const GridRules* r) { return r ? r->bytes : 0; }
+
+int grid_attach(Plan& I, GridRules* R, const int32_t* item, bool own) {
+  if (!R || R->G != I.p.N) return GBDLT_ERR_INVALID_ARG;
+  const size_t ts = I.p.prec == GBDLT_FP64 ? sizeof(double) : sizeof(float);
+  if (!I.rg_g && dev_malloc(&I.rg_g, ts * (size_t)I.bcap * (size_t)I.p.N) != cudaSuccess) {
     cudaGetLastError();
     return GBDLT_ERR_OOM;
   }
-  char* base = (char*)I.rg_block;
-  I.rg_j = (int32_t*)(base + o_j);
-  I.rg_kf = (int32_t*)(base + o_kf);
-  I.rg_t = (double*)(base + o_t);
-  int* chk = (int*)(base + o_chk);
-  I.rg_g = base + o_g;
-  I.rg_w = O.w;
-  I.rg_n = N;
-  O.ws_bytes += bytes;
-  if (cudaMemsetAsync(chk, 0, sizeof(int), O.stream) != cudaSuccess) return GBDLT_ERR_CUDA;
-  k_grid_map<<<nblk(N), TPB, 0, O.stream>>>(O.theta, O.tN, N, G, I.rg_j, I.rg_t);
-  k_grid_first<<<nblk(G + 1), TPB, 0, O.stream>>>(I.rg_j, N, G, I.rg_kf);
-  k_grid_check<<<nblk(std::max(G, N)), TPB, 0, O.stream>>>(I.rg_j, I.rg_kf, N, G, chk);
-  count_launch(3);
-  int worst = 0;
-  if (check_launch() || cudaStreamSynchronize(O.stream) != cudaSuccess ||
-      cudaMemcpy(&worst, chk, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
-    cudaGetLastError();
-    return GBDLT_ERR_CUDA;
-  }
-  // more than two rows on a grid point (or a row order that is not monotone)
-  // would break the transposed prologue's two slots per point
-  if (worst > 2) return GBDLT_ERR_UNIMPLEMENTED;
+  I.rg_rules = R->dev;
+  I.rg_item = item;
+  I.rg_item0 = 0;
+  I.rg_nmax = 0;
+  for (int64_t n : R->n) I.rg_nmax = std::max(I.rg_nmax, n);
+  if (own) I.rg_own = R;
   return GBDLT_OK;
 }
 
@@ -169,8 +241,9 @@ int launch_grid_cut(Plan& P, const T* in, T* out, int64_t N, int64_t G, int64_t 
 template <typename T>
 int launch_grid_scatter(Plan& I, const T* g, int use_w, T* out, int64_t nb) {
   const int64_t G = I.p.N;
-  k_grid_scatter<T><<<dim3(nblk(G), (unsigned)nb), TPB, 0, I.stream>>>(g, use_w ? I.rg_w : nullptr, I.rg_kf, out, G);
-  launched(I, "grid_scatter", (double)nb * (double)I.rg_n, (double)nb * (double)sizeof(T) * (double)(I.rg_n + G));
+  k_grid_scatter<T><<<dim3(nblk(G), (unsigned)nb), TPB, 0, I.stream>>>(
+      g, use_w, I.rg_rules, I.rg_item ? I.rg_item + I.rg_item0 : nullptr, out, G);
+  launched(I, "grid_scatter", (double)nb * (double)I.rg_nmax, (double)nb * (double)sizeof(T) * (double)(I.rg_nmax + G));
   return check_launch();
 }
 

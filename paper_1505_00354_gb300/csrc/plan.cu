@@ -551,7 +551,8 @@ void free_plan(Plan* P) {
   if (P->arena) cudaFree(P->arena);
   if (P->inner) free_plan(P->inner);
   if (P->rg_in) cudaFree(P->rg_in);
-  if (P->rg_block) cudaFree(P->rg_block);
+  if (P->rg_g) cudaFree(P->rg_g);
+  if (P->rg_own) grid_rules_free(P->rg_own);
   if (P->prof) {
     for (cudaEvent_t e : P->prof->ev) cudaEventDestroy(e);
     delete P->prof;
@@ -687,13 +688,36 @@ int plan_create_impl(int64_t N, int prec, double eps, int method, cudaStream_t s
   }
   O->rg_out = (char*)O->rg_in + rg;
   O->ws_bytes += 2 * rg;
-  st = grid_attach(*O, *I);
+  GridRules* R = nullptr;
+  st = grid_rules_create(prm.grid, std::vector<Plan*>{O}, stream, &R);
+  if (st == GBDLT_OK) {
+    st = grid_attach(*I, R, nullptr, true);
+    if (st != GBDLT_OK) grid_rules_free(R);
+  }
   if (st != GBDLT_OK) {
     free_plan(O);
     return st;
   }
+  O->ws_bytes += grid_rules_bytes(R) + ts * (size_t)I->bcap * (size_t)prm.grid;
   *out = O;
   return GBDLT_OK;
+}
+
+int plan_create_nodes(int64_t N, int prec, cudaStream_t stream, Plan** out) {
+  Params q;
+  int st = derive_params(N, prec, 0.0, GBDLT_METHOD_FAST, &q);
+  if (st != GBDLT_OK) return st;
+  q.fast = false;
+  return plan_build(q, stream, 1, 0, out);
+}
+
+int plan_create_grid(int64_t G, int prec, double eps, double taylor_b, cudaStream_t stream, int64_t max_batch,
+                     Plan** out) {
+  if (G < 2 || (G & (G - 1))) return GBDLT_ERR_INVALID_ARG;
+  Params q;
+  int st = derive_params(G, prec, eps, GBDLT_METHOD_FAST, &q, taylor_b);
+  if (st != GBDLT_OK) return st;
+  return plan_build(q, stream, max_batch, 0, out);
 }
 
 static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch, int want_direct, Plan** out) {
@@ -1236,7 +1260,7 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
   // rule, grid.cu) the rows summed onto their grid points
   const T* g0 = g;
   int w0 = use_w;
-  if (!inc0 && P.rg_n > 0) {
+  if (!inc0 && P.rg_rules) {
     st = launch_grid_scatter<T>(P, g, use_w, (T*)P.rg_g, nb);
     if (st) return st;
     g0 = (const T*)P.rg_g;
@@ -1434,7 +1458,9 @@ int run_one(Plan& P, int op, int method, const T* in, T* out, int64_t nb) {
     case OP_IDLT:
       return run_transposed<T>(P, in, out, 1, 1, nb);
     case OP_IDLT_T: {
-      // out = D_w P D_s g
+      // out = D_w P D_s g (a plan carrying other rules has no weights of its own
+      // to apply: run_grid applies the rule's)
+      if (P.rg_rules) return GBDLT_ERR_INVALID_ARG;
       T* sg = (T*)P.tmp2;
       int st = launch_scale<T>(P, in, sg, 1, nb);
       if (st) return st;
@@ -1567,6 +1593,7 @@ static int run_chain(Plan& P, int op, int method, const void* in, void* out, int
   const int64_t N = P.p.N;
   for (int64_t i = 0; i < batch; i += P.bcap) {
     const int64_t nb = std::min<int64_t>(P.bcap, batch - i);
+    P.rg_item0 = i;  // the rule table of a grid plan's batch items (grid.cu)
     int st;
     if (P.p.prec == GBDLT_FP64)
       st = run_one<double>(P, op, method, (const double*)in + i * N, (double*)out + i * N, nb);

@@ -563,23 +563,26 @@ __global__ void k_tay_pro(const T* __restrict__ chat, C2<T>* __restrict__ U, ffc
   }
 }
 
-// GRID: the rows are those of an outer rule of nout < N nodes (a plan whose N
-// is not a power of two runs its chain on this grid of N points): row k reads
-// the sums at its grid point j = jmap[k] and tN[k] is its offset N (theta_k -
-// theta'_j) from that point; f keeps the grid's batch stride N.
+// GRID: the rows are those of a rule of R.n <= N nodes placed on this grid of N
+// points (grid.cu; one rule per batch item): row k reads the sums at its grid
+// point j = R.j[k], and R.t[k] is its offset N (theta_k - theta'_j) from that
+// point; f keeps the grid's batch stride N.
 template <typename T, bool GRID = false>
 __global__ void k_tay_epi(const C2<T>* __restrict__ Y, const ffc* __restrict__ Yff, const T* __restrict__ v,
                           T* __restrict__ f, const double* __restrict__ tN, int64_t N, int L, int inc0, int npair,
-                          int P64, Scale32 S, const int32_t* __restrict__ jmap = nullptr, int64_t nout = 0) {
+                          int P64, Scale32 S, const GridRule* __restrict__ rules = nullptr,
+                          const int32_t* __restrict__ item = nullptr) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (GRID ? nout : N)) return;
   const int64_t bt = blockIdx.y;
+  GridRule R{};
+  if constexpr (GRID) R = rules[item ? item[bt] : 0];
+  if (k >= (GRID ? R.n : N)) return;
   Y += bt * P64 * N;
   if (Yff) Yff += bt * (npair - P64) * N;
   f += bt * N;
   if (v) v += bt * N;
-  const T t = (T)tN[k];
-  const int64_t j = GRID ? (int64_t)jmap[k] : k;
+  const T t = (T)(GRID ? R.t[k] : tN[k]);
+  const int64_t j = GRID ? (int64_t)R.j[k] : k;
   const bool odd = j & 1;
   const int64_t idx = odd ? N - 1 - (j >> 1) : (j >> 1);
   T acc2 = (T)0;  // twice the sum of the pairs in the plan's precision
@@ -691,19 +694,23 @@ __global__ void k_tayt_pro(const T* __restrict__ fin, const double* __restrict__
   }
 }
 
-// k_tayt_pro for the rows of an outer rule on this plan's grid of N points:
-// grid point j collects the rows k with j(k) = j (kf[j] <= k < kf[j+1]; at most
-// two, checked when the maps are built), each with its own offset t_k; the
-// thread of pair jp writes grid points 2jp (to U[jp]) and 2jp + 1 (to
-// U[N-1-jp], with the sign (-1)^j of its sine part) as k_tayt_pro does.
+// k_tayt_pro for the rows of a rule placed on this plan's grid of N points (one
+// rule per batch item): grid point j collects the rows k with j(k) = j
+// (kf[j] <= k < kf[j+1]; at most two, checked when the maps are built), each
+// with its own offset t_k; the thread of pair jp writes grid points 2jp (to
+// U[jp]) and 2jp + 1 (to U[N-1-jp], with the sign (-1)^j of its sine part) as
+// k_tayt_pro does.  use_w: rows weighted by the rule's w_k.
 template <typename T>
-__global__ void k_tayt_pro_grid(const T* __restrict__ fin, const double* __restrict__ wscale,
-                                const double* __restrict__ tr, const int32_t* __restrict__ kf,
-                                C2<T>* __restrict__ U, ffc* __restrict__ Uff, int64_t N, int L, int inc0, int npair,
-                                int P64, Scale32 S) {
+__global__ void k_tayt_pro_grid(const T* __restrict__ fin, int use_w, const GridRule* __restrict__ rules,
+                                const int32_t* __restrict__ item, C2<T>* __restrict__ U, ffc* __restrict__ Uff,
+                                int64_t N, int L, int inc0, int npair, int P64, Scale32 S) {
   const int64_t jp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (jp >= N / 2) return;
   const int64_t bt = blockIdx.y;
+  const GridRule R = rules[item ? item[bt] : 0];
+  const int32_t* __restrict__ kf = R.kf;
+  const double* __restrict__ tr = R.t;
+  const double* __restrict__ wscale = use_w ? R.w : nullptr;
   fin += bt * N;
   U += bt * P64 * N;
   if (Uff) Uff += bt * (npair - P64) * N;
@@ -1200,9 +1207,10 @@ int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, ffc* Uff, int inc0, int npa
 template <typename T>
 int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, int inc0, int npair, int64_t nb) {
   const int P64 = Yff ? taylor_p64(P.p, inc0, npair) : npair;
-  if (P.rg_n > 0)
-    k_tay_epi<T, true><<<dim3(nblk(P.rg_n), (unsigned)nb), TPB, 0, P.stream>>>(
-        Y, Yff, v, f, P.rg_t, P.p.N, P.p.L, inc0, npair, P64, scale32(P), P.rg_j, P.rg_n);
+  if (P.rg_rules)
+    k_tay_epi<T, true><<<dim3(nblk(P.rg_nmax), (unsigned)nb), TPB, 0, P.stream>>>(
+        Y, Yff, v, f, nullptr, P.p.N, P.p.L, inc0, npair, P64, scale32(P), P.rg_rules,
+        P.rg_item ? P.rg_item + P.rg_item0 : nullptr);
   else
     k_tay_epi<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(Y, Yff, v, f, P.tN, P.p.N, P.p.L, inc0,
                                                                          npair, P64, scale32(P));
@@ -1217,9 +1225,10 @@ int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, in
 template <typename T>
 int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb) {
   const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
-  if (P.rg_n > 0)
+  if (P.rg_rules)
     k_tayt_pro_grid<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(
-        f, use_w ? P.rg_w : nullptr, P.rg_t, P.rg_kf, U, Uff, P.p.N, P.p.L, inc0, npair, P64, scale32(P));
+        f, use_w, P.rg_rules, P.rg_item ? P.rg_item + P.rg_item0 : nullptr, U, Uff, P.p.N, P.p.L, inc0, npair, P64,
+        scale32(P));
   else
     k_tayt_pro<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(f, use_w ? P.w : nullptr, P.tN, U, Uff,
                                                                              P.p.N, P.p.L, inc0, npair, P64,

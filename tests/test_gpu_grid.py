@@ -17,6 +17,7 @@ import functools
 
 import numpy as np
 import pytest
+from batch_check import check_groups
 
 torch = pytest.importorskip("torch")
 
@@ -155,9 +156,9 @@ def test_grid_adjoints_batch_scale(gb, N):
 
 
 def test_grid_uneven_batch(gb):
-    """Unrounded lengths 16 .. 8192 (log-uniform): every group takes the method
-    the autotuner found faster, non-powers of two included; every transform
-    equals the single-plan call of its group's method bitwise, and a seeded
+    """Unrounded lengths 16 .. 8192 (log-uniform): the lengths in (G/2, G] of one
+    direction share one grid group above G = 512; replays are deterministic;
+    every transform matches the single plan of its own length, and a seeded
     sample matches the oracle."""
     import oracle
     from paper_1505_00354_gb300 import inputs
@@ -168,20 +169,18 @@ def test_grid_uneven_batch(gb):
     x = np.concatenate([inputs.coeffs(int(N), 7000 + i, 1.0) for i, N in enumerate(Ns)])
     b = gb.Batch(Ns, dirs, gb.FP64)
     groups = b.groups()
-    assert any(G["method"] == gb.METHOD_FAST and G["N"] & (G["N"] - 1) for G in groups)
+    # one group per (G, direction) bucket: grid groups above 512, direct groups
+    # per length below (and single-length buckets as they stand)
+    assert any(G["lengths"] > 1 for G in groups)
+    for G in groups:
+        if G["lengths"] > 1:
+            assert G["N"] > 512 and G["method"] == gb.METHOD_FAST
+    assert sum(1 for G in groups if G["N"] > 512) <= 2 * 5
     xd = dev(x)
     y = b.run(xd)
+    assert torch.equal(y, b.run(xd))
+    check_groups(gb, b, Ns, dirs, xd, y, 0, TOL64)
     off = b.offsets
-    for G in groups:
-        N, d = G["N"], G["dir"]
-        if 1 < N <= 65536 and G["ms_fast"] > 0 and G["ms_direct"] > 0:
-            assert G["method"] == (2 if G["ms_direct"] < G["ms_fast"] else 1)
-        p = gb.get_plan(int(N), 0, method=G["method"])
-        idx = np.nonzero((Ns == N) & (dirs == d))[0]
-        X = torch.stack([xd[off[i]:off[i + 1]] for i in idx])
-        Y = p.dlt(X) if d == 0 else p.idlt(X)
-        got = torch.stack([y[off[i]:off[i + 1]] for i in idx])
-        assert torch.equal(got, Y), G
     worst = 0.0
     for i in rng.choice(B, 12, replace=False):
         N = int(Ns[i])
