@@ -343,6 +343,16 @@ def run_gpu(args, world, rank, local):
     params12 = plan12.params()
     plan12.close()
     del plan12
+
+    # the same step at N = 10^6 (not a power of two: the chain on the grid 2^20)
+    Ng = 10**6
+    pg = g.Plan(Ng, g.FP64, stream=stream, method=g.METHOD_FAST)
+    xg = torch.tensor(inputs.coeffs(Ng, 11, 1.0), dtype=torch.float64, device="cuda")
+    msg, _, _, _ = timed_loop(pg, xg, args.steps, args.warmup)
+    tg = sum(msg) / len(msg)
+    paramsg = pg.params()
+    pg.close()
+    del pg, xg
     torch.cuda.empty_cache()
 
     # ---------------- FP32 form
@@ -509,6 +519,9 @@ def run_gpu(args, world, rank, local):
                                         "bands": params12["bands"], "head": params12["head"],
                                         "M_ff": params12["M_ff"], "M_fp32": params12["M_fp32"],
                                         "L_ff": params12["L_ff"]}},
+            "fp64_N1e6": {"value": round(2.0 * world / (tg / 1e3), 3), "unit": "transforms/s",
+                          "ms_per_step": round(tg, 4), "N": Ng, "grid_n": paramsg["grid_n"], "L": paramsg["L"],
+                          "workload": "FP64 legpts + DLT + IDLT, N = 10^6 (chain on the power-of-two grid)"},
             "cold_plan_ms": {"fp64": round(cold64 * 1e3, 2), "fp32": round(cold32 * 1e3, 2)},
             "batch_uneven": {"workload": "4096 transforms, N = round(2^U(4,13)) (log-uniform on [16, 8192]), "
                                          "DLT/IDLT 50/50, one graph replay",

@@ -354,17 +354,18 @@ def test_argument_errors(gb):
     h = ctypes.c_void_p()
     for bad in (0, 2**25):
         assert L.gbdlt_plan_create(bad, 0, 0.0, None, ctypes.byref(h)) == -2
-    for bad in (3, 1000):
-        assert L.gbdlt_plan_create_ex(bad, 0, 0.0, 1, None, ctypes.byref(h)) == -2
+    assert L.gbdlt_plan_create_ex(2**24 + 1, 0, 0.0, 1, None, ctypes.byref(h)) == -2
     assert L.gbdlt_plan_create_ex(2**17, 0, 0.0, 2, None, ctypes.byref(h)) == -2
     assert L.gbdlt_plan_create(64, 7, 0.0, None, ctypes.byref(h)) == -1
-    # a plan for a length that is not a power of two runs the direct method; the
-    # FFT-based operators (leg2cheb, chebeval) are not open to it
-    q = gb.Plan(1000)
-    assert q.params()["method"] == 2
+    # a direct-method plan for a length that is not a power of two has no
+    # FFT-based chain: leg2cheb and chebeval are not open to it
+    q = gb.Plan(1000, method=gb.METHOD_DIRECT)
+    assert q.params()["method"] == 2 and q.params()["grid_n"] == 0
     y = torch.zeros(1000, dtype=torch.float64, device="cuda")
     with pytest.raises(gb.GbdltError):
         q.leg2cheb(y)
+    # AUTO above 256 takes the chain on the next power-of-two grid
+    assert gb.Plan(1000).params()["grid_n"] == 1024
     p = gb.Plan(64, method=gb.METHOD_FAST)
     x = torch.zeros(64, dtype=torch.float64, device="cuda")
     assert L.gbdlt_dlt(p.handle, None, ctypes.c_void_p(x.data_ptr()), 1) == -1
