@@ -336,6 +336,38 @@ def run_gpu(args, world, rank, local):
     value = job_rate(world, 2.0 * args.steps, sum(ms64))
     prof, t_serial64 = profiled_loop(plan64, c, args.steps)
 
+    def per_op(plan, x, K):
+        """Median ms of each operation alone (legpts, DLT, IDLT), K runs each
+        after three warm-up calls, L2 flushed before every run."""
+        lib = g.lib()
+        f = torch.empty_like(x)
+        cb = torch.empty_like(x)
+
+        def legpts():
+            st = lib.gbdlt_legpts(plan.handle, None, None, None, None)
+            if st:
+                raise g.GbdltError(st, "legpts")
+
+        ops = {"legpts": legpts, "dlt": lambda: plan.dlt(x, out=f), "idlt": lambda: plan.idlt(f, out=cb)}
+        out = {}
+        for name, fn in ops.items():
+            for _ in range(3):  # the second call captures the chain; later calls replay it
+                fn()
+            torch.cuda.synchronize()
+            ev = []
+            for i in range(K):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                ev.append((a, b))
+            torch.cuda.synchronize()
+            out[name + "_ms"] = round(statistics.median(a.elapsed_time(b) for a, b in ev), 4)
+        return out
+
+    ops64 = per_op(plan64, c, max(args.steps, 10))
+
     # ---------------- FP64 form at the north-star tolerance (1e-12 ||c||_1)
     plan12, _ = make(g.FP64, 1e-12)
     ms12, _, f12, _ = timed_loop(plan12, c, args.steps, args.warmup)
@@ -361,6 +393,7 @@ def run_gpu(args, world, rank, local):
     ms32, _, f32, cb32 = timed_loop(plan32, c32, args.steps, args.warmup)
     t32 = sum(ms32) / len(ms32)
     prof32, _ = profiled_loop(plan32, c32, args.steps)
+    ops32 = per_op(plan32, c32, max(args.steps, 10))
     # the FP32 FFT passes with the TMA-staged kernels switched off, for comparison
     plan32.set_fft_staging(False)
     ms32u, _, _, _ = timed_loop(plan32, c32, args.steps, args.warmup)
@@ -522,6 +555,8 @@ def run_gpu(args, world, rank, local):
             "fp64_N1e6": {"value": round(2.0 * world / (tg / 1e3), 3), "unit": "transforms/s",
                           "ms_per_step": round(tg, 4), "N": Ng, "grid_n": paramsg["grid_n"], "L": paramsg["L"],
                           "workload": "FP64 legpts + DLT + IDLT, N = 10^6 (chain on the power-of-two grid)"},
+            "per_operation": {"note": "median of separate runs of each operation alone, L2 flushed before each",
+                              "fp64": ops64, "fp32": ops32},
             "cold_plan_ms": {"fp64": round(cold64 * 1e3, 2), "fp32": round(cold32 * 1e3, 2)},
             "batch_uneven": {"workload": "4096 transforms, N = round(2^U(4,13)) (log-uniform on [16, 8192]), "
                                          "DLT/IDLT 50/50, one graph replay",
