@@ -22,7 +22,7 @@
 //  * otherwise (the 8 nodes nearest theta = 0): the terminating hypergeometric
 //    series P_N(cos t) = sum_j (-N)_j (N+1)_j / (j!)^2 s^j, s = sin^2(t/2),
 //    summed in double-double (its terms reach ~1e10 before they cancel) by one
-//    warp per node (k_legpts_ends): lane l holds terms 3l..3l+2, obtains the
+//    warp per node (end_node, the first blocks of k_legpts): lane l holds terms 3l..3l+2, obtains the
 //    first of them as a prefix product of the term ratios over the lanes below,
 //    and the sums are reduced across the warp.  These nodes start Newton from
 //    j_{0,k+1}/(N+1/2), the zeros of Hilb's Bessel approximation
@@ -82,10 +82,12 @@ __device__ PD eval_asy(double Nh, int64_t k, double d, double s, double c, doubl
   const double sg = (k & 1) ? -1.0 : 1.0;
   double cr = -sg * se, ci = sg * ce;  // e^{i phi_0}, phi_0 = (k+1/2)pi + eps
   const double rr = s, ri = -c;        // e^{i(theta - pi/2)}
-  const double inv_s = 1.0 / s;
-  const double g = 0.5 * inv_s;
+  // (2 sin theta)^{-1/2} by one reciprocal square root; g = 1/(2 sin theta) and
+  // 1/sin theta follow from it by products
+  const double sg0 = rsqrt(2.0 * s);
+  const double g = sg0 * sg0;
+  const double inv_s = 2.0 * g;
   const double cot = c * inv_s;
-  const double sg0 = sqrt(g);
   double gm = sg0;  // g^{m+1/2}
   double P = 0.0, dP = 0.0;
   double mh = 0.5, nmh = Nh;  // m + 1/2 and N + m + 1/2, exact
@@ -108,24 +110,31 @@ __device__ PD eval_asy(double Nh, int64_t k, double d, double s, double c, doubl
   return r;
 }
 
-// nodes k >= kend (k < kend: k_legpts_ends)
-__global__ void k_legpts(int64_t N, int64_t kend, double CN, HTab H, double* __restrict__ theta,
-                         double* __restrict__ x, double* __restrict__ w, double* __restrict__ tN,
-                         int* __restrict__ status, int max_iter) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t half = (N + 1) / 2;
-  if (k >= half || k < kend) return;
+// Per-plan constants of the node kernels (host-computed): 1/(N+1/2) and the
+// first-order start factor 1/(8 (N+1/2)(N+3/2)).
+struct NodeConst {
+  double inv_Nh;
+  double c1;
+};
+
+// node k >= kend (k < kend: end_node)
+__device__ __forceinline__ void interior_node(int64_t N, int64_t k, double CN, const HTab& H, const NodeConst& K,
+                                              double* __restrict__ theta, double* __restrict__ x,
+                                              double* __restrict__ w, double* __restrict__ tN,
+                                              int* __restrict__ status, int max_iter) {
   const double Nh = (double)N + 0.5;
-  const double inv_Nh = 1.0 / Nh;
+  const double inv_Nh = K.inv_Nh;
   const double th0 = ((double)k + 0.75) * kPi * inv_Nh;
   double s0, c0;
-  sincos(th0, &s0, &c0);
+  sincospi(((double)k + 0.75) * inv_Nh, &s0, &c0);
   const int mode = N <= 64 ? 0 : 1;
   // interior nodes start from the zero of the first two terms of the expansion:
   // cos(phi_0) + h_1 cos(phi_1) / (2 sin theta) = 0 gives, to first order,
-  // (N+1/2) delta = cot(theta) / (8 (N+3/2)), i.e. about 1000 times closer than theta*
-  const double cot0 = c0 / s0;
-  double d = mode == 1 ? cot0 * (0.125 * inv_Nh) / ((double)N + 1.5) : 0.0;
+  // (N+1/2) delta = cot(theta) / (8 (N+3/2)), i.e. about 1000 times closer than theta*.
+  // A start needs no more than float accuracy in cot (its error 1e-7 of a
+  // correction of 1e-13 or less): 1/sin theta by the float reciprocal
+  // (sin theta* >= 25/N >= 1.5e-6 here, well inside float range).
+  double d = mode == 1 ? c0 * (double)__frcp_rn((float)s0) * K.c1 : 0.0;
   bool ok = false;
   PD r;
   double s = s0, c = c0, sh = 0, ch = 0, dp_final = 0.0;
@@ -245,14 +254,13 @@ __device__ PD eval_series_warp(int64_t N, double sh, double ch, int lane) {
   return r;
 }
 
-// one warp per node k < kend (N sin theta*_k < 25, N > 64)
-__global__ void __launch_bounds__(32) k_legpts_ends(int64_t N, double* __restrict__ theta, double* __restrict__ x,
-                                                    double* __restrict__ w, double* __restrict__ tN,
-                                                    int* __restrict__ status, int max_iter) {
-  const int64_t k = blockIdx.x;
-  const int lane = threadIdx.x;
-  const double Nh = (double)N + 0.5;
-  const double inv_Nh = 1.0 / Nh;
+// one warp per node k < kend (N sin theta*_k < 25, N > 64); every lane of the
+// warp calls it with the same k
+__device__ __forceinline__ void end_node(int64_t N, int64_t k, int lane, const NodeConst& K,
+                                         double* __restrict__ theta, double* __restrict__ x,
+                                         double* __restrict__ w, double* __restrict__ tN, int* __restrict__ status,
+                                         int max_iter) {
+  const double inv_Nh = K.inv_Nh;
   const double th0 = ((double)k + 0.75) * kPi * inv_Nh;
   double d = kJ0Zeros[k] * inv_Nh - th0;
   bool ok = false;
@@ -292,7 +300,27 @@ __global__ void __launch_bounds__(32) k_legpts_ends(int64_t N, double* __restric
   tN[km] = -tk;
 }
 
-// nodes handled by k_legpts_ends: the first k with N sin theta*_k >= 25 (at most 8)
+// One launch for every node: blocks [0, nbe) take the end nodes k < kend, one
+// warp each (the dependent double-double series sets their length, so they
+// start first and run under the interior nodes), blocks from nbe on the nodes
+// kend <= k < ceil(N/2), one thread each.
+constexpr int kNodeThreads = 128;
+__global__ void __launch_bounds__(kNodeThreads) k_legpts(int64_t N, int64_t kend, int nbe, double CN, HTab H,
+                                                         NodeConst K, double* __restrict__ theta,
+                                                         double* __restrict__ x, double* __restrict__ w,
+                                                         double* __restrict__ tN, int* __restrict__ status,
+                                                         int max_iter) {
+  if ((int)blockIdx.x < nbe) {
+    const int64_t k = (int64_t)blockIdx.x * (kNodeThreads / 32) + (threadIdx.x >> 5);
+    if (k < kend) end_node(N, k, threadIdx.x & 31, K, theta, x, w, tN, status, max_iter);
+    return;
+  }
+  const int64_t k = (int64_t)(blockIdx.x - nbe) * kNodeThreads + threadIdx.x;
+  if (k >= (N + 1) / 2 || k < kend) return;
+  interior_node(N, k, CN, H, K, theta, x, w, tN, status, max_iter);
+}
+
+// nodes handled by end_node: the first k with N sin theta*_k >= 25 (at most 8)
 int64_t end_nodes(int64_t N) {
   if (N <= 64) return 0;
   int64_t k = 0;
@@ -315,17 +343,18 @@ HTab htab(int64_t N) {
   return H;
 }
 
-// the node kernels on `stream` (callers count the launches)
-void launch_main_nodes(int64_t N, int64_t kend, double CN, double* theta, double* x, double* w, double* tN,
-                       int* status, cudaStream_t stream, int max_iter = kNodeIterMax) {
+// the node kernel on `stream` (callers count the launch)
+void launch_nodes(int64_t N, double CN, double* theta, double* x, double* w, double* tN, int* status,
+                  cudaStream_t stream, int max_iter = kNodeIterMax) {
+  const int64_t kend = end_nodes(N);
+  const int nbe = (int)((kend + kNodeThreads / 32 - 1) / (kNodeThreads / 32));
   const int64_t half = (N + 1) / 2;
-  const int threads = 128;
-  k_legpts<<<(unsigned)((half + threads - 1) / threads), threads, 0, stream>>>(N, kend, CN, htab(N), theta, x, w,
-                                                                               tN, status, max_iter);
-}
-void launch_end_nodes(int64_t N, int64_t kend, double* theta, double* x, double* w, double* tN, int* status,
-                      cudaStream_t stream, int max_iter = kNodeIterMax) {
-  if (kend > 0) k_legpts_ends<<<(unsigned)kend, 32, 0, stream>>>(N, theta, x, w, tN, status, max_iter);
+  NodeConst K;
+  const double Nh = (double)N + 0.5;
+  K.inv_Nh = 1.0 / Nh;
+  K.c1 = 0.125 / (Nh * ((double)N + 1.5));
+  const unsigned blocks = (unsigned)(nbe + (half + kNodeThreads - 1) / kNodeThreads);
+  k_legpts<<<blocks, kNodeThreads, 0, stream>>>(N, kend, nbe, CN, htab(N), K, theta, x, w, tN, status, max_iter);
 }
 
 }  // namespace
@@ -339,13 +368,8 @@ int launch_dtheta(Plan& P, double* out) {
 
 int launch_legpts(Plan& P, double CN) {
   const int64_t N = P.p.N;
-  const int64_t kend = end_nodes(N);
-  launch_main_nodes(N, kend, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max);
+  launch_nodes(N, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max);
   launched(P, "legpts", 0.0, 32.0 * N);
-  if (kend > 0) {
-    launch_end_nodes(N, kend, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max);
-    launched(P, "legpts_ends", 0.0, 64.0 * kend);
-  }
   return check_launch();
 }
 
@@ -433,13 +457,8 @@ extern "C" int gbdlt_legpts_noalloc(int64_t N, double* x, double* theta, double*
     cudaGetLastError();
     return GBDLT_ERR_CUDA;
   }
-  const int64_t kend = end_nodes(N);
-  launch_main_nodes(N, kend, cn_running(N), theta, x, w, tN, status, stream);
+  launch_nodes(N, cn_running(N), theta, x, w, tN, status, stream);
   count_launch();
-  if (kend > 0) {
-    launch_end_nodes(N, kend, theta, x, w, tN, status, stream);
-    count_launch();
-  }
   if (dtheta) {
     k_dtheta<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(tN, dtheta, N);
     count_launch();
