@@ -367,6 +367,8 @@ def run_gpu(args, world, rank, local):
         return out
 
     ops64 = per_op(plan64, c, max(args.steps, 10))
+    # the FP64 rate an FMA-chain kernel reaches on this device (library probe)
+    fp64_probe = g.fp64_fma_rate(stream)
 
     # ---------------- FP64 form at the benchmark spec's tolerance (1e-12 ||c||_1)
     plan12, _ = make(g.FP64, 1e-12)
@@ -512,6 +514,8 @@ def run_gpu(args, world, rank, local):
                     "kernel": name, "launches_per_step": d["launches"] / args.steps,
                     "ms_per_launch": round(per_launch_ms, 4),
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz",
+                    "peak_probe": round(fp64_probe / 1e12, 4),
+                    "frac_of_probe": round(achieved / (fp64_probe / 1e12), 4) if fp64_probe > 0 else None,
                     "timing": "CUDA events after every launch on the plan stream, over K profiled steps "
                               "run right after the timed steps (serial kernel order)"}
         total_prof = sum(v["ms"] for v in prof.values())

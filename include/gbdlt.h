@@ -302,6 +302,16 @@ uint64_t gbdlt_launch_count(void);
  * it was loaded: plan workspaces, plan-creation scratch and batch staging
  * buffers (all plans and batches, all threads). */
 uint64_t gbdlt_device_alloc_count(void);
+/* Measurement helper (no counterpart in the paper): the FP64 arithmetic rate
+ * this device reaches, the denominator of the roofline of the FP64 kernels,
+ * whose bound is the FP64 pipe.  Runs a kernel of independent FP64 fused
+ * multiply-add chains (8 per thread, 8 CTAs of 256 threads per SM, a fixed
+ * loop count) four times on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default) and stores 2 flops per FMA divided by the fastest of the last three
+ * runs (CUDA events) into *flops_per_second.  Synchronises the stream; makes
+ * one small device allocation.  GBDLT_ERR_INVALID_ARG for a null pointer,
+ * GBDLT_ERR_CUDA / GBDLT_ERR_OOM on a runtime failure. */
+int gbdlt_fp64_fma_rate(void* cuda_stream, double* flops_per_second);
 
 #ifdef __cplusplus
 }

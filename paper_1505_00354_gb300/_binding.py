@@ -90,7 +90,7 @@ ENTRY_POINTS = (
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
     "gbdlt_batch_create", "gbdlt_batch_create_ex", "gbdlt_batch_exec", "gbdlt_batch_info",
     "gbdlt_batch_group_info", "gbdlt_batch_group_info_ex", "gbdlt_batch_destroy",
-    "gbdlt_status_string", "gbdlt_launch_count", "gbdlt_device_alloc_count",
+    "gbdlt_status_string", "gbdlt_launch_count", "gbdlt_device_alloc_count", "gbdlt_fp64_fma_rate",
 )
 
 
@@ -142,6 +142,7 @@ def lib():
         L.gbdlt_status_string.restype = ctypes.c_char_p
         L.gbdlt_launch_count.restype = ctypes.c_uint64
         L.gbdlt_device_alloc_count.restype = ctypes.c_uint64
+        L.gbdlt_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         for name in ENTRY_POINTS:
             if name not in ("gbdlt_status_string", "gbdlt_launch_count", "gbdlt_device_alloc_count"):
                 getattr(L, name).restype = i32
@@ -170,6 +171,15 @@ def launch_count() -> int:
 def device_alloc_count() -> int:
     """Device allocations (cudaMalloc calls) the library has made since it was loaded."""
     return int(lib().gbdlt_device_alloc_count())
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """FP64 flops per second reached by the library's FMA-chain probe on the
+    current device (the roofline denominator of the FP64 kernels)."""
+    s = torch.cuda.current_stream() if stream is None else stream
+    r = ctypes.c_double()
+    _check(lib().gbdlt_fp64_fma_rate(ctypes.c_void_p(s.cuda_stream), ctypes.byref(r)), "fp64_fma_rate")
+    return float(r.value)
 
 
 def _dtype(prec: int):

@@ -503,3 +503,14 @@ def test_fft_staging_bitwise(gb, N, prec):
     assert gb.lib().gbdlt_plan_sync(p.handle) == 0
     with pytest.raises(gb.GbdltError):
         gb._binding._check(gb.lib().gbdlt_plan_set_fft_staging(p.handle, 2), "set_fft_staging")
+
+
+def test_fp64_rate_probe(gb):
+    """The FP64 FMA-chain probe reaches a rate near the FP64 pipe's peak
+    (2 FMA per SM and clock at up to 2070 MHz): the roofline denominator of the
+    FP64 kernels is a measured number, not only a derived one."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 2 * 2 * 2.07e9
+    r = gb.fp64_fma_rate()
+    print(f"FP64 FMA probe: {r / 1e12:.4f} TFLOP/s ({r / peak:.3f} of {peak / 1e12:.4f} derived)")
+    assert 0.3 * peak < r < 1.1 * peak
