@@ -192,3 +192,24 @@ def test_grid_uneven_batch(gb):
             err = np.max(np.abs(yi - oracle.idlt(xi, nd)) / ((np.arange(N) + 0.5) * np.abs(nd.w * xi).sum()))
         worst = max(worst, err)
     assert worst <= TOL64
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grid_group_many_passes(gb, prec):
+    """A grid group larger than one workspace pass (lengths 4097 .. 8192, 300
+    transforms per direction: several passes of the G = 8192 chain), so the
+    per-item rule table is read at every pass's offset; every transform matches
+    the single plan of its own length."""
+    from paper_1505_00354_gb300 import inputs
+    rng = np.random.default_rng(45)
+    B = 600
+    Ns = rng.integers(4097, 8193, B).astype(np.int64)
+    dirs = np.r_[np.zeros(B // 2), np.ones(B - B // 2)].astype(np.int32)
+    x = np.concatenate([inputs.coeffs(int(N), 7500 + i, 1.0) for i, N in enumerate(Ns)])
+    b = gb.Batch(Ns, dirs, prec)
+    groups = b.groups()
+    assert len(groups) == 2 and all(G["N"] == 8192 and G["count"] == 300 for G in groups)
+    dt = torch.float64 if prec == 0 else torch.float32
+    xd = dev(x, dt)
+    y = b.run(xd)
+    check_groups(gb, b, Ns, dirs, xd, y, prec, TOL64 if prec == 0 else TOL32)
