@@ -316,6 +316,14 @@ struct Plan {
   // row k (n = k, k+2, ..., < head) from offset head_off[k] (head.cu)
   double* head_tab = nullptr;
   int64_t* head_off = nullptr;
+  // FP32 plans with head > kHeadMM: the register-blocked head kernels (head.cu):
+  // Lam' with kHeadPad zeros on both sides, their warp tasks (forward, then
+  // transposed) and the per-item chunk partials
+  float* head_lamp = nullptr;
+  int4* head_tasks = nullptr;
+  int head_ntask_f = 0, head_ntask_t = 0;
+  double* head_part = nullptr;
+  int64_t head_part_n = 0;  // doubles per batch item
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
   RecLayout rec;    // recurrence region of the fast path (cheb1 rows)
   RecLayout drec;   // every row and column at the Legendre nodes (direct method)
@@ -569,5 +577,12 @@ template <typename T>
 int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* hout = nullptr);
 // fills P.head_tab from P.head_lam (plan creation)
 int launch_head_tab_init(Plan& P);
+// FP32 head blocks above kHeadMM columns run register-blocked warp tasks of
+// kHeadRB outputs per lane over chunks of kHeadChunk reduction indices; the host
+// side lists the tasks (x, y, z = parity, output block, chunk) of both
+// directions and sizes the partial buffer (doubles per batch item)
+constexpr int64_t kHeadMM = 2048;
+constexpr int kHeadPad = 1536;
+void head_rb_tasks(int64_t h, std::vector<int4>& fwd, std::vector<int4>& trn, int64_t* part_n);
 
 }  // namespace gbdlt

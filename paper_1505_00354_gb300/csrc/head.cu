@@ -15,7 +15,9 @@
 // runs on a pipe 64 times wider than FP64 on GB300).  Per term: one product of
 // two table entries and one multiply-add, so FP64 issue bounds the FP64 form;
 // FP64 plans with h <= kHeadTabMax use the stored products below instead.
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "gbdlt_internal.cuh"
 
@@ -224,7 +226,6 @@ __global__ void __launch_bounds__(TW * 32) k_head_t_tab(const double* __restrict
 // ascending reduction order, sequentially (an FP64 fused multiply-add chain, a
 // Kahan-compensated FP32 sum), so the result of an item does not depend on how
 // many items a call carries.  Thread t: item t mod 32, outputs 8 (t / 32) + i.
-constexpr int64_t kHeadMM = 2048;
 constexpr int MMO = 64, MMB = 32, MMR = 32;
 
 template <typename T, bool TRANS>
@@ -300,7 +301,144 @@ __global__ void __launch_bounds__(256) k_head_mm(const T* __restrict__ x, T* __r
   }
 }
 
+// ---------------------------------------------------------------- FP32, register-blocked (h > kHeadMM)
+// Per parity p the block is G_p[a][m] = Lam'_{m-a} Lam'_{m+a+p} (a <= m; k = p + 2a,
+// n = p + 2m).  A warp task takes 256 consecutive outputs of one parity (8 per
+// lane: o_i = o0 + i) and one chunk of 512 reduction indices r:
+//   forward     out a = o_i, reduction m = r:  term Lam'[r - o_i] Lam'[r + o_i + p] x_{p+2r}
+//   transposed  out m = o_i, reduction a = r:  term Lam'[o_i - r] Lam'[o_i + r + p] y_{p+2r}
+// (y_0 halved for p = 0).  From one r to the next the first factors of a lane's
+// 8 outputs move up one output and the second ones down one, so the entry a
+// lane needs next is held by its neighbour lane (a warp shuffle) and the warp
+// loads only the two entries entering at its edges and the input x_{p+2r}, each
+// one address for all lanes; terms outside the triangle read the table's zero
+// padding (index below 0) and vanish.  Each output sums its terms 8 at a time in
+// FP32 fused multiply-adds and those block sums in a Kahan-compensated FP32 sum
+// in ascending r; k_head_rb_reduce adds the chunk sums of an output in ascending
+// chunk order in double.
+constexpr int RB = 8;
+constexpr int RBW = 32 * RB;
+constexpr int RBC = 512;
+
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_head_rb(const float* __restrict__ x, const float* __restrict__ lamp,
+                                                 const int4* __restrict__ tasks, int ntask, int64_t N, int64_t h,
+                                                 double* __restrict__ part, int64_t part_n) {
+  const int task = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5);
+  if (task >= ntask) return;  // whole warp
+  const int4 tk = tasks[task];
+  const int par = tk.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t Hp = (h - par + 1) / 2;
+  const int64_t H0 = (h + 1) / 2;
+  const int64_t nch = (H0 + RBC - 1) / RBC;
+  x += (int64_t)blockIdx.y * N;
+  const float* __restrict__ lam = lamp + kHeadPad;
+  const int64_t oB = (int64_t)tk.y * RBW;
+  const int64_t o0 = oB + lane * RB;
+  const int64_t r0 = (int64_t)tk.z * RBC;
+  const int64_t rend = TRANS ? min(Hp, (int64_t)(tk.y + 1) * RBW) : Hp;
+  const int64_t r1 = min(r0 + RBC, rend);
+  // T[i] = Lam'[r - o_i] (forward) or Lam'[o_i - r] (transposed), H[i] = Lam'[r + o_i + p]
+  float T[RB], H[RB], acc[RB], cmp[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    T[i] = lam[TRANS ? (o0 + i - r0) : (r0 - o0 - i)];
+    H[i] = lam[r0 + o0 + i + par];
+    acc[i] = cmp[i] = 0.f;
+  }
+  for (int64_t R = r0; R < r1; R += RB) {
+    // the entries that enter at the warp's edges over the next RB steps (one
+    // address per load for the whole warp), and the inputs
+    float tl[RB], hl[RB], xv[RB];
+#pragma unroll
+    for (int st = 0; st < RB; ++st) {
+      const int64_t r = R + st;
+      tl[st] = lam[TRANS ? (oB - r - 1) : (r + 1 - oB)];
+      hl[st] = lam[r + 1 + oB + RBW - 1 + par];
+      float v = r < r1 ? x[par + 2 * r] : 0.f;
+      if (TRANS && par == 0 && r == 0) v *= 0.5f;
+      xv[st] = v;
+    }
+    float b[RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) b[i] = 0.f;
+#pragma unroll
+    for (int st = 0; st < RB; ++st) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) b[i] = fmaf(__fmul_rn(T[i], H[i]), xv[st], b[i]);
+      // step r -> r + 1: the first factors move up one output and the second ones
+      // down one; the entries entering a lane come from its neighbours
+      const float up = __shfl_up_sync(0xffffffffu, T[RB - 1], 1);
+      const float dn = __shfl_down_sync(0xffffffffu, H[0], 1);
+#pragma unroll
+      for (int i = RB - 1; i > 0; --i) T[i] = T[i - 1];
+#pragma unroll
+      for (int i = 0; i + 1 < RB; ++i) H[i] = H[i + 1];
+      T[0] = lane == 0 ? tl[st] : up;
+      H[RB - 1] = lane == 31 ? hl[st] : dn;
+    }
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      const float y = __fsub_rn(b[i], cmp[i]);
+      const float t = __fadd_rn(acc[i], y);
+      cmp[i] = __fsub_rn(__fsub_rn(t, acc[i]), y);
+      acc[i] = t;
+    }
+  }
+  double* dst = part + (int64_t)blockIdx.y * part_n + ((int64_t)par * nch + tk.z) * H0;
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+    if (o0 + i < Hp) dst[o0 + i] = (double)acc[i] - (double)cmp[i];
+}
+
+// out index q (k forward, n transposed), parity q & 1, position o = q >> 1: the
+// chunk sums of its task column in ascending chunk order
+template <bool TRANS>
+__global__ void k_head_rb_reduce(const double* __restrict__ part, int64_t part_n, float* __restrict__ out,
+                                 int64_t N, int64_t h, int scale_s, double* __restrict__ hout, int64_t hs) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h) return;
+  const int par = (int)(q & 1);
+  const int64_t o = q >> 1;
+  const int64_t Hp = (h - par + 1) / 2;
+  const int64_t H0 = (h + 1) / 2;
+  const int64_t nch = (H0 + RBC - 1) / RBC;
+  const int64_t blk = o / RBW;
+  // forward: chunks from the one holding the block's first output to the last;
+  // transposed: chunks up to the one holding the block's last reduction index
+  const int64_t c0 = TRANS ? 0 : (blk * RBW) / RBC;
+  const int64_t c1 = TRANS ? (min(Hp, (blk + 1) * RBW) - 1) / RBC + 1 : (Hp + RBC - 1) / RBC;
+  const double* src = part + (int64_t)blockIdx.y * part_n + (int64_t)par * nch * H0 + o;
+  double s = 0.0;
+  for (int64_t c = c0; c < c1; ++c) s += src[c * H0];
+  if (!TRANS && q == 0) s *= 0.5;
+  if (TRANS && scale_s) s *= (double)q + 0.5;
+  if (hout)
+    hout[(int64_t)blockIdx.y * hs + q] = s;
+  else
+    out[(int64_t)blockIdx.y * N + q] = (float)((double)out[(int64_t)blockIdx.y * N + q] + s);
+}
+
 }  // namespace
+
+void head_rb_tasks(int64_t h, std::vector<int4>& fwd, std::vector<int4>& trn, int64_t* part_n) {
+  fwd.clear();
+  trn.clear();
+  const int64_t H0 = (h + 1) / 2;
+  const int64_t nch = (H0 + RBC - 1) / RBC;
+  for (int par = 0; par < 2; ++par) {
+    const int64_t Hp = (h - par + 1) / 2;
+    const int64_t nblk = (Hp + RBW - 1) / RBW;
+    const int64_t nchp = (Hp + RBC - 1) / RBC;
+    for (int64_t b = 0; b < nblk; ++b) {
+      for (int64_t c = (b * RBW) / RBC; c < nchp; ++c) fwd.push_back(make_int4(par, (int)b, (int)c, 0));
+      const int64_t last = std::min(Hp, (b + 1) * RBW) - 1;
+      for (int64_t c = 0; c <= last / RBC; ++c) trn.push_back(make_int4(par, (int)b, (int)c, 0));
+    }
+  }
+  *part_n = 2 * nch * H0;
+}
 
 int launch_head_tab_init(Plan& P) {
   const int64_t h = P.p.head;
@@ -325,6 +463,17 @@ int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb, double* hout) {
                                                                    P.p.N * (int64_t)sizeof(T) / 8, nb);
     launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * (double)sizeof(T) * 2.0 * (double)h);
     return check_launch();
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (P.head_lamp) {
+      k_head_rb<false><<<dim3((unsigned)((P.head_ntask_f + 7) / 8), (unsigned)nb), 256, 0, P.stream>>>(
+          c, P.head_lamp, P.head_tasks, P.head_ntask_f, P.p.N, h, P.head_part, P.head_part_n);
+      launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 4.0 * 2.0 * (double)h);
+      k_head_rb_reduce<false><<<dim3((unsigned)((h + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
+          P.head_part, P.head_part_n, chat, P.p.N, h, 0, hout, P.p.N * (int64_t)sizeof(T) / 8);
+      launched(P, "head_reduce", 0.0, (double)nb * 8.0 * (double)P.head_part_n);
+      return check_launch();
+    }
   }
   if constexpr (sizeof(T) == 8) {
     if (P.head_tab && !hout) {
@@ -352,6 +501,17 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* 
     launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h,
              (double)nb * (double)sizeof(T) * 2.0 * (double)h);
     return check_launch();
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (P.head_lamp) {
+      k_head_rb<true><<<dim3((unsigned)((P.head_ntask_t + 7) / 8), (unsigned)nb), 256, 0, P.stream>>>(
+          y, P.head_lamp, P.head_tasks + P.head_ntask_f, P.head_ntask_t, P.p.N, h, P.head_part, P.head_part_n);
+      launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 4.0 * 2.0 * (double)h);
+      k_head_rb_reduce<true><<<dim3((unsigned)((h + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
+          P.head_part, P.head_part_n, out, P.p.N, h, scale_s, hout, P.p.N * (int64_t)sizeof(T) / 8);
+      launched(P, "head_reduce", 0.0, (double)nb * 8.0 * (double)P.head_part_n);
+      return check_launch();
+    }
   }
   if constexpr (sizeof(T) == 8) {
     if (P.head_tab) {

@@ -785,12 +785,18 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
       P->prune_R = (int)Rs;
     }
   }
+  // FP32 plans with a head block above kHeadMM columns: the register-blocked
+  // head kernels' tasks and per-item chunk partials (head.cu)
+  const bool head_rb = prec == GBDLT_FP32 && prm.fast && prm.head > kHeadMM;
+  std::vector<int4> rb_fwd, rb_trn;
+  int64_t rb_part = 0;
+  if (head_rb) head_rb_tasks(prm.head, rb_fwd, rb_trn, &rb_part);
   {
     // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
     const double per_item = 2.0 * P->nfft_max * N * cs + 2.0 * nfft32 * N * 8.0 + 2.0 * nfftff * N * 16.0 +
                             5.0 * N * ts +
                             16.0 * (R.nseg_total + D.nseg_total) +
-                            8.0 * (R.tbuf_total + D.tbuf_total);
+                            8.0 * (R.tbuf_total + D.tbuf_total) + 8.0 * (double)rb_part;
     P->bcap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(512.0 * (1 << 20) / per_item)));
     if (max_batch > 0) P->bcap = std::min<int64_t>(P->bcap, max_batch);
   }
@@ -830,6 +836,9 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
   }
   size_t o_hoff = A.take<int64_t>(head_tab ? nhead : 1);
   size_t o_htab = A.take<double>(head_tab ? htab_n : 1);
+  size_t o_lamp = A.take<float>(head_rb ? nhead + 2 * kHeadPad : 1);
+  size_t o_rbt = A.take<int4>(head_rb ? (int64_t)(rb_fwd.size() + rb_trn.size()) : 1);
+  size_t o_rbp = A.take<double>(head_rb ? BC * rb_part : 1);
   auto take_layout = [&](const RecLayout& L) {
     LayoutOff o;
     o.cut = A.take<int32_t>(L.H);
@@ -903,6 +912,14 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
   P->head_lamf = nhead > 0 ? (float*)(base + o_lamf) : nullptr;
   P->head_off = head_tab ? (int64_t*)(base + o_hoff) : nullptr;
   P->head_tab = head_tab ? (double*)(base + o_htab) : nullptr;
+  if (head_rb) {
+    P->head_lamp = (float*)(base + o_lamp);
+    P->head_tasks = (int4*)(base + o_rbt);
+    P->head_ntask_f = (int)rb_fwd.size();
+    P->head_ntask_t = (int)rb_trn.size();
+    P->head_part = (double*)(base + o_rbp);
+    P->head_part_n = rb_part;
+  }
   auto place_layout = [&](RecLayout& L, const LayoutOff& o) {
     L.cut = (int32_t*)(base + o.cut);
     L.poff = (int64_t*)(base + o.poff);
@@ -984,6 +1001,15 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     up(P->head_lam, lam.data(), sizeof(double) * lam.size());
     up(P->head_lamf, lamf.data(), sizeof(float) * lamf.size());
     if (P->head_tab) up(P->head_off, hoff.data(), sizeof(int64_t) * hoff.size());
+    if (P->head_lamp) {
+      // Lam' with kHeadPad zeros on each side: terms outside the triangle read zeros
+      std::vector<float> lamp((size_t)(nhead + 2 * kHeadPad), 0.f);
+      std::copy(lamf.begin(), lamf.end(), lamp.begin() + kHeadPad);
+      up(P->head_lamp, lamp.data(), sizeof(float) * lamp.size());
+      std::vector<int4> tasks(rb_fwd);
+      tasks.insert(tasks.end(), rb_trn.begin(), rb_trn.end());
+      up(P->head_tasks, tasks.data(), sizeof(int4) * tasks.size());
+    }
   }
   auto upload_layout = [&](RecLayout& L, const LayoutHost& h) {
     if (L.H == 0) return;
