@@ -30,6 +30,7 @@ rank) and reports the whole-job rate.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -343,8 +344,12 @@ def run_gpu(args, world, rank, local):
         f = torch.empty_like(x)
         cb = torch.empty_like(x)
 
+        nodes = [torch.empty(x.shape[-1], dtype=torch.float64, device="cuda") for _ in range(4)]
+
         def legpts():
-            st = lib.gbdlt_legpts(plan.handle, None, None, None, None)
+            # with output arrays the node kernel runs at once (without, it is
+            # deferred to the next transform, where the step times it)
+            st = lib.gbdlt_legpts(plan.handle, *[ctypes.c_void_p(t.data_ptr()) for t in nodes])
             if st:
                 raise g.GbdltError(st, "legpts")
 

@@ -184,7 +184,13 @@ int gbdlt_plan_set_wait_limit(gbdlt_plan plan, int64_t sm_cycles);
  * theta ascending, x = cos(theta) descending (1 > x_0 > ... > x_{N-1} > -1).
  * Outputs (device, N doubles each, any may be NULL): x, theta, w (Gauss-Legendre
  * weights), dtheta = theta_k - (k+1/2)pi/N (offset from the Chebyshev points of
- * the first kind, Eq. 5). */
+ * the first kind, Eq. 5).  With every output NULL the recomputation is deferred
+ * to the next call on this plan that reads the nodes: the FFT-based transforms
+ * of a power-of-two plan run it as a branch beside their first stages (which do
+ * not read the nodes) and wait for it before the Taylor step; other calls run it
+ * first; gbdlt_plan_sync runs a refresh still pending, so its status (e.g.
+ * GBDLT_ERR_NOT_CONVERGED) is reported there.  The nodes are the same either
+ * way. */
 int gbdlt_legpts(gbdlt_plan plan, double* x, double* theta, double* w, double* dtheta);
 
 /* Allocation-free Gauss-Legendre rule, for callers that cannot call

@@ -369,6 +369,13 @@ struct Plan {
   bool side_broken = false;  // creation failed: everything on the plan stream
   struct Profiler* prof = nullptr;  // per-kernel event timing (off unless enabled)
   struct GraphCache* graphs = nullptr;  // replayed transform chains (plan.cu)
+  // gbdlt_legpts without outputs defers the node kernel to the next call that
+  // reads the nodes, where it runs as a branch beside that chain's first stages
+  // (plan.cu, nodes_start / nodes_ready)
+  bool nodes_pending = false;
+  bool node_branch_open = false;  // the branch is in flight: readers wait on node_join
+  cudaStream_t node_s = nullptr;
+  cudaEvent_t node_fork = nullptr, node_join = nullptr;
   // N not a power of two (grid.cu): the fast path is the chain of `inner`, a plan
   // on the power-of-two grid G > N, fed with inputs zero-padded to G; this plan
   // keeps the N-point rule (and the direct method's layout)
@@ -425,6 +432,10 @@ inline TwT<ffd> tw_tables(const Plan& P, ffd) {
   return {P.tw4096_ff, nullptr, nullptr, nullptr, nullptr, P.twfull_ff, nullptr};
 }
 
+// Before a kernel that reads the plan's nodes (tN, w, theta, x): the plan stream
+// waits for a node branch in flight (a deferred gbdlt_legpts), if any.
+int nodes_ready(Plan& P);
+
 // plan lifecycle and the operator dispatch shared by the C ABI and the batch
 // executor; max_batch > 0 limits the batch items one workspace pass holds
 // want_direct also builds the direct layout for a fast plan (the batch autotuner
@@ -465,7 +476,9 @@ int launch_fft_tables_init(Plan& P);
 // stages.cu: the FP64 stage tables (Hnm, row_ar)
 int launch_stage_tables_init(Plan& P);
 // legpts.cu
-int launch_legpts(Plan& P, double CN);
+// blocks_per_sm > 0: a grid of that many blocks per SM strides over the nodes
+// (the node kernel as a branch beside other kernels leaves room on every SM)
+int launch_legpts(Plan& P, double CN, int blocks_per_sm = 0);
 int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N
 // fft.cu: in-place batched FFT of length N, sign DIR (+1: e^{+2 pi i nk/N}).
 // Input in `a`; result in `a` when N <= 4096, else in `b` (returned pointer).

@@ -33,6 +33,7 @@
 // by the Taylor series of Sec. 2.1 (computed from the exact difference
 // theta*_k - theta^cheb1_k = pi (N-2k-1) / (4N(N+1/2)) plus delta, so it keeps
 // full relative accuracy).
+#include <algorithm>
 #include <cmath>
 
 #include "gbdlt_internal.cuh"
@@ -305,19 +306,36 @@ __device__ __forceinline__ void end_node(int64_t N, int64_t k, int lane, const N
 // start first and run under the interior nodes), blocks from nbe on the nodes
 // kend <= k < ceil(N/2), one thread each.
 constexpr int kNodeThreads = 128;
-__global__ void __launch_bounds__(kNodeThreads) k_legpts(int64_t N, int64_t kend, int nbe, double CN, HTab H,
-                                                         NodeConst K, double* __restrict__ theta,
-                                                         double* __restrict__ x, double* __restrict__ w,
-                                                         double* __restrict__ tN, int* __restrict__ status,
-                                                         int max_iter) {
-  if ((int)blockIdx.x < nbe) {
-    const int64_t k = (int64_t)blockIdx.x * (kNodeThreads / 32) + (threadIdx.x >> 5);
+// work block b: the end nodes (b < nbe) or 128 interior nodes
+__device__ __forceinline__ void node_block(int b, int64_t N, int64_t kend, int nbe, double CN, const HTab& H,
+                                           const NodeConst& K, double* __restrict__ theta, double* __restrict__ x,
+                                           double* __restrict__ w, double* __restrict__ tN,
+                                           int* __restrict__ status, int max_iter) {
+  if (b < nbe) {
+    const int64_t k = (int64_t)b * (kNodeThreads / 32) + (threadIdx.x >> 5);
     if (k < kend) end_node(N, k, threadIdx.x & 31, K, theta, x, w, tN, status, max_iter);
     return;
   }
-  const int64_t k = (int64_t)(blockIdx.x - nbe) * kNodeThreads + threadIdx.x;
+  const int64_t k = (int64_t)(b - nbe) * kNodeThreads + threadIdx.x;
   if (k >= (N + 1) / 2 || k < kend) return;
   interior_node(N, k, CN, H, K, theta, x, w, tN, status, max_iter);
+}
+
+// STRIDE: the grid is smaller than the nblocks blocks of work and every block
+// strides over them (a node kernel run beside other kernels leaves part of each
+// SM free); otherwise one block per work block.
+template <bool STRIDE>
+__global__ void __launch_bounds__(kNodeThreads) k_legpts(int64_t N, int64_t kend, int nbe, int nblocks, double CN,
+                                                         HTab H, NodeConst K, double* __restrict__ theta,
+                                                         double* __restrict__ x, double* __restrict__ w,
+                                                         double* __restrict__ tN, int* __restrict__ status,
+                                                         int max_iter) {
+  if (!STRIDE) {
+    node_block((int)blockIdx.x, N, kend, nbe, CN, H, K, theta, x, w, tN, status, max_iter);
+    return;
+  }
+  for (int b = (int)blockIdx.x; b < nblocks; b += (int)gridDim.x)
+    node_block(b, N, kend, nbe, CN, H, K, theta, x, w, tN, status, max_iter);
 }
 
 // nodes handled by end_node: the first k with N sin theta*_k >= 25 (at most 8)
@@ -343,9 +361,10 @@ HTab htab(int64_t N) {
   return H;
 }
 
-// the node kernel on `stream` (callers count the launch)
+// the node kernel on `stream` (callers count the launch); max_grid > 0 caps the
+// grid (the blocks stride over the work)
 void launch_nodes(int64_t N, double CN, double* theta, double* x, double* w, double* tN, int* status,
-                  cudaStream_t stream, int max_iter = kNodeIterMax) {
+                  cudaStream_t stream, int max_iter = kNodeIterMax, int max_grid = 0) {
   const int64_t kend = end_nodes(N);
   const int nbe = (int)((kend + kNodeThreads / 32 - 1) / (kNodeThreads / 32));
   const int64_t half = (N + 1) / 2;
@@ -353,8 +372,13 @@ void launch_nodes(int64_t N, double CN, double* theta, double* x, double* w, dou
   const double Nh = (double)N + 0.5;
   K.inv_Nh = 1.0 / Nh;
   K.c1 = 0.125 / (Nh * ((double)N + 1.5));
-  const unsigned blocks = (unsigned)(nbe + (half + kNodeThreads - 1) / kNodeThreads);
-  k_legpts<<<blocks, kNodeThreads, 0, stream>>>(N, kend, nbe, CN, htab(N), K, theta, x, w, tN, status, max_iter);
+  const int nblocks = (int)(nbe + (half + kNodeThreads - 1) / kNodeThreads);
+  if (max_grid > 0 && max_grid < nblocks)
+    k_legpts<true><<<(unsigned)max_grid, kNodeThreads, 0, stream>>>(N, kend, nbe, nblocks, CN, htab(N), K, theta,
+                                                                    x, w, tN, status, max_iter);
+  else
+    k_legpts<false><<<(unsigned)nblocks, kNodeThreads, 0, stream>>>(N, kend, nbe, nblocks, CN, htab(N), K, theta,
+                                                                     x, w, tN, status, max_iter);
 }
 
 }  // namespace
@@ -366,9 +390,19 @@ int launch_dtheta(Plan& P, double* out) {
   return check_launch();
 }
 
-int launch_legpts(Plan& P, double CN) {
+int launch_legpts(Plan& P, double CN, int blocks_per_sm) {
   const int64_t N = P.p.N;
-  launch_nodes(N, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max);
+  int grid = 0;
+  if (blocks_per_sm > 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 1;
+    }
+    grid = blocks_per_sm * std::max(sms, 1);
+  }
+  launch_nodes(N, CN, P.theta, P.x, P.w, P.tN, P.status, P.stream, P.node_iter_max, grid);
   launched(P, "legpts", 0.0, 32.0 * N);
   return check_launch();
 }

@@ -507,6 +507,7 @@ struct Arena {
 // ---------------------------------------------------------------------------
 struct GraphEntry {
   int op = 0, method = 0;
+  bool nodes = false;  // the chain runs the deferred node kernel
   const void* in = nullptr;
   void* out = nullptr;
   int64_t batch = 0;
@@ -548,6 +549,12 @@ void free_plan(Plan* P) {
   }
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->node_s) {
+    cudaStreamSynchronize(P->node_s);
+    cudaStreamDestroy(P->node_s);
+  }
+  if (P->node_fork) cudaEventDestroy(P->node_fork);
+  if (P->node_join) cudaEventDestroy(P->node_join);
   if (P->arena) cudaFree(P->arena);
   if (P->inner) free_plan(P->inner);
   if (P->rg_in) cudaFree(P->rg_in);
@@ -1546,9 +1553,11 @@ int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out
   }
   GraphCache& G = *P.graphs;
   ++G.tick;
+  const bool with_nodes = P.nodes_pending && op != OP_L2C && op != OP_L2C_T;
   GraphEntry* E = nullptr;
   for (GraphEntry& x : G.e)
-    if (x.op == op && x.method == method && x.in == in && x.out == out && x.batch == batch) E = &x;
+    if (x.op == op && x.method == method && x.in == in && x.out == out && x.batch == batch && x.nodes == with_nodes)
+      E = &x;
   if (!E) {
     if (G.e.size() >= kGraphCacheSize) {
       size_t lru = 0;
@@ -1560,6 +1569,7 @@ int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out
     GraphEntry x;
     x.op = op;
     x.method = method;
+    x.nodes = with_nodes;
     x.in = in;
     x.out = out;
     x.batch = batch;
@@ -1610,13 +1620,58 @@ int run_op_method(gbdlt_plan plan, int op, int method, const void* in, void* out
   }
   if (cudaGraphLaunch(E->exec, G.s) != cudaSuccess) return GBDLT_ERR_CUDA;
   count_launch((int)E->kernels);
+  if (with_nodes) P.nodes_pending = false;  // the replayed chain ran the node kernel
   if (cudaEventRecord(G.out, G.s) != cudaSuccess || cudaStreamWaitEvent(P.stream, G.out, 0) != cudaSuccess)
     return GBDLT_ERR_CUDA;
   return GBDLT_OK;
 }
 
+// A deferred node refresh (gbdlt_legpts without outputs) starts with the next
+// chain that reads the nodes: as a branch on the plan's node stream beside the
+// chain's first stages when the chain is the FFT-based one of a power-of-two
+// plan (the node kernel is FP64-pipe work, the stages before the Taylor step do
+// not read the nodes), else in the plan stream before the chain.  Not as a
+// branch while profiling (the per-kernel events assume one stream).
+static int nodes_start(Plan& P, bool branch) {
+  if (!P.nodes_pending) return GBDLT_OK;
+  P.nodes_pending = false;
+  if (branch && !(P.prof && P.prof->on)) {
+    if (!P.node_s && (cudaStreamCreateWithFlags(&P.node_s, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&P.node_fork, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&P.node_join, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      return GBDLT_ERR_CUDA;
+    }
+    if (cudaEventRecord(P.node_fork, P.stream) != cudaSuccess ||
+        cudaStreamWaitEvent(P.node_s, P.node_fork, 0) != cudaSuccess)
+      return GBDLT_ERR_CUDA;
+    cudaStream_t main = P.stream;
+    P.stream = P.node_s;
+    // two blocks (8 warps) per SM keep the FP64 pipe busy and leave the rest of
+    // each SM to the chain's kernels
+    int st = launch_legpts(P, P.CN, 2);
+    P.stream = main;
+    if (st) return st;
+    if (cudaEventRecord(P.node_join, P.node_s) != cudaSuccess) return GBDLT_ERR_CUDA;
+    P.node_branch_open = true;
+    return GBDLT_OK;
+  }
+  return launch_legpts(P, P.CN);
+}
+
+int nodes_ready(Plan& P) {
+  if (!P.node_branch_open) return GBDLT_OK;
+  P.node_branch_open = false;
+  return cudaStreamWaitEvent(P.stream, P.node_join, 0) == cudaSuccess ? GBDLT_OK : GBDLT_ERR_CUDA;
+}
+
 static int run_chain(Plan& P, int op, int method, const void* in, void* out, int64_t batch) {
   const int64_t N = P.p.N;
+  if (P.nodes_pending && op != OP_L2C && op != OP_L2C_T) {
+    const bool branch = method == GBDLT_METHOD_FAST && P.p.fast && !P.inner && P.p.N > 1;
+    int st = nodes_start(P, branch);
+    if (st) return st;
+  }
   for (int64_t i = 0; i < batch; i += P.bcap) {
     const int64_t nb = std::min<int64_t>(P.bcap, batch - i);
     P.rg_item0 = i;  // the rule table of a grid plan's batch items (grid.cu)
@@ -1625,8 +1680,14 @@ static int run_chain(Plan& P, int op, int method, const void* in, void* out, int
       st = run_one<double>(P, op, method, (const double*)in + i * N, (double*)out + i * N, nb);
     else
       st = run_one<float>(P, op, method, (const float*)in + i * N, (float*)out + i * N, nb);
-    if (st) return st;
+    if (st) {
+      nodes_ready(P);
+      return st;
+    }
   }
+  // every branch rejoins the plan stream (a capture needs it; a chain whose
+  // readers all ran has joined already)
+  if (int st = nodes_ready(P)) return st;
   return check_launch();
 }
 
@@ -1766,6 +1827,11 @@ int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter) {
 int gbdlt_plan_sync(gbdlt_plan plan) {
   if (!plan) return GBDLT_ERR_INVALID_ARG;
   Plan* P = reinterpret_cast<Plan*>(plan);
+  if (P->nodes_pending) {
+    // a deferred node refresh runs now, so that its status is reported
+    P->nodes_pending = false;
+    if (int st = launch_legpts(*P, P->CN)) return st;
+  }
   if (cudaStreamSynchronize(P->stream) != cudaSuccess) return GBDLT_ERR_CUDA;
   int hs = 0, hi = 0;
   if (cudaMemcpy(&hs, P->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBDLT_ERR_CUDA;
@@ -1820,6 +1886,13 @@ int gbdlt_plan_get_params(gbdlt_plan plan, gbdlt_params* out) {
 int gbdlt_legpts(gbdlt_plan plan, double* x, double* theta, double* w, double* dtheta) {
   if (!plan) return GBDLT_ERR_INVALID_ARG;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (!x && !theta && !w && !dtheta) {
+    // nothing to copy out: the node kernel runs with the next call that reads the
+    // nodes (or at gbdlt_plan_sync)
+    P.nodes_pending = true;
+    return GBDLT_OK;
+  }
+  P.nodes_pending = false;
   int st = launch_legpts(P, P.CN);
   if (st) return st;
   const size_t bytes = sizeof(double) * (size_t)P.p.N;

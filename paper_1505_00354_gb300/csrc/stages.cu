@@ -1207,6 +1207,7 @@ int launch_tay_pro(Plan& P, const T* chat, C2<T>* U, ffc* Uff, int inc0, int npa
 template <typename T>
 int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, int inc0, int npair, int64_t nb) {
   const int P64 = Yff ? taylor_p64(P.p, inc0, npair) : npair;
+  if (int st = nodes_ready(P)) return st;
   if (P.rg_rules)
     k_tay_epi<T, true><<<dim3(nblk(P.rg_nmax), (unsigned)nb), TPB, 0, P.stream>>>(
         Y, Yff, v, f, nullptr, P.p.N, P.p.L, inc0, npair, P64, scale32(P), P.rg_rules,
@@ -1225,6 +1226,7 @@ int launch_tay_epi(Plan& P, const C2<T>* Y, const ffc* Yff, const T* v, T* f, in
 template <typename T>
 int launch_tayt_pro(Plan& P, const T* f, int use_w, C2<T>* U, ffc* Uff, int inc0, int npair, int64_t nb) {
   const int P64 = Uff ? taylor_p64(P.p, inc0, npair) : npair;
+  if (int st = nodes_ready(P)) return st;
   if (P.rg_rules)
     k_tayt_pro_grid<T><<<dim3(nblk(P.p.N / 2), (unsigned)nb), TPB, 0, P.stream>>>(
         f, use_w, P.rg_rules, P.rg_item ? P.rg_item + P.rg_item0 : nullptr, U, Uff, P.p.N, P.p.L, inc0, npair, P64,
@@ -1298,6 +1300,8 @@ int launch_absmax(Plan& P, const T* x, int64_t nb) {
 }
 template <typename T>
 int launch_scale(Plan& P, const T* in, T* out, int which, int64_t nb) {
+  if (which == 2)
+    if (int st = nodes_ready(P)) return st;  // the weights
   k_scale<T><<<dim3(nblk(P.p.N), (unsigned)nb), TPB, 0, P.stream>>>(in, out, P.w, P.p.N, which);
   {
     const double N = (double)P.p.N, ts = sizeof(T), cs = 2.0 * sizeof(T);
