@@ -131,9 +131,9 @@ int gbdlt_plan_params_ex(int64_t N, int prec, double eps, int method, gbdlt_para
  * (NULL = legacy default stream).  Computes the Legendre nodes and weights
  * (gbdlt_legpts), the per-N tables and allocates the workspace in one device
  * allocation (gbdlt_plan_get_params reports its size: FP64 plans with a head
- * block of h <= 32768 columns include its h^2/4 stored products, 537 MB at
- * N = 2^20 and 2.1 GB at 2^22).  On error *out is set to NULL and nothing is
- * leaked. */
+ * block of h <= 32768 columns include its h^2/4 stored products twice, ordered
+ * by rows and by columns, 1.07 GB at N = 2^20 and 4.3 GB at 2^22).  On error
+ * *out is set to NULL and nothing is leaked. */
 int gbdlt_plan_create(int64_t N, int prec, double eps, void* cuda_stream, gbdlt_plan* out);
 /* gbdlt_plan_create with the method given (GBDLT_METHOD_AUTO is what
  * gbdlt_plan_create uses). */

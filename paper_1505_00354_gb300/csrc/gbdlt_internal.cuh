@@ -316,6 +316,10 @@ struct Plan {
   // row k (n = k, k+2, ..., < head) from offset head_off[k] (head.cu)
   double* head_tab = nullptr;
   int64_t* head_off = nullptr;
+  // the same products column by column (column n holds rows k = n mod 2, ...,
+  // n from offset head_offT[n]): the transposed block reads them contiguously
+  double* head_tabT = nullptr;
+  int64_t* head_offT = nullptr;
   // FP32 plans with head > kHeadMM: the register-blocked head kernels (head.cu):
   // Lam' with kHeadPad zeros on both sides, their warp tasks (forward, then
   // transposed) and the per-item chunk partials

@@ -135,6 +135,58 @@ __global__ void k_head_tab_init(const double* __restrict__ lam, const int64_t* _
   for (int64_t j = threadIdx.x; j < J; j += blockDim.x) row[j] = lam[j] * lam[k + j];
 }
 
+// column n of the transposed table: entry i is row k = (n mod 2) + 2i, the
+// product Lam'_{(n-k)/2} Lam'_{(n+k)/2} rounded as in the row table
+__global__ void k_head_tabT_init(const double* __restrict__ lam, const int64_t* __restrict__ offT,
+                                 double* __restrict__ tabT, int64_t h) {
+  const int64_t n = blockIdx.x;
+  const int64_t p = n & 1;
+  const int64_t I = (n - p) / 2 + 1;
+  double* col = tabT + offT[n];
+  for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
+    const int64_t k = p + 2 * i;
+    const int64_t j = (n - k) / 2;
+    col[i] = lam[j] * lam[j + k];
+  }
+}
+
+// transposed from the column table: one warp per output n (longest columns
+// first), lanes over the rows, the row-0 term halved
+__global__ void __launch_bounds__(HW * 32) k_head_t_tabT(const double* __restrict__ y, double* __restrict__ out,
+                                                         const double* __restrict__ tabT,
+                                                         const int64_t* __restrict__ offT, int64_t N, int64_t h,
+                                                         int scale_s, double* __restrict__ hout, int64_t hs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * HW + (threadIdx.x >> 5);
+  if (q >= h) return;  // whole warp
+  const int64_t n = h - 1 - q;
+  const int64_t p = n & 1;
+  y += (int64_t)blockIdx.y * N;
+  out += (int64_t)blockIdx.y * N;
+  const int64_t I = (n - p) / 2 + 1;
+  const double* __restrict__ col = tabT + offT[n];
+  const double* __restrict__ x = y + p;
+  double a0 = 0.0, a1 = 0.0;
+  int64_t i = lane;
+#pragma unroll 4
+  for (; i + 32 < I; i += 64) {
+    a0 = fma(col[i], x[2 * i], a0);
+    a1 = fma(col[i + 32], x[2 * (i + 32)], a1);
+  }
+  if (i < I) a0 = fma(col[i], x[2 * i], a0);
+  double s = a0 + a1;
+  // the row k = 0 term (even n) enters halved: lane 0 took it in full
+  if (p == 0 && lane == 0) s = fma(-0.5 * col[0], y[0], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (scale_s) s *= (double)n + 0.5;
+    if (hout)
+      hout[(int64_t)blockIdx.y * hs + n] = s;
+    else
+      out[n] = out[n] + s;
+  }
+}
+
 // forward: one warp per output k, lanes over j (the on-the-fly kernel's order)
 __global__ void __launch_bounds__(HW * 32) k_head_fwd_tab(const double* __restrict__ c, double* __restrict__ chat,
                                                           const double* __restrict__ tab,
@@ -445,6 +497,10 @@ int launch_head_tab_init(Plan& P) {
   if (!P.head_tab || h == 0) return GBDLT_OK;
   k_head_tab_init<<<(unsigned)h, 256, 0, P.stream>>>(P.head_lam, P.head_off, P.head_tab, h);
   count_launch();
+  if (P.head_tabT) {
+    k_head_tabT_init<<<(unsigned)h, 256, 0, P.stream>>>(P.head_lam, P.head_offT, P.head_tabT, h);
+    count_launch();
+  }
   return check_launch();
 }
 
@@ -514,6 +570,12 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* 
     }
   }
   if constexpr (sizeof(T) == 8) {
+    if (P.head_tabT) {
+      k_head_t_tabT<<<dim3((unsigned)((h + HW - 1) / HW), (unsigned)nb), HW * 32, 0, P.stream>>>(
+          y, out, P.head_tabT, P.head_offT, P.p.N, h, scale_s, hout, P.p.N);
+      launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 8.0 * 0.25 * (double)h * (double)h);
+      return check_launch();
+    }
     if (P.head_tab) {
       k_head_t_tab<<<dim3((unsigned)(2 * ((h + 63) / 64)), (unsigned)nb), TW * 32, 0, P.stream>>>(
           y, out, P.head_tab, P.head_off, P.p.N, h, scale_s, hout, P.p.N);

@@ -843,6 +843,19 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
   }
   size_t o_hoff = A.take<int64_t>(head_tab ? nhead : 1);
   size_t o_htab = A.take<double>(head_tab ? htab_n : 1);
+  // the same products column by column (column n: rows k = n mod 2, ..., n), for
+  // the transposed block: column n from offset hoffT[n]
+  std::vector<int64_t> hoffT;
+  int64_t htabT_n = 0;
+  if (head_tab) {
+    hoffT.resize((size_t)nhead);
+    for (int64_t n = 0; n < nhead; ++n) {
+      hoffT[(size_t)n] = htabT_n;
+      htabT_n += n / 2 + 1;
+    }
+  }
+  size_t o_hoffT = A.take<int64_t>(head_tab ? nhead : 1);
+  size_t o_htabT = A.take<double>(head_tab ? htabT_n : 1);
   size_t o_lamp = A.take<float>(head_rb ? nhead + 2 * kHeadPad : 1);
   size_t o_rbt = A.take<int4>(head_rb ? (int64_t)(rb_fwd.size() + rb_trn.size()) : 1);
   size_t o_rbp = A.take<double>(head_rb ? BC * rb_part : 1);
@@ -919,6 +932,8 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
   P->head_lamf = nhead > 0 ? (float*)(base + o_lamf) : nullptr;
   P->head_off = head_tab ? (int64_t*)(base + o_hoff) : nullptr;
   P->head_tab = head_tab ? (double*)(base + o_htab) : nullptr;
+  P->head_offT = head_tab ? (int64_t*)(base + o_hoffT) : nullptr;
+  P->head_tabT = head_tab ? (double*)(base + o_htabT) : nullptr;
   if (head_rb) {
     P->head_lamp = (float*)(base + o_lamp);
     P->head_tasks = (int4*)(base + o_rbt);
@@ -1008,6 +1023,7 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     up(P->head_lam, lam.data(), sizeof(double) * lam.size());
     up(P->head_lamf, lamf.data(), sizeof(float) * lamf.size());
     if (P->head_tab) up(P->head_off, hoff.data(), sizeof(int64_t) * hoff.size());
+    if (P->head_tabT) up(P->head_offT, hoffT.data(), sizeof(int64_t) * hoffT.size());
     if (P->head_lamp) {
       // Lam' with kHeadPad zeros on each side: terms outside the triangle read zeros
       std::vector<float> lamp((size_t)(nhead + 2 * kHeadPad), 0.f);
