@@ -328,6 +328,7 @@ struct Plan {
   int head_ntask_f = 0, head_ntask_t = 0;
   double* head_part = nullptr;
   int64_t head_part_n = 0;  // doubles per batch item
+  int head_rbc = 0;         // reduction indices per task
   int64_t* band_dev = nullptr;  // [3K] ns, ka, kb
   RecLayout rec;    // recurrence region of the fast path (cheb1 rows)
   RecLayout drec;   // every row and column at the Legendre nodes (direct method)
@@ -594,12 +595,12 @@ template <typename T>
 int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* hout = nullptr);
 // fills P.head_tab from P.head_lam (plan creation)
 int launch_head_tab_init(Plan& P);
-// FP32 head blocks above kHeadMM columns run register-blocked warp tasks of
-// kHeadRB outputs per lane over chunks of kHeadChunk reduction indices; the host
-// side lists the tasks (x, y, z = parity, output block, chunk) of both
+// FP32 head blocks above kHeadMM columns run register-blocked warp tasks of 8
+// outputs per lane over chunks of *rbc reduction indices; the host side picks
+// the chunk, lists the tasks (x, y, z = parity, output block, chunk) of both
 // directions and sizes the partial buffer (doubles per batch item)
 constexpr int64_t kHeadMM = 2048;
 constexpr int kHeadPad = 1536;
-void head_rb_tasks(int64_t h, std::vector<int4>& fwd, std::vector<int4>& trn, int64_t* part_n);
+void head_rb_tasks(int64_t h, std::vector<int4>& fwd, std::vector<int4>& trn, int64_t* part_n, int* rbc);
 
 }  // namespace gbdlt

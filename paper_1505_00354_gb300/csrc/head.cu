@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(256) k_head_mm(const T* __restrict__ x, T* __r
 // ---------------------------------------------------------------- FP32, register-blocked (h > kHeadMM)
 // Per parity p the block is G_p[a][m] = Lam'_{m-a} Lam'_{m+a+p} (a <= m; k = p + 2a,
 // n = p + 2m).  A warp task takes 256 consecutive outputs of one parity (8 per
-// lane: o_i = o0 + i) and one chunk of 512 reduction indices r:
+// lane: o_i = o0 + i) and one chunk of rbc reduction indices r (a multiple of 8
+// chosen per plan, head_rb_tasks):
 //   forward     out a = o_i, reduction m = r:  term Lam'[r - o_i] Lam'[r + o_i + p] x_{p+2r}
 //   transposed  out m = o_i, reduction a = r:  term Lam'[o_i - r] Lam'[o_i + r + p] y_{p+2r}
 // (y_0 halved for p = 0).  From one r to the next the first factors of a lane's
@@ -370,12 +371,11 @@ __global__ void __launch_bounds__(256) k_head_mm(const T* __restrict__ x, T* __r
 // chunk order in double.
 constexpr int RB = 8;
 constexpr int RBW = 32 * RB;
-constexpr int RBC = 512;
 
 template <bool TRANS>
 __global__ void __launch_bounds__(256) k_head_rb(const float* __restrict__ x, const float* __restrict__ lamp,
                                                  const int4* __restrict__ tasks, int ntask, int64_t N, int64_t h,
-                                                 double* __restrict__ part, int64_t part_n) {
+                                                 int rbc, double* __restrict__ part, int64_t part_n) {
   const int task = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5);
   if (task >= ntask) return;  // whole warp
   const int4 tk = tasks[task];
@@ -383,14 +383,14 @@ __global__ void __launch_bounds__(256) k_head_rb(const float* __restrict__ x, co
   const int lane = threadIdx.x & 31;
   const int64_t Hp = (h - par + 1) / 2;
   const int64_t H0 = (h + 1) / 2;
-  const int64_t nch = (H0 + RBC - 1) / RBC;
+  const int64_t nch = (H0 + rbc - 1) / rbc;
   x += (int64_t)blockIdx.y * N;
   const float* __restrict__ lam = lamp + kHeadPad;
   const int64_t oB = (int64_t)tk.y * RBW;
   const int64_t o0 = oB + lane * RB;
-  const int64_t r0 = (int64_t)tk.z * RBC;
+  const int64_t r0 = (int64_t)tk.z * rbc;
   const int64_t rend = TRANS ? min(Hp, (int64_t)(tk.y + 1) * RBW) : Hp;
-  const int64_t r1 = min(r0 + RBC, rend);
+  const int64_t r1 = min(r0 + rbc, rend);
   // T[i] = Lam'[r - o_i] (forward) or Lam'[o_i - r] (transposed), H[i] = Lam'[r + o_i + p]
   float T[RB], H[RB], acc[RB], cmp[RB];
 #pragma unroll
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(256) k_head_rb(const float* __restrict__ x, co
 // out index q (k forward, n transposed), parity q & 1, position o = q >> 1: the
 // chunk sums of its task column in ascending chunk order
 template <bool TRANS>
-__global__ void k_head_rb_reduce(const double* __restrict__ part, int64_t part_n, float* __restrict__ out,
+__global__ void k_head_rb_reduce(const double* __restrict__ part, int64_t part_n, int rbc, float* __restrict__ out,
                                  int64_t N, int64_t h, int scale_s, double* __restrict__ hout, int64_t hs) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= h) return;
@@ -455,12 +455,12 @@ __global__ void k_head_rb_reduce(const double* __restrict__ part, int64_t part_n
   const int64_t o = q >> 1;
   const int64_t Hp = (h - par + 1) / 2;
   const int64_t H0 = (h + 1) / 2;
-  const int64_t nch = (H0 + RBC - 1) / RBC;
+  const int64_t nch = (H0 + rbc - 1) / rbc;
   const int64_t blk = o / RBW;
   // forward: chunks from the one holding the block's first output to the last;
   // transposed: chunks up to the one holding the block's last reduction index
-  const int64_t c0 = TRANS ? 0 : (blk * RBW) / RBC;
-  const int64_t c1 = TRANS ? (min(Hp, (blk + 1) * RBW) - 1) / RBC + 1 : (Hp + RBC - 1) / RBC;
+  const int64_t c0 = TRANS ? 0 : (blk * RBW) / rbc;
+  const int64_t c1 = TRANS ? (min(Hp, (blk + 1) * RBW) - 1) / rbc + 1 : (Hp + rbc - 1) / rbc;
   const double* src = part + (int64_t)blockIdx.y * part_n + (int64_t)par * nch * H0 + o;
   double s = 0.0;
   for (int64_t c = c0; c < c1; ++c) s += src[c * H0];
@@ -474,22 +474,35 @@ __global__ void k_head_rb_reduce(const double* __restrict__ part, int64_t part_n
 
 }  // namespace
 
-void head_rb_tasks(int64_t h, std::vector<int4>& fwd, std::vector<int4>& trn, int64_t* part_n) {
-  fwd.clear();
-  trn.clear();
-  const int64_t H0 = (h + 1) / 2;
-  const int64_t nch = (H0 + RBC - 1) / RBC;
-  for (int par = 0; par < 2; ++par) {
-    const int64_t Hp = (h - par + 1) / 2;
-    const int64_t nblk = (Hp + RBW - 1) / RBW;
-    const int64_t nchp = (Hp + RBC - 1) / RBC;
-    for (int64_t b = 0; b < nblk; ++b) {
-      for (int64_t c = (b * RBW) / RBC; c < nchp; ++c) fwd.push_back(make_int4(par, (int)b, (int)c, 0));
-      const int64_t last = std::min(Hp, (b + 1) * RBW) - 1;
-      for (int64_t c = 0; c <= last / RBC; ++c) trn.push_back(make_int4(par, (int)b, (int)c, 0));
-    }
+void head_rb_tasks(int64_t h, std::vector<int4>& fwd, std::vector<int4>& trn, int64_t* part_n, int* rbc_out) {
+  // the longest chunk (fewest partial sums) that still gives every SM two CTAs of
+  // 8 warp tasks in each direction, down to 32 reduction indices
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    sms = 152;
   }
+  const int64_t H0 = (h + 1) / 2;
+  int rbc = 512;
+  for (;; rbc /= 2) {
+    fwd.clear();
+    trn.clear();
+    for (int par = 0; par < 2; ++par) {
+      const int64_t Hp = (h - par + 1) / 2;
+      const int64_t nblk = (Hp + RBW - 1) / RBW;
+      const int64_t nchp = (Hp + rbc - 1) / rbc;
+      for (int64_t b = 0; b < nblk; ++b) {
+        for (int64_t c = (b * RBW) / rbc; c < nchp; ++c) fwd.push_back(make_int4(par, (int)b, (int)c, 0));
+        const int64_t last = std::min(Hp, (b + 1) * RBW) - 1;
+        for (int64_t c = 0; c <= last / rbc; ++c) trn.push_back(make_int4(par, (int)b, (int)c, 0));
+      }
+    }
+    if (rbc <= 32 || (int64_t)fwd.size() >= 16 * (int64_t)sms) break;
+  }
+  const int64_t nch = (H0 + rbc - 1) / rbc;
   *part_n = 2 * nch * H0;
+  *rbc_out = rbc;
 }
 
 int launch_head_tab_init(Plan& P) {
@@ -523,10 +536,10 @@ int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb, double* hout) {
   if constexpr (sizeof(T) == 4) {
     if (P.head_lamp) {
       k_head_rb<false><<<dim3((unsigned)((P.head_ntask_f + 7) / 8), (unsigned)nb), 256, 0, P.stream>>>(
-          c, P.head_lamp, P.head_tasks, P.head_ntask_f, P.p.N, h, P.head_part, P.head_part_n);
+          c, P.head_lamp, P.head_tasks, P.head_ntask_f, P.p.N, h, P.head_rbc, P.head_part, P.head_part_n);
       launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 4.0 * 2.0 * (double)h);
       k_head_rb_reduce<false><<<dim3((unsigned)((h + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
-          P.head_part, P.head_part_n, chat, P.p.N, h, 0, hout, P.p.N * (int64_t)sizeof(T) / 8);
+          P.head_part, P.head_part_n, P.head_rbc, chat, P.p.N, h, 0, hout, P.p.N * (int64_t)sizeof(T) / 8);
       launched(P, "head_reduce", 0.0, (double)nb * 8.0 * (double)P.head_part_n);
       return check_launch();
     }
@@ -561,10 +574,11 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* 
   if constexpr (sizeof(T) == 4) {
     if (P.head_lamp) {
       k_head_rb<true><<<dim3((unsigned)((P.head_ntask_t + 7) / 8), (unsigned)nb), 256, 0, P.stream>>>(
-          y, P.head_lamp, P.head_tasks + P.head_ntask_f, P.head_ntask_t, P.p.N, h, P.head_part, P.head_part_n);
+          y, P.head_lamp, P.head_tasks + P.head_ntask_f, P.head_ntask_t, P.p.N, h, P.head_rbc, P.head_part,
+          P.head_part_n);
       launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 4.0 * 2.0 * (double)h);
       k_head_rb_reduce<true><<<dim3((unsigned)((h + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
-          P.head_part, P.head_part_n, out, P.p.N, h, scale_s, hout, P.p.N * (int64_t)sizeof(T) / 8);
+          P.head_part, P.head_part_n, P.head_rbc, out, P.p.N, h, scale_s, hout, P.p.N * (int64_t)sizeof(T) / 8);
       launched(P, "head_reduce", 0.0, (double)nb * 8.0 * (double)P.head_part_n);
       return check_launch();
     }

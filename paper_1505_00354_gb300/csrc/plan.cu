@@ -797,7 +797,8 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
   const bool head_rb = prec == GBDLT_FP32 && prm.fast && prm.head > kHeadMM;
   std::vector<int4> rb_fwd, rb_trn;
   int64_t rb_part = 0;
-  if (head_rb) head_rb_tasks(prm.head, rb_fwd, rb_trn, &rb_part);
+  int rb_chunk = 0;
+  if (head_rb) head_rb_tasks(prm.head, rb_fwd, rb_trn, &rb_part, &rb_chunk);
   {
     // batch capacity: as many vectors per pass as fit in ~512 MB of workspace
     const double per_item = 2.0 * P->nfft_max * N * cs + 2.0 * nfft32 * N * 8.0 + 2.0 * nfftff * N * 16.0 +
@@ -941,6 +942,7 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     P->head_ntask_t = (int)rb_trn.size();
     P->head_part = (double*)(base + o_rbp);
     P->head_part_n = rb_part;
+    P->head_rbc = rb_chunk;
   }
   auto place_layout = [&](RecLayout& L, const LayoutOff& o) {
     L.cut = (int32_t*)(base + o.cut);
