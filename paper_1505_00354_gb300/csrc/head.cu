@@ -445,31 +445,44 @@ __global__ void __launch_bounds__(256) k_head_rb(const float* __restrict__ x, co
 }
 
 // out index q (k forward, n transposed), parity q & 1, position o = q >> 1: the
-// chunk sums of its task column in ascending chunk order
+// chunk sums of its task column, in double.  A CTA takes 32 outputs; its 8 rows
+// of threads sum the chunks c = c0 + row, c0 + row + 8, ... in ascending order,
+// and the 8 row sums are added in row order, so the result is the same on every
+// run and for any batch.
 template <bool TRANS>
-__global__ void k_head_rb_reduce(const double* __restrict__ part, int64_t part_n, int rbc, float* __restrict__ out,
-                                 int64_t N, int64_t h, int scale_s, double* __restrict__ hout, int64_t hs) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= h) return;
-  const int par = (int)(q & 1);
-  const int64_t o = q >> 1;
-  const int64_t Hp = (h - par + 1) / 2;
-  const int64_t H0 = (h + 1) / 2;
-  const int64_t nch = (H0 + rbc - 1) / rbc;
-  const int64_t blk = o / RBW;
-  // forward: chunks from the one holding the block's first output to the last;
-  // transposed: chunks up to the one holding the block's last reduction index
-  const int64_t c0 = TRANS ? 0 : (blk * RBW) / rbc;
-  const int64_t c1 = TRANS ? (min(Hp, (blk + 1) * RBW) - 1) / rbc + 1 : (Hp + rbc - 1) / rbc;
-  const double* src = part + (int64_t)blockIdx.y * part_n + (int64_t)par * nch * H0 + o;
+__global__ void __launch_bounds__(256) k_head_rb_reduce(const double* __restrict__ part, int64_t part_n, int rbc,
+                                                        float* __restrict__ out, int64_t N, int64_t h, int scale_s,
+                                                        double* __restrict__ hout, int64_t hs) {
+  __shared__ double red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 32 + tx;
   double s = 0.0;
-  for (int64_t c = c0; c < c1; ++c) s += src[c * H0];
-  if (!TRANS && q == 0) s *= 0.5;
-  if (TRANS && scale_s) s *= (double)q + 0.5;
+  if (q < h) {
+    const int par = (int)(q & 1);
+    const int64_t o = q >> 1;
+    const int64_t Hp = (h - par + 1) / 2;
+    const int64_t H0 = (h + 1) / 2;
+    const int64_t nch = (H0 + rbc - 1) / rbc;
+    const int64_t blk = o / RBW;
+    // forward: chunks from the one holding the block's first output to the last;
+    // transposed: chunks up to the one holding the block's last reduction index
+    const int64_t c0 = TRANS ? 0 : (blk * RBW) / rbc;
+    const int64_t c1 = TRANS ? (min(Hp, (blk + 1) * RBW) - 1) / rbc + 1 : (Hp + rbc - 1) / rbc;
+    const double* src = part + (int64_t)blockIdx.y * part_n + (int64_t)par * nch * H0 + o;
+    for (int64_t c = c0 + ty; c < c1; c += 8) s += src[c * H0];
+  }
+  red[ty][tx] = s;
+  __syncthreads();
+  if (ty != 0 || q >= h) return;
+  double t = 0.0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) t += red[r][tx];
+  if (!TRANS && q == 0) t *= 0.5;
+  if (TRANS && scale_s) t *= (double)q + 0.5;
   if (hout)
-    hout[(int64_t)blockIdx.y * hs + q] = s;
+    hout[(int64_t)blockIdx.y * hs + q] = t;
   else
-    out[(int64_t)blockIdx.y * N + q] = (float)((double)out[(int64_t)blockIdx.y * N + q] + s);
+    out[(int64_t)blockIdx.y * N + q] = (float)((double)out[(int64_t)blockIdx.y * N + q] + t);
 }
 
 }  // namespace
@@ -538,7 +551,7 @@ int launch_head_fwd(Plan& P, const T* c, T* chat, int64_t nb, double* hout) {
       k_head_rb<false><<<dim3((unsigned)((P.head_ntask_f + 7) / 8), (unsigned)nb), 256, 0, P.stream>>>(
           c, P.head_lamp, P.head_tasks, P.head_ntask_f, P.p.N, h, P.head_rbc, P.head_part, P.head_part_n);
       launched(P, "head", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 4.0 * 2.0 * (double)h);
-      k_head_rb_reduce<false><<<dim3((unsigned)((h + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
+      k_head_rb_reduce<false><<<dim3((unsigned)((h + 31) / 32), (unsigned)nb), 256, 0, P.stream>>>(
           P.head_part, P.head_part_n, P.head_rbc, chat, P.p.N, h, 0, hout, P.p.N * (int64_t)sizeof(T) / 8);
       launched(P, "head_reduce", 0.0, (double)nb * 8.0 * (double)P.head_part_n);
       return check_launch();
@@ -577,7 +590,7 @@ int launch_head_t(Plan& P, const T* y, T* out, int scale_s, int64_t nb, double* 
           y, P.head_lamp, P.head_tasks + P.head_ntask_f, P.head_ntask_t, P.p.N, h, P.head_rbc, P.head_part,
           P.head_part_n);
       launched(P, "head_t", (double)nb * 0.5 * (double)h * (double)h, (double)nb * 4.0 * 2.0 * (double)h);
-      k_head_rb_reduce<true><<<dim3((unsigned)((h + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(
+      k_head_rb_reduce<true><<<dim3((unsigned)((h + 31) / 32), (unsigned)nb), 256, 0, P.stream>>>(
           P.head_part, P.head_part_n, P.head_rbc, out, P.p.N, h, scale_s, hout, P.p.N * (int64_t)sizeof(T) / 8);
       launched(P, "head_reduce", 0.0, (double)nb * 8.0 * (double)P.head_part_n);
       return check_launch();
