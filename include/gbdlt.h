@@ -169,6 +169,14 @@ int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
  * A staged copy that has not landed after about two seconds makes the next
  * gbdlt_plan_sync return GBDLT_ERR_CUDA. */
 int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable);
+/* FP64 plans: run the FP64 and the float-float FFTs of each Taylor stage in one
+ * pair of launches whose thread blocks alternate between the two kinds, so that
+ * an SM holds one of each and both of GB300's FP64 and FP32 pipes work (enable
+ * = 1, the default), or as two launches on two streams (0).  The butterflies are
+ * the same either way, so results are bitwise identical; the choice only changes
+ * speed.  Clears the plan's replayed graphs.  GBDLT_ERR_INVALID_ARG for other
+ * values. */
+int gbdlt_plan_set_fft_mix(gbdlt_plan plan, int enable);
 /* SM clock cycles a staged FFT pass of this plan waits for a tile copy before
  * it gives up (0 <= sm_cycles <= 2^32; default 2^32, about two seconds).  A pass
  * that gives up records it (the next gbdlt_plan_sync returns GBDLT_ERR_CUDA and

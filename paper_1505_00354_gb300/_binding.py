@@ -84,7 +84,7 @@ class Params(ctypes.Structure):
 ENTRY_POINTS = (
     "gbdlt_plan_params", "gbdlt_plan_params_ex", "gbdlt_plan_create", "gbdlt_plan_create_ex",
     "gbdlt_plan_destroy", "gbdlt_plan_set_stream",
-    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_plan_set_node_iterations", "gbdlt_plan_set_fft_staging", "gbdlt_plan_set_wait_limit",
+    "gbdlt_plan_sync", "gbdlt_plan_get_params", "gbdlt_plan_set_node_iterations", "gbdlt_plan_set_fft_staging", "gbdlt_plan_set_fft_mix", "gbdlt_plan_set_wait_limit",
     "gbdlt_legpts", "gbdlt_legpts_noalloc", "gbdlt_leg2cheb",
     "gbdlt_leg2cheb_t", "gbdlt_chebeval", "gbdlt_chebeval_t", "gbdlt_dlt", "gbdlt_dlt_t",
     "gbdlt_idlt", "gbdlt_idlt_t", "gbdlt_plan_profile", "gbdlt_plan_profile_read",
@@ -116,6 +116,7 @@ def lib():
         L.gbdlt_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
         L.gbdlt_plan_set_node_iterations.argtypes = [vp, i32]
         L.gbdlt_plan_set_fft_staging.argtypes = [vp, i32]
+        L.gbdlt_plan_set_fft_mix.argtypes = [vp, i32]
         L.gbdlt_plan_set_wait_limit.argtypes = [vp, i64]
         L.gbdlt_legpts.argtypes = [vp, vp, vp, vp, vp]
         L.gbdlt_legpts_noalloc.argtypes = [i64, vp, vp, vp, vp, vp]
@@ -239,6 +240,10 @@ class Plan:
     def set_fft_staging(self, enable: bool):
         """FP32 FFT passes staged by the tensor memory accelerator (default) or not."""
         _check(lib().gbdlt_plan_set_fft_staging(self._h, 1 if enable else 0), "set_fft_staging")
+
+    def set_fft_mix(self, enable: bool):
+        """FP64 plans: the FP64 and float-float Taylor FFTs in one mixed launch pair (default) or two streams."""
+        _check(lib().gbdlt_plan_set_fft_mix(self._h, 1 if enable else 0), "set_fft_mix")
 
     def set_wait_limit(self, sm_cycles: int):
         """SM cycles a staged FFT pass waits for a tile copy (failure-path hook; default 2^32)."""

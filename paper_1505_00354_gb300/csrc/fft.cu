@@ -432,16 +432,16 @@ __global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
   for (int i = threadIdx.x; i < tot; i += FFT_THREADS) g[i] = sm[sidx(i >> logL, LP, i & (L - 1))];
 }
 
+// column pass of tile bx (C columns) of launch-local vector by
 template <typename T, int DIR>
-__global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
-    k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int logL1, int L2, int C, int logC,
-               const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
-               const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf,
-               VecMap vm) {
-  extern __shared__ unsigned char smraw[];
+__device__ __forceinline__ void fft_cols_tile(unsigned char* smraw, C2<T>* __restrict__ data, int64_t N, int L1,
+                                              int logL1, int L2, int C, int logC,
+                                              const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
+                                              const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull,
+                                              const double2* __restrict__ lf, VecMap vm, int bx, int64_t by) {
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
-  const int c0 = blockIdx.x * C;
-  C2<T>* g = data + vec_of(vm, blockIdx.y) * N;
+  const int c0 = bx * C;
+  C2<T>* g = data + vec_of(vm, by) * N;
   const int LP = line_pitch(L1);
   const int tot = L1 * C;
   load_tile<T>(sm, tot, [&](int i) { return sidx(i & (C - 1), LP, i >> logC); },
@@ -464,13 +464,24 @@ __global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
-    k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
-               int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096,
-               const double2* __restrict__ lf, VecMap vm) {
+    k_fft_cols(C2<T>* __restrict__ data, int64_t N, int L1, int logL1, int L2, int C, int logC,
+               const C2<T>* __restrict__ tw4096, const C2<T>* __restrict__ thi,
+               const C2<T>* __restrict__ tlo, const C2<T>* __restrict__ tfull, const double2* __restrict__ lf,
+               VecMap vm) {
   extern __shared__ unsigned char smraw[];
+  fft_cols_tile<T, DIR>(smraw, data, N, L1, logL1, L2, C, logC, tw4096, thi, tlo, tfull, lf, vm, (int)blockIdx.x,
+                        (int64_t)blockIdx.y);
+}
+
+// row pass of tile bx (C2n rows) of launch-local vector by
+template <typename T, int DIR>
+__device__ __forceinline__ void fft_rows_tile(unsigned char* smraw, const C2<T>* __restrict__ in,
+                                              C2<T>* __restrict__ out, int64_t N, int L1, int L2, int logL2,
+                                              int C2n, int logC2, const C2<T>* __restrict__ tw4096,
+                                              const double2* __restrict__ lf, VecMap vm, int bx, int64_t by) {
   C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
-  const int r0 = blockIdx.x * C2n;
-  const int64_t v = vec_of(vm, blockIdx.y);
+  const int r0 = bx * C2n;
+  const int64_t v = vec_of(vm, by);
   const C2<T>* g = in + v * N;
   C2<T>* o = out + v * N;
   const int LP = line_pitch(L2);
@@ -483,6 +494,71 @@ __global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
     const int k2 = i >> logC2, line = i & (C2n - 1);
     o[(int64_t)(r0 + line) + (int64_t)L1 * k2] = sm[sidx(line, LP, k2)];
   }
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(FFT_THREADS, is_f32<T> ? 4 : 2)
+    k_fft_rows(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, int64_t N, int L1, int L2,
+               int logL2, int C2n, int logC2, const C2<T>* __restrict__ tw4096,
+               const double2* __restrict__ lf, VecMap vm) {
+  extern __shared__ unsigned char smraw[];
+  fft_rows_tile<T, DIR>(smraw, in, out, N, L1, L2, logL2, C2n, logC2, tw4096, lf, vm, (int)blockIdx.x,
+                        (int64_t)blockIdx.y);
+}
+
+// Mixed passes: the FP64 and the float-float vectors of one stage in one launch.
+// On GB300 the FP64 and FP32 pipes are separate; a CTA of each kind on an SM
+// (the two kinds use the same registers and shared memory per CTA) keeps both
+// busy, where two launches on two streams run mostly one after the other (the
+// first launch's CTAs fill every SM).  CTA b takes, while both kinds have
+// tiles left, an FP64 tile for even b and a float-float tile for odd b; then the
+// tiles of the kind with more.  Tile t of a kind is column (row) block
+// t mod nx of launch-local vector t / nx.
+struct MixArgs {
+  C2<double>* a64;
+  C2<double>* b64;
+  ffc* aff;
+  ffc* bff;
+  int64_t n64, nff;  // tiles of each kind
+  VecMap vm64, vmff;
+};
+__device__ __forceinline__ bool mix_pick(const MixArgs& M, int64_t b, int64_t& t) {
+  const int64_t both = 2 * min(M.n64, M.nff);
+  if (b < both) {
+    t = b >> 1;
+    return (b & 1) == 0;
+  }
+  t = b - both / 2;
+  return M.n64 > M.nff;
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(FFT_THREADS, 2)
+    k_fft_cols_mix(MixArgs M, int64_t N, int L1, int logL1, int L2, int C, int logC, int nx,
+                   const double2* __restrict__ tw64, const double2* __restrict__ full64,
+                   const double2* __restrict__ lf, const ffc* __restrict__ twff, const ffc* __restrict__ fullff) {
+  extern __shared__ unsigned char smraw[];
+  int64_t t;
+  if (mix_pick(M, blockIdx.x, t))
+    fft_cols_tile<double, DIR>(smraw, M.a64, N, L1, logL1, L2, C, logC, tw64, nullptr, nullptr, full64, lf, M.vm64,
+                               (int)(t % nx), t / nx);
+  else
+    fft_cols_tile<ffd, DIR>(smraw, M.aff, N, L1, logL1, L2, C, logC, twff, nullptr, nullptr, fullff, nullptr,
+                            M.vmff, (int)(t % nx), t / nx);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(FFT_THREADS, 2)
+    k_fft_rows_mix(MixArgs M, int64_t N, int L1, int L2, int logL2, int C2n, int logC2, int nx,
+                   const double2* __restrict__ tw64, const double2* __restrict__ lf, const ffc* __restrict__ twff) {
+  extern __shared__ unsigned char smraw[];
+  int64_t t;
+  if (mix_pick(M, blockIdx.x, t))
+    fft_rows_tile<double, DIR>(smraw, M.a64, M.b64, N, L1, L2, logL2, C2n, logC2, tw64, lf, M.vm64,
+                               (int)(t % nx), t / nx);
+  else
+    fft_rows_tile<ffd, DIR>(smraw, M.aff, M.bff, N, L1, L2, logL2, C2n, logC2, twff, nullptr, M.vmff,
+                            (int)(t % nx), t / nx);
 }
 
 // ---------------------------------------------------------------- pruned passes
@@ -1363,6 +1439,58 @@ static void* four_step(Plan& P, void* a, void* b, int64_t nb, int64_t per_item, 
     launched(P, kname<T>("fft_rows", "fft32_rows", "fftff_rows"), 5.0 * lL2 * (double)N * nb * per_item, 2.0 * (double)nb * per_item * N * sizeof(CT));
   }
   return b;
+}
+
+// The FP64 and float-float vectors of one stage (both of length N > 4096, the
+// four-step sizes) through the mixed passes; results in b64 and bff.
+template <int DIR>
+static void fft_mix_dir(Plan& P, void* a64, void* b64, int64_t nv64, void* aff, void* bff, int64_t nvff) {
+  static bool attr = false;
+  const int smax = (int)(FFT_SMEM_ELEMS * sizeof(C2<double>));
+  if (!attr) {
+    cudaFuncSetAttribute(k_fft_cols_mix<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_fft_rows_mix<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    attr = true;
+  }
+  const int64_t N = P.p.N;
+  int p = 0;
+  while ((1ll << p) < N) ++p;
+  const int L1 = 1 << (p / 2);
+  const int L2 = (int)(N / L1);
+  const int C = FFT_TILE / L1;
+  const int C2n = FFT_TILE / L2;
+  const int lL1 = p / 2, lL2 = p - p / 2, lC = 12 - lL1, lC2 = 12 - lL2;
+  const TwT<double> tw = tw_tables(P, double());
+  const double2* lfd = tw.lf ? tw.lf + (DIR > 0 ? 0 : 2 * 4096) : nullptr;
+  MixArgs M;
+  M.a64 = (C2<double>*)a64;
+  M.b64 = (C2<double>*)b64;
+  M.aff = (ffc*)aff;
+  M.bff = (ffc*)bff;
+  M.vm64 = VecMap{0, std::max<int64_t>(nv64, 1), std::max<int64_t>(nv64, 1)};
+  M.vmff = VecMap{0, std::max<int64_t>(nvff, 1), std::max<int64_t>(nvff, 1)};
+  const size_t smc = (size_t)C * line_pitch(L1) * sizeof(C2<double>);
+  const size_t smr = (size_t)C2n * line_pitch(L2) * sizeof(C2<double>);
+  const int nxc = L2 / C, nxr = L1 / C2n;
+  M.n64 = (int64_t)nxc * nv64;
+  M.nff = (int64_t)nxc * nvff;
+  k_fft_cols_mix<DIR><<<(unsigned)(M.n64 + M.nff), FFT_THREADS, smc, P.stream>>>(
+      M, N, L1, lL1, L2, C, lC, nxc, tw.t4096, tw.full, lfd, P.tw4096_ff, P.twfull_ff);
+  launched(P, "fftmix_cols", (5.0 * lL1 + 6.0) * (double)N * (double)(nv64 + nvff),
+           2.0 * (double)(nv64 + nvff) * N * 16.0);
+  M.n64 = (int64_t)nxr * nv64;
+  M.nff = (int64_t)nxr * nvff;
+  k_fft_rows_mix<DIR><<<(unsigned)(M.n64 + M.nff), FFT_THREADS, smr, P.stream>>>(M, N, L1, L2, lL2, C2n, lC2,
+                                                                                  nxr, tw.t4096, lfd,
+                                                                                  P.tw4096_ff);
+  launched(P, "fftmix_rows", 5.0 * lL2 * (double)N * (double)(nv64 + nvff), 2.0 * (double)(nv64 + nvff) * N * 16.0);
+}
+
+void launch_fft_mix(Plan& P, void* a64, void* b64, int64_t nv64, void* aff, void* bff, int64_t nvff, int dir) {
+  if (dir > 0)
+    fft_mix_dir<1>(P, a64, b64, nv64, aff, bff, nvff);
+  else
+    fft_mix_dir<-1>(P, a64, b64, nv64, aff, bff, nvff);
 }
 
 template <typename T>

@@ -363,6 +363,9 @@ struct Plan {
   // plans, whose FP32 transforms run on the side stream beside FP64 kernels and
   // there leave more room to them as ordinary (non-persistent) grids
   bool no_tma = false;
+  // FP64 plans: the FP64 and float-float FFTs of the Taylor stages in one mixed
+  // pair of launches (fft.cu, launch_fft_mix) instead of two streams
+  bool fft_mix = true;
   long long tma_wait = 1ll << 32;  // SM cycles a staged pass waits for a tile copy
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;
@@ -489,6 +492,10 @@ int launch_dtheta(Plan& P, double* out);  // out_k = t_k / N
 // Input in `a`; result in `a` when N <= 4096, else in `b` (returned pointer).
 template <typename T>
 void* launch_fft(Plan& P, void* a, void* b, int64_t nvec, int dir);
+// the FP64 vectors a64 (nv64) and the float-float vectors aff (nvff) of one
+// stage, both of length N > 4096, in one pair of launches whose CTAs alternate
+// between the two kinds (separate pipes on GB300); results in b64 and bff
+void launch_fft_mix(Plan& P, void* a64, void* b64, int64_t nv64, void* aff, void* bff, int64_t nvff, int dir);
 // the K*M band FFTs of nb items (vectors [item][band][term]); bands
 // [0, prune_bands) read only the windows of their rows (transposed = 0: forward
 // chain, outputs pruned; 1: transposed chain, inputs pruned)

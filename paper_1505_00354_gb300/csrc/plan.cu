@@ -1210,6 +1210,28 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
   return head_side ? GBDLT_OK : launch_head_fwd<T>(P, c, chat, nb);
 }
 
+// The FP64 and float-float FFTs of a Taylor stage (inputs in bufA / bufAff):
+// one mixed pair of launches when both kinds have vectors at a four-step size
+// (FP64 plans, fft_mix on), else the float-float ones on the side stream beside
+// the FP64 ones.  Results: *y (the FP64 buffer the passes end in), *yff.
+template <typename T>
+int taylor_ffts(Plan& P, int64_t n64, int64_t nff, int dir, const void** y, const ffc** yff) {
+  *yff = nullptr;
+  if constexpr (is_f64<T>) {
+    if (P.fft_mix && nff > 0 && n64 > 0 && P.p.N > 4096) {
+      launch_fft_mix(P, P.bufA, P.bufB, n64, P.bufAff, P.bufBff, nff, dir);
+      *y = P.bufB;
+      *yff = (const ffc*)P.bufBff;
+      return check_launch();
+    }
+  }
+  Side sd(P, nff > 0);
+  *y = launch_fft<T>(P, P.bufA, P.bufB, n64, dir);
+  sd.enter();
+  if (nff > 0) *yff = (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nff, dir);
+  return sd.join();
+}
+
 // forward declaration (defined below)
 template <typename T>
 int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb);
@@ -1244,12 +1266,10 @@ int run_taylor(Plan& P, const T* chat, const T* v, T* f, int inc0, int64_t nb) {
   const C2<T>* Y = nullptr;
   const ffc* Yff = nullptr;
   {
-    Side sd(P, Uff != nullptr);
-    Y = (const C2<T>*)launch_fft<T>(P, P.bufA, P.bufB, nb * P64, +1);
-    sd.enter();
-    Yff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), +1) : nullptr;
-    st = sd.join();
+    const void* y = nullptr;
+    st = taylor_ffts<T>(P, nb * P64, Uff ? nb * (npair - P64) : 0, +1, &y, &Yff);
     if (st) return st;
+    Y = (const C2<T>*)y;
   }
   return launch_tay_epi<T>(P, Y, Yff, v, f, inc0, npair, nb);
 }
@@ -1278,14 +1298,8 @@ int run_transposed(Plan& P, const T* g, T* out, int use_w, int scale_s, int64_t 
     if (st) return st;
     const void* F = nullptr;
     const ffc* Fff = nullptr;
-    {
-      Side sd(P, Uff != nullptr);
-      F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
-      sd.enter();
-      Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
-      st = sd.join();
-      if (st) return st;
-    }
+    st = taylor_ffts<T>(P, nb * P64, Uff ? nb * (npair - P64) : 0, -1, &F, &Fff);
+    if (st) return st;
     void* q = other(P, F);
     st = launch_tayt_epi<T>(P, (const C2<T>*)F, Fff, (C2<T>*)q, head > 0 ? uhead : nullptr, inc0, npair, nb,
                             head);
@@ -1380,14 +1394,8 @@ int run_chebeval_t(Plan& P, const T* g, T* out, int64_t nb) {
   if (st) return st;
   const void* F = nullptr;
   const ffc* Fff = nullptr;
-  {
-    Side sd(P, Uff != nullptr);
-    F = launch_fft<T>(P, P.bufA, P.bufB, nb * P64, -1);
-    sd.enter();
-    Fff = Uff ? (const ffc*)launch_fft<ffd>(P, P.bufAff, P.bufBff, nb * (npair - P64), -1) : nullptr;
-    st = sd.join();
-    if (st) return st;
-  }
+  st = taylor_ffts<T>(P, nb * P64, Uff ? nb * (npair - P64) : 0, -1, &F, &Fff);
+  if (st) return st;
   return launch_tayt_epi<T>(P, (const C2<T>*)F, Fff, nullptr, out, 1, npair, nb);
 }
 
@@ -1891,6 +1899,20 @@ int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable) {
   }
   P->no_tma = enable == 0;
   if (P->inner) P->inner->no_tma = enable == 0;
+  return GBDLT_OK;
+}
+
+int gbdlt_plan_set_fft_mix(gbdlt_plan plan, int enable) {
+  if (!plan || (enable != 0 && enable != 1)) return GBDLT_ERR_INVALID_ARG;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (P->fft_mix == (enable != 0)) return GBDLT_OK;
+  // replayed chains hold the launches they were captured with
+  if (P->graphs) {
+    if (cudaStreamSynchronize(P->graphs->s) != cudaSuccess) return GBDLT_ERR_CUDA;
+    free_graphs(P);
+  }
+  P->fft_mix = enable != 0;
+  if (P->inner) P->inner->fft_mix = enable != 0;
   return GBDLT_OK;
 }
 

@@ -514,3 +514,18 @@ def test_fp64_rate_probe(gb):
     r = gb.fp64_fma_rate()
     print(f"FP64 FMA probe: {r / 1e12:.4f} TFLOP/s ({r / peak:.3f} of {peak / 1e12:.4f} derived)")
     assert 0.3 * peak < r < 1.1 * peak
+
+
+@pytest.mark.parametrize("N", [2**13, 2**16, 2**20])
+def test_fft_mix_bitwise(gb, N):
+    """The mixed FP64 / float-float Taylor FFT launches give bitwise the results
+    of the two-stream launches (the same butterflies on the same data)."""
+    import paper_1505_00354_gb300.inputs as inp
+    p = gb.Plan(N, method=gb.METHOD_FAST)
+    x = dev(np.stack([inp.coeffs(N, 60, 1.0), inp.coeffs(N, 61)]))
+    ops = ("dlt", "idlt", "dlt_t", "idlt_t", "chebeval", "chebeval_t")
+    p.set_fft_mix(False)
+    ref = {op: getattr(p, op)(x).clone() for op in ops}
+    p.set_fft_mix(True)
+    for op in ops:
+        assert torch.equal(getattr(p, op)(x), ref[op]), op
