@@ -60,13 +60,18 @@ HBM_FALLBACK_GBS = 6800.0
 # dram__bytes_write.sum) and the hash of the kernel sources it was taken with;
 # a traffic figure is reported only while the sources are unchanged.
 TRAFFIC = {
-    # an ncu capture of the six launches of k_fft_cols<double> in one
-    # FP64 step at N = 2^20 (14 vectors of 2^20 complex doubles) moved 330.5 MB of
-    # DRAM traffic against 2 x 14 x 2^20 x 16 B = 469.8 MB algorithmic (part of
-    # each launch's input is still in the L2 from the kernel before it); valid
-    # while the sources the kernel is built from hash to "src"
-    "fft_cols": {"dram_per_algorithmic_byte": 330.462208 / 469.762048,
-                 "files": ("fft.cu", ("gbdlt_internal.cuh", "// plan")), "src": "eda05ee551a6d491"},
+    # an ncu capture (dram__bytes_read/write.sum, one pass) of the launches of one
+    # FP64 step at N = 2^20, valid while the sources the kernel is built from hash
+    # to "src":
+    # k_fft_cols<double>: 4 launches, 8 vectors of 2^20 complex doubles, 200.9 MB
+    # of DRAM traffic against 2 x 8 x 2^20 x 16 B = 268.4 MB algorithmic (part of
+    # each launch's input is still in the L2 from the kernel before it)
+    "fft_cols": {"dram_per_algorithmic_byte": 200.924416 / 268.435456,
+                 "files": ("fft.cu", ("gbdlt_internal.cuh", "// plan")), "src": "f193e2e2f2413596"},
+    # k_rec_t<double>: 20.07 MB per launch against 21.06 MB algorithmic (z once,
+    # the segment states and the block partials)
+    "rec_t": {"dram_per_algorithmic_byte": 20.06656 / 21.0636,
+              "files": ("rec.cu", ("gbdlt_internal.cuh", "// plan")), "src": "a643d8402d287f9a"},
 }
 
 
