@@ -143,7 +143,7 @@ def job_rate(world, transforms_per_rank: float, ms_this_rank: float) -> float:
 # clocks during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi sampling every 100 ms; only the samples taken between mark()
+    """nvidia-smi sampling every 25 ms; only the samples taken between mark()
     and stop() (the timed region, host clock) are kept, plus the first one after
     it when the region is shorter than the sampling period."""
     FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -162,7 +162,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -190,7 +190,7 @@ class ClockSampler:
         self.t1 = time.time()
         if self.proc is None:
             return None
-        time.sleep(0.15)  # one more sample after the region
+        time.sleep(0.05)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)

@@ -171,12 +171,14 @@ int gbdlt_plan_set_node_iterations(gbdlt_plan plan, int max_iter);
 int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable);
 /* FP64 plans: run the FP64 and the float-float FFTs of each Taylor stage in one
  * pair of launches whose thread blocks alternate between the two kinds, so that
- * an SM holds one of each and both of GB300's FP64 and FP32 pipes work (enable
- * = 1, the default), or as two launches on two streams (0).  The butterflies are
- * the same either way, so results are bitwise identical; the choice only changes
- * speed.  Clears the plan's replayed graphs.  GBDLT_ERR_INVALID_ARG for other
- * values. */
-int gbdlt_plan_set_fft_mix(gbdlt_plan plan, int enable);
+ * an SM holds one of each and both of GB300's FP64 and FP32 pipes work, or as
+ * two launches on two streams.  mode 0: always two streams; 1 (the default):
+ * mixed launches at N >= 2^20 (the plan's grid length), where they are faster,
+ * two streams below; 2: mixed launches at every length above 4096.  The
+ * butterflies are the same either way, so results are bitwise identical; the
+ * choice only changes speed.  Clears the plan's replayed graphs.
+ * GBDLT_ERR_INVALID_ARG for other values. */
+int gbdlt_plan_set_fft_mix(gbdlt_plan plan, int mode);
 /* SM clock cycles a staged FFT pass of this plan waits for a tile copy before
  * it gives up (0 <= sm_cycles <= 2^32; default 2^32, about two seconds).  A pass
  * that gives up records it (the next gbdlt_plan_sync returns GBDLT_ERR_CUDA and

@@ -241,9 +241,10 @@ class Plan:
         """FP32 FFT passes staged by the tensor memory accelerator (default) or not."""
         _check(lib().gbdlt_plan_set_fft_staging(self._h, 1 if enable else 0), "set_fft_staging")
 
-    def set_fft_mix(self, enable: bool):
-        """FP64 plans: the FP64 and float-float Taylor FFTs in one mixed launch pair (default) or two streams."""
-        _check(lib().gbdlt_plan_set_fft_mix(self._h, 1 if enable else 0), "set_fft_mix")
+    def set_fft_mix(self, mode):
+        """FP64 plans, Taylor FFTs: 0 / False two streams; 1 / True (default) one mixed
+        FP64 / float-float launch pair at N >= 2^20; 2 mixed at every length above 4096."""
+        _check(lib().gbdlt_plan_set_fft_mix(self._h, int(mode)), "set_fft_mix")
 
     def set_wait_limit(self, sm_cycles: int):
         """SM cycles a staged FFT pass waits for a tile copy (failure-path hook; default 2^32)."""

@@ -234,6 +234,11 @@ struct Params {
 constexpr int64_t kDirectMax = 1 << 16;
 constexpr int64_t kDirectAuto = 256;
 // largest dense head block a fast plan uses (h^2/4 terms per transform)
+// Mixed FP64 / float-float Taylor FFT launches pay from this length up
+// (GB300, FP64 step: 5.56 -> 5.55 ms at 2^20, 26.7 -> 26.3 ms at 2^22); below
+// it the two-stream launches are faster (2^18: 1.76 against 1.88 ms), the mixed
+// grid being too short to keep two FP64 thread blocks on every SM.
+constexpr int64_t kFftMixMinN = 1 << 20;
 constexpr int64_t kHeadMax = 1 << 16;
 // largest head block whose products an FP64 plan stores (h^2/4 doubles: 2.1 GB)
 constexpr int64_t kHeadTabMax = 1 << 15;
@@ -364,8 +369,9 @@ struct Plan {
   // there leave more room to them as ordinary (non-persistent) grids
   bool no_tma = false;
   // FP64 plans: the FP64 and float-float FFTs of the Taylor stages in one mixed
-  // pair of launches (fft.cu, launch_fft_mix) instead of two streams
-  bool fft_mix = true;
+  // pair of launches (fft.cu, launch_fft_mix) instead of two streams: 0 never,
+  // 1 at N >= kFftMixMinN (the default), 2 at every four-step length
+  int fft_mix = 1;
   long long tma_wait = 1ll << 32;  // SM cycles a staged pass waits for a tile copy
   void* arena = nullptr; // single device allocation holding everything above
   size_t ws_bytes = 0;

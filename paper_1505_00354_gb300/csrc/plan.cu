@@ -1212,13 +1212,14 @@ int run_leg2cheb(Plan& P, const T* c, T* chat, int64_t nb) {
 
 // The FP64 and float-float FFTs of a Taylor stage (inputs in bufA / bufAff):
 // one mixed pair of launches when both kinds have vectors at a four-step size
-// (FP64 plans, fft_mix on), else the float-float ones on the side stream beside
+// (FP64 plans, by the fft_mix mode and N), else the float-float ones on the side stream beside
 // the FP64 ones.  Results: *y (the FP64 buffer the passes end in), *yff.
 template <typename T>
 int taylor_ffts(Plan& P, int64_t n64, int64_t nff, int dir, const void** y, const ffc** yff) {
   *yff = nullptr;
   if constexpr (is_f64<T>) {
-    if (P.fft_mix && nff > 0 && n64 > 0 && P.p.N > 4096) {
+    const bool mix = P.fft_mix == 2 || (P.fft_mix == 1 && P.p.N >= kFftMixMinN);
+    if (mix && nff > 0 && n64 > 0 && P.p.N > 4096) {
       launch_fft_mix(P, P.bufA, P.bufB, n64, P.bufAff, P.bufBff, nff, dir);
       *y = P.bufB;
       *yff = (const ffc*)P.bufBff;
@@ -1902,17 +1903,17 @@ int gbdlt_plan_set_fft_staging(gbdlt_plan plan, int enable) {
   return GBDLT_OK;
 }
 
-int gbdlt_plan_set_fft_mix(gbdlt_plan plan, int enable) {
-  if (!plan || (enable != 0 && enable != 1)) return GBDLT_ERR_INVALID_ARG;
+int gbdlt_plan_set_fft_mix(gbdlt_plan plan, int mode) {
+  if (!plan || mode < 0 || mode > 2) return GBDLT_ERR_INVALID_ARG;
   Plan* P = reinterpret_cast<Plan*>(plan);
-  if (P->fft_mix == (enable != 0)) return GBDLT_OK;
+  if (P->fft_mix == mode) return GBDLT_OK;
   // replayed chains hold the launches they were captured with
   if (P->graphs) {
     if (cudaStreamSynchronize(P->graphs->s) != cudaSuccess) return GBDLT_ERR_CUDA;
     free_graphs(P);
   }
-  P->fft_mix = enable != 0;
-  if (P->inner) P->inner->fft_mix = enable != 0;
+  P->fft_mix = mode;
+  if (P->inner) P->inner->fft_mix = mode;
   return GBDLT_OK;
 }
 

@@ -524,8 +524,14 @@ def test_fft_mix_bitwise(gb, N):
     p = gb.Plan(N, method=gb.METHOD_FAST)
     x = dev(np.stack([inp.coeffs(N, 60, 1.0), inp.coeffs(N, 61)]))
     ops = ("dlt", "idlt", "dlt_t", "idlt_t", "chebeval", "chebeval_t")
-    p.set_fft_mix(False)
+    p.set_fft_mix(0)
     ref = {op: getattr(p, op)(x).clone() for op in ops}
-    p.set_fft_mix(True)
+    p.set_fft_mix(2)
     for op in ops:
         assert torch.equal(getattr(p, op)(x), ref[op]), op
+    p.set_fft_mix(1)  # the default: mixed from 2^20 up
+    for op in ops:
+        assert torch.equal(getattr(p, op)(x), ref[op]), op
+    for bad in (-1, 3):
+        with pytest.raises(gb.GbdltError):
+            gb._binding._check(gb.lib().gbdlt_plan_set_fft_mix(p.handle, bad), "set_fft_mix")
