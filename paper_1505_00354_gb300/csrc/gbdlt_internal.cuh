@@ -267,6 +267,13 @@ struct RecLayout {
   int64_t* poff = nullptr;    // [H] offset of row k's segments
   int32_t* cta_rb = nullptr;  // [ncta]
   int32_t* cta_j = nullptr;   // [ncta] first segment j, A - 1 << 16, q - 1 << 20 (rec.cu, RecTask)
+  // forward recurrence: the (segment, row) pairs of each row block packed into
+  // full warps (rec.cu, k_rec_fwd): nfw warps of fwpc per CTA, per warp its row
+  // block, per lane its row within the block | segment << 8 (-1: none)
+  int64_t nfw = 0;
+  int fwpc = 8;
+  int32_t* fw_rb = nullptr;   // [nfw]
+  int32_t* fw_lane = nullptr; // [32 nfw]
   int64_t* toff = nullptr;    // [nblocks] offset of row block partials (length nseg_max*S)
   int32_t* bcutmax = nullptr; // [nblocks] nseg_max(rb) * S (partial array length)
   double* xm1 = nullptr;      // [H] x_k - 1 of the rows (cheb1 grid, or Legendre nodes)

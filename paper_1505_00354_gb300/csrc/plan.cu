@@ -576,7 +576,7 @@ namespace {
 // stores its segments j0 .. nseg-1, and a row block's transposed partials cover
 // columns [j0 S, nseg_max S).
 struct LayoutHost {
-  std::vector<int32_t> cut, cta_rb, cta_j, maxcut;
+  std::vector<int32_t> cut, cta_rb, cta_j, maxcut, fw_rb, fw_lane;
   std::vector<int64_t> poff, toff;
 };
 
@@ -616,6 +616,33 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
     if (!pack || (int64_t)h.cta_rb.size() * batch >= 2 * (int64_t)sms) break;
   }
   R.ncta = (int64_t)h.cta_rb.size();
+  // the forward recurrence's warps: per row block the pairs (segment j >= j0,
+  // row r) with r up to the last row whose cut reaches segment j, segment by
+  // segment, 32 to a warp (a block's last warp padded with -1), so that a
+  // segment whose active rows do not fill whole warps shares warps with the
+  // next; as many warps per CTA (8, 4, 2 or 1) as leave two CTAs per SM over
+  // the plan's batch
+  h.fw_rb.clear();
+  h.fw_lane.clear();
+  for (int64_t rb = 0; rb < R.nblocks; ++rb) {
+    const int64_t r0 = rb * 256, r1 = std::min<int64_t>(H, rb * 256 + 256);
+    int64_t nsm = 0;
+    for (int64_t k = r0; k < r1; ++k) nsm = std::max<int64_t>(nsm, (h.cut[(size_t)k] + S - 1) / S);
+    std::vector<int> lastr((size_t)std::max<int64_t>(nsm, 1), -1);
+    for (int64_t k = r0; k < r1; ++k) {
+      const int64_t ns = (h.cut[(size_t)k] + S - 1) / S;
+      if (ns > 0) lastr[(size_t)ns - 1] = std::max(lastr[(size_t)ns - 1], (int)(k - r0));
+    }
+    for (int64_t j = nsm - 2; j >= 0; --j) lastr[(size_t)j] = std::max(lastr[(size_t)j], lastr[(size_t)j + 1]);
+    const size_t first = h.fw_lane.size();
+    for (int64_t j = j0; j < nsm; ++j)
+      for (int r = 0; r <= lastr[(size_t)j]; ++r) h.fw_lane.push_back((int32_t)(r | (j << 8)));
+    while ((h.fw_lane.size() - first) % 32) h.fw_lane.push_back(-1);
+    for (size_t w = first / 32; w < h.fw_lane.size() / 32; ++w) h.fw_rb.push_back((int32_t)rb);
+  }
+  R.nfw = (int64_t)h.fw_rb.size();
+  R.fwpc = 8;
+  while (R.fwpc > 1 && ((R.nfw + R.fwpc - 1) / R.fwpc) * batch < 2 * (int64_t)sms) R.fwpc /= 2;
   // the transposed reduction relies on row blocks in order of non-increasing cut
   // (true by construction: full rows first, then bands of decreasing cut)
   std::vector<int32_t> mc = h.maxcut;
@@ -652,7 +679,7 @@ void build_ctas(RecLayout& R, int64_t H, int S, int j0, int pack, LayoutHost& h)
 }
 
 struct LayoutOff {
-  size_t cut, poff, crb, cj, toff, mc, xm1, state, part, tbuf, rscr;
+  size_t cut, poff, crb, cj, fwrb, fwl, toff, mc, xm1, state, part, tbuf, rscr;
 };
 
 }  // namespace
@@ -866,6 +893,8 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     o.poff = A.take<int64_t>(L.H);
     o.crb = A.take<int32_t>(L.ncta);
     o.cj = A.take<int32_t>(L.ncta);
+    o.fwrb = A.take<int32_t>(L.nfw);
+    o.fwl = A.take<int32_t>(32 * L.nfw);
     o.toff = A.take<int64_t>(L.nblocks);
     o.mc = A.take<int32_t>(L.nblocks);
     o.xm1 = A.take<double>(L.H);
@@ -949,6 +978,8 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     L.poff = (int64_t*)(base + o.poff);
     L.cta_rb = (int32_t*)(base + o.crb);
     L.cta_j = (int32_t*)(base + o.cj);
+    L.fw_rb = (int32_t*)(base + o.fwrb);
+    L.fw_lane = (int32_t*)(base + o.fwl);
     L.toff = (int64_t*)(base + o.toff);
     L.bcutmax = (int32_t*)(base + o.mc);
     L.xm1 = (double*)(base + o.xm1);
@@ -1042,6 +1073,8 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     up(L.poff, h.poff.data(), sizeof(int64_t) * (size_t)L.H);
     up(L.cta_rb, h.cta_rb.data(), sizeof(int32_t) * h.cta_rb.size());
     up(L.cta_j, h.cta_j.data(), sizeof(int32_t) * h.cta_j.size());
+    up(L.fw_rb, h.fw_rb.data(), sizeof(int32_t) * h.fw_rb.size());
+    up(L.fw_lane, h.fw_lane.data(), sizeof(int32_t) * h.fw_lane.size());
     up(L.toff, h.toff.data(), sizeof(int64_t) * h.toff.size());
     up(L.bcutmax, h.maxcut.data(), sizeof(int32_t) * h.maxcut.size());
   };

@@ -50,6 +50,9 @@ struct RecArgs {
   const double2* state;
   const int32_t* cta_rb;
   const int32_t* cta_j;
+  const int32_t* fw_rb;    // forward warps: row block per warp
+  const int32_t* fw_lane;  // forward warps: row | segment << 8 per lane (-1: none)
+  int64_t nfw;
   const int64_t* toff;
   const int32_t* maxcut;
   const double* ra;
@@ -129,6 +132,9 @@ RecArgs rec_args(const Plan& P, const RecLayout& L) {
   a.state = L.state;
   a.cta_rb = L.cta_rb;
   a.cta_j = L.cta_j;
+  a.fw_rb = L.fw_rb;
+  a.fw_lane = L.fw_lane;
+  a.nfw = L.nfw;
   a.toff = L.toff;
   a.maxcut = L.bcutmax;
   a.xm1 = L.xm1;
@@ -251,16 +257,13 @@ __global__ void k_rec_scan(RecArgs R, const double2* __restrict__ Tbuf, double2*
   }
 }
 
-// forward: per (half row, segment) the partial sums E (even n) and O (odd n) of
-// the thread's row in CTA `cta` of the layout; false when the thread has none
-// (o: its slot in the partial array)
+// forward: the partial sums E (even n) and O (odd n) of half row k over segment
+// j; false when the row's cut ends before the segment (o: its slot in the
+// partial array).  rec_fwd_body takes the thread's (k, j) from CTA `cta` of the
+// layout's CTA list.
 template <typename T>
-__device__ __forceinline__ bool rec_fwd_body(const RecArgs& R, int64_t cta, const T* __restrict__ c, int64_t& o,
-                                             double2& EO) {
-  const RecTask t = rec_task(R, cta);
-  const int64_t k = t.k;
-  const int j = t.j;
-  if (!t.in || k >= R.H) return false;
+__device__ __forceinline__ bool rec_fwd_row(const RecArgs& R, int64_t k, int j, const T* __restrict__ c, int64_t& o,
+                                            double2& EO) {
   const int cut = R.cut[k];
   if (j >= (cut + R.S - 1) / R.S) return false;
   o = R.poff[k] + j - R.j0;
@@ -283,15 +286,18 @@ __device__ __forceinline__ bool rec_fwd_body(const RecArgs& R, int64_t cta, cons
   EO = make_double2(E, O);
   return true;
 }
+template <typename T>
+__device__ __forceinline__ bool rec_fwd_body(const RecArgs& R, int64_t cta, const T* __restrict__ c, int64_t& o,
+                                             double2& EO) {
+  const RecTask t = rec_task(R, cta);
+  if (!t.in || t.k >= R.H) return false;
+  return rec_fwd_row<T>(R, t.k, t.j, c, o, EO);
+}
 
 // FP32 form: the same segment sums with the recurrence in float-float and the
 // products c_n P_n accumulated in Kahan-compensated float
-__device__ __forceinline__ bool rec_fwd_body_ff(const RecArgs& R, int64_t cta, const float* __restrict__ c,
-                                                int64_t& o, double2& EO) {
-  const RecTask t = rec_task(R, cta);
-  const int64_t k = t.k;
-  const int j = t.j;
-  if (!t.in || k >= R.H) return false;
+__device__ __forceinline__ bool rec_fwd_row_ff(const RecArgs& R, int64_t k, int j, const float* __restrict__ c,
+                                               int64_t& o, double2& EO) {
   const int cut = R.cut[k];
   if (j >= (cut + R.S - 1) / R.S) return false;
   o = R.poff[k] + j - R.j0;
@@ -314,24 +320,47 @@ __device__ __forceinline__ bool rec_fwd_body_ff(const RecArgs& R, int64_t cta, c
   EO = make_double2((double)Es - (double)Ec, (double)Os - (double)Oc);
   return true;
 }
+__device__ __forceinline__ bool rec_fwd_body_ff(const RecArgs& R, int64_t cta, const float* __restrict__ c,
+                                                int64_t& o, double2& EO) {
+  const RecTask t = rec_task(R, cta);
+  if (!t.in || t.k >= R.H) return false;
+  return rec_fwd_row_ff(R, t.k, t.j, c, o, EO);
+}
 
+// The (half row, segment) of a thread of the packed forward launch (blockDim.x
+// = 32 x warps per CTA): false when its lane has none
+__device__ __forceinline__ bool fwd_pair(const RecArgs& R, int64_t& k, int& j) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw >= R.nfw) return false;
+  const int code = R.fw_lane[gw * 32 + (threadIdx.x & 31)];
+  if (code < 0) return false;
+  k = (int64_t)R.fw_rb[gw] * RT + (code & 255);
+  j = code >> 8;
+  return k < R.H;
+}
+
+// The forward recurrence over the packed (row, segment) pairs: each thread the
+// partial sums of one row over one segment (the same arithmetic, in the same
+// order, as a thread of the per-segment CTAs of the layout's CTA list).
 template <typename T>
 __global__ void __launch_bounds__(RT) k_rec_fwd(RecArgs R, const T* __restrict__ c,
                                                 double2* __restrict__ part) {
   c += (int64_t)blockIdx.y * R.N;
   part += (int64_t)blockIdx.y * R.nseg_total;
-  int64_t o;
+  int64_t k, o;
+  int j;
   double2 EO;
-  if (rec_fwd_body<T>(R, blockIdx.x, c, o, EO)) part[o] = EO;
+  if (fwd_pair(R, k, j) && rec_fwd_row<T>(R, k, j, c, o, EO)) part[o] = EO;
 }
 
 __global__ void __launch_bounds__(RT) k_rec_fwd_ff(RecArgs R, const float* __restrict__ c,
                                                    double2* __restrict__ part) {
   c += (int64_t)blockIdx.y * R.N;
   part += (int64_t)blockIdx.y * R.nseg_total;
-  int64_t o;
+  int64_t k, o;
+  int j;
   double2 EO;
-  if (rec_fwd_body_ff(R, blockIdx.x, c, o, EO)) part[o] = EO;
+  if (fwd_pair(R, k, j) && rec_fwd_row_ff(R, k, j, c, o, EO)) part[o] = EO;
 }
 
 // sum of a half row's segment partials; warp per row for rows [r0, r1) when
@@ -749,11 +778,12 @@ int launch_rec_forward(Plan& P, RecLayout& L, const T* c, T* vrec, int64_t nb) {
   RecArgs R = rec_args(P, L);
   if (L.H == 0) return GBDLT_OK;
   // (no segments at all when the head block and the bands cover every column)
-  if (L.ncta > 0) {
+  if (L.nfw > 0) {
+    const dim3 grid((unsigned)((L.nfw + L.fwpc - 1) / L.fwpc), (unsigned)nb);
     if constexpr (sizeof(T) == 4) {
-      k_rec_fwd_ff<<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, (const float*)c, L.part);
+      k_rec_fwd_ff<<<grid, 32 * L.fwpc, 0, P.stream>>>(R, (const float*)c, L.part);
     } else {
-      k_rec_fwd<T><<<dim3((unsigned)L.ncta, (unsigned)nb), RT, 0, P.stream>>>(R, c, L.part);
+      k_rec_fwd<T><<<grid, 32 * L.fwpc, 0, P.stream>>>(R, c, L.part);
     }
     launched(P, "rec_fwd", (double)nb * 7.0 * (double)L.half_steps,
              (double)nb * ((double)sizeof(T) * P.p.N + 32.0 * (double)L.nseg_total));
