@@ -55,6 +55,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
+# FP64 instructions per algorithmic flop of the kernels whose flop count mixes
+# multiplies and fused multiply-adds: a recurrence step is one multiply and three
+# fused multiply-adds (7 flops, 4 FP64-pipe instructions)
+FP64_INST_PER_FLOP = {"rec_t": 4.0 / 7.0, "rec_fwd": 4.0 / 7.0}
 
 # DRAM traffic per launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) and the hash of the kernel sources it was taken with;
@@ -68,10 +72,10 @@ TRAFFIC = {
     # each launch's input is still in the L2 from the kernel before it)
     "fft_cols": {"dram_per_algorithmic_byte": 200.924416 / 268.435456,
                  "files": ("fft.cu", ("gbdlt_internal.cuh", "// plan")), "src": "f193e2e2f2413596"},
-    # k_rec_t<double>: 20.07 MB per launch against 21.06 MB algorithmic (z once,
+    # k_rec_t<double>: 20.06 MB per launch against 21.06 MB algorithmic (z once,
     # the segment states and the block partials)
-    "rec_t": {"dram_per_algorithmic_byte": 20.06656 / 21.0636,
-              "files": ("rec.cu", ("gbdlt_internal.cuh", "// plan")), "src": "a643d8402d287f9a"},
+    "rec_t": {"dram_per_algorithmic_byte": 20.064256 / 21.0636,
+              "files": ("rec.cu", ("gbdlt_internal.cuh", "// plan")), "src": "3c0d2e1af3bfe948"},
 }
 
 
@@ -530,6 +534,12 @@ def run_gpu(args, world, rank, local):
                     "frac_of_probe": round(achieved / (fp64_probe / 1e12), 4) if fp64_probe > 0 else None,
                     "timing": "CUDA events after every launch on the plan stream, over K profiled steps "
                               "run right after the timed steps (serial kernel order)"}
+        if name in FP64_INST_PER_FLOP:
+            # the same measurement in FP64-pipe instruction slots (2 per SM and clock)
+            inst = FP64_INST_PER_FLOP[name] * d["flops"] / d["launches"]
+            slots = per_launch_ms / 1e3 * FP64_PEAK_TFLOPS * 1e12 / 2.0
+            roofline["fp64_pipe_slots"] = {"algorithmic_inst_per_launch": round(inst),
+                                           "frac": round(inst / slots, 4)}
         total_prof = sum(v["ms"] for v in prof.values())
         breakdown = {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
                          "share": round(v["ms"] / total_prof, 4),
