@@ -274,6 +274,19 @@ struct RecLayout {
   int fwpc = 8;
   int32_t* fw_rb = nullptr;   // [nfw]
   int32_t* fw_lane = nullptr; // [32 nfw]
+  // transposed recurrence of fast layouts (rec.cu, k_rec_tp): ntw warps of twpc
+  // per CTA over the (row, segment) pairs ordered by segment; per lane its half
+  // row and slot (-1: none), per slot its segment and S column sums per batch
+  // item, per segment j >= j0 its first slot (tsegs + 1 entries)
+  int64_t ntw = 0;
+  int twpc = 8;
+  int64_t tslots = 0;
+  int tsegs = 0;
+  int32_t* tw_k = nullptr;       // [32 ntw]
+  int32_t* tw_slot = nullptr;    // [32 ntw]
+  int32_t* tslot_j = nullptr;    // [tslots]
+  int32_t* tseg_begin = nullptr; // [tsegs + 1]
+  double* tpart = nullptr;       // [batch][tslots][S]
   int64_t* toff = nullptr;    // [nblocks] offset of row block partials (length nseg_max*S)
   int32_t* bcutmax = nullptr; // [nblocks] nseg_max(rb) * S (partial array length)
   double* xm1 = nullptr;      // [H] x_k - 1 of the rows (cheb1 grid, or Legendre nodes)

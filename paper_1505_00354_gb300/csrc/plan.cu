@@ -577,13 +577,14 @@ namespace {
 // columns [j0 S, nseg_max S).
 struct LayoutHost {
   std::vector<int32_t> cut, cta_rb, cta_j, maxcut, fw_rb, fw_lane;
+  std::vector<int32_t> tw_k, tw_slot, tslot_j, tseg_begin;
   std::vector<int64_t> poff, toff;
 };
 
 void build_ctas(RecLayout& R, int64_t H, int S, int j0, int pack, LayoutHost& h);
 
 void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int j0, int sms, int64_t batch,
-                  LayoutHost& h) {
+                  bool packed_t, LayoutHost& h) {
   R.H = H;
   R.S = S;
   R.j0 = j0;
@@ -624,6 +625,7 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
   // the plan's batch
   h.fw_rb.clear();
   h.fw_lane.clear();
+  std::vector<std::vector<int>> lastr_rb((size_t)R.nblocks);  // per row block, per segment: last row
   for (int64_t rb = 0; rb < R.nblocks; ++rb) {
     const int64_t r0 = rb * 256, r1 = std::min<int64_t>(H, rb * 256 + 256);
     int64_t nsm = 0;
@@ -639,6 +641,54 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
       for (int r = 0; r <= lastr[(size_t)j]; ++r) h.fw_lane.push_back((int32_t)(r | (j << 8)));
     while ((h.fw_lane.size() - first) % 32) h.fw_lane.push_back(-1);
     for (size_t w = first / 32; w < h.fw_lane.size() / 32; ++w) h.fw_rb.push_back((int32_t)rb);
+    if (nsm > j0) lastr_rb[(size_t)rb] = std::move(lastr);
+  }
+  // the transposed recurrence's warps (fast layouts): the pairs (half row k,
+  // segment j) ordered by segment, then row block, then row, 32 to a warp; a
+  // warp's lanes of one segment form a run, and every run has a slot of S
+  // column sums (tpart), so that the slots of segment j are the contiguous range
+  // tseg_begin[j - j0] .. tseg_begin[j - j0 + 1] (rec.cu, k_rec_tp)
+  h.tw_k.clear();
+  h.tw_slot.clear();
+  h.tslot_j.clear();
+  h.tseg_begin.clear();
+  R.ntw = R.tslots = 0;
+  R.tsegs = 0;
+  if (packed_t) {
+    std::vector<int64_t> act;  // row blocks that run segments
+    int64_t jmax = j0;
+    for (int64_t rb = 0; rb < R.nblocks; ++rb)
+      if (!lastr_rb[(size_t)rb].empty()) {
+        act.push_back(rb);
+        jmax = std::max<int64_t>(jmax, (int64_t)lastr_rb[(size_t)rb].size());
+      }
+    int32_t slot = -1, last_j = -1;
+    for (int64_t j = j0; j < jmax; ++j) {
+      h.tseg_begin.push_back(slot + 1);
+      for (int64_t rb : act) {
+        const std::vector<int>& lr = lastr_rb[(size_t)rb];
+        if (j >= (int64_t)lr.size()) continue;
+        for (int r = 0; r <= lr[(size_t)j]; ++r) {
+          if (h.tw_k.size() % 32 == 0 || last_j != (int32_t)j) {
+            h.tslot_j.push_back((int32_t)j);
+            ++slot;
+          }
+          last_j = (int32_t)j;
+          h.tw_k.push_back((int32_t)(rb * 256 + r));
+          h.tw_slot.push_back(slot);
+        }
+      }
+    }
+    h.tseg_begin.push_back(slot + 1);
+    while (h.tw_k.size() % 32) {
+      h.tw_k.push_back(-1);
+      h.tw_slot.push_back(-1);
+    }
+    R.ntw = (int64_t)h.tw_k.size() / 32;
+    R.tslots = (int64_t)h.tslot_j.size();
+    R.tsegs = (int)(jmax - j0);
+    R.twpc = 8;
+    while (R.twpc > 1 && ((R.ntw + R.twpc - 1) / R.twpc) * batch < 2 * (int64_t)sms) R.twpc /= 2;
   }
   R.nfw = (int64_t)h.fw_rb.size();
   R.fwpc = 8;
@@ -679,7 +729,7 @@ void build_ctas(RecLayout& R, int64_t H, int S, int j0, int pack, LayoutHost& h)
 }
 
 struct LayoutOff {
-  size_t cut, poff, crb, cj, fwrb, fwl, toff, mc, xm1, state, part, tbuf, rscr;
+  size_t cut, poff, crb, cj, fwrb, fwl, twk, tws, tsj, tsb, tpart, toff, mc, xm1, state, part, tbuf, rscr;
 };
 
 }  // namespace
@@ -783,12 +833,12 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     std::vector<int32_t> cut((size_t)std::max<int64_t>(H, 1), (int32_t)N);
     for (const Band& b : prm.bands)
       for (int64_t k = b.ka; k < b.kb; ++k) cut[(size_t)k] = (int32_t)b.ns;
-    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), sms, batch_hint, hf);
+    layout_build(P->rec, H, prm.seg, std::move(cut), (int)(prm.head / prm.seg), sms, batch_hint, true, hf);
   }
   P->has_direct = N > 1 && N <= kDirectMax && (prm.method == GBDLT_METHOD_DIRECT || want_direct);
   if (P->has_direct) {
     const int64_t H = (N + 1) / 2;
-    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, sms, batch_hint, hd);
+    layout_build(P->drec, H, prm.seg, std::vector<int32_t>((size_t)H, (int32_t)N), 0, sms, batch_hint, false, hd);
   }
   RecLayout& R = P->rec;
   RecLayout& D = P->drec;
@@ -831,7 +881,8 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     const double per_item = 2.0 * P->nfft_max * N * cs + 2.0 * nfft32 * N * 8.0 + 2.0 * nfftff * N * 16.0 +
                             5.0 * N * ts +
                             16.0 * (R.nseg_total + D.nseg_total) +
-                            8.0 * (R.tbuf_total + D.tbuf_total) + 8.0 * (double)rb_part;
+                            8.0 * (R.tbuf_total + D.tbuf_total) + 8.0 * (double)rb_part +
+                            8.0 * (double)R.tslots * R.S;
     P->bcap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(512.0 * (1 << 20) / per_item)));
     if (max_batch > 0) P->bcap = std::min<int64_t>(P->bcap, max_batch);
   }
@@ -895,6 +946,11 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     o.cj = A.take<int32_t>(L.ncta);
     o.fwrb = A.take<int32_t>(L.nfw);
     o.fwl = A.take<int32_t>(32 * L.nfw);
+    o.twk = A.take<int32_t>(32 * L.ntw);
+    o.tws = A.take<int32_t>(32 * L.ntw);
+    o.tsj = A.take<int32_t>(L.tslots);
+    o.tsb = A.take<int32_t>(L.tsegs + 1);
+    o.tpart = A.take<double>(BC * L.tslots * L.S);
     o.toff = A.take<int64_t>(L.nblocks);
     o.mc = A.take<int32_t>(L.nblocks);
     o.xm1 = A.take<double>(L.H);
@@ -980,6 +1036,11 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     L.cta_j = (int32_t*)(base + o.cj);
     L.fw_rb = (int32_t*)(base + o.fwrb);
     L.fw_lane = (int32_t*)(base + o.fwl);
+    L.tw_k = (int32_t*)(base + o.twk);
+    L.tw_slot = (int32_t*)(base + o.tws);
+    L.tslot_j = (int32_t*)(base + o.tsj);
+    L.tseg_begin = (int32_t*)(base + o.tsb);
+    L.tpart = (double*)(base + o.tpart);
     L.toff = (int64_t*)(base + o.toff);
     L.bcutmax = (int32_t*)(base + o.mc);
     L.xm1 = (double*)(base + o.xm1);
@@ -1075,6 +1136,10 @@ static int plan_build(const Params& prm, cudaStream_t stream, int64_t max_batch,
     up(L.cta_j, h.cta_j.data(), sizeof(int32_t) * h.cta_j.size());
     up(L.fw_rb, h.fw_rb.data(), sizeof(int32_t) * h.fw_rb.size());
     up(L.fw_lane, h.fw_lane.data(), sizeof(int32_t) * h.fw_lane.size());
+    up(L.tw_k, h.tw_k.data(), sizeof(int32_t) * h.tw_k.size());
+    up(L.tw_slot, h.tw_slot.data(), sizeof(int32_t) * h.tw_slot.size());
+    up(L.tslot_j, h.tslot_j.data(), sizeof(int32_t) * h.tslot_j.size());
+    up(L.tseg_begin, h.tseg_begin.data(), sizeof(int32_t) * h.tseg_begin.size());
     up(L.toff, h.toff.data(), sizeof(int64_t) * h.toff.size());
     up(L.bcutmax, h.maxcut.data(), sizeof(int32_t) * h.maxcut.size());
   };

@@ -53,6 +53,12 @@ struct RecArgs {
   const int32_t* fw_rb;    // forward warps: row block per warp
   const int32_t* fw_lane;  // forward warps: row | segment << 8 per lane (-1: none)
   int64_t nfw;
+  const int32_t* tw_k;        // transposed warps: half row per lane (-1: none)
+  const int32_t* tw_slot;     // transposed warps: slot per lane (-1: none)
+  const int32_t* tslot_j;     // segment of each slot
+  const int32_t* tseg_begin;  // first slot of each segment j >= j0
+  int64_t ntw, tslots;
+  int tsegs;
   const int64_t* toff;
   const int32_t* maxcut;
   const double* ra;
@@ -135,6 +141,13 @@ RecArgs rec_args(const Plan& P, const RecLayout& L) {
   a.fw_rb = L.fw_rb;
   a.fw_lane = L.fw_lane;
   a.nfw = L.nfw;
+  a.tw_k = L.tw_k;
+  a.tw_slot = L.tw_slot;
+  a.tslot_j = L.tslot_j;
+  a.tseg_begin = L.tseg_begin;
+  a.ntw = L.ntw;
+  a.tslots = L.tslots;
+  a.tsegs = L.tsegs;
   a.toff = L.toff;
   a.maxcut = L.bcutmax;
   a.xm1 = L.xm1;
@@ -594,6 +607,189 @@ __global__ void __launch_bounds__(RT) k_rec_t_ff(RecArgs R, const float* __restr
   }
 }
 
+// Transposed recurrence over packed (row, segment) pairs (fast layouts).  The
+// pairs come ordered by segment, 32 to a warp, so a warp's lanes form runs of
+// one segment each (several when a segment's active rows do not fill whole
+// warps) and no lane idles where another segment has rows.  Per 32-column chunk
+// (the same relative columns c0 .. c0 + 31 in every run) each lane writes its
+// 32 values P_n(x_k) into its warp's tile; then lane i forms, per run, the dot
+// product of tile column i over the run's rows with their weights and stores it
+// in the run's slot.  Only warp-level synchronisation is used.  k_rec_tp_reduce
+// adds a column's slots in slot order.  Row weights as in k_rec_t (z_k +
+// z_{N-1-k} for even n, z_k - z_{N-1-k} for odd n: segments start at multiples
+// of 32, so the parity of lane i's column is that of i).
+struct TpLane {
+  int64_t k;
+  int j, slot, rc;  // segment, slot, columns of the segment below the row's cut
+  bool active;
+};
+__device__ __forceinline__ TpLane tp_lane(const RecArgs& R, int64_t gw, int lane) {
+  TpLane t;
+  t.k = gw < R.ntw ? R.tw_k[gw * 32 + lane] : -1;
+  t.slot = gw < R.ntw ? R.tw_slot[gw * 32 + lane] : -1;
+  t.j = t.slot >= 0 ? R.tslot_j[t.slot] : 0;
+  t.rc = 0;
+  t.active = false;
+  if (t.k >= 0 && t.k < R.H && t.slot >= 0) {
+    const int cut = R.cut[t.k];
+    if (t.j < (cut + R.S - 1) / R.S) {
+      t.active = true;
+      t.rc = min(cut - t.j * R.S, R.S);
+    }
+  }
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_rec_tp(RecArgs R, const T* __restrict__ z, double* __restrict__ tpart) {
+  z += (int64_t)blockIdx.y * R.N;
+  tpart += (int64_t)blockIdx.y * R.tslots * R.S;
+  extern __shared__ double sm[];
+  const int wpc = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * wpc + w;
+  if (gw >= R.ntw) return;  // whole warp: only warp-level synchronisation below
+  double* tile = sm + w * 32 * TP;
+  double2* zt = reinterpret_cast<double2*>(sm + wpc * 32 * TP) + w * 32;
+  const TpLane t = tp_lane(R, gw, lane);
+  double zp = 0.0, zm = 0.0, P = 0.0, G = 0.0, xm1 = 0.0;
+  if (t.active) {
+    double a = (double)z[t.k], b = (double)z[R.N - 1 - t.k];
+    if (R.zw) {
+      a *= R.zw[t.k];
+      b *= R.zw[R.N - 1 - t.k];
+    }
+    zp = t.k == R.mid ? a : a + b;
+    zm = t.k == R.mid ? a : a - b;
+    const double2 st = R.state[R.poff[t.k] + t.j - R.j0];
+    xm1 = R.xm1[t.k];
+    P = st.x;
+    G = st.y / xm1;
+  }
+  zt[lane] = make_double2(zp, zm);
+  const unsigned full = 0xffffffffu;
+  const int prev = __shfl_up_sync(full, t.slot, 1);
+  const unsigned starts = __ballot_sync(full, lane == 0 || t.slot != prev);
+  const int wrc = __reduce_max_sync(full, t.rc);
+  const int64_t nb0 = (int64_t)t.j * R.S;
+  const double* zw2 = reinterpret_cast<const double*>(zt) + (lane & 1);
+  double* mytile = tile + lane * TP;
+  __syncwarp();
+  for (int c0 = 0; c0 < R.S; c0 += 32) {
+    if (c0 < wrc) {
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        const int64_t n = nb0 + c0 + i;
+        double val = 0.0;
+        if (c0 + i < t.rc) {
+          val = P;
+          G = fma(R.ra[n], P, R.rb[n] * G);
+          P = fma(xm1, G, P);
+        }
+        mytile[i] = val;
+      }
+      __syncwarp();
+    }
+    unsigned m = starts;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int e = m ? __ffs(m) - 1 : 32;
+      const int sl = __shfl_sync(full, t.slot, b);
+      double cs = 0.0;
+      if (c0 < wrc)
+        for (int r = b; r < e; ++r) cs = fma(zw2[2 * r], tile[r * TP + lane], cs);
+      if (sl >= 0) tpart[(int64_t)sl * R.S + c0 + lane] = cs;
+    }
+    __syncwarp();
+  }
+}
+
+// FP32 form of k_rec_tp: recurrence in float-float, products and the run sums in
+// float, slots stored in double
+__global__ void __launch_bounds__(RT) k_rec_tp_ff(RecArgs R, const float* __restrict__ z,
+                                                  double* __restrict__ tpart) {
+  z += (int64_t)blockIdx.y * R.N;
+  tpart += (int64_t)blockIdx.y * R.tslots * R.S;
+  extern __shared__ float smf[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;
+  if (gw >= R.ntw) return;
+  float* tile = smf + w * 32 * TP;
+  const TpLane t = tp_lane(R, gw, lane);
+  float zp = 0.f, zm = 0.f;
+  ffv P = {0.f, 0.f}, D = {0.f, 0.f}, xm1 = {0.f, 0.f};
+  if (t.active) {
+    float a = z[t.k], b = z[R.N - 1 - t.k];
+    if (R.zw) {
+      a = (float)((double)a * R.zw[t.k]);
+      b = (float)((double)b * R.zw[R.N - 1 - t.k]);
+    }
+    zp = t.k == R.mid ? a : a + b;
+    zm = t.k == R.mid ? a : a - b;
+    const double2 st = R.state[R.poff[t.k] + t.j - R.j0];
+    P = ff_from(st.x);
+    D = ff_from(st.y);
+    xm1 = ff_from(R.xm1[t.k]);
+  }
+  const unsigned full = 0xffffffffu;
+  const int prev = __shfl_up_sync(full, t.slot, 1);
+  const unsigned starts = __ballot_sync(full, lane == 0 || t.slot != prev);
+  const int wrc = __reduce_max_sync(full, t.rc);
+  const int64_t nb0 = (int64_t)t.j * R.S;
+  float* mytile = tile + lane * TP;
+  for (int c0 = 0; c0 < R.S; c0 += 32) {
+    if (c0 < wrc) {
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        const int64_t n = nb0 + c0 + i;
+        float val = 0.f;
+        if (c0 + i < t.rc) {
+          val = ((i & 1) ? zm : zp) * P.hi;
+          D = ff_add(ff_mul_raw(ff_mul_raw(ff_ld(R.raf[n]), xm1), P), ff_mul_raw(ff_ld(R.rbf[n]), D));
+          P = ff_add(P, D);
+        }
+        mytile[i] = val;
+      }
+      __syncwarp();
+    }
+    unsigned m = starts;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int e = m ? __ffs(m) - 1 : 32;
+      const int sl = __shfl_sync(full, t.slot, b);
+      float cs = 0.f;
+      if (c0 < wrc)
+        for (int r = b; r < e; ++r) cs += tile[r * TP + lane];
+      if (sl >= 0) tpart[(int64_t)sl * R.S + c0 + lane] = (double)cs;
+    }
+    __syncwarp();
+  }
+}
+
+// out_n = the sum of segment j = n / S's slots at column n - j S, in slot order
+// (columns below n_lo belong to the dense head block and get 0 here), times n +
+// 1/2 when the chain scales its output
+template <typename T>
+__global__ void k_rec_tp_reduce(RecArgs R, const double* __restrict__ tpart, T* __restrict__ out) {
+  const int64_t bt = blockIdx.y;
+  tpart += bt * R.tslots * R.S;
+  out += bt * R.N;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= R.N) return;
+  double s = 0.0;
+  if (n >= R.n_lo) {
+    const int64_t jj = n / R.S - R.j0;
+    if (jj < R.tsegs) {
+      const int64_t c = n - (n / R.S) * R.S;
+      for (int64_t sl = R.tseg_begin[jj]; sl < R.tseg_begin[jj + 1]; ++sl) s += tpart[sl * R.S + c];
+    }
+  }
+  if (R.scale_out) s *= (double)n + 0.5;
+  out[n] = (T)s;
+}
+
 // Column sums of the row blocks' partials: out_n = sum over row blocks with
 // cut > n of tbuf[toff[rb] + n - n_lo] (row blocks come in order of non-increasing
 // cut, so the contributing blocks are a prefix; columns below n_lo belong to the
@@ -811,6 +1007,32 @@ int launch_rec_transpose(Plan& P, RecLayout& L, const T* z, T* out, int64_t nb, 
   R.zw = zw;
   R.scale_out = scale_out;
   if (L.H == 0) return GBDLT_OK;
+  if (L.ntw > 0) {
+    // fast layouts: the packed launch and its slot reduction
+    const size_t smem_tp = (size_t)L.twpc * 32 * (sizeof(T) * TP + (sizeof(T) == 8 ? 16 : 0));
+    static bool attr_tp = false;
+    const dim3 grid((unsigned)((L.ntw + L.twpc - 1) / L.twpc), (unsigned)nb);
+    if constexpr (sizeof(T) == 4) {
+      if (!attr_tp) {
+        cudaFuncSetAttribute(k_rec_tp_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * 32 * 4 * TP));
+        attr_tp = true;
+      }
+      k_rec_tp_ff<<<grid, 32 * L.twpc, smem_tp, P.stream>>>(R, (const float*)z, L.tpart);
+    } else {
+      if (!attr_tp) {
+        cudaFuncSetAttribute(k_rec_tp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * 32 * (8 * TP + 16)));
+        attr_tp = true;
+      }
+      k_rec_tp<T><<<grid, 32 * L.twpc, smem_tp, P.stream>>>(R, z, L.tpart);
+    }
+    launched(P, "rec_t", (double)nb * 7.0 * (double)L.half_steps,
+             (double)nb * ((double)sizeof(T) * P.p.N + 16.0 * (double)L.nseg_total +
+                           8.0 * (double)L.tslots * L.S));
+    k_rec_tp_reduce<T><<<dim3((unsigned)((P.p.N + 255) / 256), (unsigned)nb), 256, 0, P.stream>>>(R, L.tpart, out);
+    launched(P, "rec_t_reduce", (double)nb * (double)L.tslots * L.S,
+             (double)nb * (8.0 * (double)L.tslots * L.S + (double)sizeof(T) * P.p.N));
+    return check_launch();
+  }
   const size_t smem = sizeof(T) * (8 * 32 * TP + 8 * (size_t)L.S) + (sizeof(T) == 8 ? 16 * RT : 0);
   static bool attr_set = false;
   if (L.ncta > 0) {
