@@ -621,8 +621,9 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
   // row r) with r up to the last row whose cut reaches segment j, segment by
   // segment, 32 to a warp (a block's last warp padded with -1), so that a
   // segment whose active rows do not fill whole warps shares warps with the
-  // next; as many warps per CTA (8, 4, 2 or 1) as leave two CTAs per SM over
-  // the plan's batch
+  // next; CTAs of 2 warps (in CTAs of 8 the 857 CTAs at 2^20 fell 5 or 6 to an
+  // SM and the SMs with 5 idled at the end: 0.811 -> 0.789 ms), 1 where that
+  // would leave fewer than two CTAs per SM over the plan's batch
   h.fw_rb.clear();
   h.fw_lane.clear();
   std::vector<std::vector<int>> lastr_rb((size_t)R.nblocks);  // per row block, per segment: last row
@@ -691,7 +692,7 @@ void layout_build(RecLayout& R, int64_t H, int S, std::vector<int32_t> cut, int 
     while (R.twpc > 1 && ((R.ntw + R.twpc - 1) / R.twpc) * batch < 2 * (int64_t)sms) R.twpc /= 2;
   }
   R.nfw = (int64_t)h.fw_rb.size();
-  R.fwpc = 8;
+  R.fwpc = 2;
   while (R.fwpc > 1 && ((R.nfw + R.fwpc - 1) / R.fwpc) * batch < 2 * (int64_t)sms) R.fwpc /= 2;
   // the transposed reduction relies on row blocks in order of non-increasing cut
   // (true by construction: full rows first, then bands of decreasing cut)
