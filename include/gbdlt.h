@@ -99,7 +99,7 @@ typedef struct {
   int64_t band_ka[GBDLT_MAX_BANDS]; /* rows [ka, kb) and [N-kb, N-ka)          */
   int64_t band_kb[GBDLT_MAX_BANDS];
   int64_t rec_steps;   /* recurrence (row, n) pairs, both halves              */
-  int seg_len;         /* recurrence segment length                           */
+  int seg_len;         /* recurrence segment length of the fast path (512; 256 in FP32 plans) */
   double flops_dlt;    /* modelled arithmetic per DLT (flop)                  */
   double bytes_dlt;    /* algorithmic HBM bytes per DLT: read c, dtheta; write f */
   double bytes_idlt;   /* same for the IDLT (adds the weights)                */

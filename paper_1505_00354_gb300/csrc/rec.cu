@@ -16,8 +16,9 @@
 // directly (no cancellation near x = 1, where the plain form loses ~n^2 u):
 //   D_{n+1} = [(2n+1)(x-1) P_n + n D_n] / (n+1),   P_{n+1} = P_n + D_{n+1},
 //   (P_0, D_0) = (1, 1).
-// Each half row's column range is cut into segments of S = 512 columns; the
-// state (P, D) at every segment start depends only on N, so the plan computes it
+// Each half row's column range is cut into segments of S columns (512; 256 in
+// the fast path of FP32 plans); the state (P, D) at every segment start depends
+// only on N, so the plan computes it
 // once (two basis solutions per segment, then a scan per row) and the transforms
 // run every segment independently.  The FP64 kernels carry G_n = D_n / (x - 1)
 // instead of D_n, which takes one FP64 instruction less per step (FP64 issue is
@@ -418,7 +419,7 @@ __global__ void k_rec_fwd_reduce(RecArgs R, const double2* __restrict__ part, T*
 }
 
 // transposed: out_n = sum_k z_k P_n(x_k) over rows with n < cut(k).  A CTA takes
-// 256 half rows x one segment of S = 512 columns.  Every 32 columns each lane
+// 256 half rows x one segment of S columns.  Every 32 columns each lane
 // writes its 32 values P_n(x_k) (0 past its cut) into its warp's tile; then lane
 // i forms the dot product of tile column i with the warp's 32 row weights (a
 // shared-memory transpose; the weight product rides in the fused multiply-add
