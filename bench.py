@@ -72,10 +72,12 @@ TRAFFIC = {
     # each launch's input is still in the L2 from the kernel before it)
     "fft_cols": {"dram_per_algorithmic_byte": 200.924416 / 268.435456,
                  "files": ("fft.cu", ("gbdlt_internal.cuh", "// plan")), "src": "f193e2e2f2413596"},
-    # k_rec_t<double>: 20.06 MB per launch against 21.06 MB algorithmic (z once,
-    # the segment states and the block partials)
-    "rec_t": {"dram_per_algorithmic_byte": 20.064256 / 21.0636,
-              "files": ("rec.cu", ("gbdlt_internal.cuh", "// plan")), "src": "3c0d2e1af3bfe948"},
+    # k_rec_tp<double> (the transposed recurrence of the FP64 step, profiled as
+    # "rec_t"): 21.85 MB per launch against 47.96 MB algorithmic (z once, the
+    # segment states, and 36.1 MB of slot column sums, which stay in the L2 for
+    # the slot reduction that follows)
+    "rec_t": {"dram_per_algorithmic_byte": 21.854464 / 47.962624,
+              "files": ("rec.cu", ("gbdlt_internal.cuh", "// plan")), "src": "1a4602e16b12125f"},
 }
 
 
