@@ -147,6 +147,10 @@ def test_band_layout_is_consistent(gb, N, prec):
     # band cuts below it
     h = p["head"]
     assert h == 0 or (h % p["seg_len"] == 0 and h <= N // 4)
+    # segments of 512 columns (256 in FP32 plans); head sizes multiples of 512
+    # in both precisions
+    assert p["seg_len"] == (256 if p["prec"] == 1 else 512)
+    assert h % 512 == 0
     assert all(ns >= h for ns, _, _ in bands)
     # recurrence work matches the layout (every row starts at n = head)
     k0 = bands[0][1] if bands else H
