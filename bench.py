@@ -386,7 +386,7 @@ def run_gpu(args, world, rank, local):
     # the FP64 rate an FMA-chain kernel reaches on this device (library probe)
     fp64_probe = g.fp64_fma_rate(stream)
 
-    # ---------------- FP64 form at the benchmark spec's tolerance (1e-12 ||c||_1)
+    # ---------------- FP64 form at the required tolerance (1e-12 ||c||_1)
     plan12, _ = make(g.FP64, 1e-12)
     ms12, _, f12, _ = timed_loop(plan12, c, args.steps, args.warmup)
     t12 = sum(ms12) / len(ms12)

@@ -101,7 +101,7 @@ def test_gradcheck_small(ag):
 def test_fp32_gradients_vs_oracle(ag):
     """The FP32 form through autograd: the DLT's gradient 2 P^T r and the IDLT's
     vector-Jacobian product D_w P D_s g against the oracle, at the FP32 form's
-    bar (5e-6 in the spec normalisation)."""
+    bar (5e-6 in the ||c||_1 normalisation)."""
     import oracle
     N, B = 4096, 4
     nd = oracle.legpts(N)
